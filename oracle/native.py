@@ -1,0 +1,147 @@
+"""ctypes front end of the FP64 C oracle (``ssa_oracle.c``).  Test infrastructure only.
+
+``run`` simulates trajectories exactly as Section 2 and the Gumbel-max equation of Section 3.2
+state them, reads them out on a sample grid (HOLD or the LINEAR interpolation of Section 4.1),
+and, when an upstream gradient dL/dobs is given, returns the straight-through gradient of
+Eqs. 5 and 7 with the waiting-time term of Section 3.1, per trajectory, in float64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HOLD = 0
+LINEAR = 1
+STATUS = {"OK": 0, "ABSORBED": 1, "STEP_CAP": 2, "NEG_COUNT": 3, "OVERFLOW": 4, "BAD_RATE": 5}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ssa_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ssa_oracle.c into liboracle.so with gcc (portable flags; no -march)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Net(ctypes.Structure):
+    _fields_ = [
+        ("n_species", ctypes.c_int32),
+        ("n_reactions", ctypes.c_int32),
+        ("reactants", ctypes.c_void_p),
+        ("stoich_ptr", ctypes.c_void_p),
+        ("stoich_species", ctypes.c_void_p),
+        ("stoich_delta", ctypes.c_void_p),
+        ("n_params", ctypes.c_int32),
+        ("log_rates", ctypes.c_void_p),
+        ("rate_index", ctypes.c_void_p),
+    ]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        p = ctypes.c_void_p
+        i32, i64, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        lib.orc_run.restype = ctypes.c_int
+        lib.orc_run.argtypes = [p, i64, i64, p, i32, f64, p, i32, p, i32, u64, i32, i64, p, f64,
+                                p, p, p, p, p, p, p, i64, p, i32]
+        lib.orc_uniforms.restype = None
+        lib.orc_uniforms.argtypes = [u64, u64, u64, i64, p]
+        lib.orc_philox_blocks.restype = None
+        lib.orc_philox_blocks.argtypes = [u64, p, i64, p]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox_blocks(seed: int, counters: np.ndarray) -> np.ndarray:
+    """Philox4x32-10 of each counter row [n, 4] (uint32) under key (seed_lo, seed_hi)."""
+    lib = _load()
+    ctr = np.ascontiguousarray(counters, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(ctr)
+    lib.orc_philox_blocks(ctypes.c_uint64(seed), _ptr(ctr), ctr.shape[0], _ptr(out))
+    return out
+
+
+def uniforms(seed: int, traj: int, step: int, n_words: int) -> np.ndarray:
+    """The first n_words uniforms of step `step` of trajectory `traj` (u_0 drives tau)."""
+    lib = _load()
+    out = np.zeros(n_words, dtype=np.float64)
+    lib.orc_uniforms(ctypes.c_uint64(seed), ctypes.c_uint64(traj), ctypes.c_uint64(step), n_words, _ptr(out))
+    return out
+
+
+@dataclass
+class OracleResult:
+    obs: np.ndarray            # [n_traj, S, n_obs] float64
+    draws: np.ndarray          # [n_traj] int64, reaction draws including a crossing draw
+    status: np.ndarray         # [n_traj] int32
+    dtheta: np.ndarray | None  # [n_traj, P] float64
+    events: np.ndarray | None  # [n_traj, ev_cap] int32, -1 padded
+    margins: np.ndarray | None # [n_traj, ev_cap] float64
+    times: np.ndarray | None   # [n_traj, ev_cap] t_{k+1} of each draw
+    final_x: np.ndarray        # [n_traj, N] int32, last visited state
+
+
+def run(net, log_rates, x0, n_traj: int, t_end: float, sample_times, obs_species, seed: int,
+        readout: int = HOLD, max_steps: int = 1 << 30, traj_offset: int = 0, dl_dobs=None,
+        temperature: float = 1.0, ev_cap: int = 0, n_threads: int | None = None) -> OracleResult:
+    """Run the oracle. `net` is a ssa_workloads.NetworkSpec; x0 is [N] or [n_traj, N]."""
+    lib = _load()
+    reactants = np.ascontiguousarray(net.reactants, dtype=np.int32)
+    sptr = np.ascontiguousarray(net.stoich_ptr, dtype=np.int32)
+    ssp = np.ascontiguousarray(net.stoich_species, dtype=np.int32)
+    sdl = np.ascontiguousarray(net.stoich_delta, dtype=np.int32)
+    ridx = np.ascontiguousarray(net.rate_index, dtype=np.int32)
+    th = np.ascontiguousarray(log_rates, dtype=np.float64)
+    assert th.shape == (net.n_params,)
+    cnet = _Net(net.n_species, net.n_reactions, _ptr(reactants), _ptr(sptr), _ptr(ssp), _ptr(sdl),
+                net.n_params, _ptr(th), _ptr(ridx))
+    x0 = np.ascontiguousarray(x0, dtype=np.int32)
+    per_traj = 1 if x0.ndim == 2 else 0
+    if per_traj:
+        assert x0.shape == (n_traj, net.n_species)
+    ts = np.ascontiguousarray(sample_times, dtype=np.float64)
+    S = int(ts.shape[0])
+    obs_sp = np.ascontiguousarray(obs_species, dtype=np.int32)
+    n_obs = int(obs_sp.shape[0])
+    obs = np.zeros((n_traj, S, n_obs), dtype=np.float64)
+    draws = np.zeros(n_traj, dtype=np.int64)
+    status = np.zeros(n_traj, dtype=np.int32)
+    final_x = np.zeros((n_traj, net.n_species), dtype=np.int32)
+    dth = None
+    g = None
+    if dl_dobs is not None:
+        g = np.ascontiguousarray(dl_dobs, dtype=np.float64)
+        assert g.shape == (n_traj, S, n_obs)
+        dth = np.zeros((n_traj, net.n_params), dtype=np.float64)
+    ev = mg = tm = None
+    if ev_cap > 0:
+        ev = np.zeros((n_traj, ev_cap), dtype=np.int32)
+        mg = np.zeros((n_traj, ev_cap), dtype=np.float64)
+        tm = np.zeros((n_traj, ev_cap), dtype=np.float64)
+    if n_threads is None:
+        n_threads = min(os.cpu_count() or 1, max(1, n_traj // 8))
+    rc = lib.orc_run(ctypes.byref(cnet), n_traj, traj_offset, _ptr(x0), per_traj, float(t_end),
+                     _ptr(ts), S, _ptr(obs_sp), n_obs, ctypes.c_uint64(seed), readout, max_steps,
+                     _ptr(g), float(temperature), _ptr(obs), _ptr(draws), _ptr(status), _ptr(dth),
+                     _ptr(ev), _ptr(mg), _ptr(tm), ev_cap, _ptr(final_x), int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle rejected its inputs (orc_run returned %d)" % rc)
+    return OracleResult(obs, draws, status, dth, ev, mg, tm, final_x)

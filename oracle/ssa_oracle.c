@@ -1,0 +1,559 @@
+/*
+ * ssa_oracle.c -- plain, slow, FP64 CPU oracle of the exact Gillespie simulation with a
+ * Gumbel-max reaction choice and of its Gumbel-Softmax straight-through gradient.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may link, load or call this file:
+ * only the tests, the smoke check and the benchmark's CPU-baseline leg use it. It shares no
+ * code, header, table or constant generator with the CUDA library.
+ *
+ * What it follows (arXiv 2602.19775):
+ *   - Section 2: mass-action propensities a_j(X; theta) (first order k X_i, hetero second
+ *     order k X_i X_l, homodimer k X_i (X_i - 1)/2, zeroth order k), total rate a0 = sum_j a_j,
+ *     waiting time tau = -ln(u)/a0, update X <- X + v_j.
+ *   - Section 3.2 (the unnumbered Gumbel-max equation): j* = argmax_j [log a_j + G_j],
+ *     G_j = -ln(-ln u_j).
+ *   - Section 3.3, Eq. 3: soft sample y~_j = softmax_j((log a_j + G_j)/T) with the same G.
+ *   - Section 3.4, Eqs. 5-7: y_ST = stopgrad(y - y~) + y~; forward applies v_{j*} (Eq. 6);
+ *     the backward differentiates X_{k+1} = X_k + sum_j y~_j v_j (Eq. 7).
+ *   - Section 3.1: the reparametrised waiting time, d tau/d theta = -(tau/a0) d a0/d theta.
+ *   - Figure 1 caption: the adjoint recursion dL/dX_k = dL/dX_k|direct +
+ *     (dX_ST(k+1)/dX_k)^T dL/dX_{k+1}, with the Gumbel draws held fixed.
+ *   - Section 4.1: each trajectory is linearly interpolated onto a uniform time grid
+ *     (LINEAR readout); the HOLD readout is the right-continuous path value X(t_s).
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   - Noise: counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). Key =
+ *     (seed_lo, seed_hi); counter = (b, k, i_lo, i_hi) for trajectory i, step k and block b.
+ *     Word q of the step's stream is q = 4b + w; u_0 drives tau and u_{1+j} drives reaction j.
+ *     u = ((x >> 9) + 0.5) * 2^-23, which lies strictly inside (0,1) and is exact in binary32.
+ *   - A reaction with a_j = 0 is masked out of the argmax and of the softmax (y~_j = 0 and no
+ *     choice-path gradient); it still enters a0 and therefore the waiting-time gradient through
+ *     the polynomial derivative d a_j/dX.
+ *   - The draw that crosses t_end is made but not applied; with LINEAR readout it supplies
+ *     X_{n+1} for samples after the last event.
+ *   - a0 == 0: the state is absorbing; no further draw.
+ *   - Parameters are log rates: k_j = exp(theta_{r(j)}), several reactions may share one.
+ *
+ * Everything is double precision; event counts are exact integers.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------------------------------- */
+/* Network description (all host pointers, owned by the caller).                             */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t n_species;             /* N */
+    int32_t n_reactions;           /* M */
+    const int32_t *reactants;      /* [M][2]; species index or -1 for an empty slot */
+    const int32_t *stoich_ptr;     /* [M+1]; CSR row pointer of the net change v_j */
+    const int32_t *stoich_species; /* [nnz] */
+    const int32_t *stoich_delta;   /* [nnz] */
+    int32_t n_params;              /* P */
+    const double *log_rates;       /* [P]: theta = log k */
+    const int32_t *rate_index;     /* [M]: reaction j uses theta[rate_index[j]] */
+} orc_network;
+
+enum { ORC_HOLD = 0, ORC_LINEAR = 1 };
+
+/* per-trajectory status codes */
+enum {
+    ORC_OK = 0,           /* reached t_end (the crossing draw was made, not applied) */
+    ORC_ABSORBED = 1,     /* a0 == 0 before t_end: the state holds to t_end           */
+    ORC_STEP_CAP = 2,     /* max_steps draws were made and applied before t_end        */
+    ORC_NEG_COUNT = 3,    /* an update would make a count negative; stopped before it  */
+    ORC_OVERFLOW = 4,     /* an update would leave int32 range; stopped before it      */
+    ORC_BAD_RATE = 5      /* a propensity was not finite                               */
+};
+
+/* ---------------------------------------------------------------------------------------- */
+/* Philox4x32-10, from the published definition (Salmon et al., SC'11, Section 4):           */
+/* ten rounds of two 32x32->64 multiplications with round keys bumped by the Weyl constants.  */
+/* ---------------------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* u = ((x >> 9) + 1/2) * 2^-23, strictly inside (0,1). */
+static double orc_u01(uint32_t x)
+{
+    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+/* Uniform number q of step k of trajectory i (q = 0 drives tau, q = 1 + j drives reaction j). */
+static double orc_uniform(uint64_t seed, uint64_t traj, uint64_t step, int64_t q)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)(q / 4), (uint32_t)step, (uint32_t)traj, (uint32_t)(traj >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return orc_u01(out[q % 4]);
+}
+
+/* Exported for tests: n words of block b of step k of trajectory i, flattened. */
+void orc_uniforms(uint64_t seed, uint64_t traj, uint64_t step, int64_t n_words, double *out)
+{
+    for (int64_t q = 0; q < n_words; ++q) out[q] = orc_uniform(seed, traj, step, q);
+}
+
+void orc_philox_blocks(uint64_t seed, const uint32_t *ctrs /*[n][4]*/, int64_t n, uint32_t *out /*[n][4]*/)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctrs + 4 * i, key, out + 4 * i);
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Mass-action propensities (Section 2) and their derivatives with respect to the state.     */
+/* ---------------------------------------------------------------------------------------- */
+
+/* combinatorial factor h_j(X): 1, X_i, X_i X_l, or X_i (X_i - 1) / 2 */
+static double orc_h(const orc_network *net, int j, const double *X)
+{
+    int r1 = net->reactants[2 * j], r2 = net->reactants[2 * j + 1];
+    if (r1 < 0 && r2 < 0) return 1.0;
+    if (r1 < 0) { r1 = r2; r2 = -1; }
+    if (r2 < 0) return X[r1];
+    if (r1 == r2) return X[r1] * (X[r1] - 1.0) / 2.0;
+    return X[r1] * X[r2];
+}
+
+/* add c * d h_j / d X to grad[N] */
+static void orc_add_dh(const orc_network *net, int j, const double *X, double c, double *grad)
+{
+    int r1 = net->reactants[2 * j], r2 = net->reactants[2 * j + 1];
+    if (r1 < 0 && r2 < 0) return;
+    if (r1 < 0) { r1 = r2; r2 = -1; }
+    if (r2 < 0) { grad[r1] += c; return; }
+    if (r1 == r2) { grad[r1] += c * (2.0 * X[r1] - 1.0) / 2.0; return; }
+    grad[r1] += c * X[r2];
+    grad[r2] += c * X[r1];
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* One trajectory: the stored path.                                                           */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int64_t n_draws;   /* number of reaction draws, including a crossing draw */
+    int64_t n_states;  /* number of states X_0..X_{n_states-1} visited */
+    int32_t status;
+    int32_t crossed;   /* 1 if the last draw crossed t_end (made, not applied) */
+    /* growable arrays */
+    int64_t cap;
+    double *X;         /* [cap+1][N] state before draw k (X_0 ... ) */
+    double *t;         /* [cap+1] t_k */
+    double *tau;       /* [cap] tau_k */
+    int32_t *j;        /* [cap] j_k */
+    double *margin;    /* [cap] (s1 - s2)/s1 in the a/E form; 1 if one reaction is active */
+} orc_path;
+
+static int orc_path_grow(orc_path *p, int N, int64_t need)
+{
+    if (need <= p->cap) return 0;
+    int64_t nc = p->cap ? p->cap : 64;
+    while (nc < need) nc *= 2;
+    double *X = (double *)realloc(p->X, (size_t)(nc + 1) * N * sizeof(double));
+    double *t = (double *)realloc(p->t, (size_t)(nc + 1) * sizeof(double));
+    double *tau = (double *)realloc(p->tau, (size_t)nc * sizeof(double));
+    int32_t *jj = (int32_t *)realloc(p->j, (size_t)nc * sizeof(int32_t));
+    double *mg = (double *)realloc(p->margin, (size_t)nc * sizeof(double));
+    if (X) p->X = X;
+    if (t) p->t = t;
+    if (tau) p->tau = tau;
+    if (jj) p->j = jj;
+    if (mg) p->margin = mg;
+    if (!X || !t || !tau || !jj || !mg) return -1;
+    p->cap = nc;
+    return 0;
+}
+
+static void orc_path_free(orc_path *p)
+{
+    free(p->X); free(p->t); free(p->tau); free(p->j); free(p->margin);
+    memset(p, 0, sizeof(*p));
+}
+
+typedef struct {
+    const orc_network *net;
+    double t_end;
+    int64_t max_steps;
+    uint64_t seed;
+} orc_sim_cfg;
+
+/*
+ * Simulate trajectory `traj` from x0 (Section 2 + the Gumbel-max choice of Section 3.2).
+ * Returns 0, or -1 on allocation failure.
+ */
+static int orc_simulate_one(const orc_sim_cfg *cfg, uint64_t traj, const int32_t *x0, orc_path *p)
+{
+    const orc_network *net = cfg->net;
+    const int N = net->n_species, M = net->n_reactions;
+    double *a = (double *)malloc((size_t)(M > 0 ? M : 1) * sizeof(double));
+    if (!a) return -1;
+    p->n_draws = 0;
+    p->crossed = 0;
+    p->status = ORC_OK;
+    if (orc_path_grow(p, N, 1)) { free(a); return -1; }
+    for (int i = 0; i < N; ++i) p->X[i] = (double)x0[i];
+    p->t[0] = 0.0;
+    int64_t k = 0;
+    for (;;) {
+        double *X = p->X + (size_t)k * N;
+        if (k >= cfg->max_steps) { p->status = ORC_STEP_CAP; break; }
+        /* propensities, total rate (Section 2) */
+        double a0 = 0.0;
+        int bad = 0;
+        for (int j = 0; j < M; ++j) {
+            double kj = exp(net->log_rates[net->rate_index[j]]);
+            a[j] = kj * orc_h(net, j, X);
+            if (!isfinite(a[j]) || a[j] < 0.0) bad = 1;
+            a0 += a[j];
+        }
+        if (bad) { p->status = ORC_BAD_RATE; break; }
+        if (a0 == 0.0) { p->status = ORC_ABSORBED; break; }
+        if (orc_path_grow(p, N, k + 2)) { free(a); return -1; }
+        X = p->X + (size_t)k * N;
+        /* waiting time by inverse transform (Section 2) */
+        double u0 = orc_uniform(cfg->seed, traj, (uint64_t)k, 0);
+        double tau = -log(u0) / a0;
+        /* Gumbel-max choice over the active reactions (Section 3.2); ties to the lowest j */
+        int best = -1;
+        double s1 = -INFINITY, s2 = -INFINITY;
+        for (int j = 0; j < M; ++j) {
+            if (!(a[j] > 0.0)) continue;
+            double u = orc_uniform(cfg->seed, traj, (uint64_t)k, 1 + j);
+            double G = -log(-log(u));
+            double key = log(a[j]) + G;
+            if (key > s1) { s2 = s1; s1 = key; best = j; }
+            else if (key > s2) { s2 = key; }
+        }
+        p->j[k] = best;
+        p->tau[k] = tau;
+        p->margin[k] = (s2 == -INFINITY) ? 1.0 : -expm1(s2 - s1);
+        double t_next = p->t[k] + tau;
+        p->t[k + 1] = t_next;
+        p->n_draws = k + 1;
+        if (t_next > cfg->t_end) { p->crossed = 1; p->status = ORC_OK; break; }
+        /* integer update (Eq. 6), with range checks */
+        double *Xn = p->X + (size_t)(k + 1) * N;
+        int stop = 0;
+        for (int i = 0; i < N; ++i) Xn[i] = X[i];
+        for (int e = net->stoich_ptr[best]; e < net->stoich_ptr[best + 1]; ++e) {
+            int s = net->stoich_species[e];
+            Xn[s] += (double)net->stoich_delta[e];
+        }
+        for (int i = 0; i < N; ++i) {
+            if (Xn[i] < 0.0) { p->status = ORC_NEG_COUNT; stop = 1; }
+            else if (Xn[i] > 2147483647.0) { p->status = ORC_OVERFLOW; stop = 1; }
+        }
+        if (stop) {
+            /* the draw was made but not applied: the trajectory stops at X_k */
+            break;
+        }
+        ++k;
+    }
+    p->n_states = k + 1;
+    free(a);
+    return 0;
+}
+
+/* Bracket of sample time ts: the largest k with t_k <= ts (right-continuous path). */
+static int64_t orc_bracket(const orc_path *p, double ts)
+{
+    int64_t k = 0;
+    while (k + 1 < p->n_states && p->t[k + 1] <= ts) ++k;
+    return k;
+}
+
+/* Does state k have a draw that the LINEAR readout may interpolate towards? */
+static int orc_has_next(const orc_path *p, int64_t k)
+{
+    /* a draw exists at k if k < n_draws; it was applied if k + 1 < n_states, or it is the
+       crossing draw; a draw rejected by a range check is not interpolated */
+    if (k >= p->n_draws) return 0;
+    if (k + 1 < p->n_states) return 1;
+    return p->crossed;
+}
+
+/* Readout (Section 4.1): HOLD = X(t_s); LINEAR = linear interpolation on the event grid. */
+static void orc_readout(const orc_network *net, const orc_path *p, const double *ts, int S,
+                        const int32_t *obs_species, int n_obs, int readout, double *obs /*[S][n_obs]*/)
+{
+    const int N = net->n_species;
+    for (int s = 0; s < S; ++s) {
+        int64_t k = orc_bracket(p, ts[s]);
+        const double *X = p->X + (size_t)k * N;
+        for (int o = 0; o < n_obs; ++o) {
+            int sp = obs_species[o];
+            double v = X[sp];
+            if (readout == ORC_LINEAR && orc_has_next(p, k)) {
+                double alpha = (ts[s] - p->t[k]) / p->tau[k];
+                double dv = 0.0;
+                int j = p->j[k];
+                for (int e = net->stoich_ptr[j]; e < net->stoich_ptr[j + 1]; ++e)
+                    if (net->stoich_species[e] == sp) dv += (double)net->stoich_delta[e];
+                v = X[sp] + alpha * dv;
+            }
+            obs[(size_t)s * n_obs + o] = v;
+        }
+    }
+}
+
+/*
+ * Straight-through adjoint of one trajectory (Eqs. 3, 5, 7; Section 3.1; Figure 1 recursion).
+ * dL_dobs: [S][n_obs] for this trajectory. Adds dL/dtheta into dtheta[P].
+ */
+static int orc_adjoint_one(const orc_sim_cfg *cfg, uint64_t traj, const orc_path *p,
+                           const double *ts, int S, const int32_t *obs_species, int n_obs,
+                           int readout, const double *dL_dobs, double T, double *dtheta)
+{
+    const orc_network *net = cfg->net;
+    const int N = net->n_species, M = net->n_reactions;
+    double *lam = (double *)calloc((size_t)N, sizeof(double));     /* dL/dX_{k+1} */
+    double *lam_new = (double *)calloc((size_t)N, sizeof(double));
+    double *dXdir = (double *)calloc((size_t)N, sizeof(double));
+    double *gbar = (double *)calloc((size_t)N, sizeof(double));
+    double *a = (double *)calloc((size_t)(M > 0 ? M : 1), sizeof(double));
+    double *z = (double *)calloc((size_t)(M > 0 ? M : 1), sizeof(double));
+    double *y = (double *)calloc((size_t)(M > 0 ? M : 1), sizeof(double));
+    double *w = (double *)calloc((size_t)(M > 0 ? M : 1), sizeof(double));
+    int64_t *kb = (int64_t *)calloc((size_t)(S > 0 ? S : 1), sizeof(int64_t));
+    if (!lam || !lam_new || !dXdir || !gbar || !a || !z || !y || !w || !kb) {
+        free(lam); free(lam_new); free(dXdir); free(gbar); free(a); free(z); free(y); free(w); free(kb);
+        return -1;
+    }
+    for (int s = 0; s < S; ++s) kb[s] = orc_bracket(p, ts[s]);
+
+    double mu = 0.0; /* dL/dt_{k+1} */
+    for (int64_t k = p->n_states - 1; k >= 0; --k) {
+        const double *X = p->X + (size_t)k * N;
+        const int draw = orc_has_next(p, k);
+        double dt_dir = 0.0, dtau_dir = 0.0;
+        for (int i = 0; i < N; ++i) dXdir[i] = 0.0;
+        /* direct readout terms of the samples bracketed by state k */
+        for (int s = 0; s < S; ++s) {
+            if (kb[s] != k) continue;
+            for (int i = 0; i < N; ++i) gbar[i] = 0.0;
+            for (int o = 0; o < n_obs; ++o) gbar[obs_species[o]] += dL_dobs[(size_t)s * n_obs + o];
+            if (readout == ORC_LINEAR && draw) {
+                /* obs = X_k + alpha (X_{k+1} - X_k), alpha = (t_s - t_k)/tau_k */
+                double alpha = (ts[s] - p->t[k]) / p->tau[k];
+                double c = 0.0; /* gbar . (X_{k+1} - X_k) = gbar . v_{j_k} */
+                int j = p->j[k];
+                for (int e = net->stoich_ptr[j]; e < net->stoich_ptr[j + 1]; ++e)
+                    c += gbar[net->stoich_species[e]] * (double)net->stoich_delta[e];
+                for (int i = 0; i < N; ++i) {
+                    lam[i] += alpha * gbar[i];          /* into X_{k+1} */
+                    dXdir[i] += (1.0 - alpha) * gbar[i];
+                }
+                dt_dir += -c / p->tau[k];               /* d alpha/d t_k = -1/tau_k */
+                dtau_dir += -alpha * c / p->tau[k];     /* d alpha/d tau_k = -alpha/tau_k */
+            } else {
+                for (int i = 0; i < N; ++i) dXdir[i] += gbar[i];
+            }
+        }
+        for (int i = 0; i < N; ++i) lam_new[i] = lam[i] + dXdir[i];
+        if (draw) {
+            /* recompute the step's propensities and Gumbel perturbations (same noise) */
+            double a0 = 0.0;
+            for (int j = 0; j < M; ++j) {
+                a[j] = exp(net->log_rates[net->rate_index[j]]) * orc_h(net, j, X);
+                a0 += a[j];
+            }
+            double tau = p->tau[k];
+            double dtau = mu + dtau_dir;
+            /* Eq. 3: soft sample over the active reactions */
+            double zmax = -INFINITY;
+            for (int j = 0; j < M; ++j) {
+                if (a[j] > 0.0) {
+                    double u = orc_uniform(cfg->seed, traj, (uint64_t)k, 1 + j);
+                    z[j] = (log(a[j]) - log(-log(u))) / T;
+                    if (z[j] > zmax) zmax = z[j];
+                }
+            }
+            double Z = 0.0;
+            for (int j = 0; j < M; ++j) { y[j] = (a[j] > 0.0) ? exp(z[j] - zmax) : 0.0; Z += y[j]; }
+            for (int j = 0; j < M; ++j) y[j] /= Z;
+            /* Eq. 7: dL/dy~_j = v_j . dL/dX_{k+1} */
+            double wbar = 0.0;
+            for (int j = 0; j < M; ++j) {
+                w[j] = 0.0;
+                for (int e = net->stoich_ptr[j]; e < net->stoich_ptr[j + 1]; ++e)
+                    w[j] += (double)net->stoich_delta[e] * lam[net->stoich_species[e]];
+                wbar += y[j] * w[j];
+            }
+            /* softmax backward: dL/dz_j = y_j (w_j - sum_i y_i w_i); dL/dlog a_j = that / T */
+            /* waiting time: tau = E0/a0, so dL/da0 = -dtau * tau / a0 (Section 3.1) */
+            double dLda0 = -dtau * tau / a0;
+            for (int j = 0; j < M; ++j) {
+                double choice = (a[j] > 0.0) ? y[j] * (w[j] - wbar) / T : 0.0;
+                /* theta = log k: d log a_j / d theta = 1, d a_j / d theta = a_j */
+                dtheta[net->rate_index[j]] += choice + dLda0 * a[j];
+                /* state path: choice through d log a_j/dX = (dh/dX)/h; tau through d a_j/dX */
+                if (a[j] > 0.0) {
+                    double h = orc_h(net, j, X);
+                    orc_add_dh(net, j, X, choice / h, lam_new);
+                }
+                double kj = exp(net->log_rates[net->rate_index[j]]);
+                orc_add_dh(net, j, X, dLda0 * kj, lam_new);
+            }
+            mu = mu + dt_dir; /* t_{k+1} = t_k + tau_k */
+        }
+        for (int i = 0; i < N; ++i) lam[i] = lam_new[i];
+    }
+    free(lam); free(lam_new); free(dXdir); free(gbar); free(a); free(z); free(y); free(w); free(kb);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Batched driver with a thread pool over trajectories.                                       */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct {
+    const orc_network *net;
+    int64_t n_traj;
+    int64_t traj_offset;
+    const int32_t *x0;
+    int32_t x0_per_traj;
+    double t_end;
+    const double *ts;
+    int32_t S;
+    const int32_t *obs_species;
+    int32_t n_obs;
+    uint64_t seed;
+    int32_t readout;
+    int64_t max_steps;
+    const double *dL_dobs;     /* [n_traj][S][n_obs] or NULL */
+    double temperature;
+    double *obs_out;           /* [n_traj][S][n_obs] or NULL */
+    int64_t *draws_out;        /* [n_traj] or NULL */
+    int32_t *status_out;       /* [n_traj] or NULL */
+    double *dtheta_traj_out;   /* [n_traj][P] or NULL */
+    int32_t *events_out;       /* [n_traj][ev_cap] or NULL (-1 padded) */
+    double *margins_out;       /* [n_traj][ev_cap] or NULL */
+    double *times_out;         /* [n_traj][ev_cap] t_{k+1} per draw, or NULL */
+    int64_t ev_cap;
+    int32_t *final_x_out;      /* [n_traj][N] or NULL: last visited state */
+    /* work distribution */
+    int32_t n_threads;
+    int64_t next;              /* guarded by lock */
+    pthread_mutex_t lock;
+    int error;
+} orc_job;
+
+static void *orc_worker(void *arg)
+{
+    orc_job *job = (orc_job *)arg;
+    const orc_network *net = job->net;
+    const int N = net->n_species, P = net->n_params;
+    orc_sim_cfg cfg = {net, job->t_end, job->max_steps, job->seed};
+    orc_path path;
+    memset(&path, 0, sizeof(path));
+    double *dth = (double *)calloc((size_t)(P > 0 ? P : 1), sizeof(double));
+    double *obs = (double *)calloc((size_t)(job->S * job->n_obs > 0 ? job->S * job->n_obs : 1), sizeof(double));
+    if (!dth || !obs) { free(dth); free(obs); pthread_mutex_lock(&job->lock); job->error = 1; pthread_mutex_unlock(&job->lock); return NULL; }
+    for (;;) {
+        pthread_mutex_lock(&job->lock);
+        int64_t i = job->next++;
+        pthread_mutex_unlock(&job->lock);
+        if (i >= job->n_traj) break;
+        uint64_t traj = (uint64_t)(job->traj_offset + i);
+        const int32_t *x0 = job->x0 + (job->x0_per_traj ? (size_t)i * N : 0);
+        if (orc_simulate_one(&cfg, traj, x0, &path)) { job->error = 1; break; }
+        orc_readout(net, &path, job->ts, job->S, job->obs_species, job->n_obs, job->readout, obs);
+        if (job->obs_out)
+            memcpy(job->obs_out + (size_t)i * job->S * job->n_obs, obs, (size_t)job->S * job->n_obs * sizeof(double));
+        if (job->draws_out) job->draws_out[i] = path.n_draws;
+        if (job->status_out) job->status_out[i] = path.status;
+        if (job->final_x_out)
+            for (int s = 0; s < N; ++s)
+                job->final_x_out[(size_t)i * N + s] = (int32_t)path.X[(size_t)(path.n_states - 1) * N + s];
+        if (job->events_out || job->margins_out || job->times_out) {
+            for (int64_t q = 0; q < job->ev_cap; ++q) {
+                int have = q < path.n_draws;
+                if (job->events_out) job->events_out[(size_t)i * job->ev_cap + q] = have ? path.j[q] : -1;
+                if (job->margins_out) job->margins_out[(size_t)i * job->ev_cap + q] = have ? path.margin[q] : NAN;
+                if (job->times_out) job->times_out[(size_t)i * job->ev_cap + q] = have ? path.t[q + 1] : NAN;
+            }
+        }
+        if (job->dL_dobs && job->dtheta_traj_out) {
+            for (int r = 0; r < P; ++r) dth[r] = 0.0;
+            if (orc_adjoint_one(&cfg, traj, &path, job->ts, job->S, job->obs_species, job->n_obs,
+                                job->readout, job->dL_dobs + (size_t)i * job->S * job->n_obs,
+                                job->temperature, dth)) { job->error = 1; break; }
+            memcpy(job->dtheta_traj_out + (size_t)i * P, dth, (size_t)P * sizeof(double));
+        }
+    }
+    orc_path_free(&path);
+    free(dth);
+    free(obs);
+    return NULL;
+}
+
+/*
+ * Simulate n_traj trajectories (global ids traj_offset + i) and, if dL_dobs is given, the
+ * straight-through gradient of each one. Returns 0 on success, -1 on bad input or allocation
+ * failure.
+ */
+int orc_run(const orc_network *net, int64_t n_traj, int64_t traj_offset,
+            const int32_t *x0, int32_t x0_per_traj, double t_end,
+            const double *ts, int32_t S, const int32_t *obs_species, int32_t n_obs,
+            uint64_t seed, int32_t readout, int64_t max_steps,
+            const double *dL_dobs, double temperature,
+            double *obs_out, int64_t *draws_out, int32_t *status_out,
+            double *dtheta_traj_out,
+            int32_t *events_out, double *margins_out, double *times_out, int64_t ev_cap,
+            int32_t *final_x_out, int32_t n_threads)
+{
+    if (!net || n_traj < 0 || S < 0 || n_obs < 0 || max_steps < 0) return -1;
+    if (net->n_species <= 0 || net->n_reactions < 0) return -1;
+    for (int s = 0; s < S; ++s) {
+        if (!(ts[s] >= 0.0 && ts[s] <= t_end)) return -1;
+        if (s > 0 && ts[s] < ts[s - 1]) return -1;
+    }
+    for (int o = 0; o < n_obs; ++o)
+        if (obs_species[o] < 0 || obs_species[o] >= net->n_species) return -1;
+    if (dL_dobs && !(temperature > 0.0)) return -1;
+    orc_job job;
+    memset(&job, 0, sizeof(job));
+    job.net = net; job.n_traj = n_traj; job.traj_offset = traj_offset; job.x0 = x0;
+    job.x0_per_traj = x0_per_traj; job.t_end = t_end; job.ts = ts; job.S = S;
+    job.obs_species = obs_species; job.n_obs = n_obs; job.seed = seed; job.readout = readout;
+    job.max_steps = max_steps; job.dL_dobs = dL_dobs; job.temperature = temperature;
+    job.obs_out = obs_out; job.draws_out = draws_out; job.status_out = status_out;
+    job.dtheta_traj_out = dtheta_traj_out; job.events_out = events_out;
+    job.margins_out = margins_out; job.times_out = times_out; job.ev_cap = ev_cap;
+    job.final_x_out = final_x_out;
+    job.n_threads = n_threads > 0 ? n_threads : 1;
+    pthread_mutex_init(&job.lock, NULL);
+    if (job.n_threads == 1) {
+        orc_worker(&job);
+    } else {
+        pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)job.n_threads);
+        if (!th) { pthread_mutex_destroy(&job.lock); return -1; }
+        for (int t = 0; t < job.n_threads; ++t) pthread_create(&th[t], NULL, orc_worker, &job);
+        for (int t = 0; t < job.n_threads; ++t) pthread_join(th[t], NULL);
+        free(th);
+    }
+    pthread_mutex_destroy(&job.lock);
+    return job.error ? -1 : 0;
+}
