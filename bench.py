@@ -1,0 +1,422 @@
+"""Benchmark: SSA steps/s of the forward and of forward + straight-through adjoint on one GB300.
+
+Workload (one bench step = one pass of the whole hot path over one batch):
+    2A <-> B (a1 = k1 A (A - 1)/2, a2 = k2 B), 65,536 trajectories from A = 100, B = 0 to t_end = 50,
+    50 uniform samples of A with LINEAR readout, evaluated at k = (0.02, 0.05); record the event log
+    with checkpoints every K = 64 steps; ensemble mean; loss = mean_s (mean A(t_s) - target_s)^2 with
+    the target generated at k = (0.01, 0.1) (seed 1); straight-through backward at temperature
+    T in {0.1, 0.5, 1.0} (cycled over steps). Each step uses a fresh Philox seed.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line. `value` is forward+adjoint SSA steps per second (whole job); the forward-only
+rate and the ratio are reported beside it. Under torchrun each rank simulates its own trajectory
+ids (weak scaling, no collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SSA steps/s fwd and fwd+adjoint on 1 GB300 vs plain fwd; grad rel err vs FP64"
+WORKLOAD = "c2_dimer_2a_b_fwd_adj: 2A<->B, 65,536 traj, t_end=50, 50 LINEAR samples, K=64, T in {0.1,0.5,1.0}"
+TEMPS = (0.1, 0.5, 1.0)
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+# --------------------------------------------------------------------------------------------
+# Issue-slot roofline of the SSA kernels ("Roofline"): the minimal instruction count
+# of one SSA step of a network with M reactions, per thread, counted from the method's arithmetic
+# with the cheapest sm_103 instruction for each operation, and the SM issue rate
+# 152 SMs x 4 schedulers x 32 lanes x f_SM.
+# --------------------------------------------------------------------------------------------
+def instr_per_step_fwd(M: int) -> int:
+    nb = (M + 4) // 4
+    philox = 60 * nb                 # 10 rounds x (2 IMAD.WIDE + 2 LOP3 + 2 IADD)
+    variates = 5 * (M + 1)           # u01 (SHF, I2F, FFMA) + -ln u (MUFU.LG2, FMUL)
+    reactions = 8 * M                # propensity (LDS x2, I2F, FMUL), a0 add, key (RCP, FMUL), max
+    step = 12                        # tau, FP64 clock add and compares, state update, loop control
+    return philox + variates + reactions + step
+
+
+def instr_per_step_bwd(M: int) -> int:
+    # recompute of the forward step + softmax (LG2, FADD, FMUL, EX2, FADD) + w_j (LDS, FFMA) +
+    # g_j, psi_j, dA_j, two state-adjoint updates (~12) per reaction + event read and reversal
+    return instr_per_step_fwd(M) + 19 * M + 16
+
+
+def sm_issue_peak(sm_mhz: float, n_sm: int = 152) -> float:
+    return n_sm * 4 * 32 * sm_mhz * 1e6
+
+
+# --------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline sample)
+# --------------------------------------------------------------------------------------------
+def oracle_sample(seconds: float, chunk: int, seed0: int = 1000):
+    import ssa_workloads as W
+    from oracle import native
+    wl = W.config_c2()
+    theta = wl.log_rates.astype(np.float32).astype(np.float64)
+    cores = os.cpu_count() or 1
+    steps, t0, it = 0, time.perf_counter(), 0
+    target = np.linspace(90.0, 27.0, len(wl.sample_times))
+    while True:
+        fw = native.run(wl.net, theta, wl.x0, chunk, wl.t_end, wl.sample_times, wl.obs_species, seed0 + it,
+                        native.LINEAR, max_steps=wl.max_steps, n_threads=cores)
+        m = fw.obs[:, :, 0].mean(0)
+        g = np.broadcast_to((2.0 * (m - target) / len(m) / chunk)[None, :, None], fw.obs.shape).copy()
+        r = native.run(wl.net, theta, wl.x0, chunk, wl.t_end, wl.sample_times, wl.obs_species, seed0 + it,
+                       native.LINEAR, max_steps=wl.max_steps, dl_dobs=g, temperature=TEMPS[it % 3], n_threads=cores)
+        steps += int(r.draws.sum())
+        it += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return steps / dt, cores, it * chunk, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import native
+    native.build()
+    chunk = args.ref_chunk
+    for _ in range(args.warmup):
+        oracle_sample(0.0, chunk)
+    t0 = time.perf_counter()
+    total_steps = 0.0
+    for s in range(args.steps):
+        rate, cores, ntraj, dt = oracle_sample(0.0, chunk, seed0=2000 + 7 * s)
+        total_steps += rate * dt
+    dt = time.perf_counter() - t0
+    value = total_steps / dt
+    line = {
+        "metric": METRIC, "value": value, "unit": "SSA steps/s (fwd+adj)", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample": f"{chunk} trajectories per step (oracle fwd+adj)"},
+        "cpu_baseline": {"value": value, "unit": "SSA steps/s (fwd+adj)", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} steps x {chunk} trajectories of the workload"},
+        "e2e": {"value": value, "unit": "SSA steps/s (fwd+adj)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import ssa_workloads as W
+    from paper_2602_19775_gb300 import ssa
+
+    wl = W.config_c2(n_traj=args.n_traj)
+    n = wl.n_traj
+    S = len(wl.sample_times)
+    offset = rank * n  # each rank simulates its own global trajectory ids
+    net = ssa.Network(wl.net)
+    theta = torch.tensor(wl.log_rates.astype(np.float32), device=dev)
+    x0 = torch.tensor(wl.x0, device=dev)
+    ts = torch.tensor(wl.sample_times, device=dev)
+    obs_sp = torch.tensor(wl.obs_species, device=dev)
+    true_theta = torch.tensor(np.log([0.01, 0.1]).astype(np.float32), device=dev)
+    max_steps = 2048
+    stream = torch.cuda.current_stream()
+
+    # target: ensemble mean of A at the true rates, seed 1 (setup, untimed)
+    tfw = ssa.forward(net, true_theta, n, x0, wl.t_end, ts, obs_sp, 1, readout="linear", max_steps=max_steps,
+                      traj_offset=offset)
+    target = ssa.ensemble_mean(tfw.obs)[:, 0].clone()
+    del tfw
+
+    opts = ssa.make_opts("linear", True, 64, max_steps)
+    ws = torch.empty(ssa.workspace_bytes(net, n, S, opts), dtype=torch.uint8, device=dev)
+    obs = torch.empty((n, S, 1), dtype=torch.float32, device=dev)
+    dtheta = torch.empty(2, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(seed, T, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        fw = ssa.forward(net, theta, n, x0, wl.t_end, ts, obs_sp, seed, readout="linear", record=True,
+                         max_steps=max_steps, traj_offset=offset, workspace=ws, obs_out=obs)
+        if ev is not None:
+            ev[1].record(stream)
+        m = ssa.ensemble_mean(obs)[:, 0]
+        dl = (2.0 / (S * n)) * (m - target)          # dL/dobs, the same for every trajectory
+        if ev is not None:
+            ev[2].record(stream)
+        ssa.backward(fw, dl.view(S, 1), T, out=dtheta)
+        if ev is not None:
+            ev[3].record(stream)
+        return fw
+
+    def fwd_only(seed, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        fw = ssa.forward(net, theta, n, x0, wl.t_end, ts, obs_sp, seed, readout="linear", record=False,
+                         max_steps=max_steps, traj_offset=offset, workspace=ws, obs_out=obs)
+        if ev is not None:
+            ev[1].record(stream)
+        return fw
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for w in range(args.warmup):
+        step(100 + w, TEMPS[w % 3])
+        fwd_only(100 + w)
+    barrier()
+
+    # ---- timed: forward + adjoint ----
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    draws_tot = torch.zeros((), dtype=torch.int64, device=dev)
+    with ClockSampler(local) as clk:
+        barrier()
+        for s in range(K):
+            fw = step(1000 + s, TEMPS[s % 3], evs[s])
+            draws_tot += fw.draws.sum()
+            flush.fill_(s & 0xFF)                    # L2 flush between steps, outside the events
+        barrier()
+        # ---- timed: forward only (same seeds) ----
+        fev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+        fdraws = torch.zeros((), dtype=torch.int64, device=dev)
+        for s in range(K):
+            fw = fwd_only(1000 + s, fev[s])
+            fdraws += fw.draws.sum()
+            flush.fill_(s & 0xFF)
+        barrier()
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    bwd_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    fonly_ms = [e[0].elapsed_time(e[1]) for e in fev]
+    steps_total = int(draws_tot.item())
+    t_step = float(np.sum(step_ms)) / 1e3
+    t_fonly = float(np.sum(fonly_ms)) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_step, t_fonly], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        cnt = torch.tensor([steps_total, int(fdraws.item())], device=dev, dtype=torch.int64)
+        dist.all_reduce(cnt)
+        t_step, t_fonly = float(tt[0]), float(tt[1])
+        steps_total, fsteps = int(cnt[0]), int(cnt[1])
+    else:
+        fsteps = int(fdraws.item())
+    value = steps_total / t_step
+    fwd_value = fsteps / t_fonly
+
+    # ---- end to end through the API with host buffers ----
+    pin = lambda a: torch.tensor(a).pin_memory()  # noqa: E731
+    h_theta, h_x0, h_ts, h_sp = pin(wl.log_rates.astype(np.float32)), pin(wl.x0), pin(wl.sample_times), pin(wl.obs_species)
+    h_target = target.cpu().pin_memory()
+    h_out = torch.empty(2, dtype=torch.float32).pin_memory()
+    h_mean = torch.empty(S, dtype=torch.float32).pin_memory()
+    d_theta, d_x0, d_ts, d_sp, d_target = (torch.empty_like(t, device=dev) for t in (h_theta, h_x0, h_ts, h_sp, h_target))
+    e_steps = 0
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(K):
+        for d, h in ((d_theta, h_theta), (d_x0, h_x0), (d_ts, h_ts), (d_sp, h_sp), (d_target, h_target)):
+            d.copy_(h, non_blocking=True)
+        fw = ssa.forward(net, d_theta, n, d_x0, wl.t_end, d_ts, d_sp, 5000 + s, readout="linear", record=True,
+                         max_steps=max_steps, traj_offset=offset, workspace=ws, obs_out=obs)
+        m = ssa.ensemble_mean(obs)[:, 0]
+        dl = (2.0 / (S * n)) * (m - d_target)
+        ssa.backward(fw, dl.view(S, 1), TEMPS[s % 3], out=dtheta)
+        h_out.copy_(dtheta, non_blocking=True)
+        h_mean.copy_(m, non_blocking=True)
+        e_steps += int(fw.draws.sum().item())   # also synchronises the step, as a user's loop would
+    e1.record(stream)
+    barrier()
+    e2e_t = e0.elapsed_time(e1) / 1e3
+    h2d = sum(t.numel() * t.element_size() for t in (h_theta, h_x0, h_ts, h_sp, h_target))
+    d2h = h_out.numel() * 4 + h_mean.numel() * 4 + 8
+    e2e_value = e_steps * world / e2e_t
+
+    # ---- gradient error vs the FP64 oracle on a subset (rank 0, outside the timed regions) ----
+    grad_err = None
+    cpu_base = None
+    if rank == 0 and not args.no_oracle:
+        grad_err = grad_error_subset(ssa, net, wl, dev)
+        rate, cores, ntraj, dt = oracle_sample(args.cpu_seconds, 4096)
+        cpu_base = {"value": rate, "unit": "SSA steps/s (fwd+adj)", "cores": cores, "kind": "oracle",
+                    "sample": f"{ntraj} trajectories of the workload, fwd + adj, {dt:.1f} s"}
+
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    M = wl.net.n_reactions
+    bwd_s = float(np.mean(bwd_ms)) / 1e3
+    fwd_s = float(np.mean(fwd_ms)) / 1e3
+    per_launch_steps = steps_total / world / K
+    ach_b = instr_per_step_bwd(M) * per_launch_steps / bwd_s
+    ach_f = instr_per_step_fwd(M) * per_launch_steps / fwd_s
+    peak = sm_issue_peak(sm_mhz)
+    dominant = "adjoint" if bwd_s >= fwd_s else "forward"
+    ach = ach_b if dominant == "adjoint" else ach_f
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "SSA steps/s (fwd+adj)",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_step / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (FP64 clock, int32 counts)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_traj_per_gpu": n, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"trajectory shards x{world}"},
+        "fwd_steps_per_s": fwd_value,
+        "fwd_adj_over_fwd": value / fwd_value,
+        "ssa_steps_per_bench_step": steps_total / K,
+        "grad_rel_err_vs_fp64": grad_err,
+        "kernel_ms": {"forward_record": float(np.mean(fwd_ms)), "adjoint": float(np.mean(bwd_ms)),
+                      "forward_only": float(np.mean(fonly_ms))},
+        "roofline": {"bound": "alu", "kernel": dominant, "achieved": ach / 1e12, "peak": peak / 1e12,
+                     "unit": "T thread-instr/s", "frac": ach / peak, "traffic": None,
+                     "peak_basis": f"152 SM x 4 x 32 lanes x {sm_mhz:.0f} MHz (sampled median)"},
+        "cpu_baseline": cpu_base,
+        "e2e": {"value": e2e_value, "unit": "SSA steps/s (fwd+adj)", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 7 * K,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def grad_error_subset(ssa, net, wl, dev, n=2048):
+    """Relative error of the GPU gradient against the FP64 oracle on trajectories with identical
+    event sequences, for each temperature (same seeded inputs on both sides)."""
+    import torch
+
+    import ssa_workloads as W
+    from oracle import native
+    theta32 = wl.log_rates.astype(np.float32)
+    dl = W.seeded_dl_dobs(3, n, len(wl.sample_times), 1, scale=1.0 / n)
+    out = {}
+    fw = ssa.forward(net, torch.tensor(theta32, device=dev), n, wl.x0, wl.t_end, wl.sample_times, wl.obs_species, 77,
+                     readout="linear", record=True, max_steps=2048)
+    ev = fw.run.events(2048).cpu().numpy()
+    for T in TEMPS:
+        orc = native.run(wl.net, theta32.astype(np.float64), wl.x0, n, wl.t_end, wl.sample_times, wl.obs_species, 77,
+                         native.LINEAR, max_steps=2048, dl_dobs=dl, temperature=T, ev_cap=2048)
+        same = np.all(ev == orc.events, axis=1)
+        dl2 = dl.copy()
+        dl2[~same] = 0
+        g = ssa.backward(fw, torch.tensor(dl2, dtype=torch.float32, device=dev), T).cpu().numpy()
+        ref = orc.dtheta[same].sum(0)
+        out[str(T)] = float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
+    out["identical_event_fraction"] = float(same.mean())
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-traj", type=int, default=65536)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-chunk", type=int, default=4096)
+    ap.add_argument("--no-oracle", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

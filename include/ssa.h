@@ -1,0 +1,209 @@
+/*
+ * ssa.h -- C ABI of the GB300 (sm_103a) library for exact stochastic simulation with a
+ * Gumbel-max reaction choice and a Gumbel-Softmax straight-through adjoint
+ * (arXiv 2602.19775, "Exact Discrete Stochastic Simulation with Deep-Learning-Scale Gradient
+ * Optimization").
+ *
+ * Conventions for every entry point
+ *   - Plain C types only. `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Pointers documented as "device" must be device (or managed) memory on the current device;
+ *     "host" pointers are read before the call returns.
+ *   - The caller owns every buffer it passes, including the workspace; the library owns only the
+ *     opaque handles and the small constant tables they hold.
+ *   - Every call except ssa_create_*, ssa_destroy_*, ssa_run_status and ssa_last_error is
+ *     asynchronous on `stream`.
+ *   - Return value: SSA_OK (0) or a negative error code; ssa_last_error() gives a text for the
+ *     most recent failure on the calling thread. No C++ exception crosses this boundary.
+ *   - Per-trajectory outcomes are written as SSA_TRAJ_* codes to a device status array.
+ *
+ * Noise: Philox4x32-10 (Salmon et al., SC'11), key = (seed_lo, seed_hi), counter =
+ * (b, k, i_lo, i_hi) for global trajectory id i (= traj_offset + local index), step k and block b;
+ * word q = 4b + w of the step's stream gives u_q = ((x >> 9) + 1/2) 2^-23 in (0,1); u_0 drives the
+ * waiting time and u_{1+j} reaction j. Results depend only on (network, parameters, x0, seed,
+ * global trajectory id), never on launch shape, chunking or batching.
+ */
+#ifndef SSA_H
+#define SSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ssa_status;
+
+#define SSA_OK 0
+#define SSA_ERR_INVALID_ARG (-1) /* an argument is out of range or inconsistent */
+#define SSA_ERR_CUDA (-2)        /* a CUDA runtime call failed (text in ssa_last_error) */
+#define SSA_ERR_WORKSPACE (-3)   /* workspace too small or misaligned (need 256-byte alignment) */
+#define SSA_ERR_UNSUPPORTED (-4) /* valid but outside this build's limits (e.g. M > 65535) */
+#define SSA_ERR_STATE (-5)       /* the run handle cannot serve this call (e.g. not recorded) */
+
+/* per-trajectory status codes */
+#define SSA_TRAJ_OK 0             /* reached t_end; the crossing draw was made, not applied */
+#define SSA_TRAJ_ABSORBED 1       /* a0 == 0 before t_end; the state holds to t_end          */
+#define SSA_TRAJ_STEP_CAP 2       /* max_steps draws made and applied before t_end           */
+#define SSA_TRAJ_NEG_COUNT 3      /* the chosen update would make a count negative           */
+#define SSA_TRAJ_OVERFLOW 4       /* the chosen update would leave the int32 range           */
+#define SSA_TRAJ_BAD_RATE 5       /* a propensity or a0 was not finite                       */
+#define SSA_TRAJ_BAD_INPUT 6      /* sample times not ascending within [0, t_end]           */
+#define SSA_TRAJ_REPLAY_MISMATCH 7/* replay: the given events do not fit the trajectory     */
+#define SSA_TRAJ_N_CODES 8
+
+#define SSA_READOUT_HOLD 0   /* obs = X(t_s), right-continuous; int32 output              */
+#define SSA_READOUT_LINEAR 1 /* obs = X_k + (t_s - t_k)/tau_k (X_{k+1} - X_k); float output */
+
+typedef struct ssa_network ssa_network;
+typedef struct ssa_run ssa_run;
+
+typedef struct ssa_fwd_opts {
+    int32_t readout;          /* SSA_READOUT_HOLD or SSA_READOUT_LINEAR                          */
+    int32_t record;           /* nonzero: keep event log, checkpoints and sample brackets so that
+                                 ssa_backward can run on this forward                            */
+    int32_t ckpt_interval;    /* K: checkpoint the state every K steps (multiple of 8; 0 -> 64)   */
+    int32_t threads_per_traj; /* 0: choose; 1: one thread per trajectory; 32: one warp per
+                                 trajectory (networks with hundreds of reactions)               */
+    int64_t max_steps;        /* cap on reaction draws per trajectory (>= 1); sizes the log       */
+    int32_t block_threads;    /* 0: choose; else a multiple of 32 in [32, 1024]                  */
+    int32_t reserved;         /* must be 0                                                       */
+} ssa_fwd_opts;
+
+/*
+ * ssa_create_network -- a mass-action reaction network (Section 2).
+ *   n_species N >= 1, n_reactions M in [1, 65535].
+ *   reactants      host int32 [M][2]: reactant species of reaction j or -1 for an empty slot.
+ *                  Order = number of non-negative slots; equal slots = homodimer.
+ *                  Propensity (Section 2): a_j = k_j h_j(X) with h = 1, X_i, X_i X_l or
+ *                  X_i (X_i - 1)/2.
+ *   stoich_ptr     host int32 [M+1], CSR row pointer of the net change v_j (Eq. 6).
+ *   stoich_species host int32 [nnz] in [0, N); stoich_delta host int32 [nnz] in [-127, 127].
+ *   n_params P >= 1; rate_index host int32 [M] in [0, P): k_j = exp(theta[rate_index[j]]).
+ *   out            receives the handle (device tables are allocated here).
+ * Errors: SSA_ERR_INVALID_ARG for any out-of-range entry, SSA_ERR_CUDA on allocation failure.
+ */
+ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions, const int32_t *reactants,
+                              const int32_t *stoich_ptr, const int32_t *stoich_species,
+                              const int32_t *stoich_delta, int32_t n_params,
+                              const int32_t *rate_index, ssa_network **out);
+void ssa_destroy_network(ssa_network *net);
+
+/*
+ * ssa_forward_workspace_bytes -- bytes of device workspace ssa_forward needs for this
+ * (network, n_traj, n_samples, opts). With opts->record the size includes the event log
+ * (2 bytes per step up to max_steps), checkpoints every K steps, the sample brackets and the
+ * per-block partial sums of the backward. Returns 0 for invalid arguments.
+ */
+size_t ssa_forward_workspace_bytes(const ssa_network *net, int64_t n_traj, int32_t n_samples,
+                                   const ssa_fwd_opts *opts);
+
+/*
+ * ssa_forward -- simulate n_traj independent trajectories with the exact direct method
+ * (Section 2: propensities, a0, tau = -ln(u_0)/a0) and the Gumbel-max choice
+ * j* = argmax_j [log a_j + G_j] of Section 3.2 (computed as argmax a_j/E_j, E_j = -ln u_{1+j},
+ * the same choice), applying X <- X + v_{j*} (Eq. 6) until the clock passes t_end.
+ *   log_rates     device float [P]: theta = log k.
+ *   n_traj >= 0; traj_offset: global id of the first trajectory (Philox counter).
+ *   x0            device int32 [N] (x0_per_traj = 0) or [n_traj][N] (x0_per_traj = 1).
+ *   t_end >= 0.   sample_times device double [n_samples], ascending, each in [0, t_end].
+ *   obs_species   device int32 [n_obs] in [0, N).
+ *   workspace     device, >= ssa_forward_workspace_bytes(...), 256-byte aligned, caller-owned;
+ *                 it must stay alive and untouched until ssa_destroy_run(*run_out).
+ *   obs_out       device [n_traj][n_samples][n_obs]: int32 (HOLD) or float (LINEAR) (Section 4.1).
+ *   draws_out     device int32 [n_traj] or NULL: reaction draws including the crossing draw.
+ *   status_out    device int32 [n_traj] or NULL: SSA_TRAJ_* per trajectory.
+ *   run_out       receives a handle for ssa_backward / ssa_run_status (may be NULL).
+ * Precision: FP32 propensities, keys and waiting times; FP64 clock and sample comparisons;
+ * exact int32 counts.
+ */
+ssa_status ssa_forward(const ssa_network *net, const float *log_rates, int64_t n_traj,
+                       int64_t traj_offset, const int32_t *x0, int32_t x0_per_traj, double t_end,
+                       const double *sample_times, int32_t n_samples, const int32_t *obs_species,
+                       int32_t n_obs, uint64_t seed, const ssa_fwd_opts *opts, void *workspace,
+                       size_t workspace_bytes, void *obs_out, int32_t *draws_out,
+                       int32_t *status_out, void *stream, ssa_run **run_out);
+
+/*
+ * ssa_forward_replay -- as ssa_forward, but reaction k of trajectory i is events[i][k] (given,
+ * e.g. by an independent implementation) instead of the Gumbel-max choice; waiting times still
+ * come from the trajectory's own noise. Trajectories whose clock and given events disagree
+ * (a given event with a_j = 0, too few or too many events for t_end) get
+ * SSA_TRAJ_REPLAY_MISMATCH.
+ *   events    device uint16 [n_traj][events_stride]; n_events device int32 [n_traj].
+ */
+ssa_status ssa_forward_replay(const ssa_network *net, const float *log_rates, int64_t n_traj,
+                              int64_t traj_offset, const int32_t *x0, int32_t x0_per_traj,
+                              double t_end, const double *sample_times, int32_t n_samples,
+                              const int32_t *obs_species, int32_t n_obs, uint64_t seed,
+                              const ssa_fwd_opts *opts, const uint16_t *events,
+                              const int32_t *n_events, int64_t events_stride, void *workspace,
+                              size_t workspace_bytes, void *obs_out, int32_t *draws_out,
+                              int32_t *status_out, void *stream, ssa_run **run_out);
+
+/*
+ * ssa_backward -- straight-through gradient of a recorded forward (Eqs. 3, 5, 7; the
+ * reparametrised waiting time of Section 3.1; the adjoint recursion of Figure 1), walking each
+ * trajectory backwards and regenerating the same Gumbel noise from Philox.
+ *   dl_dobs        device float, dL/dobs of trajectory i at dl_dobs + i * dl_traj_stride, laid
+ *                  out [n_samples][n_obs]. dl_traj_stride = n_samples * n_obs for a full
+ *                  [n_traj][n_samples][n_obs] array, or 0 when every trajectory has the same
+ *                  upstream gradient (a loss on ensemble means, Section 3.5).
+ *   temperature    T > 0 (Eq. 3).
+ *   dl_dlog_rates  device float [P], overwritten with dL/dtheta summed over trajectories
+ *                  (deterministic reduction order).
+ * Trajectories whose status is not OK/ABSORBED/STEP_CAP contribute nothing. Callable any number
+ * of times on one run (e.g. several temperatures). SSA_ERR_STATE if the run was not recorded.
+ */
+ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride,
+                        float temperature, float *dl_dlog_rates, void *stream);
+
+/*
+ * ssa_run_status -- synchronises `stream`, counts the per-trajectory status codes of the run into
+ * host counts[SSA_TRAJ_N_CODES] and returns the number of backward consistency failures (the
+ * recomputed Gumbel-max choice or a checkpoint disagreeing with the log) in *host_bwd_mismatch
+ * (may be NULL; counted by the last ssa_backward).
+ */
+ssa_status ssa_run_status(const ssa_run *run, int64_t *host_counts, int64_t *host_bwd_mismatch,
+                          void *stream);
+
+/*
+ * ssa_run_events -- test hook: unpack the recorded event log into device int32
+ * [n_traj][stride], -1 after each trajectory's last draw (stride >= the longest trajectory).
+ */
+ssa_status ssa_run_events(const ssa_run *run, int32_t *events_out, int64_t stride, void *stream);
+
+/*
+ * ssa_run_brackets -- test hook: the recorded sample brackets of a recorded forward, as device
+ * int32 [n_traj][n_samples]: the index k of the state X_k with t_k <= t_s < t_{k+1}.
+ */
+ssa_status ssa_run_brackets(const ssa_run *run, int32_t *brackets_out, void *stream);
+
+void ssa_destroy_run(ssa_run *run);
+
+/*
+ * ssa_ensemble_mean -- the ensemble average that the paper's losses compare (Sections 3.5 and
+ * 4.1: MSE between simulated and target ensemble-averaged trajectories): the mean over
+ * trajectories of obs [n_traj][row_len] (device; int32 when obs_is_int, else float) into device
+ * float [row_len]. Column sums run over fixed chunks of 256 trajectories, then over chunks, in a
+ * fixed order, so the result is bitwise reproducible.
+ *   workspace: device, >= ssa_ensemble_mean_workspace_bytes(n_traj, row_len).
+ */
+size_t ssa_ensemble_mean_workspace_bytes(int64_t n_traj, int64_t row_len);
+ssa_status ssa_ensemble_mean(const void *obs, int32_t obs_is_int, int64_t n_traj, int64_t row_len,
+                             void *workspace, size_t workspace_bytes, float *mean_out, void *stream);
+
+/*
+ * ssa_philox_uniforms -- test hook: out[r][q] = u_q of step step[r] of trajectory traj[r]
+ * (device uint64 arrays [n], device float out [n][n_words]).
+ */
+ssa_status ssa_philox_uniforms(uint64_t seed, const uint64_t *traj, const uint64_t *step,
+                               int64_t n, int32_t n_words, float *out, void *stream);
+
+const char *ssa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSA_H */

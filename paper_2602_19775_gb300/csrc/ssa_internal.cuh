@@ -1,0 +1,215 @@
+// ssa_internal.cuh -- internal structures and device helpers of the GB300 SSA library.
+//
+// Everything here is private to libssa; the public ABI is include/ssa.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "../../include/ssa.h"
+
+namespace ssa {
+
+// ------------------------------------------------------------------------------------------
+// Device-side network tables (built once by ssa_create_network)
+//   rx[j]     = {r1, r2, s_begin, s_end}: reactant slots (canonical: r1 = -1 means order 0,
+//               r2 = -1 means first order, r1 == r2 a homodimer) and the CSR range of v_j
+//   stoich[e] = (species << 8) | (uint8)delta
+// The two arrays are contiguous (rx first) so one bulk copy stages both into shared memory.
+// ------------------------------------------------------------------------------------------
+struct NetTables {
+    const int4 *rx;
+    const int *stoich;
+    const int *rate_index;
+    int N, M, P, nnz;
+    uint32_t tab_bytes;  // 16 * M + 4 * nnz_pad, a multiple of 16
+};
+
+// per-step uniform mapping: u = ((x >> 9) + 1/2) 2^-23, exact in binary32
+__device__ __forceinline__ float u01(uint32_t x)
+{
+    return __fmaf_rn(__uint2float_rn(x >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, two 32x32->64 products each,
+// round keys bumped by the two Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &r, int q)
+{
+    return q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+}
+
+// Mass-action combinatorial factor h_j(X) (Section 2), formed exactly in 64-bit integers and
+// rounded once to binary32, and the propensity a_j = k_j h_j in binary32 (no contraction).
+// X points at this trajectory's counts with a stride between species.
+__device__ __forceinline__ float mass_action_h(const int4 rx, const int *X, int stride)
+{
+    if (rx.x < 0) return 1.0f;
+    const long long x1 = X[rx.x * stride];
+    if (rx.y < 0) return __ll2float_rn(x1);
+    if (rx.y == rx.x) return __ll2float_rn((x1 * (x1 - 1)) >> 1);
+    const long long x2 = X[rx.y * stride];
+    return __ll2float_rn(x1 * x2);
+}
+
+__device__ __forceinline__ int stoich_species(int e) { return e >> 8; }
+__device__ __forceinline__ int stoich_delta(int e) { return (int)(signed char)(e & 0xff); }
+
+// ------------------------------------------------------------------------------------------
+// Shared-memory staging of the network tables and the per-call rate constants with the bulk
+// (non-tensor) TMA copy engine: cp.async.bulk global -> shared, completion on an mbarrier.
+// The wait is bounded; on timeout the block records an error and skips its work.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: at most `limit` polls (each try_wait may suspend the thread for a while).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint32_t limit)
+{
+    for (uint32_t it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+// Error bits written to the workspace flag word by kernels.
+constexpr int kErrStageTimeout = 1;
+constexpr int kErrBadSamples = 2;
+constexpr int kErrBadObs = 4;
+
+// Stage `tab_bytes` of tables and `k_bytes` of rate constants (both multiples of 16, both
+// 16-byte aligned) into s_tab / s_k. Every thread of the block must call this. Returns false
+// (and sets err_flag) if the copy did not complete within the bound.
+__device__ __forceinline__ bool stage_tables(void *s_tab, const void *g_tab, uint32_t tab_bytes, void *s_k,
+                                             const void *g_k, uint32_t k_bytes, uint64_t *bar,
+                                             int *s_ok, int *err_flag)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, tab_bytes + k_bytes);
+        bulk_copy_g2s(s_tab, g_tab, tab_bytes, bar);
+        bulk_copy_g2s(s_k, g_k, k_bytes, bar);
+        bool ok = mbar_wait_bounded(bar, 0, kWaitLimit);
+        if (!ok) {
+            atomicOr(err_flag, kErrStageTimeout);
+            // give the copies in flight a second bounded chance to land before the block exits
+            mbar_wait_bounded(bar, 0, kWaitLimit);
+        }
+        *s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// Kernel parameter blocks
+// ------------------------------------------------------------------------------------------
+struct FwdParams {
+    const int4 *rx;
+    const float *k_rates;  // [M padded to 4]
+    uint32_t tab_bytes, k_bytes;
+    int N, M, nnz;
+    int64_t n_traj;
+    uint64_t traj_offset, seed;
+    const int *x0;
+    int x0_per_traj;
+    double t_end;
+    const double *ts;
+    int S;
+    const int *obs_sp;
+    int n_obs;
+    int64_t max_steps;
+    void *obs_out;
+    int *draws, *status;
+    const int *flag;  // workspace error flags (bad sample times -> every trajectory BAD_INPUT)
+    int *err;
+    // record
+    int K;
+    uint4 *ev;        // [ev_rows][n_traj], 8 uint16 events per uint4
+    int *ckpt;        // [n_ckpt][N][n_traj]
+    int *brk_k;       // [S][n_traj]
+    float *brk_a;     // [S][n_traj]
+    int *xfinal;      // [N][n_traj]
+    // replay
+    const uint16_t *ev_in;
+    const int *n_ev_in;
+    int64_t ev_in_stride;
+};
+
+struct AdjParams {
+    const int4 *rx;
+    const float *k_rates;
+    uint32_t tab_bytes, k_bytes;
+    int N, M, nnz;
+    int64_t n_traj;
+    uint64_t traj_offset, seed;
+    const double *ts;
+    int S;
+    const int *obs_sp;
+    int n_obs;
+    int K;
+    const int *draws, *status;
+    const uint4 *ev;
+    const int *ckpt;
+    const int *brk_k;
+    const float *brk_a;
+    const int *xfinal;
+    const float *dl_dobs;
+    int64_t dl_stride;  // elements between trajectories (0 = shared)
+    float invT;
+    float *partial;   // [gridDim.x][M]
+    int *mismatch;    // backward consistency failures
+    int *err;
+};
+
+}  // namespace ssa

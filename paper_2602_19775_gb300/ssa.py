@@ -1,0 +1,253 @@
+"""PyTorch front end of libssa: device buffers, streams and a torch.autograd.Function.
+
+PyTorch provides device memory and the current CUDA stream; every step of the simulation and of
+the straight-through adjoint runs in the library's CUDA kernels (include/ssa.h). Nothing here
+computes on the CPU, and there is no fallback: without a CUDA device or without libssa.so the
+calls raise.
+
+    net = Network(spec)                                   # any object with the array fields
+    out = forward(net, theta, n_traj=65536, x0=x0, t_end=50.0, sample_times=ts,
+                  obs_species=[0], seed=0, readout="linear", record=True)
+    dtheta = backward(out, dl_dobs, temperature=0.5)      # dL/dlog k  [P]
+
+    obs = simulate(net, theta, ..., temperature=0.5)      # autograd: obs.backward(...) -> theta.grad
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FwdOpts, SSAError, check
+
+READOUTS = {"hold": _lib.SSA_READOUT_HOLD, "linear": _lib.SSA_READOUT_LINEAR}
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise SSAError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise SSAError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise SSAError(f"{name} must be contiguous")
+
+
+class Network:
+    """A mass-action network held by the library (ssa_create_network)."""
+
+    def __init__(self, spec):
+        self.spec = spec
+        self.n_species = int(spec.n_species)
+        self.n_reactions = int(spec.n_reactions)
+        self.n_params = int(spec.n_params)
+        L = _lib.lib()
+        arrs = [np.ascontiguousarray(getattr(spec, f), dtype=np.int32)
+                for f in ("reactants", "stoich_ptr", "stoich_species", "stoich_delta", "rate_index")]
+        self._keep = arrs
+        h = ctypes.c_void_p()
+        check(L.ssa_create_network(self.n_species, self.n_reactions,
+                                   *(a.ctypes.data_as(ctypes.c_void_p) for a in arrs[:4]),
+                                   self.n_params, arrs[4].ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.lib().ssa_destroy_network(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Run:
+    """A forward's run handle plus the buffers it references (workspace, outputs)."""
+
+    def __init__(self, handle, workspace, net, n_traj, S, n_obs, readout):
+        self.handle = handle
+        self.workspace = workspace
+        self.net = net
+        self.n_traj = n_traj
+        self.S = S
+        self.n_obs = n_obs
+        self.readout = readout
+
+    def status_counts(self, stream=None):
+        counts = (ctypes.c_int64 * _lib.SSA_TRAJ_N_CODES)()
+        mism = ctypes.c_int64()
+        check(_lib.lib().ssa_run_status(self.handle, counts, ctypes.byref(mism), _stream(stream)))
+        return {name: int(counts[c]) for c, name in enumerate(_lib.TRAJ_CODES)}, int(mism.value)
+
+    def events(self, stride: int, stream=None) -> torch.Tensor:
+        out = torch.empty((self.n_traj, stride), dtype=torch.int32, device=self.workspace.device)
+        check(_lib.lib().ssa_run_events(self.handle, _ptr(out), stride, _stream(stream)))
+        return out
+
+    def brackets(self, stream=None) -> torch.Tensor:
+        out = torch.empty((self.n_traj, self.S), dtype=torch.int32, device=self.workspace.device)
+        check(_lib.lib().ssa_run_brackets(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.lib().ssa_destroy_run(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class ForwardResult:
+    obs: torch.Tensor       # [n_traj, S, n_obs] int32 (hold) or float32 (linear)
+    draws: torch.Tensor     # [n_traj] int32
+    status: torch.Tensor    # [n_traj] int32
+    run: Run
+
+
+def make_opts(readout="hold", record=False, ckpt_interval=64, max_steps=1 << 20, threads_per_traj=0,
+              block_threads=0) -> FwdOpts:
+    ro = READOUTS[readout] if isinstance(readout, str) else int(readout)
+    return FwdOpts(ro, 1 if record else 0, int(ckpt_interval), int(threads_per_traj), int(max_steps),
+                   int(block_threads), 0)
+
+
+def workspace_bytes(net: Network, n_traj: int, n_samples: int, opts: FwdOpts) -> int:
+    n = _lib.lib().ssa_forward_workspace_bytes(net.handle, n_traj, n_samples, ctypes.byref(opts))
+    if n == 0:
+        raise SSAError("invalid arguments for ssa_forward_workspace_bytes")
+    return int(n)
+
+
+def _as_cuda(x, dtype, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.asarray(x), dtype=dtype, device=device).contiguous()
+
+
+def forward(net: Network, log_rates, n_traj: int, x0, t_end: float, sample_times, obs_species, seed: int,
+            readout="hold", record=False, ckpt_interval=64, max_steps=1 << 20, traj_offset=0,
+            threads_per_traj=0, block_threads=0, replay_events=None, replay_n_events=None,
+            workspace: torch.Tensor | None = None, obs_out: torch.Tensor | None = None,
+            stream=None, device=None) -> ForwardResult:
+    """ssa_forward (or ssa_forward_replay when replay_events is given) on the current stream."""
+    device = torch.device(device) if device is not None else (
+        log_rates.device if isinstance(log_rates, torch.Tensor) and log_rates.is_cuda else torch.device("cuda"))
+    theta = _as_cuda(log_rates, torch.float32, device)
+    x0 = _as_cuda(x0, torch.int32, device)
+    ts = _as_cuda(sample_times, torch.float64, device)
+    obs_sp = _as_cuda(obs_species, torch.int32, device)
+    S, n_obs = int(ts.numel()), int(obs_sp.numel())
+    opts = make_opts(readout, record, ckpt_interval, max_steps, threads_per_traj, block_threads)
+    need = workspace_bytes(net, n_traj, S, opts)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=device)
+    odt = torch.int32 if opts.readout == _lib.SSA_READOUT_HOLD else torch.float32
+    if obs_out is None:
+        obs_out = torch.empty((n_traj, S, n_obs), dtype=odt, device=device)
+    draws = torch.empty(n_traj, dtype=torch.int32, device=device)
+    status = torch.empty(n_traj, dtype=torch.int32, device=device)
+    per_traj = 1 if x0.dim() == 2 else 0
+    h = ctypes.c_void_p()
+    L = _lib.lib()
+    common = (net.handle, _ptr(theta), int(n_traj), int(traj_offset), _ptr(x0), per_traj, float(t_end), _ptr(ts), S,
+              _ptr(obs_sp), n_obs, ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(opts))
+    if replay_events is None:
+        check(L.ssa_forward(*common, _ptr(workspace), need, _ptr(obs_out), _ptr(draws), _ptr(status),
+                            _stream(stream), ctypes.byref(h)))
+    else:
+        ev = _as_cuda(replay_events, torch.int32, device).to(torch.uint16) if not (
+            isinstance(replay_events, torch.Tensor) and replay_events.dtype == torch.uint16) else replay_events
+        nev = _as_cuda(replay_n_events, torch.int32, device)
+        check(L.ssa_forward_replay(*common, _ptr(ev), _ptr(nev), int(ev.shape[1]), _ptr(workspace), need,
+                                   _ptr(obs_out), _ptr(draws), _ptr(status), _stream(stream), ctypes.byref(h)))
+    run = Run(h, workspace, net, n_traj, S, n_obs, opts.readout)
+    run._keep = (theta, x0, ts, obs_sp)
+    return ForwardResult(obs_out, draws, status, run)
+
+
+def backward(fwd: ForwardResult | Run, dl_dobs: torch.Tensor, temperature: float, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    """ssa_backward: dL/dlog k [P] (float32) for a recorded forward."""
+    run = fwd.run if isinstance(fwd, ForwardResult) else fwd
+    g = dl_dobs.to(torch.float32).contiguous()
+    if tuple(g.shape) == (run.n_traj, run.S, run.n_obs):
+        stride = run.S * run.n_obs
+    elif tuple(g.shape) == (run.S, run.n_obs):
+        stride = 0  # the same upstream gradient for every trajectory
+    else:
+        raise SSAError(f"dl_dobs shape {tuple(g.shape)} is neither {(run.n_traj, run.S, run.n_obs)} "
+                       f"nor {(run.S, run.n_obs)}")
+    if out is None:
+        out = torch.empty(run.net.n_params, dtype=torch.float32, device=g.device)
+    check(_lib.lib().ssa_backward(run.handle, _ptr(g), stride, ctypes.c_float(float(temperature)), _ptr(out),
+                                  _stream(stream)))
+    return out
+
+
+def ensemble_mean(obs: torch.Tensor, stream=None) -> torch.Tensor:
+    """ssa_ensemble_mean over the first axis (deterministic order) -> float32 [obs.shape[1:]]."""
+    obs = obs.contiguous()
+    n = int(obs.shape[0])
+    row = int(np.prod(obs.shape[1:])) if obs.dim() > 1 else 1
+    L = _lib.lib()
+    need = int(L.ssa_ensemble_mean_workspace_bytes(n, row))
+    ws = torch.empty(max(need, 4), dtype=torch.uint8, device=obs.device)
+    out = torch.empty(obs.shape[1:], dtype=torch.float32, device=obs.device)
+    is_int = 1 if obs.dtype == torch.int32 else 0
+    if not is_int and obs.dtype != torch.float32:
+        raise SSAError("ensemble_mean takes int32 or float32 observables")
+    check(L.ssa_ensemble_mean(_ptr(obs), is_int, n, row, _ptr(ws), need, _ptr(out), _stream(stream)))
+    return out
+
+
+def philox_uniforms(seed: int, traj, step, n_words: int, device="cuda") -> torch.Tensor:
+    traj = _as_cuda(np.asarray(traj, dtype=np.int64), torch.int64, device)
+    step = _as_cuda(np.asarray(step, dtype=np.int64), torch.int64, device)
+    out = torch.empty((traj.numel(), n_words), dtype=torch.float32, device=device)
+    check(_lib.lib().ssa_philox_uniforms(ctypes.c_uint64(int(seed) & (2**64 - 1)), _ptr(traj), _ptr(step),
+                                         int(traj.numel()), int(n_words), _ptr(out), _stream()))
+    return out
+
+
+class SSAFunction(torch.autograd.Function):
+    """obs = SSA(theta) with the straight-through gradient of Eqs. 5 and 7 in backward."""
+
+    @staticmethod
+    def forward(ctx, log_rates, net, n_traj, x0, t_end, sample_times, obs_species, seed, readout, temperature,
+                ckpt_interval, max_steps, traj_offset):
+        res = forward(net, log_rates.detach(), n_traj, x0, t_end, sample_times, obs_species, seed, readout=readout,
+                      record=True, ckpt_interval=ckpt_interval, max_steps=max_steps, traj_offset=traj_offset)
+        ctx.run = res.run
+        ctx.temperature = float(temperature)
+        ctx.status = res.status
+        return res.obs.to(torch.float32)
+
+    @staticmethod
+    def backward(ctx, grad_obs):
+        g = backward(ctx.run, grad_obs, ctx.temperature)
+        return (g,) + (None,) * 12
+
+
+def simulate(net: Network, log_rates: torch.Tensor, n_traj: int, x0, t_end: float, sample_times, obs_species,
+             seed: int, readout="linear", temperature=1.0, ckpt_interval=64, max_steps=1 << 20, traj_offset=0):
+    """Differentiable forward: obs [n_traj, S, n_obs] float32; obs.backward() fills log_rates.grad."""
+    return SSAFunction.apply(log_rates, net, n_traj, x0, t_end, sample_times, obs_species, seed, readout,
+                             temperature, ckpt_interval, max_steps, traj_offset)
