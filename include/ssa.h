@@ -194,6 +194,26 @@ ssa_status ssa_ensemble_mean(const void *obs, int32_t obs_is_int, int64_t n_traj
                              void *workspace, size_t workspace_bytes, float *mean_out, void *stream);
 
 /*
+ * ssa_ensemble_mean_static -- the same mean as ssa_ensemble_mean, for callers that cannot allocate
+ * device memory when they call (recording into a CUDA graph, where cudaMalloc is not allowed during
+ * stream capture; real-time loops that forbid allocator calls; libraries with no access to the
+ * application's allocator). The paper has no counterpart: this is an interface convenience.
+ *   It allocates nothing: the column partial sums live in a fixed device array of 1,048,576 floats
+ *   (4 MiB) that the library defines and every GPU that loads the library keeps until the process
+ *   exits. ceil(n_traj / 256) * row_len must not exceed 1,048,576; larger inputs are rejected with
+ *   SSA_ERR_UNSUPPORTED (use ssa_ensemble_mean with a workspace instead).
+ *   The first call on a device looks up that device's address of the array
+ *   (cudaGetSymbolAddress); make that first call before any stream capture on the device.
+ *   All calls share the one array: calls that may run at the same time on the GPU (different
+ *   streams without ordering between them) race and corrupt each other's result. Each call writes
+ *   every scratch entry it reads, so no clearing is needed between calls.
+ *   obs device [n_traj][row_len] (int32 when obs_is_int, else float); mean_out device float
+ *   [row_len].
+ */
+ssa_status ssa_ensemble_mean_static(const void *obs, int32_t obs_is_int, int64_t n_traj,
+                                    int64_t row_len, float *mean_out, void *stream);
+
+/*
  * ssa_philox_uniforms -- test hook: out[r][q] = u_q of step step[r] of trajectory traj[r]
  * (device uint64 arrays [n], device float out [n][n_words]).
  */

@@ -56,6 +56,11 @@ static ssa_status fail(ssa_status code, const char *fmt, ...)
 
 extern "C" const char *ssa_last_error(void) { return g_err; }
 
+namespace ssa {
+// record an error text for ssa_last_error from another translation unit
+ssa_status set_error(ssa_status code, const char *text) { return fail(code, "%s", text); }
+}  // namespace ssa
+
 // ---------------------------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------------------------
