@@ -65,8 +65,8 @@ ssa_status set_error(ssa_status code, const char *text) { return fail(code, "%s"
 // handles
 // ---------------------------------------------------------------------------------------------
 struct ssa_network {
-    int32_t N, M, P, nnz, nnz_pad;
-    void *d_blob;       // [rx: int4 M][stoich: int nnz_pad][rate_index: int M_pad4]
+    int32_t N, M, Mp, P, nnz, nnz_pad;  // Mp = 4 * ceil((M + 1)/4): padded reaction count
+    void *d_blob;       // [rx: int4 Mp][stoich: int nnz_pad][rate_index: int Mp]
     int4 *d_rx;
     int *d_stoich;
     int *d_rate_index;
@@ -96,7 +96,7 @@ WsLayout layout(const ssa_network *net, int64_t n, int32_t S, const ssa_fwd_opts
         off = align_up(off + bytes, kAlign);
         return at;
     };
-    L.M_pad = (net->M + 3) / 4 * 4;
+    L.M_pad = net->Mp;
     L.flag = take(16 * sizeof(int));
     L.counts = take(SSA_TRAJ_N_CODES * sizeof(unsigned long long));
     L.k_rates = take((size_t)L.M_pad * sizeof(float));
@@ -142,16 +142,17 @@ size_t smem_limit()
     return (size_t)v;
 }
 
-size_t fwd_smem(const ssa_network *net, int block) { return net->tab_bytes + ((net->M + 3) / 4 * 4) * 4 + 16 + (size_t)net->N * block * 4; }
+size_t fwd_smem(const ssa_network *net, int block) { return net->tab_bytes + (size_t)net->Mp * 4 + 16 + (size_t)net->N * block * 4; }
 size_t adj_smem(const ssa_network *net, int block)
 {
-    return net->tab_bytes + ((net->M + 3) / 4 * 4) * 4 + 16 + (size_t)(3 * net->N + 2 * net->M) * block * 4;
+    return net->tab_bytes + (size_t)net->Mp * 4 + 16 + (size_t)(3 * net->N + 2 * net->M) * block * 4;
 }
 
 int pick_block(size_t (*need)(const ssa_network *, int), const ssa_network *net, int requested, size_t limit)
 {
     if (requested) return need(net, requested) <= limit ? requested : 0;
-    for (int b : {128, 64, 32})
+    // small blocks spread an uneven trajectory count evenly over the 152 SMs
+    for (int b : {64, 32})
         if (need(net, b) <= limit) return b;
     return 0;
 }
@@ -185,7 +186,8 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
         if (stoich_ptr[j + 1] < stoich_ptr[j]) return fail(SSA_ERR_INVALID_ARG, "stoich_ptr not monotone at %d", j);
     const int nnz = stoich_ptr[n_reactions];
     if (nnz > 0 && (!stoich_species || !stoich_delta)) return fail(SSA_ERR_INVALID_ARG, "NULL stoichiometry");
-    std::vector<int4> rx(n_reactions);
+    const int Mp = (n_reactions + 4) / 4 * 4;
+    std::vector<int4> rx(Mp, make_int4(-1, -1, 0, 0));  // padding: order 0, no change, rate 0
     for (int j = 0; j < n_reactions; ++j) {
         int r1 = reactants[2 * j], r2 = reactants[2 * j + 1];
         if (r1 < -1 || r1 >= n_species || r2 < -1 || r2 >= n_species)
@@ -204,8 +206,7 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
             return fail(SSA_ERR_INVALID_ARG, "stoich_delta[%d] = %d outside [-127, 127]", e, stoich_delta[e]);
         st[e] = (stoich_species[e] << 8) | (stoich_delta[e] & 0xff);
     }
-    const int M_pad = (n_reactions + 3) / 4 * 4;
-    std::vector<int> ri(M_pad, 0);
+    std::vector<int> ri(Mp, 0);
     for (int j = 0; j < n_reactions; ++j) ri[j] = rate_index[j];
 
     ssa_network *net = new (std::nothrow) ssa_network();
@@ -213,10 +214,11 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
     net->N = n_species;
     net->M = n_reactions;
     net->P = n_params;
+    net->Mp = Mp;
     net->nnz = nnz;
     net->nnz_pad = nnz_pad;
-    net->tab_bytes = (uint32_t)(16 * n_reactions + 4 * nnz_pad);
-    const size_t bytes = net->tab_bytes + (size_t)M_pad * 4;
+    net->tab_bytes = (uint32_t)(16 * Mp + 4 * nnz_pad);
+    const size_t bytes = net->tab_bytes + (size_t)Mp * 4;
     cudaError_t e = cudaMalloc(&net->d_blob, bytes);
     if (e != cudaSuccess) {
         delete net;
@@ -224,11 +226,11 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
     }
     unsigned char *b = static_cast<unsigned char *>(net->d_blob);
     net->d_rx = reinterpret_cast<int4 *>(b);
-    net->d_stoich = reinterpret_cast<int *>(b + 16 * n_reactions);
+    net->d_stoich = reinterpret_cast<int *>(b + 16 * Mp);
     net->d_rate_index = reinterpret_cast<int *>(b + net->tab_bytes);
-    e = cudaMemcpy(net->d_rx, rx.data(), 16 * (size_t)n_reactions, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(net->d_rx, rx.data(), 16 * (size_t)Mp, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(net->d_stoich, st.data(), 4 * (size_t)nnz_pad, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(net->d_rate_index, ri.data(), 4 * (size_t)M_pad, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(net->d_rate_index, ri.data(), 4 * (size_t)Mp, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(net->d_blob);
         delete net;
@@ -297,6 +299,7 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     p.k_bytes = (uint32_t)(L.M_pad * 4);
     p.N = net->N;
     p.M = net->M;
+    p.Mp = net->Mp;
     p.nnz = net->nnz;
     p.n_traj = n_traj;
     p.traj_offset = (uint64_t)traj_offset;
@@ -398,6 +401,7 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     p.k_bytes = (uint32_t)(L.M_pad * 4);
     p.N = net->N;
     p.M = net->M;
+    p.Mp = net->Mp;
     p.nnz = net->nnz;
     p.n_traj = run->n_traj;
     p.traj_offset = run->traj_offset;

@@ -23,7 +23,68 @@
 
 namespace ssa {
 
-template <int READOUT>
+// Forward helpers shared bit for bit with the forward kernels (same binary32 operations).
+template <int NQ>
+__device__ __forceinline__ void step_noise_b(float (&E)[NQ], uint32_t k, uint32_t c2, uint32_t c3, uint32_t key0,
+                                             uint32_t key1)
+{
+#pragma unroll
+    for (int b = 0; b < (NQ + 3) / 4; ++b) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
+        if (4 * b + 0 < NQ) E[4 * b + 0] = -logf(u01(r.x));
+        if (4 * b + 1 < NQ) E[4 * b + 1] = -logf(u01(r.y));
+        if (4 * b + 2 < NQ) E[4 * b + 2] = -logf(u01(r.z));
+        if (4 * b + 3 < NQ) E[4 * b + 3] = -logf(u01(r.w));
+    }
+}
+
+__device__ __forceinline__ float exp_variate_b(uint32_t k, int q, uint32_t c2, uint32_t c3, uint32_t key0,
+                                               uint32_t key1, uint4 &cache, int &cached_b)
+{
+    const int b = q >> 2;
+    if (b != cached_b) {
+        cache = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
+        cached_b = b;
+    }
+    return -logf(u01(word_of(cache, q & 3)));
+}
+
+__device__ __forceinline__ void race_b(float a, float E, int j, float &ab, float &Eb, int &jb)
+{
+    if (__fmul_rn(a, Eb) > __fmul_rn(ab, E)) {
+        ab = a;
+        Eb = E;
+        jb = j;
+    }
+}
+
+// State adjoint of reaction j: choice path psi * dlog a/dX (a > 0) and waiting-time path
+// c_tau * da/dX with c_tau = dL/da0 * k_j (polynomial derivative, also where a_j = 0).
+__device__ __forceinline__ void reaction_state_adjoint(const int4 rx, const int *X, int B, float a, float h, float psi,
+                                                       float c_tau, float *dlam)
+{
+    if (rx.x < 0) return;
+    const float x1 = (float)X[rx.x * B];
+    if (rx.y < 0) {
+        dlam[rx.x * B] += (a > 0.0f ? psi / x1 : 0.0f) + c_tau;
+    } else if (rx.y == rx.x) {
+        const float dh = x1 - 0.5f;  // d/dX [X (X - 1)/2]
+        dlam[rx.x * B] += (a > 0.0f ? psi * dh / h : 0.0f) + c_tau * dh;
+    } else {
+        const float x2 = (float)X[rx.y * B];
+        dlam[rx.x * B] += (a > 0.0f ? psi / x1 : 0.0f) + c_tau * x2;
+        dlam[rx.y * B] += (a > 0.0f ? psi / x2 : 0.0f) + c_tau * x1;
+    }
+}
+
+__device__ __forceinline__ float stoich_dot(const int4 rx, const int *s_st, const float *lam, int B)
+{
+    float w = 0.0f;
+    for (int e = rx.z; e < rx.w; ++e) w += (float)stoich_delta(s_st[e]) * lam[stoich_species(s_st[e]) * B];
+    return w;
+}
+
+template <int READOUT, int MC>
 __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -31,7 +92,7 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
     const int tid = threadIdx.x;
     const int N = p.N, M = p.M;
     int4 *s_rx = reinterpret_cast<int4 *>(smem);
-    int *s_st = reinterpret_cast<int *>(smem + 16 * M);
+    int *s_st = reinterpret_cast<int *>(smem + 16 * p.Mp);
     float *s_k = reinterpret_cast<float *>(smem + p.tab_bytes);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + p.tab_bytes + p.k_bytes);
     int *s_ok = reinterpret_cast<int *>(smem + p.tab_bytes + p.k_bytes + 8);
@@ -39,29 +100,31 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
     int *s_X = reinterpret_cast<int *>(dyn);
     float *s_lam = reinterpret_cast<float *>(dyn) + (size_t)N * B;
     float *s_dlam = s_lam + (size_t)N * B;
-    float *s_q = s_dlam + (size_t)N * B;
-    float *s_dA = s_q + (size_t)M * B;
+    float *s_dA = s_dlam + (size_t)N * B;  // [M][B]
+    float *s_q = s_dA + (size_t)M * B;     // [M][B], runtime-size variant only
 
     if (!stage_tables(smem, p.rx, p.tab_bytes, s_k, p.k_rates, p.k_bytes, s_bar, s_ok, p.err)) {
         for (int j = tid; j < M; j += B) p.partial[(int64_t)blockIdx.x * M + j] = 0.0f;
         return;
     }
-    for (int j = 0; j < M; ++j) s_dA[j * B + tid] = 0.0f;
 
     const int64_t n = p.n_traj;
     const int64_t i = (int64_t)blockIdx.x * B + tid;
     int st = -1;
     if (i < n) st = p.status[i];
     const bool active = st == SSA_TRAJ_OK || st == SSA_TRAJ_ABSORBED || st == SSA_TRAJ_STEP_CAP;
+    float dAr[MC > 0 ? MC : 1];
+#pragma unroll
+    for (int j = 0; j < (MC > 0 ? MC : 1); ++j) dAr[j] = 0.0f;
+    if (MC == 0)
+        for (int j = 0; j < M; ++j) s_dA[j * B + tid] = 0.0f;
 
     if (active) {
         int *X = s_X + tid;
         float *lam = s_lam + tid;
         float *dlam = s_dlam + tid;
-        float *qb = s_q + tid;
-        float *dA = s_dA + tid;
-        const int64_t d = p.draws[i];
-        const int64_t L = (st == SSA_TRAJ_OK) ? d - 1 : d;  // index of the last visited state
+        const int d = p.draws[i];
+        const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;  // index of the last visited state
         for (int s = 0; s < N; ++s) {
             X[s * B] = p.xfinal[(int64_t)s * n + i];
             lam[s * B] = 0.0f;
@@ -70,16 +133,15 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
         const uint64_t gid = p.traj_offset + (uint64_t)i;
         const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32);
         const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
-        const int nb = (M + 4) >> 2;
         const float invT = p.invT;
         const float *gl = p.dl_dobs + i * p.dl_stride;
 
-        int64_t row_cached = -1;
+        int row_cached = -1;
         uint4 row = make_uint4(0, 0, 0, 0);
-        auto event_at = [&](int64_t kk) -> int {
-            const int64_t r = kk >> 3;
-            if (r != row_cached) { row = p.ev[r * n + i]; row_cached = r; }
-            const int slot = (int)(kk & 7);
+        auto event_at = [&](int kk) -> int {
+            const int r = kk >> 3;
+            if (r != row_cached) { row = p.ev[(int64_t)r * n + i]; row_cached = r; }
+            const int slot = kk & 7;
             const uint32_t w = word_of(row, slot >> 1);
             return (slot & 1) ? (int)(w >> 16) : (int)(w & 0xffff);
         };
@@ -88,42 +150,58 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
         int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
         float mu = 0.0f;
         int mism = 0;
+        int ck_row = L / p.K, ck_off = L - ck_row * p.K;  // checkpoint c holds X_{cK}
 
-        for (int64_t k = L; k >= 0; --k) {
-            const bool draw = (k < L) || (st == SSA_TRAJ_OK);
+        constexpr int NQ = MC > 0 ? MC + 1 : 1;
+        float E[NQ], En[NQ];
+        const bool draw_last = st == SSA_TRAJ_OK;
+        if (MC > 0) step_noise_b<NQ>(E, (uint32_t)(draw_last ? L : (L > 0 ? L - 1 : 0)), c2, c3, key0, key1);
+
+        for (int k = L; k >= 0; --k) {
+            const bool draw = (k < L) || draw_last;
             const int s_top = s_hi;
-            while (s_hi >= 0 && brk_next == (int)k) {
+            while (s_hi >= 0 && brk_next == k) {
                 --s_hi;
                 brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
             }
             // samples s_hi+1 .. s_top are bracketed by state k
             if (draw) {
                 const int jk = event_at(k);
-                // pass 1: the forward's propensities, a0 and keys, bit for bit
-                float a0 = 0.0f, E0 = 1.0f, best = 0.0f, lmax = -CUDART_INF_F;
+                float a0 = 0.0f, ab = 0.0f, Eb = 1.0f, E0, lmax = -CUDART_INF_F;
                 int jb = -1;
-                for (int b = 0; b < nb; ++b) {
-                    const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
+                float ar[MC > 0 ? MC : 1], lr[MC > 0 ? MC : 1];
+                // pass 1: the forward's propensities, a0 and race, bit for bit; log2 keys
+                if constexpr (MC > 0) {
+                    if (k > 0) step_noise_b<NQ>(En, (uint32_t)(k - 1), c2, c3, key0, key1);  // prefetch
+                    E0 = E[0];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = 4 * b + q - 1;
-                        if (j < 0) { E0 = -logf(u01(r.x)); continue; }
-                        if (j >= M) break;
+                    for (int j = 0; j < MC; ++j) {
+                        const float a = __fmul_rn(s_k[j], mass_action_h(s_rx[j], X, B));
+                        a0 = __fadd_rn(a0, a);
+                        race_b(a, E[j + 1], j, ab, Eb, jb);
+                        ar[j] = a;
+                        lr[j] = a > 0.0f ? __log2f(a) - __log2f(E[j + 1]) : -CUDART_INF_F;
+                        lmax = fmaxf(lmax, lr[j]);
+                    }
+                } else {
+                    uint4 cache;
+                    int cb = -1;
+                    E0 = exp_variate_b((uint32_t)k, 0, c2, c3, key0, key1, cache, cb);
+                    for (int j = 0; j < M; ++j) {
                         const float a = __fmul_rn(s_k[j], mass_action_h(s_rx[j], X, B));
                         a0 = __fadd_rn(a0, a);
                         float l = -CUDART_INF_F;
                         if (a > 0.0f) {
-                            const float E = -logf(u01(word_of(r, q)));
-                            const float key = __fdiv_rn(a, E);
-                            if (key > best) { best = key; jb = j; }
-                            l = __log2f(key);
+                            const float Ej = exp_variate_b((uint32_t)k, j + 1, c2, c3, key0, key1, cache, cb);
+                            race_b(a, Ej, j, ab, Eb, jb);
+                            l = __log2f(a) - __log2f(Ej);
                             lmax = fmaxf(lmax, l);
                         }
-                        qb[j * B] = l;
+                        s_q[j * B + tid] = l;
                     }
                 }
                 mism += (jb != jk);
-                const float tau = __fdiv_rn(E0, a0);
+                const float tau = __fdividef(E0, a0);
                 const int4 rk = s_rx[jk];
                 // readout terms that involve X_{k+1} and the clock (LINEAR interpolation)
                 float dt_dir = 0.0f, dtau_dir = 0.0f;
@@ -146,50 +224,47 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
                     }
                 }
                 const float dtau = mu + dtau_dir;
-                // pass 2: soft sample weights and w_j = v_j . lambda
-                float Z = 0.0f, Wq = 0.0f;
-                for (int j = 0; j < M; ++j) {
-                    const float l = qb[j * B];
-                    const float q = (l == -CUDART_INF_F) ? 0.0f : exp2f((l - lmax) * invT);
-                    qb[j * B] = q;
-                    if (q > 0.0f) {
-                        const int4 rx = s_rx[j];
-                        float w = 0.0f;
-                        for (int e = rx.z; e < rx.w; ++e) w += (float)stoich_delta(s_st[e]) * lam[stoich_species(s_st[e]) * B];
-                        Z += q;
-                        Wq += q * w;
-                    }
-                }
-                const float invZ = 1.0f / Z;
-                const float Wbar = Wq * invZ;
                 const float dLda0 = -dtau * tau / a0;
-                // pass 3: per-reaction adjoints and the state adjoint
-                for (int j = 0; j < M; ++j) {
-                    const int4 rx = s_rx[j];
-                    const float kj = s_k[j];
-                    const float h = mass_action_h(rx, X, B);
-                    const float a = __fmul_rn(kj, h);
-                    const float q = qb[j * B];
-                    float psi = 0.0f;
-                    if (q > 0.0f) {
-                        float w = 0.0f;
-                        for (int e = rx.z; e < rx.w; ++e) w += (float)stoich_delta(s_st[e]) * lam[stoich_species(s_st[e]) * B];
-                        psi = q * invZ * (w - Wbar) * invT;
+                // pass 2: soft-sample weights y~_j ~ exp2((l_j - l_max)/T) and W = sum y~ w
+                float Z = 0.0f, Wq = 0.0f;
+                if constexpr (MC > 0) {
+                    float wr[MC];
+#pragma unroll
+                    for (int j = 0; j < MC; ++j) {
+                        const float q = lr[j] == -CUDART_INF_F ? 0.0f : exp2f((lr[j] - lmax) * invT);
+                        lr[j] = q;
+                        wr[j] = stoich_dot(s_rx[j], s_st, lam, B);
+                        Z += q;
+                        Wq += q * wr[j];
                     }
-                    dA[j * B] += psi + dLda0 * a;
-                    if (rx.x >= 0) {
-                        const float x1 = (float)X[rx.x * B];
-                        const float c_tau = dLda0 * kj;
-                        if (rx.y < 0) {
-                            dlam[rx.x * B] += (a > 0.0f ? psi / x1 : 0.0f) + c_tau;
-                        } else if (rx.y == rx.x) {
-                            const float dh = x1 - 0.5f;  // d/dX [X (X - 1)/2]
-                            dlam[rx.x * B] += (a > 0.0f ? psi * dh / h : 0.0f) + c_tau * dh;
-                        } else {
-                            const float x2 = (float)X[rx.y * B];
-                            dlam[rx.x * B] += (a > 0.0f ? psi / x1 : 0.0f) + c_tau * x2;
-                            dlam[rx.y * B] += (a > 0.0f ? psi / x2 : 0.0f) + c_tau * x1;
+                    const float invZ = 1.0f / Z, Wbar = Wq * invZ;
+                    // pass 3: per-reaction adjoints and the state adjoint
+#pragma unroll
+                    for (int j = 0; j < MC; ++j) {
+                        const float psi = lr[j] > 0.0f ? lr[j] * invZ * (wr[j] - Wbar) * invT : 0.0f;
+                        dAr[j] += psi + dLda0 * ar[j];
+                        const int4 rx = s_rx[j];
+                        reaction_state_adjoint(rx, X, B, ar[j], mass_action_h(rx, X, B), psi, dLda0 * s_k[j], dlam);
+                    }
+                } else {
+                    for (int j = 0; j < M; ++j) {
+                        const float l = s_q[j * B + tid];
+                        const float q = (l == -CUDART_INF_F) ? 0.0f : exp2f((l - lmax) * invT);
+                        s_q[j * B + tid] = q;
+                        if (q > 0.0f) {
+                            Z += q;
+                            Wq += q * stoich_dot(s_rx[j], s_st, lam, B);
                         }
+                    }
+                    const float invZ = 1.0f / Z, Wbar = Wq * invZ;
+                    for (int j = 0; j < M; ++j) {
+                        const int4 rx = s_rx[j];
+                        const float h = mass_action_h(rx, X, B);
+                        const float a = __fmul_rn(s_k[j], h);
+                        const float q = s_q[j * B + tid];
+                        const float psi = q > 0.0f ? q * invZ * (stoich_dot(rx, s_st, lam, B) - Wbar) * invT : 0.0f;
+                        s_dA[j * B + tid] += psi + dLda0 * a;
+                        reaction_state_adjoint(rx, X, B, a, h, psi, dLda0 * s_k[j], dlam);
                     }
                 }
                 mu += dt_dir;  // t_{k+1} = t_k + tau_k
@@ -205,19 +280,32 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
                     const float alpha = p.brk_a[(int64_t)s * n + i];
                     if (alpha >= 0.0f) coef = 1.0f - alpha;
                 }
-                for (int o = 0; o < p.n_obs; ++o)
-                    lam[p.obs_sp[o] * B] += coef * gl[(int64_t)s * p.n_obs + o];
+                for (int o = 0; o < p.n_obs; ++o) lam[p.obs_sp[o] * B] += coef * gl[(int64_t)s * p.n_obs + o];
             }
-            if ((k % p.K) == 0) {
-                const int *ck = p.ckpt + (k / p.K) * (int64_t)N * n + i;
-                for (int s = 0; s < N; ++s) mism += (ck[s * n] != X[s * B]);
+            if (ck_off == 0) {
+                const int *ck = p.ckpt + (int64_t)ck_row * N * n + i;
+                for (int s = 0; s < N; ++s) mism += (ck[(int64_t)s * n] != X[s * B]);
+                --ck_row;
+                ck_off = p.K;
             }
+            --ck_off;
             if (k > 0) {
                 const int4 rp = s_rx[event_at(k - 1)];
                 for (int e = rp.z; e < rp.w; ++e) X[stoich_species(s_st[e]) * B] -= stoich_delta(s_st[e]);
             }
+            if constexpr (MC > 0) {
+                if (draw) {
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) E[q] = En[q];
+                }
+            }
         }
         if (mism) atomicAdd(p.mismatch, mism);
+    }
+    if (MC > 0) {
+#pragma unroll
+        for (int j = 0; j < (MC > 0 ? MC : 1); ++j)
+            if (j < M) s_dA[j * B + tid] = dAr[j];
     }
     __syncthreads();
     // fixed-order block reduction of the per-reaction adjoints
@@ -251,22 +339,36 @@ __global__ void reduce_partials_kernel(const float *partial, int64_t nblk, int M
     }
 }
 
-template <int R>
+template <int R, int MC>
 static cudaError_t launch_adj_t(const AdjParams &p, int block, size_t smem, int64_t grid, cudaStream_t st)
 {
-    auto kern = adj_thread_kernel<R>;
+    auto kern = adj_thread_kernel<R, MC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
+int thread_kernel_mc(int M);
+
+template <int R>
+static cudaError_t launch_adj_mc(const AdjParams &p, int block, size_t smem, int64_t grid, cudaStream_t st)
+{
+    switch (thread_kernel_mc(p.M)) {
+    case 2: return launch_adj_t<R, 2>(p, block, smem, grid, st);
+    case 4: return launch_adj_t<R, 4>(p, block, smem, grid, st);
+    case 8: return launch_adj_t<R, 8>(p, block, smem, grid, st);
+    case 16: return launch_adj_t<R, 16>(p, block, smem, grid, st);
+    default: return launch_adj_t<R, 0>(p, block, smem, grid, st);
+    }
+}
+
 cudaError_t launch_backward_thread(const AdjParams &p, int readout, int block, size_t smem, int64_t grid,
                                    cudaStream_t st)
 {
     if (grid == 0) return cudaSuccess;
-    return readout == SSA_READOUT_HOLD ? launch_adj_t<0>(p, block, smem, grid, st)
-                                       : launch_adj_t<1>(p, block, smem, grid, st);
+    return readout == SSA_READOUT_HOLD ? launch_adj_mc<0>(p, block, smem, grid, st)
+                                       : launch_adj_mc<1>(p, block, smem, grid, st);
 }
 
 cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, const int *rate_index, int P,

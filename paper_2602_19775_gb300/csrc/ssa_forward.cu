@@ -18,7 +18,51 @@
 
 namespace ssa {
 
-template <int READOUT, bool RECORD, bool REPLAY>
+// Exponential variates of one step, E[q] = -ln u_q for the first NQ words of the step's Philox
+// stream (q = 0 drives the waiting time, q = 1 + j reaction j). They do not depend on the state,
+// so the kernels draw the next step's variates while the current step's state-dependent chain
+// runs (instruction-level parallelism at low occupancy).
+template <int NQ>
+__device__ __forceinline__ void step_noise(float (&E)[NQ], uint32_t k, uint32_t c2, uint32_t c3, uint32_t key0,
+                                           uint32_t key1)
+{
+#pragma unroll
+    for (int b = 0; b < (NQ + 3) / 4; ++b) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
+        if (4 * b + 0 < NQ) E[4 * b + 0] = -logf(u01(r.x));
+        if (4 * b + 1 < NQ) E[4 * b + 1] = -logf(u01(r.y));
+        if (4 * b + 2 < NQ) E[4 * b + 2] = -logf(u01(r.z));
+        if (4 * b + 3 < NQ) E[4 * b + 3] = -logf(u01(r.w));
+    }
+}
+
+// -ln u_q of one word (runtime-indexed variant for networks without a compile-time size).
+__device__ __forceinline__ float exp_variate(uint32_t k, int q, uint32_t c2, uint32_t c3, uint32_t key0, uint32_t key1,
+                                             uint4 &cache, int &cached_b)
+{
+    const int b = q >> 2;
+    if (b != cached_b) {
+        cache = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
+        cached_b = b;
+    }
+    return -logf(u01(word_of(cache, q & 3)));
+}
+
+// The Gumbel-max choice as an exponential race: argmax_j a_j/E_j, compared as a_j E_b > a_b E_j
+// (binary32 products); ties keep the lowest j. The adjoint repeats the identical comparisons.
+__device__ __forceinline__ void race(float a, float E, int j, float &ab, float &Eb, int &jb)
+{
+    if (__fmul_rn(a, Eb) > __fmul_rn(ab, E)) {
+        ab = a;
+        Eb = E;
+        jb = j;
+    }
+}
+
+// Thread-per-trajectory forward. MC > 0: the network has at most MC reactions (tables padded with
+// zero-rate, order-0 entries), per-reaction loops are unrolled and the step's variates live in
+// registers. MC == 0: runtime loops for any size.
+template <int READOUT, bool RECORD, bool REPLAY, int MC>
 __global__ void __launch_bounds__(256) fwd_thread_kernel(const FwdParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -26,7 +70,7 @@ __global__ void __launch_bounds__(256) fwd_thread_kernel(const FwdParams p)
     const int tid = threadIdx.x;
     const int N = p.N, M = p.M;
     int4 *s_rx = reinterpret_cast<int4 *>(smem);
-    int *s_st = reinterpret_cast<int *>(smem + 16 * M);
+    int *s_st = reinterpret_cast<int *>(smem + 16 * p.Mp);
     float *s_k = reinterpret_cast<float *>(smem + p.tab_bytes);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + p.tab_bytes + p.k_bytes);
     int *s_ok = reinterpret_cast<int *>(smem + p.tab_bytes + p.k_bytes + 8);
@@ -50,41 +94,47 @@ __global__ void __launch_bounds__(256) fwd_thread_kernel(const FwdParams p)
     const uint64_t gid = p.traj_offset + (uint64_t)i;
     const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32);
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
-    const int nb = (M + 4) >> 2;  // ceil((M + 1) / 4) Philox blocks per step
 
     double t = 0.0;
     int s = 0;
-    double ts_next = p.S > 0 ? p.ts[0] : CUDART_INF;
-    int status = SSA_TRAJ_OK;
-    int64_t k = 0;       // index of the current state X_k
-    int64_t draws = 0;
+    // next clock threshold: the next sample time, or t_end once every sample is written
+    double thr = p.S > 0 ? p.ts[0] : p.t_end;
+    int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
+    int k = 0;        // index of the current state X_k
+    int draws = 0;
+    int ck_left = p.K, ck_row = 0;
     uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;  // event pack (8 x uint16)
-    int64_t n_ev = 0;
+    int n_ev = 0;
     const uint16_t *ev_in = nullptr;
     if (REPLAY) {
         ev_in = p.ev_in + i * p.ev_in_stride;
-        n_ev = min((int64_t)p.n_ev_in[i], p.ev_in_stride);  // never read past the caller's row
+        n_ev = (int)min((int64_t)p.n_ev_in[i], p.ev_in_stride);  // never read past the caller's row
     }
-    if (bad_input) status = SSA_TRAJ_BAD_INPUT;
+    constexpr int NQ = MC > 0 ? MC + 1 : 1;
+    float E[NQ], En[NQ];
+    if (MC > 0) step_noise<NQ>(E, 0u, c2, c3, key0, key1);
 
     while (!bad_input) {
         if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
-        float a0 = 0.0f, E0 = 1.0f, best = 0.0f;
+        float a0 = 0.0f, ab = 0.0f, Eb = 1.0f, E0;
         int jb = -1;
-        for (int b = 0; b < nb; ++b) {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
+        if constexpr (MC > 0) {
+            step_noise<NQ>(En, (uint32_t)(k + 1), c2, c3, key0, key1);  // next step, state-independent
+            E0 = E[0];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = 4 * b + q - 1;
-                if (j < 0) { E0 = -logf(u01(r.x)); continue; }
-                if (j >= M) break;
+            for (int j = 0; j < MC; ++j) {
                 const float a = __fmul_rn(s_k[j], mass_action_h(s_rx[j], X, B));
                 a0 = __fadd_rn(a0, a);
-                if (!REPLAY && a > 0.0f) {
-                    const float E = -logf(u01(word_of(r, q)));
-                    const float key = __fdiv_rn(a, E);
-                    if (key > best) { best = key; jb = j; }
-                }
+                if (!REPLAY) race(a, E[j + 1], j, ab, Eb, jb);
+            }
+        } else {
+            uint4 cache;
+            int cb = -1;
+            E0 = exp_variate((uint32_t)k, 0, c2, c3, key0, key1, cache, cb);
+            for (int j = 0; j < M; ++j) {
+                const float a = __fmul_rn(s_k[j], mass_action_h(s_rx[j], X, B));
+                a0 = __fadd_rn(a0, a);
+                if (!REPLAY && a > 0.0f) race(a, exp_variate((uint32_t)k, j + 1, c2, c3, key0, key1, cache, cb), j, ab, Eb, jb);
             }
         }
         if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
@@ -97,18 +147,19 @@ __global__ void __launch_bounds__(256) fwd_thread_kernel(const FwdParams p)
                 break;
             }
         }
-        if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }  // keys all non-positive (NaN rates)
-        const float tau = __fdiv_rn(E0, a0);
-        const double t_next = t + (double)tau;
-        const bool cross = t_next > p.t_end;
+        if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }  // no positive key (NaN rates)
+        const float tau = __fdividef(E0, a0);
+        const double t_next = t + f2d_pos(tau);
         const int4 rj = s_rx[jb];
+        const bool slow = t_next > thr;  // a sample falls in [t_k, t_{k+1}) or the horizon ends
+        const bool cross = slow && t_next > p.t_end;
         if (!cross) {
             // range check of X + v_j before anything is written for this draw
             for (int e = rj.z; e < rj.w; ++e) {
                 const int st = s_st[e];
-                const long long v = (long long)X[stoich_species(st) * B] + stoich_delta(st);
-                if (v < 0) status = SSA_TRAJ_NEG_COUNT;
-                else if (v > 2147483647LL) status = SSA_TRAJ_OVERFLOW;
+                const int x = X[stoich_species(st) * B], d = stoich_delta(st);
+                if (d < 0 && x + d < 0) status = SSA_TRAJ_NEG_COUNT;
+                else if (d > 0 && x > 2147483647 - d) status = SSA_TRAJ_OVERFLOW;
             }
         }
         if (RECORD) {
@@ -116,41 +167,49 @@ __global__ void __launch_bounds__(256) fwd_thread_kernel(const FwdParams p)
             e1 = __funnelshift_r(e1, e2, 16);
             e2 = __funnelshift_r(e2, e3, 16);
             e3 = (e3 >> 16) | ((uint32_t)jb << 16);
-            if ((k & 7) == 7) p.ev[(k >> 3) * n + i] = make_uint4(e0, e1, e2, e3);
+            if ((k & 7) == 7) p.ev[(int64_t)(k >> 3) * n + i] = make_uint4(e0, e1, e2, e3);
         }
         draws = k + 1;
         if (status != SSA_TRAJ_OK) break;  // rejected update: samples hold X_k below
-        // samples with t_k <= t_s < t_{k+1}
-        while (ts_next < t_next) {
-            if (READOUT == SSA_READOUT_HOLD) {
-                int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                for (int c = 0; c < p.n_obs; ++c) o[c] = X[p.obs_sp[c] * B];
-            } else {
-                const float alpha = __fdiv_rn((float)(ts_next - t), tau);
-                float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                for (int c = 0; c < p.n_obs; ++c) {
-                    const int sp = p.obs_sp[c];
-                    int dv = 0;
-                    for (int e = rj.z; e < rj.w; ++e)
-                        if (stoich_species(s_st[e]) == sp) dv += stoich_delta(s_st[e]);
-                    o[c] = __fmaf_rn(alpha, (float)dv, (float)X[sp * B]);
+        if (slow) {
+            // samples with t_k <= t_s < t_{k+1}
+            while (s < p.S && p.ts[s] < t_next) {
+                if (READOUT == SSA_READOUT_HOLD) {
+                    int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                    for (int c = 0; c < p.n_obs; ++c) o[c] = X[p.obs_sp[c] * B];
+                } else {
+                    const float alpha = __fdiv_rn((float)(p.ts[s] - t), tau);
+                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                    for (int c = 0; c < p.n_obs; ++c) {
+                        const int sp = p.obs_sp[c];
+                        int dv = 0;
+                        for (int e = rj.z; e < rj.w; ++e)
+                            if (stoich_species(s_st[e]) == sp) dv += stoich_delta(s_st[e]);
+                        o[c] = __fmaf_rn(alpha, (float)dv, (float)X[sp * B]);
+                    }
+                    if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
                 }
-                if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
+                if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
+                ++s;
             }
-            if (RECORD) p.brk_k[(int64_t)s * n + i] = (int)k;
-            ++s;
-            ts_next = s < p.S ? p.ts[s] : CUDART_INF;
+            thr = s < p.S ? p.ts[s] : p.t_end;
+            if (cross) break;  // the crossing draw is made but not applied
         }
-        if (cross) break;  // the crossing draw is made but not applied
         for (int e = rj.z; e < rj.w; ++e) {
             const int st = s_st[e];
             X[stoich_species(st) * B] += stoich_delta(st);
         }
         t = t_next;
         ++k;
-        if (RECORD && (k % p.K) == 0) {
-            int *ck = p.ckpt + (k / p.K) * (int64_t)N * n + i;
-            for (int sp = 0; sp < N; ++sp) ck[sp * n] = X[sp * B];
+        if (RECORD && --ck_left == 0) {
+            ck_left = p.K;
+            ++ck_row;
+            int *ck = p.ckpt + (int64_t)ck_row * N * n + i;
+            for (int sp = 0; sp < N; ++sp) ck[(int64_t)sp * n] = X[sp * B];
+        }
+        if constexpr (MC > 0) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) E[q] = En[q];
         }
     }
     if (REPLAY && status == SSA_TRAJ_OK && draws != n_ev) status = SSA_TRAJ_REPLAY_MISMATCH;
@@ -164,19 +223,19 @@ __global__ void __launch_bounds__(256) fwd_thread_kernel(const FwdParams p)
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)X[p.obs_sp[c] * B];
             if (RECORD) p.brk_a[(int64_t)s * n + i] = -1.0f;
         }
-        if (RECORD) p.brk_k[(int64_t)s * n + i] = (int)k;
+        if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
     }
-    p.draws[i] = (int)draws;
+    p.draws[i] = draws;
     p.status[i] = status;
     if (RECORD) {
         if (draws & 7) {
-            for (int64_t pad = draws & 7; pad < 8; ++pad) {
+            for (int pad = draws & 7; pad < 8; ++pad) {
                 e0 = __funnelshift_r(e0, e1, 16);
                 e1 = __funnelshift_r(e1, e2, 16);
                 e2 = __funnelshift_r(e2, e3, 16);
                 e3 = e3 >> 16;
             }
-            p.ev[((draws - 1) >> 3) * n + i] = make_uint4(e0, e1, e2, e3);
+            p.ev[(int64_t)((draws - 1) >> 3) * n + i] = make_uint4(e0, e1, e2, e3);
         }
         for (int sp = 0; sp < N; ++sp) {
             p.xfinal[(int64_t)sp * n + i] = X[sp * B];
@@ -284,10 +343,10 @@ __global__ void status_count_kernel(const int *status, int64_t n, unsigned long 
 // ---------------------------------------------------------------------------------------------
 // Launch helpers used by the API layer
 // ---------------------------------------------------------------------------------------------
-template <int R, bool REC, bool REP>
+template <int R, bool REC, bool REP, int MC>
 static cudaError_t launch_fwd_t(const FwdParams &p, int block, size_t smem, cudaStream_t st)
 {
-    auto kern = fwd_thread_kernel<R, REC, REP>;
+    auto kern = fwd_thread_kernel<R, REC, REP, MC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = (p.n_traj + block - 1) / block;
@@ -295,16 +354,33 @@ static cudaError_t launch_fwd_t(const FwdParams &p, int block, size_t smem, cuda
     return cudaGetLastError();
 }
 
+// compile-time reaction bound used for a network of M reactions (0 = runtime loops)
+int thread_kernel_mc(int M) { return M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : M <= 16 ? 16 : 0; }
+
+template <int R, bool REC>
+static cudaError_t launch_fwd_mc(const FwdParams &p, int mc, int block, size_t smem, cudaStream_t st)
+{
+    switch (mc) {
+    case 2: return launch_fwd_t<R, REC, false, 2>(p, block, smem, st);
+    case 4: return launch_fwd_t<R, REC, false, 4>(p, block, smem, st);
+    case 8: return launch_fwd_t<R, REC, false, 8>(p, block, smem, st);
+    case 16: return launch_fwd_t<R, REC, false, 16>(p, block, smem, st);
+    default: return launch_fwd_t<R, REC, false, 0>(p, block, smem, st);
+    }
+}
+
 cudaError_t launch_forward_thread(const FwdParams &p, int readout, bool record, bool replay, int block,
                                   size_t smem, cudaStream_t st)
 {
     if (p.n_traj == 0) return cudaSuccess;
-    if (readout == SSA_READOUT_HOLD) {
-        if (replay) return record ? launch_fwd_t<0, true, true>(p, block, smem, st) : launch_fwd_t<0, false, true>(p, block, smem, st);
-        return record ? launch_fwd_t<0, true, false>(p, block, smem, st) : launch_fwd_t<0, false, false>(p, block, smem, st);
+    if (replay) {  // test hook: runtime loops, always recorded
+        return readout == SSA_READOUT_HOLD ? launch_fwd_t<0, true, true, 0>(p, block, smem, st)
+                                           : launch_fwd_t<1, true, true, 0>(p, block, smem, st);
     }
-    if (replay) return record ? launch_fwd_t<1, true, true>(p, block, smem, st) : launch_fwd_t<1, false, true>(p, block, smem, st);
-    return record ? launch_fwd_t<1, true, false>(p, block, smem, st) : launch_fwd_t<1, false, false>(p, block, smem, st);
+    const int mc = thread_kernel_mc(p.M);
+    if (readout == SSA_READOUT_HOLD)
+        return record ? launch_fwd_mc<0, true>(p, mc, block, smem, st) : launch_fwd_mc<0, false>(p, mc, block, smem, st);
+    return record ? launch_fwd_mc<1, true>(p, mc, block, smem, st) : launch_fwd_mc<1, false>(p, mc, block, smem, st);
 }
 
 cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N, int *flag,

@@ -52,17 +52,31 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &r, int q)
     return q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
 }
 
-// Mass-action combinatorial factor h_j(X) (Section 2), formed exactly in 64-bit integers and
-// rounded once to binary32, and the propensity a_j = k_j h_j in binary32 (no contraction).
-// X points at this trajectory's counts with a stride between species.
+// Mass-action combinatorial factor h_j(X) (Section 2): 1, X_i, X_i X_l or X_i (X_i - 1)/2, equal
+// to the exact integer rounded once to binary32. Counts below 2^24 are exact in binary32, so one
+// correctly rounded binary32 product gives the same value as the exact 64-bit product rounded
+// once; larger counts take the 64-bit route.
 __device__ __forceinline__ float mass_action_h(const int4 rx, const int *X, int stride)
 {
     if (rx.x < 0) return 1.0f;
-    const long long x1 = X[rx.x * stride];
-    if (rx.y < 0) return __ll2float_rn(x1);
-    if (rx.y == rx.x) return __ll2float_rn((x1 * (x1 - 1)) >> 1);
-    const long long x2 = X[rx.y * stride];
-    return __ll2float_rn(x1 * x2);
+    const int x1 = X[rx.x * stride];
+    if (rx.y < 0) return __int2float_rn(x1);
+    if (rx.y == rx.x) {
+        if (x1 < (1 << 24)) return __fmul_rn(__int2float_rn(x1), __int2float_rn(x1 - 1)) * 0.5f;
+        return __ll2float_rn(((long long)x1 * (x1 - 1)) >> 1);
+    }
+    const int x2 = X[rx.y * stride];
+    if ((x1 | x2) < (1 << 24)) return __fmul_rn(__int2float_rn(x1), __int2float_rn(x2));
+    return __ll2float_rn((long long)x1 * x2);
+}
+
+// binary32 -> binary64 for a positive normal value by re-biasing the exponent field (IEEE 754
+// layouts), which keeps the conversion off the FP64 pipe; other values take the plain conversion.
+__device__ __forceinline__ double f2d_pos(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    if (b - 0x00800000u < 0x7f000000u) return __hiloint2double((int)((b >> 3) + 0x38000000u), (int)(b << 29));
+    return (double)x;
 }
 
 __device__ __forceinline__ int stoich_species(int e) { return e >> 8; }
@@ -158,7 +172,7 @@ struct FwdParams {
     const int4 *rx;
     const float *k_rates;  // [M padded to 4]
     uint32_t tab_bytes, k_bytes;
-    int N, M, nnz;
+    int N, M, Mp, nnz;  // Mp: reaction tables padded to 4 * ceil((M + 1)/4) entries
     int64_t n_traj;
     uint64_t traj_offset, seed;
     const int *x0;
@@ -190,7 +204,7 @@ struct AdjParams {
     const int4 *rx;
     const float *k_rates;
     uint32_t tab_bytes, k_bytes;
-    int N, M, nnz;
+    int N, M, Mp, nnz;  // Mp: reaction tables padded to 4 * ceil((M + 1)/4) entries
     int64_t n_traj;
     uint64_t traj_offset, seed;
     const double *ts;
