@@ -64,16 +64,16 @@ __device__ __forceinline__ void reaction_state_adjoint(const int4 rx, const int 
                                                        float c_tau, float *dlam)
 {
     if (rx.x < 0) return;
-    const float x1 = (float)X[rx.x * B];
+    const float x1 = int2f(X[rx.x * B]);
     if (rx.y < 0) {
-        dlam[rx.x * B] += (a > 0.0f ? psi / x1 : 0.0f) + c_tau;
+        dlam[rx.x * B] += (a > 0.0f ? __fdividef(psi, x1) : 0.0f) + c_tau;
     } else if (rx.y == rx.x) {
         const float dh = x1 - 0.5f;  // d/dX [X (X - 1)/2]
-        dlam[rx.x * B] += (a > 0.0f ? psi * dh / h : 0.0f) + c_tau * dh;
+        dlam[rx.x * B] += (a > 0.0f ? __fdividef(psi * dh, h) : 0.0f) + c_tau * dh;
     } else {
-        const float x2 = (float)X[rx.y * B];
-        dlam[rx.x * B] += (a > 0.0f ? psi / x1 : 0.0f) + c_tau * x2;
-        dlam[rx.y * B] += (a > 0.0f ? psi / x2 : 0.0f) + c_tau * x1;
+        const float x2 = int2f(X[rx.y * B]);
+        dlam[rx.x * B] += (a > 0.0f ? __fdividef(psi, x1) : 0.0f) + c_tau * x2;
+        dlam[rx.y * B] += (a > 0.0f ? __fdividef(psi, x2) : 0.0f) + c_tau * x1;
     }
 }
 
@@ -219,8 +219,9 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
                                 if (stoich_species(s_st[e]) == sp) dv += stoich_delta(s_st[e]);
                             c += g * (float)dv;
                         }
-                        dt_dir -= c / tau;
-                        dtau_dir -= alpha * c / tau;
+                        const float c_tau = __fdividef(c, tau);
+                        dt_dir -= c_tau;
+                        dtau_dir -= alpha * c_tau;
                     }
                 }
                 const float dtau = mu + dtau_dir;
@@ -237,14 +238,15 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
                         Z += q;
                         Wq += q * wr[j];
                     }
-                    const float invZ = 1.0f / Z, Wbar = Wq * invZ;
+                    const float invZ = __fdividef(1.0f, Z), Wbar = Wq * invZ;
                     // pass 3: per-reaction adjoints and the state adjoint
+                    // every w_j is already read, so the state adjoint accumulates into lambda
 #pragma unroll
                     for (int j = 0; j < MC; ++j) {
                         const float psi = lr[j] > 0.0f ? lr[j] * invZ * (wr[j] - Wbar) * invT : 0.0f;
                         dAr[j] += psi + dLda0 * ar[j];
                         const int4 rx = s_rx[j];
-                        reaction_state_adjoint(rx, X, B, ar[j], mass_action_h(rx, X, B), psi, dLda0 * s_k[j], dlam);
+                        reaction_state_adjoint(rx, X, B, ar[j], mass_action_h(rx, X, B), psi, dLda0 * s_k[j], lam);
                     }
                 } else {
                     for (int j = 0; j < M; ++j) {
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
                             Wq += q * stoich_dot(s_rx[j], s_st, lam, B);
                         }
                     }
-                    const float invZ = 1.0f / Z, Wbar = Wq * invZ;
+                    const float invZ = __fdividef(1.0f, Z), Wbar = Wq * invZ;
                     for (int j = 0; j < M; ++j) {
                         const int4 rx = s_rx[j];
                         const float h = mass_action_h(rx, X, B);
@@ -270,9 +272,11 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
                 mu += dt_dir;  // t_{k+1} = t_k + tau_k
             }
             // lambda_k = lambda_{k+1} + (choice and waiting-time terms) + direct readout terms
-            for (int s = 0; s < N; ++s) {
-                lam[s * B] += dlam[s * B];
-                dlam[s * B] = 0.0f;
+            if (MC == 0) {
+                for (int s = 0; s < N; ++s) {
+                    lam[s * B] += dlam[s * B];
+                    dlam[s * B] = 0.0f;
+                }
             }
             for (int s = s_hi + 1; s <= s_top; ++s) {
                 float coef = 1.0f;

@@ -151,8 +151,9 @@ __global__ void __launch_bounds__(256) fwd_thread_kernel(const FwdParams p)
         const float tau = __fdividef(E0, a0);
         const double t_next = t + f2d_pos(tau);
         const int4 rj = s_rx[jb];
-        const bool slow = t_next > thr;  // a sample falls in [t_k, t_{k+1}) or the horizon ends
-        const bool cross = slow && t_next > p.t_end;
+        // a sample falls in [t_k, t_{k+1}) or the horizon ends (both clocks are non-negative)
+        const bool slow = gt_nonneg(t_next, thr);
+        const bool cross = slow && gt_nonneg(t_next, p.t_end);
         if (!cross) {
             // range check of X + v_j before anything is written for this draw
             for (int e = rj.z; e < rj.w; ++e) {
@@ -173,12 +174,12 @@ __global__ void __launch_bounds__(256) fwd_thread_kernel(const FwdParams p)
         if (status != SSA_TRAJ_OK) break;  // rejected update: samples hold X_k below
         if (slow) {
             // samples with t_k <= t_s < t_{k+1}
-            while (s < p.S && p.ts[s] < t_next) {
+            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
                 if (READOUT == SSA_READOUT_HOLD) {
                     int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
                     for (int c = 0; c < p.n_obs; ++c) o[c] = X[p.obs_sp[c] * B];
                 } else {
-                    const float alpha = __fdiv_rn((float)(p.ts[s] - t), tau);
+                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
                     float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
                     for (int c = 0; c < p.n_obs; ++c) {
                         const int sp = p.obs_sp[c];

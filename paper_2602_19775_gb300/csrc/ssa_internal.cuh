@@ -26,10 +26,20 @@ struct NetTables {
     uint32_t tab_bytes;  // 16 * M + 4 * nnz_pad, a multiple of 16
 };
 
-// per-step uniform mapping: u = ((x >> 9) + 1/2) 2^-23, exact in binary32
+// per-step uniform mapping: u = ((x >> 9) + 1/2) 2^-23, exact in binary32. Built from the bits:
+// 1 + m 2^-23 (m = x >> 9 placed in the mantissa of 1.0) minus (1 - 2^-24) is exactly
+// m 2^-23 + 2^-24, so no integer-to-float conversion is needed.
 __device__ __forceinline__ float u01(uint32_t x)
 {
-    return __fmaf_rn(__uint2float_rn(x >> 9), 0x1p-23f, 0x1p-24f);
+    return __fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0x1.fffffep-1f);
+}
+
+// Exact int -> binary32 for 0 <= x < 2^23 through the bits of 2^23 + x (the integer pipe), with the
+// plain conversion for other values.
+__device__ __forceinline__ float int2f(int x)
+{
+    if ((unsigned)x < (1u << 23)) return __fsub_rn(__uint_as_float(0x4B000000u | (unsigned)x), 8388608.0f);
+    return __int2float_rn(x);
 }
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, two 32x32->64 products each,
@@ -60,14 +70,39 @@ __device__ __forceinline__ float mass_action_h(const int4 rx, const int *X, int 
 {
     if (rx.x < 0) return 1.0f;
     const int x1 = X[rx.x * stride];
-    if (rx.y < 0) return __int2float_rn(x1);
+    if (rx.y < 0) return int2f(x1);
     if (rx.y == rx.x) {
-        if (x1 < (1 << 24)) return __fmul_rn(__int2float_rn(x1), __int2float_rn(x1 - 1)) * 0.5f;
+        if (x1 < 2) return 0.0f;
+        if (x1 < (1 << 23)) return __fmul_rn(int2f(x1), int2f(x1 - 1)) * 0.5f;
         return __ll2float_rn(((long long)x1 * (x1 - 1)) >> 1);
     }
     const int x2 = X[rx.y * stride];
-    if ((x1 | x2) < (1 << 24)) return __fmul_rn(__int2float_rn(x1), __int2float_rn(x2));
+    if ((x1 | x2) < (1 << 23)) return __fmul_rn(int2f(x1), int2f(x2));
     return __ll2float_rn((long long)x1 * x2);
+}
+
+// a > b for non-negative, non-NaN binary64 values: IEEE 754 orders them like their bit patterns
+// read as unsigned integers, so the comparison runs on the integer pipe instead of the FP64 pipe.
+__device__ __forceinline__ bool gt_nonneg(double a, double b)
+{
+    return (unsigned long long)__double_as_longlong(a) > (unsigned long long)__double_as_longlong(b);
+}
+
+// binary64 -> binary32, round to nearest even, for a non-negative value in the binary32 normal
+// range, from the IEEE 754 fields on the integer pipe (other values take the plain conversion):
+// the 52-bit fraction is cut to 23 bits and rounded on the 29 dropped bits; a carry out of the
+// fraction increments the exponent field, as it should.
+__device__ __forceinline__ float d2f_nonneg(double d)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const int e = (int)(hi >> 20) - 896;  // binary32 exponent field
+    if (e >= 1 && e <= 254 && (hi >> 31) == 0) {
+        uint32_t f = ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t r = lo & 0x1fffffffu;
+        f += (r > 0x10000000u) || (r == 0x10000000u && (f & 1u));
+        return __uint_as_float(f);
+    }
+    return __double2float_rn(d);
 }
 
 // binary32 -> binary64 for a positive normal value by re-biasing the exponent field (IEEE 754
