@@ -35,28 +35,45 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
 # --------------------------------------------------------------------------------------------
-# Issue-slot roofline of the SSA kernels ("Roofline"): the minimal instruction count
-# of one SSA step of a network with M reactions, per thread, counted from the method's arithmetic
-# with the cheapest sm_103 instruction for each operation, and the SM issue rate
-# 152 SMs x 4 schedulers x 32 lanes x f_SM.
+# Issue-slot roofline of the SSA kernels. The unit is one SSA step; its
+# algorithmic cost is the minimal number of issue slots (thread instructions) of the method's
+# arithmetic on sm_103, with an accurate logarithm costed at its measured throughput on this GPU
+# (ssa_pipe_rates: 128 issue slots per SM per clock / logf per SM per clock). The peak is the SM
+# issue rate: 152 SMs x 4 schedulers x 32 lanes x the sampled SM clock.
 # --------------------------------------------------------------------------------------------
-def instr_per_step_fwd(M: int) -> int:
+def instr_per_step_fwd(M: int, logf_slots: float) -> float:
     nb = (M + 4) // 4
-    philox = 60 * nb                 # 10 rounds x (2 IMAD.WIDE + 2 LOP3 + 2 IADD)
-    variates = 5 * (M + 1)           # u01 (SHF, I2F, FFMA) + -ln u (MUFU.LG2, FMUL)
-    reactions = 8 * M                # propensity (LDS x2, I2F, FMUL), a0 add, key (RCP, FMUL), max
-    step = 12                        # tau, FP64 clock add and compares, state update, loop control
+    philox = 60 * nb                          # 10 rounds x (2 wide multiplies, 2 XOR3, 2 key adds)
+    variates = (2 + logf_slots) * (M + 1)     # u from the bits (2) and an accurate -ln u
+    reactions = 12 * M                        # propensity (5), a0 add (1), race (2 mul, compare, 3 select)
+    step = 20                                 # tau (2), FP64 clock add + compare (3), update (8), log (4), loop (3)
     return philox + variates + reactions + step
 
 
-def instr_per_step_bwd(M: int) -> int:
-    # recompute of the forward step + softmax (LG2, FADD, FMUL, EX2, FADD) + w_j (LDS, FFMA) +
-    # g_j, psi_j, dA_j, two state-adjoint updates (~12) per reaction + event read and reversal
-    return instr_per_step_fwd(M) + 19 * M + 16
+def instr_per_step_bwd(M: int, logf_slots: float) -> float:
+    # the forward step recomputed, then per reaction: 2 lg2 + sub (log key), ex2 + mul (soft weight),
+    # stoichiometric dot (6), psi (5), dA (2), state adjoint (8); per step: readout, reversal, event (20)
+    return instr_per_step_fwd(M, logf_slots) + 25 * M + 20
 
 
 def sm_issue_peak(sm_mhz: float, n_sm: int = 152) -> float:
     return n_sm * 4 * 32 * sm_mhz * 1e6
+
+
+def profiled_traffic(kind: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's sources are unchanged."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic_c2.json")))
+        k = rec["kernels"][kind]
+        h = hashlib.sha256()
+        for f in k["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_2602_19775_gb300", "csrc", f), "rb").read())
+    except (OSError, ValueError, KeyError):
+        return None
+    if h.hexdigest()[:16] != k["source_sha256_16"]:
+        return None
+    return k["dram_read_bytes"] + k["dram_write_bytes"]
 
 
 # --------------------------------------------------------------------------------------------
@@ -330,12 +347,14 @@ def run_ours(args):
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     M = wl.net.n_reactions
+    rates = ssa.pipe_rates()
+    logf_slots = 128.0 / rates["logf"]
     bwd_s = float(np.mean(bwd_ms)) / 1e3
     fwd_s = float(np.mean(fwd_ms)) / 1e3
     per_launch_steps = steps_total / world / K
-    ach_b = instr_per_step_bwd(M) * per_launch_steps / bwd_s
-    ach_f = instr_per_step_fwd(M) * per_launch_steps / fwd_s
-    peak = sm_issue_peak(sm_mhz)
+    ach_b = instr_per_step_bwd(M, logf_slots) * per_launch_steps / bwd_s
+    ach_f = instr_per_step_fwd(M, logf_slots) * per_launch_steps / fwd_s
+    peak = sm_issue_peak(sm_mhz, rates["sm_count"])
     dominant = "adjoint" if bwd_s >= fwd_s else "forward"
     ach = ach_b if dominant == "adjoint" else ach_f
     line = {
@@ -360,8 +379,12 @@ def run_ours(args):
         "kernel_ms": {"forward_record": float(np.mean(fwd_ms)), "adjoint": float(np.mean(bwd_ms)),
                       "forward_only": float(np.mean(fonly_ms))},
         "roofline": {"bound": "alu", "kernel": dominant, "achieved": ach / 1e12, "peak": peak / 1e12,
-                     "unit": "T thread-instr/s", "frac": ach / peak, "traffic": None,
-                     "peak_basis": f"152 SM x 4 x 32 lanes x {sm_mhz:.0f} MHz (sampled median)"},
+                     "unit": "T thread-instr/s", "frac": ach / peak, "traffic": profiled_traffic(dominant),
+                     "algorithmic_instr_per_step": {"forward": instr_per_step_fwd(M, logf_slots),
+                                                    "adjoint": instr_per_step_bwd(M, logf_slots)},
+                     "forward_frac": ach_f / peak,
+                     "peak_basis": f"{rates['sm_count']} SM x 4 x 32 lanes x {sm_mhz:.0f} MHz (sampled median)",
+                     "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in rates.items()}},
         "cpu_baseline": cpu_base,
         "e2e": {"value": e2e_value, "unit": "SSA steps/s (fwd+adj)", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

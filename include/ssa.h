@@ -220,6 +220,15 @@ ssa_status ssa_ensemble_mean_static(const void *obs, int32_t obs_is_int, int64_t
 ssa_status ssa_philox_uniforms(uint64_t seed, const uint64_t *traj, const uint64_t *step,
                                int64_t n, int32_t n_words, float *out, void *stream);
 
+/*
+ * ssa_pipe_rates -- measurement support (no counterpart in the paper): throughput of the
+ * instruction classes an SSA step is made of on the current GPU, as operations per SM per clock at
+ * the device's maximum SM clock, written to host_rates[5] = {binary32 FMA, binary64 add, logf,
+ * 32-bit integer multiply (high and low), lg2.approx}. Also returns that clock (MHz) and the SM
+ * count. Synchronous; allocates and frees a small device buffer.
+ */
+ssa_status ssa_pipe_rates(double *host_rates, double *host_sm_clock_mhz, int32_t *host_sm_count);
+
 const char *ssa_last_error(void);
 
 #ifdef __cplusplus

@@ -227,6 +227,19 @@ def philox_uniforms(seed: int, traj, step, n_words: int, device="cuda") -> torch
     return out
 
 
+def pipe_rates() -> dict:
+    """ssa_pipe_rates: measured operations per SM per clock of the instruction classes of a step."""
+    rates = (ctypes.c_double * 5)()
+    mhz = ctypes.c_double()
+    sms = ctypes.c_int32()
+    check(_lib.lib().ssa_pipe_rates(rates, ctypes.byref(mhz), ctypes.byref(sms)))
+    names = ("ffma", "dadd", "logf", "imad", "lg2")
+    out = {n: float(rates[i]) for i, n in enumerate(names)}
+    out["sm_clock_mhz"] = float(mhz.value)
+    out["sm_count"] = int(sms.value)
+    return out
+
+
 class SSAFunction(torch.autograd.Function):
     """obs = SSA(theta) with the straight-through gradient of Eqs. 5 and 7 in backward."""
 

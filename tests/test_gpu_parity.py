@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
-Levels (the spec contract for this method):
+Parity levels for this method:
 * Philox words: bit-exact.
 * Integer states given the same event sequence (replay of the oracle's events): bit-exact.
 * Event sequences: identical on >= 99.9% of trajectories; at the first step where a trajectory
