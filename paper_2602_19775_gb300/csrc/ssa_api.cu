@@ -30,6 +30,9 @@ cudaError_t launch_backward_thread(const AdjParams &p, int readout, int block, s
                                    cudaStream_t st);
 cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, const int *rate_index, int P,
                                    float *dA_tmp, float *dtheta, cudaStream_t st);
+cudaError_t launch_forward_warp(const FwdParams &p, int readout, bool record, int warps, size_t smem, cudaStream_t st);
+cudaError_t launch_backward_warp(const AdjParams &p, int readout, int warps, size_t smem, int64_t grid,
+                                 cudaStream_t st);
 }  // namespace ssa
 
 using namespace ssa;
@@ -66,7 +69,10 @@ ssa_status set_error(ssa_status code, const char *text) { return fail(code, "%s"
 // ---------------------------------------------------------------------------------------------
 struct ssa_network {
     int32_t N, M, Mp, P, nnz, nnz_pad;  // Mp = 4 * ceil((M + 1)/4): padded reaction count
-    void *d_blob;       // [rx: int4 Mp][stoich: int nnz_pad][rate_index: int Mp]
+    // d_blob = [rx: int4 Mp][stoich: int nnz_pad][inc_ptr: int N+1, padded][inc_list: int 2M, padded]
+    //          [rate_index: int Mp]; the first four parts are the tables staged into shared memory
+    void *d_blob;
+    uint32_t inc_off, inc_list_off;
     int4 *d_rx;
     int *d_stoich;
     int *d_rate_index;
@@ -75,6 +81,7 @@ struct ssa_network {
 
 namespace {
 constexpr size_t kAlign = 256;
+constexpr int kWarpsPerBlock = 4;  // warp-per-trajectory kernels
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
@@ -108,7 +115,7 @@ WsLayout layout(const ssa_network *net, int64_t n, int32_t S, const ssa_fwd_opts
         const int K = effective_K(o);
         L.ev_rows = (o->max_steps + 7) / 8;
         L.n_ckpt = o->max_steps / K + 1;
-        L.max_blocks = (n + 31) / 32;
+        L.max_blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;  // the warp kernels launch the most blocks
         L.xfinal = take((size_t)net->N * n * sizeof(int));
         L.ev = take((size_t)L.ev_rows * n * sizeof(uint4));
         L.ckpt = take((size_t)L.n_ckpt * net->N * n * sizeof(int));
@@ -148,6 +155,23 @@ size_t adj_smem(const ssa_network *net, int block)
     return net->tab_bytes + (size_t)net->Mp * 4 + 16 + (size_t)(3 * net->N + 2 * net->M) * block * 4;
 }
 
+size_t fwd_warp_smem(const ssa_network *net)
+{
+    return net->tab_bytes + (size_t)net->Mp * 4 + 16 + (size_t)kWarpsPerBlock * ((net->N + 3) & ~3) * 4;
+}
+size_t adj_warp_smem(const ssa_network *net)
+{
+    return net->tab_bytes + (size_t)net->Mp * 4 + 16 +
+           (size_t)kWarpsPerBlock * (2 * ((net->N + 3) & ~3) + 5 * (size_t)net->Mp) * 4;
+}
+
+// one thread per trajectory up to 16 reactions (unrolled, register-resident), one warp above
+int pick_variant(const ssa_network *net, const ssa_fwd_opts *o)
+{
+    if (o->threads_per_traj) return o->threads_per_traj;
+    return net->M <= 16 ? 1 : 32;
+}
+
 int pick_block(size_t (*need)(const ssa_network *, int), const ssa_network *net, int requested, size_t limit)
 {
     if (requested) return need(net, requested) <= limit ? requested : 0;
@@ -160,6 +184,7 @@ int pick_block(size_t (*need)(const ssa_network *, int), const ssa_network *net,
 
 struct ssa_run {
     const ssa_network *net;
+    int variant;  // 1: thread per trajectory, 32: warp per trajectory
     int64_t n_traj;
     uint64_t traj_offset, seed;
     int32_t S, n_obs;
@@ -197,6 +222,12 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
             return fail(SSA_ERR_INVALID_ARG, "rate_index[%d] = %d out of range", j, rate_index[j]);
         rx[j] = make_int4(r1, r2, stoich_ptr[j], stoich_ptr[j + 1]);
     }
+    for (int j = 0; j < n_reactions; ++j)  // one entry per species in a reaction's net change
+        for (int e = stoich_ptr[j]; e < stoich_ptr[j + 1]; ++e)
+            for (int f = stoich_ptr[j]; f < e; ++f)
+                if (stoich_species[e] == stoich_species[f])
+                    return fail(SSA_ERR_INVALID_ARG, "reaction %d lists species %d twice in its net change", j,
+                                stoich_species[e]);
     const int nnz_pad = (nnz + 3) / 4 * 4;
     std::vector<int> st(nnz_pad > 0 ? nnz_pad : 4, 0);
     for (int e = 0; e < nnz; ++e) {
@@ -208,6 +239,19 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
     }
     std::vector<int> ri(Mp, 0);
     for (int j = 0; j < n_reactions; ++j) ri[j] = rate_index[j];
+    // species -> reactant slots (2j + slot) in increasing order; a homodimer lists slot 0 only
+    std::vector<int> inc_ptr(n_species + 1, 0), inc_list;
+    for (int sp = 0; sp < n_species; ++sp) {
+        for (int j = 0; j < n_reactions; ++j) {
+            if (rx[j].x == sp) inc_list.push_back(2 * j);
+            if (rx[j].y == sp && rx[j].y != rx[j].x) inc_list.push_back(2 * j + 1);
+        }
+        inc_ptr[sp + 1] = (int)inc_list.size();
+    }
+    const int inc_ptr_pad = (n_species + 1 + 3) / 4 * 4;
+    const int inc_list_pad = ((int)inc_list.size() + 3) / 4 * 4;
+    inc_ptr.resize(inc_ptr_pad, inc_ptr[n_species]);
+    inc_list.resize(inc_list_pad > 0 ? inc_list_pad : 4, 0);
 
     ssa_network *net = new (std::nothrow) ssa_network();
     if (!net) return fail(SSA_ERR_CUDA, "host allocation failed");
@@ -217,7 +261,9 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
     net->Mp = Mp;
     net->nnz = nnz;
     net->nnz_pad = nnz_pad;
-    net->tab_bytes = (uint32_t)(16 * Mp + 4 * nnz_pad);
+    net->inc_off = (uint32_t)(16 * Mp + 4 * nnz_pad);
+    net->inc_list_off = net->inc_off + (uint32_t)(4 * inc_ptr_pad);
+    net->tab_bytes = net->inc_list_off + (uint32_t)(4 * inc_list_pad);
     const size_t bytes = net->tab_bytes + (size_t)Mp * 4;
     cudaError_t e = cudaMalloc(&net->d_blob, bytes);
     if (e != cudaSuccess) {
@@ -231,6 +277,10 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
     e = cudaMemcpy(net->d_rx, rx.data(), 16 * (size_t)Mp, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(net->d_stoich, st.data(), 4 * (size_t)nnz_pad, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(net->d_rate_index, ri.data(), 4 * (size_t)Mp, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && inc_ptr_pad > 0)
+        e = cudaMemcpy(b + net->inc_off, inc_ptr.data(), 4 * (size_t)inc_ptr_pad, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && inc_list_pad > 0)
+        e = cudaMemcpy(b + net->inc_list_off, inc_list.data(), 4 * (size_t)inc_list_pad, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(net->d_blob);
         delete net;
@@ -273,15 +323,21 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     if (S > 0 && n_obs > 0 && n_traj > 0 && !obs_out) return fail(SSA_ERR_INVALID_ARG, "obs_out is NULL");
     if (ev_in && (ev_stride < 1 || !n_ev_in)) return fail(SSA_ERR_INVALID_ARG, "bad replay arguments");
     if (opts->record && opts->max_steps > 0x7fffffffLL) return fail(SSA_ERR_INVALID_ARG, "max_steps too large");
-    if (opts->threads_per_traj == 32) return fail(SSA_ERR_UNSUPPORTED, "warp-per-trajectory kernel not built");
     const WsLayout L = layout(net, n_traj, S, opts);
     if (!workspace || ws_bytes < L.total) return fail(SSA_ERR_WORKSPACE, "workspace %zu bytes < required %zu", ws_bytes, L.total);
     if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return fail(SSA_ERR_WORKSPACE, "workspace not 256-byte aligned");
     const size_t limit = smem_limit();
-    const int block = pick_block(fwd_smem, net, opts->block_threads, limit);
-    if (!block) return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory forward");
-    if (opts->record && !pick_block(adj_smem, net, 0, limit))
-        return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory adjoint");
+    const int variant = ev_in ? 1 : pick_variant(net, opts);  // replay is a thread-per-trajectory test hook
+    int block = 0;
+    if (variant == 1) {
+        block = pick_block(fwd_smem, net, opts->block_threads, limit);
+        if (!block) return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory forward");
+        if (opts->record && !pick_block(adj_smem, net, 0, limit))
+            return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory adjoint");
+    } else {
+        if (fwd_warp_smem(net) > limit || (opts->record && adj_warp_smem(net) > limit))
+            return fail(SSA_ERR_UNSUPPORTED, "network too large for the warp-per-trajectory kernels");
+    }
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char *ws = static_cast<unsigned char *>(workspace);
@@ -300,6 +356,8 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     p.N = net->N;
     p.M = net->M;
     p.Mp = net->Mp;
+    p.inc_off = net->inc_off;
+    p.inc_list_off = net->inc_list_off;
     p.nnz = net->nnz;
     p.n_traj = n_traj;
     p.traj_offset = (uint64_t)traj_offset;
@@ -328,13 +386,17 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     p.ev_in = ev_in;
     p.n_ev_in = n_ev_in;
     p.ev_in_stride = ev_stride;
-    CUDA_TRY(launch_forward_thread(p, opts->readout, opts->record != 0, ev_in != nullptr, block, fwd_smem(net, block), st));
+    if (variant == 1)
+        CUDA_TRY(launch_forward_thread(p, opts->readout, opts->record != 0, ev_in != nullptr, block, fwd_smem(net, block), st));
+    else
+        CUDA_TRY(launch_forward_warp(p, opts->readout, opts->record != 0, kWarpsPerBlock, fwd_warp_smem(net), st));
     if (n_traj > 0 && draws_out) CUDA_TRY(cudaMemcpyAsync(draws_out, p.draws, (size_t)n_traj * 4, cudaMemcpyDeviceToDevice, st));
     if (n_traj > 0 && status_out) CUDA_TRY(cudaMemcpyAsync(status_out, p.status, (size_t)n_traj * 4, cudaMemcpyDeviceToDevice, st));
     if (run_out) {
         ssa_run *run = new (std::nothrow) ssa_run();
         if (!run) return fail(SSA_ERR_CUDA, "host allocation failed");
         run->net = net;
+        run->variant = variant;
         run->n_traj = n_traj;
         run->traj_offset = (uint64_t)traj_offset;
         run->seed = seed;
@@ -389,9 +451,15 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     unsigned char *ws = run->ws;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t limit = smem_limit();
-    const int block = pick_block(adj_smem, net, 0, limit);
-    if (!block) return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory adjoint");
-    const int64_t grid = (run->n_traj + block - 1) / block;
+    int block = 0;
+    int64_t grid = 0;
+    if (run->variant == 1) {
+        block = pick_block(adj_smem, net, 0, limit);
+        if (!block) return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory adjoint");
+        grid = (run->n_traj + block - 1) / block;
+    } else {
+        grid = (run->n_traj + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    }
     int *flag = reinterpret_cast<int *>(ws + L.flag);
     CUDA_TRY(cudaMemsetAsync(flag + 2, 0, sizeof(int), st));  // mismatch counter
     AdjParams p{};
@@ -402,6 +470,8 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     p.N = net->N;
     p.M = net->M;
     p.Mp = net->Mp;
+    p.inc_off = net->inc_off;
+    p.inc_list_off = net->inc_list_off;
     p.nnz = net->nnz;
     p.n_traj = run->n_traj;
     p.traj_offset = run->traj_offset;
@@ -424,7 +494,10 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     p.partial = reinterpret_cast<float *>(ws + L.partial);
     p.mismatch = flag + 2;
     p.err = flag + 1;
-    CUDA_TRY(launch_backward_thread(p, run->opts.readout, block, adj_smem(net, block), grid, st));
+    if (run->variant == 1)
+        CUDA_TRY(launch_backward_thread(p, run->opts.readout, block, adj_smem(net, block), grid, st));
+    else
+        CUDA_TRY(launch_backward_warp(p, run->opts.readout, kWarpsPerBlock, adj_warp_smem(net), grid, st));
     CUDA_TRY(launch_reduce_partials(p.partial, grid, net->M, net->d_rate_index, net->P,
                                     reinterpret_cast<float *>(ws + L.dA), dl_dlog_rates, st));
     return SSA_OK;

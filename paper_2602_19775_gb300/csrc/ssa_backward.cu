@@ -23,41 +23,6 @@
 
 namespace ssa {
 
-// Forward helpers shared bit for bit with the forward kernels (same binary32 operations).
-template <int NQ>
-__device__ __forceinline__ void step_noise_b(float (&E)[NQ], uint32_t k, uint32_t c2, uint32_t c3, uint32_t key0,
-                                             uint32_t key1)
-{
-#pragma unroll
-    for (int b = 0; b < (NQ + 3) / 4; ++b) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
-        if (4 * b + 0 < NQ) E[4 * b + 0] = -logf(u01(r.x));
-        if (4 * b + 1 < NQ) E[4 * b + 1] = -logf(u01(r.y));
-        if (4 * b + 2 < NQ) E[4 * b + 2] = -logf(u01(r.z));
-        if (4 * b + 3 < NQ) E[4 * b + 3] = -logf(u01(r.w));
-    }
-}
-
-__device__ __forceinline__ float exp_variate_b(uint32_t k, int q, uint32_t c2, uint32_t c3, uint32_t key0,
-                                               uint32_t key1, uint4 &cache, int &cached_b)
-{
-    const int b = q >> 2;
-    if (b != cached_b) {
-        cache = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
-        cached_b = b;
-    }
-    return -logf(u01(word_of(cache, q & 3)));
-}
-
-__device__ __forceinline__ void race_b(float a, float E, int j, float &ab, float &Eb, int &jb)
-{
-    if (__fmul_rn(a, Eb) > __fmul_rn(ab, E)) {
-        ab = a;
-        Eb = E;
-        jb = j;
-    }
-}
-
 // State adjoint of reaction j: choice path psi * dlog a/dX (a > 0) and waiting-time path
 // c_tau * da/dX with c_tau = dL/da0 * k_j (polynomial derivative, also where a_j = 0).
 __device__ __forceinline__ void reaction_state_adjoint(const int4 rx, const int *X, int B, float a, float h, float psi,
@@ -155,7 +120,7 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
         constexpr int NQ = MC > 0 ? MC + 1 : 1;
         float E[NQ], En[NQ];
         const bool draw_last = st == SSA_TRAJ_OK;
-        if (MC > 0) step_noise_b<NQ>(E, (uint32_t)(draw_last ? L : (L > 0 ? L - 1 : 0)), c2, c3, key0, key1);
+        if (MC > 0) step_noise<NQ>(E, (uint32_t)(draw_last ? L : (L > 0 ? L - 1 : 0)), c2, c3, key0, key1);
 
         for (int k = L; k >= 0; --k) {
             const bool draw = (k < L) || draw_last;
@@ -172,13 +137,13 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
                 float ar[MC > 0 ? MC : 1], lr[MC > 0 ? MC : 1];
                 // pass 1: the forward's propensities, a0 and race, bit for bit; log2 keys
                 if constexpr (MC > 0) {
-                    if (k > 0) step_noise_b<NQ>(En, (uint32_t)(k - 1), c2, c3, key0, key1);  // prefetch
+                    if (k > 0) step_noise<NQ>(En, (uint32_t)(k - 1), c2, c3, key0, key1);  // prefetch
                     E0 = E[0];
 #pragma unroll
                     for (int j = 0; j < MC; ++j) {
                         const float a = __fmul_rn(s_k[j], mass_action_h(s_rx[j], X, B));
                         a0 = __fadd_rn(a0, a);
-                        race_b(a, E[j + 1], j, ab, Eb, jb);
+                        race(a, E[j + 1], j, ab, Eb, jb);
                         ar[j] = a;
                         lr[j] = a > 0.0f ? __log2f(a) - __log2f(E[j + 1]) : -CUDART_INF_F;
                         lmax = fmaxf(lmax, lr[j]);
@@ -186,14 +151,14 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
                 } else {
                     uint4 cache;
                     int cb = -1;
-                    E0 = exp_variate_b((uint32_t)k, 0, c2, c3, key0, key1, cache, cb);
+                    E0 = exp_variate((uint32_t)k, 0, c2, c3, key0, key1, cache, cb);
                     for (int j = 0; j < M; ++j) {
                         const float a = __fmul_rn(s_k[j], mass_action_h(s_rx[j], X, B));
                         a0 = __fadd_rn(a0, a);
                         float l = -CUDART_INF_F;
                         if (a > 0.0f) {
-                            const float Ej = exp_variate_b((uint32_t)k, j + 1, c2, c3, key0, key1, cache, cb);
-                            race_b(a, Ej, j, ab, Eb, jb);
+                            const float Ej = exp_variate((uint32_t)k, j + 1, c2, c3, key0, key1, cache, cb);
+                            race(a, Ej, j, ab, Eb, jb);
                             l = __log2f(a) - __log2f(Ej);
                             lmax = fmaxf(lmax, l);
                         }
@@ -323,22 +288,30 @@ __global__ void __launch_bounds__(256) adj_thread_kernel(const AdjParams p)
     }
 }
 
-// dA[j] = sum over blocks (fixed order); dtheta[r] = sum_{j: r(j) = r} dA[j] (fixed order).
-// Launched with one block so that the block barrier orders both phases.
-__global__ void reduce_partials_kernel(const float *partial, int64_t nblk, int M, const int *rate_index, int P,
-                                       float *dA_tmp, float *dtheta)
+// dA[j] = sum over blocks of partial[b][j]: one block per reaction, a fixed strided assignment of the
+// partial rows to threads and a fixed shared-memory tree, so the result does not depend on timing.
+__global__ void reduce_partials_kernel(const float *partial, int64_t nblk, int M, float *dA)
 {
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        float acc = 0.0f;
-        for (int64_t b = 0; b < nblk; ++b) acc += partial[b * M + j];
-        dA_tmp[j] = acc;
-    }
-    __threadfence_block();
+    __shared__ float red[256];
+    const int j = blockIdx.x;
+    float acc = 0.0f;
+    for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) acc += partial[b * M + j];
+    red[threadIdx.x] = acc;
     __syncthreads();
-    for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dA[j] = red[0];
+}
+
+// dtheta[r] = sum_{j: r(j) = r} dA[j], summed in increasing j.
+__global__ void map_params_kernel(const float *dA, int M, const int *rate_index, int P, float *dtheta)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P; r += gridDim.x * blockDim.x) {
         float acc = 0.0f;
         for (int j = 0; j < M; ++j)
-            if (rate_index[j] == r) acc += dA_tmp[j];
+            if (rate_index[j] == r) acc += dA[j];
         dtheta[r] = acc;
     }
 }
@@ -378,7 +351,8 @@ cudaError_t launch_backward_thread(const AdjParams &p, int readout, int block, s
 cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, const int *rate_index, int P,
                                    float *dA_tmp, float *dtheta, cudaStream_t st)
 {
-    reduce_partials_kernel<<<1, 512, 0, st>>>(partial, nblk, M, rate_index, P, dA_tmp, dtheta);
+    if (M > 0) reduce_partials_kernel<<<M, 256, 0, st>>>(partial, nblk, M, dA_tmp);
+    if (P > 0) map_params_kernel<<<(P + 255) / 256, 256, 0, st>>>(dA_tmp, M, rate_index, P, dtheta);
     return cudaGetLastError();
 }
 

@@ -18,47 +18,6 @@
 
 namespace ssa {
 
-// Exponential variates of one step, E[q] = -ln u_q for the first NQ words of the step's Philox
-// stream (q = 0 drives the waiting time, q = 1 + j reaction j). They do not depend on the state,
-// so the kernels draw the next step's variates while the current step's state-dependent chain
-// runs (instruction-level parallelism at low occupancy).
-template <int NQ>
-__device__ __forceinline__ void step_noise(float (&E)[NQ], uint32_t k, uint32_t c2, uint32_t c3, uint32_t key0,
-                                           uint32_t key1)
-{
-#pragma unroll
-    for (int b = 0; b < (NQ + 3) / 4; ++b) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
-        if (4 * b + 0 < NQ) E[4 * b + 0] = -logf(u01(r.x));
-        if (4 * b + 1 < NQ) E[4 * b + 1] = -logf(u01(r.y));
-        if (4 * b + 2 < NQ) E[4 * b + 2] = -logf(u01(r.z));
-        if (4 * b + 3 < NQ) E[4 * b + 3] = -logf(u01(r.w));
-    }
-}
-
-// -ln u_q of one word (runtime-indexed variant for networks without a compile-time size).
-__device__ __forceinline__ float exp_variate(uint32_t k, int q, uint32_t c2, uint32_t c3, uint32_t key0, uint32_t key1,
-                                             uint4 &cache, int &cached_b)
-{
-    const int b = q >> 2;
-    if (b != cached_b) {
-        cache = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
-        cached_b = b;
-    }
-    return -logf(u01(word_of(cache, q & 3)));
-}
-
-// The Gumbel-max choice as an exponential race: argmax_j a_j/E_j, compared as a_j E_b > a_b E_j
-// (binary32 products); ties keep the lowest j. The adjoint repeats the identical comparisons.
-__device__ __forceinline__ void race(float a, float E, int j, float &ab, float &Eb, int &jb)
-{
-    if (__fmul_rn(a, Eb) > __fmul_rn(ab, E)) {
-        ab = a;
-        Eb = E;
-        jb = j;
-    }
-}
-
 // Thread-per-trajectory forward. MC > 0: the network has at most MC reactions (tables padded with
 // zero-rate, order-0 entries), per-reaction loops are unrolled and the step's variates live in
 // registers. MC == 0: runtime loops for any size.
