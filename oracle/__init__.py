@@ -25,4 +25,6 @@ from .native import (  # noqa: F401
     uniforms,
     run,
     OracleResult,
+    grn_run,
+    GRNResult,
 )

@@ -86,3 +86,57 @@ def st_gradient(net, log_rates, x0, events, n_states: int, crossed: bool, seed: 
     L = (torch.as_tensor(np.asarray(dl_dobs, dtype=np.float64)) * obs).sum()
     L.backward()
     return theta.grad.detach().numpy().copy(), obs.detach().numpy()
+
+
+def grn_st_gradient(params, x, events, n_states: int, crossed: bool, seed: int, traj: int, sample_times,
+                    dl_dobs, temperature: float):
+    """dL/d(W1, b1, W2, b2, log_d) of L = sum(dl_dobs * obs) through the literal straight-through
+    graph of one GRN trajectory (HOLD readout of the outputs), by float64 autograd."""
+    W1 = torch.tensor(np.asarray(params.W1, np.float64), requires_grad=True)
+    b1 = torch.tensor(np.asarray(params.b1, np.float64), requires_grad=True)
+    W2 = torch.tensor(np.asarray(params.W2, np.float64), requires_grad=True)
+    b2 = torch.tensor(np.asarray(params.b2, np.float64), requires_grad=True)
+    ld = torch.tensor(np.asarray(params.log_d, np.float64), requires_grad=True)
+    nh, no = W1.shape[0], W2.shape[0]
+    nd = nh + no
+    M = 2 * nd
+    xin = torch.as_tensor(np.asarray(x, np.float64))
+    E1 = W1 @ xin + b1
+    V = torch.zeros((M, nd), dtype=torch.float64)
+    for s in range(nd):
+        V[s, s] = 1.0
+        V[nd + s, s] = -1.0
+    X = torch.zeros(nd, dtype=torch.float64)
+    t = 0.0
+    states, times = [X], [0.0]
+    for k in range(len(events)):
+        u = torch.as_tensor(uniforms(seed, traj, k, M + 1))
+        E2 = W2 @ X[:nh] + b2
+        a = torch.cat([params.k_max * torch.sigmoid(E1), params.k_max * torch.sigmoid(E2), torch.exp(ld) * X])
+        a0 = a.sum()
+        tau = -torch.log(u[0]) / a0
+        active = a > 0
+        safe_a = torch.where(active, a, torch.ones_like(a))
+        G = -torch.log(-torch.log(u[1:]))
+        z = torch.where(active, (torch.log(safe_a) + G) / temperature, torch.full_like(a, -float("inf")))
+        y_soft = torch.softmax(z, dim=0)
+        y_hard = torch.zeros(M, dtype=torch.float64)
+        y_hard[int(events[k])] = 1.0
+        y_st = y_soft + (y_hard - y_soft).detach()
+        X_next = X + y_st @ V
+        t_next = t + float(tau)
+        if k + 1 < n_states:
+            X, t = X_next, t_next
+            states.append(X)
+            times.append(t)
+    obs = []
+    for ts in np.asarray(sample_times, dtype=np.float64):
+        k = 0
+        while k + 1 < n_states and times[k + 1] <= ts:
+            k += 1
+        obs.append(states[k][nh:])
+    obs = torch.stack(obs)
+    L = (torch.as_tensor(np.asarray(dl_dobs, np.float64)) * obs).sum()
+    L.backward()
+    return {"W1": W1.grad.numpy().copy(), "b1": b1.grad.numpy().copy(), "W2": W2.grad.numpy().copy(),
+            "b2": b2.grad.numpy().copy(), "log_d": ld.grad.numpy().copy()}

@@ -62,6 +62,9 @@ def _load():
         lib.orc_uniforms.argtypes = [u64, u64, u64, i64, p]
         lib.orc_philox_blocks.restype = None
         lib.orc_philox_blocks.argtypes = [u64, p, i64, p]
+        lib.orc_grn_run.restype = ctypes.c_int
+        lib.orc_grn_run.argtypes = [p, i64, i64, i64, p, f64, p, i32, u64, i64, p, f64, p, p, p, p, p, p, p,
+                                    p, p, i64, i32]
         _lib = lib
     return _lib
 
@@ -145,3 +148,73 @@ def run(net, log_rates, x0, n_traj: int, t_end: float, sample_times, obs_species
     if rc != 0:
         raise ValueError("oracle rejected its inputs (orc_run returned %d)" % rc)
     return OracleResult(obs, draws, status, dth, ev, mg, tm, final_x)
+
+
+class _GRN(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("n_hid", ctypes.c_int32), ("n_out", ctypes.c_int32),
+                ("W1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("W2", ctypes.c_void_p), ("b2", ctypes.c_void_p),
+                ("log_d", ctypes.c_void_p), ("k_max", ctypes.c_double)]
+
+
+@dataclass
+class GRNResult:
+    obs: np.ndarray            # [n_traj, S, n_out] float64 (HOLD counts of the outputs)
+    draws: np.ndarray
+    status: np.ndarray
+    dE1: np.ndarray | None     # [n_traj, n_hid] dL/dE1 per trajectory
+    dW2: np.ndarray | None     # [n_traj, n_out, n_hid]
+    db2: np.ndarray | None     # [n_traj, n_out]
+    dlogd: np.ndarray | None   # [n_traj, n_hid + n_out]
+    events: np.ndarray | None
+    margins: np.ndarray | None
+
+    def grads(self, x_img, traj_per_img):
+        """Parameter gradients summed over trajectories: dW1 = sum_traj dE1 x^T, db1 = sum dE1, ..."""
+        n_img = x_img.shape[0]
+        g_img = self.dE1.reshape(n_img, traj_per_img, -1).sum(1)
+        return {"W1": g_img.T @ x_img.astype(np.float64), "b1": g_img.sum(0), "W2": self.dW2.sum(0),
+                "b2": self.db2.sum(0), "log_d": self.dlogd.sum(0)}
+
+
+def grn_run(params, x_img, traj_per_img: int, t_end: float, sample_times, seed: int, max_steps: int = 1 << 30,
+            traj_offset: int = 0, dl_dobs=None, temperature: float = 1.0, ev_cap: int = 0,
+            n_threads: int | None = None) -> GRNResult:
+    """GRN oracle (FP64): HOLD readout of the output genes at the sample times."""
+    lib = _load()
+    W1 = np.ascontiguousarray(params.W1, dtype=np.float64)
+    b1 = np.ascontiguousarray(params.b1, dtype=np.float64)
+    W2 = np.ascontiguousarray(params.W2, dtype=np.float64)
+    b2 = np.ascontiguousarray(params.b2, dtype=np.float64)
+    ld = np.ascontiguousarray(params.log_d, dtype=np.float64)
+    n_hid, n_in = W1.shape
+    n_out = W2.shape[0]
+    g = _GRN(n_in, n_hid, n_out, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2), _ptr(ld), float(params.k_max))
+    x = np.ascontiguousarray(x_img, dtype=np.int32)
+    n_img = x.shape[0]
+    n_traj = n_img * traj_per_img
+    ts = np.ascontiguousarray(sample_times, dtype=np.float64)
+    S = ts.shape[0]
+    obs = np.zeros((n_traj, S, n_out))
+    draws = np.zeros(n_traj, np.int64)
+    status = np.zeros(n_traj, np.int32)
+    gl = dE1 = dW2 = db2 = dld = None
+    if dl_dobs is not None:
+        gl = np.ascontiguousarray(dl_dobs, dtype=np.float64)
+        assert gl.shape == (n_traj, S, n_out)
+        dE1 = np.zeros((n_traj, n_hid))
+        dW2 = np.zeros((n_traj, n_out, n_hid))
+        db2 = np.zeros((n_traj, n_out))
+        dld = np.zeros((n_traj, n_hid + n_out))
+    ev = mg = None
+    if ev_cap > 0:
+        ev = np.zeros((n_traj, ev_cap), np.int32)
+        mg = np.zeros((n_traj, ev_cap))
+    if n_threads is None:
+        n_threads = min(os.cpu_count() or 1, max(1, n_traj // 4))
+    rc = lib.orc_grn_run(ctypes.byref(g), n_img, traj_per_img, traj_offset, _ptr(x), float(t_end), _ptr(ts), S,
+                         ctypes.c_uint64(seed), max_steps, _ptr(gl), float(temperature), _ptr(obs), _ptr(draws),
+                         _ptr(status), _ptr(dE1), _ptr(dW2), _ptr(db2), _ptr(dld), _ptr(ev), _ptr(mg), ev_cap,
+                         int(n_threads))
+    if rc != 0:
+        raise ValueError("GRN oracle rejected its inputs")
+    return GRNResult(obs, draws, status, dE1, dW2, db2, dld, ev, mg)

@@ -557,3 +557,269 @@ int orc_run(const orc_network *net, int64_t n_traj, int64_t traj_offset,
     pthread_mutex_destroy(&job.lock);
     return job.error ? -1 : 0;
 }
+
+/* ======================================================================================== */
+/* Gene-regulatory-network classifier (Section 4.3, Figure 4A).                               */
+/*                                                                                            */
+/* Species: n_in clamped input transcription factors x_p (constant counts), n_hid hidden gene  */
+/* products h_i and n_out output gene products y_o; the dynamic species are s = 0..n_dyn-1     */
+/* with n_dyn = n_hid + n_out (hidden first). Reactions: j < n_dyn is the production of       */
+/* species j, j >= n_dyn the degradation of species j - n_dyn. Propensities:                  */
+/*   production of h_i:  k_max sigma(E1_i),  E1 = W1 x + b1   (the promoter's ON probability    */
+/*                                                            is a logistic in an affine      */
+/*                                                            function of the regulators)     */
+/*   production of y_o:  k_max sigma(E2_o),  E2 = W2 h + b2                                     */
+/*   degradation of s:   d_s X_s,            d_s = exp(log_d_s)                                 */
+/* The simulation, the Gumbel-max choice and the straight-through adjoint follow the same      */
+/* definitions as the mass-action oracle above; parameters are W1, b1, W2, b2 and log_d.      */
+/* ======================================================================================== */
+typedef struct {
+    int32_t n_in, n_hid, n_out;
+    const double *W1;    /* [n_hid][n_in] */
+    const double *b1;    /* [n_hid] */
+    const double *W2;    /* [n_out][n_hid] */
+    const double *b2;    /* [n_out] */
+    const double *log_d; /* [n_hid + n_out] */
+    double k_max;
+} orc_grn;
+
+static double orc_sigmoid(double e) { return e >= 0.0 ? 1.0 / (1.0 + exp(-e)) : exp(e) / (1.0 + exp(e)); }
+
+typedef struct {
+    const orc_grn *g;
+    int64_t n_img, traj_per_img, traj_offset;
+    const int32_t *x_img; /* [n_img][n_in] */
+    double t_end;
+    const double *ts;
+    int32_t S;
+    uint64_t seed;
+    int64_t max_steps;
+    const double *dL_dobs; /* [n_traj][S][n_out] or NULL */
+    double T;
+    double *obs_out;       /* [n_traj][S][n_out] */
+    int64_t *draws_out;
+    int32_t *status_out;
+    double *dE1_out;       /* [n_traj][n_hid]: dL/dE1 per trajectory (or NULL) */
+    double *dW2_out;       /* [n_traj][n_out][n_hid] (or NULL) */
+    double *db2_out;       /* [n_traj][n_out] */
+    double *dlogd_out;     /* [n_traj][n_dyn] */
+    int32_t *events_out;   /* [n_traj][ev_cap] or NULL */
+    double *margins_out;
+    int64_t ev_cap;
+    int64_t next;
+    pthread_mutex_t lock;
+    int error;
+} orc_grn_job;
+
+/* propensities of all M = 2 n_dyn reactions at state X (double counts) */
+static void orc_grn_prop(const orc_grn *g, const double *E1, const double *X, double *a, double *E2)
+{
+    const int nh = g->n_hid, no = g->n_out, nd = nh + no;
+    for (int o = 0; o < no; ++o) {
+        double e = g->b2[o];
+        for (int i = 0; i < nh; ++i) e += g->W2[(size_t)o * nh + i] * X[i];
+        E2[o] = e;
+    }
+    for (int i = 0; i < nh; ++i) a[i] = g->k_max * orc_sigmoid(E1[i]);
+    for (int o = 0; o < no; ++o) a[nh + o] = g->k_max * orc_sigmoid(E2[o]);
+    for (int s = 0; s < nd; ++s) a[nd + s] = exp(g->log_d[s]) * X[s];
+}
+
+static void *orc_grn_worker(void *arg)
+{
+    orc_grn_job *job = (orc_grn_job *)arg;
+    const orc_grn *g = job->g;
+    const int nh = g->n_hid, no = g->n_out, nd = nh + no, M = 2 * nd, ni = g->n_in;
+    const int S = job->S;
+    double *E1 = (double *)malloc(sizeof(double) * nh);
+    double *E2 = (double *)malloc(sizeof(double) * no);
+    double *a = (double *)malloc(sizeof(double) * M);
+    double *y = (double *)malloc(sizeof(double) * M);
+    double *lam = (double *)malloc(sizeof(double) * nd);
+    double *lam_new = (double *)malloc(sizeof(double) * nd);
+    double *G2 = (double *)malloc(sizeof(double) * no);
+    if (!E1 || !E2 || !a || !y || !lam || !lam_new || !G2) { job->error = 1; goto done; }
+    for (;;) {
+        pthread_mutex_lock(&job->lock);
+        int64_t i = job->next++;
+        pthread_mutex_unlock(&job->lock);
+        const int64_t n_traj = job->n_img * job->traj_per_img;
+        if (i >= n_traj) break;
+        const uint64_t traj = (uint64_t)(job->traj_offset + i);
+        const int32_t *x = job->x_img + (size_t)(i / job->traj_per_img) * ni;
+        for (int h = 0; h < nh; ++h) {
+            double e = g->b1[h];
+            for (int p = 0; p < ni; ++p) e += g->W1[(size_t)h * ni + p] * (double)x[p];
+            E1[h] = e;
+        }
+        /* forward with the full path kept */
+        int64_t cap = 256, n_states = 0, n_draws = 0;
+        double *Xh = (double *)malloc(sizeof(double) * (cap + 1) * nd);
+        double *th = (double *)malloc(sizeof(double) * (cap + 1));
+        double *tauh = (double *)malloc(sizeof(double) * cap);
+        int32_t *jh = (int32_t *)malloc(sizeof(int32_t) * cap);
+        double *mh = (double *)malloc(sizeof(double) * cap);
+        if (!Xh || !th || !tauh || !jh || !mh) { job->error = 1; free(Xh); free(th); free(tauh); free(jh); free(mh); break; }
+        for (int s = 0; s < nd; ++s) Xh[s] = 0.0;
+        th[0] = 0.0;
+        int32_t status = ORC_OK, crossed = 0;
+        int64_t k = 0;
+        for (;;) {
+            if (k >= job->max_steps) { status = ORC_STEP_CAP; break; }
+            if (k + 2 > cap) {
+                cap *= 2;
+                Xh = (double *)realloc(Xh, sizeof(double) * (cap + 1) * nd);
+                th = (double *)realloc(th, sizeof(double) * (cap + 1));
+                tauh = (double *)realloc(tauh, sizeof(double) * cap);
+                jh = (int32_t *)realloc(jh, sizeof(int32_t) * cap);
+                mh = (double *)realloc(mh, sizeof(double) * cap);
+                if (!Xh || !th || !tauh || !jh || !mh) { job->error = 1; break; }
+            }
+            const double *X = Xh + (size_t)k * nd;
+            orc_grn_prop(g, E1, X, a, E2);
+            double a0 = 0.0;
+            for (int j = 0; j < M; ++j) a0 += a[j];
+            if (a0 == 0.0) { status = ORC_ABSORBED; break; }
+            const double tau = -log(orc_uniform(job->seed, traj, (uint64_t)k, 0)) / a0;
+            int best = -1;
+            double s1 = -INFINITY, s2 = -INFINITY;
+            for (int j = 0; j < M; ++j) {
+                if (!(a[j] > 0.0)) continue;
+                const double key = log(a[j]) - log(-log(orc_uniform(job->seed, traj, (uint64_t)k, 1 + j)));
+                if (key > s1) { s2 = s1; s1 = key; best = j; }
+                else if (key > s2) s2 = key;
+            }
+            jh[k] = best;
+            tauh[k] = tau;
+            mh[k] = (s2 == -INFINITY) ? 1.0 : -expm1(s2 - s1);
+            th[k + 1] = th[k] + tau;
+            n_draws = k + 1;
+            if (th[k + 1] > job->t_end) { crossed = 1; break; }
+            double *Xn = Xh + (size_t)(k + 1) * nd;
+            for (int s = 0; s < nd; ++s) Xn[s] = X[s];
+            if (best < nd) Xn[best] += 1.0;
+            else Xn[best - nd] -= 1.0;
+            ++k;
+        }
+        if (job->error) break;
+        n_states = k + 1;
+        /* readout: HOLD of the outputs at each sample time */
+        double *obs = job->obs_out + (size_t)i * S * no;
+        for (int s = 0; s < S; ++s) {
+            int64_t kb = 0;
+            while (kb + 1 < n_states && th[kb + 1] <= job->ts[s]) ++kb;
+            for (int o = 0; o < no; ++o) obs[(size_t)s * no + o] = Xh[(size_t)kb * nd + nh + o];
+        }
+        if (job->draws_out) job->draws_out[i] = n_draws;
+        if (job->status_out) job->status_out[i] = status;
+        if (job->events_out)
+            for (int64_t q = 0; q < job->ev_cap; ++q) {
+                job->events_out[(size_t)i * job->ev_cap + q] = q < n_draws ? jh[q] : -1;
+                if (job->margins_out) job->margins_out[(size_t)i * job->ev_cap + q] = q < n_draws ? mh[q] : NAN;
+            }
+        /* straight-through adjoint (HOLD readout: no time terms) */
+        if (job->dL_dobs) {
+            double *dE1 = job->dE1_out + (size_t)i * nh;
+            double *dW2 = job->dW2_out + (size_t)i * no * nh;
+            double *db2 = job->db2_out + (size_t)i * no;
+            double *dld = job->dlogd_out + (size_t)i * nd;
+            for (int h = 0; h < nh; ++h) dE1[h] = 0.0;
+            for (int q = 0; q < no * nh; ++q) dW2[q] = 0.0;
+            for (int o = 0; o < no; ++o) db2[o] = 0.0;
+            for (int s = 0; s < nd; ++s) { dld[s] = 0.0; lam[s] = 0.0; }
+            const double *gl = job->dL_dobs + (size_t)i * S * no;
+            double mu = 0.0;
+            for (int64_t kk = n_states - 1; kk >= 0; --kk) {
+                const double *X = Xh + (size_t)kk * nd;
+                const int draw = kk < n_draws && (kk + 1 < n_states || crossed);
+                for (int s = 0; s < nd; ++s) lam_new[s] = lam[s];
+                if (draw) {
+                    orc_grn_prop(g, E1, X, a, E2);
+                    double a0 = 0.0;
+                    for (int j = 0; j < M; ++j) a0 += a[j];
+                    const double tau = tauh[kk];
+                    const double dtau = mu; /* HOLD readout: no direct time terms */
+                    double zmax = -INFINITY;
+                    for (int j = 0; j < M; ++j) {
+                        if (a[j] > 0.0) {
+                            y[j] = (log(a[j]) - log(-log(orc_uniform(job->seed, traj, (uint64_t)kk, 1 + j)))) / job->T;
+                            if (y[j] > zmax) zmax = y[j];
+                        }
+                    }
+                    double Z = 0.0;
+                    for (int j = 0; j < M; ++j) { y[j] = a[j] > 0.0 ? exp(y[j] - zmax) : 0.0; Z += y[j]; }
+                    double wbar = 0.0;
+                    for (int j = 0; j < M; ++j) {
+                        y[j] /= Z;
+                        const double w = j < nd ? lam[j] : -lam[j - nd]; /* v_j = +e_s or -e_s */
+                        wbar += y[j] * w;
+                    }
+                    const double dLda0 = -dtau * tau / a0;
+                    for (int o = 0; o < no; ++o) G2[o] = 0.0;
+                    for (int j = 0; j < M; ++j) {
+                        const double w = j < nd ? lam[j] : -lam[j - nd];
+                        const double psi = a[j] > 0.0 ? y[j] * (w - wbar) / job->T : 0.0;
+                        const double tot = psi + dLda0 * a[j]; /* dL/dlog a_j */
+                        if (j < nh) {
+                            dE1[j] += tot * (1.0 - orc_sigmoid(E1[j]));
+                        } else if (j < nd) {
+                            const int o = j - nh;
+                            G2[o] = tot * (1.0 - orc_sigmoid(E2[o]));
+                        } else {
+                            const int s = j - nd;
+                            dld[s] += tot;
+                            const double d = exp(g->log_d[s]);
+                            lam_new[s] += (a[j] > 0.0 ? psi / X[s] : 0.0) + dLda0 * d;
+                        }
+                    }
+                    for (int o = 0; o < no; ++o) {
+                        db2[o] += G2[o];
+                        for (int h = 0; h < nh; ++h) {
+                            dW2[(size_t)o * nh + h] += G2[o] * X[h];
+                            lam_new[h] += g->W2[(size_t)o * nh + h] * G2[o];
+                        }
+                    }
+                }
+                for (int s = 0; s < S; ++s) {
+                    int64_t kb = 0;
+                    while (kb + 1 < n_states && th[kb + 1] <= job->ts[s]) ++kb;
+                    if (kb != kk) continue;
+                    for (int o = 0; o < no; ++o) lam_new[nh + o] += gl[(size_t)s * no + o];
+                }
+                for (int s = 0; s < nd; ++s) lam[s] = lam_new[s];
+            }
+        }
+        free(Xh); free(th); free(tauh); free(jh); free(mh);
+    }
+done:
+    free(E1); free(E2); free(a); free(y); free(lam); free(lam_new); free(G2);
+    return NULL;
+}
+
+int orc_grn_run(const orc_grn *g, int64_t n_img, int64_t traj_per_img, int64_t traj_offset, const int32_t *x_img,
+                double t_end, const double *ts, int32_t S, uint64_t seed, int64_t max_steps,
+                const double *dL_dobs, double T, double *obs_out, int64_t *draws_out, int32_t *status_out,
+                double *dE1_out, double *dW2_out, double *db2_out, double *dlogd_out,
+                int32_t *events_out, double *margins_out, int64_t ev_cap, int32_t n_threads)
+{
+    if (!g || g->n_in < 0 || g->n_hid < 1 || g->n_out < 1 || n_img < 0 || traj_per_img < 1 || S < 0) return -1;
+    for (int s = 0; s < S; ++s)
+        if (!(ts[s] >= 0.0 && ts[s] <= t_end) || (s > 0 && ts[s] < ts[s - 1])) return -1;
+    if (dL_dobs && (!(T > 0.0) || !dE1_out || !dW2_out || !db2_out || !dlogd_out)) return -1;
+    orc_grn_job job;
+    memset(&job, 0, sizeof(job));
+    job.g = g; job.n_img = n_img; job.traj_per_img = traj_per_img; job.traj_offset = traj_offset;
+    job.x_img = x_img; job.t_end = t_end; job.ts = ts; job.S = S; job.seed = seed; job.max_steps = max_steps;
+    job.dL_dobs = dL_dobs; job.T = T; job.obs_out = obs_out; job.draws_out = draws_out;
+    job.status_out = status_out; job.dE1_out = dE1_out; job.dW2_out = dW2_out; job.db2_out = db2_out;
+    job.dlogd_out = dlogd_out; job.events_out = events_out; job.margins_out = margins_out; job.ev_cap = ev_cap;
+    pthread_mutex_init(&job.lock, NULL);
+    const int nt = n_threads > 0 ? n_threads : 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nt);
+    if (!th) return -1;
+    for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, orc_grn_worker, &job);
+    for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&job.lock);
+    return job.error ? -1 : 0;
+}
