@@ -221,6 +221,18 @@ ssa_status ssa_philox_uniforms(uint64_t seed, const uint64_t *traj, const uint64
                                int64_t n, int32_t n_words, float *out, void *stream);
 
 /*
+ * ssa_bf16_gemm -- D[m][n] = sum_k A[m][k] B[n][k] (+ bias[n]) on the tcgen05 tensor cores, binary32
+ * accumulation in tensor memory. The GRN classifier's dense contraction (Section 4.3, Figure 4A:
+ * activation energy E = b + sum w x) is this product; the entry point exposes it for tests and users.
+ *   A device bf16 [M][lda], B device bf16 [N][ldb] (K-major rows; lda, ldb multiples of 8 and
+ *   16-byte aligned bases), D device float [M][ldd], bias device float [N] or NULL.
+ *   err_flag device int32, set nonzero by the kernel if a bounded wait timed out.
+ */
+ssa_status ssa_bf16_gemm(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K,
+                         int32_t lda, int32_t ldb, const float *bias, float *D, int32_t ldd,
+                         int32_t *err_flag, void *stream);
+
+/*
  * ssa_pipe_rates -- measurement support (no counterpart in the paper): throughput of the
  * instruction classes an SSA step is made of on the current GPU, as operations per SM per clock at
  * the device's maximum SM clock, written to host_rates[5] = {binary32 FMA, binary64 add, logf,

@@ -23,7 +23,7 @@ EXPORTS = (
     "ssa_create_network", "ssa_destroy_network", "ssa_forward_workspace_bytes", "ssa_forward",
     "ssa_forward_replay", "ssa_backward", "ssa_run_status", "ssa_run_events", "ssa_run_brackets", "ssa_destroy_run",
     "ssa_ensemble_mean_workspace_bytes", "ssa_ensemble_mean", "ssa_ensemble_mean_static", "ssa_philox_uniforms",
-    "ssa_pipe_rates", "ssa_last_error",
+    "ssa_bf16_gemm", "ssa_pipe_rates", "ssa_last_error",
 )
 
 
@@ -69,6 +69,7 @@ def _declare(lib):
         "ssa_ensemble_mean_static": (i32, [p, i32, i64, i64, p, p]),
         "ssa_philox_uniforms": (i32, [u64, p, p, i64, i32, p, p]),
         "ssa_pipe_rates": (i32, [p, p, p]),
+        "ssa_bf16_gemm": (i32, [p, p, i32, i32, i32, i32, i32, p, p, i32, p, p]),
         "ssa_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

@@ -1,0 +1,315 @@
+// ssa_tc_gemm.cu -- bf16 GEMM on the fifth-generation tensor cores (tcgen05) with TMA loads and
+// TMEM accumulators:  D[m][n] = sum_t sum_k A_t[m][k] B_t[n][k]  (+ bias[n]).
+//
+// It serves the one dense contraction of the gene-regulatory network (arXiv 2602.19775,
+// Section 4.3): the hidden-gene activation energies E1 = W1 x + b1 of every input image, and the
+// weight gradient dW1 = G^T x of the backward pass.
+//
+// Layout. Operands are K-major bf16 rows in global memory (row stride a multiple of 16 bytes).
+// For each 64-wide K chunk a CTA loads, per operand, eight TMA boxes of 8 elements x `rows`;
+// each box lands as `rows` x 16 bytes, so eight consecutive rows of one box form one 8 x 8
+// "core matrix" of 128 contiguous bytes -- the tcgen05 K-major layout without swizzle, with
+// core matrices 128 B apart along M/N (stride byte offset) and rows*16 B apart along K (leading
+// byte offset). Out-of-range boxes are zero-filled by TMA.
+//
+// Pipeline. One CTA of 128 threads computes a 128 x NT tile. Thread 0 issues the TMA loads of a
+// two-stage ring and the tcgen05.mma instructions (M = 128, N = NT, K = 16 per instruction), and
+// commits each stage to an mbarrier that frees it; warp 0 allocates the TMEM columns; after the
+// last commit every warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) for the epilogue.
+// Terms either share one accumulator or keep one each (`separate`); separate accumulators are
+// summed in binary64 in the epilogue. Every wait is bounded and reports a timeout in `err`.
+#include <cstring>
+
+#include <cuda.h>
+
+#include "ssa_internal.cuh"
+
+namespace ssa {
+
+constexpr int kTcMaxA = 2;
+constexpr int kTcMaxB = 8;
+
+struct TcMaps {
+    CUtensorMap a[kTcMaxA];
+    CUtensorMap b[kTcMaxB];
+};
+
+struct TcArgs {
+    int M, N, K;
+    int n_a, n_b, n_terms;  // term t multiplies A[min(t, n_a - 1)] by B[min(t, n_b - 1)]
+    int separate;           // 1: one TMEM accumulator per term, summed in binary64
+    const float *bias;      // [N] or nullptr
+    float *D;               // [M][ldd]
+    int ldd;
+    int *err;
+};
+
+namespace {
+
+constexpr int kErrTcTimeout = 8;
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor, K-major without swizzle (version 1 for this architecture)
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr(p) >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, N >> 3, M >> 4
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace
+
+template <int NT>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcArgs args)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int kTileA = 128 * 64 * 2;  // bytes of one A tile (128 rows x 64 K)
+    constexpr int kTileB = NT * 64 * 2;
+    const int stage_bytes = args.n_a * kTileA + args.n_b * kTileB;
+    unsigned char *stage0 = tc_smem;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tc_smem + 2 * stage_bytes);  // full[2], empty[2]
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 4);
+    int *s_ok = reinterpret_cast<int *>(bars + 5);
+
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
+    const int n_acc = args.separate ? args.n_terms : 1;
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)(n_acc * NT)) ncols <<= 1;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 4; ++b) mbar_init(&bars[b], 1);
+        *s_ok = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    if (tid == 0) {
+        const int n_chunks = (args.K + 63) / 64;
+        const uint32_t idesc = tc_idesc(128, NT);
+        auto issue = [&](int ch) {
+            unsigned char *st = stage0 + (ch & 1) * stage_bytes;
+            uint64_t *full = &bars[ch & 1];
+            mbar_arrive_expect_tx(full, (uint32_t)stage_bytes);
+            for (int a = 0; a < args.n_a; ++a)
+                for (int c = 0; c < 8; ++c)
+                    tma_load_2d(st + a * kTileA + c * (128 * 16), &maps.a[a], ch * 64 + 8 * c, m0, full);
+            for (int b = 0; b < args.n_b; ++b)
+                for (int c = 0; c < 8; ++c)
+                    tma_load_2d(st + args.n_a * kTileA + b * kTileB + c * (NT * 16), &maps.b[b], ch * 64 + 8 * c, n0,
+                                full);
+        };
+        bool ok = true;
+        issue(0);
+        for (int ch = 0; ch < n_chunks && ok; ++ch) {
+            if (ch + 1 < n_chunks) {
+                if (ch + 1 >= 2) ok = mbar_wait_bounded(&bars[2 + ((ch + 1) & 1)], ((ch - 1) >> 1) & 1, kWaitLimit);
+                if (!ok) break;
+                issue(ch + 1);
+            }
+            ok = mbar_wait_bounded(&bars[ch & 1], (ch >> 1) & 1, kWaitLimit);
+            if (!ok) break;
+            tc_fence_after();
+            unsigned char *st = stage0 + (ch & 1) * stage_bytes;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                for (int t = 0; t < args.n_terms; ++t) {
+                    const int ai = t < args.n_a ? t : args.n_a - 1;
+                    const int bi = t < args.n_b ? t : args.n_b - 1;
+                    const uint64_t ad = smem_desc(st + ai * kTileA + kk * 2 * (128 * 16), 128 * 16, 128);
+                    const uint64_t bd = smem_desc(st + args.n_a * kTileA + bi * kTileB + kk * 2 * (NT * 16), NT * 16, 128);
+                    const uint32_t col = args.separate ? (uint32_t)(t * NT) : 0u;
+                    const uint32_t accum = (ch > 0 || kk > 0 || (!args.separate && t > 0)) ? 1u : 0u;
+                    tc_mma(tmem + col, ad, bd, idesc, accum);
+                }
+            }
+            tc_commit(&bars[2 + (ch & 1)]);
+        }
+        if (ok) ok = mbar_wait_bounded(&bars[2 + ((n_chunks - 1) & 1)], ((n_chunks - 1) >> 1) & 1, kWaitLimit);
+        if (!ok) {
+            atomicOr(args.err, kErrTcTimeout);
+            // let anything still in flight land before the CTA releases its TMEM and exits
+            mbar_wait_bounded(&bars[2 + ((n_chunks - 1) & 1)], ((n_chunks - 1) >> 1) & 1, kWaitLimit);
+            *s_ok = 0;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (*s_ok) {
+        const int row = m0 + 32 * warp + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+        for (int c8 = 0; c8 < NT / 8; ++c8) {
+            float v[8];
+            double acc[8];
+            if (args.separate) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+                for (int t = 0; t < args.n_terms; ++t) {
+                    tmem_ld8(lane_base + (uint32_t)(t * NT + 8 * c8), v);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) acc[i] += (double)v[i];
+                }
+            } else {
+                tmem_ld8(lane_base + (uint32_t)(8 * c8), v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = (double)v[i];
+            }
+            if (row < args.M) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int col = n0 + 8 * c8 + i;
+                    if (col < args.N) {
+                        const double b = args.bias ? (double)args.bias[col] : 0.0;
+                        args.D[(int64_t)row * args.ldd + col] = (float)(acc[i] + b);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 2D bf16 K-major operand: rows x K (elements), row stride ld elements (multiple of 8), box 8 x box_rows
+bool tc_make_map(CUtensorMap *map, const void *base, int rows, int K, int ld, int box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld % 8) || K > ld) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NT>
+static cudaError_t tc_launch_t(const TcMaps &maps, const TcArgs &args, cudaStream_t st)
+{
+    const size_t stage = (size_t)args.n_a * 128 * 128 + (size_t)args.n_b * NT * 128;
+    // 64 KB of slack past the ring: every core-matrix address a descriptor can form from these
+    // tiles stays inside the CTA's shared-memory allocation
+    const size_t smem = 2 * stage + 64 + 65536;
+    if (smem > 232448) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((args.M + 127) / 128), (unsigned)((args.N + NT - 1) / NT));
+    tc_gemm_kernel<NT><<<grid, 128, smem, st>>>(maps, args);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_launch(const TcMaps &maps, const TcArgs &args, int nt, cudaStream_t st)
+{
+    if (args.M == 0 || args.N == 0) return cudaSuccess;
+    switch (nt) {
+    case 64: return tc_launch_t<64>(maps, args, st);
+    case 112: return tc_launch_t<112>(maps, args, st);
+    case 128: return tc_launch_t<128>(maps, args, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+ssa_status set_error(ssa_status code, const char *text);
+
+}  // namespace ssa
+
+extern "C" ssa_status ssa_bf16_gemm(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K,
+                                    int32_t lda, int32_t ldb, const float *bias, float *D, int32_t ldd, int32_t *err_flag,
+                                    void *stream)
+{
+    using namespace ssa;
+    if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldd < N) return set_error(SSA_ERR_INVALID_ARG, "bad GEMM sizes");
+    if ((M > 0 && N > 0) && (!A || !B || !D || !err_flag)) return set_error(SSA_ERR_INVALID_ARG, "NULL GEMM operand");
+    if ((lda % 8) || (ldb % 8)) return set_error(SSA_ERR_INVALID_ARG, "lda and ldb must be multiples of 8 (16-byte rows)");
+    if (M == 0 || N == 0) return SSA_OK;
+    TcMaps maps;
+    memset(&maps, 0, sizeof(maps));
+    if (!tc_make_map(&maps.a[0], A, M, K, lda, 128) || !tc_make_map(&maps.b[0], B, N, K, ldb, 128))
+        return set_error(SSA_ERR_INVALID_ARG, "tensor map encoding failed (alignment or driver entry point)");
+    TcArgs args{M, N, K, 1, 1, 1, 0, bias, D, ldd, err_flag};
+    cudaError_t e = tc_gemm_launch(maps, args, 128, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SSA_OK : set_error(SSA_ERR_CUDA, cudaGetErrorString(e));
+}

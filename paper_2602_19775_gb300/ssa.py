@@ -240,6 +240,27 @@ def pipe_rates() -> dict:
     return out
 
 
+def bf16_gemm(A: torch.Tensor, B: torch.Tensor, bias: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """ssa_bf16_gemm: A [M, K] bf16, B [N, K] bf16 (K-major) -> A B^T (+ bias) in float32 on tcgen05."""
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16:
+        raise SSAError("bf16_gemm takes bfloat16 operands")
+    M, K = A.shape
+    N = B.shape[0]
+    ld = (K + 7) // 8 * 8
+    Ap = torch.zeros((M, ld), dtype=torch.bfloat16, device=A.device)
+    Bp = torch.zeros((N, ld), dtype=torch.bfloat16, device=A.device)
+    Ap[:, :K] = A
+    Bp[:, :K] = B
+    D = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    b = None if bias is None else bias.to(torch.float32).contiguous()
+    check(_lib.lib().ssa_bf16_gemm(_ptr(Ap), _ptr(Bp), M, N, K, ld, ld, _ptr(b), _ptr(D), N, _ptr(err),
+                                   _stream(stream)))
+    if int(err.item()) != 0:
+        raise SSAError("tensor-core GEMM timed out waiting for its copies")
+    return D
+
+
 class SSAFunction(torch.autograd.Function):
     """obs = SSA(theta) with the straight-through gradient of Eqs. 5 and 7 in backward."""
 
