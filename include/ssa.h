@@ -182,6 +182,53 @@ ssa_status ssa_run_brackets(const ssa_run *run, int32_t *brackets_out, void *str
 void ssa_destroy_run(ssa_run *run);
 
 /*
+ * Gene-regulatory-network classifier (Section 4.3, Figure 4A): n_in clamped input counts x (the
+ * pixels, round(255 p)), n_hid hidden and n_out output gene products starting from zero. Reaction
+ * j < n_dyn = n_hid + n_out produces dynamic species j, reaction n_dyn + s degrades species s:
+ *   production of hidden i: k_max sigma(E1_i), E1 = W1 x + b1   (one tensor-core contraction per image)
+ *   production of output o: k_max sigma(E2_o), E2 = W2 h + b2   (kept exactly in integer fixed point)
+ *   degradation of s:       exp(log_d_s) X_s
+ * Trajectory i belongs to image i / traj_per_img. Readout: HOLD of the n_out outputs.
+ * Limits: n_in <= 1040 (exact tensor-core accumulation of 6-bit limbs times 8-bit counts), counts
+ * x in [0, 256], 2 (n_hid + n_out) <= 65535.
+ */
+typedef struct ssa_grn ssa_grn;
+ssa_status ssa_grn_create(int32_t n_in, int32_t n_hid, int32_t n_out, float k_max, ssa_grn **out);
+void ssa_grn_destroy(ssa_grn *g);
+size_t ssa_grn_workspace_bytes(const ssa_grn *g, int64_t n_img, int64_t traj_per_img, int32_t n_samples,
+                               const ssa_fwd_opts *opts);
+/*
+ * ssa_grn_forward -- E1 for every image on the tcgen05 tensor cores, then the exact SSA with the
+ * Gumbel-max choice, one warp per trajectory.
+ *   W1 device bf16 [n_hid][n_in], b1 device float [n_hid], W2 device bf16 [n_out][n_hid],
+ *   b2 device float [n_out], log_d device float [n_hid + n_out]; x_img device int32 [n_img][n_in].
+ *   opts->readout must be SSA_READOUT_HOLD. obs_out device int32 [n_img * traj_per_img][S][n_out].
+ *   The weights, b2 and x_img must stay alive until the backward.
+ */
+ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, const float *b1, const uint16_t *W2,
+                           const float *b2, const float *log_d, int64_t n_img, int64_t traj_per_img,
+                           int64_t traj_offset, const int32_t *x_img, double t_end,
+                           const double *sample_times, int32_t n_samples, uint64_t seed,
+                           const ssa_fwd_opts *opts, void *workspace, size_t workspace_bytes,
+                           int32_t *obs_out, int32_t *draws_out, int32_t *status_out, void *stream,
+                           ssa_run **run_out);
+/*
+ * ssa_grn_backward -- the straight-through gradient (Eqs. 3, 5, 7) of a recorded GRN forward:
+ * dW1 [n_hid][n_in] (tensor cores), db1 [n_hid], dW2 [n_out][n_hid], db2 [n_out],
+ * dlog_d [n_hid + n_out], all device float, overwritten; dl_dobs as in ssa_backward.
+ */
+ssa_status ssa_grn_backward(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride,
+                            float temperature, float *dW1, float *db1, float *dW2, float *db2,
+                            float *dlog_d, void *stream);
+/*
+ * ssa_grn_activations -- test hook: E1 [n_img][n_hid] (device float) of a GRN run, and, if
+ * host_flags is given (synchronising), host_flags[0] = inexact-input bits (1: a W1 value below the
+ * 48-bit limb grid, 2: W2 outside the fixed-point range, 4: a count outside [0, 256]) and
+ * host_flags[1] = tensor-core timeout.
+ */
+ssa_status ssa_grn_activations(const ssa_run *run, float *E1_out, int32_t *host_flags, void *stream);
+
+/*
  * ssa_ensemble_mean -- the ensemble average that the paper's losses compare (Sections 3.5 and
  * 4.1: MSE between simulated and target ensemble-averaged trajectories): the mean over
  * trajectories of obs [n_traj][row_len] (device; int32 when obs_is_int, else float) into device

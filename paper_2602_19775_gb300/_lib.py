@@ -23,7 +23,8 @@ EXPORTS = (
     "ssa_create_network", "ssa_destroy_network", "ssa_forward_workspace_bytes", "ssa_forward",
     "ssa_forward_replay", "ssa_backward", "ssa_run_status", "ssa_run_events", "ssa_run_brackets", "ssa_destroy_run",
     "ssa_ensemble_mean_workspace_bytes", "ssa_ensemble_mean", "ssa_ensemble_mean_static", "ssa_philox_uniforms",
-    "ssa_bf16_gemm", "ssa_pipe_rates", "ssa_last_error",
+    "ssa_bf16_gemm", "ssa_pipe_rates", "ssa_last_error", "ssa_grn_create", "ssa_grn_destroy",
+    "ssa_grn_workspace_bytes", "ssa_grn_forward", "ssa_grn_backward", "ssa_grn_activations",
 )
 
 
@@ -71,6 +72,13 @@ def _declare(lib):
         "ssa_pipe_rates": (i32, [p, p, p]),
         "ssa_bf16_gemm": (i32, [p, p, i32, i32, i32, i32, i32, p, p, i32, p, p]),
         "ssa_last_error": (ctypes.c_char_p, []),
+        "ssa_grn_create": (i32, [i32, i32, i32, f32, ctypes.POINTER(p)]),
+        "ssa_grn_destroy": (None, [p]),
+        "ssa_grn_workspace_bytes": (sz, [p, i64, i64, i32, opts]),
+        "ssa_grn_forward": (i32, [p, p, p, p, p, p, i64, i64, i64, p, f64, p, i32, u64, opts, p, sz, p, p, p, p,
+                                  ctypes.POINTER(p)]),
+        "ssa_grn_backward": (i32, [p, p, i64, f32, p, p, p, p, p, p]),
+        "ssa_grn_activations": (i32, [p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -9,7 +9,7 @@
 #include <new>
 #include <vector>
 
-#include "ssa_internal.cuh"
+#include "ssa_host.h"
 
 namespace ssa {
 cudaError_t launch_forward_thread(const FwdParams &p, int readout, bool record, bool replay, int block, size_t smem,
@@ -67,30 +67,14 @@ ssa_status set_error(ssa_status code, const char *text) { return fail(code, "%s"
 // ---------------------------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------------------------
-struct ssa_network {
-    int32_t N, M, Mp, P, nnz, nnz_pad;  // Mp = 4 * ceil((M + 1)/4): padded reaction count
-    // d_blob = [rx: int4 Mp][stoich: int nnz_pad][inc_ptr: int N+1, padded][inc_list: int 2M, padded]
-    //          [rate_index: int Mp]; the first four parts are the tables staged into shared memory
-    void *d_blob;
-    uint32_t inc_off, inc_list_off;
-    int4 *d_rx;
-    int *d_stoich;
-    int *d_rate_index;
-    uint32_t tab_bytes;
-};
+
 
 namespace {
 constexpr size_t kAlign = 256;
 constexpr int kWarpsPerBlock = 4;  // warp-per-trajectory kernels
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-struct WsLayout {
-    size_t flag, counts, k_rates, ts, obs_sp, draws, status;
-    size_t xfinal, ev, ckpt, brk_k, brk_a, partial, dA;
-    size_t total;
-    int64_t ev_rows, n_ckpt, max_blocks;
-    int M_pad;
-};
+
 
 int effective_K(const ssa_fwd_opts *o) { return o->ckpt_interval > 0 ? o->ckpt_interval : 64; }
 
@@ -182,17 +166,7 @@ int pick_block(size_t (*need)(const ssa_network *, int), const ssa_network *net,
 }
 }  // namespace
 
-struct ssa_run {
-    const ssa_network *net;
-    int variant;  // 1: thread per trajectory, 32: warp per trajectory
-    int64_t n_traj;
-    uint64_t traj_offset, seed;
-    int32_t S, n_obs;
-    ssa_fwd_opts opts;
-    double t_end;
-    unsigned char *ws;
-    WsLayout L;
-};
+
 
 extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions, const int32_t *reactants,
                                          const int32_t *stoich_ptr, const int32_t *stoich_species,
@@ -442,6 +416,7 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     if (run && dl_traj_stride != 0 && dl_traj_stride < (int64_t)run->S * run->n_obs)
         return fail(SSA_ERR_INVALID_ARG, "dl_traj_stride must be 0 or >= n_samples * n_obs");
     if (!run) return fail(SSA_ERR_INVALID_ARG, "run is NULL");
+    if (!run->net) return fail(SSA_ERR_STATE, "a gene-regulatory-network run is differentiated by ssa_grn_backward");
     if (!run->opts.record) return fail(SSA_ERR_STATE, "the forward was not recorded (opts.record = 0)");
     if (!(temperature > 0.0f) || !(temperature < 3.0e38f)) return fail(SSA_ERR_INVALID_ARG, "temperature must be > 0");
     if (!dl_dlog_rates) return fail(SSA_ERR_INVALID_ARG, "dl_dlog_rates is NULL");

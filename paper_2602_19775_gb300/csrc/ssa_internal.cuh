@@ -166,6 +166,40 @@ struct FwdParamsView {
     uint32_t c2, c3, key0, key1;
 };
 
+// Warp reductions shared by the warp-per-trajectory kernels (butterfly: every lane gets the same
+// bits; the race keeps the lowest j on equal products).
+__device__ __forceinline__ void warp_race_combine(float &ab, float &Eb, int &jb)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ao = __shfl_xor_sync(0xffffffffu, ab, off);
+        const float Eo = __shfl_xor_sync(0xffffffffu, Eb, off);
+        const int jo = __shfl_xor_sync(0xffffffffu, jb, off);
+        if (jo >= 0) {
+            const float lhs = __fmul_rn(ao, Eb), rhs = __fmul_rn(ab, Eo);
+            if (jb < 0 || lhs > rhs || (lhs == rhs && jo < jb)) {
+                ab = ao;
+                Eb = Eo;
+                jb = jo;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
 // ------------------------------------------------------------------------------------------
 // Shared-memory staging of the network tables and the per-call rate constants with the bulk
 // (non-tensor) TMA copy engine: cp.async.bulk global -> shared, completion on an mbarrier.

@@ -22,27 +22,9 @@
 
 #include <cuda.h>
 
-#include "ssa_internal.cuh"
+#include "ssa_tc.cuh"
 
 namespace ssa {
-
-constexpr int kTcMaxA = 2;
-constexpr int kTcMaxB = 8;
-
-struct TcMaps {
-    CUtensorMap a[kTcMaxA];
-    CUtensorMap b[kTcMaxB];
-};
-
-struct TcArgs {
-    int M, N, K;
-    int n_a, n_b, n_terms;  // term t multiplies A[min(t, n_a - 1)] by B[min(t, n_b - 1)]
-    int separate;           // 1: one TMEM accumulator per term, summed in binary64
-    const float *bias;      // [N] or nullptr
-    float *D;               // [M][ldd]
-    int ldd;
-    int *err;
-};
 
 namespace {
 

@@ -23,38 +23,6 @@ namespace ssa {
 
 namespace {
 
-__device__ __forceinline__ void warp_race_combine(float &ab, float &Eb, int &jb)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float ao = __shfl_xor_sync(0xffffffffu, ab, off);
-        const float Eo = __shfl_xor_sync(0xffffffffu, Eb, off);
-        const int jo = __shfl_xor_sync(0xffffffffu, jb, off);
-        if (jo >= 0) {
-            const float lhs = __fmul_rn(ao, Eb), rhs = __fmul_rn(ab, Eo);
-            if (jb < 0 || lhs > rhs || (lhs == rhs && jo < jb)) {
-                ab = ao;
-                Eb = Eo;
-                jb = jo;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, off));
-    return v;
-}
-
-__device__ __forceinline__ float warp_max(float v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
-    return v;
-}
-
 // One step's propensities, a0 and race over this lane's Philox blocks. Returns E_0 on lane 0.
 // If aj / lj are given, stores a_j and log2(a_j / E_j) (or -inf) for this lane's reactions.
 template <bool STORE>

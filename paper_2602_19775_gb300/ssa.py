@@ -261,6 +261,99 @@ def bf16_gemm(A: torch.Tensor, B: torch.Tensor, bias: torch.Tensor | None = None
     return D
 
 
+def _bf16_bits(w) -> torch.Tensor:
+    """bf16 bit patterns (as int16 storage) of a float tensor/array, rounded to nearest even."""
+    t = torch.as_tensor(np.asarray(w, dtype=np.float32)) if not isinstance(w, torch.Tensor) else w.float()
+    return t.to(torch.bfloat16).contiguous()
+
+
+class GRN:
+    """The gene-regulatory-network classifier held by the library (ssa_grn_create)."""
+
+    def __init__(self, n_in: int, n_hid: int, n_out: int, k_max: float = 1.0):
+        h = ctypes.c_void_p()
+        check(_lib.lib().ssa_grn_create(n_in, n_hid, n_out, ctypes.c_float(k_max), ctypes.byref(h)))
+        self.handle, self.n_in, self.n_hid, self.n_out, self.k_max = h, n_in, n_hid, n_out, k_max
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.lib().ssa_grn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class GRNForward:
+    obs: torch.Tensor       # [n_traj, S, n_out] int32
+    draws: torch.Tensor
+    status: torch.Tensor
+    run: Run
+
+
+def grn_forward(grn: GRN, W1, b1, W2, b2, log_d, x_img, traj_per_img: int, t_end: float, sample_times, seed: int,
+                record=True, ckpt_interval=64, max_steps=1 << 16, traj_offset=0, stream=None,
+                device="cuda") -> GRNForward:
+    """ssa_grn_forward. W1 [n_hid, n_in] and W2 [n_out, n_hid] are rounded to bf16; x_img int counts."""
+    dev = torch.device(device)
+    W1b = _bf16_bits(W1).to(dev)
+    W2b = _bf16_bits(W2).to(dev)
+    b1t, b2t, ldt = (_as_cuda(v, torch.float32, dev) for v in (b1, b2, log_d))
+    x = _as_cuda(x_img, torch.int32, dev)
+    ts = _as_cuda(sample_times, torch.float64, dev)
+    n_img = int(x.shape[0])
+    n = n_img * int(traj_per_img)
+    S = int(ts.numel())
+    opts = make_opts("hold", record, ckpt_interval, max_steps)
+    L = _lib.lib()
+    need = int(L.ssa_grn_workspace_bytes(grn.handle, n_img, traj_per_img, S, ctypes.byref(opts)))
+    if need == 0:
+        raise SSAError("invalid arguments for ssa_grn_workspace_bytes")
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    obs = torch.empty((n, S, grn.n_out), dtype=torch.int32, device=dev)
+    draws = torch.empty(n, dtype=torch.int32, device=dev)
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    h = ctypes.c_void_p()
+    check(L.ssa_grn_forward(grn.handle, _ptr(W1b), _ptr(b1t), _ptr(W2b), _ptr(b2t), _ptr(ldt), n_img,
+                            int(traj_per_img), int(traj_offset), _ptr(x), float(t_end), _ptr(ts), S,
+                            ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(opts), _ptr(ws), need, _ptr(obs),
+                            _ptr(draws), _ptr(status), _stream(stream), ctypes.byref(h)))
+    run = Run(h, ws, grn, n, S, grn.n_out, 0)
+    run._keep = (W1b, W2b, b1t, b2t, ldt, x, ts)
+    return GRNForward(obs, draws, status, run)
+
+
+def grn_backward(fwd: GRNForward, dl_dobs: torch.Tensor, temperature: float, stream=None) -> dict:
+    """ssa_grn_backward: gradients of W1, b1, W2, b2 and log_d (float32)."""
+    run = fwd.run
+    g = dl_dobs.to(torch.float32).contiguous()
+    stride = run.S * run.n_obs if tuple(g.shape) == (run.n_traj, run.S, run.n_obs) else 0
+    if stride == 0 and tuple(g.shape) != (run.S, run.n_obs):
+        raise SSAError("dl_dobs has the wrong shape")
+    net = run.net
+    dev = g.device
+    out = {"W1": torch.empty((net.n_hid, net.n_in), device=dev), "b1": torch.empty(net.n_hid, device=dev),
+           "W2": torch.empty((net.n_out, net.n_hid), device=dev), "b2": torch.empty(net.n_out, device=dev),
+           "log_d": torch.empty(net.n_hid + net.n_out, device=dev)}
+    check(_lib.lib().ssa_grn_backward(run.handle, _ptr(g), stride, ctypes.c_float(float(temperature)),
+                                      _ptr(out["W1"]), _ptr(out["b1"]), _ptr(out["W2"]), _ptr(out["b2"]),
+                                      _ptr(out["log_d"]), _stream(stream)))
+    return out
+
+
+def grn_activations(fwd: GRNForward, n_img: int, stream=None):
+    """E1 [n_img, n_hid] computed on the tensor cores, and the (inexact-input, timeout) flags."""
+    run = fwd.run
+    E1 = torch.empty((n_img, run.net.n_hid), dtype=torch.float32, device=run.workspace.device)
+    flags = (ctypes.c_int32 * 2)()
+    check(_lib.lib().ssa_grn_activations(run.handle, _ptr(E1), flags, _stream(stream)))
+    return E1, (int(flags[0]), int(flags[1]))
+
+
 class SSAFunction(torch.autograd.Function):
     """obs = SSA(theta) with the straight-through gradient of Eqs. 5 and 7 in backward."""
 

@@ -1,0 +1,81 @@
+"""GPU parity of the gene-regulatory-network classifier (Section 4.3) against the FP64 oracle:
+the tensor-core activation energies E1 = W1 x + b1 (exact up to one rounding), the event
+sequences (margin rule), the HOLD observables, and every gradient group on the trajectories whose
+events agree."""
+import numpy as np
+import pytest
+import torch
+
+from ssa_workloads import grn as G
+from oracle import native
+
+from test_gpu_parity import GRAD_RTOL, MARGIN_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2602_19775_gb300 import ssa
+    ssa._lib.lib()
+    return ssa
+
+
+def test_activation_energies_are_exact_on_tensor_cores(S):
+    p = G.grn_params(seed=5)
+    p.b1[:] = np.random.default_rng(1).normal(0, 0.5, p.n_hid).astype(np.float32)
+    x, _ = G.prototype_images(seed=5, n_img=512)
+    net = S.GRN(p.n_in, p.n_hid, p.n_out, p.k_max)
+    fw = S.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, 1, 0.0, [0.0], 3, record=False)
+    E1, flags = S.grn_activations(fw, 512)
+    assert flags == (0, 0), flags
+    # W1 x is exact in binary64 (bf16 weights times 8-bit counts on one grid); one rounding of (W1 x + b1)
+    exact = x.astype(np.float64) @ p.W1.astype(np.float64).T + p.b1.astype(np.float64)
+    np.testing.assert_array_equal(E1.cpu().numpy(), exact.astype(np.float32))
+
+
+def _grn_case(S, p, x, tpi, t_end, seed, T, max_steps=1 << 15):
+    n = x.shape[0] * tpi
+    ts = np.array([t_end])
+    dl = np.random.default_rng(seed + 1).standard_normal((n, 1, p.n_out)) / n
+    net = S.GRN(p.n_in, p.n_hid, p.n_out, p.k_max)
+    fw = S.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, tpi, t_end, ts, seed, max_steps=max_steps)
+    orc = native.grn_run(p, x, tpi, t_end, ts, seed, max_steps=max_steps, dl_dobs=dl, temperature=T, ev_cap=max_steps)
+    assert np.all(fw.status.cpu().numpy() == orc.status)
+    ev = fw.run.events(max_steps).cpu().numpy()
+    same = np.all(ev == orc.events, axis=1)
+    for i in np.nonzero(~same)[0]:
+        k = int(np.nonzero(ev[i] != orc.events[i])[0][0])
+        assert orc.margins[i, k] < MARGIN_TOL, (i, k, orc.margins[i, k])
+    assert same.mean() >= 0.95, same.mean()
+    obs = fw.obs.double().cpu().numpy()
+    np.testing.assert_array_equal(obs[same], orc.obs[same])
+    dl_g = dl.copy()
+    dl_g[~same] = 0
+    g = S.grn_backward(fw, torch.tensor(dl_g, dtype=torch.float32, device="cuda"), T)
+    keep = np.repeat(same, 1)
+    masked = native.GRNResult(orc.obs, orc.draws, orc.status, orc.dE1 * keep[:, None], orc.dW2 * keep[:, None, None],
+                              orc.db2 * keep[:, None], orc.dlogd * keep[:, None], None, None)
+    ref = masked.grads(x, tpi)
+    _, mism = fw.run.status_counts()
+    assert mism == 0
+    errs = {}
+    for k in ref:
+        gk = g[k].double().cpu().numpy()
+        errs[k] = np.linalg.norm(gk - ref[k]) / max(np.linalg.norm(ref[k]), 1e-300)
+    assert all(e < GRAD_RTOL for e in errs.values()), errs
+    return errs, same.mean()
+
+
+def test_tiny_grn_matches_oracle(S):
+    p = G.grn_params(seed=1, n_in=5, n_hid=4, n_out=3, w1_scale=0.02, w2_scale=0.5)
+    p.b1[:] = [0.3, -0.5, 1.0, 0.0]
+    p.b2[:] = [0.2, -0.1, 0.4]
+    x = np.array([[10, 200, 3, 0, 77], [5, 5, 5, 250, 1], [0, 0, 0, 0, 0]], np.int32)
+    _grn_case(S, p, x, 256, 6.0, 7, 0.6)
+
+
+def test_mnist_sized_grn_matches_oracle(S):
+    p = G.grn_params(seed=5)
+    x, _ = G.prototype_images(seed=5, n_img=4)
+    _grn_case(S, p, x, 8, 4.0, 9, 1.0)
