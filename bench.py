@@ -346,6 +346,7 @@ def run_ours(args):
 
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
+    osc = oscillator_extra(ssa, dev) if (rank == 0 and not args.no_extra) else None
     M = wl.net.n_reactions
     rates = ssa.pipe_rates()
     logf_slots = 128.0 / rates["logf"]
@@ -385,6 +386,8 @@ def run_ours(args):
                      "forward_frac": ach_f / peak,
                      "peak_basis": f"{rates['sm_count']} SM x 4 x 32 lanes x {sm_mhz:.0f} MHz (sampled median)",
                      "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in rates.items()}},
+        "oscillator": osc,
+        "paper_context": "1.9e9 SSA steps/s forward on the oscillator, RTX 6000 Ada + TF 2.20 (a different machine)",
         "cpu_baseline": cpu_base,
         "e2e": {"value": e2e_value, "unit": "SSA steps/s (fwd+adj)", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -396,6 +399,42 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def oscillator_extra(ssa, dev, n_fwd: int = 1 << 20, n_adj: int = 1 << 16, t_end: float = 10.0, reps: int = 2):
+    """Forward-only and forward+adjoint SSA steps/s on the activator-repressor oscillator (the workload of the
+    paper's throughput figure), 10 LINEAR samples of R, horizon t_end (truncated from 400 to bound the event
+    log), timed with CUDA events after one warm-up launch."""
+    import torch
+
+    import ssa_workloads as W
+    wl = W.config_c3(n_traj=n_fwd, t_end=t_end, S=10)
+    net = ssa.Network(wl.net)
+    th = torch.tensor(wl.log_rates.astype(np.float32), device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"Vilar oscillator, 9 species, 16 reactions, t_end={t_end}, 10 LINEAR samples of R"}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for mode, n in (("forward", n_fwd), ("forward_adjoint", n_adj)):
+        rec = mode != "forward"
+        ms, steps = 0.0, 0
+        for r in range(reps + 1):
+            if r == 1:
+                torch.cuda.synchronize()
+            if r >= 1:
+                ev[0].record(stream)
+            fw = ssa.forward(net, th, n, wl.x0, t_end, wl.sample_times, wl.obs_species, 50 + r, readout="linear",
+                             record=rec, max_steps=1 << 16)
+            if rec:
+                dl = torch.full((len(wl.sample_times), 1), 1.0 / n, device=dev)
+                ssa.backward(fw, dl, 0.1)
+            if r >= 1:
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                ms += ev[0].elapsed_time(ev[1])
+                steps += int(fw.draws.sum().item())
+            del fw
+        out[mode] = {"n_traj": n, "steps": steps // reps, "ms": ms / reps, "steps_per_s": steps / (ms / 1e3)}
+    return out
 
 
 def grad_error_subset(ssa, net, wl, dev, n=2048):
@@ -434,6 +473,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-chunk", type=int, default=4096)
     ap.add_argument("--no-oracle", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the oscillator throughput fields")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
