@@ -5,6 +5,7 @@
 // the small run handle that lets ssa_backward revisit a recorded forward.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -33,6 +34,7 @@ cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, co
 cudaError_t launch_forward_warp(const FwdParams &p, int readout, bool record, int warps, size_t smem, cudaStream_t st);
 cudaError_t launch_backward_warp(const AdjParams &p, int readout, int warps, size_t smem, int64_t grid,
                                  cudaStream_t st);
+int thread_kernel_mc(int M);
 }  // namespace ssa
 
 using namespace ssa;
@@ -185,7 +187,10 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
         if (stoich_ptr[j + 1] < stoich_ptr[j]) return fail(SSA_ERR_INVALID_ARG, "stoich_ptr not monotone at %d", j);
     const int nnz = stoich_ptr[n_reactions];
     if (nnz > 0 && (!stoich_species || !stoich_delta)) return fail(SSA_ERR_INVALID_ARG, "NULL stoichiometry");
-    const int Mp = (n_reactions + 4) / 4 * 4;
+    // at least M + 1 rounded up to 4, and at least the unrolled reaction count of the
+    // thread-per-trajectory kernels (2, 4, 8 or 16 for M <= 16), which read every padded entry
+    int Mp = (n_reactions + 4) / 4 * 4;
+    if (n_reactions <= 16) Mp = std::max(Mp, thread_kernel_mc(n_reactions));
     std::vector<int4> rx(Mp, make_int4(-1, -1, 0, 0));  // padding: order 0, no change, rate 0
     for (int j = 0; j < n_reactions; ++j) {
         int r1 = reactants[2 * j], r2 = reactants[2 * j + 1];

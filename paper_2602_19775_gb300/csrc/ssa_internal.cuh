@@ -290,7 +290,7 @@ struct FwdParams {
     const int4 *rx;
     const float *k_rates;  // [M padded to 4]
     uint32_t tab_bytes, k_bytes;
-    int N, M, Mp, nnz;  // Mp: reaction tables padded to 4 * ceil((M + 1)/4) entries
+    int N, M, Mp, nnz;  // Mp: padded reaction count, >= M + 1, multiple of 4, >= the unrolled width
     uint32_t inc_off, inc_list_off;  // byte offsets of the species -> reactant-slot incidence in the tables
     int64_t n_traj;
     uint64_t traj_offset, seed;
@@ -323,7 +323,7 @@ struct AdjParams {
     const int4 *rx;
     const float *k_rates;
     uint32_t tab_bytes, k_bytes;
-    int N, M, Mp, nnz;  // Mp: reaction tables padded to 4 * ceil((M + 1)/4) entries
+    int N, M, Mp, nnz;  // Mp: padded reaction count, >= M + 1, multiple of 4, >= the unrolled width
     uint32_t inc_off, inc_list_off;  // byte offsets of the species -> reactant-slot incidence in the tables
     int64_t n_traj;
     uint64_t traj_offset, seed;

@@ -117,3 +117,12 @@ def test_thread_and_warp_variants_agree_with_each_other(S):
     ea, eb = a.run.events(4096).cpu().numpy(), b.run.events(4096).cpu().numpy()
     # the two variants sum a0 and reduce the race in different orders: they may part only at near-ties
     assert np.mean(np.all(ea == eb, axis=1)) > 0.99
+
+
+@pytest.mark.parametrize("M", [9, 10, 11])
+def test_thread_kernel_with_nine_to_eleven_reactions(S, M):
+    # the unrolled thread kernels evaluate 16 reactions here: the padded entries must be inert
+    net = W.random_network(np.random.default_rng(100 + M), n_species_range=(3, 8), n_reactions_range=(M, M))
+    theta = net.log_rates.astype(np.float32).astype(np.float64)
+    t_end = _pilot_t_end(net, theta)
+    _parity(S, net, net.log_rates, 512, t_end, 8, np.array([0, 1], np.int32), M, LINEAR, 0.5, tpt=1)
