@@ -288,6 +288,107 @@ ssa_status ssa_bf16_gemm(const uint16_t *A, const uint16_t *B, int32_t M, int32_
  */
 ssa_status ssa_pipe_rates(double *host_rates, double *host_sm_clock_mhz, int32_t *host_sm_count);
 
+/*
+ * Batch of networks -- many reaction networks of different sizes, each with its own parameters,
+ * initial state, sample grid, observables and trajectory count, simulated and differentiated
+ * together: one persistent forward launch and one persistent adjoint launch for the whole batch
+ * (Sections 2-3: each network runs exactly the computation of ssa_forward(record) followed by
+ * ssa_backward). No counterpart in the paper, which trains one network at a time; it exists for
+ * workloads of many small networks that would each underfill the GPU.
+ *
+ * ssa_batch_item fields (all device pointers stay owned by the caller and must outlive the batch):
+ *   net              network handle from ssa_create_network.
+ *   log_rates        device float [net P]: theta, k_j = exp(theta[rate_index[j]]).
+ *   x0               device int32 [net N], shared by the item's trajectories.
+ *   n_traj >= 0, seed, traj_offset >= 0: trajectory i of the item draws the Philox stream of global
+ *                    trajectory traj_offset + i under seed, as in ssa_forward.
+ *   t_end, sample_times device double [n_samples], obs_species device int32 [n_obs] (n_obs <= 64),
+ *   max_steps, ckpt_interval (0: choose; else a multiple of 8), threads_per_traj (0: choose, 1, 32;
+ *                    1 needs N <= 16 and M <= 16): as ssa_fwd_opts.
+ *   obs_out          device [n_traj][n_samples][n_obs], int32 (HOLD) or float (LINEAR).
+ *   dl_dobs, dl_traj_stride: upstream gradient as in ssa_backward.
+ *   dl_dlog_rates    device float [net P], overwritten with the item's dL/dtheta.
+ */
+typedef struct ssa_batch ssa_batch;
+
+typedef struct ssa_batch_item {
+    const ssa_network *net;
+    const float *log_rates;
+    const int32_t *x0;
+    int64_t n_traj;
+    uint64_t seed;
+    int64_t traj_offset;
+    double t_end;
+    const double *sample_times;
+    int32_t n_samples;
+    int32_t n_obs;
+    const int32_t *obs_species;
+    int64_t max_steps;
+    int32_t ckpt_interval;
+    int32_t threads_per_traj;
+    void *obs_out;
+    const float *dl_dobs;
+    int64_t dl_traj_stride;
+    float *dl_dlog_rates;
+} ssa_batch_item;
+
+/*
+ * ssa_batch_create -- validate and copy the item descriptors (host array [n_items]); readout and
+ * temperature T > 0 apply to every item. Allocates host memory only. Errors: SSA_ERR_INVALID_ARG,
+ * SSA_ERR_UNSUPPORTED (thread variant requested for a network with N > 16 or M > 16).
+ */
+ssa_status ssa_batch_create(const ssa_batch_item *items, int32_t n_items, int32_t readout,
+                            float temperature, ssa_batch **out);
+void ssa_batch_destroy(ssa_batch *batch);
+
+/*
+ * ssa_batch_set_plan -- override the variant (1 or 32), the checkpoint interval (multiple of 8) and
+ * the expected draws per trajectory (> 0; used to order work longest first; <= 0 keeps the current
+ * estimate) of one item. Invalidates the captured graph and the workspace layout.
+ */
+ssa_status ssa_batch_set_plan(ssa_batch *batch, int32_t item, int32_t threads_per_traj,
+                              int32_t ckpt_interval, double est_draws);
+
+/* ssa_batch_workspace_bytes -- device workspace ssa_batch_run needs under the current plan. */
+size_t ssa_batch_workspace_bytes(const ssa_batch *batch);
+
+/*
+ * ssa_batch_run -- rates, input checks, persistent forward, persistent adjoint, fixed-order
+ * reduction of every item's partial sums and the map to dl_dlog_rates, enqueued on `stream`.
+ * workspace: device, 256-byte aligned, >= ssa_batch_workspace_bytes; the first call with a given
+ * workspace lays it out (copies the descriptors, synchronises the stream); later calls with the
+ * same workspace only launch. use_graph != 0 captures the launch sequence into a CUDA graph on the
+ * first call (stream must not be the legacy default stream) and replays it afterwards; the device
+ * pointers named in the items are baked in, so their contents may change between calls but not
+ * their addresses. Calls on one batch must not overlap. Results are identical with and without the
+ * graph and do not depend on the order in which the GPU runs the work units.
+ */
+ssa_status ssa_batch_run(ssa_batch *batch, void *workspace, size_t workspace_bytes, int32_t use_graph,
+                         void *stream);
+
+/*
+ * ssa_batch_item_outputs -- after ssa_batch_run: copy one item's draws and trajectory status codes
+ * (device int32 [n_traj] each, either may be NULL) and, if host_bwd_mismatch is not NULL,
+ * synchronise and return the item's count of adjoint replay disagreements (0 on a sound run).
+ */
+ssa_status ssa_batch_item_outputs(const ssa_batch *batch, int32_t item, int32_t *draws_out,
+                                  int32_t *status_out, int64_t *host_bwd_mismatch, void *stream);
+
+/*
+ * ssa_batch_autotune -- pilot-based plan (no counterpart in the paper). For each item, runs
+ * min(pilot_traj, n_traj) trajectories through ssa_forward(record) + ssa_backward under each
+ * variant the item allows (threads_per_traj = 0: thread if N, M <= 16, and warp), keeps the faster,
+ * and sets the item's cost estimate to the pilot's mean draws (host_draws_out [n_items] receives
+ * them, may be NULL). Allocates and frees pilot buffers with cudaMalloc, synchronises `stream`,
+ * writes nothing the caller owns. Invalidates the captured graph and the workspace layout; the
+ * workspace size may change (more units for the warp variant).
+ */
+ssa_status ssa_batch_autotune(ssa_batch *batch, int64_t pilot_traj, void *stream,
+                              double *host_draws_out);
+
+/* ssa_batch_item_variant -- the item's planned variant: 1 (thread) or 32 (warp); 0 if invalid. */
+int32_t ssa_batch_item_variant(const ssa_batch *batch, int32_t item);
+
 const char *ssa_last_error(void);
 
 #ifdef __cplusplus

@@ -10,7 +10,7 @@ from ._lib import SSAError, EXPORTS  # noqa: F401
 
 def __getattr__(name):
     if name in ("Network", "forward", "backward", "simulate", "ensemble_mean", "philox_uniforms", "SSAFunction",
-                "ForwardResult", "Run", "make_opts", "workspace_bytes"):
+                "ForwardResult", "Run", "make_opts", "workspace_bytes", "Batch"):
         from . import ssa
         return getattr(ssa, name)
     raise AttributeError(name)

@@ -25,6 +25,8 @@ EXPORTS = (
     "ssa_ensemble_mean_workspace_bytes", "ssa_ensemble_mean", "ssa_ensemble_mean_static", "ssa_philox_uniforms",
     "ssa_bf16_gemm", "ssa_pipe_rates", "ssa_last_error", "ssa_grn_create", "ssa_grn_destroy",
     "ssa_grn_workspace_bytes", "ssa_grn_forward", "ssa_grn_backward", "ssa_grn_activations",
+    "ssa_batch_create", "ssa_batch_destroy", "ssa_batch_set_plan", "ssa_batch_workspace_bytes", "ssa_batch_run",
+    "ssa_batch_item_outputs", "ssa_batch_autotune", "ssa_batch_item_variant",
 )
 
 
@@ -41,6 +43,29 @@ class FwdOpts(ctypes.Structure):
         ("max_steps", ctypes.c_int64),
         ("block_threads", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+    ]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [
+        ("net", ctypes.c_void_p),
+        ("log_rates", ctypes.c_void_p),
+        ("x0", ctypes.c_void_p),
+        ("n_traj", ctypes.c_int64),
+        ("seed", ctypes.c_uint64),
+        ("traj_offset", ctypes.c_int64),
+        ("t_end", ctypes.c_double),
+        ("sample_times", ctypes.c_void_p),
+        ("n_samples", ctypes.c_int32),
+        ("n_obs", ctypes.c_int32),
+        ("obs_species", ctypes.c_void_p),
+        ("max_steps", ctypes.c_int64),
+        ("ckpt_interval", ctypes.c_int32),
+        ("threads_per_traj", ctypes.c_int32),
+        ("obs_out", ctypes.c_void_p),
+        ("dl_dobs", ctypes.c_void_p),
+        ("dl_traj_stride", ctypes.c_int64),
+        ("dl_dlog_rates", ctypes.c_void_p),
     ]
 
 
@@ -79,6 +104,14 @@ def _declare(lib):
                                   ctypes.POINTER(p)]),
         "ssa_grn_backward": (i32, [p, p, i64, f32, p, p, p, p, p, p]),
         "ssa_grn_activations": (i32, [p, p, p, p]),
+        "ssa_batch_create": (i32, [ctypes.POINTER(BatchItem), i32, i32, f32, ctypes.POINTER(p)]),
+        "ssa_batch_destroy": (None, [p]),
+        "ssa_batch_set_plan": (i32, [p, i32, i32, i32, f64]),
+        "ssa_batch_workspace_bytes": (sz, [p]),
+        "ssa_batch_run": (i32, [p, p, sz, i32, p]),
+        "ssa_batch_item_outputs": (i32, [p, i32, p, p, p, p]),
+        "ssa_batch_autotune": (i32, [p, i64, p, p]),
+        "ssa_batch_item_variant": (i32, [p, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

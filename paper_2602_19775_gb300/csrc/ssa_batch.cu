@@ -1,0 +1,748 @@
+// ssa_batch.cu -- many networks of uneven size, parameter sets and trajectory counts in one
+// persistent launch per direction (forward, then the straight-through adjoint), captured with the
+// rate, validation and reduction kernels in one CUDA graph (arXiv 2602.19775, Sections 2-3: every
+// network runs the same exact SSA and the same adjoint as the single-network entry points).
+//
+// Work is cut into units: 32 trajectories of one network for the thread-per-trajectory variant (one
+// per lane), or a few trajectories run one after another by a whole warp for the warp-per-trajectory
+// variant. The host orders the units longest first (estimated draws x reactions x trajectories, from
+// the autotuner's pilot runs) and every warp of a persistent grid (one wave: SMs x resident blocks)
+// pulls the next unit from an atomic counter. The per-trajectory code is the same as the
+// single-network kernels', with the network tables read from global memory through the read-only
+// path. Each unit writes its per-reaction adjoints to its own slot, and the slots of a network are
+// summed in a fixed order, so gradients do not depend on which warp ran which unit.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ssa_fwd_body.cuh"
+#include "ssa_host.h"
+#include "ssa_warp_body.cuh"
+
+#define CUDA_TRY_B(expr)                                                                                \
+    do {                                                                                                \
+        cudaError_t e_ = (expr);                                                                        \
+        if (e_ != cudaSuccess) return set_error(SSA_ERR_CUDA, cudaGetErrorString(e_));                 \
+    } while (0)
+
+namespace ssa {
+
+struct BatchItem {
+    FwdParams f;
+    AdjParams a;
+    int variant;             // 1: thread per trajectory (compile-time bound mc), 32: warp per trajectory
+    int mc;
+    int64_t slot_off;        // first float of this network's partial slots
+    int n_units;
+    const float *log_rates;  // caller's theta
+    const int *rate_index;
+    int P;
+    float *dtheta;           // caller's dL/dlog k
+    float *dA;               // per-reaction sums (workspace)
+};
+
+struct BatchUnit {
+    int item;
+    int count;           // trajectories in the unit
+    int64_t traj_begin;  // local trajectory index within the network
+    int slot;            // canonical index of the unit within its network
+};
+
+constexpr int kBatchWarps = 4;
+constexpr int kBatchThreadMaxN = 16;  // thread variant inside a batch: N <= 16 and M <= 16
+constexpr int kBatchWarpUnit = 4;     // trajectories per warp-variant unit
+
+__global__ void batch_prepare_kernel(const BatchItem *items, int n_items)
+{
+    // per network: k_j = exp(theta_{r(j)}) rounded once, and the check of its sample grid
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem &b = items[it];
+        float *k = const_cast<float *>(b.f.k_rates);
+        for (int j = threadIdx.x; j < b.f.Mp; j += blockDim.x)
+            k[j] = j < b.f.M ? (float)exp((double)b.log_rates[b.rate_index[j]]) : 0.0f;
+        int *flag = const_cast<int *>(b.f.flag);
+        for (int s = threadIdx.x; s < b.f.S; s += blockDim.x) {
+            const bool ok = b.f.ts[s] >= 0.0 && b.f.ts[s] <= b.f.t_end && (s == 0 || b.f.ts[s] >= b.f.ts[s - 1]);
+            if (!ok) atomicOr(flag, kErrBadSamples);
+        }
+        for (int c = threadIdx.x; c < b.f.n_obs; c += blockDim.x)
+            if (b.f.obs_sp[c] < 0 || b.f.obs_sp[c] >= b.f.N) atomicOr(flag, kErrBadObs);
+    }
+}
+
+// the descriptor of the warp's current network is copied to shared memory, where the per-step
+// reads of its sizes and pointers cost a shared load instead of a global one
+constexpr int kItemWords = (int)((sizeof(BatchItem) + 15) / 16 * 4);
+
+__device__ __forceinline__ int load_item(const BatchItem *items, int item, BatchItem *dst)
+{
+    __syncwarp();
+    const int *src = reinterpret_cast<const int *>(items + item);
+    int *d = reinterpret_cast<int *>(dst);
+    for (int w = threadIdx.x & 31; w < (int)(sizeof(BatchItem) / 4); w += 32) d[w] = src[w];
+    __syncwarp();
+    return item;
+}
+
+__device__ __forceinline__ int next_unit(int *counter)
+{
+    int u = 0;
+    if ((threadIdx.x & 31) == 0) u = atomicAdd(counter, 1);
+    return __shfl_sync(0xffffffffu, u, 0);
+}
+
+template <int READOUT, int MC>
+__device__ __forceinline__ void batch_fwd_thread_unit(const BatchItem &b, const BatchUnit &u, int *Xw)
+{
+    const FwdParams &p = b.f;
+    const int lane = threadIdx.x & 31;
+    const int4 *rx = p.rx;
+    const int *st = reinterpret_cast<const int *>(reinterpret_cast<const unsigned char *>(p.rx) + 16 * p.Mp);
+    if (lane < u.count) thread_fwd_body<READOUT, true, false, MC>(p, rx, st, p.k_rates, Xw + lane, 32, u.traj_begin + lane);
+}
+
+template <int READOUT>
+__global__ void __launch_bounds__(32 * kBatchWarps) batch_fwd_kernel(const BatchItem *items, const BatchUnit *units,
+                                                                    int n_units, int *counter, int x_words)
+{
+    extern __shared__ __align__(16) int bsm[];
+    BatchItem *s_items = reinterpret_cast<BatchItem *>(bsm);
+    const int wib = threadIdx.x >> 5;
+    int *Xw = bsm + kItemWords * kBatchWarps + wib * x_words;
+    int cached = -1;
+    for (;;) {
+        const int ui = next_unit(counter);
+        if (ui >= n_units) break;
+        const BatchUnit u = units[ui];
+        if (u.item != cached) cached = load_item(items, u.item, s_items + wib);
+        const BatchItem &b = s_items[wib];
+        if (b.variant == 1) {
+            switch (b.mc) {
+            case 2: batch_fwd_thread_unit<READOUT, 2>(b, u, Xw); break;
+            case 4: batch_fwd_thread_unit<READOUT, 4>(b, u, Xw); break;
+            case 8: batch_fwd_thread_unit<READOUT, 8>(b, u, Xw); break;
+            default: batch_fwd_thread_unit<READOUT, 16>(b, u, Xw); break;
+            }
+        } else {
+            const FwdParams &p = b.f;
+            const int *st = reinterpret_cast<const int *>(reinterpret_cast<const unsigned char *>(p.rx) + 16 * p.Mp);
+            for (int c = 0; c < u.count; ++c) {
+                warp_fwd_body<READOUT, true>(p, p.rx, st, p.k_rates, Xw, u.traj_begin + c);
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int READOUT, int MC>
+__device__ __forceinline__ void batch_adj_thread_unit(const BatchItem &b, const BatchUnit &u, float *wsm)
+{
+    const AdjParams &p = b.a;
+    const int lane = threadIdx.x & 31;
+    const int4 *rx = p.rx;
+    const int *st = reinterpret_cast<const int *>(reinterpret_cast<const unsigned char *>(p.rx) + 16 * p.Mp);
+    int *X = reinterpret_cast<int *>(wsm);
+    float *lam = wsm + kBatchThreadMaxN * 32;
+    float *dlam = lam + kBatchThreadMaxN * 32;
+    float dAr[MC];
+#pragma unroll
+    for (int j = 0; j < MC; ++j) dAr[j] = 0.0f;
+    const int64_t i = u.traj_begin + lane;
+    int stt = -1;
+    if (lane < u.count) stt = p.status[i];
+    const bool active = stt == SSA_TRAJ_OK || stt == SSA_TRAJ_ABSORBED || stt == SSA_TRAJ_STEP_CAP;
+    if (active)
+        thread_adj_body<READOUT, MC>(p, rx, st, p.k_rates, X + lane, lam + lane, dlam + lane, nullptr, nullptr, 32, i,
+                                     stt, dAr);
+    // fixed-order sum over the lanes (butterfly: every lane holds the same bits), lane 0 writes the slot
+    float *slot = p.partial + b.slot_off + (int64_t)u.slot * p.M;
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+        const float v = warp_sum(dAr[j]);
+        if (lane == 0 && j < p.M) slot[j] = v;
+    }
+}
+
+template <int READOUT>
+__global__ void __launch_bounds__(32 * kBatchWarps) batch_adj_kernel(const BatchItem *items, const BatchUnit *units,
+                                                                    int n_units, int *counter, int w_words)
+{
+    extern __shared__ __align__(16) float bsa[];
+    BatchItem *s_items = reinterpret_cast<BatchItem *>(bsa);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *wsm = bsa + kItemWords * kBatchWarps + wib * w_words;
+    int cached = -1;
+    for (;;) {
+        const int ui = next_unit(counter);
+        if (ui >= n_units) break;
+        const BatchUnit u = units[ui];
+        if (u.item != cached) cached = load_item(items, u.item, s_items + wib);
+        const BatchItem &b = s_items[wib];
+        if (b.variant == 1) {
+            switch (b.mc) {
+            case 2: batch_adj_thread_unit<READOUT, 2>(b, u, wsm); break;
+            case 4: batch_adj_thread_unit<READOUT, 4>(b, u, wsm); break;
+            case 8: batch_adj_thread_unit<READOUT, 8>(b, u, wsm); break;
+            default: batch_adj_thread_unit<READOUT, 16>(b, u, wsm); break;
+            }
+        } else {
+            const AdjParams &p = b.a;
+            const int Npad = (p.N + 3) & ~3;
+            const int4 *rx = p.rx;
+            const unsigned char *tb = reinterpret_cast<const unsigned char *>(p.rx);
+            const int *st = reinterpret_cast<const int *>(tb + 16 * p.Mp);
+            const int *inc_ptr = reinterpret_cast<const int *>(tb + p.inc_off);
+            const int *inc = reinterpret_cast<const int *>(tb + p.inc_list_off);
+            int *X = reinterpret_cast<int *>(wsm);
+            float *lam = wsm + Npad;
+            float *aj = lam + Npad;
+            float *lj = aj + p.Mp;
+            float *ct = lj + p.Mp;
+            float *dA = ct + 2 * p.Mp;
+            for (int j = lane; j < p.Mp; j += 32) dA[j] = 0.0f;
+            __syncwarp();
+            for (int c = 0; c < u.count; ++c) {
+                const int64_t i = u.traj_begin + c;
+                const int stt = p.status[i];
+                if (stt == SSA_TRAJ_OK || stt == SSA_TRAJ_ABSORBED || stt == SSA_TRAJ_STEP_CAP)
+                    warp_adj_body<READOUT>(p, rx, st, inc_ptr, inc, p.k_rates, X, lam, aj, lj, ct, dA, i, stt);
+                __syncwarp();
+            }
+            float *slot = p.partial + b.slot_off + (int64_t)u.slot * p.M;
+            for (int j = lane; j < p.M; j += 32) slot[j] = dA[j];
+        }
+        __syncwarp();
+    }
+}
+
+// dA of network `it` = fixed-order sum of its unit slots; one block per (network, reaction)
+__global__ void batch_reduce_kernel(const BatchItem *items, const int *blk_item, const int *blk_j)
+{
+    __shared__ float red[256];
+    const BatchItem &b = items[blk_item[blockIdx.x]];
+    const int j = blk_j[blockIdx.x];
+    const float *base = b.a.partial + b.slot_off;
+    float acc = 0.0f;
+    for (int u = threadIdx.x; u < b.n_units; u += blockDim.x) acc += base[(int64_t)u * b.a.M + j];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) b.dA[j] = red[0];
+}
+
+__global__ void batch_params_kernel(const BatchItem *items, int n_items)
+{
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem &b = items[it];
+        for (int r = threadIdx.x; r < b.P; r += blockDim.x) {
+            float acc = 0.0f;
+            for (int j = 0; j < b.a.M; ++j)
+                if (b.rate_index[j] == r) acc += b.dA[j];
+            b.dtheta[r] = acc;
+        }
+    }
+}
+
+}  // namespace ssa
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+using namespace ssa;
+
+struct ssa_batch {
+    std::vector<ssa_batch_item> items;
+    std::vector<int> variant, mc, K;
+    std::vector<double> est_draws;
+    int readout;
+    float temperature;
+    // laid out in the caller's workspace by the first run with it
+    unsigned char *ws = nullptr;
+    int *d_flags = nullptr;  // [n_items][16]
+    BatchItem *d_items = nullptr;
+    BatchUnit *d_units = nullptr;
+    int *d_counters = nullptr;
+    int *d_blk_item = nullptr, *d_blk_j = nullptr;
+    int n_units = 0, n_red_blocks = 0;
+    int x_words = 0, w_words = 0;
+    int fwd_blocks = 0, adj_blocks = 0;
+    size_t fwd_smem = 0, adj_smem = 0;
+    std::vector<BatchItem> h_items;
+    cudaGraphExec_t graph = nullptr;
+    bool ready = false;
+};
+
+namespace {
+
+int batch_mc(int M) { return M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : 16; }
+
+bool thread_eligible(const ssa_network *net) { return net->N <= kBatchThreadMaxN && net->M <= 16; }
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+int64_t units_of(const ssa_batch *bt, size_t it)
+{
+    const int64_t n = bt->items[it].n_traj;
+    const int per = bt->variant[it] == 1 ? 32 : kBatchWarpUnit;
+    return (n + per - 1) / per;
+}
+
+// Workspace layout, shared by the size query and the build:
+//   flags [n_items][16] int | per item: k [Mp] | draws [n] | status [n] | xfinal [N][n] |
+//   events [rows][n] uint4 | checkpoints [n_ckpt][N][n] | brackets k, alpha [S][n] | dA [M] |
+//   unit slots [units][M] | item descriptors | units | reduction maps (item, j) | counters
+struct BatchLayout {
+    size_t flags = 0;
+    std::vector<size_t> k, draws, status, xfinal, ev, ckpt, brk_k, brk_a, dA;
+    size_t partial = 0, items = 0, units = 0, blk_item = 0, blk_j = 0, counters = 0, total = 0;
+    int64_t n_units = 0, n_slots = 0, n_red = 0;
+};
+
+BatchLayout batch_layout(const ssa_batch *bt)
+{
+    BatchLayout L;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t at = off;
+        off += align256(std::max<size_t>(b, 1));
+        return at;
+    };
+    const size_t n_items = bt->items.size();
+    L.flags = take(n_items * 16 * sizeof(int));
+    for (size_t it = 0; it < n_items; ++it) {
+        const ssa_batch_item &b = bt->items[it];
+        const ssa_network *net = b.net;
+        const size_t n = (size_t)b.n_traj;
+        const size_t rows = (size_t)(b.max_steps + 7) / 8, nck = (size_t)(b.max_steps / bt->K[it] + 1);
+        L.k.push_back(take((size_t)net->Mp * 4));
+        L.draws.push_back(take(n * 4));
+        L.status.push_back(take(n * 4));
+        L.xfinal.push_back(take((size_t)net->N * n * 4));
+        L.ev.push_back(take(rows * n * 16));
+        L.ckpt.push_back(take(nck * net->N * n * 4));
+        L.brk_k.push_back(take((size_t)b.n_samples * n * 4));
+        L.brk_a.push_back(take((size_t)b.n_samples * n * 4));
+        L.dA.push_back(take((size_t)net->M * 4));
+        L.n_units += units_of(bt, it);
+        L.n_slots += units_of(bt, it) * net->M;
+        L.n_red += net->M;
+    }
+    L.partial = take((size_t)L.n_slots * 4);
+    L.items = take(n_items * sizeof(BatchItem));
+    L.units = take((size_t)L.n_units * sizeof(BatchUnit));
+    L.blk_item = take((size_t)L.n_red * 4);
+    L.blk_j = take((size_t)L.n_red * 4);
+    L.counters = take(64);
+    L.total = off;
+    return L;
+}
+
+void drop_graph(ssa_batch *bt)
+{
+    if (bt->graph) cudaGraphExecDestroy(bt->graph);
+    bt->graph = nullptr;
+}
+
+int default_ckpt(const ssa_network *net)
+{
+    // checkpoints cost 4N/K bytes per draw beside the 2-byte event; K ~ 16 N keeps them near a
+    // quarter of the log while bounding the re-simulation of each adjoint segment
+    return std::min(1024, std::max(16, (16 * net->N + 7) / 8 * 8));
+}
+
+}  // namespace
+
+extern "C" ssa_status ssa_batch_create(const ssa_batch_item *items, int32_t n_items, int32_t readout,
+                                       float temperature, ssa_batch **out)
+{
+    if (!out) return set_error(SSA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!items || n_items < 1) return set_error(SSA_ERR_INVALID_ARG, "no items");
+    if (readout != SSA_READOUT_HOLD && readout != SSA_READOUT_LINEAR) return set_error(SSA_ERR_INVALID_ARG, "bad readout");
+    if (!(temperature > 0.0f)) return set_error(SSA_ERR_INVALID_ARG, "temperature must be > 0");
+    for (int it = 0; it < n_items; ++it) {
+        const ssa_batch_item &b = items[it];
+        if (!b.net || !b.log_rates || !b.x0 || b.n_traj < 0 || b.n_traj > 0x7fffffffLL || b.traj_offset < 0 ||
+            b.n_samples < 0 || b.n_obs < 0 || b.n_obs > 64 || (b.n_samples > 0 && !b.sample_times) ||
+            (b.n_obs > 0 && !b.obs_species) || !(b.t_end >= 0.0) || !b.dl_dlog_rates || b.max_steps < 1 ||
+            b.max_steps > 0x7fffffffLL || b.ckpt_interval < 0 || (b.ckpt_interval % 8) ||
+            (b.threads_per_traj != 0 && b.threads_per_traj != 1 && b.threads_per_traj != 32) || b.dl_traj_stride < 0)
+            return set_error(SSA_ERR_INVALID_ARG, "invalid batch item");
+        if (b.n_traj > 0 && b.n_samples > 0 && b.n_obs > 0 && (!b.obs_out || !b.dl_dobs))
+            return set_error(SSA_ERR_INVALID_ARG, "batch item without outputs or upstream gradient");
+        if (b.threads_per_traj == 1 && !thread_eligible(b.net))
+            return set_error(SSA_ERR_UNSUPPORTED, "thread variant in a batch needs N <= 16 and M <= 16");
+    }
+    ssa_batch *bt = new (std::nothrow) ssa_batch();
+    if (!bt) return set_error(SSA_ERR_CUDA, "host allocation failed");
+    bt->items.assign(items, items + n_items);
+    bt->readout = readout;
+    bt->temperature = temperature;
+    for (int it = 0; it < n_items; ++it) {
+        const ssa_batch_item &b = items[it];
+        int v = b.threads_per_traj;
+        if (v == 0) v = thread_eligible(b.net) ? 1 : 32;
+        bt->variant.push_back(v);
+        bt->mc.push_back(batch_mc(b.net->M));
+        bt->K.push_back(b.ckpt_interval ? b.ckpt_interval : default_ckpt(b.net));
+        bt->est_draws.push_back((double)b.max_steps / 4.0);
+    }
+    *out = bt;
+    return SSA_OK;
+}
+
+extern "C" void ssa_batch_destroy(ssa_batch *bt)
+{
+    if (!bt) return;
+    drop_graph(bt);
+    delete bt;
+}
+
+extern "C" ssa_status ssa_batch_set_plan(ssa_batch *bt, int32_t item, int32_t threads_per_traj, int32_t ckpt_interval,
+                                         double est_draws)
+{
+    if (!bt || item < 0 || item >= (int)bt->items.size()) return set_error(SSA_ERR_INVALID_ARG, "bad item");
+    if (threads_per_traj != 1 && threads_per_traj != 32) return set_error(SSA_ERR_INVALID_ARG, "threads_per_traj 1 or 32");
+    if (threads_per_traj == 1 && !thread_eligible(bt->items[item].net))
+        return set_error(SSA_ERR_UNSUPPORTED, "thread variant in a batch needs N <= 16 and M <= 16");
+    if (ckpt_interval < 8 || ckpt_interval % 8) return set_error(SSA_ERR_INVALID_ARG, "ckpt_interval: multiple of 8");
+    bt->variant[item] = threads_per_traj;
+    bt->K[item] = ckpt_interval;
+    if (est_draws > 0) bt->est_draws[item] = est_draws;
+    bt->ready = false;
+    bt->ws = nullptr;
+    drop_graph(bt);
+    return SSA_OK;
+}
+
+extern "C" size_t ssa_batch_workspace_bytes(const ssa_batch *bt) { return bt ? batch_layout(bt).total : 0; }
+
+static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cudaStream_t st)
+{
+    const BatchLayout L = batch_layout(bt);
+    if (!workspace || bytes < L.total) return set_error(SSA_ERR_WORKSPACE, "batch workspace too small");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return set_error(SSA_ERR_WORKSPACE, "workspace not 256-byte aligned");
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    const int n_items = (int)bt->items.size();
+    bt->h_items.assign(n_items, BatchItem{});
+    bt->d_flags = reinterpret_cast<int *>(ws + L.flags);
+    float *partial = reinterpret_cast<float *>(ws + L.partial);
+    int maxN = 1, maxMp = 4;
+    int64_t slot_off = 0;
+    for (int it = 0; it < n_items; ++it) {
+        const ssa_batch_item &b = bt->items[it];
+        const ssa_network *net = b.net;
+        int *flag = bt->d_flags + 16 * it;
+        float *k = reinterpret_cast<float *>(ws + L.k[it]);
+        int *draws = reinterpret_cast<int *>(ws + L.draws[it]);
+        int *status = reinterpret_cast<int *>(ws + L.status[it]);
+        int *xfinal = reinterpret_cast<int *>(ws + L.xfinal[it]);
+        uint4 *ev = reinterpret_cast<uint4 *>(ws + L.ev[it]);
+        int *ckpt = reinterpret_cast<int *>(ws + L.ckpt[it]);
+        int *brk_k = reinterpret_cast<int *>(ws + L.brk_k[it]);
+        float *brk_a = reinterpret_cast<float *>(ws + L.brk_a[it]);
+        BatchItem &bi = bt->h_items[it];
+        FwdParams &p = bi.f;
+        AdjParams &a = bi.a;
+        p.rx = a.rx = net->d_rx;
+        p.k_rates = a.k_rates = k;
+        p.tab_bytes = a.tab_bytes = net->tab_bytes;
+        p.k_bytes = a.k_bytes = (uint32_t)(net->Mp * 4);
+        p.N = a.N = net->N;
+        p.M = a.M = net->M;
+        p.Mp = a.Mp = net->Mp;
+        p.inc_off = a.inc_off = net->inc_off;
+        p.inc_list_off = a.inc_list_off = net->inc_list_off;
+        p.nnz = a.nnz = net->nnz;
+        p.n_traj = a.n_traj = b.n_traj;
+        p.traj_offset = a.traj_offset = (uint64_t)b.traj_offset;
+        p.seed = a.seed = b.seed;
+        p.ts = a.ts = b.sample_times;
+        p.S = a.S = b.n_samples;
+        p.obs_sp = a.obs_sp = b.obs_species;
+        p.n_obs = a.n_obs = b.n_obs;
+        p.K = a.K = bt->K[it];
+        p.x0 = b.x0;
+        p.x0_per_traj = 0;
+        p.t_end = b.t_end;
+        p.max_steps = b.max_steps;
+        p.obs_out = b.obs_out;
+        p.draws = draws;
+        p.status = status;
+        p.flag = flag;
+        p.err = flag + 1;
+        p.ev = ev;
+        p.ckpt = ckpt;
+        p.brk_k = brk_k;
+        p.brk_a = brk_a;
+        p.xfinal = xfinal;
+        a.draws = draws;
+        a.status = status;
+        a.ev = ev;
+        a.ckpt = ckpt;
+        a.brk_k = brk_k;
+        a.brk_a = brk_a;
+        a.xfinal = xfinal;
+        a.dl_dobs = b.dl_dobs;
+        a.dl_stride = b.dl_traj_stride;
+        a.invT = 1.0f / bt->temperature;
+        a.partial = partial;
+        a.mismatch = flag + 2;
+        a.err = flag + 1;
+        bi.variant = bt->variant[it];
+        bi.mc = bt->mc[it];
+        bi.slot_off = slot_off;
+        bi.n_units = (int)units_of(bt, it);
+        bi.log_rates = b.log_rates;
+        bi.rate_index = net->d_rate_index;
+        bi.P = net->P;
+        bi.dtheta = b.dl_dlog_rates;
+        bi.dA = reinterpret_cast<float *>(ws + L.dA[it]);
+        slot_off += (int64_t)bi.n_units * net->M;
+        maxN = std::max(maxN, net->N);
+        maxMp = std::max(maxMp, net->Mp);
+    }
+    // work units, longest first by the planned cost (draws x per-draw work x trajectories per unit)
+    std::vector<BatchUnit> units;
+    std::vector<double> cost;
+    for (int it = 0; it < n_items; ++it) {
+        const int per = bt->variant[it] == 1 ? 32 : kBatchWarpUnit;
+        const int M = bt->items[it].net->M;
+        for (int u = 0; u < bt->h_items[it].n_units; ++u) {
+            BatchUnit bu;
+            bu.item = it;
+            bu.traj_begin = (int64_t)u * per;
+            bu.count = (int)std::min<int64_t>(per, bt->items[it].n_traj - bu.traj_begin);
+            bu.slot = u;
+            units.push_back(bu);
+            // a thread unit runs its lanes side by side; a warp unit runs its trajectories in turn
+            const double per_draw = bt->variant[it] == 1 ? (double)bt->mc[it] : (double)(M + 32) / 8.0;
+            cost.push_back(bt->est_draws[it] * per_draw * (bt->variant[it] == 1 ? 1.0 : bu.count));
+        }
+    }
+    std::vector<size_t> order(units.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<BatchUnit> sorted(units.size());
+    for (size_t q = 0; q < order.size(); ++q) sorted[q] = units[order[q]];
+    std::vector<int> blk_item, blk_j;
+    for (int it = 0; it < n_items; ++it)
+        for (int j = 0; j < bt->items[it].net->M; ++j) {
+            blk_item.push_back(it);
+            blk_j.push_back(j);
+        }
+    bt->d_items = reinterpret_cast<BatchItem *>(ws + L.items);
+    bt->d_units = reinterpret_cast<BatchUnit *>(ws + L.units);
+    bt->d_blk_item = reinterpret_cast<int *>(ws + L.blk_item);
+    bt->d_blk_j = reinterpret_cast<int *>(ws + L.blk_j);
+    bt->d_counters = reinterpret_cast<int *>(ws + L.counters);
+    CUDA_TRY_B(cudaMemcpyAsync(bt->d_items, bt->h_items.data(), n_items * sizeof(BatchItem), cudaMemcpyHostToDevice, st));
+    if (!sorted.empty())
+        CUDA_TRY_B(cudaMemcpyAsync(bt->d_units, sorted.data(), sorted.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st));
+    CUDA_TRY_B(cudaMemcpyAsync(bt->d_blk_item, blk_item.data(), blk_item.size() * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY_B(cudaMemcpyAsync(bt->d_blk_j, blk_j.data(), blk_j.size() * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY_B(cudaStreamSynchronize(st));  // the host vectors above go out of scope
+    bt->n_units = (int)sorted.size();
+    bt->n_red_blocks = (int)blk_item.size();
+    const int maxNpad = (maxN + 3) & ~3;
+    bt->x_words = std::max(kBatchThreadMaxN * 32, maxNpad);
+    bt->w_words = std::max(3 * kBatchThreadMaxN * 32, 2 * maxNpad + 5 * maxMp);
+    bt->fwd_smem = (size_t)kBatchWarps * (kItemWords + bt->x_words) * 4;
+    bt->adj_smem = (size_t)kBatchWarps * (kItemWords + bt->w_words) * 4;
+    int dev = 0, sms = 0, per_sm_f = 0, per_sm_a = 0, limit = 0;
+    CUDA_TRY_B(cudaGetDevice(&dev));
+    CUDA_TRY_B(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY_B(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (bt->fwd_smem > (size_t)limit || bt->adj_smem > (size_t)limit)
+        return set_error(SSA_ERR_UNSUPPORTED, "a network in the batch is too large for the batch kernels");
+    auto fk = bt->readout == SSA_READOUT_HOLD ? batch_fwd_kernel<0> : batch_fwd_kernel<1>;
+    auto ak = bt->readout == SSA_READOUT_HOLD ? batch_adj_kernel<0> : batch_adj_kernel<1>;
+    CUDA_TRY_B(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->fwd_smem));
+    CUDA_TRY_B(cudaFuncSetAttribute(ak, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->adj_smem));
+    CUDA_TRY_B(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, fk, 32 * kBatchWarps, bt->fwd_smem));
+    CUDA_TRY_B(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, ak, 32 * kBatchWarps, bt->adj_smem));
+    if (per_sm_f < 1 || per_sm_a < 1) return set_error(SSA_ERR_UNSUPPORTED, "batch kernels do not fit on an SM");
+    // one persistent wave, never more warps than units
+    const int64_t need_blocks = (bt->n_units + kBatchWarps - 1) / kBatchWarps;
+    bt->fwd_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm_f, need_blocks));
+    bt->adj_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm_a, need_blocks));
+    bt->ws = ws;
+    bt->ready = true;
+    return SSA_OK;
+}
+
+static ssa_status batch_enqueue(ssa_batch *bt, cudaStream_t st)
+{
+    const int n_items = (int)bt->items.size();
+    CUDA_TRY_B(cudaMemsetAsync(bt->d_flags, 0, (size_t)n_items * 16 * sizeof(int), st));
+    CUDA_TRY_B(cudaMemsetAsync(bt->d_counters, 0, 64, st));
+    batch_prepare_kernel<<<std::min(n_items, 1024), 128, 0, st>>>(bt->d_items, n_items);
+    if (bt->n_units > 0) {
+        if (bt->readout == SSA_READOUT_HOLD) {
+            batch_fwd_kernel<0><<<bt->fwd_blocks, 32 * kBatchWarps, bt->fwd_smem, st>>>(
+                bt->d_items, bt->d_units, bt->n_units, bt->d_counters, bt->x_words);
+            batch_adj_kernel<0><<<bt->adj_blocks, 32 * kBatchWarps, bt->adj_smem, st>>>(
+                bt->d_items, bt->d_units, bt->n_units, bt->d_counters + 1, bt->w_words);
+        } else {
+            batch_fwd_kernel<1><<<bt->fwd_blocks, 32 * kBatchWarps, bt->fwd_smem, st>>>(
+                bt->d_items, bt->d_units, bt->n_units, bt->d_counters, bt->x_words);
+            batch_adj_kernel<1><<<bt->adj_blocks, 32 * kBatchWarps, bt->adj_smem, st>>>(
+                bt->d_items, bt->d_units, bt->n_units, bt->d_counters + 1, bt->w_words);
+        }
+    }
+    if (bt->n_red_blocks > 0) batch_reduce_kernel<<<bt->n_red_blocks, 256, 0, st>>>(bt->d_items, bt->d_blk_item, bt->d_blk_j);
+    batch_params_kernel<<<std::min(n_items, 1024), 128, 0, st>>>(bt->d_items, n_items);
+    CUDA_TRY_B(cudaGetLastError());
+    return SSA_OK;
+}
+
+extern "C" ssa_status ssa_batch_run(ssa_batch *bt, void *workspace, size_t workspace_bytes, int32_t use_graph,
+                                    void *stream)
+{
+    if (!bt) return set_error(SSA_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!bt->ready || bt->ws != workspace) {
+        drop_graph(bt);
+        const ssa_status s = batch_build(bt, workspace, workspace_bytes, st);
+        if (s != SSA_OK) return s;
+    }
+    if (!use_graph) return batch_enqueue(bt, st);
+    if (!bt->graph) {
+        if (!st) return set_error(SSA_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+        CUDA_TRY_B(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const ssa_status s = batch_enqueue(bt, st);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (s != SSA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return set_error(SSA_ERR_CUDA, cudaGetErrorString(e));
+        const cudaError_t ei = cudaGraphInstantiate(&bt->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            bt->graph = nullptr;
+            return set_error(SSA_ERR_CUDA, cudaGetErrorString(ei));
+        }
+    }
+    CUDA_TRY_B(cudaGraphLaunch(bt->graph, st));
+    return SSA_OK;
+}
+
+extern "C" ssa_status ssa_batch_item_outputs(const ssa_batch *bt, int32_t item, int32_t *draws_out, int32_t *status_out,
+                                             int64_t *host_mismatch, void *stream)
+{
+    if (!bt || !bt->ready || item < 0 || item >= (int)bt->items.size()) return set_error(SSA_ERR_INVALID_ARG, "bad item");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const BatchItem &b = bt->h_items[item];
+    const int64_t n = b.f.n_traj;
+    if (n > 0 && draws_out) CUDA_TRY_B(cudaMemcpyAsync(draws_out, b.f.draws, n * 4, cudaMemcpyDeviceToDevice, st));
+    if (n > 0 && status_out) CUDA_TRY_B(cudaMemcpyAsync(status_out, b.f.status, n * 4, cudaMemcpyDeviceToDevice, st));
+    if (host_mismatch) {
+        int f[4];
+        CUDA_TRY_B(cudaMemcpyAsync(f, b.f.flag, sizeof(f), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY_B(cudaStreamSynchronize(st));
+        *host_mismatch = f[2];
+        if (f[1] & kErrStageTimeout) return set_error(SSA_ERR_CUDA, "a kernel timed out staging its tables");
+    }
+    return SSA_OK;
+}
+
+// Pilot-based plan: for each item, run `pilot_traj` trajectories through the single-network entry
+// points (forward with record, then the adjoint) under every eligible variant, keep the faster one,
+// and take the pilot's mean draw count as the item's cost estimate; the checkpoint interval stays.
+extern "C" ssa_status ssa_batch_autotune(ssa_batch *bt, int64_t pilot_traj, void *stream, double *host_draws_out)
+{
+    if (!bt || pilot_traj < 1) return set_error(SSA_ERR_INVALID_ARG, "bad batch or pilot size");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY_B(cudaEventCreate(&e0));
+    CUDA_TRY_B(cudaEventCreate(&e1));
+    ssa_status rc = SSA_OK;
+    for (size_t it = 0; it < bt->items.size() && rc == SSA_OK; ++it) {
+        const ssa_batch_item &b = bt->items[it];
+        const int64_t n = std::min<int64_t>(pilot_traj, std::max<int64_t>(b.n_traj, 1));
+        const size_t obs_elems = (size_t)n * b.n_samples * b.n_obs;
+        std::vector<int> cands;
+        if (b.threads_per_traj) cands.push_back(b.threads_per_traj);
+        else {
+            if (thread_eligible(b.net)) cands.push_back(1);
+            cands.push_back(32);
+        }
+        double best = -1.0, best_draws = bt->est_draws[it];
+        int best_v = bt->variant[it];
+        for (int v : cands) {
+            ssa_fwd_opts o{};
+            o.readout = bt->readout;
+            o.record = 1;
+            o.ckpt_interval = bt->K[it];
+            o.threads_per_traj = v;
+            o.max_steps = b.max_steps;
+            const size_t wsb = ssa_forward_workspace_bytes(b.net, n, b.n_samples, &o);
+            if (wsb == 0) {
+                rc = set_error(SSA_ERR_INVALID_ARG, "pilot workspace size");
+                break;
+            }
+            void *ws = nullptr, *obs = nullptr, *dl = nullptr, *dth = nullptr, *dr = nullptr;
+            if (cudaMalloc(&ws, wsb) != cudaSuccess || cudaMalloc(&obs, std::max<size_t>(obs_elems, 1) * 4) != cudaSuccess ||
+                cudaMalloc(&dl, std::max<size_t>(obs_elems, 1) * 4) != cudaSuccess ||
+                cudaMalloc(&dth, (size_t)b.net->P * 4) != cudaSuccess || cudaMalloc(&dr, (size_t)n * 4) != cudaSuccess) {
+                cudaFree(ws); cudaFree(obs); cudaFree(dl); cudaFree(dth); cudaFree(dr);
+                rc = set_error(SSA_ERR_CUDA, "pilot allocation failed");
+                break;
+            }
+            cudaMemsetAsync(dl, 0, std::max<size_t>(obs_elems, 1) * 4, st);
+            ssa_run *run = nullptr;
+            ssa_status s = SSA_OK;
+            float ms_best = -1.0f;
+            for (int rep = 0; rep < 2 && s == SSA_OK; ++rep) {  // the first repetition warms the kernels up
+                cudaEventRecord(e0, st);
+                s = ssa_forward(b.net, b.log_rates, n, b.traj_offset, b.x0, 0, b.t_end, b.sample_times, b.n_samples,
+                                b.obs_species, b.n_obs, b.seed, &o, ws, wsb, obs, static_cast<int32_t *>(dr), nullptr,
+                                stream, &run);
+                if (s == SSA_OK) s = ssa_backward(run, static_cast<float *>(dl), (int64_t)b.n_samples * b.n_obs,
+                                                  bt->temperature, static_cast<float *>(dth), stream);
+                cudaEventRecord(e1, st);
+                if (run) ssa_destroy_run(run);
+                run = nullptr;
+                if (s == SSA_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms_best, e0, e1);
+            }
+            std::vector<int> hd((size_t)n);
+            if (s == SSA_OK && cudaMemcpy(hd.data(), dr, (size_t)n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+                s = set_error(SSA_ERR_CUDA, "pilot copy failed");
+            cudaFree(ws); cudaFree(obs); cudaFree(dl); cudaFree(dth); cudaFree(dr);
+            if (s != SSA_OK) {
+                rc = s;
+                break;
+            }
+            double sum = 0.0;
+            for (int d : hd) sum += d;
+            if (best < 0.0 || ms_best < best) {
+                best = ms_best;
+                best_v = v;
+                best_draws = std::max(1.0, sum / (double)n);
+            }
+        }
+        if (rc != SSA_OK) break;
+        bt->variant[it] = best_v;
+        bt->est_draws[it] = best_draws;
+        if (host_draws_out) host_draws_out[it] = best_draws;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bt->ready = false;
+    bt->ws = nullptr;
+    drop_graph(bt);
+    return rc;
+}
+
+extern "C" int32_t ssa_batch_item_variant(const ssa_batch *bt, int32_t item)
+{
+    if (!bt || item < 0 || item >= (int)bt->items.size()) return 0;
+    return bt->variant[item];
+}

@@ -17,59 +17,9 @@
 // binary32 operations in the same order.
 #include <cstdint>
 
-#include "ssa_internal.cuh"
+#include "ssa_warp_body.cuh"
 
 namespace ssa {
-
-namespace {
-
-// One step's propensities, a0 and race over this lane's Philox blocks. Returns E_0 on lane 0.
-// If aj / lj are given, stores a_j and log2(a_j / E_j) (or -inf) for this lane's reactions.
-template <bool STORE>
-__device__ __forceinline__ void warp_step_eval(const FwdParamsView &v, int k, const int *X, float &a0, float &E0,
-                                               float &ab, float &Eb, int &jb, float *aj, float *lj, float &lmax)
-{
-    const int lane = threadIdx.x & 31;
-    float a0p = 0.0f;
-    E0 = 0.0f;
-    ab = 0.0f;
-    Eb = 1.0f;
-    jb = -1;
-    lmax = -CUDART_INF_F;
-    for (int b = lane; b < v.nb; b += 32) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, v.c2, v.c3), v.key0, v.key1);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = 4 * b + q - 1;
-            if (j < 0) {
-                E0 = -logf(u01(r.x));
-                continue;
-            }
-            // padded table entries (j >= M) have rate 0
-            const float a = __fmul_rn(v.s_k[j], mass_action_h(v.s_rx[j], X, 1));
-            a0p = __fadd_rn(a0p, a);
-            float l = -CUDART_INF_F;
-            if (a > 0.0f) {
-                const float E = -logf(u01(word_of(r, q)));
-                race(a, E, j, ab, Eb, jb);
-                if (STORE) {
-                    l = __log2f(a) - __log2f(E);
-                    lmax = fmaxf(lmax, l);
-                }
-            }
-            if (STORE && j < v.M) {
-                aj[j] = a;
-                lj[j] = l;
-            }
-        }
-    }
-    a0 = warp_sum(a0p);
-    warp_race_combine(ab, Eb, jb);
-    E0 = __shfl_sync(0xffffffffu, E0, 0);
-    if (STORE) lmax = warp_max(lmax);
-}
-
-}  // namespace
 
 template <int READOUT, bool RECORD>
 __global__ void __launch_bounds__(256) fwd_warp_kernel(const FwdParams p)
@@ -88,130 +38,7 @@ __global__ void __launch_bounds__(256) fwd_warp_kernel(const FwdParams p)
     if (!stage_tables(smem, p.rx, p.tab_bytes, s_k, p.k_rates, p.k_bytes, s_bar, s_ok, p.err)) return;
     const int64_t i = (int64_t)blockIdx.x * W + wib;
     if (i >= p.n_traj) return;  // whole warp
-    const int64_t n = p.n_traj;
-
-    const int *x0 = p.x0 + (p.x0_per_traj ? i * N : 0);
-    const bool bad_obs = (*p.flag & kErrBadObs) != 0;
-    bool neg = false;
-    for (int s = lane; s < N; s += 32) {
-        X[s] = x0[s];
-        neg |= x0[s] < 0;
-    }
-    const bool bad_input = __any_sync(0xffffffffu, neg) || (*p.flag & (kErrBadSamples | kErrBadObs)) != 0;
-    __syncwarp();
-    const uint64_t gid = p.traj_offset + (uint64_t)i;
-    FwdParamsView v{s_rx, s_k, M, (M + 4) >> 2, (uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)p.seed,
-                    (uint32_t)(p.seed >> 32)};
-
-    double t = 0.0;
-    int s = 0;
-    double thr = p.S > 0 ? p.ts[0] : p.t_end;
-    int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
-    int k = 0, draws = 0, ck_left = p.K, ck_row = 0;
-    uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
-
-    while (!bad_input) {
-        if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
-        float a0, E0, ab, Eb, lmax;
-        int jb;
-        warp_step_eval<false>(v, k, X, a0, E0, ab, Eb, jb, nullptr, nullptr, lmax);
-        if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
-        if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
-        if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }
-        const float tau = __fdividef(E0, a0);
-        const double t_next = t + f2d_pos(tau);
-        const int4 rj = s_rx[jb];
-        const bool slow = gt_nonneg(t_next, thr);
-        const bool cross = slow && gt_nonneg(t_next, p.t_end);
-        if (!cross) {
-            bool bad_neg = false, bad_ovf = false;
-            for (int e = rj.z + lane; e < rj.w; e += 32) {
-                const int st = s_st[e];
-                const int x = X[stoich_species(st)], d = stoich_delta(st);
-                bad_neg |= d < 0 && x + d < 0;
-                bad_ovf |= d > 0 && x > 2147483647 - d;
-            }
-            if (__any_sync(0xffffffffu, bad_neg)) status = SSA_TRAJ_NEG_COUNT;
-            else if (__any_sync(0xffffffffu, bad_ovf)) status = SSA_TRAJ_OVERFLOW;
-        }
-        if (RECORD) {
-            e0 = __funnelshift_r(e0, e1, 16);
-            e1 = __funnelshift_r(e1, e2, 16);
-            e2 = __funnelshift_r(e2, e3, 16);
-            e3 = (e3 >> 16) | ((uint32_t)jb << 16);
-            if (lane == 0 && (k & 7) == 7) p.ev[(int64_t)(k >> 3) * n + i] = make_uint4(e0, e1, e2, e3);
-        }
-        draws = k + 1;
-        if (status != SSA_TRAJ_OK) break;
-        if (slow) {
-            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
-                if (READOUT == SSA_READOUT_HOLD) {
-                    int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    for (int c = lane; c < p.n_obs; c += 32) o[c] = X[p.obs_sp[c]];
-                } else {
-                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
-                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    for (int c = lane; c < p.n_obs; c += 32) {
-                        const int sp = p.obs_sp[c];
-                        int dv = 0;
-                        for (int e = rj.z; e < rj.w; ++e)
-                            if (stoich_species(s_st[e]) == sp) dv += stoich_delta(s_st[e]);
-                        o[c] = __fmaf_rn(alpha, (float)dv, (float)X[sp]);
-                    }
-                    if (RECORD && lane == 0) p.brk_a[(int64_t)s * n + i] = alpha;
-                }
-                if (RECORD && lane == 0) p.brk_k[(int64_t)s * n + i] = k;
-                ++s;
-            }
-            thr = s < p.S ? p.ts[s] : p.t_end;
-            if (cross) break;
-        }
-        __syncwarp();
-        for (int e = rj.z + lane; e < rj.w; e += 32) {
-            const int st = s_st[e];
-            X[stoich_species(st)] += stoich_delta(st);  // the entries of one reaction name distinct species
-        }
-        __syncwarp();
-        t = t_next;
-        ++k;
-        if (RECORD && --ck_left == 0) {
-            ck_left = p.K;
-            ++ck_row;
-            int *ck = p.ckpt + (int64_t)ck_row * N * n + i;
-            for (int sp = lane; sp < N; sp += 32) ck[(int64_t)sp * n] = X[sp];
-        }
-    }
-    __syncwarp();
-    for (; s < p.S; ++s) {
-        if (READOUT == SSA_READOUT_HOLD) {
-            int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-            for (int c = lane; c < p.n_obs; c += 32) o[c] = bad_obs ? 0 : X[p.obs_sp[c]];
-        } else {
-            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-            for (int c = lane; c < p.n_obs; c += 32) o[c] = bad_obs ? 0.0f : (float)X[p.obs_sp[c]];
-            if (RECORD && lane == 0) p.brk_a[(int64_t)s * n + i] = -1.0f;
-        }
-        if (RECORD && lane == 0) p.brk_k[(int64_t)s * n + i] = k;
-    }
-    if (lane == 0) {
-        p.draws[i] = draws;
-        p.status[i] = status;
-    }
-    if (RECORD) {
-        if ((draws & 7) && lane == 0) {
-            for (int pad = draws & 7; pad < 8; ++pad) {
-                e0 = __funnelshift_r(e0, e1, 16);
-                e1 = __funnelshift_r(e1, e2, 16);
-                e2 = __funnelshift_r(e2, e3, 16);
-                e3 = e3 >> 16;
-            }
-            p.ev[(int64_t)((draws - 1) >> 3) * n + i] = make_uint4(e0, e1, e2, e3);
-        }
-        for (int sp = lane; sp < N; sp += 32) {
-            p.xfinal[(int64_t)sp * n + i] = X[sp];
-            p.ckpt[(int64_t)sp * n + i] = x0[sp];
-        }
-    }
+    warp_fwd_body<READOUT, RECORD>(p, s_rx, s_st, s_k, X, i);
 }
 
 template <int READOUT>
@@ -250,169 +77,7 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(const AdjParams p)
     int st = -1;
     if (i < n) st = p.status[i];
     const bool active = st == SSA_TRAJ_OK || st == SSA_TRAJ_ABSORBED || st == SSA_TRAJ_STEP_CAP;
-    if (active) {
-        const int d = p.draws[i];
-        const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;
-        for (int s = lane; s < N; s += 32) {
-            X[s] = p.xfinal[(int64_t)s * n + i];
-            lam[s] = 0.0f;
-        }
-        __syncwarp();
-        const uint64_t gid = p.traj_offset + (uint64_t)i;
-        FwdParamsView v{s_rx, s_k, M, (M + 4) >> 2, (uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)p.seed,
-                        (uint32_t)(p.seed >> 32)};
-        const float invT = p.invT;
-        const float *gl = p.dl_dobs + i * p.dl_stride;
-        int row_cached = -1;
-        uint4 row = make_uint4(0, 0, 0, 0);
-        auto event_at = [&](int kk) -> int {
-            const int r = kk >> 3;
-            if (r != row_cached) { row = p.ev[(int64_t)r * n + i]; row_cached = r; }
-            const int slot = kk & 7;
-            const uint32_t w = word_of(row, slot >> 1);
-            return (slot & 1) ? (int)(w >> 16) : (int)(w & 0xffff);
-        };
-        int s_hi = p.S - 1;
-        int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
-        float mu = 0.0f;
-        int mism = 0;
-        int ck_row = L / p.K, ck_off = L - ck_row * p.K;
-
-        for (int k = L; k >= 0; --k) {
-            const bool draw = (k < L) || (st == SSA_TRAJ_OK);
-            const int s_top = s_hi;
-            while (s_hi >= 0 && brk_next == k) {
-                --s_hi;
-                brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
-            }
-            if (draw) {
-                const int jk = event_at(k);
-                float a0, E0, ab, Eb, lmax;
-                int jb;
-                warp_step_eval<true>(v, k, X, a0, E0, ab, Eb, jb, aj, lj, lmax);
-                mism += (jb != jk);
-                const float tau = __fdividef(E0, a0);
-                const int4 rk = s_rx[jk];
-                float dt_dir = 0.0f, dtau_dir = 0.0f;
-                if (READOUT == SSA_READOUT_LINEAR) {
-                    // serial on lane 0 (observed species may repeat), broadcast afterwards
-                    if (lane == 0) {
-                        for (int s = s_hi + 1; s <= s_top; ++s) {
-                            const float alpha = p.brk_a[(int64_t)s * n + i];
-                            if (alpha < 0.0f) continue;
-                            float c = 0.0f;
-                            for (int o = 0; o < p.n_obs; ++o) {
-                                const float g = gl[(int64_t)s * p.n_obs + o];
-                                const int sp = p.obs_sp[o];
-                                lam[sp] += alpha * g;
-                                int dv = 0;
-                                for (int e = rk.z; e < rk.w; ++e)
-                                    if (stoich_species(s_st[e]) == sp) dv += stoich_delta(s_st[e]);
-                                c += g * (float)dv;
-                            }
-                            const float c_tau = __fdividef(c, tau);
-                            dt_dir -= c_tau;
-                            dtau_dir -= alpha * c_tau;
-                        }
-                    }
-                    dt_dir = __shfl_sync(0xffffffffu, dt_dir, 0);
-                    dtau_dir = __shfl_sync(0xffffffffu, dtau_dir, 0);
-                }
-                __syncwarp();
-                const float dtau = mu + dtau_dir;
-                const float dLda0 = -dtau * tau / a0;
-                // pass 2: weights and w_j over this lane's reactions
-                float Zp = 0.0f, Wp = 0.0f;
-                for (int b = lane; b < v.nb; b += 32) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = 4 * b + q - 1;
-                        if (j < 0 || j >= M) continue;
-                        const float l = lj[j];
-                        const float qv = l == -CUDART_INF_F ? 0.0f : exp2f((l - lmax) * invT);
-                        lj[j] = qv;
-                        if (qv > 0.0f) {
-                            const int4 rx = s_rx[j];
-                            float w = 0.0f;
-                            for (int e = rx.z; e < rx.w; ++e) w += (float)stoich_delta(s_st[e]) * lam[stoich_species(s_st[e])];
-                            Zp += qv;
-                            Wp += qv * w;
-                        }
-                    }
-                }
-                const float Z = warp_sum(Zp), Wq = warp_sum(Wp);
-                const float invZ = __fdividef(1.0f, Z), Wbar = Wq * invZ;
-                // pass 3: per-reaction adjoints and reactant-slot contributions to the state adjoint
-                for (int b = lane; b < v.nb; b += 32) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = 4 * b + q - 1;
-                        if (j < 0 || j >= M) continue;
-                        const int4 rx = s_rx[j];
-                        const float qv = lj[j], a = aj[j];
-                        float psi = 0.0f;
-                        if (qv > 0.0f) {
-                            float w = 0.0f;
-                            for (int e = rx.z; e < rx.w; ++e) w += (float)stoich_delta(s_st[e]) * lam[stoich_species(s_st[e])];
-                            psi = qv * invZ * (w - Wbar) * invT;
-                        }
-                        dA[j] += psi + dLda0 * a;
-                        float c1 = 0.0f, c2 = 0.0f;
-                        if (rx.x >= 0) {
-                            const float c_tau = dLda0 * s_k[j];
-                            const float x1 = int2f(X[rx.x]);
-                            if (rx.y < 0) {
-                                c1 = (a > 0.0f ? __fdividef(psi, x1) : 0.0f) + c_tau;
-                            } else if (rx.y == rx.x) {
-                                const float dh = x1 - 0.5f;
-                                c1 = (a > 0.0f ? __fdividef(psi * dh, mass_action_h(rx, X, 1)) : 0.0f) + c_tau * dh;
-                            } else {
-                                const float x2 = int2f(X[rx.y]);
-                                c1 = (a > 0.0f ? __fdividef(psi, x1) : 0.0f) + c_tau * x2;
-                                c2 = (a > 0.0f ? __fdividef(psi, x2) : 0.0f) + c_tau * x1;
-                            }
-                        }
-                        ct[2 * j] = c1;
-                        ct[2 * j + 1] = c2;
-                    }
-                }
-                __syncwarp();
-                for (int sp = lane; sp < N; sp += 32) {
-                    float acc = 0.0f;
-                    for (int e = s_inc_ptr[sp]; e < s_inc_ptr[sp + 1]; ++e) acc += ct[s_inc[e]];
-                    lam[sp] += acc;
-                }
-                mu += dt_dir;
-            }
-            __syncwarp();
-            if (lane == 0) {
-                for (int s = s_hi + 1; s <= s_top; ++s) {
-                    float coef = 1.0f;
-                    if (READOUT == SSA_READOUT_LINEAR && draw) {
-                        const float alpha = p.brk_a[(int64_t)s * n + i];
-                        if (alpha >= 0.0f) coef = 1.0f - alpha;
-                    }
-                    for (int o = 0; o < p.n_obs; ++o) lam[p.obs_sp[o]] += coef * gl[(int64_t)s * p.n_obs + o];
-                }
-            }
-            if (ck_off == 0) {
-                const int *ck = p.ckpt + (int64_t)ck_row * N * n + i;
-                int bad = 0;
-                for (int s = lane; s < N; s += 32) bad += (ck[(int64_t)s * n] != X[s]);
-                mism += __reduce_add_sync(0xffffffffu, bad);
-                --ck_row;
-                ck_off = p.K;
-            }
-            --ck_off;
-            __syncwarp();
-            if (k > 0) {
-                const int4 rp = s_rx[event_at(k - 1)];
-                for (int e = rp.z + lane; e < rp.w; e += 32) X[stoich_species(s_st[e])] -= stoich_delta(s_st[e]);
-            }
-            __syncwarp();
-        }
-        if (lane == 0 && mism) atomicAdd(p.mismatch, mism);
-    }
+    if (active) warp_adj_body<READOUT>(p, s_rx, s_st, s_inc_ptr, s_inc, s_k, X, lam, aj, lj, ct, dA, i, st);
     __syncthreads();
     // fixed-order reduction over the block's warps
     float *base0 = reinterpret_cast<float *>(smem + p.tab_bytes + p.k_bytes + 16);

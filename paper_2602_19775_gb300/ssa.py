@@ -202,6 +202,120 @@ def backward(fwd: ForwardResult | Run, dl_dobs: torch.Tensor, temperature: float
     return out
 
 
+
+class Batch:
+    """Many networks simulated and differentiated together (ssa_batch_*): one persistent forward and one
+    persistent adjoint launch per run, optionally replayed from a captured CUDA graph.
+
+    items: dicts with keys net, log_rates, n_traj, x0, t_end, sample_times, obs_species, seed and
+    optionally traj_offset, max_steps, ckpt_interval, threads_per_traj, shared_dl (True: one upstream
+    gradient [S, n_obs] for all trajectories). The batch owns fixed device tensors per item --
+    log_rates[i], obs[i], dl_dobs[i], dtheta[i] -- whose addresses are baked into the plan: write new
+    parameters or upstream gradients into them in place (copy_) between runs.
+    """
+
+    def __init__(self, items, readout="hold", temperature=0.5, device=None):
+        device = torch.device(device) if device is not None else torch.device("cuda")
+        ro = READOUTS[readout] if isinstance(readout, str) else int(readout)
+        odt = torch.int32 if ro == _lib.SSA_READOUT_HOLD else torch.float32
+        self.readout, self.device = ro, device
+        self.log_rates, self.obs, self.dl_dobs, self.dtheta, self._keep = [], [], [], [], []
+        self.nets = []
+        arr = (_lib.BatchItem * len(items))()
+        for q, it in enumerate(items):
+            net = it["net"]
+            theta = _as_cuda(it["log_rates"], torch.float32, device).clone()
+            x0 = _as_cuda(it["x0"], torch.int32, device)
+            ts = _as_cuda(it["sample_times"], torch.float64, device)
+            sp = _as_cuda(it["obs_species"], torch.int32, device)
+            n, S, o = int(it["n_traj"]), int(ts.numel()), int(sp.numel())
+            obs = torch.zeros((n, S, o), dtype=odt, device=device)
+            shared = bool(it.get("shared_dl", False))
+            dl = torch.zeros((S, o) if shared else (n, S, o), dtype=torch.float32, device=device)
+            dth = torch.zeros(net.n_params, dtype=torch.float32, device=device)
+            self.nets.append(net)
+            self.log_rates.append(theta)
+            self.obs.append(obs)
+            self.dl_dobs.append(dl)
+            self.dtheta.append(dth)
+            self._keep.append((x0, ts, sp))
+            b = arr[q]
+            b.net = net.handle
+            b.log_rates = theta.data_ptr()
+            b.x0 = x0.data_ptr()
+            b.n_traj = n
+            b.seed = int(it["seed"]) & (2**64 - 1)
+            b.traj_offset = int(it.get("traj_offset", 0))
+            b.t_end = float(it["t_end"])
+            b.sample_times = ts.data_ptr() if S else None
+            b.n_samples = S
+            b.n_obs = o
+            b.obs_species = sp.data_ptr() if o else None
+            b.max_steps = int(it.get("max_steps", 1 << 14))
+            b.ckpt_interval = int(it.get("ckpt_interval", 0))
+            b.threads_per_traj = int(it.get("threads_per_traj", 0))
+            b.obs_out = obs.data_ptr() if obs.numel() else None
+            b.dl_dobs = dl.data_ptr() if dl.numel() else None
+            b.dl_traj_stride = 0 if shared else S * o
+            b.dl_dlog_rates = dth.data_ptr()
+        self._items = arr
+        h = ctypes.c_void_p()
+        check(_lib.lib().ssa_batch_create(arr, len(items), ro, ctypes.c_float(float(temperature)), ctypes.byref(h)))
+        self.handle = h
+        self.workspace = None
+
+    def __len__(self):
+        return len(self.obs)
+
+    def workspace_bytes(self) -> int:
+        return int(_lib.lib().ssa_batch_workspace_bytes(self.handle))
+
+    def autotune(self, pilot_traj: int = 256, stream=None) -> list:
+        """ssa_batch_autotune: returns the pilot's mean draws per item."""
+        out = (ctypes.c_double * len(self))()
+        check(_lib.lib().ssa_batch_autotune(self.handle, int(pilot_traj), _stream(stream), out))
+        self.workspace = None
+        return list(out)
+
+    def set_plan(self, item: int, threads_per_traj: int, ckpt_interval: int, est_draws: float = 0.0):
+        check(_lib.lib().ssa_batch_set_plan(self.handle, int(item), int(threads_per_traj), int(ckpt_interval),
+                                            float(est_draws)))
+        self.workspace = None
+
+    def variant(self, item: int) -> int:
+        return int(_lib.lib().ssa_batch_item_variant(self.handle, int(item)))
+
+    def run(self, use_graph: bool = False, stream=None) -> list:
+        """ssa_batch_run: fills obs[i] and dtheta[i] for every item; returns dtheta."""
+        need = self.workspace_bytes()
+        if self.workspace is None or self.workspace.numel() < need:
+            self.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+        check(_lib.lib().ssa_batch_run(self.handle, _ptr(self.workspace), need, 1 if use_graph else 0,
+                                       _stream(stream)))
+        return self.dtheta
+
+    def outputs(self, item: int, stream=None):
+        """(draws, status, adjoint mismatch count) of one item after run()."""
+        n = self.obs[item].shape[0]
+        draws = torch.empty(n, dtype=torch.int32, device=self.device)
+        status = torch.empty(n, dtype=torch.int32, device=self.device)
+        mism = ctypes.c_int64(0)
+        check(_lib.lib().ssa_batch_item_outputs(self.handle, int(item), _ptr(draws), _ptr(status),
+                                                ctypes.byref(mism), _stream(stream)))
+        return draws, status, int(mism.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.lib().ssa_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def ensemble_mean(obs: torch.Tensor, stream=None) -> torch.Tensor:
     """ssa_ensemble_mean over the first axis (deterministic order) -> float32 [obs.shape[1:]]."""
     obs = obs.contiguous()

@@ -22,7 +22,8 @@ LINEAR = 1
 
 
 def uniform_sample_grid(t_end: float, S: int) -> np.ndarray:
-    return (np.arange(1, S + 1, dtype=np.float64) * (t_end / S)).astype(np.float64)
+    """t_end/S, 2 t_end/S, ..., t_end; S * (t_end / S) can round one ulp above t_end, so clip."""
+    return np.minimum(np.arange(1, S + 1, dtype=np.float64) * (t_end / S), float(t_end))
 
 
 @dataclass

@@ -1,0 +1,188 @@
+"""GPU tests of the batch of networks (one persistent forward and one persistent adjoint launch for
+many networks of different sizes): each item reproduces the single-network entry points bit for bit
+in its observables, draws and status codes, and to binary32 summation order in its gradient; the
+gradient bits do not depend on which warp ran which work unit; a captured CUDA graph replays the
+same computation with updated parameters; the pilot autotuner picks a valid plan."""
+import numpy as np
+import pytest
+import torch
+
+import ssa_workloads as W
+from ssa_workloads.configs import LINEAR
+
+from test_gpu_warp import _pilot_t_end
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2602_19775_gb300 import ssa
+    ssa._lib.lib()
+    return ssa
+
+
+def _random(seed, n_sp, n_rx):
+    return W.random_network(np.random.default_rng(seed), n_species_range=n_sp, n_reactions_range=n_rx)
+
+
+@pytest.fixture(scope="module")
+def specs():
+    """(network, n_traj, t_end, n_samples, obs species, seed, threads_per_traj, max_steps) per item."""
+    dimer = W.dimerization_2a_b()
+    imm = W.immigration_death()
+    osc = W.vilar_oscillator()
+    r10 = _random(21, (3, 8), (10, 10))
+    r_big = _random(3, (8, 64), (100, 200))
+    r30 = _random(5, (6, 12), (20, 40))
+    out = [
+        (dimer, 300, 20.0, 10, [0, 1], 11, 0, 4096),
+        (imm, 33, 5.0, 5, [0], 12, 0, 4096),
+        (osc, 64, 1.0, 8, [6, 7, 8], 13, 0, 1 << 14),
+        (r10, 70, None, 6, [0, 1], 14, 0, 4096),
+        (r_big, 9, None, 6, [0, 1, 2], 15, 0, 4096),
+        (r30, 20, None, 6, [0, 1], 16, 32, 4096),
+        (dimer, 0, 20.0, 4, [0], 17, 0, 4096),
+    ]
+    res = []
+    for net, n, t_end, ns, obs, seed, tpt, ms in out:
+        if t_end is None:
+            t_end = _pilot_t_end(net, net.log_rates.astype(np.float32).astype(np.float64))
+        res.append((net, n, t_end, ns, obs, seed, tpt, ms))
+    return res
+
+
+def _items(S, specs, nets, theta_shift=0.0):
+    items = []
+    for q, (net, n, t_end, ns, obs, seed, tpt, ms) in enumerate(specs):
+        items.append(dict(net=nets[q], log_rates=(net.log_rates + theta_shift).astype(np.float32), n_traj=n,
+                          x0=net.x0, t_end=t_end, sample_times=W.uniform_sample_grid(t_end, ns), obs_species=obs,
+                          seed=seed, traj_offset=7 * q, max_steps=ms, threads_per_traj=tpt, ckpt_interval=64))
+    return items
+
+
+def _fill_dl(b, specs, seed=3):
+    for q, (net, n, t_end, ns, obs, *_rest) in enumerate(specs):
+        dl = W.seeded_dl_dobs(seed + q, n, ns, len(obs), scale=1.0 / max(n, 1))
+        b.dl_dobs[q].copy_(torch.tensor(dl, dtype=torch.float32))
+
+
+def _single(S, net, item, variant, dl, T):
+    fw = S.forward(net, torch.tensor(item["log_rates"], device="cuda"), item["n_traj"], item["x0"], item["t_end"],
+                   item["sample_times"], item["obs_species"], item["seed"], readout="linear", record=True,
+                   max_steps=item["max_steps"], traj_offset=item["traj_offset"], threads_per_traj=variant,
+                   ckpt_interval=64)
+    g = S.backward(fw, dl, T) if item["n_traj"] > 0 else torch.zeros(net.n_params, device="cuda")
+    return fw, g
+
+
+def _check_against_single(S, b, specs, nets, items, T):
+    for q in range(len(specs)):
+        v = b.variant(q)
+        assert v in (1, 32)
+        fw, g = _single(S, nets[q], items[q], v, b.dl_dobs[q], T)
+        draws, status, mism = b.outputs(q)
+        assert mism == 0
+        torch.testing.assert_close(b.obs[q], fw.obs, rtol=0, atol=0)
+        assert torch.equal(draws, fw.draws) and torch.equal(status, fw.status)
+        assert torch.all(status <= 2), q  # OK, ABSORBED or STEP_CAP
+        gb, gs = b.dtheta[q].double().cpu().numpy(), g.double().cpu().numpy()
+        scale = max(np.abs(gs).max(), 1e-12)
+        assert np.abs(gb - gs).max() <= 1e-4 * scale, (q, np.abs(gb - gs).max(), scale)
+
+
+def test_batch_matches_single_network_entry_points(S, specs):
+    nets = [S.Network(s[0]) for s in specs]
+    items = _items(S, specs, nets)
+    b = S.Batch(items, readout="linear", temperature=0.5)
+    assert [b.variant(q) for q in range(len(specs))] == [1, 1, 1, 1, 32, 32, 1]
+    _fill_dl(b, specs)
+    b.run()
+    _check_against_single(S, b, specs, nets, items, 0.5)
+    assert torch.all(b.dtheta[6] == 0)
+
+
+def test_batch_gradient_bits_do_not_depend_on_unit_order(S, specs):
+    nets = [S.Network(s[0]) for s in specs]
+    b = S.Batch(_items(S, specs, nets), readout="linear", temperature=0.5)
+    _fill_dl(b, specs)
+    b.run()
+    first = [t.clone() for t in b.dtheta]
+    for _ in range(3):
+        b.run()
+        for q in range(len(specs)):
+            assert torch.equal(b.dtheta[q], first[q]), q
+
+
+def test_batch_graph_replay_with_updated_parameters(S, specs):
+    nets = [S.Network(s[0]) for s in specs]
+    stream = torch.cuda.Stream()
+    g = S.Batch(_items(S, specs, nets), readout="linear", temperature=0.5)
+    _fill_dl(g, specs)
+    with torch.cuda.stream(stream):
+        g.run(use_graph=True, stream=stream)
+    stream.synchronize()
+    ref = S.Batch(_items(S, specs, nets), readout="linear", temperature=0.5)
+    _fill_dl(ref, specs)
+    ref.run()
+    torch.cuda.synchronize()
+    for q in range(len(specs)):
+        assert torch.equal(g.obs[q], ref.obs[q]) and torch.equal(g.dtheta[q], ref.dtheta[q]), q
+    # new parameters and upstream gradients written in place, graph replayed
+    items2 = _items(S, specs, nets, theta_shift=0.05)
+    for q in range(len(specs)):
+        g.log_rates[q].copy_(torch.tensor(items2[q]["log_rates"]))
+    _fill_dl(g, specs, seed=40)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        g.run(use_graph=True, stream=stream)
+    stream.synchronize()
+    ref2 = S.Batch(items2, readout="linear", temperature=0.5)
+    _fill_dl(ref2, specs, seed=40)
+    ref2.run()
+    torch.cuda.synchronize()
+    for q in range(len(specs)):
+        assert torch.equal(g.obs[q], ref2.obs[q]) and torch.equal(g.dtheta[q], ref2.dtheta[q]), q
+    assert not torch.equal(g.obs[0], ref.obs[0])
+
+
+def test_batch_autotune_plan_is_valid_and_exact(S, specs):
+    nets = [S.Network(s[0]) for s in specs]
+    items = _items(S, specs, nets)
+    b = S.Batch(items, readout="linear", temperature=0.7)
+    draws = b.autotune(pilot_traj=32)
+    assert all(d >= 1.0 for d in draws)
+    assert b.variant(5) == 32  # requested explicitly
+    _fill_dl(b, specs)
+    b.run()
+    _check_against_single(S, b, specs, nets, items, 0.7)
+
+
+def test_batch_item_with_bad_samples_is_isolated(S):
+    dimer = W.dimerization_2a_b()
+    net = S.Network(dimer)
+    ok = dict(net=net, log_rates=dimer.log_rates.astype(np.float32), n_traj=40, x0=dimer.x0, t_end=10.0,
+              sample_times=W.uniform_sample_grid(10.0, 5), obs_species=[0], seed=1)
+    bad = dict(ok, sample_times=np.array([1.0, 3.0, 2.0]), seed=2)
+    b = S.Batch([ok, bad], readout="hold", temperature=0.5)
+    b.run()
+    _, st_ok, _ = b.outputs(0)
+    _, st_bad, _ = b.outputs(1)
+    assert torch.all(st_ok == 0)
+    assert torch.all(st_bad == 6)  # SSA_TRAJ_BAD_INPUT
+    assert torch.all(b.dtheta[1] == 0)
+
+
+def test_batch_rejects_invalid_items(S):
+    from paper_2602_19775_gb300 import SSAError
+    dimer = W.dimerization_2a_b()
+    net = S.Network(dimer)
+    base = dict(net=net, log_rates=dimer.log_rates.astype(np.float32), n_traj=8, x0=dimer.x0, t_end=1.0,
+                sample_times=[0.5], obs_species=[0], seed=1)
+    with pytest.raises(SSAError):
+        S.Batch([dict(base, ckpt_interval=12)])
+    with pytest.raises(SSAError):
+        S.Batch([dict(base, max_steps=0)])
+    big = S.Network(_random(3, (20, 30), (40, 60)))
+    with pytest.raises(SSAError):
+        S.Batch([dict(base, net=big, x0=np.zeros(big.n_species, np.int32), threads_per_traj=1)])
