@@ -347,6 +347,8 @@ def run_ours(args):
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     osc = oscillator_extra(ssa, dev) if (rank == 0 and not args.no_extra) else None
+    batch = uneven_batch_extra(ssa, dev, args.batch_scale) if (rank == 0 and not args.no_extra) else None
+    grn = grn_extra(ssa, dev) if (rank == 0 and not args.no_extra) else None
     M = wl.net.n_reactions
     rates = ssa.pipe_rates()
     logf_slots = 128.0 / rates["logf"]
@@ -356,6 +358,8 @@ def run_ours(args):
     ach_b = instr_per_step_bwd(M, logf_slots) * per_launch_steps / bwd_s
     ach_f = instr_per_step_fwd(M, logf_slots) * per_launch_steps / fwd_s
     peak = sm_issue_peak(sm_mhz, rates["sm_count"])
+    if batch and "instr_per_s_T" in batch:
+        batch["alu_frac"] = batch["instr_per_s_T"] * 1e12 / peak
     dominant = "adjoint" if bwd_s >= fwd_s else "forward"
     ach = ach_b if dominant == "adjoint" else ach_f
     line = {
@@ -387,6 +391,8 @@ def run_ours(args):
                      "peak_basis": f"{rates['sm_count']} SM x 4 x 32 lanes x {sm_mhz:.0f} MHz (sampled median)",
                      "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in rates.items()}},
         "oscillator": osc,
+        "uneven_batch": batch,
+        "grn": grn,
         "paper_context": "1.9e9 SSA steps/s forward on the oscillator, RTX 6000 Ada + TF 2.20 (a different machine)",
         "cpu_baseline": cpu_base,
         "e2e": {"value": e2e_value, "unit": "SSA steps/s (fwd+adj)", "h2d_bytes_per_step": h2d,
@@ -437,6 +443,165 @@ def oscillator_extra(ssa, dev, n_fwd: int = 1 << 20, n_adj: int = 1 << 16, t_end
     return out
 
 
+def uneven_batch_extra(ssa, dev, traj_scale: float, reps: int = 2, sequential: bool = True):
+    """The uneven batch of random networks (256 networks, N in [2, 64], M in [4, 512], trajectories per
+    network log-uniform in [256, 65,536] x traj_scale, t_end = 10, 20 LINEAR samples, T = 0.5, loss
+    weights c ~ N(0, 1) on the trajectory means): forward + adjoint of every network in one CUDA-graph
+    launch of the persistent batch kernels, after the pilot autotuner. Event logs are sized from the
+    committed oracle pilot (twice its maximum draws + 256). Also times the same work as one forward and
+    one backward call per network, for comparison."""
+    import torch
+
+    import ssa_workloads as W
+    path = os.path.join(ROOT, "tests", "golden", "c4_pilot.json")
+    if not os.path.exists(path):
+        return {"skipped": "no oracle pilot file"}
+    pilot = json.load(open(path))
+    wl = W.config_c4(n_nets=len(pilot["accepted"]), traj_scale=traj_scale, rejected=pilot["rejected"])
+    assert [a["draw"] for a in pilot["accepted"]] == wl.draw_index.tolist()
+    max_steps = [int(2 * a["max_draws"] + 256) for a in pilot["accepted"]]
+    nets = [ssa.Network(spec) for spec in wl.nets]
+    items = []
+    for q, spec in enumerate(wl.nets):
+        items.append(dict(net=nets[q], log_rates=spec.log_rates.astype(np.float32), n_traj=int(wl.n_traj[q]),
+                          x0=spec.x0, t_end=wl.t_end, sample_times=wl.sample_times, obs_species=wl.obs_species[q],
+                          seed=900 + q, max_steps=max_steps[q], shared_dl=True))
+    b = ssa.Batch(items, readout="linear", temperature=wl.temperature, device=dev)
+    t0 = time.time()
+    b.autotune(pilot_traj=64)
+    t_tune = time.time() - t0
+    for q in range(len(items)):
+        b.dl_dobs[q].copy_(torch.tensor(wl.loss_weights[q] / wl.n_traj[q], dtype=torch.float32))
+    stream = torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        b.run(use_graph=True, stream=stream)  # lays out the workspace, captures and runs the graph once
+        stream.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            b.run(use_graph=True, stream=stream)
+        ev[1].record(stream)
+    stream.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    steps, variants, mism, bad = 0, {1: 0, 32: 0}, 0, 0
+    per_item = []
+    for q in range(len(items)):
+        d, st, mm = b.outputs(q, stream=stream)
+        sq = int(d.sum().item())
+        steps += sq
+        per_item.append(sq)
+        mism += mm
+        bad += int((st > 2).sum().item())
+        variants[b.variant(q)] += 1
+    rates = ssa.pipe_rates()
+    logf_slots = 128.0 / rates["logf"]
+    instr = sum(per_item[q] * (instr_per_step_fwd(wl.nets[q].n_reactions, logf_slots)
+                               + instr_per_step_bwd(wl.nets[q].n_reactions, logf_slots)) for q in range(len(items)))
+    out = {"workload": f"{len(items)} random networks, N in [2, 64], M in [4, 512], t_end=10, 20 LINEAR samples, "
+                       f"T=0.5, trajectories per network log-uniform [256, 65536] x {traj_scale:g}",
+           "n_traj_total": int(wl.n_traj.sum()), "ssa_steps": steps, "ms": ms, "steps_per_s": steps / (ms / 1e3),
+           "unit": "SSA steps/s (fwd+adj)", "variants": {"thread": variants[1], "warp": variants[32]},
+           "workspace_gb": b.workspace_bytes() / 1e9, "autotune_s": t_tune, "adjoint_mismatches": mism,
+           "non_ok_trajectories": bad, "instr_per_s_T": instr / (ms / 1e3) / 1e12,
+           "redraws": len(pilot["rejected"])}
+    del b
+    if sequential:
+        torch.cuda.synchronize()
+        ev[0].record()
+        for q, it in enumerate(items):
+            fw = ssa.forward(nets[q], torch.tensor(it["log_rates"], device=dev), it["n_traj"], it["x0"], wl.t_end,
+                             wl.sample_times, it["obs_species"], it["seed"], readout="linear", record=True,
+                             max_steps=it["max_steps"])
+            dl = torch.tensor(wl.loss_weights[q] / wl.n_traj[q], dtype=torch.float32, device=dev)
+            ssa.backward(fw, dl, wl.temperature)
+            del fw
+        ev[1].record()
+        torch.cuda.synchronize()
+        out["per_network_calls_ms"] = ev[0].elapsed_time(ev[1])
+    return out
+
+
+def grn_extra(ssa, dev, n_img: int = 512, tpi: int = 64, t_end: float = 20.0, reps: int = 2):
+    """The gene-regulatory-network classifier (784 -> 256 -> 10, 203,796 parameters, bf16 W1 and W2):
+    512 synthetic prototype images x 64 trajectories, t_end = 20, HOLD readout of the 10 outputs at
+    t_end, cross-entropy of the softmax of the output counts against the image label, forward +
+    straight-through backward at T = 1. Also times the tcgen05 bf16 GEMM alone on the GRN contraction's
+    shape and on a large square shape, against the measured bf16 peak."""
+    import torch
+
+    from ssa_workloads import grn as G
+    p = G.grn_params(seed=5)
+    x, labels = G.prototype_images(seed=5, n_img=n_img)
+    net = ssa.GRN(p.n_in, p.n_hid, p.n_out, p.k_max)
+    n = n_img * tpi
+    lab = torch.tensor(np.repeat(labels, tpi), device=dev)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd_ms = adj_ms = 0.0
+    steps = 0
+    for r in range(reps + 1):
+        ev[0].record(stream)
+        fw = ssa.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, tpi, t_end, [t_end], 70 + r, record=True,
+                             max_steps=1 << 14)
+        ev[1].record(stream)
+        y = fw.obs[:, 0, :].float()
+        dl = (torch.softmax(y, dim=1) - torch.nn.functional.one_hot(lab, p.n_out).float()) / n
+        ev[2].record(stream)
+        ssa.grn_backward(fw, dl.view(n, 1, p.n_out), 1.0)
+        ev_end = torch.cuda.Event(enable_timing=True)
+        ev_end.record(stream)
+        torch.cuda.synchronize()
+        if r >= 1:
+            fwd_ms += ev[0].elapsed_time(ev[1])
+            adj_ms += ev[2].elapsed_time(ev_end)
+            steps += int(fw.draws.sum().item())
+            bad = int((fw.status > 2).sum().item())
+        del fw
+    fwd_ms, adj_ms, steps = fwd_ms / reps, adj_ms / reps, steps // reps
+    out = {"workload": f"GRN 784-256-10, {n_img} images x {tpi} trajectories, t_end={t_end}, HOLD at t_end, "
+                       "cross-entropy, T=1",
+           "ssa_steps": steps, "forward_ms": fwd_ms, "backward_ms": adj_ms,
+           "fwd_steps_per_s": steps / (fwd_ms / 1e3), "fwd_adj_steps_per_s": steps / ((fwd_ms + adj_ms) / 1e3),
+           "non_ok_trajectories": bad}
+    # the tensor-core kernel alone: the GRN's contraction (8 six-bit limbs of W1 against 512 images)
+    # and a large square product
+    gem = {}
+    for name, (M, N, K) in {"grn_E1_limbs": (n_img, p.n_hid, p.n_in * 8), "square_8192": (8192, 8192, 8192)}.items():
+        A = torch.randn(M, K, device=dev).to(torch.bfloat16)
+        B = torch.randn(N, K, device=dev).to(torch.bfloat16)
+        ssa.bf16_gemm(A, B)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        it = 5 if M >= 4096 else 50
+        Ap = torch.zeros((M, (K + 7) // 8 * 8), dtype=torch.bfloat16, device=dev)
+        Bp = torch.zeros((N, (K + 7) // 8 * 8), dtype=torch.bfloat16, device=dev)
+        Ap[:, :K], Bp[:, :K] = A, B
+        D = torch.empty((M, N), device=dev)
+        err = torch.zeros(1, dtype=torch.int32, device=dev)
+        ld = Ap.shape[1]
+        L = ssa._lib.lib()
+        e0.record(stream)
+        for _ in range(it):
+            ssa.check(L.ssa_bf16_gemm(ssa._ptr(Ap), ssa._ptr(Bp), M, N, K, ld, ld, None, ssa._ptr(D), N,
+                                      ssa._ptr(err), ssa._stream()))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / it
+        gem[name] = {"M": M, "N": N, "K": K, "ms": ms, "tflops": 2.0 * M * N * K / (ms / 1e3) / 1e12,
+                     "timeout_flag": int(err.item())}
+        del A, B, Ap, Bp, D
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        basis = "of measured (cuBLAS bf16 burst)"
+    except (OSError, KeyError, ValueError):
+        peak, basis = 1900.0, "of fallback"
+    for g in gem.values():
+        g["frac"] = g["tflops"] / peak
+        g["peak_basis"] = f"{peak:g} TFLOP/s {basis}"
+    out["tcgen05_gemm"] = gem
+    return out
+
+
 def grad_error_subset(ssa, net, wl, dev, n=2048):
     """Relative error of the GPU gradient against the FP64 oracle on trajectories with identical
     event sequences, for each temperature (same seeded inputs on both sides)."""
@@ -473,7 +638,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-chunk", type=int, default=4096)
     ap.add_argument("--no-oracle", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the oscillator throughput fields")
+    ap.add_argument("--no-extra", action="store_true", help="skip the oscillator and uneven-batch fields")
+    ap.add_argument("--batch-scale", type=float, default=1.0 / 16,
+                    help="trajectories per network of the uneven batch, as a fraction of the full counts")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -375,6 +375,16 @@ ssa_status ssa_batch_item_outputs(const ssa_batch *batch, int32_t item, int32_t 
                                   int32_t *status_out, int64_t *host_bwd_mismatch, void *stream);
 
 /*
+ * ssa_batch_item_events, ssa_batch_item_brackets -- test hooks after ssa_batch_run, as
+ * ssa_run_events and ssa_run_brackets for one item: device int32 [n_traj][stride] events (-1 after
+ * the last draw) and device int32 [n_traj][n_samples] sample brackets.
+ */
+ssa_status ssa_batch_item_events(const ssa_batch *batch, int32_t item, int32_t *events_out,
+                                 int64_t stride, void *stream);
+ssa_status ssa_batch_item_brackets(const ssa_batch *batch, int32_t item, int32_t *brackets_out,
+                                   void *stream);
+
+/*
  * ssa_batch_autotune -- pilot-based plan (no counterpart in the paper). For each item, runs
  * min(pilot_traj, n_traj) trajectories through ssa_forward(record) + ssa_backward under each
  * variant the item allows (threads_per_traj = 0: thread if N, M <= 16, and warp), keeps the faster,

@@ -26,7 +26,8 @@ EXPORTS = (
     "ssa_bf16_gemm", "ssa_pipe_rates", "ssa_last_error", "ssa_grn_create", "ssa_grn_destroy",
     "ssa_grn_workspace_bytes", "ssa_grn_forward", "ssa_grn_backward", "ssa_grn_activations",
     "ssa_batch_create", "ssa_batch_destroy", "ssa_batch_set_plan", "ssa_batch_workspace_bytes", "ssa_batch_run",
-    "ssa_batch_item_outputs", "ssa_batch_autotune", "ssa_batch_item_variant",
+    "ssa_batch_item_outputs", "ssa_batch_autotune", "ssa_batch_item_variant", "ssa_batch_item_events",
+    "ssa_batch_item_brackets",
 )
 
 
@@ -112,6 +113,8 @@ def _declare(lib):
         "ssa_batch_item_outputs": (i32, [p, i32, p, p, p, p]),
         "ssa_batch_autotune": (i32, [p, i64, p, p]),
         "ssa_batch_item_variant": (i32, [p, i32]),
+        "ssa_batch_item_events": (i32, [p, i32, p, i64, p]),
+        "ssa_batch_item_brackets": (i32, [p, i32, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -27,6 +27,9 @@
     } while (0)
 
 namespace ssa {
+cudaError_t launch_unpack_events(const uint4 *ev, const int *draws, int64_t n_traj, int64_t stride, int *out,
+                                 cudaStream_t st);
+cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, int *out, cudaStream_t st);
 
 struct BatchItem {
     FwdParams f;
@@ -650,6 +653,25 @@ extern "C" ssa_status ssa_batch_item_outputs(const ssa_batch *bt, int32_t item, 
         *host_mismatch = f[2];
         if (f[1] & kErrStageTimeout) return set_error(SSA_ERR_CUDA, "a kernel timed out staging its tables");
     }
+    return SSA_OK;
+}
+
+extern "C" ssa_status ssa_batch_item_events(const ssa_batch *bt, int32_t item, int32_t *events_out, int64_t stride,
+                                            void *stream)
+{
+    if (!bt || !bt->ready || item < 0 || item >= (int)bt->items.size() || !events_out || stride < 1)
+        return set_error(SSA_ERR_INVALID_ARG, "bad arguments");
+    const FwdParams &p = bt->h_items[item].f;
+    CUDA_TRY_B(launch_unpack_events(p.ev, p.draws, p.n_traj, stride, events_out, static_cast<cudaStream_t>(stream)));
+    return SSA_OK;
+}
+
+extern "C" ssa_status ssa_batch_item_brackets(const ssa_batch *bt, int32_t item, int32_t *brackets_out, void *stream)
+{
+    if (!bt || !bt->ready || item < 0 || item >= (int)bt->items.size()) return set_error(SSA_ERR_INVALID_ARG, "bad item");
+    const FwdParams &p = bt->h_items[item].f;
+    if (!brackets_out && p.n_traj > 0 && p.S > 0) return set_error(SSA_ERR_INVALID_ARG, "brackets_out is NULL");
+    CUDA_TRY_B(launch_transpose_brackets(p.brk_k, p.n_traj, p.S, brackets_out, static_cast<cudaStream_t>(stream)));
     return SSA_OK;
 }
 

@@ -304,6 +304,19 @@ class Batch:
                                                 ctypes.byref(mism), _stream(stream)))
         return draws, status, int(mism.value)
 
+    def events(self, item: int, stride: int, stream=None) -> torch.Tensor:
+        """Recorded events of one item as int32 [n_traj, stride], -1 after the last draw."""
+        out = torch.empty((self.obs[item].shape[0], int(stride)), dtype=torch.int32, device=self.device)
+        check(_lib.lib().ssa_batch_item_events(self.handle, int(item), _ptr(out), int(stride), _stream(stream)))
+        return out
+
+    def brackets(self, item: int, stream=None) -> torch.Tensor:
+        """Sample brackets of one item as int32 [n_traj, n_samples]."""
+        n, S = self.obs[item].shape[0], self.obs[item].shape[1]
+        out = torch.empty((n, S), dtype=torch.int32, device=self.device)
+        check(_lib.lib().ssa_batch_item_brackets(self.handle, int(item), _ptr(out), _stream(stream)))
+        return out
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.lib().ssa_batch_destroy(self.handle)

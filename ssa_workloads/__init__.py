@@ -21,5 +21,6 @@ from .configs import (  # noqa: F401
     config_c1,
     config_c2,
     config_c3,
+    config_c4,
     seeded_dl_dobs,
 )

@@ -15,7 +15,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .networks import NetworkSpec, dimerization_2a_b, vilar_oscillator
+from .networks import NetworkSpec, dimerization_2a_b, vilar_oscillator, random_network
 
 HOLD = 0
 LINEAR = 1
@@ -69,3 +69,47 @@ def seeded_dl_dobs(seed: int, n_traj: int, S: int, n_obs: int, scale: float = 1.
     """Seeded upstream gradient dL/dobs [n_traj, S, n_obs] (float64) for parity cases."""
     rng = np.random.default_rng(seed)
     return (scale * rng.standard_normal((n_traj, S, n_obs))).astype(np.float64)
+
+
+@dataclass
+class BatchWorkload:
+    name: str
+    nets: list                  # NetworkSpec per network
+    n_traj: np.ndarray          # int64 [n_nets]
+    t_end: float
+    sample_times: np.ndarray    # float64 [S], shared by every network
+    obs_species: list           # int32 arrays, per network
+    loss_weights: list          # float64 [S, n_obs] per network: L = sum c * mean over trajectories of obs
+    seed: int
+    readout: int
+    temperature: float
+    draw_index: np.ndarray      # int64 [n_nets]: position of each accepted network in the generator stream
+
+
+def config_c4(n_nets: int = 256, traj_scale: float = 1.0, rejected=(), seed: int = 3, n_obs_max: int = 8
+              ) -> BatchWorkload:
+    """Uneven batch of random mass-action networks (one seeded stream, `seed`): N ~ U{2..64},
+    M ~ U{4..512} (random_network), trajectories per network log-uniform in [256, 65,536] scaled by
+    traj_scale (at least 1), t_end = 10, 20 uniform samples, LINEAR readout, T = 0.5. Networks are drawn
+    one after another from the stream; a draw whose position is in `rejected` (the redraw list of an
+    oracle pilot) is skipped and the next draw takes its place. Observed species: the first
+    min(N, n_obs_max). Loss weights c ~ N(0, 1) (seed 4)."""
+    rng = np.random.default_rng(seed)
+    trng = np.random.default_rng(seed + 1000)
+    crng = np.random.default_rng(4)
+    rejected = set(int(r) for r in rejected)
+    nets, idx = [], []
+    d = 0
+    while len(nets) < n_nets:
+        net = random_network(rng, n_species_range=(2, 64), n_reactions_range=(4, 512))
+        if d not in rejected:
+            nets.append(net)
+            idx.append(d)
+        d += 1
+    n = np.exp(trng.uniform(np.log(256.0), np.log(65536.0), size=n_nets))
+    n_traj = np.maximum(1, np.round(n * traj_scale)).astype(np.int64)
+    ts = uniform_sample_grid(10.0, 20)
+    obs = [np.arange(min(net.n_species, n_obs_max), dtype=np.int32) for net in nets]
+    c = [crng.standard_normal((len(ts), len(o))) for o in obs]
+    return BatchWorkload("c4_uneven_batch", nets, n_traj, 10.0, ts, obs, c, seed, LINEAR, 0.5,
+                         np.array(idx, np.int64))

@@ -186,3 +186,63 @@ def test_batch_rejects_invalid_items(S):
     big = S.Network(_random(3, (20, 30), (40, 60)))
     with pytest.raises(SSAError):
         S.Batch([dict(base, net=big, x0=np.zeros(big.n_species, np.int32), threads_per_traj=1)])
+
+
+def test_batch_matches_oracle_on_uneven_random_networks(S):
+    """Items of the uneven random-network workload (first draws of its seeded stream, trajectory counts
+    scaled down to oracle size) against the FP64 oracle: status codes, event sequences under the margin
+    rule, observables, and gradients on trajectories whose events and brackets agree."""
+    from oracle import native
+    from test_gpu_parity import GRAD_RTOL, _T_END, _bracket_agreement, _clock_tol, _compare_events, _oracle_brackets
+    from types import SimpleNamespace
+
+    wl = W.config_c4(n_nets=5, traj_scale=1.0 / 256)
+    cap = 1 << 15
+    nets = [S.Network(spec) for spec in wl.nets]
+    items = [dict(net=nets[q], log_rates=spec.log_rates.astype(np.float32), n_traj=int(wl.n_traj[q]), x0=spec.x0,
+                  t_end=wl.t_end, sample_times=wl.sample_times, obs_species=wl.obs_species[q], seed=60 + q,
+                  traj_offset=1000 * q, max_steps=cap) for q, spec in enumerate(wl.nets)]
+    b = S.Batch(items, readout="linear", temperature=wl.temperature)
+    dls = []
+    for q in range(len(items)):
+        dl = W.seeded_dl_dobs(80 + q, items[q]["n_traj"], len(wl.sample_times), len(wl.obs_species[q]),
+                              scale=1.0 / items[q]["n_traj"])
+        dls.append(dl)
+        b.dl_dobs[q].copy_(torch.tensor(dl, dtype=torch.float32))
+    b.run()
+    torch.cuda.synchronize()
+    _T_END["t_end"] = wl.t_end
+    for q, spec in enumerate(wl.nets):
+        it = items[q]
+        n = it["n_traj"]
+        draws, status, mism = b.outputs(q)
+        assert mism == 0
+        orc = native.run(spec, spec.log_rates.astype(np.float32).astype(np.float64), spec.x0, n, wl.t_end,
+                         wl.sample_times, wl.obs_species[q], it["seed"], LINEAR, max_steps=cap,
+                         traj_offset=it["traj_offset"], dl_dobs=dls[q], temperature=wl.temperature, ev_cap=cap)
+        np.testing.assert_array_equal(status.cpu().numpy(), orc.status)
+        fw = SimpleNamespace(draws=draws, status=status,
+                             run=SimpleNamespace(brackets=lambda q=q: b.brackets(q)))
+        same = _compare_events(orc, fw, b.events(q, cap).cpu().numpy())
+        assert same.mean() >= 0.9, (q, same.mean())  # thousands of draws per trajectory, up to 512 reactions
+        agree = _bracket_agreement(orc, fw, wl.sample_times, spec.n_reactions)
+        use = same & agree
+        obs = b.obs[q].double().cpu().numpy()
+        ob = _oracle_brackets(orc, wl.sample_times)
+        vmax = np.abs(spec.stoich_delta).max()
+        for i in np.nonzero(use)[0]:
+            t = np.concatenate([[0.0], orc.times[i, :orc.draws[i]]])
+            k = ob[i]
+            tau = t[np.minimum(k + 1, len(t) - 1)] - t[k]
+            tol = vmax * _clock_tol(spec.n_reactions, wl.sample_times) / np.maximum(tau, 1e-300) \
+                + 1e-6 * np.abs(orc.obs[i]).max(1)
+            assert np.all(np.abs(obs[i] - orc.obs[i]).max(1) <= tol), (q, i)
+        # gradient over the agreeing trajectories: rerun the item alone with the others' upstream zeroed
+        dl_g = dls[q].copy()
+        dl_g[~use] = 0
+        b.dl_dobs[q].copy_(torch.tensor(dl_g, dtype=torch.float32))
+        b.run()
+        g = b.dtheta[q].double().cpu().numpy()
+        ref = orc.dtheta[use].sum(0)
+        rel = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30)
+        assert rel < GRAD_RTOL, (q, rel)
