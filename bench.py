@@ -230,11 +230,11 @@ def run_ours(args):
     dtheta = torch.empty(2, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def step(seed, T, ev=None):
+    def step(seed, T, ev=None, specialize=True):
         if ev is not None:
             ev[0].record(stream)
         fw = ssa.forward(net, theta, n, x0, wl.t_end, ts, obs_sp, seed, readout="linear", record=True,
-                         max_steps=max_steps, traj_offset=offset, workspace=ws, obs_out=obs)
+                         max_steps=max_steps, traj_offset=offset, workspace=ws, obs_out=obs, specialize=specialize)
         if ev is not None:
             ev[1].record(stream)
         m = ssa.ensemble_mean(obs)[:, 0]
@@ -246,11 +246,11 @@ def run_ours(args):
             ev[3].record(stream)
         return fw
 
-    def fwd_only(seed, ev=None):
+    def fwd_only(seed, ev=None, specialize=True):
         if ev is not None:
             ev[0].record(stream)
         fw = ssa.forward(net, theta, n, x0, wl.t_end, ts, obs_sp, seed, readout="linear", record=False,
-                         max_steps=max_steps, traj_offset=offset, workspace=ws, obs_out=obs)
+                         max_steps=max_steps, traj_offset=offset, workspace=ws, obs_out=obs, specialize=specialize)
         if ev is not None:
             ev[1].record(stream)
         return fw
@@ -285,6 +285,22 @@ def run_ours(args):
             fdraws += fw.draws.sum()
             flush.fill_(s & 0xFF)
         barrier()
+    variant = fw.run.variant
+    # the same steps on the generic (table-driven) thread kernels, for comparison (outside the timed region)
+    gev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    gdraws = torch.zeros((), dtype=torch.int64, device=dev)
+    for w in range(2):
+        step(100 + w, TEMPS[w % 3], specialize=False)
+    for s in range(K):
+        gfw = step(1000 + s, TEMPS[s % 3], gev[s], specialize=False)
+        gdraws += gfw.draws.sum()
+        flush.fill_(s & 0xFF)
+    gvar = gfw.run.variant
+    torch.cuda.synchronize()
+    generic = {"variant": gvar, "fwd_adj_steps_per_s": float(gdraws.item()) / (sum(e[0].elapsed_time(e[3]) for e in gev) / 1e3),
+               "forward_record_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in gev])),
+               "adjoint_ms": float(np.mean([e[2].elapsed_time(e[3]) for e in gev]))}
+    del gfw
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
     bwd_ms = [e[2].elapsed_time(e[3]) for e in evs]
@@ -383,6 +399,8 @@ def run_ours(args):
         "grad_rel_err_vs_fp64": grad_err,
         "kernel_ms": {"forward_record": float(np.mean(fwd_ms)), "adjoint": float(np.mean(bwd_ms)),
                       "forward_only": float(np.mean(fonly_ms))},
+        "kernel_variant": {1: "generic thread", 2: "network-specialised thread (NVRTC)", 32: "warp"}[variant],
+        "generic_thread_kernels": generic,
         "roofline": {"bound": "alu", "kernel": dominant, "achieved": ach / 1e12, "peak": peak / 1e12,
                      "unit": "T thread-instr/s", "frac": ach / peak, "traffic": profiled_traffic(dominant),
                      "algorithmic_instr_per_step": {"forward": instr_per_step_fwd(M, logf_slots),

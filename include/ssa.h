@@ -67,7 +67,10 @@ typedef struct ssa_fwd_opts {
                                  trajectory (networks with hundreds of reactions)               */
     int64_t max_steps;        /* cap on reaction draws per trajectory (>= 1); sizes the log       */
     int32_t block_threads;    /* 0: choose; else a multiple of 32 in [32, 1024]                  */
-    int32_t reserved;         /* must be 0                                                       */
+    int32_t no_specialize;    /* 0: run the thread variant as kernels compiled for this network
+                                 (NVRTC, at most 24 species, 24 reactions, 96 stoichiometric
+                                 entries; the same results bit for bit) when it qualifies;
+                                 1: always the generic kernels                                  */
 } ssa_fwd_opts;
 
 /*
@@ -180,6 +183,18 @@ ssa_status ssa_run_events(const ssa_run *run, int32_t *events_out, int64_t strid
 ssa_status ssa_run_brackets(const ssa_run *run, int32_t *brackets_out, void *stream);
 
 void ssa_destroy_run(ssa_run *run);
+
+/* ssa_run_variant -- the kernels a run used: 1 generic thread per trajectory, 2 thread per trajectory
+ * compiled for the network, 32 warp per trajectory (0 for NULL). */
+int32_t ssa_run_variant(const ssa_run *run);
+
+/*
+ * ssa_network_specialize -- compile (once per process and network) and load the kernels specialised
+ * to this network, so that the first forward does not pay for it; *host_ok = 1 if they are
+ * available, else 0 with the reason in ssa_last_error() (network above the limits, or the run-time
+ * compiler failed). Returns SSA_OK unless an argument is NULL. No counterpart in the paper.
+ */
+ssa_status ssa_network_specialize(ssa_network *net, int32_t *host_ok);
 
 /*
  * Gene-regulatory-network classifier (Section 4.3, Figure 4A): n_in clamped input counts x (the

@@ -39,12 +39,33 @@ def _headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(PKG, "..", "include", "*.h")))
 
 
+JIT_TEXT = os.path.join(OUT_DIR, "ssa_jit_text.h")
+JIT_SOURCES = (("kJitTextDevice", os.path.join(CSRC, "ssa_device.cuh")),
+               ("kJitTextBody", os.path.join(CSRC, "ssa_jit_body.cuh")),
+               ("kJitTextApi", os.path.join(PKG, "..", "include", "ssa.h")))
+
+
+def _write_jit_text():
+    """The device sources compiled at run time (NVRTC), embedded in the library as string literals."""
+    parts = ["// generated by build.py from csrc/ssa_device.cuh, csrc/ssa_jit_body.cuh and include/ssa.h\n#pragma once\n"]
+    for name, path in JIT_SOURCES:
+        text = open(path).read()
+        if ")SSAJIT\"" in text:
+            raise RuntimeError(f"{path} contains the raw-string delimiter")
+        parts.append(f'static const char {name}[] = R"SSAJIT({text})SSAJIT";\n')
+    new = "".join(parts)
+    if not os.path.exists(JIT_TEXT) or open(JIT_TEXT).read() != new:
+        with open(JIT_TEXT + ".tmp", "w") as f:
+            f.write(new)
+        os.replace(JIT_TEXT + ".tmp", JIT_TEXT)
+
+
 def _compile(nvcc: str, src: str, extra: list[str]) -> str:
     obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-    newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
+    newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers() + [JIT_TEXT]])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
         return obj
-    cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-I", OUT_DIR, *extra, "-c", src, "-o", obj + ".tmp"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{res.stdout}\n{res.stderr}")
@@ -57,13 +78,14 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
     extra = list(extra or [])
+    _write_jit_text()
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(nvcc, s, extra), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lnvrtc"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

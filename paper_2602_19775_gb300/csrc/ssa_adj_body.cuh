@@ -15,14 +15,13 @@ __device__ __forceinline__ void reaction_state_adjoint(const int4 rx, const int 
     if (rx.x < 0) return;
     const float x1 = int2f(X[rx.x * B]);
     if (rx.y < 0) {
-        dlam[rx.x * B] += (a > 0.0f ? __fdividef(psi, x1) : 0.0f) + c_tau;
+        dlam[rx.x * B] += sadj_first(x1, a, psi, c_tau);
     } else if (rx.y == rx.x) {
-        const float dh = x1 - 0.5f;  // d/dX [X (X - 1)/2]
-        dlam[rx.x * B] += (a > 0.0f ? __fdividef(psi * dh, h) : 0.0f) + c_tau * dh;
+        dlam[rx.x * B] += sadj_homodimer(x1, a, h, psi, c_tau);
     } else {
         const float x2 = int2f(X[rx.y * B]);
-        dlam[rx.x * B] += (a > 0.0f ? __fdividef(psi, x1) : 0.0f) + c_tau * x2;
-        dlam[rx.y * B] += (a > 0.0f ? __fdividef(psi, x2) : 0.0f) + c_tau * x1;
+        dlam[rx.x * B] += sadj_hetero(x1, x2, a, psi, c_tau);
+        dlam[rx.y * B] += sadj_hetero(x2, x1, a, psi, c_tau);
     }
 }
 

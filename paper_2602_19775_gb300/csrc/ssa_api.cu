@@ -35,6 +35,14 @@ cudaError_t launch_forward_warp(const FwdParams &p, int readout, bool record, in
 cudaError_t launch_backward_warp(const AdjParams &p, int readout, int warps, size_t smem, int64_t grid,
                                  cudaStream_t st);
 int thread_kernel_mc(int M);
+struct JitKernels;
+bool jit_eligible(const ssa_network *net);
+const JitKernels *jit_kernels(const ssa_network *net, std::string &why);
+cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int readout, bool record, int block,
+                               cudaStream_t st);
+cudaError_t jit_launch_backward(const JitKernels *k, const AdjParams &p, int readout, int block, int64_t grid,
+                                cudaStream_t st);
+constexpr int kJitBlock = 64;
 }  // namespace ssa
 
 using namespace ssa;
@@ -123,7 +131,7 @@ bool opts_valid(const ssa_fwd_opts *o)
     if (o->threads_per_traj != 0 && o->threads_per_traj != 1 && o->threads_per_traj != 32) return false;
     if (o->block_threads != 0 && (o->block_threads % 32 != 0 || o->block_threads < 32 || o->block_threads > 256))
         return false;
-    if (o->reserved != 0) return false;
+    if (o->no_specialize != 0 && o->no_specialize != 1) return false;
     return true;
 }
 
@@ -155,6 +163,7 @@ size_t adj_warp_smem(const ssa_network *net)
 int pick_variant(const ssa_network *net, const ssa_fwd_opts *o)
 {
     if (o->threads_per_traj) return o->threads_per_traj;
+    if (!o->no_specialize && jit_eligible(net)) return 1;
     return net->M <= 16 ? 1 : 32;
 }
 
@@ -250,6 +259,8 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
         return fail(SSA_ERR_CUDA, "cudaMalloc(network tables): %s", cudaGetErrorString(e));
     }
     unsigned char *b = static_cast<unsigned char *>(net->d_blob);
+    net->h_rx.assign(rx.begin(), rx.begin() + n_reactions);
+    net->h_st.assign(st.begin(), st.begin() + nnz);
     net->d_rx = reinterpret_cast<int4 *>(b);
     net->d_stoich = reinterpret_cast<int *>(b + 16 * Mp);
     net->d_rate_index = reinterpret_cast<int *>(b + net->tab_bytes);
@@ -306,9 +317,18 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     if (!workspace || ws_bytes < L.total) return fail(SSA_ERR_WORKSPACE, "workspace %zu bytes < required %zu", ws_bytes, L.total);
     if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return fail(SSA_ERR_WORKSPACE, "workspace not 256-byte aligned");
     const size_t limit = smem_limit();
-    const int variant = ev_in ? 1 : pick_variant(net, opts);  // replay is a thread-per-trajectory test hook
+    int variant = ev_in ? 1 : pick_variant(net, opts);  // replay is a thread-per-trajectory test hook
+    // the thread variant runs as network-specialised kernels when the network qualifies (variant 2)
+    const JitKernels *jit = nullptr;
+    if (variant == 1 && !ev_in && !opts->no_specialize && jit_eligible(net)) {
+        std::string why;
+        jit = jit_kernels(net, why);
+        if (jit) variant = 2;
+    }
     int block = 0;
-    if (variant == 1) {
+    if (variant == 2) {
+        block = kJitBlock;
+    } else if (variant == 1) {
         block = pick_block(fwd_smem, net, opts->block_threads, limit);
         if (!block) return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory forward");
         if (opts->record && !pick_block(adj_smem, net, 0, limit))
@@ -365,7 +385,9 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     p.ev_in = ev_in;
     p.n_ev_in = n_ev_in;
     p.ev_in_stride = ev_stride;
-    if (variant == 1)
+    if (variant == 2)
+        CUDA_TRY(jit_launch_forward(jit, p, opts->readout, opts->record != 0, block, st));
+    else if (variant == 1)
         CUDA_TRY(launch_forward_thread(p, opts->readout, opts->record != 0, ev_in != nullptr, block, fwd_smem(net, block), st));
     else
         CUDA_TRY(launch_forward_warp(p, opts->readout, opts->record != 0, kWarpsPerBlock, fwd_warp_smem(net), st));
@@ -433,7 +455,14 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     const size_t limit = smem_limit();
     int block = 0;
     int64_t grid = 0;
-    if (run->variant == 1) {
+    const JitKernels *jit = nullptr;
+    if (run->variant == 2) {
+        std::string why;
+        jit = jit_kernels(net, why);
+        if (!jit) return fail(SSA_ERR_STATE, "specialised kernels unavailable: %s", why.c_str());
+        block = kJitBlock;
+        grid = (run->n_traj + block - 1) / block;
+    } else if (run->variant == 1) {
         block = pick_block(adj_smem, net, 0, limit);
         if (!block) return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory adjoint");
         grid = (run->n_traj + block - 1) / block;
@@ -474,7 +503,9 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     p.partial = reinterpret_cast<float *>(ws + L.partial);
     p.mismatch = flag + 2;
     p.err = flag + 1;
-    if (run->variant == 1)
+    if (run->variant == 2)
+        CUDA_TRY(jit_launch_backward(jit, p, run->opts.readout, block, grid, st));
+    else if (run->variant == 1)
         CUDA_TRY(launch_backward_thread(p, run->opts.readout, block, adj_smem(net, block), grid, st));
     else
         CUDA_TRY(launch_backward_warp(p, run->opts.readout, kWarpsPerBlock, adj_warp_smem(net), grid, st));
@@ -524,6 +555,8 @@ extern "C" ssa_status ssa_run_brackets(const ssa_run *run, int32_t *brackets_out
 }
 
 extern "C" void ssa_destroy_run(ssa_run *run) { delete run; }
+
+extern "C" int32_t ssa_run_variant(const ssa_run *run) { return run ? run->variant : 0; }
 
 extern "C" size_t ssa_ensemble_mean_workspace_bytes(int64_t n_traj, int64_t row_len)
 {

@@ -678,74 +678,86 @@ extern "C" ssa_status ssa_batch_item_brackets(const ssa_batch *bt, int32_t item,
 // Pilot-based plan: for each item, run `pilot_traj` trajectories through the single-network entry
 // points (forward with record, then the adjoint) under every eligible variant, keep the faster one,
 // and take the pilot's mean draw count as the item's cost estimate; the checkpoint interval stays.
+// The pilot buffers are allocated once, at the largest size any pilot needs.
 extern "C" ssa_status ssa_batch_autotune(ssa_batch *bt, int64_t pilot_traj, void *stream, double *host_draws_out)
 {
     if (!bt || pilot_traj < 1) return set_error(SSA_ERR_INVALID_ARG, "bad batch or pilot size");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    CUDA_TRY_B(cudaEventCreate(&e0));
-    CUDA_TRY_B(cudaEventCreate(&e1));
-    ssa_status rc = SSA_OK;
-    for (size_t it = 0; it < bt->items.size() && rc == SSA_OK; ++it) {
+    const size_t n_items = bt->items.size();
+    std::vector<std::vector<int>> cands(n_items);
+    size_t ws_max = 0, obs_max = 1, p_max = 1, n_max = 1;
+    for (size_t it = 0; it < n_items; ++it) {
         const ssa_batch_item &b = bt->items[it];
-        const int64_t n = std::min<int64_t>(pilot_traj, std::max<int64_t>(b.n_traj, 1));
-        const size_t obs_elems = (size_t)n * b.n_samples * b.n_obs;
-        std::vector<int> cands;
-        if (b.threads_per_traj) cands.push_back(b.threads_per_traj);
+        if (b.threads_per_traj) cands[it].push_back(b.threads_per_traj);
         else {
-            if (thread_eligible(b.net)) cands.push_back(1);
-            cands.push_back(32);
+            if (thread_eligible(b.net)) cands[it].push_back(1);
+            cands[it].push_back(32);
         }
-        double best = -1.0, best_draws = bt->est_draws[it];
-        int best_v = bt->variant[it];
-        for (int v : cands) {
+        const int64_t n = std::min<int64_t>(pilot_traj, std::max<int64_t>(b.n_traj, 1));
+        for (int v : cands[it]) {
             ssa_fwd_opts o{};
             o.readout = bt->readout;
             o.record = 1;
             o.ckpt_interval = bt->K[it];
             o.threads_per_traj = v;
             o.max_steps = b.max_steps;
-            const size_t wsb = ssa_forward_workspace_bytes(b.net, n, b.n_samples, &o);
-            if (wsb == 0) {
-                rc = set_error(SSA_ERR_INVALID_ARG, "pilot workspace size");
-                break;
-            }
-            void *ws = nullptr, *obs = nullptr, *dl = nullptr, *dth = nullptr, *dr = nullptr;
-            if (cudaMalloc(&ws, wsb) != cudaSuccess || cudaMalloc(&obs, std::max<size_t>(obs_elems, 1) * 4) != cudaSuccess ||
-                cudaMalloc(&dl, std::max<size_t>(obs_elems, 1) * 4) != cudaSuccess ||
-                cudaMalloc(&dth, (size_t)b.net->P * 4) != cudaSuccess || cudaMalloc(&dr, (size_t)n * 4) != cudaSuccess) {
-                cudaFree(ws); cudaFree(obs); cudaFree(dl); cudaFree(dth); cudaFree(dr);
-                rc = set_error(SSA_ERR_CUDA, "pilot allocation failed");
-                break;
-            }
-            cudaMemsetAsync(dl, 0, std::max<size_t>(obs_elems, 1) * 4, st);
-            ssa_run *run = nullptr;
+            o.no_specialize = 1;  // the batch runs the generic kernels
+            const size_t w = ssa_forward_workspace_bytes(b.net, n, b.n_samples, &o);
+            if (w == 0) return set_error(SSA_ERR_INVALID_ARG, "pilot workspace size");
+            ws_max = std::max(ws_max, w);
+        }
+        obs_max = std::max(obs_max, (size_t)n * b.n_samples * b.n_obs);
+        p_max = std::max(p_max, (size_t)b.net->P);
+        n_max = std::max(n_max, (size_t)n);
+    }
+    void *ws = nullptr, *obs = nullptr, *dl = nullptr, *dth = nullptr, *dr = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ssa_status rc = SSA_OK;
+    if (cudaMalloc(&ws, ws_max) != cudaSuccess || cudaMalloc(&obs, obs_max * 4) != cudaSuccess ||
+        cudaMalloc(&dl, obs_max * 4) != cudaSuccess || cudaMalloc(&dth, p_max * 4) != cudaSuccess ||
+        cudaMalloc(&dr, n_max * 4) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        rc = set_error(SSA_ERR_CUDA, "pilot allocation failed");
+    if (rc == SSA_OK && cudaMemsetAsync(dl, 0, obs_max * 4, st) != cudaSuccess)
+        rc = set_error(SSA_ERR_CUDA, "pilot memset failed");
+    std::vector<int> hd(n_max);
+    for (size_t it = 0; it < n_items && rc == SSA_OK; ++it) {
+        const ssa_batch_item &b = bt->items[it];
+        const int64_t n = std::min<int64_t>(pilot_traj, std::max<int64_t>(b.n_traj, 1));
+        double best = -1.0, best_draws = bt->est_draws[it];
+        int best_v = bt->variant[it];
+        for (int v : cands[it]) {
+            ssa_fwd_opts o{};
+            o.readout = bt->readout;
+            o.record = 1;
+            o.ckpt_interval = bt->K[it];
+            o.threads_per_traj = v;
+            o.max_steps = b.max_steps;
+            o.no_specialize = 1;
+            float ms = -1.0f;
             ssa_status s = SSA_OK;
-            float ms_best = -1.0f;
             for (int rep = 0; rep < 2 && s == SSA_OK; ++rep) {  // the first repetition warms the kernels up
+                ssa_run *run = nullptr;
                 cudaEventRecord(e0, st);
                 s = ssa_forward(b.net, b.log_rates, n, b.traj_offset, b.x0, 0, b.t_end, b.sample_times, b.n_samples,
-                                b.obs_species, b.n_obs, b.seed, &o, ws, wsb, obs, static_cast<int32_t *>(dr), nullptr,
+                                b.obs_species, b.n_obs, b.seed, &o, ws, ws_max, obs, static_cast<int32_t *>(dr), nullptr,
                                 stream, &run);
                 if (s == SSA_OK) s = ssa_backward(run, static_cast<float *>(dl), (int64_t)b.n_samples * b.n_obs,
                                                   bt->temperature, static_cast<float *>(dth), stream);
                 cudaEventRecord(e1, st);
                 if (run) ssa_destroy_run(run);
-                run = nullptr;
-                if (s == SSA_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms_best, e0, e1);
+                if (s == SSA_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
             }
-            std::vector<int> hd((size_t)n);
             if (s == SSA_OK && cudaMemcpy(hd.data(), dr, (size_t)n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
                 s = set_error(SSA_ERR_CUDA, "pilot copy failed");
-            cudaFree(ws); cudaFree(obs); cudaFree(dl); cudaFree(dth); cudaFree(dr);
             if (s != SSA_OK) {
                 rc = s;
                 break;
             }
             double sum = 0.0;
-            for (int d : hd) sum += d;
-            if (best < 0.0 || ms_best < best) {
-                best = ms_best;
+            for (int64_t q = 0; q < n; ++q) sum += hd[q];
+            if (best < 0.0 || ms < best) {
+                best = ms;
                 best_v = v;
                 best_draws = std::max(1.0, sum / (double)n);
             }
@@ -755,8 +767,13 @@ extern "C" ssa_status ssa_batch_autotune(ssa_batch *bt, int64_t pilot_traj, void
         bt->est_draws[it] = best_draws;
         if (host_draws_out) host_draws_out[it] = best_draws;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(ws);
+    cudaFree(obs);
+    cudaFree(dl);
+    cudaFree(dth);
+    cudaFree(dr);
     bt->ready = false;
     bt->ws = nullptr;
     drop_graph(bt);

@@ -1,0 +1,248 @@
+// ssa_device.cuh -- device arithmetic and kernel parameter blocks shared by the library's kernels
+// and by the network-specialised kernels compiled at run time (NVRTC), so both evaluate every step with
+// the same instructions in the same order.
+#pragma once
+
+#ifdef __CUDACC_RTC__
+#define CUDART_INF_F __int_as_float(0x7f800000)
+#else
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#endif
+
+#include "../../include/ssa.h"
+
+namespace ssa {
+
+// per-step uniform mapping: u = ((x >> 9) + 1/2) 2^-23, exact in binary32. Built from the bits:
+// 1 + m 2^-23 (m = x >> 9 placed in the mantissa of 1.0) minus (1 - 2^-24) is exactly
+// m 2^-23 + 2^-24, so no integer-to-float conversion is needed.
+__device__ __forceinline__ float u01(uint32_t x)
+{
+    return __fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0x1.fffffep-1f);
+}
+
+// Exact int -> binary32 for 0 <= x < 2^23 through the bits of 2^23 + x (the integer pipe), with the
+// plain conversion for other values.
+__device__ __forceinline__ float int2f(int x)
+{
+    if ((unsigned)x < (1u << 23)) return __fsub_rn(__uint_as_float(0x4B000000u | (unsigned)x), 8388608.0f);
+    return __int2float_rn(x);
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, two 32x32->64 products each,
+// round keys bumped by the two Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &r, int q)
+{
+    return q == 0 ? r.x : q == 1 ? r.y : q == 2 ? r.z : r.w;
+}
+
+// Mass-action combinatorial factor h_j(X) (Section 2): 1, X_i, X_i X_l or X_i (X_i - 1)/2, equal
+// to the exact integer rounded once to binary32. Counts below 2^24 are exact in binary32, so one
+// correctly rounded binary32 product gives the same value as the exact 64-bit product rounded
+// once; larger counts take the 64-bit route.
+__device__ __forceinline__ float h_first(int x1) { return int2f(x1); }
+
+__device__ __forceinline__ float h_homodimer(int x1)
+{
+    if (x1 < 2) return 0.0f;
+    if (x1 < (1 << 23)) return __fmul_rn(int2f(x1), int2f(x1 - 1)) * 0.5f;
+    return __ll2float_rn(((long long)x1 * (x1 - 1)) >> 1);
+}
+
+__device__ __forceinline__ float h_hetero(int x1, int x2)
+{
+    if ((x1 | x2) < (1 << 23)) return __fmul_rn(int2f(x1), int2f(x2));
+    return __ll2float_rn((long long)x1 * x2);
+}
+
+__device__ __forceinline__ float mass_action_h(const int4 rx, const int *X, int stride)
+{
+    if (rx.x < 0) return 1.0f;
+    const int x1 = X[rx.x * stride];
+    if (rx.y < 0) return h_first(x1);
+    if (rx.y == rx.x) return h_homodimer(x1);
+    return h_hetero(x1, X[rx.y * stride]);
+}
+
+// a > b for non-negative, non-NaN binary64 values: IEEE 754 orders them like their bit patterns
+// read as unsigned integers, so the comparison runs on the integer pipe instead of the FP64 pipe.
+__device__ __forceinline__ bool gt_nonneg(double a, double b)
+{
+    return (unsigned long long)__double_as_longlong(a) > (unsigned long long)__double_as_longlong(b);
+}
+
+// binary64 -> binary32, round to nearest even, for a non-negative value in the binary32 normal
+// range, from the IEEE 754 fields on the integer pipe (other values take the plain conversion):
+// the 52-bit fraction is cut to 23 bits and rounded on the 29 dropped bits; a carry out of the
+// fraction increments the exponent field, as it should.
+__device__ __forceinline__ float d2f_nonneg(double d)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const int e = (int)(hi >> 20) - 896;  // binary32 exponent field
+    if (e >= 1 && e <= 254 && (hi >> 31) == 0) {
+        uint32_t f = ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t r = lo & 0x1fffffffu;
+        f += (r > 0x10000000u) || (r == 0x10000000u && (f & 1u));
+        return __uint_as_float(f);
+    }
+    return __double2float_rn(d);
+}
+
+// binary32 -> binary64 for a positive normal value by re-biasing the exponent field (IEEE 754
+// layouts), which keeps the conversion off the FP64 pipe; other values take the plain conversion.
+__device__ __forceinline__ double f2d_pos(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    if (b - 0x00800000u < 0x7f000000u) return __hiloint2double((int)((b >> 3) + 0x38000000u), (int)(b << 29));
+    return (double)x;
+}
+
+__device__ __forceinline__ int stoich_species(int e) { return e >> 8; }
+__device__ __forceinline__ int stoich_delta(int e) { return (int)(signed char)(e & 0xff); }
+
+// Exponential variates of one step, E[q] = -ln u_q for the first NQ words of the step's Philox
+// stream (q = 0 drives the waiting time, q = 1 + j reaction j). They do not depend on the state,
+// so the kernels draw the next step's variates while the current step's state-dependent chain
+// runs (instruction-level parallelism at low occupancy).
+template <int NQ>
+__device__ __forceinline__ void step_noise(float (&E)[NQ], uint32_t k, uint32_t c2, uint32_t c3, uint32_t key0,
+                                           uint32_t key1)
+{
+#pragma unroll
+    for (int b = 0; b < (NQ + 3) / 4; ++b) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
+        if (4 * b + 0 < NQ) E[4 * b + 0] = -logf(u01(r.x));
+        if (4 * b + 1 < NQ) E[4 * b + 1] = -logf(u01(r.y));
+        if (4 * b + 2 < NQ) E[4 * b + 2] = -logf(u01(r.z));
+        if (4 * b + 3 < NQ) E[4 * b + 3] = -logf(u01(r.w));
+    }
+}
+
+// -ln u_q of one word (runtime-indexed variant for networks without a compile-time size).
+__device__ __forceinline__ float exp_variate(uint32_t k, int q, uint32_t c2, uint32_t c3, uint32_t key0, uint32_t key1,
+                                             uint4 &cache, int &cached_b)
+{
+    const int b = q >> 2;
+    if (b != cached_b) {
+        cache = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
+        cached_b = b;
+    }
+    return -logf(u01(word_of(cache, q & 3)));
+}
+
+// The Gumbel-max choice as an exponential race: argmax_j a_j/E_j, compared as a_j E_b > a_b E_j
+// (binary32 products); ties keep the lowest j. The adjoint repeats the identical comparisons.
+__device__ __forceinline__ void race(float a, float E, int j, float &ab, float &Eb, int &jb)
+{
+    if (__fmul_rn(a, Eb) > __fmul_rn(ab, E)) {
+        ab = a;
+        Eb = E;
+        jb = j;
+    }
+}
+
+// Increments of the state adjoint dL/dX from one reaction (mass action): the choice path
+// psi * dlog a/dX (only where a > 0) and the waiting-time path c_tau * dh/dX with c_tau = dL/da0 * k
+// (polynomial derivative, also where a = 0). xs is the species' own count, xo the other reactant's.
+__device__ __forceinline__ float sadj_first(float xs, float a, float psi, float c_tau)
+{
+    return (a > 0.0f ? __fdividef(psi, xs) : 0.0f) + c_tau;
+}
+
+__device__ __forceinline__ float sadj_homodimer(float xs, float a, float h, float psi, float c_tau)
+{
+    const float dh = xs - 0.5f;  // d/dX [X (X - 1)/2]
+    return (a > 0.0f ? __fdividef(psi * dh, h) : 0.0f) + c_tau * dh;
+}
+
+__device__ __forceinline__ float sadj_hetero(float xs, float xo, float a, float psi, float c_tau)
+{
+    return (a > 0.0f ? __fdividef(psi, xs) : 0.0f) + c_tau * xo;
+}
+
+// Error bits written to the workspace flag word by kernels.
+constexpr int kErrStageTimeout = 1;
+constexpr int kErrBadSamples = 2;
+constexpr int kErrBadObs = 4;
+
+
+// ------------------------------------------------------------------------------------------
+// Kernel parameter blocks
+// ------------------------------------------------------------------------------------------
+struct FwdParams {
+    const int4 *rx;
+    const float *k_rates;  // [M padded to 4]
+    uint32_t tab_bytes, k_bytes;
+    int N, M, Mp, nnz;  // Mp: padded reaction count, >= M + 1, multiple of 4, >= the unrolled width
+    uint32_t inc_off, inc_list_off;  // byte offsets of the species -> reactant-slot incidence in the tables
+    int64_t n_traj;
+    uint64_t traj_offset, seed;
+    const int *x0;
+    int x0_per_traj;
+    double t_end;
+    const double *ts;
+    int S;
+    const int *obs_sp;
+    int n_obs;
+    int64_t max_steps;
+    void *obs_out;
+    int *draws, *status;
+    const int *flag;  // workspace error flags (bad sample times -> every trajectory BAD_INPUT)
+    int *err;
+    // record
+    int K;
+    uint4 *ev;        // [ev_rows][n_traj], 8 uint16 events per uint4
+    int *ckpt;        // [n_ckpt][N][n_traj]
+    int *brk_k;       // [S][n_traj]
+    float *brk_a;     // [S][n_traj]
+    int *xfinal;      // [N][n_traj]
+    // replay
+    const uint16_t *ev_in;
+    const int *n_ev_in;
+    int64_t ev_in_stride;
+};
+
+struct AdjParams {
+    const int4 *rx;
+    const float *k_rates;
+    uint32_t tab_bytes, k_bytes;
+    int N, M, Mp, nnz;  // Mp: padded reaction count, >= M + 1, multiple of 4, >= the unrolled width
+    uint32_t inc_off, inc_list_off;  // byte offsets of the species -> reactant-slot incidence in the tables
+    int64_t n_traj;
+    uint64_t traj_offset, seed;
+    const double *ts;
+    int S;
+    const int *obs_sp;
+    int n_obs;
+    int K;
+    const int *draws, *status;
+    const uint4 *ev;
+    const int *ckpt;
+    const int *brk_k;
+    const float *brk_a;
+    const int *xfinal;
+    const float *dl_dobs;
+    int64_t dl_stride;  // elements between trajectories (0 = shared)
+    float invT;
+    float *partial;   // [gridDim.x][M]
+    int *mismatch;    // backward consistency failures
+    int *err;
+};
+
+
+}  // namespace ssa

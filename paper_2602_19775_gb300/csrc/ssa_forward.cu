@@ -208,6 +208,21 @@ cudaError_t launch_ensemble_mean(const void *obs, bool is_int, int64_t n_traj, i
     return cudaGetLastError();
 }
 
+// out[c] = sum over rows of x[row][c], in fixed chunks of rows and then over chunks (deterministic)
+cudaError_t launch_column_sums(const float *x, int64_t n_rows, int64_t row_len, float *partial, int64_t chunk, float *out,
+                               cudaStream_t st)
+{
+    if (row_len == 0) return cudaSuccess;
+    const int64_t n_chunks = (n_rows + chunk - 1) / chunk;
+    if (n_chunks > 65535) return cudaErrorInvalidValue;
+    if (n_chunks > 0) {
+        dim3 g((unsigned)((row_len + 127) / 128), (unsigned)n_chunks);
+        colsum_chunks_kernel<float><<<g, 128, 0, st>>>(x, n_rows, row_len, chunk, partial);
+    }
+    colsum_final_kernel<<<(unsigned)((row_len + 127) / 128), 128, 0, st>>>(partial, n_chunks, row_len, 1.0f, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_philox_uniforms(uint64_t seed, const uint64_t *traj, const uint64_t *step, int64_t n, int n_words,
                                    float *out, cudaStream_t st)
 {

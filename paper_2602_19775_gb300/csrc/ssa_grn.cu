@@ -21,6 +21,7 @@
 // hi/lo limbs of G), and dW2 = sum_k G2_k h_k^T by summation by parts: with R = sum_{m >= k} G2_m
 // accumulated backwards, undoing an event that changed h_i by delta adds delta R to dW2[:, i]
 // (h starts at zero), so each step costs O(n_out) instead of O(n_out n_hid).
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -35,6 +36,8 @@ cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, co
                                    float *dA_tmp, float *dtheta, cudaStream_t st);
 cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N, int *flag,
                                   cudaStream_t st);
+cudaError_t launch_column_sums(const float *x, int64_t n_rows, int64_t row_len, float *partial, int64_t chunk, float *out,
+                               cudaStream_t st);
 
 constexpr int kGrnLimbs = 8;       // 6-bit limbs of W1 on one grid: 48 bits of dynamic range
 constexpr int kGrnLimbBits = 6;
@@ -69,7 +72,8 @@ struct GrnParams {
     int64_t dl_stride;
     float invT;
     float *G1;            // [n_traj][n_hid]
-    float *partial;       // [blocks][n_out n_hid + n_out + n_dyn]
+    float *dW2t;          // [n_traj][n_out n_hid]: per-trajectory dL/dW2
+    float *partial;       // [blocks][n_out + n_dyn]
     int *mismatch;
 };
 
@@ -328,15 +332,14 @@ __global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, W = blockDim.x >> 5;
     const int nh = p.n_hid, no = p.n_out, nd = p.n_dyn, Mp = p.Mp;
-    int *s_W2fix = reinterpret_cast<int *>(smem);
-    float *s_W2f = reinterpret_cast<float *>(s_W2fix + no * nh);
-    float *s_d = s_W2f + no * nh;
+    float *s_d = reinterpret_cast<float *>(smem);
     float *s_b2 = s_d + nd;
     const int ndp = (nd + 3) & ~3, nhp = (nh + 3) & ~3, nop = (no + 3) & ~3;
     // per warp (words): X, lam, ctd [ndp each], aH, G1 [nhp each], E2acc [2 nop], aO, G2, R, db2 [nop each],
-    // aj, lj [Mp each], dW2 [no nh], dlogd [ndp]
-    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + 6 * (size_t)nop + 2 * (size_t)Mp + (size_t)no * nh;
-    unsigned char *wb = smem + 4 * (2 * (size_t)no * nh + nd + nop);
+    // aj, lj [Mp each], dlogd [ndp]. dL/dW2 goes to the trajectory's own row of p.dW2t (global, L2-resident
+    // while the warp works on it), which keeps the per-warp shared memory independent of n_out x n_hid.
+    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + 6 * (size_t)nop + 2 * (size_t)Mp;
+    unsigned char *wb = smem + 4 * ((size_t)nd + nop);
     wb = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(wb) + 15) & ~(uintptr_t)15);
     float *wbase = reinterpret_cast<float *>(wb) + wib * per_warp;
     int *X = reinterpret_cast<int *>(wbase);
@@ -351,16 +354,12 @@ __global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
     float *db2 = R + nop;
     float *aj = db2 + nop;
     float *lj = aj + Mp;
-    float *dW2 = lj + Mp;
-    float *dlogd = dW2 + (size_t)no * nh;
+    float *dlogd = lj + Mp;
+    const int *__restrict__ W2fix = p.W2fix;
+    const float *__restrict__ W2f = p.W2f;
 
-    for (int q = threadIdx.x; q < no * nh; q += blockDim.x) {
-        s_W2fix[q] = p.W2fix[q];
-        s_W2f[q] = p.W2f[q];
-    }
     for (int q = threadIdx.x; q < nd; q += blockDim.x) s_d[q] = p.dvec[q];
     for (int q = threadIdx.x; q < no; q += blockDim.x) s_b2[q] = p.b2[q];
-    for (int q = lane; q < no * nh; q += 32) dW2[q] = 0.0f;
     for (int q = lane; q < nd; q += 32) dlogd[q] = 0.0f;
     for (int q = lane; q < no; q += 32) db2[q] = 0.0f;
     __syncthreads();
@@ -370,6 +369,9 @@ __global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
     int st = -1;
     if (i < n) st = p.status[i];
     const bool active = st == SSA_TRAJ_OK || st == SSA_TRAJ_ABSORBED || st == SSA_TRAJ_STEP_CAP;
+    float *dW2 = p.dW2t + (i < n ? i : 0) * (int64_t)no * nh;
+    if (i < n)
+        for (int q = lane; q < no * nh; q += 32) dW2[q] = 0.0f;
     if (active) {
         const float scale = exp2f((float)p.grid[0]);
         const float *E1 = p.E1 + (i / p.tpi) * nh;
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
         // E2 at the final state, exactly (integer fixed point)
         for (int o = lane; o < no; o += 32) {
             long long acc = 0;
-            for (int h = 0; h < nh; ++h) acc += (long long)s_W2fix[o * nh + h] * X[h];
+            for (int h = 0; h < nh; ++h) acc += (long long)__ldg(W2fix + o * nh + h) * X[h];
             E2acc[o] = acc;
             aO[o] = p.k_max * sigmoid_f(e2_value(acc, scale, s_b2[o]));
             R[o] = 0.0f;
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
                 for (int s = lane; s < nd; s += 32) {
                     float acc = ctd[s];
                     if (s < nh)
-                        for (int o = 0; o < no; ++o) acc += s_W2f[o * nh + s] * G2[o];
+                        for (int o = 0; o < no; ++o) acc += __ldg(W2f + o * nh + s) * G2[o];
                     lam[s] += acc;
                 }
             }
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
                 if (sp < nh) {
                     for (int o = lane; o < no; o += 32) {
                         dW2[o * nh + sp] += (float)delta * R[o];
-                        E2acc[o] -= (long long)delta * s_W2fix[o * nh + sp];
+                        E2acc[o] -= (long long)delta * __ldg(W2fix + o * nh + sp);
                         aO[o] = p.k_max * sigmoid_f(e2_value(E2acc[o], scale, s_b2[o]));
                     }
                 }
@@ -530,18 +532,14 @@ __global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
         for (int h = lane; h < nh; h += 32) p.G1[i * nh + h] = 0.0f;
     }
     __syncthreads();
-    // fixed-order sum over the block's warps: [dW2 | db2 | dlogd]
-    const int red = no * nh + no + nd;
+    // fixed-order sum over the block's warps: [db2 | dlogd]
+    const int red = no + nd;
     float *base0 = reinterpret_cast<float *>(wb);
     for (int q = threadIdx.x; q < red; q += blockDim.x) {
         float acc = 0.0f;
         for (int w = 0; w < W; ++w) {
             const float *wp = base0 + w * per_warp;
-            const float *v;
-            if (q < no * nh) v = wp + 3 * ndp + 2 * nhp + 6 * nop + 2 * Mp + q;  // dW2
-            else if (q < no * nh + no) v = wp + 3 * ndp + 2 * nhp + 5 * nop + (q - no * nh);  // db2
-            else v = wp + 3 * ndp + 2 * nhp + 6 * nop + 2 * Mp + no * nh + (q - no * nh - no);  // dlogd
-            acc += *v;
+            acc += q < no ? wp[3 * ndp + 2 * nhp + 5 * nop + q] : wp[3 * ndp + 2 * nhp + 6 * nop + 2 * Mp + (q - no)];
         }
         p.partial[(int64_t)blockIdx.x * red + q] = acc;
     }
@@ -585,13 +583,11 @@ __global__ void grn_transpose_x_kernel(const int32_t *x_img, int64_t n_img, int 
     }
 }
 
-__global__ void grn_split_partials_kernel(const float *red, int no, int nh, int nd, float *dW2, float *db2,
-                                          float *dlogd)
+__global__ void grn_split_partials_kernel(const float *red, int no, int nd, float *db2, float *dlogd)
 {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < no * nh + no + nd; q += gridDim.x * blockDim.x) {
-        if (q < no * nh) dW2[q] = red[q];
-        else if (q < no * nh + no) db2[q - no * nh] = red[q];
-        else dlogd[q - no * nh - no] = red[q];
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < no + nd; q += gridDim.x * blockDim.x) {
+        if (q < no) db2[q] = red[q];
+        else dlogd[q - no] = red[q];
     }
 }
 
@@ -617,7 +613,7 @@ WsLayout grn_layout(const ssa_grn *g, int64_t n_img, int64_t tpi, int32_t S, con
     L.n_in_pad = (g->n_in + 7) / 8 * 8;
     L.n_img_pad = (int)((n_img + 7) / 8 * 8);
     L.limbs = kGrnLimbs;
-    L.red_len = g->n_out * g->n_hid + g->n_out + g->n_dyn;
+    L.red_len = g->n_out + g->n_dyn;
     L.M_pad = g->Mp;
     L.flag = take(16 * sizeof(int));
     L.counts = take(SSA_TRAJ_N_CODES * sizeof(unsigned long long));
@@ -650,6 +646,9 @@ WsLayout grn_layout(const ssa_grn *g, int64_t n_img, int64_t tpi, int32_t S, con
         L.Gt = take((size_t)2 * g->n_hid * L.n_img_pad * 2);
         L.xT = take((size_t)g->n_in * L.n_img_pad * 2);
         L.red = take((size_t)L.red_len * 4);
+        L.dW2t = take((size_t)(n > 0 ? n : 1) * g->n_out * g->n_hid * 4);
+        L.dW2_chunk = std::max<int64_t>(256, (n + 65534) / 65535);
+        L.dW2p = take((size_t)((n + L.dW2_chunk - 1) / L.dW2_chunk + 1) * g->n_out * g->n_hid * 4);
     }
     L.total = off;
     return L;
@@ -664,9 +663,8 @@ size_t grn_fwd_smem(const ssa_grn *g)
 size_t grn_adj_smem(const ssa_grn *g)
 {
     const int ndp = (g->n_dyn + 3) & ~3, nhp = (g->n_hid + 3) & ~3, nop = (g->n_out + 3) & ~3;
-    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + 6 * (size_t)nop + 2 * (size_t)g->Mp +
-                            (size_t)g->n_out * g->n_hid;
-    return 4 * (2 * (size_t)g->n_out * g->n_hid + g->n_dyn + nop) + 16 + 4 * (size_t)kGrnWarps * per_warp;
+    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + 6 * (size_t)nop + 2 * (size_t)g->Mp;
+    return 4 * ((size_t)g->n_dyn + nop) + 16 + 4 * (size_t)kGrnWarps * per_warp;
 }
 
 #define GRN_CUDA_TRY(expr)                                                                              \
@@ -878,6 +876,7 @@ extern "C" ssa_status ssa_grn_backward(ssa_run *run, const float *dl_dobs, int64
     p.dl_stride = dl_traj_stride;
     p.invT = 1.0f / temperature;
     p.G1 = reinterpret_cast<float *>(ws + L.G1);
+    p.dW2t = reinterpret_cast<float *>(ws + L.dW2t);
     p.partial = reinterpret_cast<float *>(ws + L.partial);
     p.mismatch = flag + 2;
     p.err = flag + 1;
@@ -890,8 +889,9 @@ extern "C" ssa_status ssa_grn_backward(ssa_run *run, const float *dl_dobs, int64
         GRN_CUDA_TRY(cudaGetLastError());
     }
     GRN_CUDA_TRY(launch_reduce_partials(p.partial, nblk, L.red_len, nullptr, 0, red, nullptr, st));
-    grn_split_partials_kernel<<<(L.red_len + 255) / 256, 256, 0, st>>>(red, g->n_out, g->n_hid, g->n_dyn, dW2, db2,
-                                                                        dlog_d);
+    grn_split_partials_kernel<<<(L.red_len + 255) / 256, 256, 0, st>>>(red, g->n_out, g->n_dyn, db2, dlog_d);
+    GRN_CUDA_TRY(launch_column_sums(p.dW2t, n, (int64_t)g->n_out * g->n_hid, reinterpret_cast<float *>(ws + L.dW2p),
+                                    L.dW2_chunk, dW2, st));
     uint16_t *Gt = reinterpret_cast<uint16_t *>(ws + L.Gt);
     uint16_t *xT = reinterpret_cast<uint16_t *>(ws + L.xT);
     const size_t gt_len = (size_t)g->n_hid * L.n_img_pad;

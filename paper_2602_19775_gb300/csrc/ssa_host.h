@@ -3,6 +3,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
+#include <vector>
 
 #include "ssa_internal.cuh"
 
@@ -16,6 +18,10 @@ struct ssa_network {
     int *d_stoich;
     int *d_rate_index;
     uint32_t tab_bytes;
+    // host copies of the reaction table and stoichiometry (canonical slot order), from which the
+    // network-specialised kernels are generated
+    std::vector<int4> h_rx;
+    std::vector<int> h_st;
 };
 
 struct ssa_grn {
@@ -31,15 +37,16 @@ struct WsLayout {
     int64_t ev_rows, n_ckpt, max_blocks;
     int M_pad;
     // gene-regulatory-network runs
-    size_t E1, W1L, xb, W2fix, W2f, dvec, grid, G1, Gimg, Gt, xT, red;
+    size_t E1, W1L, xb, W2fix, W2f, dvec, grid, G1, Gimg, Gt, xT, red, dW2t, dW2p;
     int n_in_pad, n_img_pad, limbs, red_len;
+    int64_t dW2_chunk;
 };
 ssa_status set_error(ssa_status code, const char *text);
 }  // namespace ssa
 
 struct ssa_run {
     const ssa_network *net;
-    int variant;  // 1: thread per trajectory, 32: warp per trajectory
+    int variant;  // 1: thread per trajectory, 2: thread per trajectory, network-specialised, 32: warp
     const ssa_grn *grn;  // non-null for a gene-regulatory-network run
     int64_t n_img, traj_per_img;
     const int32_t *x_img;  // caller's inputs, kept alive by the caller until the backward

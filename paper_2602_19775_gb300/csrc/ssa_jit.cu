@@ -1,0 +1,260 @@
+// ssa_jit.cu -- network-specialised kernels compiled at run time with NVRTC.
+//
+// For a network with few species and reactions, the thread-per-trajectory forward and adjoint are
+// generated with the network written into the code: the reactant indices, orders and stoichiometric
+// changes become constants, so the counts X and the state adjoint lambda live in registers, every
+// propensity is a fixed expression, and the update X += v_j is a switch over j with immediate
+// increments. The per-step arithmetic is the generic kernels' (the shared helpers of ssa_device.cuh
+// in the same order), so both give the same trajectories bit for bit; only the table lookups and
+// the shared-memory traffic go away. The generated source is compiled once per distinct network and
+// process (cached for its lifetime) for sm_103a and loaded as a context-independent CUDA library.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <nvrtc.h>
+
+#include "ssa_host.h"
+#include "ssa_jit_text.h"  // generated by build.py: the texts of ssa_device.cuh, ssa_jit_body.cuh, ssa.h
+
+namespace ssa {
+
+constexpr int kJitMaxSpecies = 24;
+constexpr int kJitMaxReactions = 24;
+constexpr int kJitMaxNnz = 96;
+
+struct JitKernels {
+    cudaKernel_t fwd[2][2];  // [readout][record]
+    cudaKernel_t adj[2];     // [readout]
+};
+
+namespace {
+
+std::mutex g_jit_mu;
+// source text -> kernels; libraries stay loaded until the process exits
+std::map<std::string, JitKernels> g_jit_cache;
+std::map<std::string, std::string> g_jit_failed;  // source text -> reason
+
+void emit(std::string &out, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+void emit(std::string &out, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    out += buf;
+}
+
+int st_species(int e) { return e >> 8; }
+int st_delta(int e) { return (int)(signed char)(e & 0xff); }
+
+// The network hooks that ssa_jit_body.cuh calls, written out for one network.
+std::string jit_source(const ssa_network *net)
+{
+    const int N = net->N, M = net->M;
+    std::string s;
+    s += "#include \"ssa_device.cuh\"\n";
+    emit(s, "#define JN %d\n#define JM %d\nnamespace ssa {\n", N, M);
+    // propensities, in reaction order
+    s += "__device__ __forceinline__ void jit_props(const int (&X)[JN], const float (&k)[JM], float (&a)[JM], "
+         "float (&h)[JM])\n{\n";
+    for (int j = 0; j < M; ++j) {
+        const int4 r = net->h_rx[j];
+        if (r.x < 0) emit(s, "    h[%d] = 1.0f;\n", j);
+        else if (r.y < 0) emit(s, "    h[%d] = h_first(X[%d]);\n", j, r.x);
+        else if (r.y == r.x) emit(s, "    h[%d] = h_homodimer(X[%d]);\n", j, r.x);
+        else emit(s, "    h[%d] = h_hetero(X[%d], X[%d]);\n", j, r.x, r.y);
+        emit(s, "    a[%d] = __fmul_rn(k[%d], h[%d]);\n", j, j, j);
+    }
+    s += "}\n";
+    // range check of X + v_jb (entries in table order; the last failing entry decides)
+    s += "__device__ __forceinline__ int jit_check(const int (&X)[JN], int jb)\n{\n    int st = SSA_TRAJ_OK;\n"
+         "    switch (jb) {\n";
+    for (int j = 0; j < M; ++j) {
+        emit(s, "    case %d:\n", j);
+        for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e) {
+            const int sp = st_species(net->h_st[e]), d = st_delta(net->h_st[e]);
+            if (d < 0) emit(s, "        if (X[%d] + (%d) < 0) st = SSA_TRAJ_NEG_COUNT;\n", sp, d);
+            else if (d > 0) emit(s, "        if (X[%d] > 2147483647 - %d) st = SSA_TRAJ_OVERFLOW;\n", sp, d);
+        }
+        s += "        break;\n";
+    }
+    s += "    default: break;\n    }\n    return st;\n}\n";
+    // X += v_jb and X -= v_jb
+    for (int dir = 0; dir < 2; ++dir) {
+        emit(s, "__device__ __forceinline__ void %s(int (&X)[JN], int jb)\n{\n    switch (jb) {\n",
+             dir == 0 ? "jit_apply" : "jit_unapply");
+        for (int j = 0; j < M; ++j) {
+            emit(s, "    case %d:\n", j);
+            for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e)
+                emit(s, "        X[%d] %s %d;\n", st_species(net->h_st[e]), dir == 0 ? "+=" : "-=", st_delta(net->h_st[e]));
+            s += "        break;\n";
+        }
+        s += "    default: break;\n    }\n}\n";
+    }
+    // component sp of v_jb
+    s += "__device__ __forceinline__ int jit_dv(int jb, int sp)\n{\n    int v = 0;\n    switch (jb) {\n";
+    for (int j = 0; j < M; ++j) {
+        emit(s, "    case %d:\n", j);
+        for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e)
+            emit(s, "        if (sp == %d) v += %d;\n", st_species(net->h_st[e]), st_delta(net->h_st[e]));
+        s += "        break;\n";
+    }
+    s += "    default: break;\n    }\n    return v;\n}\n";
+    // w_j = v_j . lambda, summed over the entries in table order from zero
+    s += "__device__ __forceinline__ void jit_w(const float (&lam)[JN], float (&w)[JM])\n{\n";
+    for (int j = 0; j < M; ++j) {
+        s += "    {\n        float v = 0.0f;\n";
+        for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e)
+            emit(s, "        v += (float)(%d) * lam[%d];\n", st_delta(net->h_st[e]), st_species(net->h_st[e]));
+        emit(s, "        w[%d] = v;\n    }\n", j);
+    }
+    s += "}\n";
+    // state adjoint of every reaction, in order
+    s += "__device__ __forceinline__ void jit_state_adj(const int (&X)[JN], const float (&a)[JM], const float (&h)[JM], "
+         "const float (&psi)[JM], const float (&ctau)[JM], float (&lam)[JN])\n{\n";
+    for (int j = 0; j < M; ++j) {
+        const int4 r = net->h_rx[j];
+        if (r.x < 0) continue;
+        if (r.y < 0) {
+            emit(s, "    lam[%d] += sadj_first(int2f(X[%d]), a[%d], psi[%d], ctau[%d]);\n", r.x, r.x, j, j, j);
+        } else if (r.y == r.x) {
+            emit(s, "    lam[%d] += sadj_homodimer(int2f(X[%d]), a[%d], h[%d], psi[%d], ctau[%d]);\n", r.x, r.x, j, j,
+                 j, j);
+        } else {
+            emit(s, "    {\n        const float x1 = int2f(X[%d]), x2 = int2f(X[%d]);\n", r.x, r.y);
+            emit(s, "        lam[%d] += sadj_hetero(x1, x2, a[%d], psi[%d], ctau[%d]);\n", r.x, j, j, j);
+            emit(s, "        lam[%d] += sadj_hetero(x2, x1, a[%d], psi[%d], ctau[%d]);\n    }\n", r.y, j, j, j);
+        }
+    }
+    s += "}\n}  // namespace ssa\n#include \"ssa_jit_body.cuh\"\n";
+    return s;
+}
+
+const char *kStddef = "#pragma once\ntypedef unsigned long size_t;\n";
+const char *kStdint =
+    "#pragma once\ntypedef signed char int8_t;\ntypedef short int16_t;\ntypedef int int32_t;\ntypedef long int64_t;\n"
+    "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\ntypedef unsigned int uint32_t;\n"
+    "typedef unsigned long uint64_t;\ntypedef unsigned long uintptr_t;\n";
+
+bool compile(const std::string &src, std::vector<char> &cubin, std::string &why)
+{
+    const char *hdr_text[] = {kJitTextDevice, kJitTextBody, kJitTextApi, kStddef, kStdint};
+    const char *hdr_name[] = {"ssa_device.cuh", "ssa_jit_body.cuh", "../../include/ssa.h", "stddef.h", "stdint.h"};
+    nvrtcProgram prog;
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "ssa_network.cu", 5, hdr_text, hdr_name);
+    if (r != NVRTC_SUCCESS) {
+        why = nvrtcGetErrorString(r);
+        return false;
+    }
+    // -default-device: the C declarations of ssa.h (for its constants) are read as device declarations
+    const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "--fmad=true", "-default-device"};
+    r = nvrtcCompileProgram(prog, 4, opts);
+    if (r != NVRTC_SUCCESS) {
+        size_t n = 0;
+        nvrtcGetProgramLogSize(prog, &n);
+        std::string log(n, '\0');
+        if (n) nvrtcGetProgramLog(prog, &log[0]);
+        why = std::string(nvrtcGetErrorString(r)) + ": " + log.substr(0, 400);
+        nvrtcDestroyProgram(&prog);
+        return false;
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    cubin.resize(n);
+    nvrtcGetCUBIN(prog, cubin.data());
+    nvrtcDestroyProgram(&prog);
+    return n > 0;
+}
+
+}  // namespace
+
+bool jit_eligible(const ssa_network *net)
+{
+    return net->N <= kJitMaxSpecies && net->M <= kJitMaxReactions && net->nnz <= kJitMaxNnz;
+}
+
+// Kernels of `net`, compiling and loading them on first use. Returns nullptr (with the reason in `why`)
+// if the network is not eligible or compilation failed.
+const JitKernels *jit_kernels(const ssa_network *net, std::string &why)
+{
+    if (!jit_eligible(net)) {
+        why = "network above the specialisation limits (24 species, 24 reactions, 96 stoichiometric entries)";
+        return nullptr;
+    }
+    const std::string src = jit_source(net);
+    std::lock_guard<std::mutex> lock(g_jit_mu);
+    auto f = g_jit_failed.find(src);
+    if (f != g_jit_failed.end()) {
+        why = f->second;
+        return nullptr;
+    }
+    auto it = g_jit_cache.find(src);
+    if (it != g_jit_cache.end()) return &it->second;
+    std::vector<char> cubin;
+    if (!compile(src, cubin, why)) {
+        g_jit_failed[src] = why;
+        return nullptr;
+    }
+    cudaLibrary_t lib = nullptr;
+    cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) {
+        why = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
+        g_jit_failed[src] = why;
+        return nullptr;
+    }
+    JitKernels k{};
+    const char *fwd_names[2][2] = {{"ssa_jit_fwd_hold", "ssa_jit_fwd_hold_rec"},
+                                   {"ssa_jit_fwd_linear", "ssa_jit_fwd_linear_rec"}};
+    const char *adj_names[2] = {"ssa_jit_adj_hold", "ssa_jit_adj_linear"};
+    bool ok = true;
+    for (int r = 0; r < 2; ++r) {
+        for (int rec = 0; rec < 2; ++rec) ok &= cudaLibraryGetKernel(&k.fwd[r][rec], lib, fwd_names[r][rec]) == cudaSuccess;
+        ok &= cudaLibraryGetKernel(&k.adj[r], lib, adj_names[r]) == cudaSuccess;
+    }
+    if (!ok) {
+        why = "a specialised kernel is missing from the library";
+        g_jit_failed[src] = why;
+        cudaLibraryUnload(lib);
+        return nullptr;
+    }
+    return &(g_jit_cache[src] = k);
+}
+
+cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int readout, bool record, int block,
+                               cudaStream_t st)
+{
+    if (p.n_traj == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((p.n_traj + block - 1) / block);
+    void *args[] = {const_cast<FwdParams *>(&p)};
+    return cudaLaunchKernel(reinterpret_cast<const void *>(k->fwd[readout == SSA_READOUT_HOLD ? 0 : 1][record ? 1 : 0]),
+                            dim3(grid), dim3((unsigned)block), args, 0, st);
+}
+
+cudaError_t jit_launch_backward(const JitKernels *k, const AdjParams &p, int readout, int block, int64_t grid,
+                                cudaStream_t st)
+{
+    if (grid == 0) return cudaSuccess;
+    void *args[] = {const_cast<AdjParams *>(&p)};
+    const size_t smem = (size_t)4 * p.M * block;
+    return cudaLaunchKernel(reinterpret_cast<const void *>(k->adj[readout == SSA_READOUT_HOLD ? 0 : 1]),
+                            dim3((unsigned)grid), dim3((unsigned)block), args, smem, st);
+}
+
+}  // namespace ssa
+
+using namespace ssa;
+
+extern "C" ssa_status ssa_network_specialize(ssa_network *net, int32_t *host_ok)
+{
+    if (!net || !host_ok) return set_error(SSA_ERR_INVALID_ARG, "NULL argument");
+    std::string why;
+    *host_ok = jit_kernels(net, why) ? 1 : 0;
+    if (!*host_ok) set_error(SSA_OK, why.c_str());
+    return SSA_OK;
+}

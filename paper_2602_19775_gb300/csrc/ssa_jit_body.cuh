@@ -1,0 +1,354 @@
+// ssa_jit_body.cuh -- thread-per-trajectory forward and straight-through adjoint specialised to one
+// network at run time (arXiv 2602.19775, Section 2, Section 3.2, Eqs. 3, 5, 6, 7, Section 3.1).
+//
+// This file is compiled by NVRTC, not by nvcc: the library prepends a generated prologue that
+// defines JN (species), JM (reactions) and the network hooks
+//     jit_props(X, k, a, h)       h_j(X) and a_j = k_j h_j for every reaction, in reaction order
+//     jit_check(X, jb)            status of applying v_jb to X (negative count / overflow)
+//     jit_apply(X, jb), jit_unapply(X, jb)
+//     jit_dv(jb, sp)              component sp of v_jb
+//     jit_w(lam, w)               w_j = v_j . lambda for every reaction
+//     jit_state_adj(X, a, h, psi, ctau, lam)   the state adjoint of every reaction, in order
+// with the reactant indices and stoichiometry written into the code as constants. Counts and the
+// state adjoint then live in registers and every table lookup disappears. The arithmetic is the
+// generic thread kernels' (same helpers from ssa_device.cuh, same order), so a specialised run
+// reproduces the generic run's trajectories bit for bit.
+
+namespace ssa {
+
+__device__ __forceinline__ int jit_xsel(const int (&X)[JN], int sp)
+{
+    int v = 0;
+#pragma unroll
+    for (int s = 0; s < JN; ++s) v = (s == sp) ? X[s] : v;
+    return v;
+}
+
+__device__ __forceinline__ void jit_lam_add(float (&lam)[JN], int sp, float v)
+{
+#pragma unroll
+    for (int s = 0; s < JN; ++s)
+        if (s == sp) lam[s] += v;
+}
+
+template <int READOUT, bool RECORD>
+__device__ __forceinline__ void jit_fwd(const FwdParams &p)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_traj) return;
+    const int64_t n = p.n_traj;
+    float kr[JM];
+#pragma unroll
+    for (int j = 0; j < JM; ++j) kr[j] = p.k_rates[j];
+
+    const int *x0 = p.x0 + (p.x0_per_traj ? i * JN : 0);
+    const bool bad_obs = (*p.flag & kErrBadObs) != 0;
+    bool bad_input = (*p.flag & (kErrBadSamples | kErrBadObs)) != 0;
+    int X[JN];
+#pragma unroll
+    for (int s = 0; s < JN; ++s) {
+        X[s] = x0[s];
+        bad_input |= X[s] < 0;
+    }
+    const uint64_t gid = p.traj_offset + (uint64_t)i;
+    const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32);
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+
+    double t = 0.0;
+    int s = 0;
+    double thr = p.S > 0 ? p.ts[0] : p.t_end;
+    int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
+    int k = 0, draws = 0;
+    int ck_left = p.K, ck_row = 0;
+    uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+    constexpr int NQ = JM + 1;
+    float E[NQ], En[NQ];
+    step_noise<NQ>(E, 0u, c2, c3, key0, key1);
+
+    while (!bad_input) {
+        if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
+        step_noise<NQ>(En, (uint32_t)(k + 1), c2, c3, key0, key1);  // next step, state-independent
+        float a[JM], h[JM];
+        jit_props(X, kr, a, h);
+        float a0 = 0.0f, ab = 0.0f, Eb = 1.0f;
+        int jb = -1;
+        const float E0 = E[0];
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+            a0 = __fadd_rn(a0, a[j]);
+            race(a[j], E[j + 1], j, ab, Eb, jb);
+        }
+        if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
+        if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
+        if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }
+        const float tau = __fdividef(E0, a0);
+        const double t_next = t + f2d_pos(tau);
+        const bool slow = gt_nonneg(t_next, thr);
+        const bool cross = slow && gt_nonneg(t_next, p.t_end);
+        if (!cross) status = jit_check(X, jb);
+        if (RECORD) {
+            e0 = __funnelshift_r(e0, e1, 16);
+            e1 = __funnelshift_r(e1, e2, 16);
+            e2 = __funnelshift_r(e2, e3, 16);
+            e3 = (e3 >> 16) | ((uint32_t)jb << 16);
+            if ((k & 7) == 7) p.ev[(int64_t)(k >> 3) * n + i] = make_uint4(e0, e1, e2, e3);
+        }
+        draws = k + 1;
+        if (status != SSA_TRAJ_OK) break;
+        if (slow) {
+            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
+                if (READOUT == SSA_READOUT_HOLD) {
+                    int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                    for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
+                } else {
+                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
+                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                    for (int c = 0; c < p.n_obs; ++c) {
+                        const int sp = p.obs_sp[c];
+                        o[c] = __fmaf_rn(alpha, (float)jit_dv(jb, sp), (float)jit_xsel(X, sp));
+                    }
+                    if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
+                }
+                if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
+                ++s;
+            }
+            thr = s < p.S ? p.ts[s] : p.t_end;
+            if (cross) break;  // the crossing draw is made but not applied
+        }
+        jit_apply(X, jb);
+        t = t_next;
+        ++k;
+        if (RECORD && --ck_left == 0) {
+            ck_left = p.K;
+            ++ck_row;
+            int *ck = p.ckpt + (int64_t)ck_row * JN * n + i;
+#pragma unroll
+            for (int sp = 0; sp < JN; ++sp) ck[(int64_t)sp * n] = X[sp];
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) E[q] = En[q];
+    }
+    for (; s < p.S; ++s) {
+        if (READOUT == SSA_READOUT_HOLD) {
+            int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+            for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : jit_xsel(X, p.obs_sp[c]);
+        } else {
+            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+            for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)jit_xsel(X, p.obs_sp[c]);
+            if (RECORD) p.brk_a[(int64_t)s * n + i] = -1.0f;
+        }
+        if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
+    }
+    p.draws[i] = draws;
+    p.status[i] = status;
+    if (RECORD) {
+        if (draws & 7) {
+            for (int pad = draws & 7; pad < 8; ++pad) {
+                e0 = __funnelshift_r(e0, e1, 16);
+                e1 = __funnelshift_r(e1, e2, 16);
+                e2 = __funnelshift_r(e2, e3, 16);
+                e3 = e3 >> 16;
+            }
+            p.ev[(int64_t)((draws - 1) >> 3) * n + i] = make_uint4(e0, e1, e2, e3);
+        }
+#pragma unroll
+        for (int sp = 0; sp < JN; ++sp) {
+            p.xfinal[(int64_t)sp * n + i] = X[sp];
+            p.ckpt[(int64_t)sp * n + i] = x0[sp];  // checkpoint 0 = X_0
+        }
+    }
+}
+
+// Per-trajectory adjoint; returns the trajectory's per-reaction adjoints in dAr.
+template <int READOUT>
+__device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&kr)[JM], const int64_t i, const int st,
+                                             float (&dAr)[JM])
+{
+    const int64_t n = p.n_traj;
+    const int d = p.draws[i];
+    const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;  // index of the last visited state
+    int X[JN];
+    float lam[JN];
+#pragma unroll
+    for (int s = 0; s < JN; ++s) {
+        X[s] = p.xfinal[(int64_t)s * n + i];
+        lam[s] = 0.0f;
+    }
+    const uint64_t gid = p.traj_offset + (uint64_t)i;
+    const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32);
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    const float invT = p.invT;
+    const float *gl = p.dl_dobs + i * p.dl_stride;
+
+    int row_cached = -1;
+    uint4 row = make_uint4(0, 0, 0, 0);
+    auto event_at = [&](int kk) -> int {
+        const int r = kk >> 3;
+        if (r != row_cached) { row = p.ev[(int64_t)r * n + i]; row_cached = r; }
+        const int slot = kk & 7;
+        const uint32_t w = word_of(row, slot >> 1);
+        return (slot & 1) ? (int)(w >> 16) : (int)(w & 0xffff);
+    };
+
+    int s_hi = p.S - 1;
+    int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    float mu = 0.0f;
+    int mism = 0;
+    int ck_row = L / p.K, ck_off = L - ck_row * p.K;  // checkpoint c holds X_{cK}
+
+    constexpr int NQ = JM + 1;
+    float E[NQ], En[NQ];
+    const bool draw_last = st == SSA_TRAJ_OK;
+    step_noise<NQ>(E, (uint32_t)(draw_last ? L : (L > 0 ? L - 1 : 0)), c2, c3, key0, key1);
+
+    for (int k = L; k >= 0; --k) {
+        const bool draw = (k < L) || draw_last;
+        const int s_top = s_hi;
+        while (s_hi >= 0 && brk_next == k) {
+            --s_hi;
+            brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+        }
+        // samples s_hi+1 .. s_top are bracketed by state k
+        if (draw) {
+            const int jk = event_at(k);
+            if (k > 0) step_noise<NQ>(En, (uint32_t)(k - 1), c2, c3, key0, key1);  // prefetch
+            float a[JM], h[JM], lr[JM];
+            jit_props(X, kr, a, h);
+            float a0 = 0.0f, ab = 0.0f, Eb = 1.0f, lmax = -CUDART_INF_F;
+            int jb = -1;
+            const float E0 = E[0];
+            // pass 1: the forward's a0 and race, bit for bit; log2 keys
+#pragma unroll
+            for (int j = 0; j < JM; ++j) {
+                a0 = __fadd_rn(a0, a[j]);
+                race(a[j], E[j + 1], j, ab, Eb, jb);
+                lr[j] = a[j] > 0.0f ? __log2f(a[j]) - __log2f(E[j + 1]) : -CUDART_INF_F;
+                lmax = fmaxf(lmax, lr[j]);
+            }
+            mism += (jb != jk);
+            const float tau = __fdividef(E0, a0);
+            // readout terms that involve X_{k+1} and the clock (LINEAR interpolation)
+            float dt_dir = 0.0f, dtau_dir = 0.0f;
+            if (READOUT == SSA_READOUT_LINEAR) {
+                for (int s = s_hi + 1; s <= s_top; ++s) {
+                    const float alpha = p.brk_a[(int64_t)s * n + i];
+                    if (alpha < 0.0f) continue;
+                    float c = 0.0f;
+                    for (int o = 0; o < p.n_obs; ++o) {
+                        const float g = gl[(int64_t)s * p.n_obs + o];
+                        const int sp = p.obs_sp[o];
+                        jit_lam_add(lam, sp, alpha * g);
+                        c += g * (float)jit_dv(jk, sp);
+                    }
+                    const float c_tau = __fdividef(c, tau);
+                    dt_dir -= c_tau;
+                    dtau_dir -= alpha * c_tau;
+                }
+            }
+            const float dtau = mu + dtau_dir;
+            const float dLda0 = -dtau * tau / a0;
+            // pass 2: soft-sample weights y~_j ~ exp2((l_j - l_max)/T) and W = sum y~ w
+            float wr[JM];
+            jit_w(lam, wr);
+            float Z = 0.0f, Wq = 0.0f;
+#pragma unroll
+            for (int j = 0; j < JM; ++j) {
+                const float q = lr[j] == -CUDART_INF_F ? 0.0f : exp2f((lr[j] - lmax) * invT);
+                lr[j] = q;
+                Z += q;
+                Wq += q * wr[j];
+            }
+            const float invZ = __fdividef(1.0f, Z), Wbar = Wq * invZ;
+            // pass 3: per-reaction adjoints, then the state adjoint of every reaction in order
+            float psi[JM], ctau[JM];
+#pragma unroll
+            for (int j = 0; j < JM; ++j) {
+                psi[j] = lr[j] > 0.0f ? lr[j] * invZ * (wr[j] - Wbar) * invT : 0.0f;
+                dAr[j] += psi[j] + dLda0 * a[j];
+                ctau[j] = dLda0 * kr[j];
+            }
+            jit_state_adj(X, a, h, psi, ctau, lam);
+            mu += dt_dir;  // t_{k+1} = t_k + tau_k
+        }
+        for (int s = s_hi + 1; s <= s_top; ++s) {
+            float coef = 1.0f;
+            if (READOUT == SSA_READOUT_LINEAR && draw) {
+                const float alpha = p.brk_a[(int64_t)s * n + i];
+                if (alpha >= 0.0f) coef = 1.0f - alpha;
+            }
+            for (int o = 0; o < p.n_obs; ++o) jit_lam_add(lam, p.obs_sp[o], coef * gl[(int64_t)s * p.n_obs + o]);
+        }
+        if (ck_off == 0) {
+            const int *ck = p.ckpt + (int64_t)ck_row * JN * n + i;
+#pragma unroll
+            for (int s = 0; s < JN; ++s) mism += (ck[(int64_t)s * n] != X[s]);
+            --ck_row;
+            ck_off = p.K;
+        }
+        --ck_off;
+        if (k > 0) jit_unapply(X, event_at(k - 1));
+        if (draw) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) E[q] = En[q];
+        }
+    }
+    if (mism) atomicAdd(p.mismatch, mism);
+}
+
+template <int READOUT>
+__device__ __forceinline__ void jit_adj(const AdjParams &p)
+{
+    extern __shared__ float s_dA[];  // [JM][blockDim.x]
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int64_t n = p.n_traj;
+    const int64_t i = (int64_t)blockIdx.x * B + tid;
+    float kr[JM], dAr[JM];
+#pragma unroll
+    for (int j = 0; j < JM; ++j) {
+        kr[j] = p.k_rates[j];
+        dAr[j] = 0.0f;
+    }
+    int st = -1;
+    if (i < n) st = p.status[i];
+    const bool active = st == SSA_TRAJ_OK || st == SSA_TRAJ_ABSORBED || st == SSA_TRAJ_STEP_CAP;
+    if (active) jit_adj_traj<READOUT>(p, kr, i, st, dAr);
+#pragma unroll
+    for (int j = 0; j < JM; ++j) s_dA[j * B + tid] = dAr[j];
+    __syncthreads();
+    // fixed-order block reduction of the per-reaction adjoints (the generic kernels' order)
+    const int warp = tid >> 5, lane = tid & 31, nwarps = B >> 5;
+    for (int j = warp; j < JM; j += nwarps) {
+        float acc = 0.0f;
+        for (int u = lane; u < B; u += 32) acc += s_dA[j * B + u];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) p.partial[(int64_t)blockIdx.x * JM + j] = acc;
+    }
+}
+
+}  // namespace ssa
+
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_hold(const ssa::FwdParams p)
+{
+    ssa::jit_fwd<SSA_READOUT_HOLD, false>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_hold_rec(const ssa::FwdParams p)
+{
+    ssa::jit_fwd<SSA_READOUT_HOLD, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_linear(const ssa::FwdParams p)
+{
+    ssa::jit_fwd<SSA_READOUT_LINEAR, false>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_linear_rec(const ssa::FwdParams p)
+{
+    ssa::jit_fwd<SSA_READOUT_LINEAR, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_hold(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_HOLD>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_linear(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_LINEAR>(p);
+}

@@ -62,6 +62,12 @@ class Network:
                                    self.n_params, arrs[4].ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
         self.handle = h
 
+    def specialize(self) -> tuple[bool, str]:
+        """ssa_network_specialize: compile the network-specialised kernels now; (available, reason)."""
+        ok = ctypes.c_int32(0)
+        check(_lib.lib().ssa_network_specialize(self.handle, ctypes.byref(ok)))
+        return bool(ok.value), ("" if ok.value else _lib.lib().ssa_last_error().decode(errors="replace"))
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             _lib.lib().ssa_destroy_network(self.handle)
@@ -102,6 +108,11 @@ class Run:
         check(_lib.lib().ssa_run_brackets(self.handle, _ptr(out), _stream(stream)))
         return out
 
+    @property
+    def variant(self) -> int:
+        """1 generic thread kernels, 2 network-specialised thread kernels, 32 warp kernels."""
+        return int(_lib.lib().ssa_run_variant(self.handle))
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             _lib.lib().ssa_destroy_run(self.handle)
@@ -123,10 +134,10 @@ class ForwardResult:
 
 
 def make_opts(readout="hold", record=False, ckpt_interval=64, max_steps=1 << 20, threads_per_traj=0,
-              block_threads=0) -> FwdOpts:
+              block_threads=0, specialize=True) -> FwdOpts:
     ro = READOUTS[readout] if isinstance(readout, str) else int(readout)
     return FwdOpts(ro, 1 if record else 0, int(ckpt_interval), int(threads_per_traj), int(max_steps),
-                   int(block_threads), 0)
+                   int(block_threads), 0 if specialize else 1)
 
 
 def workspace_bytes(net: Network, n_traj: int, n_samples: int, opts: FwdOpts) -> int:
@@ -144,7 +155,7 @@ def _as_cuda(x, dtype, device):
 
 def forward(net: Network, log_rates, n_traj: int, x0, t_end: float, sample_times, obs_species, seed: int,
             readout="hold", record=False, ckpt_interval=64, max_steps=1 << 20, traj_offset=0,
-            threads_per_traj=0, block_threads=0, replay_events=None, replay_n_events=None,
+            threads_per_traj=0, block_threads=0, specialize=True, replay_events=None, replay_n_events=None,
             workspace: torch.Tensor | None = None, obs_out: torch.Tensor | None = None,
             stream=None, device=None) -> ForwardResult:
     """ssa_forward (or ssa_forward_replay when replay_events is given) on the current stream."""
@@ -155,7 +166,7 @@ def forward(net: Network, log_rates, n_traj: int, x0, t_end: float, sample_times
     ts = _as_cuda(sample_times, torch.float64, device)
     obs_sp = _as_cuda(obs_species, torch.int32, device)
     S, n_obs = int(ts.numel()), int(obs_sp.numel())
-    opts = make_opts(readout, record, ckpt_interval, max_steps, threads_per_traj, block_threads)
+    opts = make_opts(readout, record, ckpt_interval, max_steps, threads_per_traj, block_threads, specialize)
     need = workspace_bytes(net, n_traj, S, opts)
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=device)
