@@ -362,9 +362,10 @@ def run_ours(args):
 
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
-    osc = oscillator_extra(ssa, dev) if (rank == 0 and not args.no_extra) else None
-    batch = uneven_batch_extra(ssa, dev, args.batch_scale) if (rank == 0 and not args.no_extra) else None
-    grn = grn_extra(ssa, dev) if (rank == 0 and not args.no_extra) else None
+    legs = set() if args.no_extra else {x for x in args.legs.split(",") if x}
+    osc = oscillator_extra(ssa, dev) if (rank == 0 and "oscillator" in legs) else None
+    batch = uneven_batch_extra(ssa, dev, args.batch_scale) if (rank == 0 and "batch" in legs) else None
+    grn = grn_extra(ssa, dev) if (rank == 0 and "grn" in legs) else None
     M = wl.net.n_reactions
     rates = ssa.pipe_rates()
     logf_slots = 128.0 / rates["logf"]
@@ -657,6 +658,8 @@ def main():
     ap.add_argument("--ref-chunk", type=int, default=4096)
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the oscillator and uneven-batch fields")
+    ap.add_argument("--legs", default="oscillator,batch,grn",
+                    help="comma-separated extra fields to measure: oscillator, batch, grn ('none' for none)")
     ap.add_argument("--batch-scale", type=float, default=1.0 / 16,
                     help="trajectories per network of the uneven batch, as a fraction of the full counts")
     args = ap.parse_args()

@@ -400,13 +400,14 @@ ssa_status ssa_batch_item_brackets(const ssa_batch *batch, int32_t item, int32_t
                                    void *stream);
 
 /*
- * ssa_batch_autotune -- pilot-based plan (no counterpart in the paper). For each item, runs
- * min(pilot_traj, n_traj) trajectories through ssa_forward(record) + ssa_backward under each
- * variant the item allows (threads_per_traj = 0: thread if N, M <= 16, and warp), keeps the faster,
- * and sets the item's cost estimate to the pilot's mean draws (host_draws_out [n_items] receives
- * them, may be NULL). Allocates and frees pilot buffers with cudaMalloc, synchronises `stream`,
- * writes nothing the caller owns. Invalidates the captured graph and the workspace layout; the
- * workspace size may change (more units for the warp variant).
+ * ssa_batch_autotune -- pilot-based plan (no counterpart in the paper). Items that may run either
+ * variant (threads_per_traj = 0 and N, M <= 16) time min(pilot_traj, n_traj) trajectories through
+ * ssa_forward(record) + ssa_backward under both and keep the faster. Then all items' pilots run
+ * together as one pilot batch, and each item's cost estimate (used to order the work longest first)
+ * becomes its pilot's mean draws (host_draws_out [n_items] receives them, may be NULL). Allocates and
+ * frees pilot buffers with cudaMalloc, synchronises `stream`, writes nothing the caller owns.
+ * Invalidates the captured graph and the workspace layout; the workspace size may change (more units
+ * for the warp variant).
  */
 ssa_status ssa_batch_autotune(ssa_batch *batch, int64_t pilot_traj, void *stream,
                               double *host_draws_out);

@@ -675,58 +675,57 @@ extern "C" ssa_status ssa_batch_item_brackets(const ssa_batch *bt, int32_t item,
     return SSA_OK;
 }
 
-// Pilot-based plan: for each item, run `pilot_traj` trajectories through the single-network entry
-// points (forward with record, then the adjoint) under every eligible variant, keep the faster one,
-// and take the pilot's mean draw count as the item's cost estimate; the checkpoint interval stays.
-// The pilot buffers are allocated once, at the largest size any pilot needs.
+// Pilot-based plan. Items that may run either variant (N, M <= 16 and no variant requested) time a
+// pilot of `pilot_traj` trajectories through the single-network entry points (forward with record,
+// then the adjoint) under both variants and keep the faster. Every item's cost estimate is the mean
+// draw count of its pilot trajectories, all of which run together as one pilot batch (one persistent
+// launch per direction), so the plan costs about one launch of the pilot sizes. Buffers are
+// allocated once.
 extern "C" ssa_status ssa_batch_autotune(ssa_batch *bt, int64_t pilot_traj, void *stream, double *host_draws_out)
 {
     if (!bt || pilot_traj < 1) return set_error(SSA_ERR_INVALID_ARG, "bad batch or pilot size");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t n_items = bt->items.size();
-    std::vector<std::vector<int>> cands(n_items);
-    size_t ws_max = 0, obs_max = 1, p_max = 1, n_max = 1;
+    std::vector<int64_t> np(n_items);
+    size_t obs_total = 0, ws_max = 0, p_max = 1, n_max = 1;
     for (size_t it = 0; it < n_items; ++it) {
         const ssa_batch_item &b = bt->items[it];
-        if (b.threads_per_traj) cands[it].push_back(b.threads_per_traj);
-        else {
-            if (thread_eligible(b.net)) cands[it].push_back(1);
-            cands[it].push_back(32);
-        }
-        const int64_t n = std::min<int64_t>(pilot_traj, std::max<int64_t>(b.n_traj, 1));
-        for (int v : cands[it]) {
-            ssa_fwd_opts o{};
-            o.readout = bt->readout;
-            o.record = 1;
-            o.ckpt_interval = bt->K[it];
-            o.threads_per_traj = v;
-            o.max_steps = b.max_steps;
-            o.no_specialize = 1;  // the batch runs the generic kernels
-            const size_t w = ssa_forward_workspace_bytes(b.net, n, b.n_samples, &o);
-            if (w == 0) return set_error(SSA_ERR_INVALID_ARG, "pilot workspace size");
-            ws_max = std::max(ws_max, w);
-        }
-        obs_max = std::max(obs_max, (size_t)n * b.n_samples * b.n_obs);
+        np[it] = std::min<int64_t>(pilot_traj, b.n_traj);
+        obs_total += (size_t)np[it] * b.n_samples * b.n_obs;
         p_max = std::max(p_max, (size_t)b.net->P);
-        n_max = std::max(n_max, (size_t)n);
+        n_max = std::max(n_max, (size_t)std::max<int64_t>(np[it], 1));
+        if (!b.threads_per_traj && thread_eligible(b.net) && np[it] > 0) {
+            for (int v : {1, 32}) {
+                ssa_fwd_opts o{};
+                o.readout = bt->readout;
+                o.record = 1;
+                o.ckpt_interval = bt->K[it];
+                o.threads_per_traj = v;
+                o.max_steps = b.max_steps;
+                o.no_specialize = 1;  // the batch runs the generic kernels
+                const size_t w = ssa_forward_workspace_bytes(b.net, np[it], b.n_samples, &o);
+                if (w == 0) return set_error(SSA_ERR_INVALID_ARG, "pilot workspace size");
+                ws_max = std::max(ws_max, w);
+            }
+        }
     }
-    void *ws = nullptr, *obs = nullptr, *dl = nullptr, *dth = nullptr, *dr = nullptr;
+    void *obs = nullptr, *dl = nullptr, *dth = nullptr, *dr = nullptr, *ws = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ssa_status rc = SSA_OK;
-    if (cudaMalloc(&ws, ws_max) != cudaSuccess || cudaMalloc(&obs, obs_max * 4) != cudaSuccess ||
-        cudaMalloc(&dl, obs_max * 4) != cudaSuccess || cudaMalloc(&dth, p_max * 4) != cudaSuccess ||
-        cudaMalloc(&dr, n_max * 4) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+    if (cudaMalloc(&obs, std::max<size_t>(obs_total, 1) * 4) != cudaSuccess ||
+        cudaMalloc(&dl, std::max<size_t>(obs_total, 1) * 4) != cudaSuccess ||
+        cudaMalloc(&dth, p_max * 4 * n_items) != cudaSuccess || cudaMalloc(&dr, n_max * 4) != cudaSuccess ||
+        (ws_max > 0 && cudaMalloc(&ws, ws_max) != cudaSuccess) || cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess)
         rc = set_error(SSA_ERR_CUDA, "pilot allocation failed");
-    if (rc == SSA_OK && cudaMemsetAsync(dl, 0, obs_max * 4, st) != cudaSuccess)
+    if (rc == SSA_OK && cudaMemsetAsync(dl, 0, std::max<size_t>(obs_total, 1) * 4, st) != cudaSuccess)
         rc = set_error(SSA_ERR_CUDA, "pilot memset failed");
-    std::vector<int> hd(n_max);
+    // 1. variant choice for the items that have one
     for (size_t it = 0; it < n_items && rc == SSA_OK; ++it) {
         const ssa_batch_item &b = bt->items[it];
-        const int64_t n = std::min<int64_t>(pilot_traj, std::max<int64_t>(b.n_traj, 1));
-        double best = -1.0, best_draws = bt->est_draws[it];
-        int best_v = bt->variant[it];
-        for (int v : cands[it]) {
+        if (b.threads_per_traj || !thread_eligible(b.net) || np[it] == 0) continue;
+        float best = -1.0f;
+        for (int v : {1, 32}) {
             ssa_fwd_opts o{};
             o.readout = bt->readout;
             o.record = 1;
@@ -739,34 +738,65 @@ extern "C" ssa_status ssa_batch_autotune(ssa_batch *bt, int64_t pilot_traj, void
             for (int rep = 0; rep < 2 && s == SSA_OK; ++rep) {  // the first repetition warms the kernels up
                 ssa_run *run = nullptr;
                 cudaEventRecord(e0, st);
-                s = ssa_forward(b.net, b.log_rates, n, b.traj_offset, b.x0, 0, b.t_end, b.sample_times, b.n_samples,
-                                b.obs_species, b.n_obs, b.seed, &o, ws, ws_max, obs, static_cast<int32_t *>(dr), nullptr,
-                                stream, &run);
+                s = ssa_forward(b.net, b.log_rates, np[it], b.traj_offset, b.x0, 0, b.t_end, b.sample_times,
+                                b.n_samples, b.obs_species, b.n_obs, b.seed, &o, ws, ws_max, obs,
+                                static_cast<int32_t *>(dr), nullptr, stream, &run);
                 if (s == SSA_OK) s = ssa_backward(run, static_cast<float *>(dl), (int64_t)b.n_samples * b.n_obs,
                                                   bt->temperature, static_cast<float *>(dth), stream);
                 cudaEventRecord(e1, st);
                 if (run) ssa_destroy_run(run);
                 if (s == SSA_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
             }
-            if (s == SSA_OK && cudaMemcpy(hd.data(), dr, (size_t)n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-                s = set_error(SSA_ERR_CUDA, "pilot copy failed");
             if (s != SSA_OK) {
                 rc = s;
                 break;
             }
-            double sum = 0.0;
-            for (int64_t q = 0; q < n; ++q) sum += hd[q];
-            if (best < 0.0 || ms < best) {
+            if (best < 0.0f || ms < best) {
                 best = ms;
-                best_v = v;
-                best_draws = std::max(1.0, sum / (double)n);
+                bt->variant[it] = v;
             }
         }
-        if (rc != SSA_OK) break;
-        bt->variant[it] = best_v;
-        bt->est_draws[it] = best_draws;
-        if (host_draws_out) host_draws_out[it] = best_draws;
     }
+    // 2. cost estimates from one pilot batch under the chosen variants
+    if (rc == SSA_OK) {
+        std::vector<ssa_batch_item> pil(bt->items);
+        size_t off = 0;
+        for (size_t it = 0; it < n_items; ++it) {
+            ssa_batch_item &q = pil[it];
+            q.n_traj = np[it];
+            q.threads_per_traj = bt->variant[it];
+            q.ckpt_interval = bt->K[it];
+            q.obs_out = static_cast<float *>(obs) + off;
+            q.dl_dobs = static_cast<float *>(dl) + off;
+            q.dl_traj_stride = (int64_t)q.n_samples * q.n_obs;
+            q.dl_dlog_rates = static_cast<float *>(dth) + p_max * it;
+            off += (size_t)np[it] * q.n_samples * q.n_obs;
+        }
+        ssa_batch *pb = nullptr;
+        rc = ssa_batch_create(pil.data(), (int32_t)n_items, bt->readout, bt->temperature, &pb);
+        void *pws = nullptr;
+        if (rc == SSA_OK) {
+            const size_t need = ssa_batch_workspace_bytes(pb);
+            if (cudaMalloc(&pws, need) != cudaSuccess) rc = set_error(SSA_ERR_CUDA, "pilot batch allocation failed");
+            if (rc == SSA_OK) rc = ssa_batch_run(pb, pws, need, 0, stream);
+            std::vector<int> hd(n_max);
+            for (size_t it = 0; it < n_items && rc == SSA_OK; ++it) {
+                if (np[it] == 0) continue;
+                rc = ssa_batch_item_outputs(pb, (int32_t)it, static_cast<int32_t *>(dr), nullptr, nullptr, stream);
+                if (rc == SSA_OK && cudaMemcpyAsync(hd.data(), dr, (size_t)np[it] * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                    rc = set_error(SSA_ERR_CUDA, "pilot copy failed");
+                if (rc == SSA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = set_error(SSA_ERR_CUDA, "pilot failed");
+                if (rc != SSA_OK) break;
+                double sum = 0.0;
+                for (int64_t k = 0; k < np[it]; ++k) sum += hd[k];
+                bt->est_draws[it] = std::max(1.0, sum / (double)np[it]);
+            }
+        }
+        if (pws) cudaFree(pws);
+        ssa_batch_destroy(pb);
+    }
+    if (host_draws_out)
+        for (size_t it = 0; it < n_items; ++it) host_draws_out[it] = bt->est_draws[it];
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(ws);
