@@ -38,22 +38,22 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # Issue-slot roofline of the SSA kernels. The unit is one SSA step; its
 # algorithmic cost is the minimal number of issue slots (thread instructions) of the method's
 # arithmetic on sm_103, with an accurate logarithm costed at its measured throughput on this GPU
-# (ssa_pipe_rates: 128 issue slots per SM per clock / logf per SM per clock). The peak is the SM
+# (ssa_pipe_rates: 128 issue slots per SM per clock / exponential variates per SM per clock). The peak is the SM
 # issue rate: 152 SMs x 4 schedulers x 32 lanes x the sampled SM clock.
 # --------------------------------------------------------------------------------------------
-def instr_per_step_fwd(M: int, logf_slots: float) -> float:
+def instr_per_step_fwd(M: int, log_slots: float) -> float:
     nb = (M + 4) // 4
     philox = 60 * nb                          # 10 rounds x (2 wide multiplies, 2 XOR3, 2 key adds)
-    variates = (2 + logf_slots) * (M + 1)     # u from the bits (2) and an accurate -ln u
+    variates = (2 + log_slots) * (M + 1)     # u from the bits (2) and an accurate -ln u
     reactions = 12 * M                        # propensity (5), a0 add (1), race (2 mul, compare, 3 select)
     step = 20                                 # tau (2), FP64 clock add + compare (3), update (8), log (4), loop (3)
     return philox + variates + reactions + step
 
 
-def instr_per_step_bwd(M: int, logf_slots: float) -> float:
+def instr_per_step_bwd(M: int, log_slots: float) -> float:
     # the forward step recomputed, then per reaction: 2 lg2 + sub (log key), ex2 + mul (soft weight),
     # stoichiometric dot (6), psi (5), dA (2), state adjoint (8); per step: readout, reversal, event (20)
-    return instr_per_step_fwd(M, logf_slots) + 25 * M + 20
+    return instr_per_step_fwd(M, log_slots) + 25 * M + 20
 
 
 def sm_issue_peak(sm_mhz: float, n_sm: int = 152) -> float:
@@ -366,17 +366,21 @@ def run_ours(args):
     osc = oscillator_extra(ssa, dev) if (rank == 0 and "oscillator" in legs) else None
     batch = uneven_batch_extra(ssa, dev, args.batch_scale) if (rank == 0 and "batch" in legs) else None
     grn = grn_extra(ssa, dev) if (rank == 0 and "grn" in legs) else None
+    warp = warp_extra(ssa, dev) if (rank == 0 and "warp" in legs) else None
     M = wl.net.n_reactions
     rates = ssa.pipe_rates()
-    logf_slots = 128.0 / rates["logf"]
+    log_slots = 128.0 / rates["neglog"]
     bwd_s = float(np.mean(bwd_ms)) / 1e3
     fwd_s = float(np.mean(fwd_ms)) / 1e3
     per_launch_steps = steps_total / world / K
-    ach_b = instr_per_step_bwd(M, logf_slots) * per_launch_steps / bwd_s
-    ach_f = instr_per_step_fwd(M, logf_slots) * per_launch_steps / fwd_s
+    ach_b = instr_per_step_bwd(M, log_slots) * per_launch_steps / bwd_s
+    ach_f = instr_per_step_fwd(M, log_slots) * per_launch_steps / fwd_s
     peak = sm_issue_peak(sm_mhz, rates["sm_count"])
     if batch and "instr_per_s_T" in batch:
         batch["alu_frac"] = batch["instr_per_s_T"] * 1e12 / peak
+    if warp:
+        warp["fwd_alu_frac"] = warp["fwd_instr_per_s_T"] * 1e12 / peak
+        warp["adj_alu_frac"] = warp["adj_instr_per_s_T"] * 1e12 / peak
     dominant = "adjoint" if bwd_s >= fwd_s else "forward"
     ach = ach_b if dominant == "adjoint" else ach_f
     line = {
@@ -404,14 +408,15 @@ def run_ours(args):
         "generic_thread_kernels": generic,
         "roofline": {"bound": "alu", "kernel": dominant, "achieved": ach / 1e12, "peak": peak / 1e12,
                      "unit": "T thread-instr/s", "frac": ach / peak, "traffic": profiled_traffic(dominant),
-                     "algorithmic_instr_per_step": {"forward": instr_per_step_fwd(M, logf_slots),
-                                                    "adjoint": instr_per_step_bwd(M, logf_slots)},
+                     "algorithmic_instr_per_step": {"forward": instr_per_step_fwd(M, log_slots),
+                                                    "adjoint": instr_per_step_bwd(M, log_slots)},
                      "forward_frac": ach_f / peak,
                      "peak_basis": f"{rates['sm_count']} SM x 4 x 32 lanes x {sm_mhz:.0f} MHz (sampled median)",
                      "pipe_rates_per_sm_clk": {k: round(v, 3) for k, v in rates.items()}},
         "oscillator": osc,
         "uneven_batch": batch,
         "grn": grn,
+        "warp_kernels": warp,
         "paper_context": "1.9e9 SSA steps/s forward on the oscillator, RTX 6000 Ada + TF 2.20 (a different machine)",
         "cpu_baseline": cpu_base,
         "e2e": {"value": e2e_value, "unit": "SSA steps/s (fwd+adj)", "h2d_bytes_per_step": h2d,
@@ -513,9 +518,9 @@ def uneven_batch_extra(ssa, dev, traj_scale: float, reps: int = 2, sequential: b
         bad += int((st > 2).sum().item())
         variants[b.variant(q)] += 1
     rates = ssa.pipe_rates()
-    logf_slots = 128.0 / rates["logf"]
-    instr = sum(per_item[q] * (instr_per_step_fwd(wl.nets[q].n_reactions, logf_slots)
-                               + instr_per_step_bwd(wl.nets[q].n_reactions, logf_slots)) for q in range(len(items)))
+    log_slots = 128.0 / rates["neglog"]
+    instr = sum(per_item[q] * (instr_per_step_fwd(wl.nets[q].n_reactions, log_slots)
+                               + instr_per_step_bwd(wl.nets[q].n_reactions, log_slots)) for q in range(len(items)))
     out = {"workload": f"{len(items)} random networks, N in [2, 64], M in [4, 512], t_end=10, 20 LINEAR samples, "
                        f"T=0.5, trajectories per network log-uniform [256, 65536] x {traj_scale:g}",
            "n_traj_total": int(wl.n_traj.sum()), "ssa_steps": steps, "ms": ms, "steps_per_s": steps / (ms / 1e3),
@@ -537,6 +542,49 @@ def uneven_batch_extra(ssa, dev, traj_scale: float, reps: int = 2, sequential: b
         ev[1].record()
         torch.cuda.synchronize()
         out["per_network_calls_ms"] = ev[0].elapsed_time(ev[1])
+    return out
+
+
+def warp_extra(ssa, dev, n: int = 16384, reps: int = 2):
+    """The warp-per-trajectory kernels alone: forward (recorded) and adjoint on the network of the uneven
+    batch whose reaction count is closest to 300, n trajectories to t_end = 10 with 20 LINEAR samples,
+    timed with CUDA events after one warm-up launch; steps/s and the issue-slot rate of each kernel."""
+    import torch
+
+    import ssa_workloads as W
+    pilot = json.load(open(os.path.join(ROOT, "tests", "golden", "c4_pilot.json")))
+    wl = W.config_c4(n_nets=len(pilot["accepted"]), rejected=pilot["rejected"])
+    q = int(np.argmin([abs(s.n_reactions - 300) for s in wl.nets]))
+    spec = wl.nets[q]
+    net = ssa.Network(spec)
+    th = torch.tensor(spec.log_rates.astype(np.float32), device=dev)
+    max_steps = int(2 * pilot["accepted"][q]["max_draws"] + 256)
+    dl = torch.tensor(wl.loss_weights[q] / n, dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fms = ams = 0.0
+    steps = 0
+    for r in range(reps + 1):
+        ev[0].record()
+        fw = ssa.forward(net, th, n, spec.x0, wl.t_end, wl.sample_times, wl.obs_species[q], 300 + r, readout="linear",
+                         record=True, max_steps=max_steps, threads_per_traj=32)
+        ev[1].record()
+        ssa.backward(fw, dl, wl.temperature)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if r >= 1:
+            fms += ev[0].elapsed_time(ev[1])
+            ams += ev[1].elapsed_time(ev[2])
+            steps += int(fw.draws.sum().item())
+        del fw
+    rates = ssa.pipe_rates()
+    log_slots = 128.0 / rates["neglog"]
+    M = spec.n_reactions
+    out = {"workload": f"uneven-batch network {q}: N={spec.n_species}, M={M}, {n} trajectories, t_end={wl.t_end}, "
+                       "20 LINEAR samples, warp per trajectory",
+           "ssa_steps": steps // reps, "forward_ms": fms / reps, "adjoint_ms": ams / reps,
+           "fwd_steps_per_s": steps / (fms / 1e3), "adj_steps_per_s": steps / (ams / 1e3),
+           "fwd_instr_per_s_T": instr_per_step_fwd(M, log_slots) * steps / (fms / 1e3) / 1e12,
+           "adj_instr_per_s_T": instr_per_step_bwd(M, log_slots) * steps / (ams / 1e3) / 1e12}
     return out
 
 
@@ -658,8 +706,8 @@ def main():
     ap.add_argument("--ref-chunk", type=int, default=4096)
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the oscillator and uneven-batch fields")
-    ap.add_argument("--legs", default="oscillator,batch,grn",
-                    help="comma-separated extra fields to measure: oscillator, batch, grn ('none' for none)")
+    ap.add_argument("--legs", default="oscillator,batch,grn,warp",
+                    help="comma-separated extra fields to measure: oscillator, batch, grn, warp ('none' for none)")
     ap.add_argument("--batch-scale", type=float, default=1.0 / 16,
                     help="trajectories per network of the uneven batch, as a fraction of the full counts")
     args = ap.parse_args()

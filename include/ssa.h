@@ -295,10 +295,18 @@ ssa_status ssa_bf16_gemm(const uint16_t *A, const uint16_t *B, int32_t M, int32_
                          int32_t *err_flag, void *stream);
 
 /*
+ * ssa_exp_variates -- test hook: out[i] = -ln u(words[i]) with u(x) = ((x >> 9) + 1/2) 2^-23, the
+ * exponential variate every kernel draws from a Philox word (device uint32 words [n], device float
+ * out [n]), with the logarithm the kernels use (within one unit in the last place).
+ */
+ssa_status ssa_exp_variates(const uint32_t *words, int64_t n, float *out, void *stream);
+
+/*
  * ssa_pipe_rates -- measurement support (no counterpart in the paper): throughput of the
  * instruction classes an SSA step is made of on the current GPU, as operations per SM per clock at
- * the device's maximum SM clock, written to host_rates[5] = {binary32 FMA, binary64 add, logf,
- * 32-bit integer multiply (high and low), lg2.approx}. Also returns that clock (MHz) and the SM
+ * the device's maximum SM clock, written to host_rates[5] = {binary32 FMA, binary64 add, the
+ * exponential variate -ln u the kernels use (an accurate binary32 logarithm), 32-bit integer multiply
+ * (high and low), lg2.approx}. Also returns that clock (MHz) and the SM
  * count. Synchronous; allocates and frees a small device buffer.
  */
 ssa_status ssa_pipe_rates(double *host_rates, double *host_sm_clock_mhz, int32_t *host_sm_count);

@@ -35,6 +35,7 @@ cudaError_t launch_forward_warp(const FwdParams &p, int readout, bool record, in
 cudaError_t launch_backward_warp(const AdjParams &p, int readout, int warps, size_t smem, int64_t grid,
                                  cudaStream_t st);
 int thread_kernel_mc(int M);
+cudaError_t launch_exp_variates(const uint32_t *words, int64_t n, float *out, cudaStream_t st);
 struct JitKernels;
 bool jit_eligible(const ssa_network *net);
 const JitKernels *jit_kernels(const ssa_network *net, std::string &why);
@@ -557,6 +558,13 @@ extern "C" ssa_status ssa_run_brackets(const ssa_run *run, int32_t *brackets_out
 extern "C" void ssa_destroy_run(ssa_run *run) { delete run; }
 
 extern "C" int32_t ssa_run_variant(const ssa_run *run) { return run ? run->variant : 0; }
+
+extern "C" ssa_status ssa_exp_variates(const uint32_t *words, int64_t n, float *out, void *stream)
+{
+    if (n < 0 || (n > 0 && (!words || !out))) return fail(SSA_ERR_INVALID_ARG, "bad arguments");
+    CUDA_TRY(launch_exp_variates(words, n, out, static_cast<cudaStream_t>(stream)));
+    return SSA_OK;
+}
 
 extern "C" size_t ssa_ensemble_mean_workspace_bytes(int64_t n_traj, int64_t row_len)
 {

@@ -4,7 +4,7 @@
 // network runs the same exact SSA and the same adjoint as the single-network entry points).
 //
 // Work is cut into units: 32 trajectories of one network for the thread-per-trajectory variant (one
-// per lane), or a few trajectories run one after another by a whole warp for the warp-per-trajectory
+// per lane), or one trajectory run by a whole warp for the warp-per-trajectory
 // variant. The host orders the units longest first (estimated draws x reactions x trajectories, from
 // the autotuner's pilot runs) and every warp of a persistent grid (one wave: SMs x resident blocks)
 // pulls the next unit from an atomic counter. The per-trajectory code is the same as the
@@ -54,7 +54,8 @@ struct BatchUnit {
 
 constexpr int kBatchWarps = 4;
 constexpr int kBatchThreadMaxN = 16;  // thread variant inside a batch: N <= 16 and M <= 16
-constexpr int kBatchWarpUnit = 4;     // trajectories per warp-variant unit
+constexpr int kBatchWarpBlocks = 6;  // resident blocks per SM the warp-unit kernels are compiled for
+constexpr int kBatchWarpUnit = 1;     // trajectories per warp-variant unit (one: the finest grain for the tail)
 
 __global__ void batch_prepare_kernel(const BatchItem *items, int n_items)
 {
@@ -105,8 +106,10 @@ __device__ __forceinline__ void batch_fwd_thread_unit(const BatchItem &b, const 
     if (lane < u.count) thread_fwd_body<READOUT, true, false, MC>(p, rx, st, p.k_rates, Xw + lane, 32, u.traj_begin + lane);
 }
 
-template <int READOUT>
-__global__ void __launch_bounds__(32 * kBatchWarps) batch_fwd_kernel(const BatchItem *items, const BatchUnit *units,
+// VARIANT 1 runs the thread units, VARIANT 32 the warp units (separate kernels, so that the warp
+// kernel is not compiled with the register budget of the unrolled thread bodies)
+template <int READOUT, int VARIANT>
+__global__ void __launch_bounds__(32 * kBatchWarps, VARIANT == 1 ? 1 : kBatchWarpBlocks) batch_fwd_kernel(const BatchItem *items, const BatchUnit *units,
                                                                     int n_units, int *counter, int x_words)
 {
     extern __shared__ __align__(16) int bsm[];
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps) batch_fwd_kernel(const Batch
         const BatchUnit u = units[ui];
         if (u.item != cached) cached = load_item(items, u.item, s_items + wib);
         const BatchItem &b = s_items[wib];
-        if (b.variant == 1) {
+        if constexpr (VARIANT == 1) {
             switch (b.mc) {
             case 2: batch_fwd_thread_unit<READOUT, 2>(b, u, Xw); break;
             case 4: batch_fwd_thread_unit<READOUT, 4>(b, u, Xw); break;
@@ -168,8 +171,8 @@ __device__ __forceinline__ void batch_adj_thread_unit(const BatchItem &b, const 
     }
 }
 
-template <int READOUT>
-__global__ void __launch_bounds__(32 * kBatchWarps) batch_adj_kernel(const BatchItem *items, const BatchUnit *units,
+template <int READOUT, int VARIANT>
+__global__ void __launch_bounds__(32 * kBatchWarps, VARIANT == 1 ? 1 : kBatchWarpBlocks) batch_adj_kernel(const BatchItem *items, const BatchUnit *units,
                                                                     int n_units, int *counter, int w_words)
 {
     extern __shared__ __align__(16) float bsa[];
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps) batch_adj_kernel(const Batch
         const BatchUnit u = units[ui];
         if (u.item != cached) cached = load_item(items, u.item, s_items + wib);
         const BatchItem &b = s_items[wib];
-        if (b.variant == 1) {
+        if constexpr (VARIANT == 1) {
             switch (b.mc) {
             case 2: batch_adj_thread_unit<READOUT, 2>(b, u, wsm); break;
             case 4: batch_adj_thread_unit<READOUT, 4>(b, u, wsm); break;
@@ -271,10 +274,12 @@ struct ssa_batch {
     BatchUnit *d_units = nullptr;
     int *d_counters = nullptr;
     int *d_blk_item = nullptr, *d_blk_j = nullptr;
-    int n_units = 0, n_red_blocks = 0;
-    int x_words = 0, w_words = 0;
-    int fwd_blocks = 0, adj_blocks = 0;
-    size_t fwd_smem = 0, adj_smem = 0;
+    int n_red_blocks = 0;
+    // per kernel variant (0: thread units, 1: warp units): units [unit_begin, unit_begin + n_units)
+    int unit_begin[2] = {0, 0}, n_units[2] = {0, 0};
+    int x_words[2] = {0, 0}, w_words[2] = {0, 0};
+    int fwd_blocks[2] = {0, 0}, adj_blocks[2] = {0, 0};
+    size_t fwd_smem[2] = {0, 0}, adj_smem[2] = {0, 0};
     std::vector<BatchItem> h_items;
     cudaGraphExec_t graph = nullptr;
     bool ready = false;
@@ -530,7 +535,11 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
     }
     std::vector<size_t> order(units.size());
     for (size_t q = 0; q < order.size(); ++q) order[q] = q;
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        const bool tx = bt->variant[units[x].item] == 1, ty = bt->variant[units[y].item] == 1;
+        if (tx != ty) return tx;  // thread units first: they run in their own kernel
+        return cost[x] > cost[y];
+    });
     std::vector<BatchUnit> sorted(units.size());
     for (size_t q = 0; q < order.size(); ++q) sorted[q] = units[order[q]];
     std::vector<int> blk_item, blk_j;
@@ -550,30 +559,50 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
     CUDA_TRY_B(cudaMemcpyAsync(bt->d_blk_item, blk_item.data(), blk_item.size() * 4, cudaMemcpyHostToDevice, st));
     CUDA_TRY_B(cudaMemcpyAsync(bt->d_blk_j, blk_j.data(), blk_j.size() * 4, cudaMemcpyHostToDevice, st));
     CUDA_TRY_B(cudaStreamSynchronize(st));  // the host vectors above go out of scope
-    bt->n_units = (int)sorted.size();
+    int n_thread_units = 0;
+    for (const BatchUnit &u : sorted) n_thread_units += bt->variant[u.item] == 1;
+    bt->unit_begin[0] = 0;
+    bt->n_units[0] = n_thread_units;
+    bt->unit_begin[1] = n_thread_units;
+    bt->n_units[1] = (int)sorted.size() - n_thread_units;
     bt->n_red_blocks = (int)blk_item.size();
-    const int maxNpad = (maxN + 3) & ~3;
-    bt->x_words = std::max(kBatchThreadMaxN * 32, maxNpad);
-    bt->w_words = std::max(3 * kBatchThreadMaxN * 32, 2 * maxNpad + 5 * maxMp);
-    bt->fwd_smem = (size_t)kBatchWarps * (kItemWords + bt->x_words) * 4;
-    bt->adj_smem = (size_t)kBatchWarps * (kItemWords + bt->w_words) * 4;
-    int dev = 0, sms = 0, per_sm_f = 0, per_sm_a = 0, limit = 0;
+    int maxNw = 1, maxMpw = 4;  // largest warp-variant network
+    for (int it = 0; it < n_items; ++it)
+        if (bt->variant[it] != 1) {
+            maxNw = std::max(maxNw, bt->items[it].net->N);
+            maxMpw = std::max(maxMpw, bt->items[it].net->Mp);
+        }
+    const int maxNpad = (maxNw + 3) & ~3;
+    bt->x_words[0] = kBatchThreadMaxN * 32;
+    bt->w_words[0] = 3 * kBatchThreadMaxN * 32;
+    bt->x_words[1] = maxNpad;
+    bt->w_words[1] = 2 * maxNpad + 5 * maxMpw;
+    int dev = 0, sms = 0, limit = 0;
     CUDA_TRY_B(cudaGetDevice(&dev));
     CUDA_TRY_B(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY_B(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (bt->fwd_smem > (size_t)limit || bt->adj_smem > (size_t)limit)
-        return set_error(SSA_ERR_UNSUPPORTED, "a network in the batch is too large for the batch kernels");
-    auto fk = bt->readout == SSA_READOUT_HOLD ? batch_fwd_kernel<0> : batch_fwd_kernel<1>;
-    auto ak = bt->readout == SSA_READOUT_HOLD ? batch_adj_kernel<0> : batch_adj_kernel<1>;
-    CUDA_TRY_B(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->fwd_smem));
-    CUDA_TRY_B(cudaFuncSetAttribute(ak, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->adj_smem));
-    CUDA_TRY_B(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, fk, 32 * kBatchWarps, bt->fwd_smem));
-    CUDA_TRY_B(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, ak, 32 * kBatchWarps, bt->adj_smem));
-    if (per_sm_f < 1 || per_sm_a < 1) return set_error(SSA_ERR_UNSUPPORTED, "batch kernels do not fit on an SM");
-    // one persistent wave, never more warps than units
-    const int64_t need_blocks = (bt->n_units + kBatchWarps - 1) / kBatchWarps;
-    bt->fwd_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm_f, need_blocks));
-    bt->adj_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm_a, need_blocks));
+    const bool hold = bt->readout == SSA_READOUT_HOLD;
+    const void *fk[2] = {hold ? (const void *)batch_fwd_kernel<0, 1> : (const void *)batch_fwd_kernel<1, 1>,
+                         hold ? (const void *)batch_fwd_kernel<0, 32> : (const void *)batch_fwd_kernel<1, 32>};
+    const void *ak[2] = {hold ? (const void *)batch_adj_kernel<0, 1> : (const void *)batch_adj_kernel<1, 1>,
+                         hold ? (const void *)batch_adj_kernel<0, 32> : (const void *)batch_adj_kernel<1, 32>};
+    for (int v = 0; v < 2; ++v) {
+        bt->fwd_smem[v] = (size_t)kBatchWarps * (kItemWords + bt->x_words[v]) * 4;
+        bt->adj_smem[v] = (size_t)kBatchWarps * (kItemWords + bt->w_words[v]) * 4;
+        if (bt->n_units[v] == 0) continue;
+        if (bt->fwd_smem[v] > (size_t)limit || bt->adj_smem[v] > (size_t)limit)
+            return set_error(SSA_ERR_UNSUPPORTED, "a network in the batch is too large for the batch kernels");
+        int per_sm_f = 0, per_sm_a = 0;
+        CUDA_TRY_B(cudaFuncSetAttribute(fk[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->fwd_smem[v]));
+        CUDA_TRY_B(cudaFuncSetAttribute(ak[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->adj_smem[v]));
+        CUDA_TRY_B(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, fk[v], 32 * kBatchWarps, bt->fwd_smem[v]));
+        CUDA_TRY_B(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_a, ak[v], 32 * kBatchWarps, bt->adj_smem[v]));
+        if (per_sm_f < 1 || per_sm_a < 1) return set_error(SSA_ERR_UNSUPPORTED, "batch kernels do not fit on an SM");
+        // one persistent wave, never more warps than units
+        const int64_t need_blocks = (bt->n_units[v] + kBatchWarps - 1) / kBatchWarps;
+        bt->fwd_blocks[v] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm_f, need_blocks));
+        bt->adj_blocks[v] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm_a, need_blocks));
+    }
     bt->ws = ws;
     bt->ready = true;
     return SSA_OK;
@@ -585,17 +614,33 @@ static ssa_status batch_enqueue(ssa_batch *bt, cudaStream_t st)
     CUDA_TRY_B(cudaMemsetAsync(bt->d_flags, 0, (size_t)n_items * 16 * sizeof(int), st));
     CUDA_TRY_B(cudaMemsetAsync(bt->d_counters, 0, 64, st));
     batch_prepare_kernel<<<std::min(n_items, 1024), 128, 0, st>>>(bt->d_items, n_items);
-    if (bt->n_units > 0) {
-        if (bt->readout == SSA_READOUT_HOLD) {
-            batch_fwd_kernel<0><<<bt->fwd_blocks, 32 * kBatchWarps, bt->fwd_smem, st>>>(
-                bt->d_items, bt->d_units, bt->n_units, bt->d_counters, bt->x_words);
-            batch_adj_kernel<0><<<bt->adj_blocks, 32 * kBatchWarps, bt->adj_smem, st>>>(
-                bt->d_items, bt->d_units, bt->n_units, bt->d_counters + 1, bt->w_words);
+    const bool hold = bt->readout == SSA_READOUT_HOLD;
+    const BatchUnit *u0 = bt->d_units + bt->unit_begin[0], *u1 = bt->d_units + bt->unit_begin[1];
+    const dim3 blk(32 * kBatchWarps);
+    if (bt->n_units[0] > 0) {  // thread units: forward then adjoint
+        if (hold) {
+            batch_fwd_kernel<0, 1><<<bt->fwd_blocks[0], blk, bt->fwd_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
+                                                                                  bt->d_counters, bt->x_words[0]);
+            batch_adj_kernel<0, 1><<<bt->adj_blocks[0], blk, bt->adj_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
+                                                                                  bt->d_counters + 1, bt->w_words[0]);
         } else {
-            batch_fwd_kernel<1><<<bt->fwd_blocks, 32 * kBatchWarps, bt->fwd_smem, st>>>(
-                bt->d_items, bt->d_units, bt->n_units, bt->d_counters, bt->x_words);
-            batch_adj_kernel<1><<<bt->adj_blocks, 32 * kBatchWarps, bt->adj_smem, st>>>(
-                bt->d_items, bt->d_units, bt->n_units, bt->d_counters + 1, bt->w_words);
+            batch_fwd_kernel<1, 1><<<bt->fwd_blocks[0], blk, bt->fwd_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
+                                                                                  bt->d_counters, bt->x_words[0]);
+            batch_adj_kernel<1, 1><<<bt->adj_blocks[0], blk, bt->adj_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
+                                                                                  bt->d_counters + 1, bt->w_words[0]);
+        }
+    }
+    if (bt->n_units[1] > 0) {  // warp units
+        if (hold) {
+            batch_fwd_kernel<0, 32><<<bt->fwd_blocks[1], blk, bt->fwd_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
+                                                                                   bt->d_counters + 2, bt->x_words[1]);
+            batch_adj_kernel<0, 32><<<bt->adj_blocks[1], blk, bt->adj_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
+                                                                                   bt->d_counters + 3, bt->w_words[1]);
+        } else {
+            batch_fwd_kernel<1, 32><<<bt->fwd_blocks[1], blk, bt->fwd_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
+                                                                                   bt->d_counters + 2, bt->x_words[1]);
+            batch_adj_kernel<1, 32><<<bt->adj_blocks[1], blk, bt->adj_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
+                                                                                   bt->d_counters + 3, bt->w_words[1]);
         }
     }
     if (bt->n_red_blocks > 0) batch_reduce_kernel<<<bt->n_red_blocks, 256, 0, st>>>(bt->d_items, bt->d_blk_item, bt->d_blk_j);

@@ -115,6 +115,10 @@ __device__ __forceinline__ double f2d_pos(float x)
 __device__ __forceinline__ int stoich_species(int e) { return e >> 8; }
 __device__ __forceinline__ int stoich_delta(int e) { return (int)(signed char)(e & 0xff); }
 
+// Exponential variate E = -ln u of a uniform u in (0, 1), the one function every kernel draws its
+// waiting times and race variates with (CUDA's logf, within one unit in the last place).
+__device__ __forceinline__ float neg_log_unit(float u) { return -logf(u); }
+
 // Exponential variates of one step, E[q] = -ln u_q for the first NQ words of the step's Philox
 // stream (q = 0 drives the waiting time, q = 1 + j reaction j). They do not depend on the state,
 // so the kernels draw the next step's variates while the current step's state-dependent chain
@@ -126,10 +130,10 @@ __device__ __forceinline__ void step_noise(float (&E)[NQ], uint32_t k, uint32_t 
 #pragma unroll
     for (int b = 0; b < (NQ + 3) / 4; ++b) {
         const uint4 r = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
-        if (4 * b + 0 < NQ) E[4 * b + 0] = -logf(u01(r.x));
-        if (4 * b + 1 < NQ) E[4 * b + 1] = -logf(u01(r.y));
-        if (4 * b + 2 < NQ) E[4 * b + 2] = -logf(u01(r.z));
-        if (4 * b + 3 < NQ) E[4 * b + 3] = -logf(u01(r.w));
+        if (4 * b + 0 < NQ) E[4 * b + 0] = neg_log_unit(u01(r.x));
+        if (4 * b + 1 < NQ) E[4 * b + 1] = neg_log_unit(u01(r.y));
+        if (4 * b + 2 < NQ) E[4 * b + 2] = neg_log_unit(u01(r.z));
+        if (4 * b + 3 < NQ) E[4 * b + 3] = neg_log_unit(u01(r.w));
     }
 }
 
@@ -142,7 +146,7 @@ __device__ __forceinline__ float exp_variate(uint32_t k, int q, uint32_t c2, uin
         cache = philox4x32_10(make_uint4((uint32_t)b, k, c2, c3), key0, key1);
         cached_b = b;
     }
-    return -logf(u01(word_of(cache, q & 3)));
+    return neg_log_unit(u01(word_of(cache, q & 3)));
 }
 
 // The Gumbel-max choice as an exponential race: argmax_j a_j/E_j, compared as a_j E_b > a_b E_j

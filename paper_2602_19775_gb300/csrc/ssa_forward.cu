@@ -12,6 +12,7 @@
 // index is packed 8-per-uint4 into an event log laid out [step/8][trajectory] (coalesced: the
 // threads of a warp advance their step counters together), the state is checkpointed every K
 // steps, and each sample records its bracketing step and interpolation weight.
+#include <algorithm>
 #include <cstdint>
 
 #include "ssa_fwd_body.cuh"
@@ -81,6 +82,13 @@ __global__ void colsum_final_kernel(const float *partial, int64_t n_chunks, int6
         for (int64_t b = 0; b < n_chunks; ++b) acc += partial[b * row_len + c];
         out[c] = acc * inv_n;
     }
+}
+
+// Test hook: the exponential variates -ln u of given Philox words.
+__global__ void exp_variates_kernel(const uint32_t *words, int64_t n, float *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = neg_log_unit(u01(words[i]));
 }
 
 // Test hook: uniforms of arbitrary (trajectory, step) pairs.
@@ -220,6 +228,13 @@ cudaError_t launch_column_sums(const float *x, int64_t n_rows, int64_t row_len, 
         colsum_chunks_kernel<float><<<g, 128, 0, st>>>(x, n_rows, row_len, chunk, partial);
     }
     colsum_final_kernel<<<(unsigned)((row_len + 127) / 128), 128, 0, st>>>(partial, n_chunks, row_len, 1.0f, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exp_variates(const uint32_t *words, int64_t n, float *out, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    exp_variates_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(words, n, out);
     return cudaGetLastError();
 }
 

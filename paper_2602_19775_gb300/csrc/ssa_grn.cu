@@ -241,10 +241,10 @@ __global__ void __launch_bounds__(128) grn_fwd_kernel(const GrnParams p, int rec
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int j = 4 * b + q - 1;
-                if (j < 0) { E0 = -logf(u01(r.x)); continue; }
+                if (j < 0) { E0 = neg_log_unit(u01(r.x)); continue; }
                 const float a = grn_prop(p, j, aH, aO, X, s_d);
                 a0p = __fadd_rn(a0p, a);
-                if (a > 0.0f) race(a, -logf(u01(word_of(r, q))), j, ab, Eb, jb);
+                if (a > 0.0f) race(a, neg_log_unit(u01(word_of(r, q))), j, ab, Eb, jb);
             }
         }
         const float a0 = warp_sum(a0p);
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
                         const float a = grn_prop(p, j, aH, aO, X, s_d);
                         float l = -CUDART_INF_F;
                         if (a > 0.0f) {
-                            const float E = -logf(u01(word_of(r, q)));
+                            const float E = neg_log_unit(u01(word_of(r, q)));
                             race(a, E, j, ab, Eb, jb);
                             l = __log2f(a) - __log2f(E);
                             lmaxp = fmaxf(lmaxp, l);

@@ -40,7 +40,7 @@ __global__ void probe_logf(float *out)
 {
     float a = 0.3f + threadIdx.x * 1e-6f, c = 0.5f, d = 0.6f, e = 0.7f, s = 0.0f;
     for (int i = 0; i < kIters; ++i) {
-        s += logf(a) + logf(c) + logf(d) + logf(e);
+        s += ssa::neg_log_unit(a) + ssa::neg_log_unit(c) + ssa::neg_log_unit(d) + ssa::neg_log_unit(e);
         a += 1e-7f;
         c += 1e-7f;
         d += 1e-7f;

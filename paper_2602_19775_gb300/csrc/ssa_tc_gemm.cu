@@ -214,6 +214,159 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------------------------
+// Plain GEMM kernel (one A, one B, one accumulator), built for throughput: 128 x 256 tiles, 64-wide
+// K blocks loaded by one TMA box per operand into the 128-byte-swizzled K-major layout (each row of a
+// block is 128 bytes, eight rows form a 1,024-byte swizzle atom), a four-stage mbarrier ring, one
+// thread issuing the TMA loads and another issuing tcgen05.mma, so loads run ahead of the tensor
+// cores; the accumulator is 256 TMEM columns read back by all four warps.
+// ---------------------------------------------------------------------------------------------
+constexpr int kSwBN = 256;
+constexpr int kSwStages = 4;
+constexpr int kSwTileA = 128 * 128;    // bytes: 128 rows x 64 bf16
+constexpr int kSwTileB = kSwBN * 128;  // bytes: 256 rows x 64 bf16
+constexpr int kSwStage = kSwTileA + kSwTileB;
+
+// shared-memory matrix descriptor, K-major, 128-byte swizzle: stride between 8-row groups 1,024 B
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void *p)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr(p) >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)2 << 61;               // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1) tc_gemm_sw128_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                                const __grid_constant__ CUtensorMap mapB, int M,
+                                                                int N, int K, const float *bias, float *D, int ldd,
+                                                                int *err)
+{
+    extern __shared__ __align__(1024) unsigned char sw_raw[];
+    // the swizzled tiles need 1,024-byte alignment
+    unsigned char *sw = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(sw_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sw + kSwStages * kSwStage);
+    uint64_t *empty = full + kSwStages;
+    uint64_t *done = empty + kSwStages;
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(done + 1);
+    int *s_ok = reinterpret_cast<int *>(s_tmem + 1);
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * kSwBN;
+    const int nkb = (K + 63) / 64;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
+                     "r"(kSwBN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        for (int b = 0; b < kSwStages; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], 1);
+        }
+        mbar_init(done, 1);
+        *s_ok = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    if (tid == 0) {
+        // TMA producer: wait for the stage to be free, then load both operands of k block kb
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % kSwStages, round = kb / kSwStages;
+            if (round > 0 && !mbar_wait_bounded(&empty[st], (round - 1) & 1, kWaitLimit)) {
+                atomicOr(err, kErrTcTimeout);
+                *s_ok = 0;
+                break;
+            }
+            if (!*(volatile int *)s_ok) break;
+            unsigned char *stage = sw + st * kSwStage;
+            mbar_arrive_expect_tx(&full[st], (uint32_t)kSwStage);
+            tma_load_2d(stage, &mapA, kb * 64, m0, &full[st]);
+            tma_load_2d(stage + kSwTileA, &mapB, kb * 64, n0, &full[st]);
+        }
+    } else if (tid == 32) {
+        // MMA issuer: four K = 16 steps per block, advancing the descriptors by 32 bytes inside the atom
+        const uint32_t idesc = tc_idesc(128, kSwBN);
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int st = kb % kSwStages, round = kb / kSwStages;
+            ok = mbar_wait_bounded(&full[st], round & 1, kWaitLimit) && *(volatile int *)s_ok;
+            if (!ok) break;
+            tc_fence_after();
+            const unsigned char *stage = sw + st * kSwStage;
+            const uint64_t ad = smem_desc_sw128(stage), bd = smem_desc_sw128(stage + kSwTileA);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc_mma(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(&empty[st]);  // the stage is free once these MMAs have read it
+        }
+        if (ok) tc_commit(done);
+        else {
+            atomicOr(err, kErrTcTimeout);
+            *(volatile int *)s_ok = 0;
+        }
+    }
+    __syncwarp();
+    // epilogue: wait for the last MMA, then every warp reads its 32 TMEM lanes
+    bool have = mbar_wait_bounded(done, 0, kWaitLimit);
+    if (!have && tid == 0) atomicOr(err, kErrTcTimeout);
+    tc_fence_after();
+    if (have && *(volatile int *)s_ok) {
+        const int row = m0 + 32 * warp + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+        for (int c16 = 0; c16 < kSwBN / 16; ++c16) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)(16 * c16), v);
+            const int col0 = n0 + 16 * c16;
+            if (row < M) {
+                float *dst = D + (int64_t)row * ldd + col0;
+                if (col0 + 16 <= N && (ldd % 4) == 0 && (reinterpret_cast<uintptr_t>(D) & 15) == 0) {
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4) {
+                        float4 o = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                        if (bias) {
+                            o.x += bias[col0 + i];
+                            o.y += bias[col0 + i + 1];
+                            o.z += bias[col0 + i + 2];
+                            o.w += bias[col0 + i + 3];
+                        }
+                        *reinterpret_cast<float4 *>(dst + i) = o;
+                    }
+                } else {
+                    for (int i = 0; i < 16 && col0 + i < N; ++i) dst[i] = v[i] + (bias ? bias[col0 + i] : 0.0f);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kSwBN) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -246,6 +399,32 @@ bool tc_make_map(CUtensorMap *map, const void *base, int rows, int K, int ld, in
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the same operand with one 64-element x box_rows box per K block, 128-byte swizzled in shared memory
+static bool tc_make_map_sw128(CUtensorMap *map, const void *base, int rows, int K, int ld, int box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld % 8) || K > ld) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static cudaError_t tc_gemm_sw128_launch(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
+                                        const float *bias, float *D, int ldd, int *err, cudaStream_t st)
+{
+    const size_t smem = (size_t)kSwStages * kSwStage + 128 + 1024;  // ring, barriers, alignment slack
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_sw128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + kSwBN - 1) / kSwBN));
+    tc_gemm_sw128_kernel<<<grid, 128, smem, st>>>(ma, mb, M, N, K, bias, D, ldd, err);
+    return cudaGetLastError();
 }
 
 template <int NT>
@@ -287,11 +466,9 @@ extern "C" ssa_status ssa_bf16_gemm(const uint16_t *A, const uint16_t *B, int32_
     if ((M > 0 && N > 0) && (!A || !B || !D || !err_flag)) return set_error(SSA_ERR_INVALID_ARG, "NULL GEMM operand");
     if ((lda % 8) || (ldb % 8)) return set_error(SSA_ERR_INVALID_ARG, "lda and ldb must be multiples of 8 (16-byte rows)");
     if (M == 0 || N == 0) return SSA_OK;
-    TcMaps maps;
-    memset(&maps, 0, sizeof(maps));
-    if (!tc_make_map(&maps.a[0], A, M, K, lda, 128) || !tc_make_map(&maps.b[0], B, N, K, ldb, 128))
+    CUtensorMap ma, mb;
+    if (!tc_make_map_sw128(&ma, A, M, K, lda, 128) || !tc_make_map_sw128(&mb, B, N, K, ldb, kSwBN))
         return set_error(SSA_ERR_INVALID_ARG, "tensor map encoding failed (alignment or driver entry point)");
-    TcArgs args{M, N, K, 1, 1, 1, 0, bias, D, ldd, err_flag};
-    cudaError_t e = tc_gemm_launch(maps, args, 128, static_cast<cudaStream_t>(stream));
+    cudaError_t e = tc_gemm_sw128_launch(ma, mb, M, N, K, bias, D, ldd, err_flag, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? SSA_OK : set_error(SSA_ERR_CUDA, cudaGetErrorString(e));
 }

@@ -6,12 +6,17 @@
 
 namespace ssa {
 
-// One step's propensities, a0 and race over this lane's Philox blocks. Returns E_0 on lane 0.
-// If aj / lj are given, stores a_j and log2(a_j / E_j) (or -inf) for this lane's reactions.
+// One step's propensities, a0 and race over this lane's Philox blocks b = lane, lane + 32, ...
+// Returns E_0 on lane 0. If aj / lj are given, stores a_j and log2(a_j / E_j) (or -inf) for this
+// lane's reactions. The forward takes the lane's blocks four at a time: their Philox words and
+// variates are drawn first (four independent dependency chains for the scheduler to interleave), then
+// the reactions are evaluated in increasing j, so the sums and the race see the same values in the
+// same order as the adjoint's one-block-at-a-time loop (which keeps fewer values live).
 template <bool STORE>
 __device__ __forceinline__ void warp_step_eval(const FwdParamsView &v, int k, const int *X, float &a0, float &E0,
                                                float &ab, float &Eb, int &jb, float *aj, float *lj, float &lmax)
 {
+    constexpr int CH = STORE ? 1 : 4;
     const int lane = threadIdx.x & 31;
     float a0p = 0.0f;
     E0 = 0.0f;
@@ -19,30 +24,46 @@ __device__ __forceinline__ void warp_step_eval(const FwdParamsView &v, int k, co
     Eb = 1.0f;
     jb = -1;
     lmax = -CUDART_INF_F;
-    for (int b = lane; b < v.nb; b += 32) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, v.c2, v.c3), v.key0, v.key1);
+    const int n_rounds = (v.nb + 31) >> 5;  // blocks per lane, rounded up
+    for (int t0 = 0; t0 < n_rounds; t0 += CH) {
+        float E[CH][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = 4 * b + q - 1;
-            if (j < 0) {
-                E0 = -logf(u01(r.x));
-                continue;
+        for (int t = 0; t < CH; ++t) {
+            const int b = lane + 32 * (t0 + t);
+            if (b < v.nb) {
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, v.c2, v.c3), v.key0, v.key1);
+                E[t][0] = neg_log_unit(u01(r.x));
+                E[t][1] = neg_log_unit(u01(r.y));
+                E[t][2] = neg_log_unit(u01(r.z));
+                E[t][3] = neg_log_unit(u01(r.w));
             }
-            // padded table entries (j >= M) have rate 0
-            const float a = __fmul_rn(v.s_k[j], mass_action_h(v.s_rx[j], X, 1));
-            a0p = __fadd_rn(a0p, a);
-            float l = -CUDART_INF_F;
-            if (a > 0.0f) {
-                const float E = -logf(u01(word_of(r, q)));
-                race(a, E, j, ab, Eb, jb);
-                if (STORE) {
-                    l = __log2f(a) - __log2f(E);
-                    lmax = fmaxf(lmax, l);
+        }
+#pragma unroll
+        for (int t = 0; t < CH; ++t) {
+            const int b = lane + 32 * (t0 + t);
+            if (b >= v.nb) break;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * b + q - 1;
+                if (j < 0) {
+                    E0 = E[t][0];
+                    continue;
                 }
-            }
-            if (STORE && j < v.M) {
-                aj[j] = a;
-                lj[j] = l;
+                // padded table entries (j >= M) have rate 0
+                const float a = __fmul_rn(v.s_k[j], mass_action_h(v.s_rx[j], X, 1));
+                a0p = __fadd_rn(a0p, a);
+                float l = -CUDART_INF_F;
+                if (a > 0.0f) {
+                    race(a, E[t][q], j, ab, Eb, jb);
+                    if (STORE) {
+                        l = __log2f(a) - __log2f(E[t][q]);
+                        lmax = fmaxf(lmax, l);
+                    }
+                }
+                if (STORE && j < v.M) {
+                    aj[j] = a;
+                    lj[j] = l;
+                }
             }
         }
     }

@@ -365,13 +365,21 @@ def philox_uniforms(seed: int, traj, step, n_words: int, device="cuda") -> torch
     return out
 
 
+def exp_variates(words) -> torch.Tensor:
+    """ssa_exp_variates: E = -ln u of the uniforms u of the given Philox words, as the kernels compute it."""
+    w = _as_cuda(np.asarray(words, dtype=np.uint32).view(np.int32), torch.int32, "cuda")
+    out = torch.empty(w.numel(), dtype=torch.float32, device="cuda")
+    check(_lib.lib().ssa_exp_variates(_ptr(w), int(w.numel()), _ptr(out), _stream()))
+    return out
+
+
 def pipe_rates() -> dict:
     """ssa_pipe_rates: measured operations per SM per clock of the instruction classes of a step."""
     rates = (ctypes.c_double * 5)()
     mhz = ctypes.c_double()
     sms = ctypes.c_int32()
     check(_lib.lib().ssa_pipe_rates(rates, ctypes.byref(mhz), ctypes.byref(sms)))
-    names = ("ffma", "dadd", "logf", "imad", "lg2")
+    names = ("ffma", "dadd", "neglog", "imad", "lg2")
     out = {n: float(rates[i]) for i, n in enumerate(names)}
     out["sm_clock_mhz"] = float(mhz.value)
     out["sm_count"] = int(sms.value)

@@ -6,7 +6,8 @@ import torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (512, 256, 784), (100, 200, 72), (256, 784, 512), (7, 9, 16)])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (512, 256, 784), (100, 200, 72), (256, 784, 512), (7, 9, 16),
+                                   (129, 257, 65), (300, 520, 200), (1024, 1024, 1024)])
 def test_bf16_gemm_matches_float64_reference(M, N, K):
     from paper_2602_19775_gb300 import ssa
     g = torch.Generator(device="cuda").manual_seed(M * 1000 + N + K)
