@@ -17,7 +17,7 @@ cudaError_t launch_forward_thread(const FwdParams &p, int readout, bool record, 
                                   cudaStream_t st);
 cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N, int *flag,
                                   cudaStream_t st);
-cudaError_t launch_rates(const float *log_rates, const int *rate_index, int M, int M_pad, float *k_out,
+cudaError_t launch_rates(const float *log_rates, const int *rate_index, int M, int M_pad, int lane_major, float *k_out,
                          cudaStream_t st);
 cudaError_t launch_ensemble_mean(const void *obs, bool is_int, int64_t n_traj, int64_t row_len, float *partial,
                                  int64_t chunk, float *out, cudaStream_t st);
@@ -253,7 +253,8 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
     net->inc_off = (uint32_t)(16 * Mp + 4 * nnz_pad);
     net->inc_list_off = net->inc_off + (uint32_t)(4 * inc_ptr_pad);
     net->tab_bytes = net->inc_list_off + (uint32_t)(4 * inc_list_pad);
-    const size_t bytes = net->tab_bytes + (size_t)Mp * 4;
+    // blob = [tables][rate_index: int Mp][tables again, with rx in the warp kernels' lane-major order]
+    const size_t bytes = 2 * (size_t)net->tab_bytes + (size_t)Mp * 4;
     cudaError_t e = cudaMalloc(&net->d_blob, bytes);
     if (e != cudaSuccess) {
         delete net;
@@ -272,6 +273,14 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
         e = cudaMemcpy(b + net->inc_off, inc_ptr.data(), 4 * (size_t)inc_ptr_pad, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && inc_list_pad > 0)
         e = cudaMemcpy(b + net->inc_list_off, inc_list.data(), 4 * (size_t)inc_list_pad, cudaMemcpyHostToDevice);
+    net->d_rx_warp = reinterpret_cast<int4 *>(b + net->tab_bytes + (size_t)Mp * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(net->d_rx_warp, net->d_rx, net->tab_bytes, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) {
+        const int nb = (n_reactions + 4) >> 2;
+        std::vector<int4> rxp(Mp, make_int4(-1, -1, 0, 0));
+        for (int j = 0; j < n_reactions; ++j) rxp[((j + 1) & 3) * nb + ((j + 1) >> 2)] = rx[j];
+        e = cudaMemcpy(net->d_rx_warp, rxp.data(), 16 * (size_t)Mp, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(net->d_blob);
         delete net;
@@ -345,11 +354,13 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     CUDA_TRY(cudaMemsetAsync(flag, 0, 16 * sizeof(int), st));
     if (S > 0) CUDA_TRY(cudaMemcpyAsync(ws + L.ts, sample_times, (size_t)S * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (n_obs > 0) CUDA_TRY(cudaMemcpyAsync(ws + L.obs_sp, obs_species, (size_t)n_obs * sizeof(int), cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(launch_rates(log_rates, net->d_rate_index, net->M, L.M_pad, reinterpret_cast<float *>(ws + L.k_rates), st));
+    // the warp kernels read their tables and rates lane-major
+    CUDA_TRY(launch_rates(log_rates, net->d_rate_index, net->M, L.M_pad, variant == 32 ? 1 : 0,
+                          reinterpret_cast<float *>(ws + L.k_rates), st));
     CUDA_TRY(launch_validate_inputs(reinterpret_cast<const double *>(ws + L.ts), S, t_end,
                                     reinterpret_cast<const int *>(ws + L.obs_sp), n_obs, net->N, flag, st));
     FwdParams p{};
-    p.rx = net->d_rx;
+    p.rx = variant == 32 ? net->d_rx_warp : net->d_rx;
     p.k_rates = reinterpret_cast<const float *>(ws + L.k_rates);
     p.tab_bytes = net->tab_bytes;
     p.k_bytes = (uint32_t)(L.M_pad * 4);
@@ -473,7 +484,7 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     int *flag = reinterpret_cast<int *>(ws + L.flag);
     CUDA_TRY(cudaMemsetAsync(flag + 2, 0, sizeof(int), st));  // mismatch counter
     AdjParams p{};
-    p.rx = net->d_rx;
+    p.rx = run->variant == 32 ? net->d_rx_warp : net->d_rx;
     p.k_rates = reinterpret_cast<const float *>(ws + L.k_rates);
     p.tab_bytes = net->tab_bytes;
     p.k_bytes = (uint32_t)(L.M_pad * 4);

@@ -63,8 +63,12 @@ __global__ void batch_prepare_kernel(const BatchItem *items, int n_items)
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const BatchItem &b = items[it];
         float *k = const_cast<float *>(b.f.k_rates);
-        for (int j = threadIdx.x; j < b.f.Mp; j += blockDim.x)
-            k[j] = j < b.f.M ? (float)exp((double)b.log_rates[b.rate_index[j]]) : 0.0f;
+        const int nb = (b.f.M + 4) >> 2;
+        for (int e = threadIdx.x; e < b.f.Mp; e += blockDim.x) {
+            // warp items keep their rates lane-major (position q nb + b holds reaction 4 b + q - 1)
+            const int j = b.variant == 1 ? e : (e < 4 * nb ? 4 * (e % nb) + e / nb - 1 : -1);
+            k[e] = (j >= 0 && j < b.f.M) ? (float)exp((double)b.log_rates[b.rate_index[j]]) : 0.0f;
+        }
         int *flag = const_cast<int *>(b.f.flag);
         for (int s = threadIdx.x; s < b.f.S; s += blockDim.x) {
             const bool ok = b.f.ts[s] >= 0.0 && b.f.ts[s] <= b.f.t_end && (s == 0 || b.f.ts[s] >= b.f.ts[s - 1]);
@@ -217,7 +221,8 @@ __global__ void __launch_bounds__(32 * kBatchWarps, VARIANT == 1 ? 1 : kBatchWar
                 __syncwarp();
             }
             float *slot = p.partial + b.slot_off + (int64_t)u.slot * p.M;
-            for (int j = lane; j < p.M; j += 32) slot[j] = dA[j];
+            const int nb = (p.M + 4) >> 2;
+            for (int j = lane; j < p.M; j += 32) slot[j] = dA[jpos(j, nb)];
         }
         __syncwarp();
     }
@@ -457,7 +462,7 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
         BatchItem &bi = bt->h_items[it];
         FwdParams &p = bi.f;
         AdjParams &a = bi.a;
-        p.rx = a.rx = net->d_rx;
+        p.rx = a.rx = bt->variant[it] == 32 ? net->d_rx_warp : net->d_rx;  // warp items: lane-major tables
         p.k_rates = a.k_rates = k;
         p.tab_bytes = a.tab_bytes = net->tab_bytes;
         p.k_bytes = a.k_bytes = (uint32_t)(net->Mp * 4);

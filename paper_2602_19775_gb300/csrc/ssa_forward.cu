@@ -55,11 +55,16 @@ __global__ void validate_inputs_kernel(const double *ts, int S, double t_end, co
         if (obs_sp[c] < 0 || obs_sp[c] >= N) atomicOr(flag, kErrBadObs);
 }
 
-// k_j = exp(theta_{r(j)}) rounded once to binary32 (computed in binary64).
-__global__ void rates_kernel(const float *log_rates, const int *rate_index, int M, int M_pad, float *k_out)
+// k_j = exp(theta_{r(j)}) rounded once to binary32 (computed in binary64); lane_major stores reaction j
+// at jpos(j) for the warp kernels (position q nb + b holds reaction 4 b + q - 1).
+__global__ void rates_kernel(const float *log_rates, const int *rate_index, int M, int M_pad, int lane_major,
+                             float *k_out)
 {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M_pad; j += gridDim.x * blockDim.x)
-        k_out[j] = j < M ? (float)exp((double)log_rates[rate_index[j]]) : 0.0f;
+    const int nb = (M + 4) >> 2;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M_pad; e += gridDim.x * blockDim.x) {
+        const int j = !lane_major ? e : (e < 4 * nb ? 4 * (e % nb) + e / nb - 1 : -1);
+        k_out[e] = (j >= 0 && j < M) ? (float)exp((double)log_rates[rate_index[j]]) : 0.0f;
+    }
 }
 
 // Deterministic ensemble mean: per-chunk column sums (fixed order), then a fixed-order sum.
@@ -195,9 +200,10 @@ cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_rates(const float *log_rates, const int *rate_index, int M, int M_pad, float *k_out, cudaStream_t st)
+cudaError_t launch_rates(const float *log_rates, const int *rate_index, int M, int M_pad, int lane_major, float *k_out,
+                         cudaStream_t st)
 {
-    rates_kernel<<<(M_pad + 255) / 256, 256, 0, st>>>(log_rates, rate_index, M, M_pad, k_out);
+    rates_kernel<<<(M_pad + 255) / 256, 256, 0, st>>>(log_rates, rate_index, M, M_pad, lane_major, k_out);
     return cudaGetLastError();
 }
 

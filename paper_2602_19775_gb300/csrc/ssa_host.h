@@ -11,10 +11,12 @@
 struct ssa_network {
     int32_t N, M, Mp, P, nnz, nnz_pad;  // Mp = 4 * ceil((M + 1)/4): padded reaction count
     // d_blob = [rx: int4 Mp][stoich: int nnz_pad][inc_ptr: int N+1, padded][inc_list: int 2M, padded]
-    //          [rate_index: int Mp]; the first four parts are the tables staged into shared memory
+    //          [rate_index: int Mp][the four table parts again, rx lane-major]; a table region is what
+    //          the kernels stage into shared memory
     void *d_blob;
     uint32_t inc_off, inc_list_off;
     int4 *d_rx;
+    int4 *d_rx_warp;  // the same tables with rx in lane-major order (jpos), for the warp kernels
     int *d_stoich;
     int *d_rate_index;
     uint32_t tab_bytes;

@@ -30,6 +30,12 @@ struct FwdParamsView {
     uint32_t c2, c3, key0, key1;
 };
 
+// Lane-major position of reaction j in the tables of the warp-per-trajectory kernels. Reaction j is
+// driven by word q = (j + 1) % 4 of Philox block b = (j + 1) / 4, which lane b % 32 draws; storing it
+// at q * nb + b (nb = number of blocks) puts the entries the 32 lanes read for one word q side by
+// side, so those shared-memory accesses are free of bank conflicts.
+__device__ __forceinline__ int jpos(int j, int nb) { return ((j + 1) & 3) * nb + ((j + 1) >> 2); }
+
 // Warp reductions shared by the warp-per-trajectory kernels (butterfly: every lane gets the same
 // bits; the race keeps the lowest j on equal products).
 __device__ __forceinline__ void warp_race_combine(float &ab, float &Eb, int &jb)

@@ -11,6 +11,8 @@
 //     and ties to the lowest j;
 //   - the clock, the sample writes and the state update are warp-uniform (lanes share the stoichiometry
 //     and observable loops).
+// The network tables and the per-reaction values are stored lane-major (jpos in ssa_internal.cuh), so
+// the lanes' table reads are free of shared-memory bank conflicts.
 // The adjoint keeps per-reaction values in per-warp shared memory and accumulates the state adjoint
 // through a species -> reactant-slot incidence table in a fixed order (no atomics, deterministic).
 // A run recorded by the warp forward is differentiated by the warp adjoint, which repeats the same
@@ -81,9 +83,10 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(const AdjParams p)
     __syncthreads();
     // fixed-order reduction over the block's warps
     float *base0 = reinterpret_cast<float *>(smem + p.tab_bytes + p.k_bytes + 16);
+    const int nb = (M + 4) >> 2;
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         float acc = 0.0f;
-        for (int w = 0; w < W; ++w) acc += base0[w * per_warp + 2 * Npad + 4 * Mp + j];
+        for (int w = 0; w < W; ++w) acc += base0[w * per_warp + 2 * Npad + 4 * Mp + jpos(j, nb)];
         p.partial[(int64_t)blockIdx.x * M + j] = acc;
     }
 }

@@ -4,6 +4,12 @@
 
 #include "ssa_adj_body.cuh"
 
+// Philox blocks a lane draws together in the adjoint's first pass (the forward draws four); a tuning
+// constant: more blocks give the scheduler more independent work but keep more registers live.
+#ifndef SSA_WARP_ADJ_CHUNK
+#define SSA_WARP_ADJ_CHUNK 1
+#endif
+
 namespace ssa {
 
 // One step's propensities, a0 and race over this lane's Philox blocks b = lane, lane + 32, ...
@@ -16,7 +22,7 @@ template <bool STORE>
 __device__ __forceinline__ void warp_step_eval(const FwdParamsView &v, int k, const int *X, float &a0, float &E0,
                                                float &ab, float &Eb, int &jb, float *aj, float *lj, float &lmax)
 {
-    constexpr int CH = STORE ? 1 : 4;
+    constexpr int CH = STORE ? SSA_WARP_ADJ_CHUNK : 4;
     const int lane = threadIdx.x & 31;
     float a0p = 0.0f;
     E0 = 0.0f;
@@ -49,8 +55,9 @@ __device__ __forceinline__ void warp_step_eval(const FwdParamsView &v, int k, co
                     E0 = E[t][0];
                     continue;
                 }
-                // padded table entries (j >= M) have rate 0
-                const float a = __fmul_rn(v.s_k[j], mass_action_h(v.s_rx[j], X, 1));
+                // tables in lane-major order; padded entries (j >= M) have rate 0
+                const int pos = q * v.nb + b;
+                const float a = __fmul_rn(v.s_k[pos], mass_action_h(v.s_rx[pos], X, 1));
                 a0p = __fadd_rn(a0p, a);
                 float l = -CUDART_INF_F;
                 if (a > 0.0f) {
@@ -61,8 +68,8 @@ __device__ __forceinline__ void warp_step_eval(const FwdParamsView &v, int k, co
                     }
                 }
                 if (STORE && j < v.M) {
-                    aj[j] = a;
-                    lj[j] = l;
+                    aj[pos] = a;
+                    lj[pos] = l;
                 }
             }
         }
@@ -112,7 +119,7 @@ __device__ __forceinline__ void warp_fwd_body(const FwdParams &p, const int4 *s_
         if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }
         const float tau = __fdividef(E0, a0);
         const double t_next = t + f2d_pos(tau);
-        const int4 rj = s_rx[jb];
+        const int4 rj = s_rx[jpos(jb, v.nb)];
         const bool slow = gt_nonneg(t_next, thr);
         const bool cross = slow && gt_nonneg(t_next, p.t_end);
         if (!cross) {
@@ -258,7 +265,7 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
             warp_step_eval<true>(v, k, X, a0, E0, ab, Eb, jb, aj, lj, lmax);
             mism += (jb != jk);
             const float tau = __fdividef(E0, a0);
-            const int4 rk = s_rx[jk];
+            const int4 rk = s_rx[jpos(jk, v.nb)];
             float dt_dir = 0.0f, dtau_dir = 0.0f;
             if (READOUT == SSA_READOUT_LINEAR) {
                 // serial on lane 0 (observed species may repeat), broadcast afterwards
@@ -294,13 +301,15 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
                 for (int q = 0; q < 4; ++q) {
                     const int j = 4 * b + q - 1;
                     if (j < 0 || j >= M) continue;
-                    const float l = lj[j];
+                    const int pos = q * v.nb + b;
+                    const float l = lj[pos];
                     const float qv = l == -CUDART_INF_F ? 0.0f : exp2f((l - lmax) * invT);
-                    lj[j] = qv;
+                    lj[pos] = qv;
                     if (qv > 0.0f) {
-                        const int4 rx = s_rx[j];
+                        const int4 rx = s_rx[pos];
                         float w = 0.0f;
                         for (int e = rx.z; e < rx.w; ++e) w += (float)stoich_delta(s_st[e]) * lam[stoich_species(s_st[e])];
+                        ct[pos] = w;  // kept for pass 3, which overwrites the slot afterwards
                         Zp += qv;
                         Wp += qv * w;
                     }
@@ -314,18 +323,15 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
                 for (int q = 0; q < 4; ++q) {
                     const int j = 4 * b + q - 1;
                     if (j < 0 || j >= M) continue;
-                    const int4 rx = s_rx[j];
-                    const float qv = lj[j], a = aj[j];
+                    const int pos = q * v.nb + b;
+                    const int4 rx = s_rx[pos];
+                    const float qv = lj[pos], a = aj[pos];
                     float psi = 0.0f;
-                    if (qv > 0.0f) {
-                        float w = 0.0f;
-                        for (int e = rx.z; e < rx.w; ++e) w += (float)stoich_delta(s_st[e]) * lam[stoich_species(s_st[e])];
-                        psi = qv * invZ * (w - Wbar) * invT;
-                    }
-                    dA[j] += psi + dLda0 * a;
+                    if (qv > 0.0f) psi = qv * invZ * (ct[pos] - Wbar) * invT;  // w_j from pass 2
+                    dA[pos] += psi + dLda0 * a;
                     float c1 = 0.0f, c2 = 0.0f;
                     if (rx.x >= 0) {
-                        const float c_tau = dLda0 * s_k[j];
+                        const float c_tau = dLda0 * s_k[pos];
                         const float x1 = int2f(X[rx.x]);
                         if (rx.y < 0) {
                             c1 = (a > 0.0f ? __fdividef(psi, x1) : 0.0f) + c_tau;
@@ -338,15 +344,39 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
                             c2 = (a > 0.0f ? __fdividef(psi, x2) : 0.0f) + c_tau * x1;
                         }
                     }
-                    ct[2 * j] = c1;
-                    ct[2 * j + 1] = c2;
+                    ct[pos] = c1;          // reactant slot 0
+                    ct[p.Mp + pos] = c2;   // reactant slot 1
                 }
             }
             __syncwarp();
-            for (int sp = lane; sp < N; sp += 32) {
-                float acc = 0.0f;
-                for (int e = s_inc_ptr[sp]; e < s_inc_ptr[sp + 1]; ++e) acc += ct[s_inc[e]];
-                lam[sp] += acc;
+            // lambda_s += sum of the reactant-slot contributions of species s. With N <= 32 each species
+            // gets g = 32 / 2^ceil(log2 N) lanes that stride over its incidence list with four
+            // accumulators and combine by a butterfly inside the group; with more species each lane takes
+            // whole species. The order is fixed, so the result is the same on every run.
+            int pow2 = 1;
+            while (pow2 < N && pow2 < 32) pow2 <<= 1;
+            const int gsz = N <= 32 ? 32 / pow2 : 1;
+            for (int base = 0; base < N; base += 32 / gsz) {
+                const int sp = base + lane / gsz, r = lane % gsz;
+                float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f;
+                if (sp < N) {
+                    const int e1 = s_inc_ptr[sp + 1];
+                    int e = s_inc_ptr[sp] + r;
+                    auto slot_val = [&](int ee) {
+                        const int slot = s_inc[ee];  // 2 j + reactant slot
+                        return ct[(slot & 1) * p.Mp + jpos(slot >> 1, v.nb)];
+                    };
+                    for (; e + 3 * gsz < e1; e += 4 * gsz) {
+                        c0 += slot_val(e);
+                        c1 += slot_val(e + gsz);
+                        c2 += slot_val(e + 2 * gsz);
+                        c3 += slot_val(e + 3 * gsz);
+                    }
+                    for (; e < e1; e += gsz) c0 += slot_val(e);
+                }
+                float acc = (c0 + c1) + (c2 + c3);
+                for (int off = gsz >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                if (r == 0 && sp < N) lam[sp] += acc;
             }
             mu += dt_dir;
         }
@@ -372,7 +402,7 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
         --ck_off;
         __syncwarp();
         if (k > 0) {
-            const int4 rp = s_rx[event_at(k - 1)];
+            const int4 rp = s_rx[jpos(event_at(k - 1), v.nb)];
             for (int e = rp.z + lane; e < rp.w; e += 32) X[stoich_species(s_st[e])] -= stoich_delta(s_st[e]);
         }
         __syncwarp();
