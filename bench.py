@@ -365,8 +365,8 @@ def run_ours(args):
     legs = set() if args.no_extra else {x for x in args.legs.split(",") if x}
     osc = oscillator_extra(ssa, dev) if (rank == 0 and "oscillator" in legs) else None
     batch = uneven_batch_extra(ssa, dev, args.batch_scale) if (rank == 0 and "batch" in legs) else None
-    grn = grn_extra(ssa, dev) if (rank == 0 and "grn" in legs) else None
-    warp = warp_extra(ssa, dev) if (rank == 0 and "warp" in legs) else None
+    grn = grn_extra(ssa, dev, n_img=args.grn_images) if (rank == 0 and "grn" in legs) else None
+    warp = warp_extra(ssa, dev, n=args.warp_traj) if (rank == 0 and "warp" in legs) else None
     M = wl.net.n_reactions
     rates = ssa.pipe_rates()
     log_slots = 128.0 / rates["neglog"]
@@ -708,6 +708,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the oscillator and uneven-batch fields")
     ap.add_argument("--legs", default="oscillator,batch,grn,warp",
                     help="comma-separated extra fields to measure: oscillator, batch, grn, warp ('none' for none)")
+    ap.add_argument("--grn-images", type=int, default=512, help="images of the GRN field (64 trajectories each)")
+    ap.add_argument("--warp-traj", type=int, default=16384, help="trajectories of the warp-kernel field")
     ap.add_argument("--batch-scale", type=float, default=1.0 / 16,
                     help="trajectories per network of the uneven batch, as a fraction of the full counts")
     args = ap.parse_args()
