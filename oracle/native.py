@@ -58,6 +58,8 @@ def _load():
         lib.orc_run.restype = ctypes.c_int
         lib.orc_run.argtypes = [p, i64, i64, p, i32, f64, p, i32, p, i32, u64, i32, i64, p, f64,
                                 p, p, p, p, p, p, p, i64, p, i32]
+        lib.orc_run_sel.restype = ctypes.c_int
+        lib.orc_run_sel.argtypes = [i32] + lib.orc_run.argtypes
         lib.orc_uniforms.restype = None
         lib.orc_uniforms.argtypes = [u64, u64, u64, i64, p]
         lib.orc_philox_blocks.restype = None
@@ -104,8 +106,12 @@ class OracleResult:
 
 def run(net, log_rates, x0, n_traj: int, t_end: float, sample_times, obs_species, seed: int,
         readout: int = HOLD, max_steps: int = 1 << 30, traj_offset: int = 0, dl_dobs=None,
-        temperature: float = 1.0, ev_cap: int = 0, n_threads: int | None = None) -> OracleResult:
-    """Run the oracle. `net` is a ssa_workloads.NetworkSpec; x0 is [N] or [n_traj, N]."""
+        temperature: float = 1.0, ev_cap: int = 0, n_threads: int | None = None,
+        selector: str = "gumbel") -> OracleResult:
+    """Run the oracle. `net` is a ssa_workloads.NetworkSpec; x0 is [N] or [n_traj, N]. selector "gumbel"
+    is the Gumbel-max choice (Section 3.2); "direct" the standard direct method (Section 2: u_1 a0 against
+    the cumulative propensities), forward only; its margins are distances of u_1 a0 to the nearest
+    cumulative boundary, relative to a0."""
     lib = _load()
     reactants = np.ascontiguousarray(net.reactants, dtype=np.int32)
     sptr = np.ascontiguousarray(net.stoich_ptr, dtype=np.int32)
@@ -141,7 +147,8 @@ def run(net, log_rates, x0, n_traj: int, t_end: float, sample_times, obs_species
         tm = np.zeros((n_traj, ev_cap), dtype=np.float64)
     if n_threads is None:
         n_threads = min(os.cpu_count() or 1, max(1, n_traj // 8))
-    rc = lib.orc_run(ctypes.byref(cnet), n_traj, traj_offset, _ptr(x0), per_traj, float(t_end),
+    sel = {"gumbel": 0, "direct": 1}[selector]
+    rc = lib.orc_run_sel(sel, ctypes.byref(cnet), n_traj, traj_offset, _ptr(x0), per_traj, float(t_end),
                      _ptr(ts), S, _ptr(obs_sp), n_obs, ctypes.c_uint64(seed), readout, max_steps,
                      _ptr(g), float(temperature), _ptr(obs), _ptr(draws), _ptr(status), _ptr(dth),
                      _ptr(ev), _ptr(mg), _ptr(tm), ev_cap, _ptr(final_x), int(n_threads))

@@ -198,6 +198,7 @@ typedef struct {
     double t_end;
     int64_t max_steps;
     uint64_t seed;
+    int32_t selector; /* 0: Gumbel-max (Section 3.2); 1: the standard direct method (Section 2) */
 } orc_sim_cfg;
 
 /*
@@ -236,20 +237,37 @@ static int orc_simulate_one(const orc_sim_cfg *cfg, uint64_t traj, const int32_t
         /* waiting time by inverse transform (Section 2) */
         double u0 = orc_uniform(cfg->seed, traj, (uint64_t)k, 0);
         double tau = -log(u0) / a0;
-        /* Gumbel-max choice over the active reactions (Section 3.2); ties to the lowest j */
         int best = -1;
-        double s1 = -INFINITY, s2 = -INFINITY;
-        for (int j = 0; j < M; ++j) {
-            if (!(a[j] > 0.0)) continue;
-            double u = orc_uniform(cfg->seed, traj, (uint64_t)k, 1 + j);
-            double G = -log(-log(u));
-            double key = log(a[j]) + G;
-            if (key > s1) { s2 = s1; s1 = key; best = j; }
-            else if (key > s2) { s2 = key; }
+        if (cfg->selector == 0) {
+            /* Gumbel-max choice over the active reactions (Section 3.2); ties to the lowest j */
+            double s1 = -INFINITY, s2 = -INFINITY;
+            for (int j = 0; j < M; ++j) {
+                if (!(a[j] > 0.0)) continue;
+                double u = orc_uniform(cfg->seed, traj, (uint64_t)k, 1 + j);
+                double G = -log(-log(u));
+                double key = log(a[j]) + G;
+                if (key > s1) { s2 = s1; s1 = key; best = j; }
+                else if (key > s2) { s2 = key; }
+            }
+            p->margin[k] = (s2 == -INFINITY) ? 1.0 : -expm1(s2 - s1);
+        } else {
+            /* direct method (Section 2): the first reaction whose cumulative propensity exceeds u_1 a0;
+               the margin is the distance of u_1 a0 to the nearest cumulative boundary, relative to a0 */
+            double r = orc_uniform(cfg->seed, traj, (uint64_t)k, 1) * a0, cum = 0.0, lo = 0.0;
+            for (int j = 0; j < M; ++j) {
+                if (!(a[j] > 0.0)) continue;
+                best = j;
+                lo = cum;
+                cum += a[j];
+                if (cum > r) break;
+            }
+            const double d_lo = best >= 0 && lo > 0.0 ? r - lo : INFINITY;
+            const double d_hi = cum > r && cum < a0 ? cum - r : INFINITY;
+            const double d = d_lo < d_hi ? d_lo : d_hi;
+            p->margin[k] = isfinite(d) ? d / a0 : 1.0;
         }
         p->j[k] = best;
         p->tau[k] = tau;
-        p->margin[k] = (s2 == -INFINITY) ? 1.0 : -expm1(s2 - s1);
         double t_next = p->t[k] + tau;
         p->t[k + 1] = t_next;
         p->n_draws = k + 1;
@@ -453,6 +471,7 @@ typedef struct {
     double *times_out;         /* [n_traj][ev_cap] t_{k+1} per draw, or NULL */
     int64_t ev_cap;
     int32_t *final_x_out;      /* [n_traj][N] or NULL: last visited state */
+    int32_t selector;          /* 0: Gumbel-max, 1: direct method */
     /* work distribution */
     int32_t n_threads;
     int64_t next;              /* guarded by lock */
@@ -465,7 +484,7 @@ static void *orc_worker(void *arg)
     orc_job *job = (orc_job *)arg;
     const orc_network *net = job->net;
     const int N = net->n_species, P = net->n_params;
-    orc_sim_cfg cfg = {net, job->t_end, job->max_steps, job->seed};
+    orc_sim_cfg cfg = {net, job->t_end, job->max_steps, job->seed, job->selector};
     orc_path path;
     memset(&path, 0, sizeof(path));
     double *dth = (double *)calloc((size_t)(P > 0 ? P : 1), sizeof(double));
@@ -514,17 +533,19 @@ static void *orc_worker(void *arg)
  * straight-through gradient of each one. Returns 0 on success, -1 on bad input or allocation
  * failure.
  */
-int orc_run(const orc_network *net, int64_t n_traj, int64_t traj_offset,
-            const int32_t *x0, int32_t x0_per_traj, double t_end,
-            const double *ts, int32_t S, const int32_t *obs_species, int32_t n_obs,
-            uint64_t seed, int32_t readout, int64_t max_steps,
-            const double *dL_dobs, double temperature,
-            double *obs_out, int64_t *draws_out, int32_t *status_out,
-            double *dtheta_traj_out,
-            int32_t *events_out, double *margins_out, double *times_out, int64_t ev_cap,
-            int32_t *final_x_out, int32_t n_threads)
+int orc_run_sel(int32_t selector, const orc_network *net, int64_t n_traj, int64_t traj_offset,
+                const int32_t *x0, int32_t x0_per_traj, double t_end,
+                const double *ts, int32_t S, const int32_t *obs_species, int32_t n_obs,
+                uint64_t seed, int32_t readout, int64_t max_steps,
+                const double *dL_dobs, double temperature,
+                double *obs_out, int64_t *draws_out, int32_t *status_out,
+                double *dtheta_traj_out,
+                int32_t *events_out, double *margins_out, double *times_out, int64_t ev_cap,
+                int32_t *final_x_out, int32_t n_threads)
 {
     if (!net || n_traj < 0 || S < 0 || n_obs < 0 || max_steps < 0) return -1;
+    if (selector != 0 && selector != 1) return -1;
+    if (selector == 1 && dL_dobs) return -1;  /* the straight-through gradient is of the Gumbel-max choice */
     if (net->n_species <= 0 || net->n_reactions < 0) return -1;
     for (int s = 0; s < S; ++s) {
         if (!(ts[s] >= 0.0 && ts[s] <= t_end)) return -1;
@@ -543,6 +564,7 @@ int orc_run(const orc_network *net, int64_t n_traj, int64_t traj_offset,
     job.dtheta_traj_out = dtheta_traj_out; job.events_out = events_out;
     job.margins_out = margins_out; job.times_out = times_out; job.ev_cap = ev_cap;
     job.final_x_out = final_x_out;
+    job.selector = selector;
     job.n_threads = n_threads > 0 ? n_threads : 1;
     pthread_mutex_init(&job.lock, NULL);
     if (job.n_threads == 1) {
@@ -556,6 +578,21 @@ int orc_run(const orc_network *net, int64_t n_traj, int64_t traj_offset,
     }
     pthread_mutex_destroy(&job.lock);
     return job.error ? -1 : 0;
+}
+
+int orc_run(const orc_network *net, int64_t n_traj, int64_t traj_offset,
+            const int32_t *x0, int32_t x0_per_traj, double t_end,
+            const double *ts, int32_t S, const int32_t *obs_species, int32_t n_obs,
+            uint64_t seed, int32_t readout, int64_t max_steps,
+            const double *dL_dobs, double temperature,
+            double *obs_out, int64_t *draws_out, int32_t *status_out,
+            double *dtheta_traj_out,
+            int32_t *events_out, double *margins_out, double *times_out, int64_t ev_cap,
+            int32_t *final_x_out, int32_t n_threads)
+{
+    return orc_run_sel(0, net, n_traj, traj_offset, x0, x0_per_traj, t_end, ts, S, obs_species, n_obs, seed,
+                       readout, max_steps, dL_dobs, temperature, obs_out, draws_out, status_out,
+                       dtheta_traj_out, events_out, margins_out, times_out, ev_cap, final_x_out, n_threads);
 }
 
 /* ======================================================================================== */
