@@ -246,11 +246,12 @@ def run_ours(args):
             ev[3].record(stream)
         return fw
 
-    def fwd_only(seed, ev=None, specialize=True):
+    def fwd_only(seed, ev=None, specialize=True, selector="gumbel"):
         if ev is not None:
             ev[0].record(stream)
         fw = ssa.forward(net, theta, n, x0, wl.t_end, ts, obs_sp, seed, readout="linear", record=False,
-                         max_steps=max_steps, traj_offset=offset, workspace=ws, obs_out=obs, specialize=specialize)
+                         max_steps=max_steps, traj_offset=offset, workspace=ws, obs_out=obs, specialize=specialize,
+                         selector=selector)
         if ev is not None:
             ev[1].record(stream)
         return fw
@@ -286,6 +287,19 @@ def run_ours(args):
             flush.fill_(s & 0xFF)
         barrier()
     variant = fw.run.variant
+    # the plain direct method (one uniform and a cumulative search per step) on the same steps: the
+    # plain-SSA forward the method's forward and forward+adjoint compare with (outside the timed region)
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    pdraws = torch.zeros((), dtype=torch.int64, device=dev)
+    for w in range(2):
+        fwd_only(100 + w, selector="direct")
+    for s in range(K):
+        pfw = fwd_only(1000 + s, pev[s], selector="direct")
+        pdraws += pfw.draws.sum()
+        flush.fill_(s & 0xFF)
+    torch.cuda.synchronize()
+    plain_fwd = float(pdraws.item()) / (sum(e[0].elapsed_time(e[1]) for e in pev) / 1e3)
+    del pfw
     # the same steps on the generic (table-driven) thread kernels, for comparison (outside the timed region)
     gev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     gdraws = torch.zeros((), dtype=torch.int64, device=dev)
@@ -400,6 +414,9 @@ def run_ours(args):
                    "parallelism": f"trajectory shards x{world}"},
         "fwd_steps_per_s": fwd_value,
         "fwd_adj_over_fwd": value / fwd_value,
+        "plain_direct_fwd_steps_per_s": plain_fwd,
+        "fwd_adj_over_plain_fwd": value / plain_fwd,
+        "fwd_over_plain_fwd": fwd_value / plain_fwd,
         "ssa_steps_per_bench_step": steps_total / K,
         "grad_rel_err_vs_fp64": grad_err,
         "kernel_ms": {"forward_record": float(np.mean(fwd_ms)), "adjoint": float(np.mean(bwd_ms)),

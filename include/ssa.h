@@ -71,7 +71,15 @@ typedef struct ssa_fwd_opts {
                                  (NVRTC, at most 24 species, 24 reactions, 96 stoichiometric
                                  entries; the same results bit for bit) when it qualifies;
                                  1: always the generic kernels                                  */
+    int32_t selector;         /* SSA_SELECT_GUMBEL (the method) or SSA_SELECT_DIRECT (the plain
+                                 direct method, forward only: record must be 0; runs on the
+                                 network-specialised kernels)                                   */
+    int32_t reserved;         /* must be 0                                                       */
 } ssa_fwd_opts;
+
+#define SSA_SELECT_GUMBEL 0 /* j* = argmax_j a_j / E_{1+j}, the Gumbel-max choice (Section 3.2)    */
+#define SSA_SELECT_DIRECT 1 /* the first j with a_1 + ... + a_j > u_1 a0 in reaction order: the
+                               standard direct method (Section 2), the plain-SSA comparator       */
 
 /*
  * ssa_create_network -- a mass-action reaction network (Section 2).

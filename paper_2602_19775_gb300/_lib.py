@@ -44,6 +44,8 @@ class FwdOpts(ctypes.Structure):
         ("max_steps", ctypes.c_int64),
         ("block_threads", ctypes.c_int32),
         ("no_specialize", ctypes.c_int32),
+        ("selector", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -39,8 +39,8 @@ cudaError_t launch_exp_variates(const uint32_t *words, int64_t n, float *out, cu
 struct JitKernels;
 bool jit_eligible(const ssa_network *net);
 const JitKernels *jit_kernels(const ssa_network *net, std::string &why);
-cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int readout, bool record, int block,
-                               cudaStream_t st);
+cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int readout, bool record, int selector,
+                               int block, cudaStream_t st);
 cudaError_t jit_launch_backward(const JitKernels *k, const AdjParams &p, int readout, int block, int64_t grid,
                                 cudaStream_t st);
 constexpr int kJitBlock = 64;
@@ -133,6 +133,9 @@ bool opts_valid(const ssa_fwd_opts *o)
     if (o->block_threads != 0 && (o->block_threads % 32 != 0 || o->block_threads < 32 || o->block_threads > 256))
         return false;
     if (o->no_specialize != 0 && o->no_specialize != 1) return false;
+    if (o->selector != SSA_SELECT_GUMBEL && o->selector != SSA_SELECT_DIRECT) return false;
+    if (o->selector == SSA_SELECT_DIRECT && o->record) return false;  // the gradient is of the Gumbel-max choice
+    if (o->reserved != 0) return false;
     return true;
 }
 
@@ -335,6 +338,8 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
         jit = jit_kernels(net, why);
         if (jit) variant = 2;
     }
+    if (opts->selector == SSA_SELECT_DIRECT && (variant != 2 || ev_in))
+        return fail(SSA_ERR_UNSUPPORTED, "the direct method runs on the network-specialised kernels (N and M <= 24)");
     int block = 0;
     if (variant == 2) {
         block = kJitBlock;
@@ -398,7 +403,7 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     p.n_ev_in = n_ev_in;
     p.ev_in_stride = ev_stride;
     if (variant == 2)
-        CUDA_TRY(jit_launch_forward(jit, p, opts->readout, opts->record != 0, block, st));
+        CUDA_TRY(jit_launch_forward(jit, p, opts->readout, opts->record != 0, opts->selector, block, st));
     else if (variant == 1)
         CUDA_TRY(launch_forward_thread(p, opts->readout, opts->record != 0, ev_in != nullptr, block, fwd_smem(net, block), st));
     else

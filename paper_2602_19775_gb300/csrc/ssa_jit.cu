@@ -28,8 +28,9 @@ constexpr int kJitMaxReactions = 24;
 constexpr int kJitMaxNnz = 96;
 
 struct JitKernels {
-    cudaKernel_t fwd[2][2];  // [readout][record]
-    cudaKernel_t adj[2];     // [readout]
+    cudaKernel_t fwd[2][2];     // [readout][record], Gumbel-max choice
+    cudaKernel_t fwd_direct[2]; // [readout], direct method, forward only
+    cudaKernel_t adj[2];        // [readout]
 };
 
 namespace {
@@ -212,10 +213,12 @@ const JitKernels *jit_kernels(const ssa_network *net, std::string &why)
     const char *fwd_names[2][2] = {{"ssa_jit_fwd_hold", "ssa_jit_fwd_hold_rec"},
                                    {"ssa_jit_fwd_linear", "ssa_jit_fwd_linear_rec"}};
     const char *adj_names[2] = {"ssa_jit_adj_hold", "ssa_jit_adj_linear"};
+    const char *direct_names[2] = {"ssa_jit_fwd_hold_direct", "ssa_jit_fwd_linear_direct"};
     bool ok = true;
     for (int r = 0; r < 2; ++r) {
         for (int rec = 0; rec < 2; ++rec) ok &= cudaLibraryGetKernel(&k.fwd[r][rec], lib, fwd_names[r][rec]) == cudaSuccess;
         ok &= cudaLibraryGetKernel(&k.adj[r], lib, adj_names[r]) == cudaSuccess;
+        ok &= cudaLibraryGetKernel(&k.fwd_direct[r], lib, direct_names[r]) == cudaSuccess;
     }
     if (!ok) {
         why = "a specialised kernel is missing from the library";
@@ -226,14 +229,15 @@ const JitKernels *jit_kernels(const ssa_network *net, std::string &why)
     return &(g_jit_cache[src] = k);
 }
 
-cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int readout, bool record, int block,
-                               cudaStream_t st)
+cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int readout, bool record, int selector,
+                               int block, cudaStream_t st)
 {
     if (p.n_traj == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((p.n_traj + block - 1) / block);
     void *args[] = {const_cast<FwdParams *>(&p)};
-    return cudaLaunchKernel(reinterpret_cast<const void *>(k->fwd[readout == SSA_READOUT_HOLD ? 0 : 1][record ? 1 : 0]),
-                            dim3(grid), dim3((unsigned)block), args, 0, st);
+    const int r = readout == SSA_READOUT_HOLD ? 0 : 1;
+    const cudaKernel_t f = selector == SSA_SELECT_DIRECT ? k->fwd_direct[r] : k->fwd[r][record ? 1 : 0];
+    return cudaLaunchKernel(reinterpret_cast<const void *>(f), dim3(grid), dim3((unsigned)block), args, 0, st);
 }
 
 cudaError_t jit_launch_backward(const JitKernels *k, const AdjParams &p, int readout, int block, int64_t grid,

@@ -12,7 +12,8 @@
 // with the reactant indices and stoichiometry written into the code as constants. Counts and the
 // state adjoint then live in registers and every table lookup disappears. The arithmetic is the
 // generic thread kernels' (same helpers from ssa_device.cuh, same order), so a specialised run
-// reproduces the generic run's trajectories bit for bit.
+// reproduces the generic run's trajectories bit for bit. A third forward runs the plain direct method
+// (Section 2) for comparison.
 
 namespace ssa {
 
@@ -157,6 +158,105 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
             p.ckpt[(int64_t)sp * n + i] = x0[sp];  // checkpoint 0 = X_0
         }
     }
+}
+
+// The plain direct method (Section 2), forward only: per step one Philox block gives E_0 = -ln u_0
+// for the waiting time and u_1 for the choice, the first reaction j (in reaction order) whose
+// cumulative propensity exceeds u_1 a0 (all in binary32, the cumulative sum in the order of a0).
+// Everything else -- clock, samples, range checks, update -- is the Gumbel-max forward's.
+template <int READOUT>
+__device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_traj) return;
+    const int64_t n = p.n_traj;
+    float kr[JM];
+#pragma unroll
+    for (int j = 0; j < JM; ++j) kr[j] = p.k_rates[j];
+    const int *x0 = p.x0 + (p.x0_per_traj ? i * JN : 0);
+    const bool bad_obs = (*p.flag & kErrBadObs) != 0;
+    bool bad_input = (*p.flag & (kErrBadSamples | kErrBadObs)) != 0;
+    int X[JN];
+#pragma unroll
+    for (int s = 0; s < JN; ++s) {
+        X[s] = x0[s];
+        bad_input |= X[s] < 0;
+    }
+    const uint64_t gid = p.traj_offset + (uint64_t)i;
+    const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32);
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    double t = 0.0;
+    int s = 0;
+    double thr = p.S > 0 ? p.ts[0] : p.t_end;
+    int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
+    int k = 0, draws = 0;
+    uint4 r = philox4x32_10(make_uint4(0u, 0u, c2, c3), key0, key1);
+    float E0 = neg_log_unit(u01(r.x)), U1 = u01(r.y);
+    while (!bad_input) {
+        if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
+        r = philox4x32_10(make_uint4(0u, (uint32_t)(k + 1), c2, c3), key0, key1);  // next step
+        float a[JM], h[JM];
+        jit_props(X, kr, a, h);
+        float a0 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < JM; ++j) a0 = __fadd_rn(a0, a[j]);
+        if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
+        if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
+        const float target = __fmul_rn(U1, a0);
+        float cum = 0.0f;
+        int jb = -1, last = -1;
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+            if (a[j] > 0.0f) {
+                last = j;
+                cum = __fadd_rn(cum, a[j]);
+                if (jb < 0 && cum > target) jb = j;
+            }
+        }
+        if (jb < 0) jb = last;  // u_1 a0 rounded up to a0: the last active reaction
+        if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }
+        const float tau = __fdividef(E0, a0);
+        const double t_next = t + f2d_pos(tau);
+        const bool slow = gt_nonneg(t_next, thr);
+        const bool cross = slow && gt_nonneg(t_next, p.t_end);
+        if (!cross) status = jit_check(X, jb);
+        draws = k + 1;
+        if (status != SSA_TRAJ_OK) break;
+        if (slow) {
+            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
+                if (READOUT == SSA_READOUT_HOLD) {
+                    int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                    for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
+                } else {
+                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
+                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                    for (int c = 0; c < p.n_obs; ++c) {
+                        const int sp = p.obs_sp[c];
+                        o[c] = __fmaf_rn(alpha, (float)jit_dv(jb, sp), (float)jit_xsel(X, sp));
+                    }
+                }
+                ++s;
+            }
+            thr = s < p.S ? p.ts[s] : p.t_end;
+            if (cross) break;
+        }
+        jit_apply(X, jb);
+        t = t_next;
+        ++k;
+        E0 = neg_log_unit(u01(r.x));
+        U1 = u01(r.y);
+    }
+    for (; s < p.S; ++s) {
+        if (READOUT == SSA_READOUT_HOLD) {
+            int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+            for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : jit_xsel(X, p.obs_sp[c]);
+        } else {
+            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+            for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)jit_xsel(X, p.obs_sp[c]);
+        }
+    }
+    p.draws[i] = draws;
+    p.status[i] = status;
 }
 
 // Per-trajectory adjoint; returns the trajectory's per-reaction adjoints in dAr.
@@ -343,6 +443,14 @@ extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_linear(const ssa::
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_linear_rec(const ssa::FwdParams p)
 {
     ssa::jit_fwd<SSA_READOUT_LINEAR, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_hold_direct(const ssa::FwdParams p)
+{
+    ssa::jit_fwd_direct<SSA_READOUT_HOLD>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_linear_direct(const ssa::FwdParams p)
+{
+    ssa::jit_fwd_direct<SSA_READOUT_LINEAR>(p);
 }
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_hold(const ssa::AdjParams p)
 {

@@ -24,6 +24,7 @@ from . import _lib
 from ._lib import FwdOpts, SSAError, check
 
 READOUTS = {"hold": _lib.SSA_READOUT_HOLD, "linear": _lib.SSA_READOUT_LINEAR}
+SELECTORS = {"gumbel": 0, "direct": 1}
 
 
 def _ptr(t: torch.Tensor | None):
@@ -134,10 +135,10 @@ class ForwardResult:
 
 
 def make_opts(readout="hold", record=False, ckpt_interval=64, max_steps=1 << 20, threads_per_traj=0,
-              block_threads=0, specialize=True) -> FwdOpts:
+              block_threads=0, specialize=True, selector="gumbel") -> FwdOpts:
     ro = READOUTS[readout] if isinstance(readout, str) else int(readout)
     return FwdOpts(ro, 1 if record else 0, int(ckpt_interval), int(threads_per_traj), int(max_steps),
-                   int(block_threads), 0 if specialize else 1)
+                   int(block_threads), 0 if specialize else 1, SELECTORS[selector], 0)
 
 
 def workspace_bytes(net: Network, n_traj: int, n_samples: int, opts: FwdOpts) -> int:
@@ -155,7 +156,8 @@ def _as_cuda(x, dtype, device):
 
 def forward(net: Network, log_rates, n_traj: int, x0, t_end: float, sample_times, obs_species, seed: int,
             readout="hold", record=False, ckpt_interval=64, max_steps=1 << 20, traj_offset=0,
-            threads_per_traj=0, block_threads=0, specialize=True, replay_events=None, replay_n_events=None,
+            threads_per_traj=0, block_threads=0, specialize=True, selector="gumbel", replay_events=None,
+            replay_n_events=None,
             workspace: torch.Tensor | None = None, obs_out: torch.Tensor | None = None,
             stream=None, device=None) -> ForwardResult:
     """ssa_forward (or ssa_forward_replay when replay_events is given) on the current stream."""
@@ -166,7 +168,7 @@ def forward(net: Network, log_rates, n_traj: int, x0, t_end: float, sample_times
     ts = _as_cuda(sample_times, torch.float64, device)
     obs_sp = _as_cuda(obs_species, torch.int32, device)
     S, n_obs = int(ts.numel()), int(obs_sp.numel())
-    opts = make_opts(readout, record, ckpt_interval, max_steps, threads_per_traj, block_threads, specialize)
+    opts = make_opts(readout, record, ckpt_interval, max_steps, threads_per_traj, block_threads, specialize, selector)
     need = workspace_bytes(net, n_traj, S, opts)
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=device)

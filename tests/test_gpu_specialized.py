@@ -84,3 +84,49 @@ def test_default_choice_uses_the_specialised_kernels(S):
     fw = S.forward(net, torch.tensor(wl.log_rates.astype(np.float32), device="cuda"), 256, wl.x0, wl.t_end,
                    wl.sample_times, wl.obs_species, 0, readout="linear", record=True, max_steps=4096)
     assert fw.run.variant == 2
+
+
+@pytest.mark.parametrize("case", ["dimer", "mixed_orders", "oscillator"])
+def test_direct_method_matches_oracle(S, case):
+    """The plain direct method (u_1 a0 against the cumulative propensities) against the FP64 oracle's
+    direct method on the same uniforms: identical draw counts and HOLD observables on all but a few
+    trajectories (a choice can flip only where u_1 a0 lies within binary32 rounding of a cumulative
+    boundary)."""
+    from oracle import native
+    spec, t_end, obs = CASES[case]()
+    net = S.Network(spec)
+    theta32 = spec.log_rates.astype(np.float32)
+    ts = W.uniform_sample_grid(t_end, 10)
+    n = 2000
+    fw = S.forward(net, torch.tensor(theta32, device="cuda"), n, spec.x0, t_end, ts, obs, 21, readout="hold",
+                   max_steps=1 << 15, selector="direct", traj_offset=5)
+    assert fw.run.variant == 2
+    orc = native.run(spec, theta32.astype(np.float64), spec.x0, n, t_end, ts, np.array(obs, np.int32), 21,
+                     native.HOLD, max_steps=1 << 15, traj_offset=5, selector="direct")
+    np.testing.assert_array_equal(fw.status.cpu().numpy(), orc.status)
+    same = (fw.draws.cpu().numpy() == orc.draws) & np.all(fw.obs.cpu().numpy() == orc.obs, axis=(1, 2))
+    assert same.mean() >= 0.99, same.mean()
+
+
+def test_direct_method_moments_match_exact_cme(S):
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "dimer_2a_b_cme.json")))
+    wl = W.config_c1(n_traj=65536)
+    net = S.Network(wl.net)
+    fw = S.forward(net, torch.tensor(wl.log_rates.astype(np.float32), device="cuda"), wl.n_traj, wl.x0, wl.t_end,
+                   wl.sample_times, wl.obs_species, 0, readout="hold", max_steps=4096, selector="direct")
+    A = fw.obs[:, :, 0].double().cpu().numpy()
+    m = A.mean(0)
+    se = A.std(0, ddof=1) / np.sqrt(wl.n_traj)
+    z = (m - np.array(gold["mean_A"])) / se
+    assert np.all(np.abs(z) < 3.5), z  # 50 sample times at once
+
+
+def test_direct_method_is_forward_only(S):
+    from paper_2602_19775_gb300 import SSAError
+    spec = W.dimerization_2a_b()
+    net = S.Network(spec)
+    with pytest.raises(SSAError):
+        S.forward(net, torch.tensor(spec.log_rates.astype(np.float32), device="cuda"), 8, spec.x0, 1.0, [1.0], [0],
+                  0, record=True, selector="direct")
