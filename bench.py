@@ -208,7 +208,8 @@ def run_ours(args):
     wl = W.config_c2(n_traj=args.n_traj)
     n = wl.n_traj
     S = len(wl.sample_times)
-    offset = rank * n  # each rank simulates its own global trajectory ids
+    from paper_2602_19775_gb300.shard import max_over_ranks, shard_range, total_over_ranks
+    offset, _ = shard_range(n * world, rank, world)  # each rank simulates its own global trajectory ids
     net = ssa.Network(wl.net)
     theta = torch.tensor(wl.log_rates.astype(np.float32), device=dev)
     x0 = torch.tensor(wl.x0, device=dev)
@@ -322,16 +323,8 @@ def run_ours(args):
     steps_total = int(draws_tot.item())
     t_step = float(np.sum(step_ms)) / 1e3
     t_fonly = float(np.sum(fonly_ms)) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step, t_fonly], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        cnt = torch.tensor([steps_total, int(fdraws.item())], device=dev, dtype=torch.int64)
-        dist.all_reduce(cnt)
-        t_step, t_fonly = float(tt[0]), float(tt[1])
-        steps_total, fsteps = int(cnt[0]), int(cnt[1])
-    else:
-        fsteps = int(fdraws.item())
+    t_step, t_fonly = max_over_ranks(t_step, dev), max_over_ranks(t_fonly, dev)
+    steps_total, fsteps = total_over_ranks(steps_total, dev), total_over_ranks(int(fdraws.item()), dev)
     value = steps_total / t_step
     fwd_value = fsteps / t_fonly
 

@@ -1,0 +1,84 @@
+"""The multi-rank path on CPU: two gloo ranks each simulate their contiguous share of trajectory ids
+(with the FP64 oracle standing in for each rank's GPU) and combine them with the sharding helpers' all-
+reduces; the ensemble mean and the summed gradient equal those of one process over all ids, because
+every random number is keyed by the global trajectory id. Also checks the partition and the max/sum
+reductions the benchmark uses."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_2602_19775_gb300.shard import (global_ensemble_mean, global_gradient, max_over_ranks, shard_range,
+                                          total_over_ranks)
+
+
+def test_shard_range_partitions_contiguously():
+    for n in (0, 1, 7, 64, 1001):
+        for world in (1, 2, 3, 8):
+            spans = [shard_range(n, r, world) for r in range(world)]
+            assert sum(c for _, c in spans) == n
+            pos = 0
+            for off, c in spans:
+                assert off == pos
+                pos += c
+            assert max(c for _, c in spans) - min(c for _, c in spans) <= 1
+    with pytest.raises(ValueError):
+        shard_range(10, 2, 2)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, n_total, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import ssa_workloads as W
+        from oracle import native
+        wl = W.config_c2(n_traj=n_total)
+        off, cnt = shard_range(n_total, rank, world)
+        dl = np.full((cnt, len(wl.sample_times), 1), 1.0 / n_total)
+        r = native.run(wl.net, wl.log_rates, wl.x0, cnt, wl.t_end, wl.sample_times, wl.obs_species, 5, native.LINEAR,
+                       max_steps=4096, traj_offset=off, dl_dobs=dl, temperature=0.5, n_threads=1)
+        mean = global_ensemble_mean(torch.tensor(r.obs))
+        grad = global_gradient(torch.tensor(r.dtheta.sum(0)))
+        t = max_over_ranks(1.0 + rank)
+        steps = total_over_ranks(int(r.draws.sum()))
+        if rank == 0:
+            out.put((mean.numpy(), grad.numpy(), t, steps))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reproduce_one_process():
+    import ssa_workloads as W
+    from oracle import native
+    n_total = 301  # uneven split
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, n_total, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    mean, grad, t, steps = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    wl = W.config_c2(n_traj=n_total)
+    dl = np.full((n_total, len(wl.sample_times), 1), 1.0 / n_total)
+    r = native.run(wl.net, wl.log_rates, wl.x0, n_total, wl.t_end, wl.sample_times, wl.obs_species, 5, native.LINEAR,
+                   max_steps=4096, dl_dobs=dl, temperature=0.5, n_threads=1)
+    np.testing.assert_allclose(mean, r.obs.mean(0), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(grad, r.dtheta.sum(0), rtol=1e-12, atol=1e-15)
+    assert t == 2.0
+    assert steps == int(r.draws.sum())
