@@ -374,6 +374,7 @@ def run_ours(args):
     batch = uneven_batch_extra(ssa, dev, args.batch_scale) if (rank == 0 and "batch" in legs) else None
     grn = grn_extra(ssa, dev, n_img=args.grn_images) if (rank == 0 and "grn" in legs) else None
     warp = warp_extra(ssa, dev, n=args.warp_traj) if (rank == 0 and "warp" in legs) else None
+    c3 = c3_extra(ssa, dev) if (rank == 0 and "c3" in legs) else None
     M = wl.net.n_reactions
     rates = ssa.pipe_rates()
     log_slots = 128.0 / rates["neglog"]
@@ -427,6 +428,7 @@ def run_ours(args):
         "uneven_batch": batch,
         "grn": grn,
         "warp_kernels": warp,
+        "oscillator_full": c3,
         "paper_context": "1.9e9 SSA steps/s forward on the oscillator, RTX 6000 Ada + TF 2.20 (a different machine)",
         "cpu_baseline": cpu_base,
         "e2e": {"value": e2e_value, "unit": "SSA steps/s (fwd+adj)", "h2d_bytes_per_step": h2d,
@@ -552,6 +554,79 @@ def uneven_batch_extra(ssa, dev, traj_scale: float, reps: int = 2, sequential: b
         ev[1].record()
         torch.cuda.synchronize()
         out["per_network_calls_ms"] = ev[0].elapsed_time(ev[1])
+    return out
+
+
+def c3_extra(ssa, dev, n_fwd: int = 1 << 20, n_adj: int = 1 << 14, lag: int = 12, T: float = 0.1):
+    """The activator-repressor oscillator at its full configuration: 2^20 trajectories to t_end = 400 with 400
+    LINEAR samples of R, forward only (one launch); then one trajectory chunk of n_adj with the event log
+    (about 1.1e6 draws per trajectory, 2 bytes each) through forward + straight-through adjoint of the loss
+    L = mean_s (m_s - m*_s)^2 + (c_lag - c*_lag)^2 on the ensemble mean m_s of R and the ensemble mean of the
+    per-trajectory normalised autocovariance c at `lag` samples, at the true rates (targets from n_adj other
+    trajectories, seed 1), T = 0.1. This measures throughput: over ~1e6 draws the surrogate's adjoint grows
+    without bound at every temperature (near-ties of the race feed 1/T-scaled kicks into lambda, which the
+    recursion carries forward), so the chunk's gradient overflows binary32; `grad_finite` reports it."""
+    import torch
+
+    import ssa_workloads as W
+    wl = W.config_c3(n_traj=n_fwd)
+    net = ssa.Network(wl.net)
+    S = len(wl.sample_times)
+    true = torch.tensor(wl.log_rates.astype(np.float32), device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {"workload": f"Vilar oscillator, {n_fwd} trajectories, t_end={wl.t_end}, {S} LINEAR samples of R"}
+    ssa.forward(net, true, 1024, wl.x0, wl.t_end, wl.sample_times, wl.obs_species, 9, readout="linear",
+                max_steps=1 << 21)  # warm-up
+    torch.cuda.synchronize()
+    ev[0].record()
+    fw = ssa.forward(net, true, n_fwd, wl.x0, wl.t_end, wl.sample_times, wl.obs_species, 10, readout="linear",
+                     max_steps=1 << 21)
+    ev[1].record()
+    torch.cuda.synchronize()
+    steps = int(fw.draws.sum().item())
+    ms = ev[0].elapsed_time(ev[1])
+    out["forward"] = {"n_traj": n_fwd, "ssa_steps": steps, "ms": ms, "steps_per_s": steps / (ms / 1e3),
+                      "non_ok": int((fw.status > 1).sum().item())}
+    del fw
+    torch.cuda.empty_cache()
+
+    def stats(obs):
+        R = obs[:, :, 0].double()
+        m = R.mean(0)
+        x = R - R.mean(1, keepdim=True)
+        c = (x[:, :-lag] * x[:, lag:]).mean(1) / (x * x).mean(1).clamp_min(1e-12)
+        return m, c.mean()
+
+    max_steps = 1_400_000
+    tfw = ssa.forward(net, true, n_adj, wl.x0, wl.t_end, wl.sample_times, wl.obs_species, 1, readout="linear",
+                      max_steps=max_steps)
+    m_t, c_t = stats(tfw.obs)
+    del tfw
+    torch.cuda.empty_cache()
+    ev[0].record()
+    fw = ssa.forward(net, true, n_adj, wl.x0, wl.t_end, wl.sample_times, wl.obs_species, 3, readout="linear",
+                     record=True, max_steps=max_steps)
+    ev[1].record()
+    obs = fw.obs.detach().clone().requires_grad_(True)
+    m, c = stats(obs)
+    loss = ((m - m_t) ** 2).mean() + (c - c_t) ** 2
+    loss.backward()
+    dl = obs.grad.float().contiguous()
+    torch.cuda.synchronize()
+    ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev2[0].record()
+    g = ssa.backward(fw, dl, T)
+    ev2[1].record()
+    torch.cuda.synchronize()
+    steps = int(fw.draws.sum().item())
+    fms, ams = ev[0].elapsed_time(ev[1]), ev2[0].elapsed_time(ev2[1])
+    out["forward_adjoint_chunk"] = {
+        "n_traj": n_adj, "ssa_steps": steps, "forward_record_ms": fms, "adjoint_ms": ams,
+        "steps_per_s": steps / ((fms + ams) / 1e3), "workspace_gb": fw.run.workspace.numel() / 1e9,
+        "loss": float(loss.item()), "grad_finite": bool(torch.isfinite(g).all().item()), "temperature": T,
+        "non_ok": int((fw.status > 1).sum().item()), "variant": fw.run.variant}
+    del fw
+    torch.cuda.empty_cache()
     return out
 
 
@@ -717,7 +792,8 @@ def main():
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the oscillator and uneven-batch fields")
     ap.add_argument("--legs", default="oscillator,batch,grn,warp",
-                    help="comma-separated extra fields to measure: oscillator, batch, grn, warp ('none' for none)")
+                    help="comma-separated extra fields to measure: oscillator, batch, grn, warp, c3 (the oscillator at its "
+                         "full size, about two minutes; not in the default) ('none' for none)")
     ap.add_argument("--grn-images", type=int, default=512, help="images of the GRN field (64 trajectories each)")
     ap.add_argument("--warp-traj", type=int, default=16384, help="trajectories of the warp-kernel field")
     ap.add_argument("--batch-scale", type=float, default=1.0 / 16,
