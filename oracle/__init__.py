@@ -9,7 +9,7 @@ Modules:
 * ``native``   -- ctypes front end of ``ssa_oracle.c`` (FP64 simulation + hand adjoint), and the
                   gcc build of that file.
 * ``cme``      -- chemical master equation tools (Eq. 1): finite generator matrices, transient
-                  laws by matrix exponential, stationary laws, the Poisson law of
+                  laws by matrix exponential and their bin averages, stationary laws, the Poisson law of
                   immigration-death, and exact enumeration of short jump chains.
 * ``autodiff`` -- the literal straight-through graph of Eq. 5 in float64 PyTorch CPU autograd,
                   for small cases; it pins the hand adjoint.
@@ -19,6 +19,7 @@ Modules:
 from .native import (  # noqa: F401
     HOLD,
     LINEAR,
+    BIN,
     STATUS,
     build,
     philox_blocks,

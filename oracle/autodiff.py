@@ -6,7 +6,9 @@ describes it: propensities a(X_k; theta) from a real-valued state, the Gumbel pe
 the same noise, the soft sample of Eq. 3, y_ST = y~ + stopgrad(onehot(j_k) - y~) (Eq. 5),
 X_{k+1} = X_k + y_ST V (whose value is Eq. 6 and whose derivative is Eq. 7), the reparametrised
 waiting time tau_k = -ln(u_0)/a0 (Section 3.1), t_{k+1} = t_k + tau_k, and the HOLD or LINEAR
-readout (Section 4.1). Autograd then gives dL/dtheta for L = sum(c * obs), with no hand-written
+readout (Section 4.1) or the exact bin average (Section 4.4: the cumulative integral of the step
+path at the bin edges, differenced and divided by the bin width, with the event times as graph
+nodes). Autograd then gives dL/dtheta for L = sum(c * obs), with no hand-written
 derivative anywhere. Reactions with a_j = 0 are masked from the softmax (y~_j = 0) with a
 gradient-safe double `where`; they still enter a0.
 
@@ -17,7 +19,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .native import HOLD, LINEAR, uniforms
+from .native import BIN, HOLD, LINEAR, uniforms
 
 
 def _h(reactants, X):
@@ -70,7 +72,28 @@ def st_gradient(net, log_rates, x0, events, n_states: int, crossed: bool, seed: 
     assert len(states) == n_states
     obs = []
     tvals = [float(tt) for tt in times]
-    for ts in np.asarray(sample_times, dtype=np.float64):
+    sel = torch.as_tensor(np.asarray(obs_species), dtype=torch.long)
+
+    def bracket(b):
+        k = 0
+        while k + 1 < n_states and tvals[k + 1] <= b:
+            k += 1
+        return k
+
+    def cumulative(b):
+        # int_0^b X(t) dt of the right-continuous step path, through the graph's times
+        k = bracket(b)
+        c = states[k] * (b - times[k])
+        for q in range(k):
+            c = c + states[q] * (times[q + 1] - times[q])
+        return c
+
+    if readout == BIN:
+        lo = 0.0
+        for b in np.asarray(sample_times, dtype=np.float64):
+            obs.append(((cumulative(float(b)) - cumulative(lo)) / (float(b) - lo))[sel])
+            lo = float(b)
+    for ts in (np.asarray(sample_times, dtype=np.float64) if readout != BIN else ()):
         k = 0
         while k + 1 < n_states and tvals[k + 1] <= ts:
             k += 1
@@ -81,9 +104,11 @@ def st_gradient(net, log_rates, x0, events, n_states: int, crossed: bool, seed: 
             val = Xk + alpha * (nexts[k] - Xk)
         else:
             val = Xk
-        obs.append(val[torch.as_tensor(np.asarray(obs_species), dtype=torch.long)])
+        obs.append(val[sel])
     obs = torch.stack(obs) if obs else torch.zeros((0, len(obs_species)), dtype=torch.float64)
     L = (torch.as_tensor(np.asarray(dl_dobs, dtype=np.float64)) * obs).sum()
+    if not L.requires_grad:  # a path that never moves: the readout does not depend on theta
+        return np.zeros_like(theta.detach().numpy()), obs.detach().numpy()
     L.backward()
     return theta.grad.detach().numpy().copy(), obs.detach().numpy()
 

@@ -13,6 +13,7 @@ propensities of Section 2, and give exact laws against which simulations are che
 * ``enumerate_jump_chain``  the exact law of X_n after n jumps, P(path) = prod a_j/a0, and the
                  exact E[t_n] = E[sum_k 1/a0(X_k)]
 * ``transient_gradient`` d p(t)/d log k_r via expm of [[Q, dQ], [0, Q]] (Van Loan's block form)
+* ``transient_bin_average`` the average of p(t) over each bin, via expm of [[Q, I], [0, 0]]
 """
 from __future__ import annotations
 
@@ -110,6 +111,28 @@ def transient_gradient(Q, dQ, p0, times):
     for t in times:
         E = scipy.linalg.expm(B * t)
         out.append(p0 @ E[:n, n:])
+    return np.stack(out)
+
+
+def transient_bin_average(Q, p0, edges):
+    """(1/D_s) int over (b_{s-1}, b_s] of p(t) dt for the bins whose right edges are `edges` (b_{-1} = 0,
+    D_s = b_s - b_{s-1} > 0): p(b_{s-1}) times the top-right block of expm([[Q, I], [0, 0]] D_s), which is
+    int_0^D expm(Q u) du (Van Loan's block form), divided by D_s. These are the exact means of the
+    bin-averaged readout of Section 4.4 for a finite chain."""
+    n = Q.shape[0]
+    B = np.zeros((2 * n, 2 * n))
+    B[:n, :n] = Q
+    B[:n, n:] = np.eye(n)
+    out = []
+    lo = 0.0
+    p_lo = np.asarray(p0, dtype=np.float64)
+    for b in np.asarray(edges, dtype=np.float64):
+        D = b - lo
+        assert D > 0.0
+        E = scipy.linalg.expm(B * D)
+        out.append(p_lo @ E[:n, n:] / D)
+        p_lo = p_lo @ E[:n, :n]
+        lo = b
     return np.stack(out)
 
 

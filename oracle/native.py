@@ -1,7 +1,8 @@
 """ctypes front end of the FP64 C oracle (``ssa_oracle.c``).  Test infrastructure only.
 
 ``run`` simulates trajectories exactly as Section 2 and the Gumbel-max equation of Section 3.2
-state them, reads them out on a sample grid (HOLD or the LINEAR interpolation of Section 4.1),
+state them, reads them out on a sample grid (HOLD, the LINEAR interpolation of Section 4.1, or the
+exact bin average BIN of Section 4.4 over the bins (t_{s-1}, t_s], t_{-1} = 0),
 and, when an upstream gradient dL/dobs is given, returns the straight-through gradient of
 Eqs. 5 and 7 with the waiting-time term of Section 3.1, per trajectory, in float64.
 """
@@ -16,6 +17,7 @@ import numpy as np
 
 HOLD = 0
 LINEAR = 1
+BIN = 2
 STATUS = {"OK": 0, "ABSORBED": 1, "STEP_CAP": 2, "NEG_COUNT": 3, "OVERFLOW": 4, "BAD_RATE": 5}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

@@ -20,6 +20,11 @@
  *     (dX_ST(k+1)/dX_k)^T dL/dX_{k+1}, with the Gumbel draws held fixed.
  *   - Section 4.1: each trajectory is linearly interpolated onto a uniform time grid
  *     (LINEAR readout); the HOLD readout is the right-continuous path value X(t_s).
+ *   - Section 4.4: the BIN readout averages the piecewise-constant path exactly over each bin,
+ *     through its cumulative integral C(b) = int_0^b X(t) dt: obs_s = (C(b_s) - C(b_{s-1}))/
+ *     (b_s - b_{s-1}). Reading: the bins are (b_{s-1}, b_s] with b_s = t_s and b_{-1} = 0 (the
+ *     sample times are the bins' right edges), strictly increasing with t_0 > 0; the path holds
+ *     its last state after it stops.
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   - Noise: counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). Key =
@@ -57,7 +62,7 @@ typedef struct {
     const int32_t *rate_index;     /* [M]: reaction j uses theta[rate_index[j]] */
 } orc_network;
 
-enum { ORC_HOLD = 0, ORC_LINEAR = 1 };
+enum { ORC_HOLD = 0, ORC_LINEAR = 1, ORC_BIN = 2 };
 
 /* per-trajectory status codes */
 enum {
@@ -313,11 +318,33 @@ static int orc_has_next(const orc_path *p, int64_t k)
     return p->crossed;
 }
 
-/* Readout (Section 4.1): HOLD = X(t_s); LINEAR = linear interpolation on the event grid. */
+/* Cumulative integral C(b) = int_0^b X_sp(t) dt of the right-continuous step path (Section 4.4):
+   the whole intervals [t_i, t_{i+1}) before the bracket of b, then the part [t_k, b]. */
+static double orc_cumulative(const orc_path *p, int N, int sp, double b)
+{
+    const int64_t kb = orc_bracket(p, b);
+    double c = 0.0;
+    for (int64_t i = 0; i < kb; ++i) c += p->X[(size_t)i * N + sp] * (p->t[i + 1] - p->t[i]);
+    return c + p->X[(size_t)kb * N + sp] * (b - p->t[kb]);
+}
+
+/* Readout (Section 4.1): HOLD = X(t_s); LINEAR = linear interpolation on the event grid;
+   (Section 4.4) BIN = exact average over the bin (t_{s-1}, t_s], t_{-1} = 0. */
 static void orc_readout(const orc_network *net, const orc_path *p, const double *ts, int S,
                         const int32_t *obs_species, int n_obs, int readout, double *obs /*[S][n_obs]*/)
 {
     const int N = net->n_species;
+    if (readout == ORC_BIN) {
+        for (int s = 0; s < S; ++s) {
+            const double lo = s > 0 ? ts[s - 1] : 0.0;
+            for (int o = 0; o < n_obs; ++o) {
+                const int sp = obs_species[o];
+                obs[(size_t)s * n_obs + o] =
+                    (orc_cumulative(p, N, sp, ts[s]) - orc_cumulative(p, N, sp, lo)) / (ts[s] - lo);
+            }
+        }
+        return;
+    }
     for (int s = 0; s < S; ++s) {
         int64_t k = orc_bracket(p, ts[s]);
         const double *X = p->X + (size_t)k * N;
@@ -368,8 +395,26 @@ static int orc_adjoint_one(const orc_sim_cfg *cfg, uint64_t traj, const orc_path
         const int draw = orc_has_next(p, k);
         double dt_dir = 0.0, dtau_dir = 0.0;
         for (int i = 0; i < N; ++i) dXdir[i] = 0.0;
-        /* direct readout terms of the samples bracketed by state k */
-        for (int s = 0; s < S; ++s) {
+        /* BIN: obs_e = (C(b_e) - C(b_{e-1}))/D_e, so dL/dC(b_e) = g_e - g_{e+1} with g_e = dL/dobs_e / D_e.
+           C(b) = sum_{i<kb} X_i (t_{i+1} - t_i) + X_kb (b - t_kb) gives dC/dX_k = t_{k+1} - t_k (k < kb) or
+           b - t_k (k = kb), and dC/dt_k = X_{k-1} - X_k for 1 <= k <= kb (t_k ends the previous interval
+           and starts this one); b_{-1} = 0 is fixed. */
+        if (readout == ORC_BIN) {
+            for (int e = 0; e < S; ++e) {
+                if (kb[e] < k) continue;
+                const double lo = e > 0 ? ts[e - 1] : 0.0;
+                for (int o = 0; o < n_obs; ++o) {
+                    const int sp = obs_species[o];
+                    const double g_e = dL_dobs[(size_t)e * n_obs + o] / (ts[e] - lo);
+                    const double g_n = e + 1 < S ? dL_dobs[(size_t)(e + 1) * n_obs + o] / (ts[e + 1] - ts[e]) : 0.0;
+                    const double gC = g_e - g_n;
+                    dXdir[sp] += gC * (kb[e] > k ? p->t[k + 1] - p->t[k] : ts[e] - p->t[k]);
+                    if (k >= 1) dt_dir += gC * (p->X[(size_t)(k - 1) * N + sp] - X[sp]);
+                }
+            }
+        }
+        /* direct readout terms of the samples bracketed by state k (HOLD, LINEAR) */
+        for (int s = 0; s < S && readout != ORC_BIN; ++s) {
             if (kb[s] != k) continue;
             for (int i = 0; i < N; ++i) gbar[i] = 0.0;
             for (int o = 0; o < n_obs; ++o) gbar[obs_species[o]] += dL_dobs[(size_t)s * n_obs + o];
@@ -435,8 +480,8 @@ static int orc_adjoint_one(const orc_sim_cfg *cfg, uint64_t traj, const orc_path
                 double kj = exp(net->log_rates[net->rate_index[j]]);
                 orc_add_dh(net, j, X, dLda0 * kj, lam_new);
             }
-            mu = mu + dt_dir; /* t_{k+1} = t_k + tau_k */
         }
+        mu = mu + dt_dir; /* t_{k+1} = t_k + tau_k: mu becomes dL/dt_k */
         for (int i = 0; i < N; ++i) lam[i] = lam_new[i];
     }
     free(lam); free(lam_new); free(dXdir); free(gbar); free(a); free(z); free(y); free(w); free(kb);
@@ -547,9 +592,12 @@ int orc_run_sel(int32_t selector, const orc_network *net, int64_t n_traj, int64_
     if (selector != 0 && selector != 1) return -1;
     if (selector == 1 && dL_dobs) return -1;  /* the straight-through gradient is of the Gumbel-max choice */
     if (net->n_species <= 0 || net->n_reactions < 0) return -1;
+    if (readout != ORC_HOLD && readout != ORC_LINEAR && readout != ORC_BIN) return -1;
     for (int s = 0; s < S; ++s) {
         if (!(ts[s] >= 0.0 && ts[s] <= t_end)) return -1;
         if (s > 0 && ts[s] < ts[s - 1]) return -1;
+        /* BIN: bins (t_{s-1}, t_s] of positive width, t_{-1} = 0 */
+        if (readout == ORC_BIN && !(ts[s] > (s > 0 ? ts[s - 1] : 0.0))) return -1;
     }
     for (int o = 0; o < n_obs; ++o)
         if (obs_species[o] < 0 || obs_species[o] >= net->n_species) return -1;
