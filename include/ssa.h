@@ -54,12 +54,21 @@ typedef int32_t ssa_status;
 
 #define SSA_READOUT_HOLD 0   /* obs = X(t_s), right-continuous; int32 output              */
 #define SSA_READOUT_LINEAR 1 /* obs = X_k + (t_s - t_k)/tau_k (X_{k+1} - X_k); float output */
+/* Exact bin average (Section 4.4): obs_s = the integral of the piecewise-constant path over the
+ * bin (t_{s-1}, t_s], t_{-1} = 0, divided by its width; float output. The sample times are the
+ * bins' right edges and must be strictly increasing with t_0 > 0 (else every trajectory reports
+ * SSA_TRAJ_BAD_INPUT); a stopped path holds its last state. At most SSA_BIN_MAX_OBS observables
+ * per call (call again with other species: the paths depend only on the seed). Runs on the
+ * thread-per-trajectory kernels (generic and network-specialised); threads_per_traj = 32, the
+ * batch and the GRN calls return SSA_ERR_UNSUPPORTED for it. */
+#define SSA_READOUT_BIN 2
+#define SSA_BIN_MAX_OBS 4
 
 typedef struct ssa_network ssa_network;
 typedef struct ssa_run ssa_run;
 
 typedef struct ssa_fwd_opts {
-    int32_t readout;          /* SSA_READOUT_HOLD or SSA_READOUT_LINEAR                          */
+    int32_t readout;          /* SSA_READOUT_HOLD, SSA_READOUT_LINEAR or SSA_READOUT_BIN          */
     int32_t record;           /* nonzero: keep event log, checkpoints and sample brackets so that
                                  ssa_backward can run on this forward                            */
     int32_t ckpt_interval;    /* K: checkpoint the state every K steps (multiple of 8; 0 -> 64)   */
@@ -117,11 +126,13 @@ size_t ssa_forward_workspace_bytes(const ssa_network *net, int64_t n_traj, int32
  *   log_rates     device float [P]: theta = log k.
  *   n_traj >= 0; traj_offset: global id of the first trajectory (Philox counter).
  *   x0            device int32 [N] (x0_per_traj = 0) or [n_traj][N] (x0_per_traj = 1).
- *   t_end >= 0.   sample_times device double [n_samples], ascending, each in [0, t_end].
- *   obs_species   device int32 [n_obs] in [0, N).
+ *   t_end >= 0.   sample_times device double [n_samples], ascending, each in [0, t_end]
+ *                 (BIN: strictly increasing, the first > 0).
+ *   obs_species   device int32 [n_obs] in [0, N) (BIN: n_obs <= SSA_BIN_MAX_OBS).
  *   workspace     device, >= ssa_forward_workspace_bytes(...), 256-byte aligned, caller-owned;
  *                 it must stay alive and untouched until ssa_destroy_run(*run_out).
- *   obs_out       device [n_traj][n_samples][n_obs]: int32 (HOLD) or float (LINEAR) (Section 4.1).
+ *   obs_out       device [n_traj][n_samples][n_obs]: int32 (HOLD) or float (LINEAR, Section 4.1;
+ *                 BIN, Section 4.4).
  *   draws_out     device int32 [n_traj] or NULL: reaction draws including the crossing draw.
  *   status_out    device int32 [n_traj] or NULL: SSA_TRAJ_* per trajectory.
  *   run_out       receives a handle for ssa_backward / ssa_run_status (may be NULL).

@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(_HERE, "libssa.so")
 SSA_OK = 0
 SSA_READOUT_HOLD = 0
 SSA_READOUT_LINEAR = 1
+SSA_READOUT_BIN = 2
+SSA_BIN_MAX_OBS = 4
 TRAJ_CODES = ("OK", "ABSORBED", "STEP_CAP", "NEG_COUNT", "OVERFLOW", "BAD_RATE", "BAD_INPUT", "REPLAY_MISMATCH")
 SSA_TRAJ_N_CODES = len(TRAJ_CODES)
 

@@ -77,6 +77,22 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
     const bool draw_last = st == SSA_TRAJ_OK;
     if (MC > 0) step_noise<NQ>(E, (uint32_t)(draw_last ? L : (L > 0 ? L - 1 : 0)), c2, c3, key0, key1);
 
+    // BIN readout: gq = g of the bin that contains t_{k+1} (none past the last edge), xo = X_{k+1}
+    // at the observables
+    constexpr bool kBin = READOUT == SSA_READOUT_BIN;
+    float gq[kBinMaxObs], gk[kBinMaxObs];
+    int osp[kBinMaxObs], xo[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) osp[c] = (kBin && c < p.n_obs) ? p.obs_sp[c] : 0;
+    auto xobs = [&](int c) { return X[osp[c] * B]; };
+    auto addx = [&](int c, float v) { lam[osp[c] * B] += v; };
+    auto brk = [&](int s) { return p.brk_a[(int64_t)s * n + i]; };
+    if (kBin) {
+        bin_grad(gq, gl, p.n_obs, p.ts, p.S, p.S);
+#pragma unroll
+        for (int c = 0; c < kBinMaxObs; ++c) xo[c] = c < p.n_obs ? xobs(c) : 0;
+    }
+
     for (int k = L; k >= 0; --k) {
         const bool draw = (k < L) || draw_last;
         const int s_top = s_hi;
@@ -85,6 +101,14 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
             brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
         }
         // samples s_hi+1 .. s_top are bracketed by state k
+        if (kBin) {
+            if (s_hi < s_top) bin_grad(gk, gl, p.n_obs, p.ts, p.S, s_hi + 1);
+            else {
+#pragma unroll
+                for (int c = 0; c < kBinMaxObs; ++c) gk[c] = gq[c];
+            }
+        }
+        float tau_k = 0.0f;
         if (draw) {
             const int jk = event_at(k);
             float a0 = 0.0f, ab = 0.0f, Eb = 1.0f, E0, lmax = -CUDART_INF_F;
@@ -122,7 +146,10 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
             }
             mism += (jb != jk);
             const float tau = __fdividef(E0, a0);
+            tau_k = tau;
             const int4 rk = s_rx[jk];
+            // BIN: t_{k+1} ends this interval and starts the next, in the bin of gq
+            if (kBin) mu -= bin_transition(xobs, xo, gq, p.n_obs);
             // readout terms that involve X_{k+1} and the clock (LINEAR interpolation)
             float dt_dir = 0.0f, dtau_dir = 0.0f;
             if (READOUT == SSA_READOUT_LINEAR) {
@@ -198,13 +225,22 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
                 dlam[s * B] = 0.0f;
             }
         }
-        for (int s = s_hi + 1; s <= s_top; ++s) {
-            float coef = 1.0f;
-            if (READOUT == SSA_READOUT_LINEAR && draw) {
-                const float alpha = p.brk_a[(int64_t)s * n + i];
-                if (alpha >= 0.0f) coef = 1.0f - alpha;
+        if (kBin) {
+            bin_state_terms(addx, brk, gl, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
+#pragma unroll
+            for (int c = 0; c < kBinMaxObs; ++c) {
+                gq[c] = gk[c];
+                if (c < p.n_obs) xo[c] = xobs(c);
             }
-            for (int o = 0; o < p.n_obs; ++o) lam[p.obs_sp[o] * B] += coef * gl[(int64_t)s * p.n_obs + o];
+        } else {
+            for (int s = s_hi + 1; s <= s_top; ++s) {
+                float coef = 1.0f;
+                if (READOUT == SSA_READOUT_LINEAR && draw) {
+                    const float alpha = p.brk_a[(int64_t)s * n + i];
+                    if (alpha >= 0.0f) coef = 1.0f - alpha;
+                }
+                for (int o = 0; o < p.n_obs; ++o) lam[p.obs_sp[o] * B] += coef * gl[(int64_t)s * p.n_obs + o];
+            }
         }
         if (ck_off == 0) {
             const int *ck = p.ckpt + (int64_t)ck_row * N * n + i;

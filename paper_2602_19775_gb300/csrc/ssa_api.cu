@@ -15,8 +15,8 @@
 namespace ssa {
 cudaError_t launch_forward_thread(const FwdParams &p, int readout, bool record, bool replay, int block, size_t smem,
                                   cudaStream_t st);
-cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N, int *flag,
-                                  cudaStream_t st);
+cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N,
+                                  int strict, int *flag, cudaStream_t st);
 cudaError_t launch_rates(const float *log_rates, const int *rate_index, int M, int M_pad, int lane_major, float *k_out,
                          cudaStream_t st);
 cudaError_t launch_ensemble_mean(const void *obs, bool is_int, int64_t n_traj, int64_t row_len, float *partial,
@@ -126,7 +126,7 @@ WsLayout layout(const ssa_network *net, int64_t n, int32_t S, const ssa_fwd_opts
 bool opts_valid(const ssa_fwd_opts *o)
 {
     if (!o) return false;
-    if (o->readout != SSA_READOUT_HOLD && o->readout != SSA_READOUT_LINEAR) return false;
+    if (o->readout != SSA_READOUT_HOLD && o->readout != SSA_READOUT_LINEAR && o->readout != SSA_READOUT_BIN) return false;
     if (o->max_steps < 1 || o->max_steps > 0x7fffffffLL) return false;
     if (o->ckpt_interval < 0 || (o->ckpt_interval % 8) != 0) return false;
     if (o->threads_per_traj != 0 && o->threads_per_traj != 1 && o->threads_per_traj != 32) return false;
@@ -167,6 +167,7 @@ size_t adj_warp_smem(const ssa_network *net)
 int pick_variant(const ssa_network *net, const ssa_fwd_opts *o)
 {
     if (o->threads_per_traj) return o->threads_per_traj;
+    if (o->readout == SSA_READOUT_BIN) return 1;  // the bin readout runs on the thread kernels only
     if (!o->no_specialize && jit_eligible(net)) return 1;
     return net->M <= 16 ? 1 : 32;
 }
@@ -338,6 +339,10 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
         jit = jit_kernels(net, why);
         if (jit) variant = 2;
     }
+    if (opts->readout == SSA_READOUT_BIN && variant == 32)
+        return fail(SSA_ERR_UNSUPPORTED, "the bin readout runs on the thread-per-trajectory kernels only");
+    if (opts->readout == SSA_READOUT_BIN && n_obs > SSA_BIN_MAX_OBS)
+        return fail(SSA_ERR_UNSUPPORTED, "the bin readout takes at most %d observables per call", SSA_BIN_MAX_OBS);
     if (opts->selector == SSA_SELECT_DIRECT && (variant != 2 || ev_in))
         return fail(SSA_ERR_UNSUPPORTED, "the direct method runs on the network-specialised kernels (N and M <= 24)");
     int block = 0;
@@ -363,7 +368,8 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     CUDA_TRY(launch_rates(log_rates, net->d_rate_index, net->M, L.M_pad, variant == 32 ? 1 : 0,
                           reinterpret_cast<float *>(ws + L.k_rates), st));
     CUDA_TRY(launch_validate_inputs(reinterpret_cast<const double *>(ws + L.ts), S, t_end,
-                                    reinterpret_cast<const int *>(ws + L.obs_sp), n_obs, net->N, flag, st));
+                                    reinterpret_cast<const int *>(ws + L.obs_sp), n_obs, net->N,
+                                    opts->readout == SSA_READOUT_BIN ? 1 : 0, flag, st));
     FwdParams p{};
     p.rx = variant == 32 ? net->d_rx_warp : net->d_rx;
     p.k_rates = reinterpret_cast<const float *>(ws + L.k_rates);

@@ -134,8 +134,11 @@ cudaError_t launch_backward_thread(const AdjParams &p, int readout, int block, s
                                    cudaStream_t st)
 {
     if (grid == 0) return cudaSuccess;
-    return readout == SSA_READOUT_HOLD ? launch_adj_mc<0>(p, block, smem, grid, st)
-                                       : launch_adj_mc<1>(p, block, smem, grid, st);
+    switch (readout) {
+    case SSA_READOUT_HOLD: return launch_adj_mc<SSA_READOUT_HOLD>(p, block, smem, grid, st);
+    case SSA_READOUT_LINEAR: return launch_adj_mc<SSA_READOUT_LINEAR>(p, block, smem, grid, st);
+    default: return launch_adj_mc<SSA_READOUT_BIN>(p, block, smem, grid, st);
+    }
 }
 
 cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, const int *rate_index, int P,

@@ -376,6 +376,7 @@ extern "C" ssa_status ssa_batch_create(const ssa_batch_item *items, int32_t n_it
     if (!out) return set_error(SSA_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!items || n_items < 1) return set_error(SSA_ERR_INVALID_ARG, "no items");
+    if (readout == SSA_READOUT_BIN) return set_error(SSA_ERR_UNSUPPORTED, "the batch reads out with HOLD or LINEAR");
     if (readout != SSA_READOUT_HOLD && readout != SSA_READOUT_LINEAR) return set_error(SSA_ERR_INVALID_ARG, "bad readout");
     if (!(temperature > 0.0f)) return set_error(SSA_ERR_INVALID_ARG, "temperature must be > 0");
     for (int it = 0; it < n_items; ++it) {

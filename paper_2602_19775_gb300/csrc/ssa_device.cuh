@@ -179,6 +179,107 @@ __device__ __forceinline__ float sadj_hetero(float xs, float xo, float a, float 
     return (a > 0.0f ? __fdividef(psi, xs) : 0.0f) + c_tau * xo;
 }
 
+// ------------------------------------------------------------------------------------------
+// Exact bin-averaged readout (Section 4.4): obs_s = (1/D_s) * integral over (t_{s-1}, t_s] of the
+// piecewise-constant path, t_{-1} = 0, D_s = t_s - t_{s-1}. The forward keeps, per observable, the
+// integral acc of the open bin from its left edge up to t_k, adding X_k tau_k for every step that stays
+// inside the bin. An edge t_s in [t_k, t_{k+1}), at offset d = t_s - t_k, closes a bin: the first edge
+// of a step closes the bin that began before t_k, obs = (acc + X_k d) / D_s; a later edge closes a bin
+// that lies inside the step, where the path is X_k, obs = X_k. The rest of the step, t_{k+1} minus the
+// last edge, opens the next bin. A stopped path holds its last state. The recorded bracket value of
+// edge s is d.
+//
+// The adjoint walks the same pieces backwards. With g_b = dL/dobs_b / D_b, the state X_k receives the
+// overlap of its interval with every bin times that bin's g; the event time t_{k+1} (the end of one
+// interval and the start of the next) receives g_b (X_k - X_{k+1}) for the bin b that contains it,
+// which enters dL/dtau_k with the later times.
+// ------------------------------------------------------------------------------------------
+constexpr int kBinMaxObs = SSA_BIN_MAX_OBS;
+
+// acc[c] += X_c len for the observables (xobs(c) = count of observable c)
+template <class XF>
+__device__ __forceinline__ void bin_accumulate(float (&acc)[kBinMaxObs], const XF &xobs, int n_obs, float len)
+{
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c)
+        if (c < n_obs) acc[c] = __fmaf_rn(int2f(xobs(c)), len, acc[c]);
+}
+
+// Close bin s at its right edge ts[s] >= t_k and write its averages to o; first: the bin began before
+// t_k (acc holds its integral up to t_k). Clears acc and returns d = ts[s] - t_k.
+template <class XF>
+__device__ __forceinline__ float bin_close(float (&acc)[kBinMaxObs], const XF &xobs, int n_obs, const double *ts, int s,
+                                           double t_k, bool first, float *o)
+{
+    const float d = d2f_nonneg(ts[s] - t_k);
+    const float D = d2f_nonneg(ts[s] - (s > 0 ? ts[s - 1] : 0.0));
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) {
+        if (c < n_obs) {
+            const float x = int2f(xobs(c));
+            o[c] = first ? __fdiv_rn(__fmaf_rn(x, d, acc[c]), D) : x;
+            acc[c] = 0.0f;
+        }
+    }
+    return d;
+}
+
+// g[c] = dL/dobs_b[c] / D_b for bin b, 0 past the last bin
+__device__ __forceinline__ void bin_grad(float (&g)[kBinMaxObs], const float *gl, int n_obs, const double *ts, int S,
+                                         int b)
+{
+    const bool in = b < S;
+    const float D = in ? d2f_nonneg(ts[b] - (b > 0 ? ts[b - 1] : 0.0)) : 1.0f;
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) g[c] = (in && c < n_obs) ? __fdiv_rn(gl[(int64_t)b * n_obs + c], D) : 0.0f;
+}
+
+// sum_c g_c (X_{k+1} - X_k)_c at the observables (xo: X_{k+1}); dL/dt_{k+1} receives minus this
+template <class XF>
+__device__ __forceinline__ float bin_transition(const XF &xobs, const int (&xo)[kBinMaxObs], const float (&g)[kBinMaxObs],
+                                                int n_obs)
+{
+    float c = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kBinMaxObs; ++q)
+        if (q < n_obs) c = __fmaf_rn(g[q], (float)(xo[q] - xobs(q)), c);
+    return c;
+}
+
+// dL/dX_k from the bins that the interval of state k overlaps. Edges s_first..s_last (none if
+// s_first > s_last) lie in it; gq: g of the bin that contains t_{k+1}, gk: of the bin that contains t_k;
+// draw: the interval ends at t_{k+1} = t_k + tau (else the path holds X_k to the end); brk(s): offset
+// of edge s from t_k; addx(c, v) adds v to the adjoint of observable c.
+template <class AF, class BF>
+__device__ __forceinline__ void bin_state_terms(const AF &addx, const BF &brk, const float *gl, int n_obs, int s_first,
+                                                int s_last, bool draw, float tau, const float (&gq)[kBinMaxObs],
+                                                const float (&gk)[kBinMaxObs])
+{
+    if (s_first > s_last) {  // the interval lies inside one bin
+        if (draw) {
+#pragma unroll
+            for (int c = 0; c < kBinMaxObs; ++c)
+                if (c < n_obs) addx(c, gq[c] * tau);
+        }
+        return;
+    }
+    if (draw) {  // t_{k+1} - t_{s_last} in the bin after the last edge
+        const float r = tau - brk(s_last);
+#pragma unroll
+        for (int c = 0; c < kBinMaxObs; ++c)
+            if (c < n_obs) addx(c, gq[c] * r);
+    }
+    for (int s = s_first + 1; s <= s_last; ++s) {  // whole bins: overlap D_s, so g_s D_s = dL/dobs_s
+#pragma unroll
+        for (int c = 0; c < kBinMaxObs; ++c)
+            if (c < n_obs) addx(c, gl[(int64_t)s * n_obs + c]);
+    }
+    const float d = brk(s_first);  // t_{s_first} - t_k in the bin that contains t_k
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c)
+        if (c < n_obs) addx(c, gk[c] * d);
+}
+
 // Error bits written to the workspace flag word by kernels.
 constexpr int kErrStageTimeout = 1;
 constexpr int kErrBadSamples = 2;

@@ -42,13 +42,15 @@ __global__ void __launch_bounds__(256) fwd_thread_kernel(const FwdParams p)
     thread_fwd_body<READOUT, RECORD, REPLAY, MC>(p, s_rx, s_st, s_k, s_X + tid, B, i);
 }
 
-// Validate the per-call inputs once: sample times ascending within [0, t_end], observed species
-// within [0, N). A failure marks every trajectory SSA_TRAJ_BAD_INPUT.
+// Validate the per-call inputs once: sample times ascending within [0, t_end] (strictly, from above 0,
+// for the bin readout, whose bins (t_{s-1}, t_s] must not be empty), observed species within [0, N).
+// A failure marks every trajectory SSA_TRAJ_BAD_INPUT.
 __global__ void validate_inputs_kernel(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N,
-                                       int *flag)
+                                       int strict, int *flag)
 {
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
-        const bool ok = ts[s] >= 0.0 && ts[s] <= t_end && (s == 0 || ts[s] >= ts[s - 1]);
+        const double lo = s > 0 ? ts[s - 1] : 0.0;
+        const bool ok = ts[s] >= 0.0 && ts[s] <= t_end && (s == 0 || ts[s] >= ts[s - 1]) && (!strict || ts[s] > lo);
         if (!ok) atomicOr(flag, kErrBadSamples);
     }
     for (int c = threadIdx.x; c < n_obs; c += blockDim.x)
@@ -184,19 +186,30 @@ cudaError_t launch_forward_thread(const FwdParams &p, int readout, bool record, 
 {
     if (p.n_traj == 0) return cudaSuccess;
     if (replay) {  // test hook: runtime loops, always recorded
-        return readout == SSA_READOUT_HOLD ? launch_fwd_t<0, true, true, 0>(p, block, smem, st)
-                                           : launch_fwd_t<1, true, true, 0>(p, block, smem, st);
+        switch (readout) {
+        case SSA_READOUT_HOLD: return launch_fwd_t<SSA_READOUT_HOLD, true, true, 0>(p, block, smem, st);
+        case SSA_READOUT_LINEAR: return launch_fwd_t<SSA_READOUT_LINEAR, true, true, 0>(p, block, smem, st);
+        default: return launch_fwd_t<SSA_READOUT_BIN, true, true, 0>(p, block, smem, st);
+        }
     }
     const int mc = thread_kernel_mc(p.M);
-    if (readout == SSA_READOUT_HOLD)
-        return record ? launch_fwd_mc<0, true>(p, mc, block, smem, st) : launch_fwd_mc<0, false>(p, mc, block, smem, st);
-    return record ? launch_fwd_mc<1, true>(p, mc, block, smem, st) : launch_fwd_mc<1, false>(p, mc, block, smem, st);
+    switch (readout) {
+    case SSA_READOUT_HOLD:
+        return record ? launch_fwd_mc<SSA_READOUT_HOLD, true>(p, mc, block, smem, st)
+                      : launch_fwd_mc<SSA_READOUT_HOLD, false>(p, mc, block, smem, st);
+    case SSA_READOUT_LINEAR:
+        return record ? launch_fwd_mc<SSA_READOUT_LINEAR, true>(p, mc, block, smem, st)
+                      : launch_fwd_mc<SSA_READOUT_LINEAR, false>(p, mc, block, smem, st);
+    default:
+        return record ? launch_fwd_mc<SSA_READOUT_BIN, true>(p, mc, block, smem, st)
+                      : launch_fwd_mc<SSA_READOUT_BIN, false>(p, mc, block, smem, st);
+    }
 }
 
-cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N, int *flag,
-                                  cudaStream_t st)
+cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N,
+                                  int strict, int *flag, cudaStream_t st)
 {
-    if (S > 0 || n_obs > 0) validate_inputs_kernel<<<1, 256, 0, st>>>(ts, S, t_end, obs_sp, n_obs, N, flag);
+    if (S > 0 || n_obs > 0) validate_inputs_kernel<<<1, 256, 0, st>>>(ts, S, t_end, obs_sp, n_obs, N, strict, flag);
     return cudaGetLastError();
 }
 

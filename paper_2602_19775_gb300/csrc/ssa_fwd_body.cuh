@@ -45,6 +45,15 @@ __device__ __forceinline__ void thread_fwd_body(const FwdParams &p, const int4 *
     constexpr int NQ = MC > 0 ? MC + 1 : 1;
     float E[NQ], En[NQ];
     if (MC > 0) step_noise<NQ>(E, 0u, c2, c3, key0, key1);
+    // BIN readout: integral of the open bin up to t_k per observable (species clamped when invalid)
+    float bacc[kBinMaxObs];
+    int osp[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) {
+        bacc[c] = 0.0f;
+        osp[c] = (READOUT == SSA_READOUT_BIN && c < p.n_obs && !bad_obs) ? p.obs_sp[c] : 0;
+    }
+    auto xobs = [&](int c) { return X[osp[c] * B]; };
 
     while (!bad_input) {
         if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
@@ -106,10 +115,15 @@ __device__ __forceinline__ void thread_fwd_body(const FwdParams &p, const int4 *
         if (status != SSA_TRAJ_OK) break;  // rejected update: samples hold X_k below
         if (slow) {
             // samples with t_k <= t_s < t_{k+1}
+            const int s_first = s;
             while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
                 if (READOUT == SSA_READOUT_HOLD) {
                     int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
                     for (int c = 0; c < p.n_obs; ++c) o[c] = X[p.obs_sp[c] * B];
+                } else if (READOUT == SSA_READOUT_BIN) {
+                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                    const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_first, o);
+                    if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
                 } else {
                     const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
                     float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
@@ -125,8 +139,13 @@ __device__ __forceinline__ void thread_fwd_body(const FwdParams &p, const int4 *
                 if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
                 ++s;
             }
+            // BIN: the rest of [t_k, t_{k+1}) after the last edge opens the next bin
+            if (READOUT == SSA_READOUT_BIN && !cross && s > s_first)
+                bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
             thr = s < p.S ? p.ts[s] : p.t_end;
             if (cross) break;  // the crossing draw is made but not applied
+        } else if (READOUT == SSA_READOUT_BIN) {
+            bin_accumulate(bacc, xobs, p.n_obs, tau);
         }
         for (int e = rj.z; e < rj.w; ++e) {
             const int st = s_st[e];
@@ -147,10 +166,17 @@ __device__ __forceinline__ void thread_fwd_body(const FwdParams &p, const int4 *
     }
     if (REPLAY && status == SSA_TRAJ_OK && draws != n_ev) status = SSA_TRAJ_REPLAY_MISMATCH;
     // samples after the last state hold it (absorbed, capped, rejected or bad input)
+    const int s_tail = s;
     for (; s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : X[p.obs_sp[c] * B];
+        } else if (READOUT == SSA_READOUT_BIN) {
+            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+            const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_tail, o);
+            if (bad_obs)
+                for (int c = 0; c < p.n_obs; ++c) o[c] = 0.0f;
+            if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
         } else {
             float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)X[p.obs_sp[c] * B];

@@ -34,8 +34,8 @@ namespace ssa {
 
 cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, const int *rate_index, int P,
                                    float *dA_tmp, float *dtheta, cudaStream_t st);
-cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N, int *flag,
-                                  cudaStream_t st);
+cudaError_t launch_validate_inputs(const double *ts, int S, double t_end, const int *obs_sp, int n_obs, int N,
+                                  int strict, int *flag, cudaStream_t st);
 cudaError_t launch_column_sums(const float *x, int64_t n_rows, int64_t row_len, float *partial, int64_t chunk, float *out,
                                cudaStream_t st);
 
@@ -742,7 +742,7 @@ extern "C" ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, cons
     GRN_CUDA_TRY(cudaMemcpyAsync(grid, init_grid, sizeof(init_grid), cudaMemcpyHostToDevice, st));
     if (S > 0) GRN_CUDA_TRY(cudaMemcpyAsync(ws + L.ts, sample_times, (size_t)S * 8, cudaMemcpyDeviceToDevice, st));
     GRN_CUDA_TRY(launch_validate_inputs(reinterpret_cast<const double *>(ws + L.ts), S, t_end, nullptr, 0, g->n_dyn,
-                                        flag, st));
+                                        0, flag, st));
     grn_exponents_kernel<<<64, 256, 0, st>>>(W1, (int64_t)g->n_hid * g->n_in, W2, (int64_t)g->n_out * g->n_hid, grid);
     grn_prepare_kernel<<<256, 256, 0, st>>>(W1, W2, x_img, log_d, g->n_in, g->n_hid, g->n_out, n_img, L.n_in_pad,
                                             reinterpret_cast<uint16_t *>(ws + L.W1L), reinterpret_cast<int *>(ws + L.W2fix),

@@ -28,9 +28,9 @@ constexpr int kJitMaxReactions = 24;
 constexpr int kJitMaxNnz = 96;
 
 struct JitKernels {
-    cudaKernel_t fwd[2][2];     // [readout][record], Gumbel-max choice
-    cudaKernel_t fwd_direct[2]; // [readout], direct method, forward only
-    cudaKernel_t adj[2];        // [readout]
+    cudaKernel_t fwd[3][2];     // [readout][record], Gumbel-max choice
+    cudaKernel_t fwd_direct[3]; // [readout], direct method, forward only
+    cudaKernel_t adj[3];        // [readout]
 };
 
 namespace {
@@ -210,12 +210,13 @@ const JitKernels *jit_kernels(const ssa_network *net, std::string &why)
         return nullptr;
     }
     JitKernels k{};
-    const char *fwd_names[2][2] = {{"ssa_jit_fwd_hold", "ssa_jit_fwd_hold_rec"},
-                                   {"ssa_jit_fwd_linear", "ssa_jit_fwd_linear_rec"}};
-    const char *adj_names[2] = {"ssa_jit_adj_hold", "ssa_jit_adj_linear"};
-    const char *direct_names[2] = {"ssa_jit_fwd_hold_direct", "ssa_jit_fwd_linear_direct"};
+    const char *fwd_names[3][2] = {{"ssa_jit_fwd_hold", "ssa_jit_fwd_hold_rec"},
+                                   {"ssa_jit_fwd_linear", "ssa_jit_fwd_linear_rec"},
+                                   {"ssa_jit_fwd_bin", "ssa_jit_fwd_bin_rec"}};
+    const char *adj_names[3] = {"ssa_jit_adj_hold", "ssa_jit_adj_linear", "ssa_jit_adj_bin"};
+    const char *direct_names[3] = {"ssa_jit_fwd_hold_direct", "ssa_jit_fwd_linear_direct", "ssa_jit_fwd_bin_direct"};
     bool ok = true;
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < 3; ++r) {
         for (int rec = 0; rec < 2; ++rec) ok &= cudaLibraryGetKernel(&k.fwd[r][rec], lib, fwd_names[r][rec]) == cudaSuccess;
         ok &= cudaLibraryGetKernel(&k.adj[r], lib, adj_names[r]) == cudaSuccess;
         ok &= cudaLibraryGetKernel(&k.fwd_direct[r], lib, direct_names[r]) == cudaSuccess;
@@ -235,7 +236,7 @@ cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int read
     if (p.n_traj == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((p.n_traj + block - 1) / block);
     void *args[] = {const_cast<FwdParams *>(&p)};
-    const int r = readout == SSA_READOUT_HOLD ? 0 : 1;
+    const int r = readout;  // SSA_READOUT_HOLD, _LINEAR, _BIN index the tables
     const cudaKernel_t f = selector == SSA_SELECT_DIRECT ? k->fwd_direct[r] : k->fwd[r][record ? 1 : 0];
     return cudaLaunchKernel(reinterpret_cast<const void *>(f), dim3(grid), dim3((unsigned)block), args, 0, st);
 }
@@ -246,7 +247,7 @@ cudaError_t jit_launch_backward(const JitKernels *k, const AdjParams &p, int rea
     if (grid == 0) return cudaSuccess;
     void *args[] = {const_cast<AdjParams *>(&p)};
     const size_t smem = (size_t)4 * p.M * block;
-    return cudaLaunchKernel(reinterpret_cast<const void *>(k->adj[readout == SSA_READOUT_HOLD ? 0 : 1]),
+    return cudaLaunchKernel(reinterpret_cast<const void *>(k->adj[readout]),
                             dim3((unsigned)grid), dim3((unsigned)block), args, smem, st);
 }
 

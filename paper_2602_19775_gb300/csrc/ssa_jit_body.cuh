@@ -32,6 +32,17 @@ __device__ __forceinline__ void jit_lam_add(float (&lam)[JN], int sp, float v)
         if (s == sp) lam[s] += v;
 }
 
+// BIN readout state of a forward: cleared integrals, observed species (0 where the list is invalid)
+__device__ __forceinline__ void jit_bin_init(const FwdParams &p, bool bad_obs, float (&bacc)[kBinMaxObs],
+                                             int (&osp)[kBinMaxObs])
+{
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) {
+        bacc[c] = 0.0f;
+        osp[c] = (c < p.n_obs && !bad_obs) ? p.obs_sp[c] : 0;
+    }
+}
+
 template <int READOUT, bool RECORD>
 __device__ __forceinline__ void jit_fwd(const FwdParams &p)
 {
@@ -65,6 +76,10 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
     constexpr int NQ = JM + 1;
     float E[NQ], En[NQ];
     step_noise<NQ>(E, 0u, c2, c3, key0, key1);
+    float bacc[kBinMaxObs];
+    int osp[kBinMaxObs];
+    jit_bin_init(p, bad_obs, bacc, osp);
+    auto xobs = [&](int c) { return jit_xsel(X, osp[c]); };
 
     while (!bad_input) {
         if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
@@ -97,10 +112,15 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
         draws = k + 1;
         if (status != SSA_TRAJ_OK) break;
         if (slow) {
+            const int s_first = s;
             while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
                 if (READOUT == SSA_READOUT_HOLD) {
                     int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
                     for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
+                } else if (READOUT == SSA_READOUT_BIN) {
+                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                    const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_first, o);
+                    if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
                 } else {
                     const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
                     float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
@@ -113,8 +133,12 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
                 if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
                 ++s;
             }
+            if (READOUT == SSA_READOUT_BIN && !cross && s > s_first)
+                bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
             thr = s < p.S ? p.ts[s] : p.t_end;
             if (cross) break;  // the crossing draw is made but not applied
+        } else if (READOUT == SSA_READOUT_BIN) {
+            bin_accumulate(bacc, xobs, p.n_obs, tau);
         }
         jit_apply(X, jb);
         t = t_next;
@@ -129,10 +153,17 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) E[q] = En[q];
     }
+    const int s_tail = s;
     for (; s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : jit_xsel(X, p.obs_sp[c]);
+        } else if (READOUT == SSA_READOUT_BIN) {
+            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+            const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_tail, o);
+            if (bad_obs)
+                for (int c = 0; c < p.n_obs; ++c) o[c] = 0.0f;
+            if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
         } else {
             float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)jit_xsel(X, p.obs_sp[c]);
@@ -192,6 +223,10 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
     int k = 0, draws = 0;
     uint4 r = philox4x32_10(make_uint4(0u, 0u, c2, c3), key0, key1);
     float E0 = neg_log_unit(u01(r.x)), U1 = u01(r.y);
+    float bacc[kBinMaxObs];
+    int osp[kBinMaxObs];
+    jit_bin_init(p, bad_obs, bacc, osp);
+    auto xobs = [&](int c) { return jit_xsel(X, osp[c]); };
     while (!bad_input) {
         if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
         r = philox4x32_10(make_uint4(0u, (uint32_t)(k + 1), c2, c3), key0, key1);  // next step
@@ -223,10 +258,15 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
         draws = k + 1;
         if (status != SSA_TRAJ_OK) break;
         if (slow) {
+            const int s_first = s;
             while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
                 if (READOUT == SSA_READOUT_HOLD) {
                     int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
                     for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
+                } else if (READOUT == SSA_READOUT_BIN) {
+                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                    const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_first, o);
+                    (void)d;
                 } else {
                     const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
                     float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
@@ -237,8 +277,12 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
                 }
                 ++s;
             }
+            if (READOUT == SSA_READOUT_BIN && !cross && s > s_first)
+                bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
             thr = s < p.S ? p.ts[s] : p.t_end;
             if (cross) break;
+        } else if (READOUT == SSA_READOUT_BIN) {
+            bin_accumulate(bacc, xobs, p.n_obs, tau);
         }
         jit_apply(X, jb);
         t = t_next;
@@ -246,10 +290,16 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
         E0 = neg_log_unit(u01(r.x));
         U1 = u01(r.y);
     }
+    const int s_tail = s;
     for (; s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : jit_xsel(X, p.obs_sp[c]);
+        } else if (READOUT == SSA_READOUT_BIN) {
+            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+            bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_tail, o);
+            if (bad_obs)
+                for (int c = 0; c < p.n_obs; ++c) o[c] = 0.0f;
         } else {
             float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)jit_xsel(X, p.obs_sp[c]);
@@ -301,6 +351,21 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
     const bool draw_last = st == SSA_TRAJ_OK;
     step_noise<NQ>(E, (uint32_t)(draw_last ? L : (L > 0 ? L - 1 : 0)), c2, c3, key0, key1);
 
+    // BIN readout: gq = g of the bin that contains t_{k+1}, xo = X_{k+1} at the observables
+    constexpr bool kBin = READOUT == SSA_READOUT_BIN;
+    float gq[kBinMaxObs], gk[kBinMaxObs];
+    int osp[kBinMaxObs], xo[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) osp[c] = (kBin && c < p.n_obs) ? p.obs_sp[c] : 0;
+    auto xobs = [&](int c) { return jit_xsel(X, osp[c]); };
+    auto addx = [&](int c, float v) { jit_lam_add(lam, osp[c], v); };
+    auto brk = [&](int s) { return p.brk_a[(int64_t)s * n + i]; };
+    if (kBin) {
+        bin_grad(gq, gl, p.n_obs, p.ts, p.S, p.S);
+#pragma unroll
+        for (int c = 0; c < kBinMaxObs; ++c) xo[c] = c < p.n_obs ? xobs(c) : 0;
+    }
+
     for (int k = L; k >= 0; --k) {
         const bool draw = (k < L) || draw_last;
         const int s_top = s_hi;
@@ -309,6 +374,14 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
         }
         // samples s_hi+1 .. s_top are bracketed by state k
+        if (kBin) {
+            if (s_hi < s_top) bin_grad(gk, gl, p.n_obs, p.ts, p.S, s_hi + 1);
+            else {
+#pragma unroll
+                for (int c = 0; c < kBinMaxObs; ++c) gk[c] = gq[c];
+            }
+        }
+        float tau_k = 0.0f;
         if (draw) {
             const int jk = event_at(k);
             if (k > 0) step_noise<NQ>(En, (uint32_t)(k - 1), c2, c3, key0, key1);  // prefetch
@@ -327,6 +400,9 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             }
             mism += (jb != jk);
             const float tau = __fdividef(E0, a0);
+            tau_k = tau;
+            // BIN: t_{k+1} ends this interval and starts the next, in the bin of gq
+            if (kBin) mu -= bin_transition(xobs, xo, gq, p.n_obs);
             // readout terms that involve X_{k+1} and the clock (LINEAR interpolation)
             float dt_dir = 0.0f, dtau_dir = 0.0f;
             if (READOUT == SSA_READOUT_LINEAR) {
@@ -370,13 +446,22 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             jit_state_adj(X, a, h, psi, ctau, lam);
             mu += dt_dir;  // t_{k+1} = t_k + tau_k
         }
-        for (int s = s_hi + 1; s <= s_top; ++s) {
-            float coef = 1.0f;
-            if (READOUT == SSA_READOUT_LINEAR && draw) {
-                const float alpha = p.brk_a[(int64_t)s * n + i];
-                if (alpha >= 0.0f) coef = 1.0f - alpha;
+        if (kBin) {
+            bin_state_terms(addx, brk, gl, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
+#pragma unroll
+            for (int c = 0; c < kBinMaxObs; ++c) {
+                gq[c] = gk[c];
+                if (c < p.n_obs) xo[c] = xobs(c);
             }
-            for (int o = 0; o < p.n_obs; ++o) jit_lam_add(lam, p.obs_sp[o], coef * gl[(int64_t)s * p.n_obs + o]);
+        } else {
+            for (int s = s_hi + 1; s <= s_top; ++s) {
+                float coef = 1.0f;
+                if (READOUT == SSA_READOUT_LINEAR && draw) {
+                    const float alpha = p.brk_a[(int64_t)s * n + i];
+                    if (alpha >= 0.0f) coef = 1.0f - alpha;
+                }
+                for (int o = 0; o < p.n_obs; ++o) jit_lam_add(lam, p.obs_sp[o], coef * gl[(int64_t)s * p.n_obs + o]);
+            }
         }
         if (ck_off == 0) {
             const int *ck = p.ckpt + (int64_t)ck_row * JN * n + i;
@@ -444,6 +529,18 @@ extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_linear_rec(const s
 {
     ssa::jit_fwd<SSA_READOUT_LINEAR, true>(p);
 }
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_bin(const ssa::FwdParams p)
+{
+    ssa::jit_fwd<SSA_READOUT_BIN, false>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_bin_rec(const ssa::FwdParams p)
+{
+    ssa::jit_fwd<SSA_READOUT_BIN, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_bin_direct(const ssa::FwdParams p)
+{
+    ssa::jit_fwd_direct<SSA_READOUT_BIN>(p);
+}
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_hold_direct(const ssa::FwdParams p)
 {
     ssa::jit_fwd_direct<SSA_READOUT_HOLD>(p);
@@ -459,4 +556,8 @@ extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_hold(const ssa::Ad
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_linear(const ssa::AdjParams p)
 {
     ssa::jit_adj<SSA_READOUT_LINEAR>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_bin(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_BIN>(p);
 }

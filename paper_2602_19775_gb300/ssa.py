@@ -23,7 +23,7 @@ import torch
 from . import _lib
 from ._lib import FwdOpts, SSAError, check
 
-READOUTS = {"hold": _lib.SSA_READOUT_HOLD, "linear": _lib.SSA_READOUT_LINEAR}
+READOUTS = {"hold": _lib.SSA_READOUT_HOLD, "linear": _lib.SSA_READOUT_LINEAR, "bin": _lib.SSA_READOUT_BIN}
 SELECTORS = {"gumbel": 0, "direct": 1}
 
 

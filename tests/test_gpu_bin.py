@@ -1,0 +1,181 @@
+"""GPU tests of the exact bin-averaged readout (arXiv 2602.19775, Section 4.4) against the FP64 oracle:
+bin averages element by element on the same seeded trajectories, the straight-through gradient through
+them, the ensemble means of the ion-channel workload (262,144 trajectories, 800 bins of 0.01 ms) against
+the master equation averaged over each bin, and the input rules and limits of the readout.
+
+Tolerance of a bin average on a trajectory whose event sequence matches the oracle's: every event time
+inside the bin may be off by the FP32 clock tolerance, moving a jump of at most max|v| by that much, and
+the binary32 sum over the bin's pieces adds a few roundings of the largest count:
+    |obs_gpu - obs_oracle| <= (n_events * max|v| * tol(t_s) + (n_events + 4) * 4 eps32 * max X * D_s) / D_s.
+"""
+import numpy as np
+import pytest
+import torch
+
+import ssa_workloads as W
+from oracle import cme, native
+
+from test_gpu_parity import EPS32, GRAD_RTOL, _T_END, _bracket_agreement, _clock_tol, _compare_events, _theta32
+
+pytestmark = pytest.mark.gpu
+BIN = native.BIN
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2602_19775_gb300 import ssa
+    ssa._lib.lib()
+    return ssa
+
+
+def _lo(ts):
+    return np.concatenate([[0.0], np.asarray(ts)[:-1]])
+
+
+def _run_both(S, net, n, t_end, ts, obs_sp, seed, dl=None, T=1.0, max_steps=4096, specialize=True, K=64):
+    t32, t64 = _theta32(net.log_rates)
+    snet = S.Network(net)
+    fw = S.forward(snet, torch.tensor(t32, device="cuda"), n, net.x0, t_end, ts, obs_sp, seed, readout="bin",
+                   record=True, max_steps=max_steps, specialize=specialize, ckpt_interval=K)
+    torch.cuda.synchronize()
+    orc = native.run(net, t64, net.x0, n, t_end, ts, np.asarray(obs_sp, np.int32), seed, BIN, max_steps=max_steps,
+                     dl_dobs=dl, temperature=T, ev_cap=max_steps)
+    return snet, fw, orc, fw.run.events(max_steps).cpu().numpy()
+
+
+def _check_obs(net, fw, orc, same, ts, obs_sp):
+    V = net.stoich_dense()
+    vmax = np.abs(V[:, obs_sp]).max(0)
+    lo, D = _lo(ts), np.asarray(ts) - _lo(ts)
+    obs_g = fw.obs.double().cpu().numpy()
+    tol_t = _clock_tol(net.n_reactions, np.asarray(ts))
+    worst = 0.0
+    for i in np.nonzero(same)[0]:
+        t_ev = orc.times[i, :orc.draws[i]]
+        xmax = np.abs(orc.obs[i]).max(0) * 2 + 1
+        for s in range(len(ts)):
+            n_ev = np.sum((t_ev > lo[s] - tol_t[s]) & (t_ev <= ts[s] + tol_t[s]))
+            bound = (n_ev * vmax * tol_t[s] + (n_ev + 4) * 4 * EPS32 * xmax * D[s]) / D[s]
+            err = np.abs(obs_g[i, s] - orc.obs[i, s])
+            assert np.all(err <= bound), (i, s, obs_g[i, s], orc.obs[i, s], bound)
+            worst = max(worst, float((err / bound).max()))
+    return worst
+
+
+CASES = {
+    "ion_channel": lambda: (W.ion_channel_coi(), 8.0, W.uniform_sample_grid(8.0, 80), [1], 4096),
+    "mixed_orders": lambda: (W.mixed_orders_toy(), 6.0, W.uniform_sample_grid(6.0, 11), [0, 1, 2], 1000),
+    "dimer": lambda: (W.dimerization_2a_b(0.02, 0.05, 100), 50.0, W.uniform_sample_grid(50.0, 50), [0, 1], 2048),
+    "ragged_bins": lambda: (W.mixed_orders_toy(), 5.0, np.array([1e-3, 0.5, 0.5 + 1e-6, 0.75, 3.0, 4.999, 5.0]),
+                            [0, 2], 777),
+}
+
+
+@pytest.mark.parametrize("specialize", [True, False])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_bin_forward_matches_oracle(S, case, specialize):
+    net, t_end, ts, obs_sp, n = CASES[case]()
+    _T_END["t_end"] = t_end
+    snet, fw, orc, gev = _run_both(S, net, n, t_end, ts, obs_sp, 3, specialize=specialize)
+    assert fw.run.variant == (2 if specialize else 1)
+    assert np.all(fw.status.cpu().numpy() <= 1)
+    same = _compare_events(orc, fw, gev)
+    assert same.mean() >= 0.999, same.mean()
+    _check_obs(net, fw, orc, same, ts, np.asarray(obs_sp))
+
+
+@pytest.mark.parametrize("case,T", [("ion_channel", 0.5), ("mixed_orders", 0.5), ("dimer", 0.1), ("dimer", 1.0),
+                                    ("ragged_bins", 0.3)])
+def test_bin_backward_matches_oracle(S, case, T):
+    net, t_end, ts, obs_sp, n = CASES[case]()
+    _T_END["t_end"] = t_end
+    dl = W.seeded_dl_dobs(5, n, len(ts), len(obs_sp), scale=1.0 / n)
+    snet, fw, orc, gev = _run_both(S, net, n, t_end, ts, obs_sp, 9, dl=dl, T=T, K=16)
+    same = _compare_events(orc, fw, gev)
+    assert same.mean() >= 0.999, same.mean()
+    # an event within the clock tolerance of an edge moves its time derivative to the other bin
+    agree = _bracket_agreement(orc, fw, np.asarray(ts), net.n_reactions)
+    assert agree.mean() >= 0.99, agree.mean()
+    same &= agree
+    dl_g = dl.copy()
+    dl_g[~same] = 0.0
+    g = S.backward(fw, torch.tensor(dl_g, dtype=torch.float32, device="cuda"), T).cpu().numpy().astype(np.float64)
+    ref = orc.dtheta[same].sum(0)
+    assert fw.run.status_counts()[1] == 0
+    rel = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert rel < GRAD_RTOL, (rel, g, ref)
+    big = np.abs(ref) > 1e-3 * np.linalg.norm(ref)
+    np.testing.assert_allclose(g[big], ref[big], rtol=2 * GRAD_RTOL)
+
+
+def test_ion_channel_bin_means_match_cme(S):
+    """The Section 4.4 workload at its size: 2 channels C <-> O -> I, 262,144 trajectories, 800 bins of
+    0.01 ms over 8 ms; ensemble means of the open count against the CME law averaged over each bin."""
+    net = W.ion_channel_coi()
+    ts = W.uniform_sample_grid(8.0, 800)
+    n = 262144
+    snet = S.Network(net)
+    fw = S.forward(snet, torch.tensor(net.log_rates.astype(np.float32), device="cuda"), n, net.x0, 8.0, ts, [1], 17,
+                   readout="bin", max_steps=64)
+    assert int((fw.status > 1).sum()) == 0
+    O = fw.obs[:, :, 0].double()
+    m = O.mean(0).cpu().numpy()
+    se = (O.std(0) / np.sqrt(n)).cpu().numpy()
+    k32 = net.log_rates.astype(np.float32).astype(np.float64)
+    states, index = cme.reachable_states(net, net.x0)
+    Q = cme.generator(net, k32, states, index)
+    p0 = np.zeros(len(states))
+    p0[index[tuple(int(v) for v in net.x0)]] = 1.0
+    exact = cme.transient_bin_average(Q, p0, ts) @ np.array([x[1] for x in states], dtype=np.float64)
+    z = (m - exact) / np.maximum(se, 1e-12)
+    # 800 correlated bins: 4.5 SE each keeps the family-wise false-alarm rate under 1%
+    assert np.all(np.abs(z) < 4.5), (np.abs(z).max(), int(np.abs(z).argmax()))
+
+
+def test_bin_autograd_function_matches_backward(S):
+    net = W.ion_channel_coi()
+    ts = W.uniform_sample_grid(8.0, 40)
+    theta = torch.tensor(net.log_rates.astype(np.float32), device="cuda", requires_grad=True)
+    target = torch.linspace(0.0, 0.5, 40, device="cuda")[:, None]
+    snet = S.Network(net)
+    obs = S.simulate(snet, theta, 8192, net.x0, 8.0, ts, [1], 4, readout="bin", temperature=0.5, max_steps=64)
+    loss = ((obs.mean(0) - target) ** 2).mean()
+    loss.backward()
+    fw = S.forward(snet, theta.detach(), 8192, net.x0, 8.0, ts, [1], 4, readout="bin", record=True, max_steps=64)
+    assert torch.equal(fw.obs, obs.detach())
+    dl = 2.0 * (fw.obs.mean(0) - target) / target.numel() / 8192
+    g = S.backward(fw, dl.expand(8192, -1, -1).contiguous(), 0.5)
+    torch.testing.assert_close(theta.grad, g, rtol=1e-5, atol=1e-7)
+
+
+def test_bin_input_rules_and_limits(S):
+    net = W.mixed_orders_toy()
+    snet = S.Network(net)
+    theta = torch.tensor(net.log_rates.astype(np.float32), device="cuda")
+    # a path that cannot move: every bin holds the initial state exactly, and the gradient is zero
+    frozen = W.network_from_reactions(["A", "B"], [(["A", "B"], ["B"], "k")], rates={"k": 1.0}, x0={"A": 3})
+    fnet = S.Network(frozen)
+    fw = S.forward(fnet, torch.tensor(frozen.log_rates.astype(np.float32), device="cuda"), 5, frozen.x0, 2.0,
+                   [0.5, 1.0, 2.0], [0, 1], 0, readout="bin", record=True)
+    assert torch.equal(fw.obs.cpu(), torch.tensor([[3.0, 0.0]] * 3).expand(5, 3, 2))
+    assert int(fw.status[0]) == 1
+    g = S.backward(fw, torch.ones(5, 3, 2, device="cuda"), 0.5)
+    assert torch.count_nonzero(g) == 0
+    # empty first bin (t_0 = 0) or a repeated edge: every trajectory is BAD_INPUT
+    for ts in ([0.0, 1.0], [0.5, 0.5, 1.0]):
+        fw = S.forward(snet, theta, 8, net.x0, 1.0, ts, [0], 0, readout="bin")
+        assert torch.all(fw.status == 6), ts
+    # the same edges are fine for the HOLD readout
+    fw = S.forward(snet, theta, 8, net.x0, 1.0, [0.0, 1.0], [0], 0, readout="hold")
+    assert torch.all(fw.status <= 1)
+    # more than SSA_BIN_MAX_OBS observables, the warp kernels and the batch refuse the readout
+    with pytest.raises(RuntimeError):
+        S.forward(snet, theta, 8, net.x0, 1.0, [1.0], [0, 1, 2, 0, 1], 0, readout="bin")
+    with pytest.raises(RuntimeError):
+        S.forward(snet, theta, 8, net.x0, 1.0, [1.0], [0], 0, readout="bin", threads_per_traj=32)
+    with pytest.raises(RuntimeError):
+        S.Batch([dict(net=snet, log_rates=theta, n_traj=8, x0=net.x0, t_end=1.0, sample_times=[1.0],
+                      obs_species=[0], seed=0)], readout="bin")
+    # empty batch of trajectories
+    fw = S.forward(snet, theta, 0, net.x0, 1.0, [0.5, 1.0], [0], 0, readout="bin", record=True)
+    assert fw.obs.shape == (0, 2, 1)

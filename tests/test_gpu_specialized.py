@@ -1,7 +1,7 @@
 """GPU tests of the network-specialised kernels (compiled at run time for one network): they reproduce
 the generic thread-per-trajectory kernels bit for bit -- observables, draws, status codes, event logs,
 sample brackets -- and their gradients to binary32 rounding, on networks covering every mass-action
-order, HOLD and LINEAR readouts, and the size limits; networks above the limits keep the generic
+order, the HOLD, LINEAR and BIN readouts, and the size limits; networks above the limits keep the generic
 kernels. Parity of the specialised kernels with the FP64 oracle is covered by the oracle tests, which
 run them by default."""
 import numpy as np
@@ -29,6 +29,7 @@ def _random(seed, n_sp, n_rx):
 CASES = {
     "dimer": lambda: (W.dimerization_2a_b(), 50.0, [0, 1]),
     "immigration_death": lambda: (W.immigration_death(), 5.0, [0]),
+    "ion_channel": lambda: (W.ion_channel_coi(), 8.0, [1]),
     "mixed_orders": lambda: (W.mixed_orders_toy(), 6.0, [0, 1, 2]),
     "oscillator": lambda: (W.vilar_oscillator(), 1.0, [6, 7, 8]),
     "random_10": lambda: (_random(21, (3, 8), (10, 10)), None, [0, 1]),
@@ -37,7 +38,7 @@ CASES = {
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
-@pytest.mark.parametrize("readout", ["hold", "linear"])
+@pytest.mark.parametrize("readout", ["hold", "linear", "bin"])
 def test_specialised_kernels_match_generic(S, case, readout):
     spec, t_end, obs = CASES[case]()
     if t_end is None:
