@@ -375,6 +375,7 @@ def run_ours(args):
     grn = grn_extra(ssa, dev, n_img=args.grn_images) if (rank == 0 and "grn" in legs) else None
     warp = warp_extra(ssa, dev, n=args.warp_traj) if (rank == 0 and "warp" in legs) else None
     c3 = c3_extra(ssa, dev) if (rank == 0 and "c3" in legs) else None
+    ion = ion_channel_extra(ssa, dev) if (rank == 0 and "ion" in legs) else None
     M = wl.net.n_reactions
     rates = ssa.pipe_rates()
     log_slots = 128.0 / rates["neglog"]
@@ -429,6 +430,7 @@ def run_ours(args):
         "grn": grn,
         "warp_kernels": warp,
         "oscillator_full": c3,
+        "ion_channel": ion,
         "paper_context": "1.9e9 SSA steps/s forward on the oscillator, RTX 6000 Ada + TF 2.20 (a different machine)",
         "cpu_baseline": cpu_base,
         "e2e": {"value": e2e_value, "unit": "SSA steps/s (fwd+adj)", "h2d_bytes_per_step": h2d,
@@ -476,6 +478,46 @@ def oscillator_extra(ssa, dev, n_fwd: int = 1 << 20, n_adj: int = 1 << 16, t_end
                 steps += int(fw.draws.sum().item())
             del fw
         out[mode] = {"n_traj": n, "steps": steps // reps, "ms": ms / reps, "steps_per_s": steps / (ms / 1e3)}
+    return out
+
+
+def ion_channel_extra(ssa, dev, n: int = 262144, reps: int = 3, T: float = 0.05):
+    """The ion-channel workload of Section 4.4: two channels C <-> O -> I from all closed, 262,144
+    trajectories, the open count averaged exactly over 800 bins of 0.01 ms (8 ms). One gradient step =
+    recorded forward + the loss gradient of the bin-mean MSE against a target + the straight-through
+    adjoint; timed with CUDA events after one warm-up step, and a forward alone beside it."""
+    import torch
+
+    import ssa_workloads as W
+    spec = W.ion_channel_coi()
+    net = ssa.Network(spec)
+    ts = W.uniform_sample_grid(8.0, 800)
+    th = torch.tensor(spec.log_rates.astype(np.float32), device=dev)
+    target = ssa.forward(net, th, n, spec.x0, 8.0, ts, [1], 999, readout="bin", max_steps=64).obs.mean(0)
+    theta = th + 0.2
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {"workload": "ion channel C <-> O -> I, 2 channels, 262,144 trajectories, 800 bins of 0.01 ms, BIN readout"}
+    for mode in ("forward", "gradient_step"):
+        ms, steps = 0.0, 0
+        for r in range(reps + 1):
+            if r == 1:
+                torch.cuda.synchronize()
+            if r >= 1:
+                ev[0].record(stream)
+            fw = ssa.forward(net, theta, n, spec.x0, 8.0, ts, [1], 60 + r, readout="bin",
+                             record=mode != "forward", max_steps=64)
+            if mode != "forward":
+                dl = 2.0 * (fw.obs.mean(0) - target) / (target.numel() * n)
+                ssa.backward(fw, dl, T)
+            if r >= 1:
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                ms += ev[0].elapsed_time(ev[1])
+                steps += int(fw.draws.sum().item())
+            del fw
+        out[mode] = {"ms": ms / reps, "ssa_steps": steps // reps, "steps_per_s": steps / (ms / 1e3)}
+    out["paper_context_ms_per_epoch"] = 112e3 / 400
     return out
 
 
@@ -791,8 +833,9 @@ def main():
     ap.add_argument("--ref-chunk", type=int, default=4096)
     ap.add_argument("--no-oracle", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the oscillator and uneven-batch fields")
-    ap.add_argument("--legs", default="oscillator,batch,grn,warp",
-                    help="comma-separated extra fields to measure: oscillator, batch, grn, warp, c3 (the oscillator at its "
+    ap.add_argument("--legs", default="oscillator,batch,grn,warp,ion",
+                    help="comma-separated extra fields to measure: oscillator, batch, grn, warp, ion (the ion channel of "
+                         "Section 4.4), c3 (the oscillator at its "
                          "full size, about two minutes; not in the default) ('none' for none)")
     ap.add_argument("--grn-images", type=int, default=512, help="images of the GRN field (64 trajectories each)")
     ap.add_argument("--warp-traj", type=int, default=16384, help="trajectories of the warp-kernel field")

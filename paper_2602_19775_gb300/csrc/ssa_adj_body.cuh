@@ -66,7 +66,8 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
         return (slot & 1) ? (int)(w >> 16) : (int)(w & 0xffff);
     };
 
-    int s_hi = p.S - 1;
+    // BIN: the edges after brk_tail[i] belong to the last state and are not stored
+    int s_hi = READOUT == SSA_READOUT_BIN ? min(p.brk_tail[i], p.S - 1) : p.S - 1;
     int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
     float mu = 0.0f;
     int mism = 0;
@@ -95,7 +96,7 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
 
     for (int k = L; k >= 0; --k) {
         const bool draw = (k < L) || draw_last;
-        const int s_top = s_hi;
+        const int s_top = (READOUT == SSA_READOUT_BIN && k == L) ? p.S - 1 : s_hi;
         while (s_hi >= 0 && brk_next == k) {
             --s_hi;
             brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;

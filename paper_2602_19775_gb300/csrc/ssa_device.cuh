@@ -315,6 +315,7 @@ struct FwdParams {
     int *ckpt;        // [n_ckpt][N][n_traj]
     int *brk_k;       // [S][n_traj]
     float *brk_a;     // [S][n_traj]
+    int *brk_tail;    // [n_traj], BIN readout: first edge bracketed by the last state (S: none)
     int *xfinal;      // [N][n_traj]
     // replay
     const uint16_t *ev_in;
@@ -340,6 +341,7 @@ struct AdjParams {
     const int *ckpt;
     const int *brk_k;
     const float *brk_a;
+    const int *brk_tail;
     const int *xfinal;
     const float *dl_dobs;
     int64_t dl_stride;  // elements between trajectories (0 = shared)
@@ -349,5 +351,53 @@ struct AdjParams {
     int *err;
 };
 
+
+// Bin readout, after the last state X_k (held from t_k on): the first remaining bin s may have begun
+// before t_k, the later ones hold X_k exactly. Each thread closes its first remaining bin; then the warp
+// writes the held rows of its trajectories together, one trajectory at a time with consecutive lanes
+// on consecutive floats, so the stores of a long constant tail are coalesced. Recording stores the
+// bracket of the first remaining edge and, in tail[i], its index (S if none): the edges after it are
+// not stored. Every lane of the warp whose trajectory index is below n_traj must call this.
+template <bool RECORD, class XF>
+__device__ __forceinline__ void bin_tail(const FwdParams &p, int64_t i, int s, double t_k, int k,
+                                         float (&acc)[kBinMaxObs], const XF &xobs, bool bad_obs)
+{
+    const int64_t n = p.n_traj;
+    const int S = p.S, no = p.n_obs;
+    float *obs = static_cast<float *>(p.obs_out);
+    if (s < S) {
+        float *o = obs + ((int64_t)i * S + s) * no;
+        const float d = bin_close(acc, xobs, no, p.ts, s, t_k, true, o);
+        if (bad_obs)
+            for (int c = 0; c < no; ++c) o[c] = 0.0f;
+        if (RECORD) {
+            p.brk_a[(int64_t)s * n + i] = d;
+            p.brk_k[(int64_t)s * n + i] = k;
+        }
+    }
+    if (RECORD) p.brk_tail[i] = s < S ? s : S;
+    float xv[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) xv[c] = (c < no && !bad_obs) ? int2f(xobs(c)) : 0.0f;
+    const int lane = (int)(threadIdx.x & 31);
+    const int64_t base = i - lane;
+    const unsigned mask = base + 32 <= n ? 0xffffffffu : ((1u << (unsigned)(n - base)) - 1u);
+    const int first = s + 1;  // first held row
+    for (int j = 0; j < 32 && ((mask >> j) & 1u); ++j) {
+        const int fj = __shfl_sync(mask, first, j);
+        float vj[kBinMaxObs];
+#pragma unroll
+        for (int c = 0; c < kBinMaxObs; ++c) vj[c] = __shfl_sync(mask, xv[c], j);
+        if (fj >= S) continue;  // the same for every lane
+        float *row = obs + (base + j) * (int64_t)S * no;
+        for (int64_t e = (int64_t)fj * no + lane; e < (int64_t)S * no; e += 32) {
+            const int c = no == 1 ? 0 : (int)(e % no);
+            float v = vj[0];
+#pragma unroll
+            for (int q = 1; q < kBinMaxObs; ++q) v = c == q ? vj[q] : v;
+            row[e] = v;
+        }
+    }
+}
 
 }  // namespace ssa

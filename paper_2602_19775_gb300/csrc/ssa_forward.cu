@@ -128,14 +128,17 @@ __global__ void unpack_events_kernel(const uint4 *ev, const int *draws, int64_t 
     out[idx] = v;
 }
 
-// Test hook: brackets [S][n] -> [n][S].
-__global__ void transpose_brackets_kernel(const int *brk, int64_t n_traj, int S, int *out)
+// Test hook: brackets [S][n] -> [n][S]. With the bin readout the edges after the first one bracketed
+// by the last state are not stored (tail[i] is that first edge); they belong to the last state.
+__global__ void transpose_brackets_kernel(const int *brk, int64_t n_traj, int S, const int *tail, const int *draws,
+                                          const int *status, int *out)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n_traj * S) return;
     const int64_t i = idx / S;
     const int s = (int)(idx % S);
-    out[idx] = brk[(int64_t)s * n_traj + i];
+    if (tail && s > tail[i]) out[idx] = status[i] == SSA_TRAJ_OK ? draws[i] - 1 : draws[i];
+    else out[idx] = brk[(int64_t)s * n_traj + i];
 }
 
 // Status histogram for ssa_run_status.
@@ -274,11 +277,13 @@ cudaError_t launch_unpack_events(const uint4 *ev, const int *draws, int64_t n_tr
     return cudaGetLastError();
 }
 
-cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, int *out, cudaStream_t st)
+cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, const int *tail, const int *draws,
+                                      const int *status, int *out, cudaStream_t st)
 {
     const int64_t total = n_traj * S;
     if (total == 0) return cudaSuccess;
-    transpose_brackets_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(brk, n_traj, S, out);
+    transpose_brackets_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(brk, n_traj, S, tail, draws, status,
+                                                                               out);
     return cudaGetLastError();
 }
 

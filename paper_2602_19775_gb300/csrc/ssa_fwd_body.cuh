@@ -166,17 +166,11 @@ __device__ __forceinline__ void thread_fwd_body(const FwdParams &p, const int4 *
     }
     if (REPLAY && status == SSA_TRAJ_OK && draws != n_ev) status = SSA_TRAJ_REPLAY_MISMATCH;
     // samples after the last state hold it (absorbed, capped, rejected or bad input)
-    const int s_tail = s;
-    for (; s < p.S; ++s) {
+    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs);
+    for (; READOUT != SSA_READOUT_BIN && s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : X[p.obs_sp[c] * B];
-        } else if (READOUT == SSA_READOUT_BIN) {
-            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-            const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_tail, o);
-            if (bad_obs)
-                for (int c = 0; c < p.n_obs; ++c) o[c] = 0.0f;
-            if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
         } else {
             float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)X[p.obs_sp[c] * B];

@@ -153,17 +153,11 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) E[q] = En[q];
     }
-    const int s_tail = s;
-    for (; s < p.S; ++s) {
+    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs);
+    for (; READOUT != SSA_READOUT_BIN && s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : jit_xsel(X, p.obs_sp[c]);
-        } else if (READOUT == SSA_READOUT_BIN) {
-            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-            const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_tail, o);
-            if (bad_obs)
-                for (int c = 0; c < p.n_obs; ++c) o[c] = 0.0f;
-            if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
         } else {
             float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)jit_xsel(X, p.obs_sp[c]);
@@ -290,16 +284,11 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
         E0 = neg_log_unit(u01(r.x));
         U1 = u01(r.y);
     }
-    const int s_tail = s;
-    for (; s < p.S; ++s) {
+    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<false>(p, i, s, t, k, bacc, xobs, bad_obs);
+    for (; READOUT != SSA_READOUT_BIN && s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : jit_xsel(X, p.obs_sp[c]);
-        } else if (READOUT == SSA_READOUT_BIN) {
-            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-            bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_tail, o);
-            if (bad_obs)
-                for (int c = 0; c < p.n_obs; ++c) o[c] = 0.0f;
         } else {
             float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)jit_xsel(X, p.obs_sp[c]);
@@ -340,7 +329,8 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
         return (slot & 1) ? (int)(w >> 16) : (int)(w & 0xffff);
     };
 
-    int s_hi = p.S - 1;
+    // BIN: the edges after brk_tail[i] belong to the last state and are not stored
+    int s_hi = READOUT == SSA_READOUT_BIN ? min(p.brk_tail[i], p.S - 1) : p.S - 1;
     int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
     float mu = 0.0f;
     int mism = 0;
@@ -368,7 +358,7 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
 
     for (int k = L; k >= 0; --k) {
         const bool draw = (k < L) || draw_last;
-        const int s_top = s_hi;
+        const int s_top = (READOUT == SSA_READOUT_BIN && k == L) ? p.S - 1 : s_hi;
         while (s_hi >= 0 && brk_next == k) {
             --s_hi;
             brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
