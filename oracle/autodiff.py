@@ -34,11 +34,14 @@ def _h(reactants, X):
 
 
 def st_gradient(net, log_rates, x0, events, n_states: int, crossed: bool, seed: int, traj: int,
-                t_end: float, sample_times, obs_species, readout: int, dl_dobs, temperature: float):
+                t_end: float, sample_times, obs_species, readout: int, dl_dobs, temperature: float,
+                soft: bool = False):
     """dL/dtheta of L = sum(dl_dobs * obs) through the literal Eq.-5 graph of one trajectory.
 
     events: the hard choices j_0..j_{n_draws-1}; n_states: number of visited states; crossed:
-    whether the last draw crossed t_end (made but not applied)."""
+    whether the last draw crossed t_end (made but not applied). soft: the relaxed forward of Eq. 4
+    instead (the update is the soft sample itself, real-valued states, negative mass-action factors
+    clipped to 0)."""
     theta = torch.tensor(np.asarray(log_rates, dtype=np.float64), requires_grad=True)
     k_rates = torch.exp(theta)[torch.as_tensor(net.rate_index, dtype=torch.long)]
     V = torch.as_tensor(net.stoich_dense(), dtype=torch.float64)
@@ -49,7 +52,10 @@ def st_gradient(net, log_rates, x0, events, n_states: int, crossed: bool, seed: 
     n_draws = len(events)
     for k in range(n_draws):
         u = torch.as_tensor(uniforms(seed, traj, k, M + 1))
-        a = torch.stack([k_rates[j] * _h(net.reactants[j], X) for j in range(M)])
+        hs = [_h(net.reactants[j], X) for j in range(M)]
+        if soft:
+            hs = [torch.clamp(h, min=0.0) for h in hs]
+        a = torch.stack([k_rates[j] * hs[j] for j in range(M)])
         a0 = a.sum()
         tau = -torch.log(u[0]) / a0
         active = a > 0
@@ -60,7 +66,7 @@ def st_gradient(net, log_rates, x0, events, n_states: int, crossed: bool, seed: 
         y_soft = torch.softmax(z, dim=0)
         y_hard = torch.zeros(M, dtype=torch.float64)
         y_hard[int(events[k])] = 1.0
-        y_st = y_soft + (y_hard - y_soft).detach()          # Eq. 5
+        y_st = y_soft if soft else y_soft + (y_hard - y_soft).detach()   # Eq. 4 or Eq. 5
         X_next = X + y_st @ V                              # Eqs. 6 and 7
         t_next = t + tau
         taus.append(tau)

@@ -113,7 +113,9 @@ def run(net, log_rates, x0, n_traj: int, t_end: float, sample_times, obs_species
     """Run the oracle. `net` is a ssa_workloads.NetworkSpec; x0 is [N] or [n_traj, N]. selector "gumbel"
     is the Gumbel-max choice (Section 3.2); "direct" the standard direct method (Section 2: u_1 a0 against
     the cumulative propensities), forward only; its margins are distances of u_1 a0 to the nearest
-    cumulative boundary, relative to a0."""
+    cumulative boundary, relative to a0. "soft" is the relaxed forward of Eq. 4 at temperature
+    `temperature` (real-valued states, obs as float64; final_x truncated to int32); with dl_dobs its
+    gradient is the exact gradient of that relaxed model."""
     lib = _load()
     reactants = np.ascontiguousarray(net.reactants, dtype=np.int32)
     sptr = np.ascontiguousarray(net.stoich_ptr, dtype=np.int32)
@@ -149,7 +151,7 @@ def run(net, log_rates, x0, n_traj: int, t_end: float, sample_times, obs_species
         tm = np.zeros((n_traj, ev_cap), dtype=np.float64)
     if n_threads is None:
         n_threads = min(os.cpu_count() or 1, max(1, n_traj // 8))
-    sel = {"gumbel": 0, "direct": 1}[selector]
+    sel = {"gumbel": 0, "direct": 1, "soft": 2}[selector]
     rc = lib.orc_run_sel(sel, ctypes.byref(cnet), n_traj, traj_offset, _ptr(x0), per_traj, float(t_end),
                      _ptr(ts), S, _ptr(obs_sp), n_obs, ctypes.c_uint64(seed), readout, max_steps,
                      _ptr(g), float(temperature), _ptr(obs), _ptr(draws), _ptr(status), _ptr(dth),

@@ -20,6 +20,9 @@
  *     (dX_ST(k+1)/dX_k)^T dL/dX_{k+1}, with the Gumbel draws held fixed.
  *   - Section 4.1: each trajectory is linearly interpolated onto a uniform time grid
  *     (LINEAR readout); the HOLD readout is the right-continuous path value X(t_s).
+ *   - Section 3.3, Eq. 4 (the soft forward, selector 2): the state is real-valued and moves by the
+ *     expected stoichiometry sum_j y~_j v_j of the soft sample, every step; its gradient is the exact
+ *     gradient of that relaxed model, which the same adjoint computes along the soft path.
  *   - Section 4.4: the BIN readout averages the piecewise-constant path exactly over each bin,
  *     through its cumulative integral C(b) = int_0^b X(t) dt: obs_s = (C(b_s) - C(b_{s-1}))/
  *     (b_s - b_{s-1}). Reading: the bins are (b_{s-1}, b_s] with b_s = t_s and b_{-1} = 0 (the
@@ -38,6 +41,10 @@
  *     X_{n+1} for samples after the last event.
  *   - a0 == 0: the state is absorbing; no further draw.
  *   - Parameters are log rates: k_j = exp(theta_{r(j)}), several reactions may share one.
+ *   - Soft forward: a relaxed state can leave the integers; a mass-action factor h_j(X) that comes out
+ *     negative there (X_i < 0, or 0 < X_i < 1 in a homodimer) is taken as 0, and so is its derivative.
+ *     No range checks apply; the draw that crosses t_end still supplies the soft target X_{k+1} for the
+ *     LINEAR readout.
  *
  * Everything is double precision; event counts are exact integers.
  */
@@ -203,8 +210,17 @@ typedef struct {
     double t_end;
     int64_t max_steps;
     uint64_t seed;
-    int32_t selector; /* 0: Gumbel-max (Section 3.2); 1: the standard direct method (Section 2) */
+    int32_t selector; /* 0: Gumbel-max (Section 3.2); 1: the standard direct method (Section 2);
+                         2: the soft forward (Eq. 4) */
+    double temperature; /* T of the soft forward */
 } orc_sim_cfg;
+
+/* h_j on the state of the path: the relaxed state of the soft forward clips a negative factor to 0 */
+static double orc_h_path(const orc_network *net, int j, const double *X, int soft)
+{
+    const double h = orc_h(net, j, X);
+    return (soft && h < 0.0) ? 0.0 : h;
+}
 
 /*
  * Simulate trajectory `traj` from x0 (Section 2 + the Gumbel-max choice of Section 3.2).
@@ -215,11 +231,12 @@ static int orc_simulate_one(const orc_sim_cfg *cfg, uint64_t traj, const int32_t
     const orc_network *net = cfg->net;
     const int N = net->n_species, M = net->n_reactions;
     double *a = (double *)malloc((size_t)(M > 0 ? M : 1) * sizeof(double));
-    if (!a) return -1;
+    double *ys = (double *)malloc((size_t)(M > 0 ? M : 1) * sizeof(double)); /* soft sample */
+    if (!a || !ys) { free(a); free(ys); return -1; }
     p->n_draws = 0;
     p->crossed = 0;
     p->status = ORC_OK;
-    if (orc_path_grow(p, N, 1)) { free(a); return -1; }
+    if (orc_path_grow(p, N, 1)) { free(a); free(ys); return -1; }
     for (int i = 0; i < N; ++i) p->X[i] = (double)x0[i];
     p->t[0] = 0.0;
     int64_t k = 0;
@@ -231,19 +248,37 @@ static int orc_simulate_one(const orc_sim_cfg *cfg, uint64_t traj, const int32_t
         int bad = 0;
         for (int j = 0; j < M; ++j) {
             double kj = exp(net->log_rates[net->rate_index[j]]);
-            a[j] = kj * orc_h(net, j, X);
+            a[j] = kj * orc_h_path(net, j, X, cfg->selector == 2);
             if (!isfinite(a[j]) || a[j] < 0.0) bad = 1;
             a0 += a[j];
         }
         if (bad) { p->status = ORC_BAD_RATE; break; }
         if (a0 == 0.0) { p->status = ORC_ABSORBED; break; }
-        if (orc_path_grow(p, N, k + 2)) { free(a); return -1; }
+        if (orc_path_grow(p, N, k + 2)) { free(a); free(ys); return -1; }
         X = p->X + (size_t)k * N;
         /* waiting time by inverse transform (Section 2) */
         double u0 = orc_uniform(cfg->seed, traj, (uint64_t)k, 0);
         double tau = -log(u0) / a0;
         int best = -1;
-        if (cfg->selector == 0) {
+        if (cfg->selector == 2) {
+            /* soft sample (Eq. 3) over the active reactions; best = its largest weight (the hard choice) */
+            double zmax = -INFINITY, s2 = -INFINITY, Z = 0.0;
+            for (int j = 0; j < M; ++j) {
+                ys[j] = -INFINITY;
+                if (!(a[j] > 0.0)) continue;
+                double u = orc_uniform(cfg->seed, traj, (uint64_t)k, 1 + j);
+                double z = (log(a[j]) - log(-log(u))) / cfg->temperature;
+                ys[j] = z;
+                if (z > zmax) { s2 = zmax; zmax = z; best = j; }
+                else if (z > s2) { s2 = z; }
+            }
+            for (int j = 0; j < M; ++j) {
+                ys[j] = ys[j] == -INFINITY ? 0.0 : exp(ys[j] - zmax);
+                Z += ys[j];
+            }
+            for (int j = 0; j < M; ++j) ys[j] /= Z;
+            p->margin[k] = (s2 == -INFINITY) ? 1.0 : -expm1((s2 - zmax) * cfg->temperature);
+        } else if (cfg->selector == 0) {
             /* Gumbel-max choice over the active reactions (Section 3.2); ties to the lowest j */
             double s1 = -INFINITY, s2 = -INFINITY;
             for (int j = 0; j < M; ++j) {
@@ -276,9 +311,23 @@ static int orc_simulate_one(const orc_sim_cfg *cfg, uint64_t traj, const int32_t
         double t_next = p->t[k] + tau;
         p->t[k + 1] = t_next;
         p->n_draws = k + 1;
+        double *Xn = p->X + (size_t)(k + 1) * N;
+        if (cfg->selector == 2) {
+            /* relaxed update (Eq. 4): X_{k+1} = X_k + sum_j y~_j v_j; also written for the crossing draw,
+               whose X_{k+1} is not a visited state but is what LINEAR interpolates towards */
+            for (int i = 0; i < N; ++i) Xn[i] = X[i];
+            for (int j = 0; j < M; ++j)
+                for (int e = net->stoich_ptr[j]; e < net->stoich_ptr[j + 1]; ++e)
+                    Xn[net->stoich_species[e]] += ys[j] * (double)net->stoich_delta[e];
+            if (t_next > cfg->t_end) { p->crossed = 1; p->status = ORC_OK; break; }
+            int bad_x = 0;
+            for (int i = 0; i < N; ++i) bad_x |= !isfinite(Xn[i]);
+            if (bad_x) { p->status = ORC_BAD_RATE; break; }
+            ++k;
+            continue;
+        }
         if (t_next > cfg->t_end) { p->crossed = 1; p->status = ORC_OK; break; }
         /* integer update (Eq. 6), with range checks */
-        double *Xn = p->X + (size_t)(k + 1) * N;
         int stop = 0;
         for (int i = 0; i < N; ++i) Xn[i] = X[i];
         for (int e = net->stoich_ptr[best]; e < net->stoich_ptr[best + 1]; ++e) {
@@ -297,6 +346,7 @@ static int orc_simulate_one(const orc_sim_cfg *cfg, uint64_t traj, const int32_t
     }
     p->n_states = k + 1;
     free(a);
+    free(ys);
     return 0;
 }
 
@@ -331,7 +381,7 @@ static double orc_cumulative(const orc_path *p, int N, int sp, double b)
 /* Readout (Section 4.1): HOLD = X(t_s); LINEAR = linear interpolation on the event grid;
    (Section 4.4) BIN = exact average over the bin (t_{s-1}, t_s], t_{-1} = 0. */
 static void orc_readout(const orc_network *net, const orc_path *p, const double *ts, int S,
-                        const int32_t *obs_species, int n_obs, int readout, double *obs /*[S][n_obs]*/)
+                        const int32_t *obs_species, int n_obs, int readout, int soft, double *obs /*[S][n_obs]*/)
 {
     const int N = net->n_species;
     if (readout == ORC_BIN) {
@@ -355,8 +405,10 @@ static void orc_readout(const orc_network *net, const orc_path *p, const double 
                 double alpha = (ts[s] - p->t[k]) / p->tau[k];
                 double dv = 0.0;
                 int j = p->j[k];
-                for (int e = net->stoich_ptr[j]; e < net->stoich_ptr[j + 1]; ++e)
-                    if (net->stoich_species[e] == sp) dv += (double)net->stoich_delta[e];
+                if (soft) dv = p->X[(size_t)(k + 1) * N + sp] - X[sp]; /* the soft step (Eq. 4) */
+                else
+                    for (int e = net->stoich_ptr[j]; e < net->stoich_ptr[j + 1]; ++e)
+                        if (net->stoich_species[e] == sp) dv += (double)net->stoich_delta[e];
                 v = X[sp] + alpha * dv;
             }
             obs[(size_t)s * n_obs + o] = v;
@@ -374,6 +426,7 @@ static int orc_adjoint_one(const orc_sim_cfg *cfg, uint64_t traj, const orc_path
 {
     const orc_network *net = cfg->net;
     const int N = net->n_species, M = net->n_reactions;
+    const int soft = cfg->selector == 2;
     double *lam = (double *)calloc((size_t)N, sizeof(double));     /* dL/dX_{k+1} */
     double *lam_new = (double *)calloc((size_t)N, sizeof(double));
     double *dXdir = (double *)calloc((size_t)N, sizeof(double));
@@ -421,10 +474,13 @@ static int orc_adjoint_one(const orc_sim_cfg *cfg, uint64_t traj, const orc_path
             if (readout == ORC_LINEAR && draw) {
                 /* obs = X_k + alpha (X_{k+1} - X_k), alpha = (t_s - t_k)/tau_k */
                 double alpha = (ts[s] - p->t[k]) / p->tau[k];
-                double c = 0.0; /* gbar . (X_{k+1} - X_k) = gbar . v_{j_k} */
+                double c = 0.0; /* gbar . (X_{k+1} - X_k): gbar . v_{j_k}, or the soft step */
                 int j = p->j[k];
-                for (int e = net->stoich_ptr[j]; e < net->stoich_ptr[j + 1]; ++e)
-                    c += gbar[net->stoich_species[e]] * (double)net->stoich_delta[e];
+                if (soft)
+                    for (int i = 0; i < N; ++i) c += gbar[i] * (p->X[(size_t)(k + 1) * N + i] - X[i]);
+                else
+                    for (int e = net->stoich_ptr[j]; e < net->stoich_ptr[j + 1]; ++e)
+                        c += gbar[net->stoich_species[e]] * (double)net->stoich_delta[e];
                 for (int i = 0; i < N; ++i) {
                     lam[i] += alpha * gbar[i];          /* into X_{k+1} */
                     dXdir[i] += (1.0 - alpha) * gbar[i];
@@ -440,7 +496,7 @@ static int orc_adjoint_one(const orc_sim_cfg *cfg, uint64_t traj, const orc_path
             /* recompute the step's propensities and Gumbel perturbations (same noise) */
             double a0 = 0.0;
             for (int j = 0; j < M; ++j) {
-                a[j] = exp(net->log_rates[net->rate_index[j]]) * orc_h(net, j, X);
+                a[j] = exp(net->log_rates[net->rate_index[j]]) * orc_h_path(net, j, X, soft);
                 a0 += a[j];
             }
             double tau = p->tau[k];
@@ -478,7 +534,7 @@ static int orc_adjoint_one(const orc_sim_cfg *cfg, uint64_t traj, const orc_path
                     orc_add_dh(net, j, X, choice / h, lam_new);
                 }
                 double kj = exp(net->log_rates[net->rate_index[j]]);
-                orc_add_dh(net, j, X, dLda0 * kj, lam_new);
+                if (!soft || orc_h(net, j, X) >= 0.0) orc_add_dh(net, j, X, dLda0 * kj, lam_new);
             }
         }
         mu = mu + dt_dir; /* t_{k+1} = t_k + tau_k: mu becomes dL/dt_k */
@@ -529,7 +585,7 @@ static void *orc_worker(void *arg)
     orc_job *job = (orc_job *)arg;
     const orc_network *net = job->net;
     const int N = net->n_species, P = net->n_params;
-    orc_sim_cfg cfg = {net, job->t_end, job->max_steps, job->seed, job->selector};
+    orc_sim_cfg cfg = {net, job->t_end, job->max_steps, job->seed, job->selector, job->temperature};
     orc_path path;
     memset(&path, 0, sizeof(path));
     double *dth = (double *)calloc((size_t)(P > 0 ? P : 1), sizeof(double));
@@ -543,7 +599,7 @@ static void *orc_worker(void *arg)
         uint64_t traj = (uint64_t)(job->traj_offset + i);
         const int32_t *x0 = job->x0 + (job->x0_per_traj ? (size_t)i * N : 0);
         if (orc_simulate_one(&cfg, traj, x0, &path)) { job->error = 1; break; }
-        orc_readout(net, &path, job->ts, job->S, job->obs_species, job->n_obs, job->readout, obs);
+        orc_readout(net, &path, job->ts, job->S, job->obs_species, job->n_obs, job->readout, job->selector == 2, obs);
         if (job->obs_out)
             memcpy(job->obs_out + (size_t)i * job->S * job->n_obs, obs, (size_t)job->S * job->n_obs * sizeof(double));
         if (job->draws_out) job->draws_out[i] = path.n_draws;
@@ -589,8 +645,9 @@ int orc_run_sel(int32_t selector, const orc_network *net, int64_t n_traj, int64_
                 int32_t *final_x_out, int32_t n_threads)
 {
     if (!net || n_traj < 0 || S < 0 || n_obs < 0 || max_steps < 0) return -1;
-    if (selector != 0 && selector != 1) return -1;
+    if (selector != 0 && selector != 1 && selector != 2) return -1;
     if (selector == 1 && dL_dobs) return -1;  /* the straight-through gradient is of the Gumbel-max choice */
+    if (selector == 2 && !(temperature > 0.0)) return -1; /* the soft forward needs its T */
     if (net->n_species <= 0 || net->n_reactions < 0) return -1;
     if (readout != ORC_HOLD && readout != ORC_LINEAR && readout != ORC_BIN) return -1;
     for (int s = 0; s < S; ++s) {
