@@ -456,10 +456,13 @@ def oscillator_extra(ssa, dev, n_fwd: int = 1 << 20, n_adj: int = 1 << 16, t_end
     net = ssa.Network(wl.net)
     th = torch.tensor(wl.log_rates.astype(np.float32), device=dev)
     stream = torch.cuda.current_stream()
-    out = {"workload": f"Vilar oscillator, 9 species, 16 reactions, t_end={t_end}, 10 LINEAR samples of R"}
+    out = {"workload": f"Vilar oscillator, 9 species, 16 reactions, t_end={t_end}, 10 LINEAR samples of R",
+           "selectors": "forward: Gumbel-max (the method); forward_direct: the plain direct method; forward_soft: "
+                        "the relaxed forward of Eq. 4 at T = 0.5 (its own, different, step count)"}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for mode, n in (("forward", n_fwd), ("forward_adjoint", n_adj)):
-        rec = mode != "forward"
+    for mode, n in (("forward", n_fwd), ("forward_direct", n_fwd), ("forward_soft", n_fwd), ("forward_adjoint", n_adj)):
+        rec = mode == "forward_adjoint"
+        sel = {"forward_direct": "direct", "forward_soft": "soft"}.get(mode, "gumbel")
         ms, steps = 0.0, 0
         for r in range(reps + 1):
             if r == 1:
@@ -467,7 +470,7 @@ def oscillator_extra(ssa, dev, n_fwd: int = 1 << 20, n_adj: int = 1 << 16, t_end
             if r >= 1:
                 ev[0].record(stream)
             fw = ssa.forward(net, th, n, wl.x0, t_end, wl.sample_times, wl.obs_species, 50 + r, readout="linear",
-                             record=rec, max_steps=1 << 16)
+                             record=rec, max_steps=1 << 16, selector=sel, temperature=0.5 if sel == "soft" else None)
             if rec:
                 dl = torch.full((len(wl.sample_times), 1), 1.0 / n, device=dev)
                 ssa.backward(fw, dl, 0.1)

@@ -80,15 +80,24 @@ typedef struct ssa_fwd_opts {
                                  (NVRTC, at most 24 species, 24 reactions, 96 stoichiometric
                                  entries; the same results bit for bit) when it qualifies;
                                  1: always the generic kernels                                  */
-    int32_t selector;         /* SSA_SELECT_GUMBEL (the method) or SSA_SELECT_DIRECT (the plain
-                                 direct method, forward only: record must be 0; runs on the
-                                 network-specialised kernels)                                   */
-    int32_t reserved;         /* must be 0                                                       */
+    int32_t selector;         /* SSA_SELECT_GUMBEL (the method), SSA_SELECT_DIRECT (the plain
+                                 direct method, forward only: record must be 0) or
+                                 SSA_SELECT_SOFT (the relaxed forward of Eq. 4); the last two run
+                                 on the network-specialised kernels only                        */
+    float temperature;        /* SSA_SELECT_SOFT: T > 0 of its soft sample; else must be 0       */
 } ssa_fwd_opts;
 
 #define SSA_SELECT_GUMBEL 0 /* j* = argmax_j a_j / E_{1+j}, the Gumbel-max choice (Section 3.2)    */
 #define SSA_SELECT_DIRECT 1 /* the first j with a_1 + ... + a_j > u_1 a0 in reaction order: the
                                standard direct method (Section 2), the plain-SSA comparator       */
+/* The soft forward (Section 3.3, Eq. 4): the state is real-valued and moves every step by the
+ * expected stoichiometry sum_j y~_j v_j of the soft sample y~ = softmax((log a + G)/T) of the same
+ * Gumbel noise; a mass-action factor that comes out negative on a relaxed state is taken as 0. The
+ * clock, the samples and the three readouts are the forward's; observables are float for every
+ * readout. Recorded, it checkpoints the float state every 8 steps (ckpt_interval is ignored), and
+ * ssa_backward then gives the exact gradient of this relaxed model (it re-runs each 8-step segment,
+ * so its temperature argument must equal opts.temperature). No event log is kept. */
+#define SSA_SELECT_SOFT 2
 
 /*
  * ssa_create_network -- a mass-action reaction network (Section 2).
@@ -171,7 +180,7 @@ ssa_status ssa_forward_replay(const ssa_network *net, const float *log_rates, in
  *                  out [n_samples][n_obs]. dl_traj_stride = n_samples * n_obs for a full
  *                  [n_traj][n_samples][n_obs] array, or 0 when every trajectory has the same
  *                  upstream gradient (a loss on ensemble means, Section 3.5).
- *   temperature    T > 0 (Eq. 3).
+ *   temperature    T > 0 (Eq. 3); for a soft forward (SSA_SELECT_SOFT) the forward's T.
  *   dl_dlog_rates  device float [P], overwritten with dL/dtheta summed over trajectories
  *                  (deterministic reduction order).
  * Trajectories whose status is not OK/ABSORBED/STEP_CAP contribute nothing. Callable any number

@@ -16,6 +16,9 @@ SSA_OK = 0
 SSA_READOUT_HOLD = 0
 SSA_READOUT_LINEAR = 1
 SSA_READOUT_BIN = 2
+SSA_SELECT_GUMBEL = 0
+SSA_SELECT_DIRECT = 1
+SSA_SELECT_SOFT = 2
 SSA_BIN_MAX_OBS = 4
 TRAJ_CODES = ("OK", "ABSORBED", "STEP_CAP", "NEG_COUNT", "OVERFLOW", "BAD_RATE", "BAD_INPUT", "REPLAY_MISMATCH")
 SSA_TRAJ_N_CODES = len(TRAJ_CODES)
@@ -47,7 +50,7 @@ class FwdOpts(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("no_specialize", ctypes.c_int32),
         ("selector", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("temperature", ctypes.c_float),
     ]
 
 

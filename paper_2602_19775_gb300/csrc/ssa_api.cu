@@ -40,6 +40,7 @@ cudaError_t launch_exp_variates(const uint32_t *words, int64_t n, float *out, cu
 struct JitKernels;
 bool jit_eligible(const ssa_network *net);
 const JitKernels *jit_kernels(const ssa_network *net, std::string &why);
+const JitKernels *jit_soft_kernels(const ssa_network *net, std::string &why);
 cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int readout, bool record, int selector,
                                int block, cudaStream_t st);
 cudaError_t jit_launch_backward(const JitKernels *k, const AdjParams &p, int readout, int block, int64_t grid,
@@ -88,7 +89,11 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 
 
-int effective_K(const ssa_fwd_opts *o) { return o->ckpt_interval > 0 ? o->ckpt_interval : 64; }
+int effective_K(const ssa_fwd_opts *o)
+{
+    if (o->selector == SSA_SELECT_SOFT) return kSoftK;  // float checkpoints; the adjoint re-runs each segment
+    return o->ckpt_interval > 0 ? o->ckpt_interval : 64;
+}
 
 WsLayout layout(const ssa_network *net, int64_t n, int32_t S, const ssa_fwd_opts *o)
 {
@@ -135,9 +140,14 @@ bool opts_valid(const ssa_fwd_opts *o)
     if (o->block_threads != 0 && (o->block_threads % 32 != 0 || o->block_threads < 32 || o->block_threads > 256))
         return false;
     if (o->no_specialize != 0 && o->no_specialize != 1) return false;
-    if (o->selector != SSA_SELECT_GUMBEL && o->selector != SSA_SELECT_DIRECT) return false;
+    if (o->selector != SSA_SELECT_GUMBEL && o->selector != SSA_SELECT_DIRECT && o->selector != SSA_SELECT_SOFT)
+        return false;
     if (o->selector == SSA_SELECT_DIRECT && o->record) return false;  // the gradient is of the Gumbel-max choice
-    if (o->reserved != 0) return false;
+    if (o->selector == SSA_SELECT_SOFT) {
+        if (!(o->temperature > 0.0f) || !(o->temperature < 3.0e38f)) return false;
+    } else if (o->temperature != 0.0f) {
+        return false;
+    }
     return true;
 }
 
@@ -336,7 +346,14 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     int variant = ev_in ? 1 : pick_variant(net, opts);  // replay is a thread-per-trajectory test hook
     // the thread variant runs as network-specialised kernels when the network qualifies (variant 2)
     const JitKernels *jit = nullptr;
-    if (variant == 1 && !ev_in && !opts->no_specialize && jit_eligible(net)) {
+    if (opts->selector == SSA_SELECT_SOFT) {  // the soft forward exists as specialised kernels only
+        if (variant != 1 || ev_in || opts->no_specialize)
+            return fail(SSA_ERR_UNSUPPORTED, "the soft forward runs on the network-specialised thread kernels only");
+        std::string why;
+        jit = jit_soft_kernels(net, why);
+        if (!jit) return fail(SSA_ERR_UNSUPPORTED, "soft forward unavailable: %s", why.c_str());
+        variant = 2;
+    } else if (variant == 1 && !ev_in && !opts->no_specialize && jit_eligible(net)) {
         std::string why;
         jit = jit_kernels(net, why);
         if (jit) variant = 2;
@@ -394,6 +411,7 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     p.obs_sp = reinterpret_cast<const int *>(ws + L.obs_sp);
     p.n_obs = n_obs;
     p.max_steps = opts->max_steps;
+    p.invT = opts->selector == SSA_SELECT_SOFT ? 1.0f / opts->temperature : 0.0f;
     p.obs_out = obs_out;
     p.draws = reinterpret_cast<int *>(ws + L.draws);
     p.status = reinterpret_cast<int *>(ws + L.status);
@@ -482,9 +500,12 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     int block = 0;
     int64_t grid = 0;
     const JitKernels *jit = nullptr;
+    const bool soft = run->opts.selector == SSA_SELECT_SOFT;
+    if (soft && temperature != run->opts.temperature)
+        return fail(SSA_ERR_INVALID_ARG, "the gradient of a soft forward is taken at the forward's temperature");
     if (run->variant == 2) {
         std::string why;
-        jit = jit_kernels(net, why);
+        jit = soft ? jit_soft_kernels(net, why) : jit_kernels(net, why);
         if (!jit) return fail(SSA_ERR_STATE, "specialised kernels unavailable: %s", why.c_str());
         block = kJitBlock;
         grid = (run->n_traj + block - 1) / block;
@@ -565,6 +586,7 @@ extern "C" ssa_status ssa_run_events(const ssa_run *run, int32_t *events_out, in
 {
     if (!run || !events_out || stride < 1) return fail(SSA_ERR_INVALID_ARG, "bad arguments");
     if (!run->opts.record) return fail(SSA_ERR_STATE, "the forward was not recorded");
+    if (run->opts.selector == SSA_SELECT_SOFT) return fail(SSA_ERR_STATE, "a soft forward keeps no event log");
     unsigned char *ws = run->ws;
     CUDA_TRY(launch_unpack_events(reinterpret_cast<const uint4 *>(ws + run->L.ev),
                                   reinterpret_cast<const int *>(ws + run->L.draws), run->n_traj, stride, events_out,

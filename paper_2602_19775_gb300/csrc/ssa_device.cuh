@@ -70,6 +70,12 @@ __device__ __forceinline__ float h_hetero(int x1, int x2)
     return __ll2float_rn((long long)x1 * x2);
 }
 
+// Mass-action factors of the real-valued state of the soft forward (Eq. 4); a relaxed state can leave the
+// integers, and a factor that comes out negative there is taken as 0 (a propensity cannot be negative).
+__device__ __forceinline__ float hs_first(float x1) { return fmaxf(x1, 0.0f); }
+__device__ __forceinline__ float hs_homodimer(float x1) { return fmaxf(__fmul_rn(x1, x1 - 1.0f) * 0.5f, 0.0f); }
+__device__ __forceinline__ float hs_hetero(float x1, float x2) { return fmaxf(__fmul_rn(x1, x2), 0.0f); }
+
 __device__ __forceinline__ float mass_action_h(const int4 rx, const int *X, int stride)
 {
     if (rx.x < 0) return 1.0f;
@@ -196,13 +202,17 @@ __device__ __forceinline__ float sadj_hetero(float xs, float xo, float a, float 
 // ------------------------------------------------------------------------------------------
 constexpr int kBinMaxObs = SSA_BIN_MAX_OBS;
 
+// an observed count as binary32: integer states (exact below 2^23) and the real states of the soft forward
+__device__ __forceinline__ float obs_f(int x) { return int2f(x); }
+__device__ __forceinline__ float obs_f(float x) { return x; }
+
 // acc[c] += X_c len for the observables (xobs(c) = count of observable c)
 template <class XF>
 __device__ __forceinline__ void bin_accumulate(float (&acc)[kBinMaxObs], const XF &xobs, int n_obs, float len)
 {
 #pragma unroll
     for (int c = 0; c < kBinMaxObs; ++c)
-        if (c < n_obs) acc[c] = __fmaf_rn(int2f(xobs(c)), len, acc[c]);
+        if (c < n_obs) acc[c] = __fmaf_rn(obs_f(xobs(c)), len, acc[c]);
 }
 
 // Close bin s at its right edge ts[s] >= t_k and write its averages to o; first: the bin began before
@@ -216,7 +226,7 @@ __device__ __forceinline__ float bin_close(float (&acc)[kBinMaxObs], const XF &x
 #pragma unroll
     for (int c = 0; c < kBinMaxObs; ++c) {
         if (c < n_obs) {
-            const float x = int2f(xobs(c));
+            const float x = obs_f(xobs(c));
             o[c] = first ? __fdiv_rn(__fmaf_rn(x, d, acc[c]), D) : x;
             acc[c] = 0.0f;
         }
@@ -280,6 +290,9 @@ __device__ __forceinline__ void bin_state_terms(const AF &addx, const BF &brk, c
         if (c < n_obs) addx(c, gk[c] * d);
 }
 
+// Soft forward: the float state is checkpointed every kSoftK steps; the adjoint re-runs each segment.
+constexpr int kSoftK = 8;
+
 // Error bits written to the workspace flag word by kernels.
 constexpr int kErrStageTimeout = 1;
 constexpr int kErrBadSamples = 2;
@@ -305,6 +318,7 @@ struct FwdParams {
     const int *obs_sp;
     int n_obs;
     int64_t max_steps;
+    float invT;       // soft forward (Eq. 4): 1/T of its soft sample
     void *obs_out;
     int *draws, *status;
     const int *flag;  // workspace error flags (bad sample times -> every trajectory BAD_INPUT)
@@ -378,7 +392,7 @@ __device__ __forceinline__ void bin_tail(const FwdParams &p, int64_t i, int s, d
     if (RECORD) p.brk_tail[i] = s < S ? s : S;
     float xv[kBinMaxObs];
 #pragma unroll
-    for (int c = 0; c < kBinMaxObs; ++c) xv[c] = (c < no && !bad_obs) ? int2f(xobs(c)) : 0.0f;
+    for (int c = 0; c < kBinMaxObs; ++c) xv[c] = (c < no && !bad_obs) ? obs_f(xobs(c)) : 0.0f;
     const int lane = (int)(threadIdx.x & 31);
     const int64_t base = i - lane;
     const unsigned mask = base + 32 <= n ? 0xffffffffu : ((1u << (unsigned)(n - base)) - 1u);

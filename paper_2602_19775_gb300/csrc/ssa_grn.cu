@@ -718,7 +718,7 @@ extern "C" ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, cons
     if (run_out) *run_out = nullptr;
     if (!g || !opts) return set_error(SSA_ERR_INVALID_ARG, "NULL network or options");
     if (opts->readout != SSA_READOUT_HOLD) return set_error(SSA_ERR_UNSUPPORTED, "the GRN reads out with HOLD only");
-    if (opts->selector != SSA_SELECT_GUMBEL || opts->reserved != 0)
+    if (opts->selector != SSA_SELECT_GUMBEL || opts->temperature != 0.0f)
         return set_error(SSA_ERR_UNSUPPORTED, "the GRN runs the Gumbel-max selector");
     if (opts->max_steps < 1 || opts->max_steps > 0x7fffffffLL || (opts->ckpt_interval % 8) || opts->ckpt_interval < 0)
         return set_error(SSA_ERR_INVALID_ARG, "invalid options");

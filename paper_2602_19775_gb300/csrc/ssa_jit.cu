@@ -28,8 +28,8 @@ constexpr int kJitMaxReactions = 24;
 constexpr int kJitMaxNnz = 96;
 
 struct JitKernels {
-    cudaKernel_t fwd[3][2];     // [readout][record], Gumbel-max choice
-    cudaKernel_t fwd_direct[3]; // [readout], direct method, forward only
+    cudaKernel_t fwd[3][2];     // [readout][record], Gumbel-max choice (soft set: the soft forward)
+    cudaKernel_t fwd_direct[3]; // [readout], direct method, forward only (not in the soft set)
     cudaKernel_t adj[3];        // [readout]
 };
 
@@ -133,6 +133,46 @@ std::string jit_source(const ssa_network *net)
             emit(s, "        lam[%d] += sadj_hetero(x2, x1, a[%d], psi[%d], ctau[%d]);\n    }\n", r.y, j, j, j);
         }
     }
+    s += "}\n";
+    // soft forward (Eq. 4): propensities of the real-valued state (negative factors clipped to 0), the
+    // relaxed update dX = sum_j y_j v_j (entries in table order), and the state adjoint with the
+    // waiting-time derivative of a clipped factor removed
+    s += "__device__ __forceinline__ void jit_props_soft(const float (&X)[JN], const float (&k)[JM], float (&a)[JM], "
+         "float (&h)[JM])\n{\n";
+    for (int j = 0; j < M; ++j) {
+        const int4 r = net->h_rx[j];
+        if (r.x < 0) emit(s, "    h[%d] = 1.0f;\n", j);
+        else if (r.y < 0) emit(s, "    h[%d] = hs_first(X[%d]);\n", j, r.x);
+        else if (r.y == r.x) emit(s, "    h[%d] = hs_homodimer(X[%d]);\n", j, r.x);
+        else emit(s, "    h[%d] = hs_hetero(X[%d], X[%d]);\n", j, r.x, r.y);
+        emit(s, "    a[%d] = __fmul_rn(k[%d], h[%d]);\n", j, j, j);
+    }
+    s += "}\n";
+    s += "__device__ __forceinline__ void jit_dx_soft(const float (&y)[JM], float (&dX)[JN])\n{\n";
+    s += "#pragma unroll\n    for (int q = 0; q < JN; ++q) dX[q] = 0.0f;\n";
+    for (int j = 0; j < M; ++j)
+        for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e)
+            emit(s, "    dX[%d] = __fmaf_rn(y[%d], %d.0f, dX[%d]);\n", st_species(net->h_st[e]), j, st_delta(net->h_st[e]),
+                 st_species(net->h_st[e]));
+    s += "}\n";
+    s += "__device__ __forceinline__ void jit_state_adj_soft(const float (&X)[JN], const float (&a)[JM], "
+         "const float (&h)[JM], const float (&psi)[JM], const float (&ctau)[JM], float (&lam)[JN])\n{\n";
+    for (int j = 0; j < M; ++j) {
+        const int4 r = net->h_rx[j];
+        if (r.x < 0) continue;
+        if (r.y < 0) {
+            emit(s, "    lam[%d] += sadj_first(X[%d], a[%d], psi[%d], X[%d] < 0.0f ? 0.0f : ctau[%d]);\n", r.x, r.x, j, j,
+                 r.x, j);
+        } else if (r.y == r.x) {
+            emit(s, "    lam[%d] += sadj_homodimer(X[%d], a[%d], h[%d], psi[%d], __fmul_rn(X[%d], X[%d] - 1.0f) < 0.0f ? "
+                    "0.0f : ctau[%d]);\n", r.x, r.x, j, j, j, r.x, r.x, j);
+        } else {
+            emit(s, "    {\n        const float x1 = X[%d], x2 = X[%d];\n", r.x, r.y);
+            emit(s, "        const float c = __fmul_rn(x1, x2) < 0.0f ? 0.0f : ctau[%d];\n", j);
+            emit(s, "        lam[%d] += sadj_hetero(x1, x2, a[%d], psi[%d], c);\n", r.x, j, j);
+            emit(s, "        lam[%d] += sadj_hetero(x2, x1, a[%d], psi[%d], c);\n    }\n", r.y, j, j);
+        }
+    }
     s += "}\n}  // namespace ssa\n#include \"ssa_jit_body.cuh\"\n";
     return s;
 }
@@ -180,15 +220,17 @@ bool jit_eligible(const ssa_network *net)
     return net->N <= kJitMaxSpecies && net->M <= kJitMaxReactions && net->nnz <= kJitMaxNnz;
 }
 
-// Kernels of `net`, compiling and loading them on first use. Returns nullptr (with the reason in `why`)
-// if the network is not eligible or compilation failed.
-const JitKernels *jit_kernels(const ssa_network *net, std::string &why)
+namespace {
+// Kernels of `net` (soft: the soft-forward program of the same text), compiling and loading them on
+// first use. Returns nullptr (with the reason in `why`) if the network is not eligible or compilation
+// failed.
+const JitKernels *jit_load(const ssa_network *net, bool soft, std::string &why)
 {
     if (!jit_eligible(net)) {
         why = "network above the specialisation limits (24 species, 24 reactions, 96 stoichiometric entries)";
         return nullptr;
     }
-    const std::string src = jit_source(net);
+    const std::string src = (soft ? std::string("#define SSA_JIT_SOFT 1\n") : std::string()) + jit_source(net);
     std::lock_guard<std::mutex> lock(g_jit_mu);
     auto f = g_jit_failed.find(src);
     if (f != g_jit_failed.end()) {
@@ -210,16 +252,17 @@ const JitKernels *jit_kernels(const ssa_network *net, std::string &why)
         return nullptr;
     }
     JitKernels k{};
-    const char *fwd_names[3][2] = {{"ssa_jit_fwd_hold", "ssa_jit_fwd_hold_rec"},
-                                   {"ssa_jit_fwd_linear", "ssa_jit_fwd_linear_rec"},
-                                   {"ssa_jit_fwd_bin", "ssa_jit_fwd_bin_rec"}};
-    const char *adj_names[3] = {"ssa_jit_adj_hold", "ssa_jit_adj_linear", "ssa_jit_adj_bin"};
-    const char *direct_names[3] = {"ssa_jit_fwd_hold_direct", "ssa_jit_fwd_linear_direct", "ssa_jit_fwd_bin_direct"};
+    const char *rname[3] = {"hold", "linear", "bin"};
     bool ok = true;
     for (int r = 0; r < 3; ++r) {
-        for (int rec = 0; rec < 2; ++rec) ok &= cudaLibraryGetKernel(&k.fwd[r][rec], lib, fwd_names[r][rec]) == cudaSuccess;
-        ok &= cudaLibraryGetKernel(&k.adj[r], lib, adj_names[r]) == cudaSuccess;
-        ok &= cudaLibraryGetKernel(&k.fwd_direct[r], lib, direct_names[r]) == cudaSuccess;
+        const std::string base = std::string(rname[r]) + (soft ? "_soft" : "");
+        for (int rec = 0; rec < 2; ++rec) {
+            const std::string nm = "ssa_jit_fwd_" + base + (rec ? "_rec" : "");
+            ok &= cudaLibraryGetKernel(&k.fwd[r][rec], lib, nm.c_str()) == cudaSuccess;
+        }
+        ok &= cudaLibraryGetKernel(&k.adj[r], lib, ("ssa_jit_adj_" + base).c_str()) == cudaSuccess;
+        if (!soft)
+            ok &= cudaLibraryGetKernel(&k.fwd_direct[r], lib, ("ssa_jit_fwd_" + base + "_direct").c_str()) == cudaSuccess;
     }
     if (!ok) {
         why = "a specialised kernel is missing from the library";
@@ -229,6 +272,10 @@ const JitKernels *jit_kernels(const ssa_network *net, std::string &why)
     }
     return &(g_jit_cache[src] = k);
 }
+}  // namespace
+
+const JitKernels *jit_kernels(const ssa_network *net, std::string &why) { return jit_load(net, false, why); }
+const JitKernels *jit_soft_kernels(const ssa_network *net, std::string &why) { return jit_load(net, true, why); }
 
 cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int readout, bool record, int selector,
                                int block, cudaStream_t st)

@@ -13,7 +13,8 @@
 // state adjoint then live in registers and every table lookup disappears. The arithmetic is the
 // generic thread kernels' (same helpers from ssa_device.cuh, same order), so a specialised run
 // reproduces the generic run's trajectories bit for bit. A third forward runs the plain direct method
-// (Section 2) for comparison.
+// (Section 2) for comparison. Compiled with SSA_JIT_SOFT defined, the same text yields the soft-forward
+// kernels (Eq. 4) and their adjoint instead.
 
 namespace ssa {
 
@@ -470,7 +471,301 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
     if (mism) atomicAdd(p.mismatch, mism);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Soft forward (Section 3.3, Eq. 4): the state is real and moves every step by the expected
+// stoichiometry sum_j y~_j v_j of the soft sample y~ = softmax((log a + G)/T), drawn from the same
+// variates as the Gumbel-max forward. Clock, samples and readouts are the forward's; there are no range
+// checks. Its gradient is the exact gradient of this relaxed model: the straight-through adjoint's
+// arithmetic along the soft path, whose states the adjoint regenerates segment by segment from float
+// checkpoints taken every kSoftK steps.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float jit_fsel(const float (&X)[JN], int sp)
+{
+    float v = 0.0f;
+#pragma unroll
+    for (int s = 0; s < JN; ++s) v = (s == sp) ? X[s] : v;
+    return v;
+}
+
+// Propensities, soft sample and relaxed update of the state X with the step variates E (E[0] for the
+// waiting time, E[1 + j] for reaction j): keys l_j = log2 a_j - log2 E_{1+j} = (ln a_j + G_j)/ln 2, so
+// y~_j = exp2((l_j - l_max)/T) / Z. Returns a0.
+__device__ __forceinline__ float jit_soft_step(const float (&X)[JN], const float (&kr)[JM], const float (&E)[JM + 1],
+                                               float invT, float (&a)[JM], float (&h)[JM], float (&y)[JM],
+                                               float (&dX)[JN])
+{
+    jit_props_soft(X, kr, a, h);
+    float a0 = 0.0f, lmax = -CUDART_INF_F;
+#pragma unroll
+    for (int j = 0; j < JM; ++j) {
+        a0 = __fadd_rn(a0, a[j]);
+        y[j] = a[j] > 0.0f ? log2f(a[j]) - log2f(E[j + 1]) : -CUDART_INF_F;
+        lmax = fmaxf(lmax, y[j]);
+    }
+    float Z = 0.0f;
+#pragma unroll
+    for (int j = 0; j < JM; ++j) {
+        y[j] = y[j] == -CUDART_INF_F ? 0.0f : exp2f((y[j] - lmax) * invT);
+        Z += y[j];
+    }
+    const float invZ = __fdividef(1.0f, Z);
+#pragma unroll
+    for (int j = 0; j < JM; ++j) y[j] *= invZ;
+    jit_dx_soft(y, dX);
+    return a0;
+}
+
+template <int READOUT, bool RECORD>
+__device__ __forceinline__ void jit_fwd_soft(const FwdParams &p)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_traj) return;
+    const int64_t n = p.n_traj;
+    float kr[JM];
+#pragma unroll
+    for (int j = 0; j < JM; ++j) kr[j] = p.k_rates[j];
+    const int *x0 = p.x0 + (p.x0_per_traj ? i * JN : 0);
+    const bool bad_obs = (*p.flag & kErrBadObs) != 0;
+    bool bad_input = (*p.flag & (kErrBadSamples | kErrBadObs)) != 0;
+    float X[JN];
+#pragma unroll
+    for (int s = 0; s < JN; ++s) {
+        const int v = x0[s];
+        X[s] = int2f(v);
+        bad_input |= v < 0;
+    }
+    const uint64_t gid = p.traj_offset + (uint64_t)i;
+    const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32);
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    double t = 0.0;
+    int s = 0;
+    double thr = p.S > 0 ? p.ts[0] : p.t_end;
+    int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
+    int k = 0, draws = 0;
+    int ck_left = p.K, ck_row = 0;
+    constexpr int NQ = JM + 1;
+    float E[NQ], En[NQ];
+    step_noise<NQ>(E, 0u, c2, c3, key0, key1);
+    float bacc[kBinMaxObs];
+    int osp[kBinMaxObs];
+    jit_bin_init(p, bad_obs, bacc, osp);
+    auto xobs = [&](int c) { return jit_fsel(X, osp[c]); };
+    float *obs = static_cast<float *>(p.obs_out);
+    float *ckf = reinterpret_cast<float *>(p.ckpt);
+
+    while (!bad_input) {
+        if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
+        step_noise<NQ>(En, (uint32_t)(k + 1), c2, c3, key0, key1);
+        float a[JM], h[JM], y[JM], dX[JN];
+        const float a0 = jit_soft_step(X, kr, E, p.invT, a, h, y, dX);
+        if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
+        if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
+        const float tau = __fdividef(E[0], a0);
+        const double t_next = t + f2d_pos(tau);
+        const bool slow = gt_nonneg(t_next, thr);
+        const bool cross = slow && gt_nonneg(t_next, p.t_end);
+        bool finite = true;
+#pragma unroll
+        for (int q = 0; q < JN; ++q) finite &= fabsf(__fadd_rn(X[q], dX[q])) < CUDART_INF_F;
+        draws = k + 1;
+        if (!cross && !finite) { status = SSA_TRAJ_BAD_RATE; break; }
+        if (slow) {
+            const int s_first = s;
+            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
+                float *o = obs + ((int64_t)i * p.S + s) * p.n_obs;
+                if (READOUT == SSA_READOUT_HOLD) {
+                    for (int c = 0; c < p.n_obs; ++c) o[c] = jit_fsel(X, p.obs_sp[c]);
+                } else if (READOUT == SSA_READOUT_BIN) {
+                    const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_first, o);
+                    if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
+                } else {
+                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
+                    for (int c = 0; c < p.n_obs; ++c) {
+                        const int sp = p.obs_sp[c];
+                        o[c] = __fmaf_rn(alpha, jit_fsel(dX, sp), jit_fsel(X, sp));
+                    }
+                    if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
+                }
+                if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
+                ++s;
+            }
+            if (READOUT == SSA_READOUT_BIN && !cross && s > s_first)
+                bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
+            thr = s < p.S ? p.ts[s] : p.t_end;
+            if (cross) break;
+        } else if (READOUT == SSA_READOUT_BIN) {
+            bin_accumulate(bacc, xobs, p.n_obs, tau);
+        }
+#pragma unroll
+        for (int q = 0; q < JN; ++q) X[q] = __fadd_rn(X[q], dX[q]);
+        t = t_next;
+        ++k;
+        if (RECORD && --ck_left == 0) {
+            ck_left = p.K;
+            ++ck_row;
+#pragma unroll
+            for (int q = 0; q < JN; ++q) ckf[((int64_t)ck_row * JN + q) * n + i] = X[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) E[q] = En[q];
+    }
+    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs);
+    for (; READOUT != SSA_READOUT_BIN && s < p.S; ++s) {
+        float *o = obs + ((int64_t)i * p.S + s) * p.n_obs;
+        for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : jit_fsel(X, p.obs_sp[c]);
+        if (RECORD && READOUT == SSA_READOUT_LINEAR) p.brk_a[(int64_t)s * n + i] = -1.0f;
+        if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
+    }
+    p.draws[i] = draws;
+    p.status[i] = status;
+    if (RECORD) {
+#pragma unroll
+        for (int q = 0; q < JN; ++q) ckf[(int64_t)q * n + i] = int2f(x0[q]);  // checkpoint 0 = X_0
+    }
+}
+
+// Exact gradient of the soft forward, one trajectory; per-reaction adjoints into dAr.
 template <int READOUT>
+__device__ __forceinline__ void jit_adj_soft_traj(const AdjParams &p, const float (&kr)[JM], const int64_t i,
+                                                  const int st, float (&dAr)[JM])
+{
+    const int64_t n = p.n_traj;
+    const int d = p.draws[i];
+    const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;  // index of the last visited state
+    const bool draw_last = st == SSA_TRAJ_OK;
+    const int K = p.K;  // == kSoftK
+    const uint64_t gid = p.traj_offset + (uint64_t)i;
+    const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32);
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    const float invT = p.invT;
+    const float *gl = p.dl_dobs + i * p.dl_stride;
+    const float *ckf = reinterpret_cast<const float *>(p.ckpt);
+    constexpr int NQ = JM + 1;
+    float lam[JN];
+#pragma unroll
+    for (int q = 0; q < JN; ++q) lam[q] = 0.0f;
+
+    int s_hi = READOUT == SSA_READOUT_BIN ? min(p.brk_tail[i], p.S - 1) : p.S - 1;
+    int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    float mu = 0.0f;
+    int mism = 0;
+    constexpr bool kBin = READOUT == SSA_READOUT_BIN;
+    float gq[kBinMaxObs], gk[kBinMaxObs];
+    int osp[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) osp[c] = (kBin && c < p.n_obs) ? p.obs_sp[c] : 0;
+    auto addx = [&](int c, float v) { jit_lam_add(lam, osp[c], v); };
+    auto brk = [&](int s) { return p.brk_a[(int64_t)s * n + i]; };
+    if (kBin) bin_grad(gq, gl, p.n_obs, p.ts, p.S, p.S);
+
+    float Xs[kSoftK][JN];  // states k0 .. k1 of the segment being walked
+    for (int c = L / K; c >= 0; --c) {
+        const int k0 = c * K, k1 = min(k0 + K - 1, L);
+        float X[JN];
+#pragma unroll
+        for (int q = 0; q < JN; ++q) X[q] = ckf[((int64_t)c * JN + q) * n + i];
+        // regenerate the segment's states with the forward's arithmetic
+        for (int kk = k0; kk <= k1; ++kk) {
+#pragma unroll
+            for (int q = 0; q < JN; ++q) Xs[kk - k0][q] = X[q];
+            if (kk < L) {
+                float E[NQ], a[JM], h[JM], y[JM], dX[JN];
+                step_noise<NQ>(E, (uint32_t)kk, c2, c3, key0, key1);
+                jit_soft_step(X, kr, E, invT, a, h, y, dX);
+#pragma unroll
+                for (int q = 0; q < JN; ++q) X[q] = __fadd_rn(X[q], dX[q]);
+            }
+        }
+        if (k1 < L) {  // the state after the segment is the next checkpoint, bit for bit
+#pragma unroll
+            for (int q = 0; q < JN; ++q) mism += X[q] != ckf[((int64_t)(c + 1) * JN + q) * n + i];
+        }
+        for (int k = k1; k >= k0; --k) {
+            float Xk[JN];
+#pragma unroll
+            for (int q = 0; q < JN; ++q) Xk[q] = Xs[k - k0][q];
+            const bool draw = (k < L) || draw_last;
+            const int s_top = (READOUT == SSA_READOUT_BIN && k == L) ? p.S - 1 : s_hi;
+            while (s_hi >= 0 && brk_next == k) {
+                --s_hi;
+                brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+            }
+            if (kBin) {
+                if (s_hi < s_top) bin_grad(gk, gl, p.n_obs, p.ts, p.S, s_hi + 1);
+                else {
+#pragma unroll
+                    for (int c2b = 0; c2b < kBinMaxObs; ++c2b) gk[c2b] = gq[c2b];
+                }
+            }
+            float tau_k = 0.0f;
+            if (draw) {
+                float E[NQ], a[JM], h[JM], y[JM], dX[JN];
+                step_noise<NQ>(E, (uint32_t)k, c2, c3, key0, key1);
+                const float a0 = jit_soft_step(Xk, kr, E, invT, a, h, y, dX);
+                const float tau = __fdividef(E[0], a0);
+                tau_k = tau;
+                float dt_dir = 0.0f, dtau_dir = 0.0f;
+                if (kBin) {  // t_{k+1} ends this interval and starts the next, in the bin of gq
+                    float cb = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < kBinMaxObs; ++q)
+                        if (q < p.n_obs) cb = __fmaf_rn(gq[q], jit_fsel(dX, osp[q]), cb);
+                    mu -= cb;
+                }
+                if (READOUT == SSA_READOUT_LINEAR) {
+                    for (int s = s_hi + 1; s <= s_top; ++s) {
+                        const float alpha = p.brk_a[(int64_t)s * n + i];
+                        if (alpha < 0.0f) continue;
+                        float cl = 0.0f;
+                        for (int o = 0; o < p.n_obs; ++o) {
+                            const float g = gl[(int64_t)s * p.n_obs + o];
+                            const int sp = p.obs_sp[o];
+                            jit_lam_add(lam, sp, alpha * g);
+                            cl += g * jit_fsel(dX, sp);
+                        }
+                        const float c_tau = __fdividef(cl, tau);
+                        dt_dir -= c_tau;
+                        dtau_dir -= alpha * c_tau;
+                    }
+                }
+                const float dtau = mu + dtau_dir;
+                const float dLda0 = -dtau * tau / a0;
+                float wr[JM];
+                jit_w(lam, wr);
+                float Wbar = 0.0f;
+#pragma unroll
+                for (int j = 0; j < JM; ++j) Wbar += y[j] * wr[j];
+                float psi[JM], ctau[JM];
+#pragma unroll
+                for (int j = 0; j < JM; ++j) {
+                    psi[j] = y[j] > 0.0f ? y[j] * (wr[j] - Wbar) * invT : 0.0f;
+                    dAr[j] += psi[j] + dLda0 * a[j];
+                    ctau[j] = dLda0 * kr[j];
+                }
+                jit_state_adj_soft(Xk, a, h, psi, ctau, lam);
+                mu += dt_dir;
+            }
+            if (kBin) {
+                bin_state_terms(addx, brk, gl, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
+#pragma unroll
+                for (int q = 0; q < kBinMaxObs; ++q) gq[q] = gk[q];
+            } else {
+                for (int s = s_hi + 1; s <= s_top; ++s) {
+                    float coef = 1.0f;
+                    if (READOUT == SSA_READOUT_LINEAR && draw) {
+                        const float alpha = p.brk_a[(int64_t)s * n + i];
+                        if (alpha >= 0.0f) coef = 1.0f - alpha;
+                    }
+                    for (int o = 0; o < p.n_obs; ++o)
+                        jit_lam_add(lam, p.obs_sp[o], coef * gl[(int64_t)s * p.n_obs + o]);
+                }
+            }
+        }
+    }
+    if (mism) atomicAdd(p.mismatch, mism);
+}
+
+template <int READOUT, bool SOFT>
 __device__ __forceinline__ void jit_adj(const AdjParams &p)
 {
     extern __shared__ float s_dA[];  // [JM][blockDim.x]
@@ -486,7 +781,10 @@ __device__ __forceinline__ void jit_adj(const AdjParams &p)
     int st = -1;
     if (i < n) st = p.status[i];
     const bool active = st == SSA_TRAJ_OK || st == SSA_TRAJ_ABSORBED || st == SSA_TRAJ_STEP_CAP;
-    if (active) jit_adj_traj<READOUT>(p, kr, i, st, dAr);
+    if (active) {
+        if constexpr (SOFT) jit_adj_soft_traj<READOUT>(p, kr, i, st, dAr);
+        else jit_adj_traj<READOUT>(p, kr, i, st, dAr);
+    }
 #pragma unroll
     for (int j = 0; j < JM; ++j) s_dA[j * B + tid] = dAr[j];
     __syncthreads();
@@ -503,6 +801,7 @@ __device__ __forceinline__ void jit_adj(const AdjParams &p)
 
 }  // namespace ssa
 
+#ifndef SSA_JIT_SOFT
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_hold(const ssa::FwdParams p)
 {
     ssa::jit_fwd<SSA_READOUT_HOLD, false>(p);
@@ -541,13 +840,51 @@ extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_linear_direct(cons
 }
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_hold(const ssa::AdjParams p)
 {
-    ssa::jit_adj<SSA_READOUT_HOLD>(p);
+    ssa::jit_adj<SSA_READOUT_HOLD, false>(p);
 }
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_linear(const ssa::AdjParams p)
 {
-    ssa::jit_adj<SSA_READOUT_LINEAR>(p);
+    ssa::jit_adj<SSA_READOUT_LINEAR, false>(p);
 }
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_bin(const ssa::AdjParams p)
 {
-    ssa::jit_adj<SSA_READOUT_BIN>(p);
+    ssa::jit_adj<SSA_READOUT_BIN, false>(p);
 }
+#else  // the soft-forward program of the same network
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_hold_soft(const ssa::FwdParams p)
+{
+    ssa::jit_fwd_soft<SSA_READOUT_HOLD, false>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_hold_soft_rec(const ssa::FwdParams p)
+{
+    ssa::jit_fwd_soft<SSA_READOUT_HOLD, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_hold_soft(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_HOLD, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_linear_soft(const ssa::FwdParams p)
+{
+    ssa::jit_fwd_soft<SSA_READOUT_LINEAR, false>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_linear_soft_rec(const ssa::FwdParams p)
+{
+    ssa::jit_fwd_soft<SSA_READOUT_LINEAR, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_linear_soft(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_LINEAR, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_bin_soft(const ssa::FwdParams p)
+{
+    ssa::jit_fwd_soft<SSA_READOUT_BIN, false>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_bin_soft_rec(const ssa::FwdParams p)
+{
+    ssa::jit_fwd_soft<SSA_READOUT_BIN, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_bin_soft(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_BIN, true>(p);
+}
+#endif

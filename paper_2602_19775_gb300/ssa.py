@@ -24,7 +24,7 @@ from . import _lib
 from ._lib import FwdOpts, SSAError, check
 
 READOUTS = {"hold": _lib.SSA_READOUT_HOLD, "linear": _lib.SSA_READOUT_LINEAR, "bin": _lib.SSA_READOUT_BIN}
-SELECTORS = {"gumbel": 0, "direct": 1}
+SELECTORS = {"gumbel": _lib.SSA_SELECT_GUMBEL, "direct": _lib.SSA_SELECT_DIRECT, "soft": _lib.SSA_SELECT_SOFT}
 
 
 def _ptr(t: torch.Tensor | None):
@@ -135,10 +135,13 @@ class ForwardResult:
 
 
 def make_opts(readout="hold", record=False, ckpt_interval=64, max_steps=1 << 20, threads_per_traj=0,
-              block_threads=0, specialize=True, selector="gumbel") -> FwdOpts:
+              block_threads=0, specialize=True, selector="gumbel", temperature=None) -> FwdOpts:
+    """ssa_fwd_opts; temperature is the soft forward's T (selector "soft" only)."""
     ro = READOUTS[readout] if isinstance(readout, str) else int(readout)
+    sel = SELECTORS[selector]
+    T = float(temperature) if sel == _lib.SSA_SELECT_SOFT and temperature is not None else 0.0
     return FwdOpts(ro, 1 if record else 0, int(ckpt_interval), int(threads_per_traj), int(max_steps),
-                   int(block_threads), 0 if specialize else 1, SELECTORS[selector], 0)
+                   int(block_threads), 0 if specialize else 1, sel, T)
 
 
 def workspace_bytes(net: Network, n_traj: int, n_samples: int, opts: FwdOpts) -> int:
@@ -156,7 +159,8 @@ def _as_cuda(x, dtype, device):
 
 def forward(net: Network, log_rates, n_traj: int, x0, t_end: float, sample_times, obs_species, seed: int,
             readout="hold", record=False, ckpt_interval=64, max_steps=1 << 20, traj_offset=0,
-            threads_per_traj=0, block_threads=0, specialize=True, selector="gumbel", replay_events=None,
+            threads_per_traj=0, block_threads=0, specialize=True, selector="gumbel", temperature=None,
+            replay_events=None,
             replay_n_events=None,
             workspace: torch.Tensor | None = None, obs_out: torch.Tensor | None = None,
             stream=None, device=None) -> ForwardResult:
@@ -168,11 +172,13 @@ def forward(net: Network, log_rates, n_traj: int, x0, t_end: float, sample_times
     ts = _as_cuda(sample_times, torch.float64, device)
     obs_sp = _as_cuda(obs_species, torch.int32, device)
     S, n_obs = int(ts.numel()), int(obs_sp.numel())
-    opts = make_opts(readout, record, ckpt_interval, max_steps, threads_per_traj, block_threads, specialize, selector)
+    opts = make_opts(readout, record, ckpt_interval, max_steps, threads_per_traj, block_threads, specialize, selector,
+                     temperature)
     need = workspace_bytes(net, n_traj, S, opts)
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=device)
-    odt = torch.int32 if opts.readout == _lib.SSA_READOUT_HOLD else torch.float32
+    soft = opts.selector == _lib.SSA_SELECT_SOFT  # real-valued states: float observables
+    odt = torch.int32 if opts.readout == _lib.SSA_READOUT_HOLD and not soft else torch.float32
     if obs_out is None:
         obs_out = torch.empty((n_traj, S, n_obs), dtype=odt, device=device)
     draws = torch.empty(n_traj, dtype=torch.int32, device=device)
@@ -507,9 +513,10 @@ class SSAFunction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, log_rates, net, n_traj, x0, t_end, sample_times, obs_species, seed, readout, temperature,
-                ckpt_interval, max_steps, traj_offset):
+                ckpt_interval, max_steps, traj_offset, selector="gumbel"):
         res = forward(net, log_rates.detach(), n_traj, x0, t_end, sample_times, obs_species, seed, readout=readout,
-                      record=True, ckpt_interval=ckpt_interval, max_steps=max_steps, traj_offset=traj_offset)
+                      record=True, ckpt_interval=ckpt_interval, max_steps=max_steps, traj_offset=traj_offset,
+                      selector=selector, temperature=temperature)
         ctx.run = res.run
         ctx.temperature = float(temperature)
         ctx.status = res.status
@@ -518,11 +525,14 @@ class SSAFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_obs):
         g = backward(ctx.run, grad_obs, ctx.temperature)
-        return (g,) + (None,) * 12
+        return (g,) + (None,) * 13
 
 
 def simulate(net: Network, log_rates: torch.Tensor, n_traj: int, x0, t_end: float, sample_times, obs_species,
-             seed: int, readout="linear", temperature=1.0, ckpt_interval=64, max_steps=1 << 20, traj_offset=0):
-    """Differentiable forward: obs [n_traj, S, n_obs] float32; obs.backward() fills log_rates.grad."""
+             seed: int, readout="linear", temperature=1.0, ckpt_interval=64, max_steps=1 << 20, traj_offset=0,
+             soft=False):
+    """Differentiable forward: obs [n_traj, S, n_obs] float32; obs.backward() fills log_rates.grad. soft: the
+    relaxed forward of Eq. 4 at `temperature` and the exact gradient of that model (instead of the exact
+    forward with the straight-through gradient)."""
     return SSAFunction.apply(log_rates, net, n_traj, x0, t_end, sample_times, obs_species, seed, readout,
-                             temperature, ckpt_interval, max_steps, traj_offset)
+                             temperature, ckpt_interval, max_steps, traj_offset, "soft" if soft else "gumbel")
