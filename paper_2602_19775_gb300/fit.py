@@ -1,10 +1,14 @@
-"""Parameter inference through the library (arXiv 2602.19775, Section 4.1): fit the log rate constants
-of a network so that the ensemble-mean observables of simulated trajectories match a target, with the
+"""Parameter inference through the library. Section 4.1 (and 4.4): fit the log rate constants of a network
+so that the ensemble-mean observables of simulated trajectories match a target, with the
 straight-through gradient of the exact SSA, RMSprop on theta = log k, and the temperature and the learning
 rate annealed geometrically over the iterations (Section 4.1 anneals T from 1.0 to 0.001 with a geometric
 learning-rate decay). The estimator's variance grows as T falls: on the 2A <-> B workload (about 250 draws
 per trajectory) single-batch gradients at T = 0.01 reach 1e7 where T = 0.1 gives ~2e2, so the learning rate
 has to fall with T.
+
+Section 4.2, the start-point map: states sampled along one long reference trajectory start short
+replicated segments, whose rates of change of the observed species are matched to the targets while only
+some rates are trained (reference_start_points, segment_rates, fit_start_point_map).
 
 The simulation and its gradient run in the library (simulate / SSAFunction); this module is the host-side
 loop around them.
@@ -16,7 +20,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from .ssa import Network, simulate
+from .ssa import Network, forward, simulate
 
 
 @dataclass
@@ -58,3 +62,68 @@ def fit_ensemble_mean(net: Network, theta0, x0, t_end: float, sample_times, obs_
         hist.theta.append(theta.detach().double().cpu().numpy())
         hist.temperature.append(T)
     return theta.detach().double().cpu().numpy(), hist
+
+
+def reference_start_points(net: Network, theta, x0, n_points: int, t_ref: float, seed: int,
+                           max_steps: int = 1 << 24) -> np.ndarray:
+    """Start points of the start-point map (Section 4.2): the states of one long reference trajectory
+    (simulated at theta) at n_points uniformly random times in (0, t_ref], in time order; int32 [n_points, N]."""
+    rng = np.random.default_rng(seed)
+    times = np.sort(rng.uniform(0.0, t_ref, n_points))
+    theta = torch.as_tensor(np.asarray(theta, dtype=np.float32), device="cuda")
+    fw = forward(net, theta, 1, x0, t_ref, times, list(range(net.n_species)), seed, readout="hold",
+                 max_steps=max_steps)
+    if int(fw.status[0]) > 1:
+        raise RuntimeError(f"reference trajectory stopped with status {int(fw.status[0])}")
+    return fw.obs[0].cpu().numpy().astype(np.int32)
+
+
+def segment_rates(net: Network, theta: torch.Tensor, starts, replicates: int, horizon: float, obs_species, seed: int,
+                  temperature: float, max_steps: int = 4096) -> torch.Tensor:
+    """Rates of change of the start-point map (Section 4.2), differentiable in theta: from each start point,
+    `replicates` segments of length `horizon`; the rate of observable c is (the ensemble mean of its exact
+    average over the final two thirds of the segment - its start value) / (2 horizon / 3), the time from the
+    start to the middle of that window. Returns [n_points, n_obs]."""
+    starts = torch.as_tensor(np.asarray(starts, dtype=np.int32), device="cuda")
+    x0 = starts.repeat_interleave(replicates, dim=0)
+    edges = [horizon / 3.0, horizon]
+    obs = simulate(net, theta, x0.shape[0], x0, horizon, edges, obs_species, seed, readout="bin",
+                   temperature=temperature, max_steps=max_steps)
+    window = obs[:, 1, :].reshape(starts.shape[0], replicates, -1).mean(1)
+    start = starts[:, torch.as_tensor(np.asarray(obs_species), device="cuda").long()].float()
+    return (window - start) / (2.0 * horizon / 3.0)
+
+
+def fit_start_point_map(net: Network, theta0, trainable, starts, target_rates, obs_species, horizon: float,
+                        replicates: int, batch: int, iters: int, temperature: float, lr: float = 0.1,
+                        lr_final: float | None = None, seed0: int = 0, optimizer: str = "rmsprop"
+                        ) -> tuple[np.ndarray, FitHistory]:
+    """RMSprop on the trainable log rates (the others stay at theta0) to match the segment rates of a batch of
+    start points per iteration to their targets (mean squared error), at a fixed temperature with a geometric
+    learning-rate decay (Section 4.2). target_rates: [n_points, n_obs] for the rows of `starts`."""
+    dev = torch.device("cuda")
+    base = torch.tensor(np.asarray(theta0, dtype=np.float32), device=dev)
+    mask = torch.zeros_like(base)
+    mask[list(trainable)] = 1.0
+    free = torch.zeros_like(base, requires_grad=True)
+    opt = torch.optim.RMSprop([free], lr=lr) if optimizer == "rmsprop" else torch.optim.Adam([free], lr=lr)
+    tgt = torch.as_tensor(np.asarray(target_rates, dtype=np.float32), device=dev)
+    starts = np.asarray(starts)
+    rng = np.random.default_rng(seed0)
+    lr_final = lr if lr_final is None else lr_final
+    hist = FitHistory()
+    for it in range(iters):
+        frac = it / max(iters - 1, 1)
+        for grp in opt.param_groups:
+            grp["lr"] = lr * (lr_final / lr) ** frac
+        rows = rng.choice(starts.shape[0], size=batch, replace=False)
+        theta = base + mask * free
+        rates = segment_rates(net, theta, starts[rows], replicates, horizon, obs_species, seed0 + 1 + it, temperature)
+        loss = ((rates - tgt[torch.as_tensor(rows, device=dev)]) ** 2).mean()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        hist.loss.append(float(loss.item()))
+        hist.theta.append((base + mask * free).detach().double().cpu().numpy())
+        hist.temperature.append(temperature)
+    return (base + mask * free).detach().double().cpu().numpy(), hist
