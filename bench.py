@@ -375,7 +375,7 @@ def run_ours(args):
     grn = grn_extra(ssa, dev, n_img=args.grn_images) if (rank == 0 and "grn" in legs) else None
     warp = warp_extra(ssa, dev, n=args.warp_traj) if (rank == 0 and "warp" in legs) else None
     c3 = c3_extra(ssa, dev) if (rank == 0 and "c3" in legs) else None
-    ion = ion_channel_extra(ssa, dev) if (rank == 0 and "ion" in legs) else None
+    ion = ion_channel_extra(ssa, dev, n=args.ion_traj) if (rank == 0 and "ion" in legs) else None
     M = wl.net.n_reactions
     rates = ssa.pipe_rates()
     log_slots = 128.0 / rates["neglog"]
@@ -500,7 +500,7 @@ def ion_channel_extra(ssa, dev, n: int = 262144, reps: int = 3, T: float = 0.05)
     theta = th + 0.2
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    out = {"workload": "ion channel C <-> O -> I, 2 channels, 262,144 trajectories, 800 bins of 0.01 ms, BIN readout"}
+    out = {"workload": f"ion channel C <-> O -> I, 2 channels, {n} trajectories, 800 bins of 0.01 ms, BIN readout"}
     for mode in ("forward", "gradient_step"):
         ms, steps = 0.0, 0
         for r in range(reps + 1):
@@ -841,6 +841,7 @@ def main():
                          "Section 4.4), c3 (the oscillator at its "
                          "full size, about two minutes; not in the default) ('none' for none)")
     ap.add_argument("--grn-images", type=int, default=512, help="images of the GRN field (64 trajectories each)")
+    ap.add_argument("--ion-traj", type=int, default=262144, help="trajectories of the ion-channel field")
     ap.add_argument("--warp-traj", type=int, default=16384, help="trajectories of the warp-kernel field")
     ap.add_argument("--batch-scale", type=float, default=1.0 / 16,
                     help="trajectories per network of the uneven batch, as a fraction of the full counts")

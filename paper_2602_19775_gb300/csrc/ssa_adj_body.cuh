@@ -66,9 +66,12 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
         return (slot & 1) ? (int)(w >> 16) : (int)(w & 0xffff);
     };
 
-    // BIN: the edges after brk_tail[i] belong to the last state and are not stored
-    int s_hi = READOUT == SSA_READOUT_BIN ? min(p.brk_tail[i], p.S - 1) : p.S - 1;
-    int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    int s_hi = p.S - 1;
+    int brk_next = (READOUT != SSA_READOUT_BIN && s_hi >= 0) ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    // BIN: one recorded slot per state interval that holds edges
+    BinSlots bslots{-1, -1};
+    float d_first = 0.0f, d_last = 0.0f;
+    if (READOUT == SSA_READOUT_BIN) bin_slots_init(bslots, p.brk_k, p.brk_tail, n, i);
     float mu = 0.0f;
     int mism = 0;
     int ck_row = L / p.K, ck_off = L - ck_row * p.K;  // checkpoint c holds X_{cK}
@@ -87,7 +90,6 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
     for (int c = 0; c < kBinMaxObs; ++c) osp[c] = (kBin && c < p.n_obs) ? p.obs_sp[c] : 0;
     auto xobs = [&](int c) { return X[osp[c] * B]; };
     auto addx = [&](int c, float v) { lam[osp[c] * B] += v; };
-    auto brk = [&](int s) { return p.brk_a[(int64_t)s * n + i]; };
     if (kBin) {
         bin_grad(gq, gl, p.n_obs, p.ts, p.S, p.S);
 #pragma unroll
@@ -96,10 +98,14 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
 
     for (int k = L; k >= 0; --k) {
         const bool draw = (k < L) || draw_last;
-        const int s_top = (READOUT == SSA_READOUT_BIN && k == L) ? p.S - 1 : s_hi;
-        while (s_hi >= 0 && brk_next == k) {
-            --s_hi;
-            brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+        const int s_top = s_hi;
+        if (READOUT == SSA_READOUT_BIN) {
+            bin_slots_step(bslots, p.brk_k, p.brk_s, p.brk_a, p.ts, n, i, k, s_hi, d_first, d_last);
+        } else {
+            while (s_hi >= 0 && brk_next == k) {
+                --s_hi;
+                brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+            }
         }
         // samples s_hi+1 .. s_top are bracketed by state k
         if (kBin) {
@@ -227,7 +233,7 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
             }
         }
         if (kBin) {
-            bin_state_terms(addx, brk, gl, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
+            bin_state_terms(addx, d_first, d_last, gl, p.bin_prefix, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
 #pragma unroll
             for (int c = 0; c < kBinMaxObs; ++c) {
                 gq[c] = gk[c];

@@ -26,8 +26,9 @@ cudaError_t launch_philox_uniforms(uint64_t seed, const uint64_t *traj, const ui
 cudaError_t launch_unpack_events(const uint4 *ev, const int *draws, int64_t n_traj, int64_t stride, int *out,
                                  cudaStream_t st);
 cudaError_t launch_status_count(const int *status, int64_t n, unsigned long long *counts, cudaStream_t st);
-cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, const int *tail, const int *draws,
-                                      const int *status, int *out, cudaStream_t st);
+cudaError_t launch_bin_prefix(const float *g, int S, int n_obs, double *prefix, cudaStream_t st);
+cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, const int *first, const int *nslots,
+                                      int *out, cudaStream_t st);
 cudaError_t launch_backward_thread(const AdjParams &p, int readout, int block, size_t smem, int64_t grid,
                                    cudaStream_t st);
 cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, const int *rate_index, int P,
@@ -122,7 +123,9 @@ WsLayout layout(const ssa_network *net, int64_t n, int32_t S, const ssa_fwd_opts
         L.ckpt = take((size_t)L.n_ckpt * net->N * n * sizeof(int));
         L.brk_k = take((size_t)S * n * sizeof(int));
         L.brk_a = take((size_t)S * n * sizeof(float));
+        L.brk_s = take((size_t)S * n * sizeof(int));
         L.brk_tail = take((size_t)(n > 0 ? n : 1) * sizeof(int));
+        L.bin_prefix = take((size_t)(S + 1) * SSA_BIN_MAX_OBS * sizeof(double));
         L.partial = take((size_t)(L.max_blocks > 0 ? L.max_blocks : 1) * net->M * sizeof(float));
         L.dA = take((size_t)net->M * sizeof(float));
     }
@@ -423,6 +426,7 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
         p.ckpt = reinterpret_cast<int *>(ws + L.ckpt);
         p.brk_k = reinterpret_cast<int *>(ws + L.brk_k);
         p.brk_a = reinterpret_cast<float *>(ws + L.brk_a);
+        p.brk_s = reinterpret_cast<int *>(ws + L.brk_s);
         p.brk_tail = reinterpret_cast<int *>(ws + L.brk_tail);
         p.xfinal = reinterpret_cast<int *>(ws + L.xfinal);
     }
@@ -543,10 +547,17 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     p.ckpt = reinterpret_cast<const int *>(ws + L.ckpt);
     p.brk_k = reinterpret_cast<const int *>(ws + L.brk_k);
     p.brk_a = reinterpret_cast<const float *>(ws + L.brk_a);
+    p.brk_s = reinterpret_cast<const int *>(ws + L.brk_s);
     p.brk_tail = reinterpret_cast<const int *>(ws + L.brk_tail);
     p.xfinal = reinterpret_cast<const int *>(ws + L.xfinal);
     p.dl_dobs = dl_dobs;
     p.dl_stride = dl_traj_stride;
+    p.bin_prefix = nullptr;
+    if (run->opts.readout == SSA_READOUT_BIN && dl_traj_stride == 0 && run->S > 0 && run->n_obs > 0) {
+        double *pre = reinterpret_cast<double *>(ws + L.bin_prefix);
+        CUDA_TRY(launch_bin_prefix(dl_dobs, run->S, run->n_obs, pre, st));
+        p.bin_prefix = pre;
+    }
     p.invT = 1.0f / temperature;
     p.partial = reinterpret_cast<float *>(ws + L.partial);
     p.mismatch = flag + 2;
@@ -600,9 +611,8 @@ extern "C" ssa_status ssa_run_brackets(const ssa_run *run, int32_t *brackets_out
     if (!run->opts.record) return fail(SSA_ERR_STATE, "the forward was not recorded");
     const bool bin = run->opts.readout == SSA_READOUT_BIN;
     CUDA_TRY(launch_transpose_brackets(reinterpret_cast<const int *>(run->ws + run->L.brk_k), run->n_traj, run->S,
-                                       bin ? reinterpret_cast<const int *>(run->ws + run->L.brk_tail) : nullptr,
-                                       reinterpret_cast<const int *>(run->ws + run->L.draws),
-                                       reinterpret_cast<const int *>(run->ws + run->L.status), brackets_out,
+                                       bin ? reinterpret_cast<const int *>(run->ws + run->L.brk_s) : nullptr,
+                                       reinterpret_cast<const int *>(run->ws + run->L.brk_tail), brackets_out,
                                        static_cast<cudaStream_t>(stream)));
     return SSA_OK;
 }

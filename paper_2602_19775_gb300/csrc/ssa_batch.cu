@@ -29,8 +29,8 @@
 namespace ssa {
 cudaError_t launch_unpack_events(const uint4 *ev, const int *draws, int64_t n_traj, int64_t stride, int *out,
                                  cudaStream_t st);
-cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, const int *tail, const int *draws,
-                                      const int *status, int *out, cudaStream_t st);
+cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, const int *first, const int *nslots,
+                                      int *out, cudaStream_t st);
 
 struct BatchItem {
     FwdParams f;
@@ -723,7 +723,7 @@ extern "C" ssa_status ssa_batch_item_brackets(const ssa_batch *bt, int32_t item,
     if (!bt || !bt->ready || item < 0 || item >= (int)bt->items.size()) return set_error(SSA_ERR_INVALID_ARG, "bad item");
     const FwdParams &p = bt->h_items[item].f;
     if (!brackets_out && p.n_traj > 0 && p.S > 0) return set_error(SSA_ERR_INVALID_ARG, "brackets_out is NULL");
-    CUDA_TRY_B(launch_transpose_brackets(p.brk_k, p.n_traj, p.S, nullptr, nullptr, nullptr, brackets_out,
+    CUDA_TRY_B(launch_transpose_brackets(p.brk_k, p.n_traj, p.S, nullptr, nullptr, brackets_out,
                                          static_cast<cudaStream_t>(stream)));
     return SSA_OK;
 }

@@ -192,8 +192,10 @@ __device__ __forceinline__ float sadj_hetero(float xs, float xo, float a, float 
 // inside the bin. An edge t_s in [t_k, t_{k+1}), at offset d = t_s - t_k, closes a bin: the first edge
 // of a step closes the bin that began before t_k, obs = (acc + X_k d) / D_s; a later edge closes a bin
 // that lies inside the step, where the path is X_k, obs = X_k. The rest of the step, t_{k+1} minus the
-// last edge, opens the next bin. A stopped path holds its last state. The recorded bracket value of
-// edge s is d.
+// last edge, opens the next bin. A stopped path holds its last state. The bins held at X_k inside a step
+// are buffered as runs and written by the warp when the trajectories stop (coalesced), and recording keeps
+// one slot per state interval that holds edges -- its state k, first edge and that edge's offset d -- not
+// one bracket per edge.
 //
 // The adjoint walks the same pieces backwards. With g_b = dL/dobs_b / D_b, the state X_k receives the
 // overlap of its interval with every bin times that bin's g; the event time t_{k+1} (the end of one
@@ -257,12 +259,15 @@ __device__ __forceinline__ float bin_transition(const XF &xobs, const int (&xo)[
 }
 
 // dL/dX_k from the bins that the interval of state k overlaps. Edges s_first..s_last (none if
-// s_first > s_last) lie in it; gq: g of the bin that contains t_{k+1}, gk: of the bin that contains t_k;
-// draw: the interval ends at t_{k+1} = t_k + tau (else the path holds X_k to the end); brk(s): offset
-// of edge s from t_k; addx(c, v) adds v to the adjoint of observable c.
-template <class AF, class BF>
-__device__ __forceinline__ void bin_state_terms(const AF &addx, const BF &brk, const float *gl, int n_obs, int s_first,
-                                                int s_last, bool draw, float tau, const float (&gq)[kBinMaxObs],
+// s_first > s_last) lie in it, at offsets d_first and d_last from t_k; gq: g of the bin that contains
+// t_{k+1}, gk: of the bin that contains t_k; draw: the interval ends at t_{k+1} = t_k + tau (else the path
+// holds X_k to the end); addx(c, v) adds v to the adjoint of observable c.
+// prefix: when every trajectory has the same upstream gradient, prefix[s][c] = sum over bins below s of
+// dL/dobs (binary64, [S + 1][kBinMaxObs]), so a run of whole bins costs one difference; else nullptr.
+template <class AF>
+__device__ __forceinline__ void bin_state_terms(const AF &addx, float d_first, float d_last, const float *gl,
+                                                const double *prefix, int n_obs, int s_first, int s_last, bool draw,
+                                                float tau, const float (&gq)[kBinMaxObs],
                                                 const float (&gk)[kBinMaxObs])
 {
     if (s_first > s_last) {  // the interval lies inside one bin
@@ -274,20 +279,56 @@ __device__ __forceinline__ void bin_state_terms(const AF &addx, const BF &brk, c
         return;
     }
     if (draw) {  // t_{k+1} - t_{s_last} in the bin after the last edge
-        const float r = tau - brk(s_last);
+        const float r = tau - d_last;
 #pragma unroll
         for (int c = 0; c < kBinMaxObs; ++c)
             if (c < n_obs) addx(c, gq[c] * r);
     }
-    for (int s = s_first + 1; s <= s_last; ++s) {  // whole bins: overlap D_s, so g_s D_s = dL/dobs_s
+    // whole bins: overlap D_s, so g_s D_s = dL/dobs_s
+    if (prefix) {
+        if (s_last > s_first) {
 #pragma unroll
-        for (int c = 0; c < kBinMaxObs; ++c)
-            if (c < n_obs) addx(c, gl[(int64_t)s * n_obs + c]);
+            for (int c = 0; c < kBinMaxObs; ++c)
+                if (c < n_obs)
+                    addx(c, (float)(prefix[(int64_t)(s_last + 1) * kBinMaxObs + c] -
+                                    prefix[(int64_t)(s_first + 1) * kBinMaxObs + c]));
+        }
+    } else {
+        for (int s = s_first + 1; s <= s_last; ++s) {
+#pragma unroll
+            for (int c = 0; c < kBinMaxObs; ++c)
+                if (c < n_obs) addx(c, gl[(int64_t)s * n_obs + c]);
+        }
     }
-    const float d = brk(s_first);  // t_{s_first} - t_k in the bin that contains t_k
 #pragma unroll
-    for (int c = 0; c < kBinMaxObs; ++c)
-        if (c < n_obs) addx(c, gk[c] * d);
+    for (int c = 0; c < kBinMaxObs; ++c)  // t_{s_first} - t_k in the bin that contains t_k
+        if (c < n_obs) addx(c, gk[c] * d_first);
+}
+
+// The adjoint's walk over the recorded slots of the bin readout (from the last): at state k, if the
+// slot below is k's, its edges are first..s_top, and s_hi drops below them. Returns whether state k holds
+// edges; d_first/d_last are the offsets of its first and last edge from t_k.
+struct BinSlots {
+    int q;     // next slot to read, from the last
+    int kq;    // its state (-1: none left)
+};
+__device__ __forceinline__ void bin_slots_init(BinSlots &w, const int *brk_k, const int *brk_tail, int64_t n, int64_t i)
+{
+    w.q = brk_tail[i] - 1;
+    w.kq = w.q >= 0 ? brk_k[(int64_t)w.q * n + i] : -1;
+}
+__device__ __forceinline__ void bin_slots_step(BinSlots &w, const int *brk_k, const int *brk_s, const float *brk_a,
+                                               const double *ts, int64_t n, int64_t i, int k, int &s_hi,
+                                               float &d_first, float &d_last)
+{
+    if (w.kq != k) return;
+    const int64_t at = (int64_t)w.q * n + i;
+    const int first = brk_s[at];
+    d_first = brk_a[at];
+    d_last = s_hi > first ? d_first + d2f_nonneg(ts[s_hi] - ts[first]) : d_first;
+    s_hi = first - 1;
+    --w.q;
+    w.kq = w.q >= 0 ? brk_k[(int64_t)w.q * n + i] : -1;
 }
 
 // Soft forward: the float state is checkpointed every kSoftK steps; the adjoint re-runs each segment.
@@ -329,7 +370,8 @@ struct FwdParams {
     int *ckpt;        // [n_ckpt][N][n_traj]
     int *brk_k;       // [S][n_traj]
     float *brk_a;     // [S][n_traj]
-    int *brk_tail;    // [n_traj], BIN readout: first edge bracketed by the last state (S: none)
+    int *brk_s;       // [S][n_traj], BIN readout: first edge of slot q (brk_k, brk_a: its state, offset)
+    int *brk_tail;    // [n_traj], BIN readout: number of slots
     int *xfinal;      // [N][n_traj]
     // replay
     const uint16_t *ev_in;
@@ -355,10 +397,12 @@ struct AdjParams {
     const int *ckpt;
     const int *brk_k;
     const float *brk_a;
+    const int *brk_s;
     const int *brk_tail;
     const int *xfinal;
     const float *dl_dobs;
     int64_t dl_stride;  // elements between trajectories (0 = shared)
+    const double *bin_prefix;  // BIN readout with a shared dl_dobs: its prefix sums over bins, else nullptr
     float invT;
     float *partial;   // [gridDim.x][M]
     int *mismatch;    // backward consistency failures
@@ -366,30 +410,102 @@ struct AdjParams {
 };
 
 
+// Bin readout, forward: the held runs of bins buffered for the warp-wide write, and the slot count.
+constexpr int kBinRuns = 8;
+struct BinRuns {
+    int n;                           // buffered runs
+    int slots;                       // recorded slots
+    int lo[kBinRuns], hi[kBinRuns];  // bins lo..hi hold v
+    float v[kBinRuns][kBinMaxObs];
+};
+__device__ __forceinline__ void bin_runs_init(BinRuns &r)
+{
+    r.n = 0;
+    r.slots = 0;
+#pragma unroll
+    for (int q = 0; q < kBinRuns; ++q) {
+        r.lo[q] = r.hi[q] = 0;
+#pragma unroll
+        for (int c = 0; c < kBinMaxObs; ++c) r.v[q][c] = 0.0f;
+    }
+}
+
+// The first edge s of a state interval (t_k <= t_s): close its bin, and record the interval's slot.
+template <bool RECORD, class XF>
+__device__ __forceinline__ void bin_first_edge(const FwdParams &p, int64_t i, int s, double t_k, int k,
+                                               float (&acc)[kBinMaxObs], const XF &xobs, BinRuns &r)
+{
+    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+    const float d = bin_close(acc, xobs, p.n_obs, p.ts, s, t_k, true, o);
+    if (RECORD) {
+        const int64_t at = (int64_t)r.slots * p.n_traj + i;
+        p.brk_k[at] = k;
+        p.brk_s[at] = s;
+        p.brk_a[at] = d;
+        ++r.slots;
+    }
+}
+
+// Bins lo..hi lie inside the interval of X_k: buffer the run (the thread writes it itself when the buffer
+// is full).
+template <class XF>
+__device__ __forceinline__ void bin_held_run(const FwdParams &p, int64_t i, int lo, int hi, const XF &xobs, BinRuns &r)
+{
+    if (lo > hi) return;
+    const int no = p.n_obs;
+    if (r.n < kBinRuns) {
+        r.lo[r.n] = lo;
+        r.hi[r.n] = hi;
+#pragma unroll
+        for (int c = 0; c < kBinMaxObs; ++c) r.v[r.n][c] = c < no ? obs_f(xobs(c)) : 0.0f;
+        ++r.n;
+        return;
+    }
+    float *row = static_cast<float *>(p.obs_out) + (int64_t)i * p.S * no;
+    for (int s = lo; s <= hi; ++s)
+        for (int c = 0; c < no; ++c) row[(int64_t)s * no + c] = obs_f(xobs(c));
+}
+
+// Bin readout, one state interval [t_k, t_next): the edges in it from s on are found by bisection (the
+// edges increase strictly); the first closes its bin, the others are whole bins held at X_k. Returns the
+// index of the first edge at or after t_next.
+template <bool RECORD, class XF>
+__device__ __forceinline__ int bin_edges(const FwdParams &p, int64_t i, int s, double t_k, double t_next, int k,
+                                         float (&acc)[kBinMaxObs], const XF &xobs, BinRuns &r)
+{
+    int lo = s, hi = p.S;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (gt_nonneg(t_next, p.ts[mid])) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo > s) {
+        bin_first_edge<RECORD>(p, i, s, t_k, k, acc, xobs, r);
+        bin_held_run(p, i, s + 1, lo - 1, xobs, r);
+    }
+    return lo;
+}
+
 // Bin readout, after the last state X_k (held from t_k on): the first remaining bin s may have begun
-// before t_k, the later ones hold X_k exactly. Each thread closes its first remaining bin; then the warp
-// writes the held rows of its trajectories together, one trajectory at a time with consecutive lanes
-// on consecutive floats, so the stores of a long constant tail are coalesced. Recording stores the
-// bracket of the first remaining edge and, in tail[i], its index (S if none): the edges after it are
-// not stored. Every lane of the warp whose trajectory index is below n_traj must call this.
+// before t_k, the later ones hold X_k exactly. Each thread closes its first remaining bin (and records its
+// slot); then the warp writes the buffered runs and the held tails of its trajectories together, one run
+// at a time with consecutive lanes on consecutive floats, so these stores are coalesced. Recording stores
+// the number of slots in brk_tail[i]. Every lane of the warp whose trajectory index is below n_traj must
+// call this.
 template <bool RECORD, class XF>
 __device__ __forceinline__ void bin_tail(const FwdParams &p, int64_t i, int s, double t_k, int k,
-                                         float (&acc)[kBinMaxObs], const XF &xobs, bool bad_obs)
+                                         float (&acc)[kBinMaxObs], const XF &xobs, bool bad_obs, BinRuns &r)
 {
     const int64_t n = p.n_traj;
     const int S = p.S, no = p.n_obs;
     float *obs = static_cast<float *>(p.obs_out);
     if (s < S) {
         float *o = obs + ((int64_t)i * S + s) * no;
-        const float d = bin_close(acc, xobs, no, p.ts, s, t_k, true, o);
+        bin_first_edge<RECORD>(p, i, s, t_k, k, acc, xobs, r);
         if (bad_obs)
             for (int c = 0; c < no; ++c) o[c] = 0.0f;
-        if (RECORD) {
-            p.brk_a[(int64_t)s * n + i] = d;
-            p.brk_k[(int64_t)s * n + i] = k;
-        }
     }
-    if (RECORD) p.brk_tail[i] = s < S ? s : S;
+    if (RECORD) p.brk_tail[i] = r.slots;
     float xv[kBinMaxObs];
 #pragma unroll
     for (int c = 0; c < kBinMaxObs; ++c) xv[c] = (c < no && !bad_obs) ? obs_f(xobs(c)) : 0.0f;
@@ -398,6 +514,21 @@ __device__ __forceinline__ void bin_tail(const FwdParams &p, int64_t i, int s, d
     const unsigned mask = base + 32 <= n ? 0xffffffffu : ((1u << (unsigned)(n - base)) - 1u);
     const int first = s + 1;  // first held row
     for (int j = 0; j < 32 && ((mask >> j) & 1u); ++j) {
+        const int nj = __shfl_sync(mask, r.n, j);
+        for (int q = 0; q < nj; ++q) {  // lane j's buffered runs
+            const int lo = __shfl_sync(mask, r.lo[q], j), hi = __shfl_sync(mask, r.hi[q], j);
+            float vq[kBinMaxObs];
+#pragma unroll
+            for (int c = 0; c < kBinMaxObs; ++c) vq[c] = __shfl_sync(mask, r.v[q][c], j);
+            float *row = obs + (base + j) * (int64_t)S * no;
+            for (int64_t e = (int64_t)lo * no + lane; e < (int64_t)(hi + 1) * no; e += 32) {
+                const int c = no == 1 ? 0 : (int)(e % no);
+                float v = vq[0];
+#pragma unroll
+                for (int c2 = 1; c2 < kBinMaxObs; ++c2) v = c == c2 ? vq[c2] : v;
+                row[e] = v;
+            }
+        }
         const int fj = __shfl_sync(mask, first, j);
         float vj[kBinMaxObs];
 #pragma unroll

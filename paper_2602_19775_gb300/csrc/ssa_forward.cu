@@ -128,17 +128,42 @@ __global__ void unpack_events_kernel(const uint4 *ev, const int *draws, int64_t 
     out[idx] = v;
 }
 
-// Test hook: brackets [S][n] -> [n][S]. With the bin readout the edges after the first one bracketed
-// by the last state are not stored (tail[i] is that first edge); they belong to the last state.
-__global__ void transpose_brackets_kernel(const int *brk, int64_t n_traj, int S, const int *tail, const int *draws,
-                                          const int *status, int *out)
+// Bin readout with a shared upstream gradient g [S][n_obs]: prefix[s][c] = sum_{b < s} g[b][c] in binary64,
+// for s = 0..S ([S + 1][SSA_BIN_MAX_OBS]).
+__global__ void bin_prefix_kernel(const float *g, int S, int n_obs, double *prefix)
+{
+    const int c = threadIdx.x;
+    if (c >= SSA_BIN_MAX_OBS) return;
+    double acc = 0.0;
+    prefix[c] = 0.0;
+    for (int s = 0; s < S; ++s) {
+        if (c < n_obs) acc += (double)g[(int64_t)s * n_obs + c];
+        prefix[(int64_t)(s + 1) * SSA_BIN_MAX_OBS + c] = acc;
+    }
+}
+
+// Test hook: brackets [S][n] -> [n][S].
+__global__ void transpose_brackets_kernel(const int *brk, int64_t n_traj, int S, int *out)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n_traj * S) return;
     const int64_t i = idx / S;
     const int s = (int)(idx % S);
-    if (tail && s > tail[i]) out[idx] = status[i] == SSA_TRAJ_OK ? draws[i] - 1 : draws[i];
-    else out[idx] = brk[(int64_t)s * n_traj + i];
+    out[idx] = brk[(int64_t)s * n_traj + i];
+}
+
+// Test hook, bin readout: the per-edge brackets from the slots (slot q of trajectory i: state brk[q],
+// edges from first[q] up to the next slot's first edge; nslots[i] slots).
+__global__ void bin_brackets_kernel(const int *brk, const int *first, const int *nslots, int64_t n_traj, int S, int *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_traj) return;
+    const int nq = min(nslots[i], S);
+    for (int q = 0; q < nq; ++q) {
+        const int lo = max(first[(int64_t)q * n_traj + i], 0);
+        const int hi = q + 1 < nq ? min(first[(int64_t)(q + 1) * n_traj + i], S) : S;
+        for (int s = lo; s < hi; ++s) out[i * S + s] = brk[(int64_t)q * n_traj + i];
+    }
 }
 
 // Status histogram for ssa_run_status.
@@ -277,13 +302,21 @@ cudaError_t launch_unpack_events(const uint4 *ev, const int *draws, int64_t n_tr
     return cudaGetLastError();
 }
 
-cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, const int *tail, const int *draws,
-                                      const int *status, int *out, cudaStream_t st)
+cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, const int *first, const int *nslots,
+                                      int *out, cudaStream_t st)
 {
     const int64_t total = n_traj * S;
     if (total == 0) return cudaSuccess;
-    transpose_brackets_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(brk, n_traj, S, tail, draws, status,
-                                                                               out);
+    if (first)
+        bin_brackets_kernel<<<(unsigned)((n_traj + 255) / 256), 256, 0, st>>>(brk, first, nslots, n_traj, S, out);
+    else
+        transpose_brackets_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(brk, n_traj, S, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_prefix(const float *g, int S, int n_obs, double *prefix, cudaStream_t st)
+{
+    bin_prefix_kernel<<<1, 32, 0, st>>>(g, S, n_obs, prefix);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,8 @@ __device__ __forceinline__ void thread_fwd_body(const FwdParams &p, const int4 *
     if (MC > 0) step_noise<NQ>(E, 0u, c2, c3, key0, key1);
     // BIN readout: integral of the open bin up to t_k per observable (species clamped when invalid)
     float bacc[kBinMaxObs];
+    BinRuns bruns;
+    bin_runs_init(bruns);
     int osp[kBinMaxObs];
 #pragma unroll
     for (int c = 0; c < kBinMaxObs; ++c) {
@@ -116,28 +118,28 @@ __device__ __forceinline__ void thread_fwd_body(const FwdParams &p, const int4 *
         if (slow) {
             // samples with t_k <= t_s < t_{k+1}
             const int s_first = s;
-            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
-                if (READOUT == SSA_READOUT_HOLD) {
-                    int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    for (int c = 0; c < p.n_obs; ++c) o[c] = X[p.obs_sp[c] * B];
-                } else if (READOUT == SSA_READOUT_BIN) {
-                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_first, o);
-                    if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
-                } else {
-                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
-                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    for (int c = 0; c < p.n_obs; ++c) {
-                        const int sp = p.obs_sp[c];
-                        int dv = 0;
-                        for (int e = rj.z; e < rj.w; ++e)
-                            if (stoich_species(s_st[e]) == sp) dv += stoich_delta(s_st[e]);
-                        o[c] = __fmaf_rn(alpha, (float)dv, (float)X[sp * B]);
+            if constexpr (READOUT == SSA_READOUT_BIN) {
+                s = bin_edges<RECORD>(p, i, s, t, t_next, k, bacc, xobs, bruns);
+            } else {
+                while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
+                    if (READOUT == SSA_READOUT_HOLD) {
+                        int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                        for (int c = 0; c < p.n_obs; ++c) o[c] = X[p.obs_sp[c] * B];
+                    } else {
+                        const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
+                        float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                        for (int c = 0; c < p.n_obs; ++c) {
+                            const int sp = p.obs_sp[c];
+                            int dv = 0;
+                            for (int e = rj.z; e < rj.w; ++e)
+                                if (stoich_species(s_st[e]) == sp) dv += stoich_delta(s_st[e]);
+                            o[c] = __fmaf_rn(alpha, (float)dv, (float)X[sp * B]);
+                        }
+                        if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
                     }
-                    if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
+                    if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
+                    ++s;
                 }
-                if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
-                ++s;
             }
             // BIN: the rest of [t_k, t_{k+1}) after the last edge opens the next bin
             if (READOUT == SSA_READOUT_BIN && !cross && s > s_first)
@@ -166,7 +168,7 @@ __device__ __forceinline__ void thread_fwd_body(const FwdParams &p, const int4 *
     }
     if (REPLAY && status == SSA_TRAJ_OK && draws != n_ev) status = SSA_TRAJ_REPLAY_MISMATCH;
     // samples after the last state hold it (absorbed, capped, rejected or bad input)
-    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs);
+    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs, bruns);
     for (; READOUT != SSA_READOUT_BIN && s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;

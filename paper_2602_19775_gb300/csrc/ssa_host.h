@@ -34,7 +34,7 @@ struct ssa_grn {
 namespace ssa {
 struct WsLayout {
     size_t flag, counts, k_rates, ts, obs_sp, draws, status;
-    size_t xfinal, ev, ckpt, brk_k, brk_a, brk_tail, partial, dA;
+    size_t xfinal, ev, ckpt, brk_k, brk_a, brk_s, brk_tail, bin_prefix, partial, dA;
     size_t total;
     int64_t ev_rows, n_ckpt, max_blocks;
     int M_pad;

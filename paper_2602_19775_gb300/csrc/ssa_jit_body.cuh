@@ -78,6 +78,8 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
     float E[NQ], En[NQ];
     step_noise<NQ>(E, 0u, c2, c3, key0, key1);
     float bacc[kBinMaxObs];
+    BinRuns bruns;
+    bin_runs_init(bruns);
     int osp[kBinMaxObs];
     jit_bin_init(p, bad_obs, bacc, osp);
     auto xobs = [&](int c) { return jit_xsel(X, osp[c]); };
@@ -114,25 +116,25 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
         if (status != SSA_TRAJ_OK) break;
         if (slow) {
             const int s_first = s;
-            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
-                if (READOUT == SSA_READOUT_HOLD) {
-                    int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
-                } else if (READOUT == SSA_READOUT_BIN) {
-                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_first, o);
-                    if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
-                } else {
-                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
-                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    for (int c = 0; c < p.n_obs; ++c) {
-                        const int sp = p.obs_sp[c];
-                        o[c] = __fmaf_rn(alpha, (float)jit_dv(jb, sp), (float)jit_xsel(X, sp));
+            if constexpr (READOUT == SSA_READOUT_BIN) {
+                s = bin_edges<RECORD>(p, i, s, t, t_next, k, bacc, xobs, bruns);
+            } else {
+                while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
+                    if (READOUT == SSA_READOUT_HOLD) {
+                        int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                        for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
+                    } else {
+                        const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
+                        float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                        for (int c = 0; c < p.n_obs; ++c) {
+                            const int sp = p.obs_sp[c];
+                            o[c] = __fmaf_rn(alpha, (float)jit_dv(jb, sp), (float)jit_xsel(X, sp));
+                        }
+                        if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
                     }
-                    if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
+                    if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
+                    ++s;
                 }
-                if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
-                ++s;
             }
             if (READOUT == SSA_READOUT_BIN && !cross && s > s_first)
                 bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
@@ -154,7 +156,7 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) E[q] = En[q];
     }
-    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs);
+    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs, bruns);
     for (; READOUT != SSA_READOUT_BIN && s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
@@ -219,6 +221,8 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
     uint4 r = philox4x32_10(make_uint4(0u, 0u, c2, c3), key0, key1);
     float E0 = neg_log_unit(u01(r.x)), U1 = u01(r.y);
     float bacc[kBinMaxObs];
+    BinRuns bruns;
+    bin_runs_init(bruns);
     int osp[kBinMaxObs];
     jit_bin_init(p, bad_obs, bacc, osp);
     auto xobs = [&](int c) { return jit_xsel(X, osp[c]); };
@@ -254,23 +258,23 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
         if (status != SSA_TRAJ_OK) break;
         if (slow) {
             const int s_first = s;
-            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
-                if (READOUT == SSA_READOUT_HOLD) {
-                    int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
-                } else if (READOUT == SSA_READOUT_BIN) {
-                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_first, o);
-                    (void)d;
-                } else {
-                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
-                    float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                    for (int c = 0; c < p.n_obs; ++c) {
-                        const int sp = p.obs_sp[c];
-                        o[c] = __fmaf_rn(alpha, (float)jit_dv(jb, sp), (float)jit_xsel(X, sp));
+            if constexpr (READOUT == SSA_READOUT_BIN) {
+                s = bin_edges<false>(p, i, s, t, t_next, k, bacc, xobs, bruns);
+            } else {
+                while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
+                    if (READOUT == SSA_READOUT_HOLD) {
+                        int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                        for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
+                    } else {
+                        const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
+                        float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                        for (int c = 0; c < p.n_obs; ++c) {
+                            const int sp = p.obs_sp[c];
+                            o[c] = __fmaf_rn(alpha, (float)jit_dv(jb, sp), (float)jit_xsel(X, sp));
+                        }
                     }
+                    ++s;
                 }
-                ++s;
             }
             if (READOUT == SSA_READOUT_BIN && !cross && s > s_first)
                 bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
@@ -285,7 +289,7 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
         E0 = neg_log_unit(u01(r.x));
         U1 = u01(r.y);
     }
-    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<false>(p, i, s, t, k, bacc, xobs, bad_obs);
+    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<false>(p, i, s, t, k, bacc, xobs, bad_obs, bruns);
     for (; READOUT != SSA_READOUT_BIN && s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
@@ -330,9 +334,12 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
         return (slot & 1) ? (int)(w >> 16) : (int)(w & 0xffff);
     };
 
-    // BIN: the edges after brk_tail[i] belong to the last state and are not stored
-    int s_hi = READOUT == SSA_READOUT_BIN ? min(p.brk_tail[i], p.S - 1) : p.S - 1;
-    int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    int s_hi = p.S - 1;
+    int brk_next = (READOUT != SSA_READOUT_BIN && s_hi >= 0) ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    // BIN: one recorded slot per state interval that holds edges
+    BinSlots bslots{-1, -1};
+    float d_first = 0.0f, d_last = 0.0f;
+    if (READOUT == SSA_READOUT_BIN) bin_slots_init(bslots, p.brk_k, p.brk_tail, n, i);
     float mu = 0.0f;
     int mism = 0;
     int ck_row = L / p.K, ck_off = L - ck_row * p.K;  // checkpoint c holds X_{cK}
@@ -350,7 +357,6 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
     for (int c = 0; c < kBinMaxObs; ++c) osp[c] = (kBin && c < p.n_obs) ? p.obs_sp[c] : 0;
     auto xobs = [&](int c) { return jit_xsel(X, osp[c]); };
     auto addx = [&](int c, float v) { jit_lam_add(lam, osp[c], v); };
-    auto brk = [&](int s) { return p.brk_a[(int64_t)s * n + i]; };
     if (kBin) {
         bin_grad(gq, gl, p.n_obs, p.ts, p.S, p.S);
 #pragma unroll
@@ -359,10 +365,14 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
 
     for (int k = L; k >= 0; --k) {
         const bool draw = (k < L) || draw_last;
-        const int s_top = (READOUT == SSA_READOUT_BIN && k == L) ? p.S - 1 : s_hi;
-        while (s_hi >= 0 && brk_next == k) {
-            --s_hi;
-            brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+        const int s_top = s_hi;
+        if (READOUT == SSA_READOUT_BIN) {
+            bin_slots_step(bslots, p.brk_k, p.brk_s, p.brk_a, p.ts, n, i, k, s_hi, d_first, d_last);
+        } else {
+            while (s_hi >= 0 && brk_next == k) {
+                --s_hi;
+                brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+            }
         }
         // samples s_hi+1 .. s_top are bracketed by state k
         if (kBin) {
@@ -438,7 +448,7 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             mu += dt_dir;  // t_{k+1} = t_k + tau_k
         }
         if (kBin) {
-            bin_state_terms(addx, brk, gl, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
+            bin_state_terms(addx, d_first, d_last, gl, p.bin_prefix, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
 #pragma unroll
             for (int c = 0; c < kBinMaxObs; ++c) {
                 gq[c] = gk[c];
@@ -547,6 +557,8 @@ __device__ __forceinline__ void jit_fwd_soft(const FwdParams &p)
     float E[NQ], En[NQ];
     step_noise<NQ>(E, 0u, c2, c3, key0, key1);
     float bacc[kBinMaxObs];
+    BinRuns bruns;
+    bin_runs_init(bruns);
     int osp[kBinMaxObs];
     jit_bin_init(p, bad_obs, bacc, osp);
     auto xobs = [&](int c) { return jit_fsel(X, osp[c]); };
@@ -571,23 +583,24 @@ __device__ __forceinline__ void jit_fwd_soft(const FwdParams &p)
         if (!cross && !finite) { status = SSA_TRAJ_BAD_RATE; break; }
         if (slow) {
             const int s_first = s;
-            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
-                float *o = obs + ((int64_t)i * p.S + s) * p.n_obs;
-                if (READOUT == SSA_READOUT_HOLD) {
-                    for (int c = 0; c < p.n_obs; ++c) o[c] = jit_fsel(X, p.obs_sp[c]);
-                } else if (READOUT == SSA_READOUT_BIN) {
-                    const float d = bin_close(bacc, xobs, p.n_obs, p.ts, s, t, s == s_first, o);
-                    if (RECORD) p.brk_a[(int64_t)s * n + i] = d;
-                } else {
-                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
-                    for (int c = 0; c < p.n_obs; ++c) {
-                        const int sp = p.obs_sp[c];
-                        o[c] = __fmaf_rn(alpha, jit_fsel(dX, sp), jit_fsel(X, sp));
+            if constexpr (READOUT == SSA_READOUT_BIN) {
+                s = bin_edges<RECORD>(p, i, s, t, t_next, k, bacc, xobs, bruns);
+            } else {
+                while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
+                    float *o = obs + ((int64_t)i * p.S + s) * p.n_obs;
+                    if (READOUT == SSA_READOUT_HOLD) {
+                        for (int c = 0; c < p.n_obs; ++c) o[c] = jit_fsel(X, p.obs_sp[c]);
+                    } else {
+                        const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
+                        for (int c = 0; c < p.n_obs; ++c) {
+                            const int sp = p.obs_sp[c];
+                            o[c] = __fmaf_rn(alpha, jit_fsel(dX, sp), jit_fsel(X, sp));
+                        }
+                        if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
                     }
-                    if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
+                    if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
+                    ++s;
                 }
-                if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
-                ++s;
             }
             if (READOUT == SSA_READOUT_BIN && !cross && s > s_first)
                 bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
@@ -609,7 +622,7 @@ __device__ __forceinline__ void jit_fwd_soft(const FwdParams &p)
 #pragma unroll
         for (int q = 0; q < NQ; ++q) E[q] = En[q];
     }
-    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs);
+    if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs, bruns);
     for (; READOUT != SSA_READOUT_BIN && s < p.S; ++s) {
         float *o = obs + ((int64_t)i * p.S + s) * p.n_obs;
         for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : jit_fsel(X, p.obs_sp[c]);
@@ -645,8 +658,12 @@ __device__ __forceinline__ void jit_adj_soft_traj(const AdjParams &p, const floa
 #pragma unroll
     for (int q = 0; q < JN; ++q) lam[q] = 0.0f;
 
-    int s_hi = READOUT == SSA_READOUT_BIN ? min(p.brk_tail[i], p.S - 1) : p.S - 1;
-    int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    int s_hi = p.S - 1;
+    int brk_next = (READOUT != SSA_READOUT_BIN && s_hi >= 0) ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    // BIN: one recorded slot per state interval that holds edges
+    BinSlots bslots{-1, -1};
+    float d_first = 0.0f, d_last = 0.0f;
+    if (READOUT == SSA_READOUT_BIN) bin_slots_init(bslots, p.brk_k, p.brk_tail, n, i);
     float mu = 0.0f;
     int mism = 0;
     constexpr bool kBin = READOUT == SSA_READOUT_BIN;
@@ -655,7 +672,6 @@ __device__ __forceinline__ void jit_adj_soft_traj(const AdjParams &p, const floa
 #pragma unroll
     for (int c = 0; c < kBinMaxObs; ++c) osp[c] = (kBin && c < p.n_obs) ? p.obs_sp[c] : 0;
     auto addx = [&](int c, float v) { jit_lam_add(lam, osp[c], v); };
-    auto brk = [&](int s) { return p.brk_a[(int64_t)s * n + i]; };
     if (kBin) bin_grad(gq, gl, p.n_obs, p.ts, p.S, p.S);
 
     float Xs[kSoftK][JN];  // states k0 .. k1 of the segment being walked
@@ -685,10 +701,14 @@ __device__ __forceinline__ void jit_adj_soft_traj(const AdjParams &p, const floa
 #pragma unroll
             for (int q = 0; q < JN; ++q) Xk[q] = Xs[k - k0][q];
             const bool draw = (k < L) || draw_last;
-            const int s_top = (READOUT == SSA_READOUT_BIN && k == L) ? p.S - 1 : s_hi;
-            while (s_hi >= 0 && brk_next == k) {
-                --s_hi;
-                brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+            const int s_top = s_hi;
+            if (READOUT == SSA_READOUT_BIN) {
+                bin_slots_step(bslots, p.brk_k, p.brk_s, p.brk_a, p.ts, n, i, k, s_hi, d_first, d_last);
+            } else {
+                while (s_hi >= 0 && brk_next == k) {
+                    --s_hi;
+                    brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+                }
             }
             if (kBin) {
                 if (s_hi < s_top) bin_grad(gk, gl, p.n_obs, p.ts, p.S, s_hi + 1);
@@ -746,7 +766,7 @@ __device__ __forceinline__ void jit_adj_soft_traj(const AdjParams &p, const floa
                 mu += dt_dir;
             }
             if (kBin) {
-                bin_state_terms(addx, brk, gl, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
+                bin_state_terms(addx, d_first, d_last, gl, p.bin_prefix, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
 #pragma unroll
                 for (int q = 0; q < kBinMaxObs; ++q) gq[q] = gk[q];
             } else {

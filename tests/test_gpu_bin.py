@@ -179,3 +179,21 @@ def test_bin_input_rules_and_limits(S):
     # empty batch of trajectories
     fw = S.forward(snet, theta, 0, net.x0, 1.0, [0.5, 1.0], [0], 0, readout="bin", record=True)
     assert fw.obs.shape == (0, 2, 1)
+
+
+@pytest.mark.parametrize("specialize", [True, False])
+def test_bin_shared_upstream_gradient_matches_full(S, specialize):
+    """A loss on ensemble means gives every trajectory the same dL/dobs; passed once ([S][n_obs], stride 0)
+    the adjoint sums it over runs of whole bins by binary64 prefix sums, passed per trajectory it sums
+    bin by bin: the two gradients agree to binary32 rounding."""
+    net = W.ion_channel_coi()
+    ts = W.uniform_sample_grid(8.0, 800)
+    snet = S.Network(net)
+    theta = torch.tensor(net.log_rates.astype(np.float32), device="cuda")
+    n = 65536
+    fw = S.forward(snet, theta, n, net.x0, 8.0, ts, [1], 21, readout="bin", record=True, max_steps=64,
+                   specialize=specialize)
+    g = torch.tensor(W.seeded_dl_dobs(3, 1, 800, 1)[0] / n, dtype=torch.float32, device="cuda")
+    shared = S.backward(fw, g, 0.5).double().cpu().numpy()
+    full = S.backward(fw, g.expand(n, -1, -1).contiguous(), 0.5).double().cpu().numpy()
+    assert np.abs(shared - full).max() <= 1e-4 * np.abs(full).max(), (shared, full)
