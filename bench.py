@@ -520,6 +520,16 @@ def ion_channel_extra(ssa, dev, n: int = 262144, reps: int = 3, T: float = 0.05)
                 steps += int(fw.draws.sum().item())
             del fw
         out[mode] = {"ms": ms / reps, "ssa_steps": steps // reps, "steps_per_s": steps / (ms / 1e3)}
+    # the forward is bound by the stores of the bin rows: 4 B per bin per trajectory
+    rows = 4.0 * n * len(ts)
+    out["forward"]["bin_row_bytes"] = rows
+    out["forward"]["achieved_gbs"] = rows / (out["forward"]["ms"] / 1e3) / 1e9
+    try:
+        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        out["forward"]["hbm_frac"] = out["forward"]["achieved_gbs"] / hbm
+        out["forward"]["peak_basis"] = f"{hbm:.0f} GB/s of measured (copy)"
+    except (OSError, ValueError, KeyError):
+        out["forward"]["hbm_frac"] = None
     out["paper_context_ms_per_epoch"] = 112e3 / 400
     return out
 
