@@ -129,16 +129,34 @@ __global__ void unpack_events_kernel(const uint4 *ev, const int *draws, int64_t 
 }
 
 // Bin readout with a shared upstream gradient g [S][n_obs]: prefix[s][c] = sum_{b < s} g[b][c] in binary64,
-// for s = 0..S ([S + 1][SSA_BIN_MAX_OBS]).
-__global__ void bin_prefix_kernel(const float *g, int S, int n_obs, double *prefix)
+// for s = 0..S ([S + 1][SSA_BIN_MAX_OBS]). One block: each thread sums a contiguous chunk of bins, the chunk
+// totals are scanned in shared memory (fixed order), and each thread writes its chunk's prefixes.
+constexpr int kPrefixThreads = 256;
+__global__ void __launch_bounds__(kPrefixThreads) bin_prefix_kernel(const float *g, int S, int n_obs, double *prefix)
 {
-    const int c = threadIdx.x;
-    if (c >= SSA_BIN_MAX_OBS) return;
-    double acc = 0.0;
-    prefix[c] = 0.0;
-    for (int s = 0; s < S; ++s) {
-        if (c < n_obs) acc += (double)g[(int64_t)s * n_obs + c];
-        prefix[(int64_t)(s + 1) * SSA_BIN_MAX_OBS + c] = acc;
+    __shared__ double part[kPrefixThreads];
+    const int tid = threadIdx.x;
+    const int chunk = (S + kPrefixThreads - 1) / kPrefixThreads;
+    const int lo = min(tid * chunk, S), hi = min(lo + chunk, S);
+    for (int c = 0; c < SSA_BIN_MAX_OBS; ++c) {
+        double acc = 0.0;
+        if (c < n_obs)
+            for (int b = lo; b < hi; ++b) acc += (double)g[(int64_t)b * n_obs + c];
+        part[tid] = acc;
+        __syncthreads();
+        for (int off = 1; off < kPrefixThreads; off <<= 1) {  // inclusive scan of the chunk totals
+            const double v = tid >= off ? part[tid - off] : 0.0;
+            __syncthreads();
+            part[tid] += v;
+            __syncthreads();
+        }
+        double run = tid > 0 ? part[tid - 1] : 0.0;  // sum of the bins below this chunk
+        if (tid == 0) prefix[c] = 0.0;
+        for (int b = lo; b < hi; ++b) {
+            if (c < n_obs) run += (double)g[(int64_t)b * n_obs + c];
+            prefix[(int64_t)(b + 1) * SSA_BIN_MAX_OBS + c] = run;
+        }
+        __syncthreads();
     }
 }
 
@@ -316,7 +334,7 @@ cudaError_t launch_transpose_brackets(const int *brk, int64_t n_traj, int S, con
 
 cudaError_t launch_bin_prefix(const float *g, int S, int n_obs, double *prefix, cudaStream_t st)
 {
-    bin_prefix_kernel<<<1, 32, 0, st>>>(g, S, n_obs, prefix);
+    bin_prefix_kernel<<<1, kPrefixThreads, 0, st>>>(g, S, n_obs, prefix);
     return cudaGetLastError();
 }
 
