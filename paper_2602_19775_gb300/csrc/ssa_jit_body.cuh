@@ -197,7 +197,6 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n_traj) return;
-    const int64_t n = p.n_traj;
     float kr[JM];
 #pragma unroll
     for (int j = 0; j < JM; ++j) kr[j] = p.k_rates[j];
