@@ -197,3 +197,43 @@ def test_bin_shared_upstream_gradient_matches_full(S, specialize):
     shared = S.backward(fw, g, 0.5).double().cpu().numpy()
     full = S.backward(fw, g.expand(n, -1, -1).contiguous(), 0.5).double().cpu().numpy()
     assert np.abs(shared - full).max() <= 1e-4 * np.abs(full).max(), (shared, full)
+
+
+def test_bin_on_the_generic_runtime_loop_kernels(S):
+    """A network above the specialisation limits (M = 30) runs the generic thread kernels with runtime loops
+    over the reactions; the bin readout and its gradient still match the oracle."""
+    spec = W.random_network(np.random.default_rng(5), n_species_range=(6, 12), n_reactions_range=(30, 30))
+    from test_gpu_warp import _pilot_t_end
+    t_end = _pilot_t_end(spec, spec.log_rates.astype(np.float32).astype(np.float64))
+    ts = W.uniform_sample_grid(t_end, 9)
+    obs_sp = [0, 1, 2]
+    n = 512
+    _T_END["t_end"] = t_end
+    dl = W.seeded_dl_dobs(4, n, len(ts), len(obs_sp), scale=1.0 / n)
+    snet, fw, orc, gev = _run_both(S, spec, n, t_end, ts, obs_sp, 6, dl=dl, T=0.5, max_steps=1 << 14)
+    assert fw.run.variant == 1
+    same = _compare_events(orc, fw, gev)
+    assert same.mean() >= 0.99, same.mean()
+    _check_obs(spec, fw, orc, same, ts, np.asarray(obs_sp))
+    agree = _bracket_agreement(orc, fw, np.asarray(ts), spec.n_reactions)
+    same &= agree
+    dl_g = dl.copy()
+    dl_g[~same] = 0.0
+    g = S.backward(fw, torch.tensor(dl_g, dtype=torch.float32, device="cuda"), 0.5).double().cpu().numpy()
+    ref = orc.dtheta[same].sum(0)
+    assert np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30) < GRAD_RTOL
+
+
+@pytest.mark.parametrize("selector", ["gumbel", "soft"])
+def test_bin_shards_reproduce_the_full_run(S, selector):
+    """Trajectory ids are global: a run of ids [offset, offset + count) gives the same bin rows as the same
+    rows of one run over all ids (the sharded multi-GPU path relies on it)."""
+    net = W.ion_channel_coi()
+    ts = W.uniform_sample_grid(8.0, 100)
+    snet = S.Network(net)
+    theta = torch.tensor(net.log_rates.astype(np.float32), device="cuda")
+    kw = dict(readout="bin", max_steps=64, selector=selector, temperature=0.3 if selector == "soft" else None)
+    full = S.forward(snet, theta, 3000, net.x0, 8.0, ts, [1], 8, **kw)
+    part = S.forward(snet, theta, 1000, net.x0, 8.0, ts, [1], 8, traj_offset=1234, **kw)
+    assert torch.equal(part.obs, full.obs[1234:2234])
+    assert torch.equal(part.draws, full.draws[1234:2234])
