@@ -512,6 +512,7 @@ __device__ __forceinline__ void bin_tail(const FwdParams &p, int64_t i, int s, d
     const int lane = (int)(threadIdx.x & 31);
     const int64_t base = i - lane;
     const unsigned mask = base + 32 <= n ? 0xffffffffu : ((1u << (unsigned)(n - base)) - 1u);
+    const int writers = __popc(mask);  // the live lanes 0 .. writers-1 of the (last, partial) warp
     const int first = s + 1;  // first held row
     for (int j = 0; j < 32 && ((mask >> j) & 1u); ++j) {
         const int nj = __shfl_sync(mask, r.n, j);
@@ -521,7 +522,7 @@ __device__ __forceinline__ void bin_tail(const FwdParams &p, int64_t i, int s, d
 #pragma unroll
             for (int c = 0; c < kBinMaxObs; ++c) vq[c] = __shfl_sync(mask, r.v[q][c], j);
             float *row = obs + (base + j) * (int64_t)S * no;
-            for (int64_t e = (int64_t)lo * no + lane; e < (int64_t)(hi + 1) * no; e += 32) {
+            for (int64_t e = (int64_t)lo * no + lane; e < (int64_t)(hi + 1) * no; e += writers) {
                 const int c = no == 1 ? 0 : (int)(e % no);
                 float v = vq[0];
 #pragma unroll
@@ -535,7 +536,7 @@ __device__ __forceinline__ void bin_tail(const FwdParams &p, int64_t i, int s, d
         for (int c = 0; c < kBinMaxObs; ++c) vj[c] = __shfl_sync(mask, xv[c], j);
         if (fj >= S) continue;  // the same for every lane
         float *row = obs + (base + j) * (int64_t)S * no;
-        for (int64_t e = (int64_t)fj * no + lane; e < (int64_t)S * no; e += 32) {
+        for (int64_t e = (int64_t)fj * no + lane; e < (int64_t)S * no; e += writers) {
             const int c = no == 1 ? 0 : (int)(e % no);
             float v = vj[0];
 #pragma unroll
