@@ -164,7 +164,12 @@ def forward(net: Network, log_rates, n_traj: int, x0, t_end: float, sample_times
             replay_n_events=None,
             workspace: torch.Tensor | None = None, obs_out: torch.Tensor | None = None,
             stream=None, device=None) -> ForwardResult:
-    """ssa_forward (or ssa_forward_replay when replay_events is given) on the current stream."""
+    """ssa_forward (or ssa_forward_replay when replay_events is given) on the current stream.
+
+    readout: "hold", "linear" or "bin" (the exact bin average over (t_{s-1}, t_s], t_{-1} = 0). selector:
+    "gumbel" (the method), "direct" (the plain direct method, forward only) or "soft" (the relaxed forward of
+    Eq. 4 at `temperature`; float observables for every readout). Observables are int32 for "hold" with an
+    exact selector, float32 otherwise."""
     device = torch.device(device) if device is not None else (
         log_rates.device if isinstance(log_rates, torch.Tensor) and log_rates.is_cuda else torch.device("cuda"))
     theta = _as_cuda(log_rates, torch.float32, device)
