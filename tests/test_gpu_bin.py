@@ -260,3 +260,36 @@ def test_bin_writes_every_bin_with_a_partial_last_warp(S, selector, record, spec
     assert not np.isnan(o).any(), np.argwhere(np.isnan(o))[:5]
     if selector == "gumbel":
         assert o.min() >= 0.0 and o.max() <= 2.0
+
+
+@pytest.mark.parametrize("n", [96, 100])
+def test_bin_many_held_runs_overflow_the_run_buffer(S, n):
+    """Immigration-death at low rates on a fine grid: each interval spans tens of bins, so a trajectory
+    holds far more runs of whole bins than the per-thread buffer keeps; the runs past it are written by the
+    thread itself. Bin averages and gradients against the oracle, full and partial last warp."""
+    net = W.immigration_death(1.0, 0.1)
+    ts = W.uniform_sample_grid(100.0, 5000)
+    _T_END["t_end"] = 100.0
+    dl = W.seeded_dl_dobs(2, n, len(ts), 1, scale=1.0 / n)
+    snet, fw, orc, gev = _run_both(S, net, n, 100.0, ts, [0], 12, dl=dl, T=0.5, max_steps=2048, K=64)
+    assert np.all(fw.status.cpu().numpy() <= 1)
+    same = _compare_events(orc, fw, gev)
+    assert same.mean() >= 0.99
+    _check_obs(net, fw, orc, same, ts, np.array([0]))
+    agree = _bracket_agreement(orc, fw, np.asarray(ts), net.n_reactions)
+    same &= agree
+    dl_g = dl.copy()
+    dl_g[~same] = 0.0
+    g = S.backward(fw, torch.tensor(dl_g, dtype=torch.float32, device="cuda"), 0.5).double().cpu().numpy()
+    ref = orc.dtheta[same].sum(0)
+    assert np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30) < GRAD_RTOL
+
+
+def test_bin_without_samples(S):
+    net = W.ion_channel_coi()
+    snet = S.Network(net)
+    theta = torch.tensor(net.log_rates.astype(np.float32), device="cuda")
+    fw = S.forward(snet, theta, 64, net.x0, 8.0, np.zeros(0), [1], 0, readout="bin", record=True, max_steps=64)
+    assert fw.obs.shape == (64, 0, 1) and torch.all(fw.status <= 1)
+    g = S.backward(fw, torch.zeros(0, 1, device="cuda"), 0.5)
+    assert torch.count_nonzero(g) == 0
