@@ -47,6 +47,7 @@ cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int read
 cudaError_t jit_launch_backward(const JitKernels *k, const AdjParams &p, int readout, int block, int64_t grid,
                                 cudaStream_t st);
 constexpr int kJitBlock = 64;
+constexpr int kJitAdjBlock = 128;  // the specialised adjoint orders a block's trajectories by length over its 4 warps
 }  // namespace ssa
 
 using namespace ssa;
@@ -511,7 +512,7 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
         std::string why;
         jit = soft ? jit_soft_kernels(net, why) : jit_kernels(net, why);
         if (!jit) return fail(SSA_ERR_STATE, "specialised kernels unavailable: %s", why.c_str());
-        block = kJitBlock;
+        block = kJitAdjBlock;
         grid = (run->n_traj + block - 1) / block;
     } else if (run->variant == 1) {
         block = pick_block(adj_smem, net, 0, limit);

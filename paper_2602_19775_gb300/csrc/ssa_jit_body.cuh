@@ -788,9 +788,23 @@ template <int READOUT, bool SOFT>
 __device__ __forceinline__ void jit_adj(const AdjParams &p)
 {
     extern __shared__ float s_dA[];  // [JM][blockDim.x]
+    __shared__ int s_len[256], s_perm[256];
     const int B = blockDim.x, tid = threadIdx.x;
     const int64_t n = p.n_traj;
-    const int64_t i = (int64_t)blockIdx.x * B + tid;
+    // the threads of the block take its trajectories longest first, so that each warp walks trajectories
+    // of similar length (a warp's reverse walk lasts as long as its longest lane)
+    const int64_t i0 = (int64_t)blockIdx.x * B;
+    s_len[tid] = i0 + tid < n ? p.draws[i0 + tid] : -1;
+    __syncthreads();
+    const int key = s_len[tid];
+    int rank = 0;
+    for (int u = 0; u < B; ++u) {
+        const int ku = s_len[u];
+        rank += (ku > key) || (ku == key && u < tid);
+    }
+    s_perm[rank] = tid;
+    __syncthreads();
+    const int64_t i = i0 + s_perm[tid];
     float kr[JM], dAr[JM];
 #pragma unroll
     for (int j = 0; j < JM; ++j) {
