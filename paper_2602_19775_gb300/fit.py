@@ -100,7 +100,8 @@ def fit_start_point_map(net: Network, theta0, trainable, starts, target_rates, o
                         ) -> tuple[np.ndarray, FitHistory]:
     """RMSprop on the trainable log rates (the others stay at theta0) to match the segment rates of a batch of
     start points per iteration to their targets (mean squared error), at a fixed temperature with a geometric
-    learning-rate decay (Section 4.2). target_rates: [n_points, n_obs] for the rows of `starts`."""
+    learning-rate decay (Section 4.2). target_rates: [n_points, n_obs] for the rows of `starts`. optimizer:
+    "rmsprop" (the paper's) or "adam"."""
     dev = torch.device("cuda")
     base = torch.tensor(np.asarray(theta0, dtype=np.float32), device=dev)
     mask = torch.zeros_like(base)

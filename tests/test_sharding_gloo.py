@@ -2,7 +2,8 @@
 (with the FP64 oracle standing in for each rank's GPU) and combine them with the sharding helpers' all-
 reduces; the ensemble mean and the summed gradient equal those of one process over all ids, because
 every random number is keyed by the global trajectory id. Also checks the partition and the max/sum
-reductions the benchmark uses."""
+reductions the benchmark uses. Cases: the LINEAR readout of 2A <-> B, and the bin readout of the ion
+channel with the exact and with the soft forward."""
 import os
 import socket
 
@@ -38,18 +39,30 @@ def _free_port():
     return port
 
 
-def _rank_main(rank, world, port, n_total, out):
+def _case(kind, n_total):
+    """(network spec, log rates, x0, t_end, sample times, observed species, readout, selector) of a case."""
+    import ssa_workloads as W
+    from oracle import native
+    if kind == "c2_linear":
+        wl = W.config_c2(n_traj=n_total)
+        return wl.net, wl.log_rates, wl.x0, wl.t_end, wl.sample_times, wl.obs_species, native.LINEAR, "gumbel"
+    net = W.ion_channel_coi()
+    ts = W.uniform_sample_grid(8.0, 40)
+    sel = "soft" if kind == "ion_bin_soft" else "gumbel"
+    return net, net.log_rates, net.x0, 8.0, ts, np.array([1], np.int32), native.BIN, sel
+
+
+def _rank_main(rank, world, port, n_total, kind, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        import ssa_workloads as W
         from oracle import native
-        wl = W.config_c2(n_traj=n_total)
+        net, theta, x0, t_end, ts, obs_sp, readout, sel = _case(kind, n_total)
         off, cnt = shard_range(n_total, rank, world)
-        dl = np.full((cnt, len(wl.sample_times), 1), 1.0 / n_total)
-        r = native.run(wl.net, wl.log_rates, wl.x0, cnt, wl.t_end, wl.sample_times, wl.obs_species, 5, native.LINEAR,
-                       max_steps=4096, traj_offset=off, dl_dobs=dl, temperature=0.5, n_threads=1)
+        dl = np.full((cnt, len(ts), len(obs_sp)), 1.0 / n_total)
+        r = native.run(net, theta, x0, cnt, t_end, ts, obs_sp, 5, readout, max_steps=4096, traj_offset=off, dl_dobs=dl,
+                       temperature=0.5, n_threads=1, selector=sel)
         mean = global_ensemble_mean(torch.tensor(r.obs))
         grad = global_gradient(torch.tensor(r.dtheta.sum(0)))
         t = max_over_ranks(1.0 + rank)
@@ -60,24 +73,24 @@ def _rank_main(rank, world, port, n_total, out):
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_reproduce_one_process():
-    import ssa_workloads as W
+@pytest.mark.parametrize("kind", ["c2_linear", "ion_bin", "ion_bin_soft"])
+def test_two_gloo_ranks_reproduce_one_process(kind):
     from oracle import native
     n_total = 301  # uneven split
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, n_total, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, n_total, kind, q)) for r in range(2)]
     for p in procs:
         p.start()
     mean, grad, t, steps = q.get(timeout=300)
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    wl = W.config_c2(n_traj=n_total)
-    dl = np.full((n_total, len(wl.sample_times), 1), 1.0 / n_total)
-    r = native.run(wl.net, wl.log_rates, wl.x0, n_total, wl.t_end, wl.sample_times, wl.obs_species, 5, native.LINEAR,
-                   max_steps=4096, dl_dobs=dl, temperature=0.5, n_threads=1)
+    net, theta, x0, t_end, ts, obs_sp, readout, sel = _case(kind, n_total)
+    dl = np.full((n_total, len(ts), len(obs_sp)), 1.0 / n_total)
+    r = native.run(net, theta, x0, n_total, t_end, ts, obs_sp, 5, readout, max_steps=4096, dl_dobs=dl, temperature=0.5,
+                   n_threads=1, selector=sel)
     np.testing.assert_allclose(mean, r.obs.mean(0), rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(grad, r.dtheta.sum(0), rtol=1e-12, atol=1e-15)
     assert t == 2.0
