@@ -120,9 +120,10 @@ def st_gradient(net, log_rates, x0, events, n_states: int, crossed: bool, seed: 
 
 
 def grn_st_gradient(params, x, events, n_states: int, crossed: bool, seed: int, traj: int, sample_times,
-                    dl_dobs, temperature: float):
+                    dl_dobs, temperature: float, soft: bool = False):
     """dL/d(W1, b1, W2, b2, log_d) of L = sum(dl_dobs * obs) through the literal straight-through
-    graph of one GRN trajectory (HOLD readout of the outputs), by float64 autograd."""
+    graph of one GRN trajectory (HOLD readout of the outputs), by float64 autograd. soft: the relaxed graph
+    of Eq. 4 (the update is the soft sample itself; a negative count degrades at rate 0)."""
     W1 = torch.tensor(np.asarray(params.W1, np.float64), requires_grad=True)
     b1 = torch.tensor(np.asarray(params.b1, np.float64), requires_grad=True)
     W2 = torch.tensor(np.asarray(params.W2, np.float64), requires_grad=True)
@@ -143,7 +144,8 @@ def grn_st_gradient(params, x, events, n_states: int, crossed: bool, seed: int, 
     for k in range(len(events)):
         u = torch.as_tensor(uniforms(seed, traj, k, M + 1))
         E2 = W2 @ X[:nh] + b2
-        a = torch.cat([params.k_max * torch.sigmoid(E1), params.k_max * torch.sigmoid(E2), torch.exp(ld) * X])
+        Xd = torch.clamp(X, min=0.0) if soft else X
+        a = torch.cat([params.k_max * torch.sigmoid(E1), params.k_max * torch.sigmoid(E2), torch.exp(ld) * Xd])
         a0 = a.sum()
         tau = -torch.log(u[0]) / a0
         active = a > 0
@@ -153,7 +155,7 @@ def grn_st_gradient(params, x, events, n_states: int, crossed: bool, seed: int, 
         y_soft = torch.softmax(z, dim=0)
         y_hard = torch.zeros(M, dtype=torch.float64)
         y_hard[int(events[k])] = 1.0
-        y_st = y_soft + (y_hard - y_soft).detach()
+        y_st = y_soft if soft else y_soft + (y_hard - y_soft).detach()
         X_next = X + y_st @ V
         t_next = t + float(tau)
         if k + 1 < n_states:

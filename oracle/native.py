@@ -69,6 +69,8 @@ def _load():
         lib.orc_grn_run.restype = ctypes.c_int
         lib.orc_grn_run.argtypes = [p, i64, i64, i64, p, f64, p, i32, u64, i64, p, f64, p, p, p, p, p, p, p,
                                     p, p, i64, i32]
+        lib.orc_grn_run_sel.restype = ctypes.c_int
+        lib.orc_grn_run_sel.argtypes = [i32] + lib.orc_grn_run.argtypes
         _lib = lib
     return _lib
 
@@ -189,8 +191,9 @@ class GRNResult:
 
 def grn_run(params, x_img, traj_per_img: int, t_end: float, sample_times, seed: int, max_steps: int = 1 << 30,
             traj_offset: int = 0, dl_dobs=None, temperature: float = 1.0, ev_cap: int = 0,
-            n_threads: int | None = None) -> GRNResult:
-    """GRN oracle (FP64): HOLD readout of the output genes at the sample times."""
+            n_threads: int | None = None, soft: bool = False) -> GRNResult:
+    """GRN oracle (FP64): HOLD readout of the output genes at the sample times. soft: the relaxed forward
+    of Eq. 4 at `temperature` (real-valued counts) and, with dl_dobs, the exact gradient of that model."""
     lib = _load()
     W1 = np.ascontiguousarray(params.W1, dtype=np.float64)
     b1 = np.ascontiguousarray(params.b1, dtype=np.float64)
@@ -222,7 +225,7 @@ def grn_run(params, x_img, traj_per_img: int, t_end: float, sample_times, seed: 
         mg = np.zeros((n_traj, ev_cap))
     if n_threads is None:
         n_threads = min(os.cpu_count() or 1, max(1, n_traj // 4))
-    rc = lib.orc_grn_run(ctypes.byref(g), n_img, traj_per_img, traj_offset, _ptr(x), float(t_end), _ptr(ts), S,
+    rc = lib.orc_grn_run_sel(1 if soft else 0, ctypes.byref(g), n_img, traj_per_img, traj_offset, _ptr(x), float(t_end), _ptr(ts), S,
                          ctypes.c_uint64(seed), max_steps, _ptr(gl), float(temperature), _ptr(obs), _ptr(draws),
                          _ptr(status), _ptr(dE1), _ptr(dW2), _ptr(db2), _ptr(dld), _ptr(ev), _ptr(mg), ev_cap,
                          int(n_threads))

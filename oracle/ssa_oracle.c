@@ -714,6 +714,9 @@ int orc_run(const orc_network *net, int64_t n_traj, int64_t traj_offset,
 /*   degradation of s:   d_s X_s,            d_s = exp(log_d_s)                                 */
 /* The simulation, the Gumbel-max choice and the straight-through adjoint follow the same      */
 /* definitions as the mass-action oracle above; parameters are W1, b1, W2, b2 and log_d.      */
+/* With soft = 1 the forward is the relaxed one of Eq. 4 (the first training phase of Section  */
+/* 3.5): real-valued counts moved every step by the soft sample, a degradation propensity of a */
+/* negative count taken as 0, and the gradient is the exact gradient of that relaxed model.   */
 /* ======================================================================================== */
 typedef struct {
     int32_t n_in, n_hid, n_out;
@@ -748,13 +751,14 @@ typedef struct {
     int32_t *events_out;   /* [n_traj][ev_cap] or NULL */
     double *margins_out;
     int64_t ev_cap;
+    int32_t soft;          /* 1: the relaxed forward of Eq. 4 at temperature T */
     int64_t next;
     pthread_mutex_t lock;
     int error;
 } orc_grn_job;
 
-/* propensities of all M = 2 n_dyn reactions at state X (double counts) */
-static void orc_grn_prop(const orc_grn *g, const double *E1, const double *X, double *a, double *E2)
+/* propensities of all M = 2 n_dyn reactions at state X (double counts; soft: a negative count degrades at 0) */
+static void orc_grn_prop(const orc_grn *g, const double *E1, const double *X, double *a, double *E2, int soft)
 {
     const int nh = g->n_hid, no = g->n_out, nd = nh + no;
     for (int o = 0; o < no; ++o) {
@@ -764,7 +768,7 @@ static void orc_grn_prop(const orc_grn *g, const double *E1, const double *X, do
     }
     for (int i = 0; i < nh; ++i) a[i] = g->k_max * orc_sigmoid(E1[i]);
     for (int o = 0; o < no; ++o) a[nh + o] = g->k_max * orc_sigmoid(E2[o]);
-    for (int s = 0; s < nd; ++s) a[nd + s] = exp(g->log_d[s]) * X[s];
+    for (int s = 0; s < nd; ++s) a[nd + s] = exp(g->log_d[s]) * (soft && X[s] < 0.0 ? 0.0 : X[s]);
 }
 
 static void *orc_grn_worker(void *arg)
@@ -818,7 +822,7 @@ static void *orc_grn_worker(void *arg)
                 if (!Xh || !th || !tauh || !jh || !mh) { job->error = 1; break; }
             }
             const double *X = Xh + (size_t)k * nd;
-            orc_grn_prop(g, E1, X, a, E2);
+            orc_grn_prop(g, E1, X, a, E2, job->soft);
             double a0 = 0.0;
             for (int j = 0; j < M; ++j) a0 += a[j];
             if (a0 == 0.0) { status = ORC_ABSORBED; break; }
@@ -839,8 +843,25 @@ static void *orc_grn_worker(void *arg)
             if (th[k + 1] > job->t_end) { crossed = 1; break; }
             double *Xn = Xh + (size_t)(k + 1) * nd;
             for (int s = 0; s < nd; ++s) Xn[s] = X[s];
-            if (best < nd) Xn[best] += 1.0;
-            else Xn[best - nd] -= 1.0;
+            if (job->soft) {
+                /* relaxed update (Eq. 4): production j adds y~_j to species j, degradation removes it */
+                double zmax = -INFINITY, Z = 0.0;
+                for (int j = 0; j < M; ++j) {
+                    y[j] = -INFINITY;
+                    if (a[j] > 0.0)
+                        y[j] = (log(a[j]) - log(-log(orc_uniform(job->seed, traj, (uint64_t)k, 1 + j)))) / job->T;
+                    if (y[j] > zmax) zmax = y[j];
+                }
+                for (int j = 0; j < M; ++j) { y[j] = y[j] == -INFINITY ? 0.0 : exp(y[j] - zmax); Z += y[j]; }
+                for (int j = 0; j < M; ++j) {
+                    if (j < nd) Xn[j] += y[j] / Z;
+                    else Xn[j - nd] -= y[j] / Z;
+                }
+            } else if (best < nd) {
+                Xn[best] += 1.0;
+            } else {
+                Xn[best - nd] -= 1.0;
+            }
             ++k;
         }
         if (job->error) break;
@@ -876,7 +897,7 @@ static void *orc_grn_worker(void *arg)
                 const int draw = kk < n_draws && (kk + 1 < n_states || crossed);
                 for (int s = 0; s < nd; ++s) lam_new[s] = lam[s];
                 if (draw) {
-                    orc_grn_prop(g, E1, X, a, E2);
+                    orc_grn_prop(g, E1, X, a, E2, job->soft);
                     double a0 = 0.0;
                     for (int j = 0; j < M; ++j) a0 += a[j];
                     const double tau = tauh[kk];
@@ -911,7 +932,8 @@ static void *orc_grn_worker(void *arg)
                             const int s = j - nd;
                             dld[s] += tot;
                             const double d = exp(g->log_d[s]);
-                            lam_new[s] += (a[j] > 0.0 ? psi / X[s] : 0.0) + dLda0 * d;
+                            lam_new[s] += (a[j] > 0.0 ? psi / X[s] : 0.0) +
+                                          (job->soft && X[s] < 0.0 ? 0.0 : dLda0 * d);
                         }
                     }
                     for (int o = 0; o < no; ++o) {
@@ -938,13 +960,16 @@ done:
     return NULL;
 }
 
-int orc_grn_run(const orc_grn *g, int64_t n_img, int64_t traj_per_img, int64_t traj_offset, const int32_t *x_img,
-                double t_end, const double *ts, int32_t S, uint64_t seed, int64_t max_steps,
-                const double *dL_dobs, double T, double *obs_out, int64_t *draws_out, int32_t *status_out,
-                double *dE1_out, double *dW2_out, double *db2_out, double *dlogd_out,
-                int32_t *events_out, double *margins_out, int64_t ev_cap, int32_t n_threads)
+/* soft = 1: the relaxed forward of Eq. 4 at temperature T (T > 0 required) and its exact gradient. */
+int orc_grn_run_sel(int32_t soft, const orc_grn *g, int64_t n_img, int64_t traj_per_img, int64_t traj_offset,
+                    const int32_t *x_img, double t_end, const double *ts, int32_t S, uint64_t seed, int64_t max_steps,
+                    const double *dL_dobs, double T, double *obs_out, int64_t *draws_out, int32_t *status_out,
+                    double *dE1_out, double *dW2_out, double *db2_out, double *dlogd_out,
+                    int32_t *events_out, double *margins_out, int64_t ev_cap, int32_t n_threads)
 {
     if (!g || g->n_in < 0 || g->n_hid < 1 || g->n_out < 1 || n_img < 0 || traj_per_img < 1 || S < 0) return -1;
+    if (soft != 0 && soft != 1) return -1;
+    if (soft && !(T > 0.0)) return -1;
     for (int s = 0; s < S; ++s)
         if (!(ts[s] >= 0.0 && ts[s] <= t_end) || (s > 0 && ts[s] < ts[s - 1])) return -1;
     if (dL_dobs && (!(T > 0.0) || !dE1_out || !dW2_out || !db2_out || !dlogd_out)) return -1;
@@ -955,6 +980,7 @@ int orc_grn_run(const orc_grn *g, int64_t n_img, int64_t traj_per_img, int64_t t
     job.dL_dobs = dL_dobs; job.T = T; job.obs_out = obs_out; job.draws_out = draws_out;
     job.status_out = status_out; job.dE1_out = dE1_out; job.dW2_out = dW2_out; job.db2_out = db2_out;
     job.dlogd_out = dlogd_out; job.events_out = events_out; job.margins_out = margins_out; job.ev_cap = ev_cap;
+    job.soft = soft;
     pthread_mutex_init(&job.lock, NULL);
     const int nt = n_threads > 0 ? n_threads : 1;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nt);
@@ -964,4 +990,15 @@ int orc_grn_run(const orc_grn *g, int64_t n_img, int64_t traj_per_img, int64_t t
     free(th);
     pthread_mutex_destroy(&job.lock);
     return job.error ? -1 : 0;
+}
+
+int orc_grn_run(const orc_grn *g, int64_t n_img, int64_t traj_per_img, int64_t traj_offset, const int32_t *x_img,
+                double t_end, const double *ts, int32_t S, uint64_t seed, int64_t max_steps,
+                const double *dL_dobs, double T, double *obs_out, int64_t *draws_out, int32_t *status_out,
+                double *dE1_out, double *dW2_out, double *db2_out, double *dlogd_out,
+                int32_t *events_out, double *margins_out, int64_t ev_cap, int32_t n_threads)
+{
+    return orc_grn_run_sel(0, g, n_img, traj_per_img, traj_offset, x_img, t_end, ts, S, seed, max_steps, dL_dobs, T,
+                           obs_out, draws_out, status_out, dE1_out, dW2_out, db2_out, dlogd_out, events_out,
+                           margins_out, ev_cap, n_threads);
 }

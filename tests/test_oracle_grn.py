@@ -55,3 +55,69 @@ def test_grn_without_regulation_is_immigration_death():
     mean = cme.immigration_death_mean(lam, 0.8, ts)
     se = np.sqrt(mean / n)
     assert np.all(np.abs(y.mean(0) - mean) < 3 * se), (y.mean(0), mean)
+
+
+# ---------------------------------------------------------------------------------------------
+# The soft forward of Eq. 4 on the GRN (the first training phase of Section 3.5)
+# ---------------------------------------------------------------------------------------------
+def test_soft_grn_at_low_temperature_is_the_hard_path():
+    """T -> 0: the soft sample is one-hot on the Gumbel-max choice; where every key gap exceeds 1e-4,
+    T = 1e-9 leaves exp(-1e5) on the other reactions and the soft path is the hard one exactly."""
+    p, x = _tiny()
+    ts = np.array([1.0, 3.0, 6.0])
+    hard = native.grn_run(p, x, 16, 6.0, ts, 3, ev_cap=4000)
+    soft = native.grn_run(p, x, 16, 6.0, ts, 3, ev_cap=4000, soft=True, temperature=1e-9)
+    clear = np.array([np.nanmin(hard.margins[i, :hard.draws[i]]) > 1e-4 for i in range(32)])
+    assert clear.sum() >= 8
+    np.testing.assert_array_equal(soft.obs[clear], hard.obs[clear])
+    np.testing.assert_array_equal(soft.events[clear], hard.events[clear])
+
+
+def _soft_refs(r, i, x):
+    return {"W1": np.outer(r.dE1[i], x), "b1": r.dE1[i], "W2": r.dW2[i], "b2": r.db2[i], "log_d": r.dlogd[i]}
+
+
+def test_soft_grn_hand_adjoint_matches_autograd():
+    """The exact gradient of the relaxed GRN (hand adjoint along the soft path) against float64 autograd of
+    the relaxed graph at two temperatures; relaxed counts go below 0 at both (about 6% of the output samples at
+    T = 0.6), so the clipped degradation (a zero propensity, masked from the soft sample) is exercised. With
+    the HOLD readout the waiting time carries no gradient, so the clip's own derivative never enters."""
+    p, x = _tiny()
+    ts = np.array([1.0, 3.0, 6.0])
+    for T in (0.6, 3.0):
+        dl = np.random.default_rng(5).standard_normal((4, 3, 3))
+        r = native.grn_run(p, x, 2, 6.0, ts, 9, dl_dobs=dl, temperature=T, ev_cap=4000, soft=True)
+        assert np.all(r.status == 0)
+        for i in range(4):
+            nd = int(r.draws[i])
+            g = autodiff.grn_st_gradient(p, x[i // 2], r.events[i, :nd], nd, True, 9, i, ts, dl[i], T, soft=True)
+            ref = _soft_refs(r, i, x[i // 2])
+            for k in g:
+                scale = max(np.abs(g[k]).max(), 1e-300)
+                assert np.abs(g[k] - ref[k]).max() / scale < 1e-9, (T, i, k)
+
+
+def test_soft_grn_gradient_matches_finite_differences():
+    """For fixed noise the soft path is smooth in the parameters (while its step count does not change),
+    so the relaxed model's gradient is the limit of central differences."""
+    import dataclasses
+    p, x = _tiny()
+    p = dataclasses.replace(p, W1=p.W1.astype(np.float64), b1=p.b1.astype(np.float64), W2=p.W2.astype(np.float64),
+                            b2=p.b2.astype(np.float64), log_d=p.log_d.astype(np.float64))
+    ts = np.array([1.0, 3.0, 6.0])
+    T, h = 0.8, 1e-6
+    dl = np.random.default_rng(6).standard_normal((4, 3, 3))
+    base = native.grn_run(p, x, 2, 6.0, ts, 13, dl_dobs=dl, temperature=T, soft=True)
+    for name, idx in (("b2", (1,)), ("W2", (0, 2)), ("log_d", (5,)), ("b1", (2,)), ("W1", (1, 4))):
+        arr = getattr(p, name)
+        plus, minus = arr.copy(), arr.copy()
+        plus[idx] += h
+        minus[idx] -= h
+        rp = native.grn_run(dataclasses.replace(p, **{name: plus}), x, 2, 6.0, ts, 13, temperature=T, soft=True)
+        rm = native.grn_run(dataclasses.replace(p, **{name: minus}), x, 2, 6.0, ts, 13, temperature=T, soft=True)
+        same = (rp.draws == base.draws) & (rm.draws == base.draws)
+        assert same.sum() >= 3
+        fd = ((rp.obs - rm.obs) * dl).sum((1, 2)) / (2 * h)
+        for i in np.nonzero(same)[0]:
+            g = _soft_refs(base, i, x[i // 2])[name][idx]
+            assert abs(fd[i] - g) <= 1e-5 * max(abs(g), 1e-3), (name, i, fd[i], g)
