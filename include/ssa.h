@@ -247,6 +247,8 @@ size_t ssa_grn_workspace_bytes(const ssa_grn *g, int64_t n_img, int64_t traj_per
  *   b2 device float [n_out], log_d device float [n_hid + n_out]; x_img device int32 [n_img][n_in].
  *   opts->readout must be SSA_READOUT_HOLD. obs_out device int32 [n_img * traj_per_img][S][n_out].
  *   The weights, b2 and x_img must stay alive until the backward.
+ *   opts->selector SSA_SELECT_SOFT (temperature > 0, record = 0): the soft forward of Eq. 4 (the first
+ *   training phase of Section 3.5), relaxed counts, forward only; obs_out then holds float values.
  */
 ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, const float *b1, const uint16_t *W2,
                            const float *b2, const float *log_d, int64_t n_img, int64_t traj_per_img,

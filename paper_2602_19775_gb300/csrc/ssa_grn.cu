@@ -325,6 +325,116 @@ __global__ void __launch_bounds__(128) grn_fwd_kernel(const GrnParams p, int rec
 }
 
 // ---------------------------------------------------------------------------------------------
+// soft forward (Section 3.3, Eq. 4; the first training phase of Section 3.5): one warp per trajectory and
+// real-valued counts. Every step all reactions enter the soft sample y~ = softmax((log a + G)/T) of the same
+// Gumbel noise, and every count moves by its expected change y~_prod - y~_deg; a negative count degrades at
+// rate 0. E2 = W2 h + b2 is recomputed from the relaxed hidden counts (binary32 W2). Forward only; the
+// outputs are written as float counts.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, float *obs)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int nh = p.n_hid, no = p.n_out, nd = p.n_dyn, M = p.M;
+    const int ndp = (nd + 3) & ~3, nhp = (nh + 3) & ~3, nop = (no + 3) & ~3, Mq = (M + 3) & ~3;
+    float *s_W2 = reinterpret_cast<float *>(smem);  // [no][nh]
+    float *s_d = s_W2 + (size_t)no * nh;            // [nd]
+    float *s_b2 = s_d + nd;                         // [no]
+    float *X = s_b2 + nop + (size_t)wib * (ndp + nhp + nop + Mq);
+    float *aH = X + ndp;   // production of the hidden genes: constant per image
+    float *aO = aH + nhp;  // production of the outputs
+    float *q = aO + nop;   // per reaction: key, then unnormalised soft weight
+    for (int u = threadIdx.x; u < no * nh; u += blockDim.x) s_W2[u] = p.W2f[u];
+    for (int u = threadIdx.x; u < nd; u += blockDim.x) s_d[u] = p.dvec[u];
+    for (int u = threadIdx.x; u < no; u += blockDim.x) s_b2[u] = p.b2[u];
+    __syncthreads();
+
+    const int64_t i = (int64_t)blockIdx.x * W + wib;
+    if (i >= p.n_traj) return;
+    const float *E1 = p.E1 + (i / p.tpi) * nh;
+    for (int u = lane; u < nd; u += 32) X[u] = 0.0f;
+    for (int h = lane; h < nh; h += 32) aH[h] = p.k_max * sigmoid_f(E1[h]);
+    for (int o = lane; o < no; o += 32) aO[o] = p.k_max * sigmoid_f(s_b2[o]);
+    __syncwarp();
+    const bool bad_input = (*p.flag & kErrBadSamples) != 0;
+    const uint64_t gid = p.traj_offset + (uint64_t)i;
+    const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32), key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    const float invT = p.invT;
+
+    double t = 0.0;
+    int s = 0;
+    double thr = p.S > 0 ? p.ts[0] : p.t_end;
+    int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
+    int k = 0, draws = 0;
+    while (!bad_input) {
+        if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
+        // propensities of the relaxed state and keys l_j = log2 a_j - log2 E_{1+j}
+        float a0p = 0.0f, lmaxp = -CUDART_INF_F, E0 = 0.0f;
+        for (int b = lane; b < p.nb; b += 32) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const int j = 4 * b + w - 1;
+                if (j < 0) { E0 = neg_log_unit(u01(r.x)); continue; }
+                if (j >= M) continue;
+                const float a = j < nh ? aH[j] : j < nd ? aO[j - nh] : __fmul_rn(s_d[j - nd], fmaxf(X[j - nd], 0.0f));
+                a0p = __fadd_rn(a0p, a);
+                const float l = a > 0.0f ? log2f(a) - log2f(neg_log_unit(u01(word_of(r, w)))) : -CUDART_INF_F;
+                q[j] = l;
+                lmaxp = fmaxf(lmaxp, l);
+            }
+        }
+        const float a0 = warp_sum(a0p), lmax = warp_max(lmaxp);
+        E0 = __shfl_sync(0xffffffffu, E0, 0);
+        if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
+        if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
+        __syncwarp();
+        float Zp = 0.0f;
+        for (int j = lane; j < M; j += 32) {
+            const float wgt = q[j] == -CUDART_INF_F ? 0.0f : exp2f((q[j] - lmax) * invT);
+            q[j] = wgt;
+            Zp += wgt;
+        }
+        const float invZ = __fdividef(1.0f, warp_sum(Zp));
+        const float tau = __fdividef(E0, a0);
+        const double t_next = t + f2d_pos(tau);
+        const bool slow = gt_nonneg(t_next, thr);
+        const bool cross = slow && gt_nonneg(t_next, p.t_end);
+        draws = k + 1;
+        if (slow) {
+            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
+                float *o = obs + ((int64_t)i * p.S + s) * no;
+                for (int c = lane; c < no; c += 32) o[c] = X[nh + c];
+                ++s;
+            }
+            thr = s < p.S ? p.ts[s] : p.t_end;
+            if (cross) break;
+        }
+        __syncwarp();
+        for (int u = lane; u < nd; u += 32) X[u] = __fadd_rn(X[u], (q[u] - q[nd + u]) * invZ);
+        __syncwarp();
+        for (int o = 0; o < no; ++o) {  // E2 = W2 h + b2 of the new hidden counts
+            float part = 0.0f;
+            for (int h = lane; h < nh; h += 32) part = __fmaf_rn(s_W2[(size_t)o * nh + h], X[h], part);
+            const float e2 = __fadd_rn(warp_sum(part), s_b2[o]);
+            if (lane == (o & 31)) aO[o] = p.k_max * sigmoid_f(e2);
+        }
+        __syncwarp();
+        t = t_next;
+        ++k;
+    }
+    __syncwarp();
+    for (; s < p.S; ++s) {
+        float *o = obs + ((int64_t)i * p.S + s) * no;
+        for (int c = lane; c < no; c += 32) o[c] = X[nh + c];
+    }
+    if (lane == 0) {
+        p.draws[i] = draws;
+        p.status[i] = status;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // backward: one warp per trajectory, reverse walk
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
@@ -660,6 +770,12 @@ size_t grn_fwd_smem(const ssa_grn *g)
     return 4 * ((size_t)g->n_out * g->n_hid + g->n_dyn + nop) + 16 + 4 * (size_t)kGrnWarps * (ndp + nhp + 3 * (size_t)nop);
 }
 
+size_t grn_soft_fwd_smem(const ssa_grn *g)
+{
+    const int ndp = (g->n_dyn + 3) & ~3, nhp = (g->n_hid + 3) & ~3, nop = (g->n_out + 3) & ~3, Mq = (g->M + 3) & ~3;
+    return 4 * ((size_t)g->n_out * g->n_hid + g->n_dyn + nop) + 4 * (size_t)kGrnWarps * (ndp + nhp + nop + Mq);
+}
+
 size_t grn_adj_smem(const ssa_grn *g)
 {
     const int ndp = (g->n_dyn + 3) & ~3, nhp = (g->n_hid + 3) & ~3, nop = (g->n_out + 3) & ~3;
@@ -718,8 +834,11 @@ extern "C" ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, cons
     if (run_out) *run_out = nullptr;
     if (!g || !opts) return set_error(SSA_ERR_INVALID_ARG, "NULL network or options");
     if (opts->readout != SSA_READOUT_HOLD) return set_error(SSA_ERR_UNSUPPORTED, "the GRN reads out with HOLD only");
-    if (opts->selector != SSA_SELECT_GUMBEL || opts->temperature != 0.0f)
-        return set_error(SSA_ERR_UNSUPPORTED, "the GRN runs the Gumbel-max selector");
+    const bool soft = opts->selector == SSA_SELECT_SOFT;
+    if (!soft && (opts->selector != SSA_SELECT_GUMBEL || opts->temperature != 0.0f))
+        return set_error(SSA_ERR_UNSUPPORTED, "the GRN runs the Gumbel-max selector or the soft forward");
+    if (soft && (!(opts->temperature > 0.0f) || !(opts->temperature < 3.0e38f) || opts->record))
+        return set_error(SSA_ERR_UNSUPPORTED, "the GRN's soft forward needs T > 0 and is forward only (record = 0)");
     if (opts->max_steps < 1 || opts->max_steps > 0x7fffffffLL || (opts->ckpt_interval % 8) || opts->ckpt_interval < 0)
         return set_error(SSA_ERR_INVALID_ARG, "invalid options");
     if (n_img < 0 || traj_per_img < 1 || traj_offset < 0 || S < 0 || !(t_end >= 0.0) || !(t_end < 1e300))
@@ -798,7 +917,14 @@ extern "C" ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, cons
         p.brk_k = reinterpret_cast<int *>(ws + L.brk_k);
         p.xfinal = reinterpret_cast<int *>(ws + L.xfinal);
     }
-    if (n > 0) {
+    if (n > 0 && soft) {
+        p.invT = 1.0f / opts->temperature;
+        const size_t smem = grn_soft_fwd_smem(g);
+        GRN_CUDA_TRY(cudaFuncSetAttribute(grn_soft_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        grn_soft_fwd_kernel<<<(unsigned)((n + kGrnWarps - 1) / kGrnWarps), 32 * kGrnWarps, smem, st>>>(
+            p, reinterpret_cast<float *>(obs_out));
+        GRN_CUDA_TRY(cudaGetLastError());
+    } else if (n > 0) {
         const size_t smem = grn_fwd_smem(g);
         GRN_CUDA_TRY(cudaFuncSetAttribute(grn_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         grn_fwd_kernel<<<(unsigned)((n + kGrnWarps - 1) / kGrnWarps), 32 * kGrnWarps, smem, st>>>(p, opts->record);

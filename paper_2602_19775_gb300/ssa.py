@@ -456,8 +456,9 @@ class GRNForward:
 
 def grn_forward(grn: GRN, W1, b1, W2, b2, log_d, x_img, traj_per_img: int, t_end: float, sample_times, seed: int,
                 record=True, ckpt_interval=64, max_steps=1 << 16, traj_offset=0, stream=None,
-                device="cuda") -> GRNForward:
-    """ssa_grn_forward. W1 [n_hid, n_in] and W2 [n_out, n_hid] are rounded to bf16; x_img int counts."""
+                device="cuda", soft_temperature=None) -> GRNForward:
+    """ssa_grn_forward. W1 [n_hid, n_in] and W2 [n_out, n_hid] are rounded to bf16; x_img int counts.
+    soft_temperature: run the soft forward of Eq. 4 at that T instead (forward only; float observables)."""
     dev = torch.device(device)
     W1b = _bf16_bits(W1).to(dev)
     W2b = _bf16_bits(W2).to(dev)
@@ -467,13 +468,15 @@ def grn_forward(grn: GRN, W1, b1, W2, b2, log_d, x_img, traj_per_img: int, t_end
     n_img = int(x.shape[0])
     n = n_img * int(traj_per_img)
     S = int(ts.numel())
-    opts = make_opts("hold", record, ckpt_interval, max_steps)
+    soft = soft_temperature is not None
+    opts = make_opts("hold", record and not soft, ckpt_interval, max_steps, selector="soft" if soft else "gumbel",
+                     temperature=soft_temperature)
     L = _lib.lib()
     need = int(L.ssa_grn_workspace_bytes(grn.handle, n_img, traj_per_img, S, ctypes.byref(opts)))
     if need == 0:
         raise SSAError("invalid arguments for ssa_grn_workspace_bytes")
     ws = torch.empty(need, dtype=torch.uint8, device=dev)
-    obs = torch.empty((n, S, grn.n_out), dtype=torch.int32, device=dev)
+    obs = torch.empty((n, S, grn.n_out), dtype=torch.float32 if soft else torch.int32, device=dev)
     draws = torch.empty(n, dtype=torch.int32, device=dev)
     status = torch.empty(n, dtype=torch.int32, device=dev)
     h = ctypes.c_void_p()

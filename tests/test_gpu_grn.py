@@ -79,3 +79,50 @@ def test_mnist_sized_grn_matches_oracle(S):
     p = G.grn_params(seed=5)
     x, _ = G.prototype_images(seed=5, n_img=4)
     _grn_case(S, p, x, 8, 4.0, 9, 1.0)
+
+
+@pytest.mark.parametrize("size", ["tiny", "mnist_shape"])
+def test_grn_soft_forward_matches_oracle(S, size):
+    """The soft forward of Eq. 4 on the GRN (the first training phase of Section 3.5) against the oracle's on
+    the same noise. The relaxed path is smooth in its noise, so the binary32 GPU path drifts from the binary64
+    one by roundoff amplified by the dynamics: the bound per sample is k 64 2^-24 (max|X| + 1) after k steps
+    plus 4 x the oracle's response to a perturbation of the biases and degradation rates scaled to 64 ulp;
+    required on 99% of the samples and for every sample's ensemble mean."""
+    import dataclasses
+    if size == "tiny":
+        p = G.grn_params(seed=1, n_in=5, n_hid=4, n_out=3, w1_scale=0.02, w2_scale=0.5)
+        p.b1[:] = [0.3, -0.5, 1.0, 0.0]
+        p.b2[:] = [0.2, -0.1, 0.4]
+        x = np.array([[10, 200, 3, 0, 77], [5, 5, 5, 250, 1]], np.int32)
+        tpi, t_end, T = 64, 6.0, 0.7
+    else:
+        p = G.grn_params(seed=5)
+        x, _ = G.prototype_images(seed=5, n_img=4)
+        tpi, t_end, T = 16, 4.0, 1.0
+    ts = np.linspace(t_end / 8, t_end, 8)
+    net = S.GRN(p.n_in, p.n_hid, p.n_out, p.k_max)
+    fw = S.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, tpi, t_end, ts, 3, soft_temperature=T,
+                       max_steps=1 << 14)
+    T32 = float(np.float32(T))
+    pd = dataclasses.replace(p, W1=p.W1.astype(np.float64), b1=p.b1.astype(np.float64), W2=p.W2.astype(np.float64),
+                             b2=p.b2.astype(np.float64), log_d=p.log_d.astype(np.float64))
+    orc = native.grn_run(pd, x, tpi, t_end, ts, 3, max_steps=1 << 14, soft=True, temperature=T32, ev_cap=1 << 14)
+    st = fw.status.cpu().numpy()
+    assert np.all(st == orc.status)
+    same = fw.draws.cpu().numpy() == orc.draws
+    assert same.mean() > 0.95
+    delta = 1e-6
+    sens = np.zeros_like(orc.obs)
+    for name in ("b1", "b2", "log_d"):
+        o2 = native.grn_run(dataclasses.replace(pd, **{name: getattr(pd, name) + delta}), x, tpi, t_end, ts, 3,
+                            max_steps=1 << 14, soft=True, temperature=T32)
+        sens += np.abs(o2.obs - orc.obs)
+    amp = 4 * 64 * 2.0 ** -24 / delta * sens
+    obs = fw.obs.double().cpu().numpy()
+    idx = np.nonzero(same)[0]
+    k = orc.draws[idx].astype(float)[:, None, None]
+    xmax = np.abs(orc.obs[idx]).max(axis=(1, 2), keepdims=True) + 1.0
+    bound = (k + 1) * 64 * 2.0 ** -24 * xmax + amp[idx]
+    err = np.abs(obs[idx] - orc.obs[idx])
+    assert (err <= bound).mean() >= 0.99, ((err <= bound).mean(), err.max())
+    assert np.all(np.abs((obs[idx] - orc.obs[idx]).mean(0)) <= bound.mean(0))
