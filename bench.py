@@ -770,6 +770,20 @@ def grn_extra(ssa, dev, n_img: int = 512, tpi: int = 64, t_end: float = 20.0, re
            "ssa_steps": steps, "forward_ms": fwd_ms, "backward_ms": adj_ms,
            "fwd_steps_per_s": steps / (fwd_ms / 1e3), "fwd_adj_steps_per_s": steps / ((fwd_ms + adj_ms) / 1e3),
            "non_ok_trajectories": bad}
+    # the soft forward of Eq. 4 (the first training phase of Section 3.5) on the same inputs, at T = 1
+    soft_ms, soft_steps = 0.0, 0
+    for r in range(reps + 1):
+        ev[0].record(stream)
+        fw = ssa.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, tpi, t_end, [t_end], 70 + r,
+                             max_steps=1 << 14, soft_temperature=1.0)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if r >= 1:
+            soft_ms += ev[0].elapsed_time(ev[1])
+            soft_steps += int(fw.draws.sum().item())
+        del fw
+    out["soft_forward"] = {"ms": soft_ms / reps, "ssa_steps": soft_steps // reps,
+                           "steps_per_s": soft_steps / (soft_ms / 1e3), "temperature": 1.0}
     # the tensor-core kernel alone: the GRN's contraction (8 six-bit limbs of W1 against 512 images)
     # and a large square product
     gem = {}
