@@ -328,10 +328,76 @@ __global__ void __launch_bounds__(128) grn_fwd_kernel(const GrnParams p, int rec
 // soft forward (Section 3.3, Eq. 4; the first training phase of Section 3.5): one warp per trajectory and
 // real-valued counts. Every step all reactions enter the soft sample y~ = softmax((log a + G)/T) of the same
 // Gumbel noise, and every count moves by its expected change y~_prod - y~_deg; a negative count degrades at
-// rate 0. E2 = W2 h + b2 is recomputed from the relaxed hidden counts (binary32 W2). Forward only; the
-// outputs are written as float counts.
+// rate 0. E2 = W2 h + b2 is recomputed from the relaxed hidden counts (binary32 W2). The step is one shared
+// routine, so the adjoint's re-runs from the float checkpoints reproduce the forward's states bit for bit.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, float *obs)
+namespace {
+
+constexpr int kGrnSoftK = 8;  // float checkpoints of the soft forward every 8 steps
+
+// output propensities k_max sigma(W2 h + b2) of the relaxed state X (the warp's lanes cooperate)
+__device__ __forceinline__ void grn_soft_outputs(const GrnParams &p, const float *s_W2, const float *s_b2,
+                                                 const float *X, float *aO, int lane)
+{
+    const int nh = p.n_hid, no = p.n_out;
+    for (int o = 0; o < no; ++o) {
+        float part = 0.0f;
+        for (int h = lane; h < nh; h += 32) part = __fmaf_rn(s_W2[(size_t)o * nh + h], X[h], part);
+        const float e2 = __fadd_rn(warp_sum(part), s_b2[o]);
+        if (lane == (o & 31)) aO[o] = p.k_max * sigmoid_f(e2);
+    }
+    __syncwarp();
+}
+
+// one soft step from state X at step k: propensities (into aj if given), keys, then the unnormalised
+// weights q_j = exp2((l_j - l_max)/T); returns a0 and sets E0 and invZ = 1/sum q
+__device__ __forceinline__ float grn_soft_weights(const GrnParams &p, const float *s_d, const float *X, const float *aH,
+                                                  const float *aO, float *q, float *aj, int k, uint32_t c2,
+                                                  uint32_t c3, uint32_t key0, uint32_t key1, int lane, float &E0,
+                                                  float &invZ)
+{
+    const int nh = p.n_hid, nd = p.n_dyn, M = p.M;
+    float a0p = 0.0f, lmaxp = -CUDART_INF_F, e0 = 0.0f;
+    for (int b = lane; b < p.nb; b += 32) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int j = 4 * b + w - 1;
+            if (j < 0) { e0 = neg_log_unit(u01(r.x)); continue; }
+            if (j >= M) continue;
+            const float a = j < nh ? aH[j] : j < nd ? aO[j - nh] : __fmul_rn(s_d[j - nd], fmaxf(X[j - nd], 0.0f));
+            a0p = __fadd_rn(a0p, a);
+            const float l = a > 0.0f ? log2f(a) - log2f(neg_log_unit(u01(word_of(r, w)))) : -CUDART_INF_F;
+            q[j] = l;
+            if (aj) aj[j] = a;
+            lmaxp = fmaxf(lmaxp, l);
+        }
+    }
+    const float a0 = warp_sum(a0p), lmax = warp_max(lmaxp);
+    E0 = __shfl_sync(0xffffffffu, e0, 0);
+    __syncwarp();
+    float Zp = 0.0f;
+    for (int j = lane; j < M; j += 32) {
+        const float wgt = q[j] == -CUDART_INF_F ? 0.0f : exp2f((q[j] - lmax) * p.invT);
+        q[j] = wgt;
+        Zp += wgt;
+    }
+    invZ = __fdividef(1.0f, warp_sum(Zp));
+    __syncwarp();
+    return a0;
+}
+
+// the relaxed update X += (y~_prod - y~_deg) for every dynamic species
+__device__ __forceinline__ void grn_soft_update(const GrnParams &p, float *X, const float *q, float invZ, int lane)
+{
+    const int nd = p.n_dyn;
+    for (int u = lane; u < nd; u += 32) X[u] = __fadd_rn(X[u], (q[u] - q[nd + u]) * invZ);
+    __syncwarp();
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, float *obs, int record)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, W = blockDim.x >> 5;
@@ -351,51 +417,28 @@ __global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, fl
 
     const int64_t i = (int64_t)blockIdx.x * W + wib;
     if (i >= p.n_traj) return;
+    const int64_t n = p.n_traj;
+    float *ckf = reinterpret_cast<float *>(p.ckpt);
     const float *E1 = p.E1 + (i / p.tpi) * nh;
     for (int u = lane; u < nd; u += 32) X[u] = 0.0f;
     for (int h = lane; h < nh; h += 32) aH[h] = p.k_max * sigmoid_f(E1[h]);
-    for (int o = lane; o < no; o += 32) aO[o] = p.k_max * sigmoid_f(s_b2[o]);
     __syncwarp();
+    grn_soft_outputs(p, s_W2, s_b2, X, aO, lane);
     const bool bad_input = (*p.flag & kErrBadSamples) != 0;
     const uint64_t gid = p.traj_offset + (uint64_t)i;
     const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32), key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
-    const float invT = p.invT;
 
     double t = 0.0;
     int s = 0;
     double thr = p.S > 0 ? p.ts[0] : p.t_end;
     int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
-    int k = 0, draws = 0;
+    int k = 0, draws = 0, ck_left = kGrnSoftK, ck_row = 0;
     while (!bad_input) {
         if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
-        // propensities of the relaxed state and keys l_j = log2 a_j - log2 E_{1+j}
-        float a0p = 0.0f, lmaxp = -CUDART_INF_F, E0 = 0.0f;
-        for (int b = lane; b < p.nb; b += 32) {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const int j = 4 * b + w - 1;
-                if (j < 0) { E0 = neg_log_unit(u01(r.x)); continue; }
-                if (j >= M) continue;
-                const float a = j < nh ? aH[j] : j < nd ? aO[j - nh] : __fmul_rn(s_d[j - nd], fmaxf(X[j - nd], 0.0f));
-                a0p = __fadd_rn(a0p, a);
-                const float l = a > 0.0f ? log2f(a) - log2f(neg_log_unit(u01(word_of(r, w)))) : -CUDART_INF_F;
-                q[j] = l;
-                lmaxp = fmaxf(lmaxp, l);
-            }
-        }
-        const float a0 = warp_sum(a0p), lmax = warp_max(lmaxp);
-        E0 = __shfl_sync(0xffffffffu, E0, 0);
+        float E0, invZ;
+        const float a0 = grn_soft_weights(p, s_d, X, aH, aO, q, nullptr, k, c2, c3, key0, key1, lane, E0, invZ);
         if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
         if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
-        __syncwarp();
-        float Zp = 0.0f;
-        for (int j = lane; j < M; j += 32) {
-            const float wgt = q[j] == -CUDART_INF_F ? 0.0f : exp2f((q[j] - lmax) * invT);
-            q[j] = wgt;
-            Zp += wgt;
-        }
-        const float invZ = __fdividef(1.0f, warp_sum(Zp));
         const float tau = __fdividef(E0, a0);
         const double t_next = t + f2d_pos(tau);
         const bool slow = gt_nonneg(t_next, thr);
@@ -405,32 +448,190 @@ __global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, fl
             while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
                 float *o = obs + ((int64_t)i * p.S + s) * no;
                 for (int c = lane; c < no; c += 32) o[c] = X[nh + c];
+                if (record && lane == 0) p.brk_k[(int64_t)s * n + i] = k;
                 ++s;
             }
             thr = s < p.S ? p.ts[s] : p.t_end;
             if (cross) break;
         }
-        __syncwarp();
-        for (int u = lane; u < nd; u += 32) X[u] = __fadd_rn(X[u], (q[u] - q[nd + u]) * invZ);
-        __syncwarp();
-        for (int o = 0; o < no; ++o) {  // E2 = W2 h + b2 of the new hidden counts
-            float part = 0.0f;
-            for (int h = lane; h < nh; h += 32) part = __fmaf_rn(s_W2[(size_t)o * nh + h], X[h], part);
-            const float e2 = __fadd_rn(warp_sum(part), s_b2[o]);
-            if (lane == (o & 31)) aO[o] = p.k_max * sigmoid_f(e2);
-        }
-        __syncwarp();
+        grn_soft_update(p, X, q, invZ, lane);
+        grn_soft_outputs(p, s_W2, s_b2, X, aO, lane);
         t = t_next;
         ++k;
+        if (record && --ck_left == 0) {
+            ck_left = kGrnSoftK;
+            ++ck_row;
+            for (int u = lane; u < nd; u += 32) ckf[((int64_t)ck_row * nd + u) * n + i] = X[u];
+        }
     }
     __syncwarp();
     for (; s < p.S; ++s) {
         float *o = obs + ((int64_t)i * p.S + s) * no;
         for (int c = lane; c < no; c += 32) o[c] = X[nh + c];
+        if (record && lane == 0) p.brk_k[(int64_t)s * n + i] = k;
     }
     if (lane == 0) {
         p.draws[i] = draws;
         p.status[i] = status;
+    }
+    if (record)
+        for (int u = lane; u < nd; u += 32) ckf[(int64_t)u * n + i] = 0.0f;  // checkpoint 0: every gene at zero
+}
+
+// ---------------------------------------------------------------------------------------------
+// soft adjoint: the exact gradient of the relaxed model (the straight-through adjoint's arithmetic along
+// the soft path). Per 8-step segment the states are re-run from their float checkpoint with the forward's
+// routines (the end must equal the next checkpoint bit for bit), then walked backwards. In the relaxed
+// model every hidden count changes every step, so dL/dW2 = sum_k G2_k h_k^T is accumulated per step in the
+// warp's shared memory and written once per trajectory.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) grn_soft_adj_kernel(const GrnParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int nh = p.n_hid, no = p.n_out, nd = p.n_dyn, M = p.M;
+    const int ndp = (nd + 3) & ~3, nhp = (nh + 3) & ~3, nop = (no + 3) & ~3, Mq = (M + 3) & ~3;
+    float *s_W2 = reinterpret_cast<float *>(smem);
+    float *s_d = s_W2 + (size_t)no * nh;
+    float *s_b2 = s_d + nd;
+    const size_t per_warp = (size_t)(kGrnSoftK + 4) * ndp + 2 * (size_t)nhp + 3 * (size_t)nop + 2 * (size_t)Mq +
+                            (size_t)no * nh;
+    float *wbase = s_b2 + nop + (size_t)wib * per_warp;
+    float *Xseg = wbase;                   // [kGrnSoftK][ndp]: the segment's states
+    float *X = Xseg + kGrnSoftK * ndp;     // working state of the re-run
+    float *lam = X + ndp;
+    float *ctd = lam + ndp;
+    float *dlogd = ctd + ndp;
+    float *aH = dlogd + ndp;
+    float *G1 = aH + nhp;
+    float *aO = G1 + nhp;
+    float *G2 = aO + nop;
+    float *db2 = G2 + nop;
+    float *q = db2 + nop;
+    float *aj = q + Mq;
+    float *dW2s = aj + Mq;                 // [no][nh]
+    for (int u = threadIdx.x; u < no * nh; u += blockDim.x) s_W2[u] = p.W2f[u];
+    for (int u = threadIdx.x; u < nd; u += blockDim.x) s_d[u] = p.dvec[u];
+    for (int u = threadIdx.x; u < no; u += blockDim.x) s_b2[u] = p.b2[u];
+    for (int u = lane; u < nd; u += 32) dlogd[u] = 0.0f;
+    for (int u = lane; u < no; u += 32) db2[u] = 0.0f;
+    __syncthreads();
+
+    const int64_t n = p.n_traj;
+    const int64_t i = (int64_t)blockIdx.x * W + wib;
+    int st = -1;
+    if (i < n) st = p.status[i];
+    const bool active = st == SSA_TRAJ_OK || st == SSA_TRAJ_ABSORBED || st == SSA_TRAJ_STEP_CAP;
+    if (active) {
+        const float *ckf = reinterpret_cast<const float *>(p.ckpt);
+        const float *E1 = p.E1 + (i / p.tpi) * nh;
+        const int d = p.draws[i];
+        const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;
+        for (int u = lane; u < nd; u += 32) lam[u] = 0.0f;
+        for (int h = lane; h < nh; h += 32) {
+            aH[h] = p.k_max * sigmoid_f(E1[h]);
+            G1[h] = 0.0f;
+        }
+        for (int u = lane; u < no * nh; u += 32) dW2s[u] = 0.0f;
+        __syncwarp();
+        const uint64_t gid = p.traj_offset + (uint64_t)i;
+        const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32), key0 = (uint32_t)p.seed,
+                       key1 = (uint32_t)(p.seed >> 32);
+        const float invT = p.invT;
+        const float *gl = p.dl_dobs + i * p.dl_stride;
+        int s_hi = p.S - 1;
+        int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+        int mism = 0;
+        for (int c = L / kGrnSoftK; c >= 0; --c) {
+            const int k0 = c * kGrnSoftK, k1 = min(k0 + kGrnSoftK - 1, L);
+            for (int u = lane; u < nd; u += 32) X[u] = ckf[((int64_t)c * nd + u) * n + i];
+            __syncwarp();
+            for (int kk = k0; kk <= k1; ++kk) {  // re-run the segment with the forward's routines
+                for (int u = lane; u < nd; u += 32) Xseg[(kk - k0) * ndp + u] = X[u];
+                __syncwarp();
+                if (kk < L) {
+                    grn_soft_outputs(p, s_W2, s_b2, X, aO, lane);
+                    float E0, invZ;
+                    grn_soft_weights(p, s_d, X, aH, aO, q, nullptr, kk, c2, c3, key0, key1, lane, E0, invZ);
+                    grn_soft_update(p, X, q, invZ, lane);
+                }
+            }
+            if (k1 < L) {
+                int bad = 0;
+                for (int u = lane; u < nd; u += 32) bad += X[u] != ckf[((int64_t)(c + 1) * nd + u) * n + i];
+                mism += __reduce_add_sync(0xffffffffu, bad);
+            }
+            for (int k = k1; k >= k0; --k) {
+                const float *Xk = Xseg + (k - k0) * ndp;
+                // the crossing draw (k = L of a finished run) moves no observed state: its adjoint is zero
+                const bool draw = k < L;
+                const int s_top = s_hi;
+                while (s_hi >= 0 && brk_next == k) {
+                    --s_hi;
+                    brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+                }
+                if (draw) {
+                    grn_soft_outputs(p, s_W2, s_b2, Xk, aO, lane);
+                    float E0, invZ;
+                    grn_soft_weights(p, s_d, Xk, aH, aO, q, aj, k, c2, c3, key0, key1, lane, E0, invZ);
+                    // W = sum_j q_j w_j / Z with w_j = +lam_s (production) or -lam_s (degradation)
+                    float Wp = 0.0f;
+                    for (int j = lane; j < M; j += 32) Wp += q[j] * (j < nd ? lam[j] : -lam[j - nd]);
+                    const float Wbar = warp_sum(Wp) * invZ;
+                    // choice-path adjoints per reaction (HOLD readout: no waiting-time path)
+                    for (int j = lane; j < M; j += 32) {
+                        const float w = j < nd ? lam[j] : -lam[j - nd];
+                        const float psi = q[j] > 0.0f ? q[j] * invZ * (w - Wbar) * invT : 0.0f;
+                        if (j < nh) {
+                            G1[j] += psi * (1.0f - __fdividef(aH[j], p.k_max));
+                        } else if (j < nd) {
+                            G2[j - nh] = psi * (1.0f - __fdividef(aO[j - nh], p.k_max));
+                        } else {
+                            const int u = j - nd;
+                            dlogd[u] += psi;
+                            ctd[u] = aj[j] > 0.0f ? __fdividef(psi, Xk[u]) : 0.0f;
+                        }
+                    }
+                    __syncwarp();
+                    for (int o = lane; o < no; o += 32) db2[o] += G2[o];
+                    for (int h = lane; h < nh; h += 32) {
+                        const float xh = Xk[h];
+                        for (int o = 0; o < no; ++o) dW2s[(size_t)o * nh + h] = __fmaf_rn(G2[o], xh, dW2s[(size_t)o * nh + h]);
+                    }
+                    for (int u = lane; u < nd; u += 32) {
+                        float acc = ctd[u];
+                        if (u < nh)
+                            for (int o = 0; o < no; ++o) acc += s_W2[(size_t)o * nh + u] * G2[o];
+                        lam[u] += acc;
+                    }
+                }
+                __syncwarp();
+                // HOLD samples of the outputs at state k
+                for (int s = s_hi + 1; s <= s_top; ++s)
+                    for (int o = lane; o < no; o += 32) lam[nh + o] += gl[(int64_t)s * no + o];
+                __syncwarp();
+            }
+        }
+        for (int h = lane; h < nh; h += 32) p.G1[i * nh + h] = G1[h];
+        float *dW2 = p.dW2t + i * (int64_t)no * nh;
+        for (int u = lane; u < no * nh; u += 32) dW2[u] = dW2s[u];
+        if (lane == 0 && mism) atomicAdd(p.mismatch, mism);
+    } else if (i < n) {
+        for (int h = lane; h < nh; h += 32) p.G1[i * nh + h] = 0.0f;
+        float *dW2 = p.dW2t + i * (int64_t)no * nh;
+        for (int u = lane; u < no * nh; u += 32) dW2[u] = 0.0f;
+    }
+    __syncthreads();
+    // fixed-order sum over the block's warps: [db2 | dlogd]
+    const int red = no + nd;
+    const float *base0 = s_b2 + nop;
+    for (int u = threadIdx.x; u < red; u += blockDim.x) {
+        float acc = 0.0f;
+        for (int w = 0; w < W; ++w) {
+            const float *wp = base0 + w * per_warp;
+            acc += u < no ? wp[(kGrnSoftK + 4) * ndp + 2 * nhp + 2 * nop + u] : wp[(kGrnSoftK + 3) * ndp + (u - no)];
+        }
+        p.partial[(int64_t)blockIdx.x * red + u] = acc;
     }
 }
 
@@ -740,7 +941,8 @@ WsLayout grn_layout(const ssa_grn *g, int64_t n_img, int64_t tpi, int32_t S, con
     L.dvec = take((size_t)g->n_dyn * 4);
     L.grid = take(16 * sizeof(int));
     if (o->record) {
-        const int K = o->ckpt_interval > 0 ? o->ckpt_interval : 64;
+        // the soft forward keeps float checkpoints every 8 steps; the hard one int counts every K
+        const int K = o->selector == SSA_SELECT_SOFT ? kGrnSoftK : o->ckpt_interval > 0 ? o->ckpt_interval : 64;
         L.ev_rows = (o->max_steps + 7) / 8;
         L.n_ckpt = o->max_steps / K + 1;
         L.max_blocks = (n + kGrnWarps - 1) / kGrnWarps;
@@ -775,6 +977,17 @@ size_t grn_soft_fwd_smem(const ssa_grn *g)
     const int ndp = (g->n_dyn + 3) & ~3, nhp = (g->n_hid + 3) & ~3, nop = (g->n_out + 3) & ~3, Mq = (g->M + 3) & ~3;
     return 4 * ((size_t)g->n_out * g->n_hid + g->n_dyn + nop) + 4 * (size_t)kGrnWarps * (ndp + nhp + nop + Mq);
 }
+
+size_t grn_soft_adj_smem(const ssa_grn *g)
+{
+    const int ndp = (g->n_dyn + 3) & ~3, nhp = (g->n_hid + 3) & ~3, nop = (g->n_out + 3) & ~3, Mq = (g->M + 3) & ~3;
+    const size_t per_warp = (size_t)(kGrnSoftK + 4) * ndp + 2 * (size_t)nhp + 3 * (size_t)nop + 2 * (size_t)Mq +
+                            (size_t)g->n_out * g->n_hid;
+    return 4 * ((size_t)g->n_out * g->n_hid + g->n_dyn + nop + (size_t)kGrnWarps * per_warp);
+}
+
+// shared memory one CTA may hold on sm_103a
+constexpr size_t kGrnMaxSmem = 227 * 1024;
 
 size_t grn_adj_smem(const ssa_grn *g)
 {
@@ -837,8 +1050,11 @@ extern "C" ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, cons
     const bool soft = opts->selector == SSA_SELECT_SOFT;
     if (!soft && (opts->selector != SSA_SELECT_GUMBEL || opts->temperature != 0.0f))
         return set_error(SSA_ERR_UNSUPPORTED, "the GRN runs the Gumbel-max selector or the soft forward");
-    if (soft && (!(opts->temperature > 0.0f) || !(opts->temperature < 3.0e38f) || opts->record))
-        return set_error(SSA_ERR_UNSUPPORTED, "the GRN's soft forward needs T > 0 and is forward only (record = 0)");
+    if (soft && (!(opts->temperature > 0.0f) || !(opts->temperature < 3.0e38f)))
+        return set_error(SSA_ERR_UNSUPPORTED, "the GRN's soft forward needs T > 0");
+    if (soft && (grn_soft_fwd_smem(g) > kGrnMaxSmem || (opts->record && grn_soft_adj_smem(g) > kGrnMaxSmem)))
+        return set_error(SSA_ERR_UNSUPPORTED, "the GRN's soft path keeps W2 (and a recorded run dL/dW2) in shared memory: "
+                                              "n_out * n_hid too large");
     if (opts->max_steps < 1 || opts->max_steps > 0x7fffffffLL || (opts->ckpt_interval % 8) || opts->ckpt_interval < 0)
         return set_error(SSA_ERR_INVALID_ARG, "invalid options");
     if (n_img < 0 || traj_per_img < 1 || traj_offset < 0 || S < 0 || !(t_end >= 0.0) || !(t_end < 1e300))
@@ -922,7 +1138,7 @@ extern "C" ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, cons
         const size_t smem = grn_soft_fwd_smem(g);
         GRN_CUDA_TRY(cudaFuncSetAttribute(grn_soft_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         grn_soft_fwd_kernel<<<(unsigned)((n + kGrnWarps - 1) / kGrnWarps), 32 * kGrnWarps, smem, st>>>(
-            p, reinterpret_cast<float *>(obs_out));
+            p, reinterpret_cast<float *>(obs_out), opts->record);
         GRN_CUDA_TRY(cudaGetLastError());
     } else if (n > 0) {
         const size_t smem = grn_fwd_smem(g);
@@ -962,6 +1178,9 @@ extern "C" ssa_status ssa_grn_backward(ssa_run *run, const float *dl_dobs, int64
     if (!run || !run->grn) return set_error(SSA_ERR_INVALID_ARG, "not a GRN run");
     if (!run->opts.record) return set_error(SSA_ERR_STATE, "the forward was not recorded");
     if (!(temperature > 0.0f)) return set_error(SSA_ERR_INVALID_ARG, "temperature must be > 0");
+    const bool soft = run->opts.selector == SSA_SELECT_SOFT;
+    if (soft && temperature != run->opts.temperature)
+        return set_error(SSA_ERR_INVALID_ARG, "the gradient of the soft forward is taken at the forward's temperature");
     if (!dW1 || !db1 || !dW2 || !db2 || !dlog_d) return set_error(SSA_ERR_INVALID_ARG, "NULL gradient output");
     if (dl_traj_stride != 0 && dl_traj_stride < (int64_t)run->S * run->n_obs)
         return set_error(SSA_ERR_INVALID_ARG, "dl_traj_stride must be 0 or >= n_samples * n_out");
@@ -1010,7 +1229,12 @@ extern "C" ssa_status ssa_grn_backward(ssa_run *run, const float *dl_dobs, int64
     p.err = flag + 1;
     const int64_t nblk = (n + kGrnWarps - 1) / kGrnWarps;
     float *red = reinterpret_cast<float *>(ws + L.red);
-    if (n > 0) {
+    if (n > 0 && soft) {
+        const size_t smem = grn_soft_adj_smem(g);
+        GRN_CUDA_TRY(cudaFuncSetAttribute(grn_soft_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        grn_soft_adj_kernel<<<(unsigned)nblk, 32 * kGrnWarps, smem, st>>>(p);
+        GRN_CUDA_TRY(cudaGetLastError());
+    } else if (n > 0) {
         const size_t smem = grn_adj_smem(g);
         GRN_CUDA_TRY(cudaFuncSetAttribute(grn_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         grn_adj_kernel<<<(unsigned)nblk, 32 * kGrnWarps, smem, st>>>(p);

@@ -448,7 +448,7 @@ class GRN:
 
 @dataclass
 class GRNForward:
-    obs: torch.Tensor       # [n_traj, S, n_out] int32
+    obs: torch.Tensor       # [n_traj, S, n_out] int32 (float32 for the soft forward)
     draws: torch.Tensor
     status: torch.Tensor
     run: Run
@@ -458,7 +458,8 @@ def grn_forward(grn: GRN, W1, b1, W2, b2, log_d, x_img, traj_per_img: int, t_end
                 record=True, ckpt_interval=64, max_steps=1 << 16, traj_offset=0, stream=None,
                 device="cuda", soft_temperature=None) -> GRNForward:
     """ssa_grn_forward. W1 [n_hid, n_in] and W2 [n_out, n_hid] are rounded to bf16; x_img int counts.
-    soft_temperature: run the soft forward of Eq. 4 at that T instead (forward only; float observables)."""
+    soft_temperature: run the soft forward of Eq. 4 at that T instead (float observables); a recorded soft run
+    is differentiated by grn_backward at the same T (the exact gradient of the relaxed model)."""
     dev = torch.device(device)
     W1b = _bf16_bits(W1).to(dev)
     W2b = _bf16_bits(W2).to(dev)
@@ -469,7 +470,7 @@ def grn_forward(grn: GRN, W1, b1, W2, b2, log_d, x_img, traj_per_img: int, t_end
     n = n_img * int(traj_per_img)
     S = int(ts.numel())
     soft = soft_temperature is not None
-    opts = make_opts("hold", record and not soft, ckpt_interval, max_steps, selector="soft" if soft else "gumbel",
+    opts = make_opts("hold", record, ckpt_interval, max_steps, selector="soft" if soft else "gumbel",
                      temperature=soft_temperature)
     L = _lib.lib()
     need = int(L.ssa_grn_workspace_bytes(grn.handle, n_img, traj_per_img, S, ctypes.byref(opts)))

@@ -126,3 +126,56 @@ def test_grn_soft_forward_matches_oracle(S, size):
     err = np.abs(obs[idx] - orc.obs[idx])
     assert (err <= bound).mean() >= 0.99, ((err <= bound).mean(), err.max())
     assert np.all(np.abs((obs[idx] - orc.obs[idx]).mean(0)) <= bound.mean(0))
+
+
+@pytest.mark.parametrize("size", ["tiny", "mnist_shape"])
+def test_grn_soft_gradient_matches_oracle(S, size):
+    """The exact gradient of the relaxed GRN (the soft forward of Eq. 4, differentiated along its own path) against
+    the oracle's on the same noise. One sample at t_end reads the last state, so a trajectory with the oracle's
+    draw count has the oracle's bracket; the others (a crossing decided within the clock tolerance) are left out.
+    The path is smooth in its parameters, so binary32 against binary64 differ by roundoff: over the 1e2 steps of
+    these runs about 1e2 x 64 ulp per trajectory at worst, averaging down over the ensemble: 2e-3 in norm."""
+    import dataclasses
+    if size == "tiny":
+        p = G.grn_params(seed=1, n_in=5, n_hid=4, n_out=3, w1_scale=0.02, w2_scale=0.5)
+        p.b1[:] = [0.3, -0.5, 1.0, 0.0]
+        p.b2[:] = [0.2, -0.1, 0.4]
+        x = np.array([[10, 200, 3, 0, 77], [5, 5, 5, 250, 1]], np.int32)
+        tpi, t_end, T = 128, 6.0, 0.7
+    else:
+        p = G.grn_params(seed=5)
+        x, _ = G.prototype_images(seed=5, n_img=4)
+        tpi, t_end, T = 16, 1.0, 1.0
+    n = x.shape[0] * tpi
+    ts = np.array([t_end])
+    T32 = float(np.float32(T))
+    dl = np.random.default_rng(21).standard_normal((n, 1, p.n_out)) / n
+    net = S.GRN(p.n_in, p.n_hid, p.n_out, p.k_max)
+    fw = S.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, tpi, t_end, ts, 13, soft_temperature=T,
+                       max_steps=1 << 12)
+    pd = dataclasses.replace(p, W1=p.W1.astype(np.float64), b1=p.b1.astype(np.float64), W2=p.W2.astype(np.float64),
+                             b2=p.b2.astype(np.float64), log_d=p.log_d.astype(np.float64))
+    orc = native.grn_run(pd, x, tpi, t_end, ts, 13, max_steps=1 << 12, soft=True, temperature=T32, dl_dobs=dl,
+                         ev_cap=1 << 12)
+    assert np.all(fw.status.cpu().numpy() == orc.status)
+    same = fw.draws.cpu().numpy() == orc.draws
+    assert same.mean() > 0.95
+    dl_g = dl.copy()
+    dl_g[~same] = 0
+    g = S.grn_backward(fw, torch.tensor(dl_g, dtype=torch.float32, device="cuda"), T)
+    _, mism = fw.run.status_counts()
+    assert mism == 0  # every re-run segment ends on its checkpoint, bit for bit
+    masked = native.GRNResult(orc.obs, orc.draws, orc.status, orc.dE1 * same[:, None], orc.dW2 * same[:, None, None],
+                              orc.db2 * same[:, None], orc.dlogd * same[:, None], None, None)
+    ref = masked.grads(x, tpi)
+    errs = {k: np.linalg.norm(g[k].double().cpu().numpy() - ref[k]) / max(np.linalg.norm(ref[k]), 1e-300)
+            for k in ref}
+    assert all(e < 2e-3 for e in errs.values()), errs
+    # the observables of a recorded soft run are those of an unrecorded one
+    fw2 = S.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, tpi, t_end, ts, 13, soft_temperature=T,
+                        max_steps=1 << 12, record=False)
+    assert torch.equal(fw.obs, fw2.obs)
+    with pytest.raises(RuntimeError):  # the relaxed model's gradient is at its own temperature
+        S.grn_backward(fw, torch.tensor(dl_g, dtype=torch.float32, device="cuda"), 2 * T)
+    with pytest.raises(RuntimeError):  # a soft run keeps no event log
+        fw.run.events(16)
