@@ -784,6 +784,33 @@ def grn_extra(ssa, dev, n_img: int = 512, tpi: int = 64, t_end: float = 20.0, re
         del fw
     out["soft_forward"] = {"ms": soft_ms / reps, "ssa_steps": soft_steps // reps,
                            "steps_per_s": soft_steps / (soft_ms / 1e3), "temperature": 1.0}
+    # its exact gradient (the relaxed model differentiated along the soft path) on a quarter of the images: a
+    # recorded soft run keeps every dynamic count every 8 steps (about 18 GB here)
+    n_sg = max(1, n_img // 4)
+    ns = n_sg * tpi
+    xs, lab_s = x[:n_sg], lab[:ns]
+    sf_ms = sa_ms = 0.0
+    sg_steps = 0
+    for r in range(reps + 1):
+        ev[0].record(stream)
+        fw = ssa.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, xs, tpi, t_end, [t_end], 90 + r, record=True,
+                             max_steps=1 << 14, soft_temperature=1.0)
+        ev[1].record(stream)
+        dl = (torch.softmax(fw.obs[:, 0, :], dim=1) - torch.nn.functional.one_hot(lab_s, p.n_out).float()) / ns
+        ev[2].record(stream)
+        ssa.grn_backward(fw, dl.view(ns, 1, p.n_out), 1.0)
+        ev_end = torch.cuda.Event(enable_timing=True)
+        ev_end.record(stream)
+        torch.cuda.synchronize()
+        if r >= 1:
+            sf_ms += ev[0].elapsed_time(ev[1])
+            sa_ms += ev[2].elapsed_time(ev_end)
+            sg_steps += int(fw.draws.sum().item())
+        del fw
+    sf_ms, sa_ms, sg_steps = sf_ms / reps, sa_ms / reps, sg_steps // reps
+    out["soft_gradient"] = {"images": n_sg, "trajectories": ns, "ssa_steps": sg_steps, "forward_rec_ms": sf_ms,
+                            "backward_ms": sa_ms, "fwd_adj_steps_per_s": sg_steps / ((sf_ms + sa_ms) / 1e3),
+                            "temperature": 1.0}
     # the tensor-core kernel alone: the GRN's contraction (8 six-bit limbs of W1 against 512 images)
     # and a large square product
     gem = {}

@@ -64,7 +64,7 @@ struct GrnParams {
     int *err;
     int K;
     uint4 *ev;
-    int *ckpt;            // [n_ckpt][n_dyn][n_traj]
+    int *ckpt;            // hard path: [n_ckpt][n_dyn][n_traj]
     int *brk_k;           // [S][n_traj]
     int *xfinal;          // [n_dyn][n_traj]
     // backward
@@ -75,6 +75,10 @@ struct GrnParams {
     float *dW2t;          // [n_traj][n_out n_hid]: per-trajectory dL/dW2
     float *partial;       // [blocks][n_out + n_dyn]
     int *mismatch;
+    // soft path: float checkpoints [n_traj][n_ckpt][n_dyn] (trajectory-major, one warp writes a row) and the
+    // adjoint's states of the segment being walked [n_traj][8][n_dyn rounded up to 4]
+    int64_t n_ckpt;
+    float *seg;
 };
 
 namespace {
@@ -349,10 +353,10 @@ __device__ __forceinline__ void grn_soft_outputs(const GrnParams &p, const float
     __syncwarp();
 }
 
-// one soft step from state X at step k: propensities (into aj if given), keys, then the unnormalised
+// one soft step from state X at step k: propensities, keys, then the unnormalised
 // weights q_j = exp2((l_j - l_max)/T); returns a0 and sets E0 and invZ = 1/sum q
 __device__ __forceinline__ float grn_soft_weights(const GrnParams &p, const float *s_d, const float *X, const float *aH,
-                                                  const float *aO, float *q, float *aj, int k, uint32_t c2,
+                                                  const float *aO, float *q, int k, uint32_t c2,
                                                   uint32_t c3, uint32_t key0, uint32_t key1, int lane, float &E0,
                                                   float &invZ)
 {
@@ -369,7 +373,6 @@ __device__ __forceinline__ float grn_soft_weights(const GrnParams &p, const floa
             a0p = __fadd_rn(a0p, a);
             const float l = a > 0.0f ? log2f(a) - log2f(neg_log_unit(u01(word_of(r, w)))) : -CUDART_INF_F;
             q[j] = l;
-            if (aj) aj[j] = a;
             lmaxp = fmaxf(lmaxp, l);
         }
     }
@@ -436,7 +439,7 @@ __global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, fl
     while (!bad_input) {
         if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
         float E0, invZ;
-        const float a0 = grn_soft_weights(p, s_d, X, aH, aO, q, nullptr, k, c2, c3, key0, key1, lane, E0, invZ);
+        const float a0 = grn_soft_weights(p, s_d, X, aH, aO, q, k, c2, c3, key0, key1, lane, E0, invZ);
         if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
         if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
         const float tau = __fdividef(E0, a0);
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, fl
         if (record && --ck_left == 0) {
             ck_left = kGrnSoftK;
             ++ck_row;
-            for (int u = lane; u < nd; u += 32) ckf[((int64_t)ck_row * nd + u) * n + i] = X[u];
+            for (int u = lane; u < nd; u += 32) ckf[((int64_t)i * p.n_ckpt + ck_row) * nd + u] = X[u];
         }
     }
     __syncwarp();
@@ -475,17 +478,18 @@ __global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, fl
         p.status[i] = status;
     }
     if (record)
-        for (int u = lane; u < nd; u += 32) ckf[(int64_t)u * n + i] = 0.0f;  // checkpoint 0: every gene at zero
+        for (int u = lane; u < nd; u += 32) ckf[(int64_t)i * p.n_ckpt * nd + u] = 0.0f;  // checkpoint 0: all at zero
 }
 
 // ---------------------------------------------------------------------------------------------
 // soft adjoint: the exact gradient of the relaxed model (the straight-through adjoint's arithmetic along
 // the soft path). Per 8-step segment the states are re-run from their float checkpoint with the forward's
-// routines (the end must equal the next checkpoint bit for bit), then walked backwards. In the relaxed
-// model every hidden count changes every step, so dL/dW2 = sum_k G2_k h_k^T is accumulated per step in the
-// warp's shared memory and written once per trajectory.
+// routines (the end must equal the next checkpoint bit for bit) into the trajectory's row of a global
+// scratch, then walked backwards. In the relaxed model every hidden count changes every step, so
+// dL/dW2 = sum_k G2_k h_k^T takes a rank-8 update of the trajectory's dW2 row once per segment. Shared
+// memory holds W2 and ~9 KB per warp, so four 4-warp blocks share an SM.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) grn_soft_adj_kernel(const GrnParams p)
+__global__ void __launch_bounds__(128, 4) grn_soft_adj_kernel(const GrnParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, W = blockDim.x >> 5;
@@ -494,22 +498,17 @@ __global__ void __launch_bounds__(128) grn_soft_adj_kernel(const GrnParams p)
     float *s_W2 = reinterpret_cast<float *>(smem);
     float *s_d = s_W2 + (size_t)no * nh;
     float *s_b2 = s_d + nd;
-    const size_t per_warp = (size_t)(kGrnSoftK + 4) * ndp + 2 * (size_t)nhp + 3 * (size_t)nop + 2 * (size_t)Mq +
-                            (size_t)no * nh;
-    float *wbase = s_b2 + nop + (size_t)wib * per_warp;
-    float *Xseg = wbase;                   // [kGrnSoftK][ndp]: the segment's states
-    float *X = Xseg + kGrnSoftK * ndp;     // working state of the re-run
-    float *lam = X + ndp;
-    float *ctd = lam + ndp;
+    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + (2 + kGrnSoftK) * (size_t)nop + (size_t)Mq;
+    float *X = s_b2 + nop + (size_t)wib * per_warp;  // the state being stepped or differentiated
+    float *lam = X + ndp;                             // dL/dX of the state after the step
+    float *ctd = lam + ndp;                           // per species: psi of its degradation / X
     float *dlogd = ctd + ndp;
     float *aH = dlogd + ndp;
     float *G1 = aH + nhp;
     float *aO = G1 + nhp;
-    float *G2 = aO + nop;
-    float *db2 = G2 + nop;
-    float *q = db2 + nop;
-    float *aj = q + Mq;
-    float *dW2s = aj + Mq;                 // [no][nh]
+    float *db2 = aO + nop;
+    float *G2h = db2 + nop;                           // [kGrnSoftK][nop]: dL/dE2 of the segment's steps
+    float *q = G2h + kGrnSoftK * nop;
     for (int u = threadIdx.x; u < no * nh; u += blockDim.x) s_W2[u] = p.W2f[u];
     for (int u = threadIdx.x; u < nd; u += blockDim.x) s_d[u] = p.dvec[u];
     for (int u = threadIdx.x; u < no; u += blockDim.x) s_b2[u] = p.b2[u];
@@ -522,17 +521,26 @@ __global__ void __launch_bounds__(128) grn_soft_adj_kernel(const GrnParams p)
     int st = -1;
     if (i < n) st = p.status[i];
     const bool active = st == SSA_TRAJ_OK || st == SSA_TRAJ_ABSORBED || st == SSA_TRAJ_STEP_CAP;
+    if (i < n) {  // zeroed with the lane mapping of the per-segment updates
+        float *dW2 = p.dW2t + i * (int64_t)no * nh;
+        for (int h = lane; h < nh; h += 32)
+            for (int o = 0; o < no; ++o) dW2[(size_t)o * nh + h] = 0.0f;
+        if (!active)
+            for (int h = lane; h < nh; h += 32) p.G1[i * nh + h] = 0.0f;
+    }
     if (active) {
-        const float *ckf = reinterpret_cast<const float *>(p.ckpt);
+        const float *ckf = reinterpret_cast<const float *>(p.ckpt) + i * p.n_ckpt * nd;
+        float *seg = p.seg + i * (int64_t)kGrnSoftK * ndp;
+        float *dW2 = p.dW2t + i * (int64_t)no * nh;
         const float *E1 = p.E1 + (i / p.tpi) * nh;
         const int d = p.draws[i];
+        // a finished run's last draw is the crossing one, which moves no observed state
         const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;
         for (int u = lane; u < nd; u += 32) lam[u] = 0.0f;
         for (int h = lane; h < nh; h += 32) {
             aH[h] = p.k_max * sigmoid_f(E1[h]);
             G1[h] = 0.0f;
         }
-        for (int u = lane; u < no * nh; u += 32) dW2s[u] = 0.0f;
         __syncwarp();
         const uint64_t gid = p.traj_offset + (uint64_t)i;
         const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32), key0 = (uint32_t)p.seed,
@@ -544,41 +552,42 @@ __global__ void __launch_bounds__(128) grn_soft_adj_kernel(const GrnParams p)
         int mism = 0;
         for (int c = L / kGrnSoftK; c >= 0; --c) {
             const int k0 = c * kGrnSoftK, k1 = min(k0 + kGrnSoftK - 1, L);
-            for (int u = lane; u < nd; u += 32) X[u] = ckf[((int64_t)c * nd + u) * n + i];
+            for (int u = lane; u < nd; u += 32) X[u] = ckf[(int64_t)c * nd + u];
             __syncwarp();
             for (int kk = k0; kk <= k1; ++kk) {  // re-run the segment with the forward's routines
-                for (int u = lane; u < nd; u += 32) Xseg[(kk - k0) * ndp + u] = X[u];
-                __syncwarp();
+                for (int u = lane; u < nd; u += 32) seg[(kk - k0) * ndp + u] = X[u];
                 if (kk < L) {
                     grn_soft_outputs(p, s_W2, s_b2, X, aO, lane);
                     float E0, invZ;
-                    grn_soft_weights(p, s_d, X, aH, aO, q, nullptr, kk, c2, c3, key0, key1, lane, E0, invZ);
+                    grn_soft_weights(p, s_d, X, aH, aO, q, kk, c2, c3, key0, key1, lane, E0, invZ);
                     grn_soft_update(p, X, q, invZ, lane);
                 }
             }
             if (k1 < L) {
                 int bad = 0;
-                for (int u = lane; u < nd; u += 32) bad += X[u] != ckf[((int64_t)(c + 1) * nd + u) * n + i];
+                for (int u = lane; u < nd; u += 32) bad += X[u] != ckf[(int64_t)(c + 1) * nd + u];
                 mism += __reduce_add_sync(0xffffffffu, bad);
             }
             for (int k = k1; k >= k0; --k) {
-                const float *Xk = Xseg + (k - k0) * ndp;
-                // the crossing draw (k = L of a finished run) moves no observed state: its adjoint is zero
-                const bool draw = k < L;
+                float *G2 = G2h + (k - k0) * nop;
+                for (int u = lane; u < nd; u += 32) X[u] = seg[(k - k0) * ndp + u];
+                for (int o = lane; o < no; o += 32) G2[o] = 0.0f;
+                __syncwarp();
                 const int s_top = s_hi;
                 while (s_hi >= 0 && brk_next == k) {
                     --s_hi;
                     brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
                 }
-                if (draw) {
-                    grn_soft_outputs(p, s_W2, s_b2, Xk, aO, lane);
+                if (k < L) {
+                    grn_soft_outputs(p, s_W2, s_b2, X, aO, lane);
                     float E0, invZ;
-                    grn_soft_weights(p, s_d, Xk, aH, aO, q, aj, k, c2, c3, key0, key1, lane, E0, invZ);
+                    grn_soft_weights(p, s_d, X, aH, aO, q, k, c2, c3, key0, key1, lane, E0, invZ);
                     // W = sum_j q_j w_j / Z with w_j = +lam_s (production) or -lam_s (degradation)
                     float Wp = 0.0f;
                     for (int j = lane; j < M; j += 32) Wp += q[j] * (j < nd ? lam[j] : -lam[j - nd]);
                     const float Wbar = warp_sum(Wp) * invZ;
-                    // choice-path adjoints per reaction (HOLD readout: no waiting-time path)
+                    // choice-path adjoints psi_j = dL/dlog a_j (HOLD readout: no waiting-time path); a weight
+                    // q_j > 0 implies a_j > 0, so a degraded species with q_j > 0 has X > 0
                     for (int j = lane; j < M; j += 32) {
                         const float w = j < nd ? lam[j] : -lam[j - nd];
                         const float psi = q[j] > 0.0f ? q[j] * invZ * (w - Wbar) * invT : 0.0f;
@@ -589,15 +598,10 @@ __global__ void __launch_bounds__(128) grn_soft_adj_kernel(const GrnParams p)
                         } else {
                             const int u = j - nd;
                             dlogd[u] += psi;
-                            ctd[u] = aj[j] > 0.0f ? __fdividef(psi, Xk[u]) : 0.0f;
+                            ctd[u] = q[j] > 0.0f ? __fdividef(psi, X[u]) : 0.0f;
                         }
                     }
                     __syncwarp();
-                    for (int o = lane; o < no; o += 32) db2[o] += G2[o];
-                    for (int h = lane; h < nh; h += 32) {
-                        const float xh = Xk[h];
-                        for (int o = 0; o < no; ++o) dW2s[(size_t)o * nh + h] = __fmaf_rn(G2[o], xh, dW2s[(size_t)o * nh + h]);
-                    }
                     for (int u = lane; u < nd; u += 32) {
                         float acc = ctd[u];
                         if (u < nh)
@@ -611,15 +615,26 @@ __global__ void __launch_bounds__(128) grn_soft_adj_kernel(const GrnParams p)
                     for (int o = lane; o < no; o += 32) lam[nh + o] += gl[(int64_t)s * no + o];
                 __syncwarp();
             }
+            // the segment's rank-(k1 - k0 + 1) update of dL/dW2 and dL/db2
+            const int len = k1 - k0 + 1;
+            for (int h = lane; h < nh; h += 32) {
+                float xs[kGrnSoftK];
+#pragma unroll
+                for (int r = 0; r < kGrnSoftK; ++r) xs[r] = r < len ? seg[r * ndp + h] : 0.0f;
+                for (int o = 0; o < no; ++o) {
+                    float acc = dW2[(size_t)o * nh + h];
+#pragma unroll
+                    for (int r = 0; r < kGrnSoftK; ++r)
+                        if (r < len) acc = __fmaf_rn(G2h[r * nop + o], xs[r], acc);
+                    dW2[(size_t)o * nh + h] = acc;
+                }
+            }
+            for (int o = lane; o < no; o += 32)
+                for (int r = 0; r < len; ++r) db2[o] += G2h[r * nop + o];
+            __syncwarp();
         }
         for (int h = lane; h < nh; h += 32) p.G1[i * nh + h] = G1[h];
-        float *dW2 = p.dW2t + i * (int64_t)no * nh;
-        for (int u = lane; u < no * nh; u += 32) dW2[u] = dW2s[u];
         if (lane == 0 && mism) atomicAdd(p.mismatch, mism);
-    } else if (i < n) {
-        for (int h = lane; h < nh; h += 32) p.G1[i * nh + h] = 0.0f;
-        float *dW2 = p.dW2t + i * (int64_t)no * nh;
-        for (int u = lane; u < no * nh; u += 32) dW2[u] = 0.0f;
     }
     __syncthreads();
     // fixed-order sum over the block's warps: [db2 | dlogd]
@@ -629,7 +644,7 @@ __global__ void __launch_bounds__(128) grn_soft_adj_kernel(const GrnParams p)
         float acc = 0.0f;
         for (int w = 0; w < W; ++w) {
             const float *wp = base0 + w * per_warp;
-            acc += u < no ? wp[(kGrnSoftK + 4) * ndp + 2 * nhp + 2 * nop + u] : wp[(kGrnSoftK + 3) * ndp + (u - no)];
+            acc += u < no ? wp[4 * ndp + 2 * nhp + nop + u] : wp[3 * ndp + (u - no)];
         }
         p.partial[(int64_t)blockIdx.x * red + u] = acc;
     }
@@ -961,6 +976,8 @@ WsLayout grn_layout(const ssa_grn *g, int64_t n_img, int64_t tpi, int32_t S, con
         L.dW2t = take((size_t)(n > 0 ? n : 1) * g->n_out * g->n_hid * 4);
         L.dW2_chunk = std::max<int64_t>(256, (n + 65534) / 65535);
         L.dW2p = take((size_t)((n + L.dW2_chunk - 1) / L.dW2_chunk + 1) * g->n_out * g->n_hid * 4);
+        if (o->selector == SSA_SELECT_SOFT)
+            L.soft_seg = take((size_t)(n > 0 ? n : 1) * kGrnSoftK * ((g->n_dyn + 3) & ~3) * 4);
     }
     L.total = off;
     return L;
@@ -981,8 +998,7 @@ size_t grn_soft_fwd_smem(const ssa_grn *g)
 size_t grn_soft_adj_smem(const ssa_grn *g)
 {
     const int ndp = (g->n_dyn + 3) & ~3, nhp = (g->n_hid + 3) & ~3, nop = (g->n_out + 3) & ~3, Mq = (g->M + 3) & ~3;
-    const size_t per_warp = (size_t)(kGrnSoftK + 4) * ndp + 2 * (size_t)nhp + 3 * (size_t)nop + 2 * (size_t)Mq +
-                            (size_t)g->n_out * g->n_hid;
+    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + (2 + kGrnSoftK) * (size_t)nop + (size_t)Mq;
     return 4 * ((size_t)g->n_out * g->n_hid + g->n_dyn + nop + (size_t)kGrnWarps * per_warp);
 }
 
@@ -1132,6 +1148,7 @@ extern "C" ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, cons
         p.ckpt = reinterpret_cast<int *>(ws + L.ckpt);
         p.brk_k = reinterpret_cast<int *>(ws + L.brk_k);
         p.xfinal = reinterpret_cast<int *>(ws + L.xfinal);
+        p.n_ckpt = L.n_ckpt;
     }
     if (n > 0 && soft) {
         p.invT = 1.0f / opts->temperature;
@@ -1227,6 +1244,8 @@ extern "C" ssa_status ssa_grn_backward(ssa_run *run, const float *dl_dobs, int64
     p.partial = reinterpret_cast<float *>(ws + L.partial);
     p.mismatch = flag + 2;
     p.err = flag + 1;
+    p.n_ckpt = L.n_ckpt;
+    p.seg = soft ? reinterpret_cast<float *>(ws + L.soft_seg) : nullptr;
     const int64_t nblk = (n + kGrnWarps - 1) / kGrnWarps;
     float *red = reinterpret_cast<float *>(ws + L.red);
     if (n > 0 && soft) {
