@@ -247,8 +247,11 @@ size_t ssa_grn_workspace_bytes(const ssa_grn *g, int64_t n_img, int64_t traj_per
  *   b2 device float [n_out], log_d device float [n_hid + n_out]; x_img device int32 [n_img][n_in].
  *   opts->readout must be SSA_READOUT_HOLD. obs_out device int32 [n_img * traj_per_img][S][n_out].
  *   The weights, b2 and x_img must stay alive until the backward.
- *   opts->selector SSA_SELECT_SOFT (temperature > 0, record = 0): the soft forward of Eq. 4 (the first
- *   training phase of Section 3.5), relaxed counts, forward only; obs_out then holds float values.
+ *   opts->selector SSA_SELECT_SOFT (temperature > 0): the soft forward of Eq. 4 (the first training
+ *   phase of Section 3.5), relaxed counts; obs_out then holds float values. Recorded, it keeps every
+ *   count every 8 steps (opts->ckpt_interval is ignored) and ssa_grn_backward returns the exact
+ *   gradient of that relaxed model. The soft path holds W2 (n_out * n_hid floats) in shared memory:
+ *   SSA_ERR_UNSUPPORTED when it does not fit.
  */
 ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, const float *b1, const uint16_t *W2,
                            const float *b2, const float *log_d, int64_t n_img, int64_t traj_per_img,
@@ -260,7 +263,8 @@ ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, const float *b1
 /*
  * ssa_grn_backward -- the straight-through gradient (Eqs. 3, 5, 7) of a recorded GRN forward:
  * dW1 [n_hid][n_in] (tensor cores), db1 [n_hid], dW2 [n_out][n_hid], db2 [n_out],
- * dlog_d [n_hid + n_out], all device float, overwritten; dl_dobs as in ssa_backward.
+ * dlog_d [n_hid + n_out], all device float, overwritten; dl_dobs as in ssa_backward. For a soft
+ * forward, temperature must equal the forward's (SSA_ERR_INVALID_ARG otherwise).
  */
 ssa_status ssa_grn_backward(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride,
                             float temperature, float *dW1, float *db1, float *dW2, float *db2,
