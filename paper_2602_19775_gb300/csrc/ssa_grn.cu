@@ -76,7 +76,8 @@ struct GrnParams {
     float *partial;       // [blocks][n_out + n_dyn]
     int *mismatch;
     // soft path: float checkpoints [n_traj][n_ckpt][n_dyn] (trajectory-major, one warp writes a row) and the
-    // adjoint's states of the segment being walked [n_traj][8][n_dyn rounded up to 4]
+    // adjoint's scratch [n_traj][8][grn_soft_row]: per step of the segment being walked, its state, output
+    // propensities, unnormalised soft weights and 1/Z
     int64_t n_ckpt;
     float *seg;
 };
@@ -483,26 +484,37 @@ __global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, fl
 
 // ---------------------------------------------------------------------------------------------
 // soft adjoint: the exact gradient of the relaxed model (the straight-through adjoint's arithmetic along
-// the soft path). Per 8-step segment the states are re-run from their float checkpoint with the forward's
-// routines (the end must equal the next checkpoint bit for bit) into the trajectory's row of a global
-// scratch, then walked backwards. In the relaxed model every hidden count changes every step, so
-// dL/dW2 = sum_k G2_k h_k^T takes a rank-8 update of the trajectory's dW2 row once per segment. Shared
-// memory holds W2 and ~9 KB per warp, so four 4-warp blocks share an SM.
+// the soft path). Per 8-step segment the forward's own step routines re-run the states from their float
+// checkpoint (the end must equal the next checkpoint bit for bit) and leave, per step, the state, the output
+// propensities, the unnormalised soft weights and 1/Z in the trajectory's row of a global scratch; the walk
+// back reads them instead of drawing the step again. In the relaxed model every hidden count changes every
+// step, so dL/dW2 = sum_k G2_k h_k^T takes a rank-8 update of the trajectory's dW2 row once per segment.
+// Shared memory holds W2 per block and ~8 KB per warp.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 4) grn_soft_adj_kernel(const GrnParams p)
+namespace {
+
+// one step's row of the soft adjoint's segment scratch: X [ndp] | aO [nop] | q [Mq] | 1/Z and padding [4]
+__host__ __device__ inline int grn_soft_row(int nd, int no, int M)
+{
+    return ((nd + 3) & ~3) + ((no + 3) & ~3) + ((M + 3) & ~3) + 4;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128, 5) grn_soft_adj_kernel(const GrnParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, W = blockDim.x >> 5;
     const int nh = p.n_hid, no = p.n_out, nd = p.n_dyn, M = p.M;
     const int ndp = (nd + 3) & ~3, nhp = (nh + 3) & ~3, nop = (no + 3) & ~3, Mq = (M + 3) & ~3;
+    const int RS = grn_soft_row(nd, no, M);
     float *s_W2 = reinterpret_cast<float *>(smem);
     float *s_d = s_W2 + (size_t)no * nh;
     float *s_b2 = s_d + nd;
-    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + (2 + kGrnSoftK) * (size_t)nop + (size_t)Mq;
+    const size_t per_warp = 3 * (size_t)ndp + 2 * (size_t)nhp + (2 + kGrnSoftK) * (size_t)nop + (size_t)Mq;
     float *X = s_b2 + nop + (size_t)wib * per_warp;  // the state being stepped or differentiated
     float *lam = X + ndp;                             // dL/dX of the state after the step
-    float *ctd = lam + ndp;                           // per species: psi of its degradation / X
-    float *dlogd = ctd + ndp;
+    float *dlogd = lam + ndp;
     float *aH = dlogd + ndp;
     float *G1 = aH + nhp;
     float *aO = G1 + nhp;
@@ -530,7 +542,7 @@ __global__ void __launch_bounds__(128, 4) grn_soft_adj_kernel(const GrnParams p)
     }
     if (active) {
         const float *ckf = reinterpret_cast<const float *>(p.ckpt) + i * p.n_ckpt * nd;
-        float *seg = p.seg + i * (int64_t)kGrnSoftK * ndp;
+        float *seg = p.seg + i * (int64_t)kGrnSoftK * RS;
         float *dW2 = p.dW2t + i * (int64_t)no * nh;
         const float *E1 = p.E1 + (i / p.tpi) * nh;
         const int d = p.draws[i];
@@ -555,11 +567,15 @@ __global__ void __launch_bounds__(128, 4) grn_soft_adj_kernel(const GrnParams p)
             for (int u = lane; u < nd; u += 32) X[u] = ckf[(int64_t)c * nd + u];
             __syncwarp();
             for (int kk = k0; kk <= k1; ++kk) {  // re-run the segment with the forward's routines
-                for (int u = lane; u < nd; u += 32) seg[(kk - k0) * ndp + u] = X[u];
+                float *row = seg + (kk - k0) * RS;
+                for (int u = lane; u < nd; u += 32) row[u] = X[u];
                 if (kk < L) {
                     grn_soft_outputs(p, s_W2, s_b2, X, aO, lane);
                     float E0, invZ;
                     grn_soft_weights(p, s_d, X, aH, aO, q, kk, c2, c3, key0, key1, lane, E0, invZ);
+                    for (int o = lane; o < no; o += 32) row[ndp + o] = aO[o];
+                    for (int j = lane; j < M; j += 32) row[ndp + nop + j] = q[j];
+                    if (lane == 0) row[ndp + nop + Mq] = invZ;
                     grn_soft_update(p, X, q, invZ, lane);
                 }
             }
@@ -568,42 +584,44 @@ __global__ void __launch_bounds__(128, 4) grn_soft_adj_kernel(const GrnParams p)
                 for (int u = lane; u < nd; u += 32) bad += X[u] != ckf[(int64_t)(c + 1) * nd + u];
                 mism += __reduce_add_sync(0xffffffffu, bad);
             }
+            __syncwarp();  // the scratch rows were written lane-strided; the walk reads them across lanes
             for (int k = k1; k >= k0; --k) {
+                const float *row = seg + (k - k0) * RS;
                 float *G2 = G2h + (k - k0) * nop;
-                for (int u = lane; u < nd; u += 32) X[u] = seg[(k - k0) * ndp + u];
                 for (int o = lane; o < no; o += 32) G2[o] = 0.0f;
-                __syncwarp();
                 const int s_top = s_hi;
                 while (s_hi >= 0 && brk_next == k) {
                     --s_hi;
                     brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
                 }
                 if (k < L) {
-                    grn_soft_outputs(p, s_W2, s_b2, X, aO, lane);
-                    float E0, invZ;
-                    grn_soft_weights(p, s_d, X, aH, aO, q, k, c2, c3, key0, key1, lane, E0, invZ);
+                    for (int u = lane; u < nd; u += 32) X[u] = row[u];
+                    for (int o = lane; o < no; o += 32) aO[o] = row[ndp + o];
+                    const float invZ = row[ndp + nop + Mq];
                     // W = sum_j q_j w_j / Z with w_j = +lam_s (production) or -lam_s (degradation)
                     float Wp = 0.0f;
-                    for (int j = lane; j < M; j += 32) Wp += q[j] * (j < nd ? lam[j] : -lam[j - nd]);
-                    const float Wbar = warp_sum(Wp) * invZ;
-                    // choice-path adjoints psi_j = dL/dlog a_j (HOLD readout: no waiting-time path); a weight
-                    // q_j > 0 implies a_j > 0, so a degraded species with q_j > 0 has X > 0
                     for (int j = lane; j < M; j += 32) {
-                        const float w = j < nd ? lam[j] : -lam[j - nd];
-                        const float psi = q[j] > 0.0f ? q[j] * invZ * (w - Wbar) * invT : 0.0f;
-                        if (j < nh) {
+                        const float qj = row[ndp + nop + j];
+                        q[j] = qj;
+                        Wp += qj * (j < nd ? lam[j] : -lam[j - nd]);
+                    }
+                    const float Wbar = warp_sum(Wp) * invZ;
+                    __syncwarp();
+                    // choice-path adjoints psi_j = dL/dlog a_j of the productions (HOLD readout: no waiting-time path)
+                    for (int j = lane; j < nd; j += 32) {
+                        const float psi = q[j] > 0.0f ? q[j] * invZ * (lam[j] - Wbar) * invT : 0.0f;
+                        if (j < nh)
                             G1[j] += psi * (1.0f - __fdividef(aH[j], p.k_max));
-                        } else if (j < nd) {
+                        else
                             G2[j - nh] = psi * (1.0f - __fdividef(aO[j - nh], p.k_max));
-                        } else {
-                            const int u = j - nd;
-                            dlogd[u] += psi;
-                            ctd[u] = q[j] > 0.0f ? __fdividef(psi, X[u]) : 0.0f;
-                        }
                     }
                     __syncwarp();
+                    // the degradations: psi of d_u max(X_u, 0); a weight q > 0 implies a > 0, so X_u > 0 there
                     for (int u = lane; u < nd; u += 32) {
-                        float acc = ctd[u];
+                        const float qd = q[nd + u];
+                        const float psi = qd > 0.0f ? qd * invZ * (-lam[u] - Wbar) * invT : 0.0f;
+                        dlogd[u] += psi;
+                        float acc = qd > 0.0f ? __fdividef(psi, X[u]) : 0.0f;
                         if (u < nh)
                             for (int o = 0; o < no; ++o) acc += s_W2[(size_t)o * nh + u] * G2[o];
                         lam[u] += acc;
@@ -620,7 +638,7 @@ __global__ void __launch_bounds__(128, 4) grn_soft_adj_kernel(const GrnParams p)
             for (int h = lane; h < nh; h += 32) {
                 float xs[kGrnSoftK];
 #pragma unroll
-                for (int r = 0; r < kGrnSoftK; ++r) xs[r] = r < len ? seg[r * ndp + h] : 0.0f;
+                for (int r = 0; r < kGrnSoftK; ++r) xs[r] = r < len ? seg[r * RS + h] : 0.0f;
                 for (int o = 0; o < no; ++o) {
                     float acc = dW2[(size_t)o * nh + h];
 #pragma unroll
@@ -644,7 +662,7 @@ __global__ void __launch_bounds__(128, 4) grn_soft_adj_kernel(const GrnParams p)
         float acc = 0.0f;
         for (int w = 0; w < W; ++w) {
             const float *wp = base0 + w * per_warp;
-            acc += u < no ? wp[4 * ndp + 2 * nhp + nop + u] : wp[3 * ndp + (u - no)];
+            acc += u < no ? wp[3 * ndp + 2 * nhp + nop + u] : wp[2 * ndp + (u - no)];
         }
         p.partial[(int64_t)blockIdx.x * red + u] = acc;
     }
@@ -977,7 +995,7 @@ WsLayout grn_layout(const ssa_grn *g, int64_t n_img, int64_t tpi, int32_t S, con
         L.dW2_chunk = std::max<int64_t>(256, (n + 65534) / 65535);
         L.dW2p = take((size_t)((n + L.dW2_chunk - 1) / L.dW2_chunk + 1) * g->n_out * g->n_hid * 4);
         if (o->selector == SSA_SELECT_SOFT)
-            L.soft_seg = take((size_t)(n > 0 ? n : 1) * kGrnSoftK * ((g->n_dyn + 3) & ~3) * 4);
+            L.soft_seg = take((size_t)(n > 0 ? n : 1) * kGrnSoftK * grn_soft_row(g->n_dyn, g->n_out, g->M) * 4);
     }
     L.total = off;
     return L;
@@ -998,7 +1016,7 @@ size_t grn_soft_fwd_smem(const ssa_grn *g)
 size_t grn_soft_adj_smem(const ssa_grn *g)
 {
     const int ndp = (g->n_dyn + 3) & ~3, nhp = (g->n_hid + 3) & ~3, nop = (g->n_out + 3) & ~3, Mq = (g->M + 3) & ~3;
-    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + (2 + kGrnSoftK) * (size_t)nop + (size_t)Mq;
+    const size_t per_warp = 3 * (size_t)ndp + 2 * (size_t)nhp + (2 + kGrnSoftK) * (size_t)nop + (size_t)Mq;
     return 4 * ((size_t)g->n_out * g->n_hid + g->n_dyn + nop + (size_t)kGrnWarps * per_warp);
 }
 

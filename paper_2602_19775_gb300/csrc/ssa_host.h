@@ -40,7 +40,7 @@ struct WsLayout {
     int M_pad;
     // gene-regulatory-network runs
     size_t E1, W1L, xb, W2fix, W2f, dvec, grid, G1, Gimg, Gt, xT, red, dW2t, dW2p;
-    size_t soft_seg;  // soft adjoint: the states of the segment being walked
+    size_t soft_seg;  // soft adjoint: per step of the segment being walked, state, aO, weights, 1/Z
     int n_in_pad, n_img_pad, limbs, red_len;
     int64_t dW2_chunk;
 };
