@@ -47,3 +47,24 @@ def test_binding_declares_signatures_without_gpu():
     st = lib.ssa_create_network(0, 1, None, None, None, None, 1, None, ctypes.byref(h))
     assert st == -1 and b"n_species" in lib.ssa_last_error()
     assert lib.ssa_forward_workspace_bytes(None, 1, 1, None) == 0
+
+
+def test_grn_soft_path_rejects_shapes_beyond_shared_memory_without_gpu():
+    """The soft GRN kernels keep W2 (n_out x n_hid floats) in shared memory: a 4096-1024 output layer
+    (16 MiB) is refused with SSA_ERR_UNSUPPORTED before any device call, and so is a soft call at T = 0."""
+    from paper_2602_19775_gb300 import _lib
+    lib = _lib.lib()
+    g = ctypes.c_void_p()
+    assert lib.ssa_grn_create(16, 4096, 1024, ctypes.c_float(1.0), ctypes.byref(g)) == 0
+    try:
+        opts = _lib.FwdOpts(_lib.SSA_READOUT_HOLD, 0, 0, 0, 64, 0, 0, _lib.SSA_SELECT_SOFT, 1.0)
+        run = ctypes.c_void_p()
+        args = [g] + [None] * 5 + [1, 1, 0, None, 1.0, None, 0, 0, ctypes.byref(opts), None, 0, None, None, None,
+                                    None, ctypes.byref(run)]
+        assert lib.ssa_grn_forward(*args) == -4
+        assert b"shared memory" in lib.ssa_last_error()
+        opts.temperature = 0.0  # the soft forward needs T > 0
+        assert lib.ssa_grn_forward(*args) == -4
+        assert b"T > 0" in lib.ssa_last_error()
+    finally:
+        lib.ssa_grn_destroy(g)
