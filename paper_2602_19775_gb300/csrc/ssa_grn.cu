@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(128, 5) grn_soft_adj_kernel(const GrnParams p)
 // ---------------------------------------------------------------------------------------------
 // backward: one warp per trajectory, reverse walk
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) grn_adj_kernel(const GrnParams p)
+__global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, W = blockDim.x >> 5;
