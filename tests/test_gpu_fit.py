@@ -82,3 +82,35 @@ def test_start_point_map_segments():
     assert float(loss0) > 3.0 * loss_true, (float(loss0), loss_true)
     loss0.backward()
     assert torch.all(torch.isfinite(th0.grad)) and float(th0.grad[train].abs().sum()) > 0
+
+
+def test_start_point_map_fit_recovers_the_protein_rates():
+    """Section 4.2's start-point map fit on the oscillator: the five protein rates perturbed by 20-30% and
+    trained together from 2,048 start points (256 per step, 16 replicates each) at T = 0.1, by gradient
+    descent with the largest per-parameter step clipped to 0.05 log units. The paper's RMSprop diverges on
+    this objective (every rate moves at the same speed although the production and degradation of A are
+    strongly coupled and gammaC's gradient is small and biased); gradient descent follows the large
+    components first. On the CPU oracle this recipe ended, over three seeds, within 5% of the true rates
+    (gammaC within 8%) after 300 steps; required here: within 10% (gammaC within 20%) and the loss at least
+    halved."""
+    from paper_2602_19775_gb300 import ssa
+    from paper_2602_19775_gb300.fit import fit_start_point_map, reference_start_points, segment_rates
+    spec = W.vilar_oscillator()
+    net = ssa.Network(spec)
+    true = spec.log_rates.astype(np.float32).astype(np.float64)
+    names = list(spec.param_names)
+    train = [names.index(x) for x in ("betaA", "betaR", "deltaA", "deltaR", "gammaC")]
+    starts = reference_start_points(net, true, spec.x0, 2048, 400.0, 1)
+    obs, H = [6, 7, 8], 0.05
+    th_true = torch.tensor(true, dtype=torch.float32, device="cuda")
+    with torch.no_grad():
+        tgt = torch.cat([segment_rates(net, th_true, starts[i:i + 512], 128, H, obs, 999 + i, 0.1)
+                         for i in range(0, 2048, 512)])
+    theta0 = true.copy()
+    theta0[train] += np.log([1.3, 0.75, 1.25, 0.8, 1.3])
+    theta, hist = fit_start_point_map(net, theta0, train, starts, tgt.cpu().numpy(), obs, H, replicates=16,
+                                      batch=256, iters=300, temperature=0.1, lr=2e-6, seed0=5, optimizer="sgd",
+                                      max_step=0.05)
+    ratio = np.exp(theta[train] - true[train])
+    assert np.all(np.abs(ratio[:4] - 1.0) < 0.1) and abs(ratio[4] - 1.0) < 0.2, ratio
+    assert np.mean(hist.loss[-50:]) < 0.5 * hist.loss[0], (hist.loss[0], np.mean(hist.loss[-50:]))
