@@ -774,7 +774,7 @@ def grn_extra(ssa, dev, n_img: int = 512, tpi: int = 64, t_end: float = 20.0, re
     soft_ms, soft_steps = 0.0, 0
     for r in range(reps + 1):
         ev[0].record(stream)
-        fw = ssa.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, tpi, t_end, [t_end], 70 + r,
+        fw = ssa.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, tpi, t_end, [t_end], 70 + r, record=False,
                              max_steps=1 << 14, soft_temperature=1.0)
         ev[1].record(stream)
         torch.cuda.synchronize()
