@@ -68,3 +68,38 @@ def test_grn_soft_path_rejects_shapes_beyond_shared_memory_without_gpu():
         assert b"T > 0" in lib.ssa_last_error()
     finally:
         lib.ssa_grn_destroy(g)
+
+
+def _net_args(**over):
+    """2A -> B, B -> 2A as host tables, with fields replaced by `over`."""
+    a = dict(N=2, M=2, reactants=[0, 0, 1, -1], ptr=[0, 2, 4], sp=[0, 1, 0, 1], dl=[-2, 1, 2, -1], P=2, ri=[0, 1])
+    a.update(over)
+    arr = lambda v: None if v is None else (ctypes.c_int32 * len(v))(*v)
+    return (a["N"], a["M"], arr(a["reactants"]), arr(a["ptr"]), arr(a["sp"]), arr(a["dl"]), a["P"], arr(a["ri"]))
+
+
+@pytest.mark.parametrize("over, code, text", [
+    (dict(N=0), -1, b"n_species"),
+    (dict(M=0), -1, b"n_reactions"),
+    (dict(M=65536), -4, b"65535"),
+    (dict(P=0), -1, b"n_params"),
+    (dict(ri=None), -1, b"NULL table"),
+    (dict(ptr=[1, 2, 4]), -1, b"stoich_ptr[0]"),
+    (dict(ptr=[0, 3, 2]), -1, b"monotone"),
+    (dict(sp=None), -1, b"NULL stoichiometry"),
+    (dict(reactants=[0, 2, 1, -1]), -1, b"reactant of reaction 0"),
+    (dict(reactants=[0, 0, -2, -1]), -1, b"reactant of reaction 1"),
+    (dict(ri=[0, 2]), -1, b"rate_index[1]"),
+    (dict(sp=[0, 0, 0, 1]), -1, b"twice"),
+    (dict(sp=[0, 1, 0, 2]), -1, b"stoich_species[3]"),
+    (dict(dl=[-2, 1, 128, -1]), -1, b"stoich_delta[2]"),
+])
+def test_network_tables_are_validated_on_the_host(over, code, text):
+    """ssa_create_network checks every table entry (Section 2's mass-action network: reactant slots,
+    the CSR net change, rate indices) before it allocates anything on a device."""
+    from paper_2602_19775_gb300 import _lib
+    lib = _lib.lib()
+    h = ctypes.c_void_p(1)
+    assert lib.ssa_create_network(*_net_args(**over), ctypes.byref(h)) == code
+    assert text in lib.ssa_last_error(), lib.ssa_last_error()
+    assert h.value is None  # the handle is cleared on failure
