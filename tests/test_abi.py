@@ -103,3 +103,25 @@ def test_network_tables_are_validated_on_the_host(over, code, text):
     assert lib.ssa_create_network(*_net_args(**over), ctypes.byref(h)) == code
     assert text in lib.ssa_last_error(), lib.ssa_last_error()
     assert h.value is None  # the handle is cleared on failure
+
+
+@pytest.mark.parametrize("args, code, text", [
+    ((0, 4, 3, 1.0), -1, b"sizes"),
+    ((5, 4097, 3, 1.0), -1, b"sizes"),
+    ((5, 4, 1025, 1.0), -1, b"sizes"),
+    ((1041, 4, 3, 1.0), -4, b"n_in above 1040"),
+    ((5, 4, 3, 0.0), -1, b"k_max"),
+    ((5, 4, 3, float("nan")), -1, b"k_max"),
+])
+def test_grn_sizes_are_validated_on_the_host(args, code, text):
+    """ssa_grn_create: the layer sizes, the exactness bound of the tensor-core contraction (one 6-bit limb of
+    W1 times 8-bit counts summed over n_in stays below 2^24) and k_max > 0."""
+    from paper_2602_19775_gb300 import _lib
+    lib = _lib.lib()
+    g = ctypes.c_void_p(1)
+    n_in, n_hid, n_out, k_max = args
+    assert lib.ssa_grn_create(n_in, n_hid, n_out, ctypes.c_float(k_max), ctypes.byref(g)) == code
+    assert text in lib.ssa_last_error(), lib.ssa_last_error()
+    assert g.value is None
+    assert lib.ssa_grn_create(1040, 4096, 1024, ctypes.c_float(1.0), ctypes.byref(g)) == 0  # the largest accepted
+    lib.ssa_grn_destroy(g)
