@@ -125,3 +125,29 @@ def test_grn_sizes_are_validated_on_the_host(args, code, text):
     assert g.value is None
     assert lib.ssa_grn_create(1040, 4096, 1024, ctypes.c_float(1.0), ctypes.byref(g)) == 0  # the largest accepted
     lib.ssa_grn_destroy(g)
+
+
+def test_grn_workspace_sizes_on_the_host():
+    """ssa_grn_workspace_bytes: a recorded soft run holds float checkpoints of all n_hid + n_out counts every 8
+    steps for every trajectory (and the adjoint's scratch); a recorded hard run the 2-byte event log and int
+    checkpoints every K steps; an unrecorded run neither. Invalid arguments give 0."""
+    from paper_2602_19775_gb300 import _lib
+    lib = _lib.lib()
+    g = ctypes.c_void_p()
+    assert lib.ssa_grn_create(784, 256, 10, ctypes.c_float(1.0), ctypes.byref(g)) == 0
+    try:
+        n_img, tpi, S, steps = 16, 64, 1, 4096
+        n, nd = n_img * tpi, 266
+        size = lambda sel, rec, T: lib.ssa_grn_workspace_bytes(
+            g, n_img, tpi, S, ctypes.byref(_lib.FwdOpts(_lib.SSA_READOUT_HOLD, rec, 64, 0, steps, 0, 0, sel, T)))
+        hard_fwd = size(_lib.SSA_SELECT_GUMBEL, 0, 0.0)
+        hard_rec = size(_lib.SSA_SELECT_GUMBEL, 1, 0.0)
+        soft_rec = size(_lib.SSA_SELECT_SOFT, 1, 1.0)
+        assert 0 < hard_fwd < hard_rec < soft_rec
+        assert hard_rec - hard_fwd >= n * (2 * steps + 4 * nd * (steps // 64 + 1))
+        assert soft_rec - hard_fwd >= n * 4 * nd * (steps // 8 + 1)
+        assert lib.ssa_grn_workspace_bytes(g, -1, tpi, S, ctypes.byref(_lib.FwdOpts(0, 0, 64, 0, steps))) == 0
+        assert lib.ssa_grn_workspace_bytes(g, n_img, 0, S, ctypes.byref(_lib.FwdOpts(0, 0, 64, 0, steps))) == 0
+        assert lib.ssa_grn_workspace_bytes(g, n_img, tpi, S, ctypes.byref(_lib.FwdOpts(0, 0, 64, 0, 0))) == 0
+    finally:
+        lib.ssa_grn_destroy(g)
