@@ -1290,6 +1290,10 @@ extern "C" ssa_status ssa_grn_backward(ssa_run *run, const float *dl_dobs, int64
                                                            g->n_hid, db1);
     grn_transpose_x_kernel<<<256, 256, 0, st>>>(run->x_img, run->n_img, g->n_in, L.n_img_pad, xT);
     GRN_CUDA_TRY(cudaGetLastError());
+    if (run->n_img == 0) {  // no images: dL/dW1 is an empty sum (and a zero-length K has no tensor map)
+        GRN_CUDA_TRY(cudaMemsetAsync(dW1, 0, (size_t)g->n_hid * g->n_in * sizeof(float), st));
+        return SSA_OK;
+    }
     // dW1[h][p] = sum_img G[img][h] x[img][p] on the tensor cores (hi + lo bf16 limbs of G)
     TcMaps maps;
     memset(&maps, 0, sizeof(maps));

@@ -179,3 +179,17 @@ def test_grn_soft_gradient_matches_oracle(S, size):
         S.grn_backward(fw, torch.tensor(dl_g, dtype=torch.float32, device="cuda"), 2 * T)
     with pytest.raises(RuntimeError):  # a soft run keeps no event log
         fw.run.events(16)
+
+
+@pytest.mark.parametrize("soft", [False, True], ids=["hard", "soft"])
+def test_grn_empty_batch(S, soft):
+    """No images: the forward writes nothing and the backward returns zero gradients."""
+    p = G.grn_params(seed=1, n_in=5, n_hid=4, n_out=3, w1_scale=0.02, w2_scale=0.5)
+    net = S.GRN(p.n_in, p.n_hid, p.n_out, p.k_max)
+    x = np.zeros((0, 5), np.int32)
+    fw = S.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, 8, 2.0, [1.0, 2.0], 3,
+                       soft_temperature=0.5 if soft else None)
+    assert fw.obs.shape == (0, 2, 3) and fw.draws.numel() == 0
+    g = S.grn_backward(fw, torch.zeros((0, 2, 3), device="cuda"), 0.5)
+    for k, v in g.items():
+        assert torch.count_nonzero(v) == 0, k
