@@ -151,3 +151,19 @@ def test_grn_workspace_sizes_on_the_host():
         assert lib.ssa_grn_workspace_bytes(g, n_img, tpi, S, ctypes.byref(_lib.FwdOpts(0, 0, 64, 0, 0))) == 0
     finally:
         lib.ssa_grn_destroy(g)
+
+
+def test_binding_bf16_weights_match_the_generators_rounding():
+    """The binding hands the GRN its weights as bf16 (torch's round-to-nearest-even cast); the input
+    generators' own bit-level rounding gives the same values, ties included, so the oracle and the GPU
+    path see identical weights."""
+    import numpy as np
+    import torch
+    from paper_2602_19775_gb300.ssa import _bf16_bits
+    from ssa_workloads.grn import round_bf16
+    rng = np.random.default_rng(4)
+    w = np.concatenate([rng.normal(0, 0.05, 4096), rng.normal(0, 30.0, 4096)]).astype(np.float32)
+    ties = (np.arange(1, 257, dtype=np.uint32) << 16 | 0x8000).view(np.float32)  # exactly half-way
+    w = np.concatenate([w, ties, -ties])
+    got = _bf16_bits(w).to(torch.float32).numpy()
+    np.testing.assert_array_equal(got, round_bf16(w))
