@@ -250,9 +250,8 @@ size_t ssa_grn_workspace_bytes(const ssa_grn *g, int64_t n_img, int64_t traj_per
  *   opts->selector SSA_SELECT_SOFT (temperature > 0): the soft forward of Eq. 4 (the first training
  *   phase of Section 3.5), relaxed counts; obs_out then holds float values. Recorded, it keeps every
  *   count every 8 steps (opts->ckpt_interval, still checked to be 0 or a positive multiple of 8, does
- *   not apply) and ssa_grn_backward returns the exact
- *   gradient of that relaxed model. The soft path holds W2 (n_out * n_hid floats) in shared memory:
- *   SSA_ERR_UNSUPPORTED when it does not fit.
+ *   not apply) and ssa_grn_backward returns the exact gradient of that relaxed model. The soft path
+ *   holds W2 (n_out * n_hid floats) in shared memory: SSA_ERR_UNSUPPORTED when it does not fit.
  */
 ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, const float *b1, const uint16_t *W2,
                            const float *b2, const float *log_d, int64_t n_img, int64_t traj_per_img,
