@@ -167,3 +167,11 @@ def test_binding_bf16_weights_match_the_generators_rounding():
     w = np.concatenate([w, ties, -ties])
     got = _bf16_bits(w).to(torch.float32).numpy()
     np.testing.assert_array_equal(got, round_bf16(w))
+
+
+def test_start_point_fit_rejects_an_unknown_optimizer_on_the_host():
+    import numpy as np
+    from paper_2602_19775_gb300.fit import fit_start_point_map
+    with pytest.raises(ValueError):
+        fit_start_point_map(None, np.zeros(2), [0], np.zeros((1, 2), np.int32), np.zeros((1, 1)), [0], 0.1, 1, 1, 1,
+                            0.1, optimizer="momentum")
