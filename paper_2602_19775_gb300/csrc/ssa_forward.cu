@@ -70,15 +70,20 @@ __global__ void rates_kernel(const float *log_rates, const int *rate_index, int 
 }
 
 // Deterministic ensemble mean: per-chunk column sums (fixed order), then a fixed-order sum.
+// Chunk b (rows b*chunk .. b*chunk + chunk - 1) is summed by the blocks with blockIdx.y = b mod gridDim.y, so
+// any number of chunks fits the 65,535 limit of gridDim.y; each chunk's sum is the same whatever the grid.
 template <typename T>
 __global__ void colsum_chunks_kernel(const T *obs, int64_t n_traj, int64_t row_len, int64_t chunk, float *partial)
 {
-    const int64_t t0 = (int64_t)blockIdx.y * chunk;
-    const int64_t t1 = min(n_traj, t0 + chunk);
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < row_len; c += (int64_t)gridDim.x * blockDim.x) {
-        float acc = 0.0f;
-        for (int64_t t = t0; t < t1; ++t) acc += (float)obs[t * row_len + c];
-        partial[(int64_t)blockIdx.y * row_len + c] = acc;
+    const int64_t n_chunks = (n_traj + chunk - 1) / chunk;
+    for (int64_t b = blockIdx.y; b < n_chunks; b += gridDim.y) {
+        const int64_t t0 = b * chunk;
+        const int64_t t1 = min(n_traj, t0 + chunk);
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < row_len; c += (int64_t)gridDim.x * blockDim.x) {
+            float acc = 0.0f;
+            for (int64_t t = t0; t < t1; ++t) acc += (float)obs[t * row_len + c];
+            partial[b * row_len + c] = acc;
+        }
     }
 }
 
@@ -273,11 +278,12 @@ cudaError_t launch_ensemble_mean(const void *obs, bool is_int, int64_t n_traj, i
     const int64_t n_chunks = (n_traj + chunk - 1) / chunk;
     const float inv_n = n_traj > 0 ? 1.0f / (float)n_traj : 0.0f;
     if (n_chunks > 0) {
-        dim3 g((unsigned)((row_len + 127) / 128), (unsigned)n_chunks);
+        dim3 g((unsigned)std::min<int64_t>((row_len + 127) / 128, 65535), (unsigned)std::min<int64_t>(n_chunks, 65535));
         if (is_int) colsum_chunks_kernel<int><<<g, 128, 0, st>>>(static_cast<const int *>(obs), n_traj, row_len, chunk, partial);
         else colsum_chunks_kernel<float><<<g, 128, 0, st>>>(static_cast<const float *>(obs), n_traj, row_len, chunk, partial);
     }
-    colsum_final_kernel<<<(unsigned)((row_len + 127) / 128), 128, 0, st>>>(partial, n_chunks, row_len, inv_n, out);
+    colsum_final_kernel<<<(unsigned)std::min<int64_t>((row_len + 127) / 128, 65535), 128, 0, st>>>(partial, n_chunks, row_len,
+                                                                                                  inv_n, out);
     return cudaGetLastError();
 }
 
@@ -287,12 +293,12 @@ cudaError_t launch_column_sums(const float *x, int64_t n_rows, int64_t row_len, 
 {
     if (row_len == 0) return cudaSuccess;
     const int64_t n_chunks = (n_rows + chunk - 1) / chunk;
-    if (n_chunks > 65535) return cudaErrorInvalidValue;
     if (n_chunks > 0) {
-        dim3 g((unsigned)((row_len + 127) / 128), (unsigned)n_chunks);
+        dim3 g((unsigned)std::min<int64_t>((row_len + 127) / 128, 65535), (unsigned)std::min<int64_t>(n_chunks, 65535));
         colsum_chunks_kernel<float><<<g, 128, 0, st>>>(x, n_rows, row_len, chunk, partial);
     }
-    colsum_final_kernel<<<(unsigned)((row_len + 127) / 128), 128, 0, st>>>(partial, n_chunks, row_len, 1.0f, out);
+    colsum_final_kernel<<<(unsigned)std::min<int64_t>((row_len + 127) / 128, 65535), 128, 0, st>>>(partial, n_chunks, row_len,
+                                                                                                  1.0f, out);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,9 @@
 // The scratch is the file-scope array below. Every GPU that loads the library holds it until the
 // process exits. Host code cannot use the array's name as a device address (in host code it names
 // a host-side stand-in), so the address is obtained once per device with cudaGetSymbolAddress
-// while that device is current, and passed to the kernels.
+// while that device is current, and passed to the kernels. The address is cached per device index for
+// the life of the process; after cudaDeviceReset the device code may be reloaded elsewhere, so the entry
+// point must not be used across a reset of the device.
 #include <mutex>
 
 #include "ssa_internal.cuh"
@@ -34,8 +36,10 @@ float *g_scratch_addr[kMaxDevices] = {};
 
 }  // namespace
 
-// Resolve the device address of the scratch array for the current device (once per device).
-static ssa_status static_scratch(float **out)
+// Resolve the device address of the scratch array for the current device (once per device). The lookup
+// may load the library's device code, which a stream that is being captured into a graph does not allow:
+// a first call on a capturing stream is refused with a message instead of failing inside the capture.
+static ssa_status static_scratch(float **out, cudaStream_t stream)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -43,6 +47,11 @@ static ssa_status static_scratch(float **out)
     if (dev < 0 || dev >= kMaxDevices) return ssa::set_error(SSA_ERR_UNSUPPORTED, "device index above 63");
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_addr[dev]) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone)
+            return ssa::set_error(SSA_ERR_UNSUPPORTED,
+                                  "ssa_ensemble_mean_static: the first call on a device looks up its scratch address "
+                                  "and cannot run during stream capture; make one call before capturing");
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_mean_scratch);
         if (e != cudaSuccess || !p)
@@ -65,7 +74,7 @@ extern "C" ssa_status ssa_ensemble_mean_static(const void *obs, int32_t obs_is_i
                               "ssa_ensemble_mean_static: ceil(n_traj/256) * row_len exceeds the 1,048,576-float "
                               "static scratch; use ssa_ensemble_mean with a workspace");
     float *scratch = nullptr;
-    const ssa_status s = static_scratch(&scratch);
+    const ssa_status s = static_scratch(&scratch, static_cast<cudaStream_t>(stream));
     if (s != SSA_OK) return s;
     // every scratch entry the reduction reads is written earlier in the same call, so nothing has to
     // be cleared between calls
