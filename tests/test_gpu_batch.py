@@ -193,7 +193,7 @@ def test_batch_matches_oracle_on_uneven_random_networks(S):
     scaled down to oracle size) against the FP64 oracle: status codes, event sequences under the margin
     rule, observables, and gradients on trajectories whose events and brackets agree."""
     from oracle import native
-    from test_gpu_parity import GRAD_RTOL, _T_END, _bracket_agreement, _clock_tol, _compare_events, _oracle_brackets
+    from test_gpu_parity import GRAD_RTOL, _bracket_agreement, _clock_tol, _compare_events, _oracle_brackets
     from types import SimpleNamespace
 
     wl = W.config_c4(n_nets=5, traj_scale=1.0 / 256)
@@ -211,7 +211,6 @@ def test_batch_matches_oracle_on_uneven_random_networks(S):
         b.dl_dobs[q].copy_(torch.tensor(dl, dtype=torch.float32))
     b.run()
     torch.cuda.synchronize()
-    _T_END["t_end"] = wl.t_end
     for q, spec in enumerate(wl.nets):
         it = items[q]
         n = it["n_traj"]
@@ -223,8 +222,8 @@ def test_batch_matches_oracle_on_uneven_random_networks(S):
         np.testing.assert_array_equal(status.cpu().numpy(), orc.status)
         fw = SimpleNamespace(draws=draws, status=status,
                              run=SimpleNamespace(brackets=lambda q=q: b.brackets(q)))
-        same = _compare_events(orc, fw, b.events(q, cap).cpu().numpy())
-        assert same.mean() >= 0.9, (q, same.mean())  # thousands of draws per trajectory, up to 512 reactions
+        # thousands of draws per trajectory, up to 512 reactions: the count rule, and a floor of 0.9
+        same = _compare_events(orc, fw, b.events(q, cap).cpu().numpy(), wl.t_end, spec.n_reactions, floor=0.9)
         agree = _bracket_agreement(orc, fw, wl.sample_times, spec.n_reactions)
         use = same & agree
         obs = b.obs[q].double().cpu().numpy()
@@ -244,5 +243,78 @@ def test_batch_matches_oracle_on_uneven_random_networks(S):
         b.run()
         g = b.dtheta[q].double().cpu().numpy()
         ref = orc.dtheta[use].sum(0)
+        rel = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30)
+        assert rel < GRAD_RTOL, (q, rel)
+
+
+def test_batch_matches_oracle_on_all_256_networks(S):
+    """Every network of the uneven random-network workload, four trajectories each, in one batch against
+    the FP64 oracle: status codes; event sequences under the margin rule and the long-trajectory count
+    rule per network, with at least 90% identical over all trajectories; observables and each network's
+    gradient on the trajectories whose events and sample brackets agree."""
+    from concurrent.futures import ThreadPoolExecutor
+    from types import SimpleNamespace
+    from oracle import native
+    from test_gpu_parity import GRAD_RTOL, _bracket_agreement, _clock_tol, _compare_events, _oracle_brackets
+
+    wl = W.config_c4(n_nets=256)
+    cap = 1 << 16
+    n = 4
+    nets = [S.Network(spec) for spec in wl.nets]
+    items = [dict(net=nets[q], log_rates=spec.log_rates.astype(np.float32), n_traj=n, x0=spec.x0,
+                  t_end=wl.t_end, sample_times=wl.sample_times, obs_species=wl.obs_species[q], seed=300 + q,
+                  traj_offset=7 * q, max_steps=cap) for q, spec in enumerate(wl.nets)]
+    b = S.Batch(items, readout="linear", temperature=wl.temperature)
+    dls = [W.seeded_dl_dobs(900 + q, n, len(wl.sample_times), len(wl.obs_species[q]), scale=1.0 / n)
+           for q in range(len(items))]
+    for q in range(len(items)):
+        b.dl_dobs[q].copy_(torch.tensor(dls[q], dtype=torch.float32))
+    b.run()
+    torch.cuda.synchronize()
+
+    def oracle(q):
+        spec, it = wl.nets[q], items[q]
+        return native.run(spec, spec.log_rates.astype(np.float32).astype(np.float64), spec.x0, n, wl.t_end,
+                          wl.sample_times, wl.obs_species[q], it["seed"], LINEAR, max_steps=cap,
+                          traj_offset=it["traj_offset"], dl_dobs=dls[q], temperature=wl.temperature, ev_cap=cap,
+                          n_threads=1)
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        orcs = list(ex.map(oracle, range(len(items))))
+    uses, n_same = [], 0
+    for q, spec in enumerate(wl.nets):
+        orc = orcs[q]
+        draws, status, mism = b.outputs(q)
+        assert mism == 0
+        np.testing.assert_array_equal(status.cpu().numpy(), orc.status)
+        fw = SimpleNamespace(draws=draws, status=status, run=SimpleNamespace(brackets=lambda q=q: b.brackets(q)))
+        same = _compare_events(orc, fw, b.events(q, cap).cpu().numpy(), wl.t_end, spec.n_reactions, floor=None)
+        n_same += int(same.sum())
+        use = same & _bracket_agreement(orc, fw, wl.sample_times, spec.n_reactions)
+        obs = b.obs[q].double().cpu().numpy()
+        ob = _oracle_brackets(orc, wl.sample_times)
+        vmax = np.abs(spec.stoich_delta).max()
+        for i in np.nonzero(use)[0]:
+            t = np.concatenate([[0.0], orc.times[i, :orc.draws[i]]])
+            k = ob[i]
+            tau = t[np.minimum(k + 1, len(t) - 1)] - t[k]
+            tol = vmax * _clock_tol(spec.n_reactions, wl.sample_times) / np.maximum(tau, 1e-300) \
+                + 1e-6 * np.abs(orc.obs[i]).max(1)
+            assert np.all(np.abs(obs[i] - orc.obs[i]).max(1) <= tol), (q, i)
+        uses.append(use)
+    assert n_same >= 0.9 * n * len(items), n_same
+    # gradients over the agreeing trajectories of every network, from one more run of the batch
+    for q in range(len(items)):
+        dl_g = dls[q].copy()
+        dl_g[~uses[q]] = 0
+        b.dl_dobs[q].copy_(torch.tensor(dl_g, dtype=torch.float32))
+    b.run()
+    torch.cuda.synchronize()
+    for q in range(len(items)):
+        g = b.dtheta[q].double().cpu().numpy()
+        ref = orcs[q].dtheta[uses[q]].sum(0)
+        if not uses[q].any():
+            assert np.all(g == 0)
+            continue
         rel = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30)
         assert rel < GRAD_RTOL, (q, rel)

@@ -9,7 +9,7 @@ import torch
 from ssa_workloads import grn as G
 from oracle import native
 
-from test_gpu_parity import GRAD_RTOL, MARGIN_TOL
+from test_gpu_parity import GRAD_RTOL, _divergence_rule
 
 pytestmark = pytest.mark.gpu
 
@@ -43,10 +43,9 @@ def _grn_case(S, p, x, tpi, t_end, seed, T, max_steps=1 << 15):
     orc = native.grn_run(p, x, tpi, t_end, ts, seed, max_steps=max_steps, dl_dobs=dl, temperature=T, ev_cap=max_steps)
     assert np.all(fw.status.cpu().numpy() == orc.status)
     ev = fw.run.events(max_steps).cpu().numpy()
-    same = np.all(ev == orc.events, axis=1)
-    for i in np.nonzero(~same)[0]:
-        k = int(np.nonzero(ev[i] != orc.events[i])[0][0])
-        assert orc.margins[i, k] < MARGIN_TOL, (i, k, orc.margins[i, k])
+    # margin rule at each first divergence and the long-trajectory count rule (532 reactions per race,
+    # thousands of draws), beside a floor of 0.95
+    same = _divergence_rule(ev, fw.draws.cpu().numpy(), orc)
     assert same.mean() >= 0.95, same.mean()
     obs = fw.obs.double().cpu().numpy()
     np.testing.assert_array_equal(obs[same], orc.obs[same])

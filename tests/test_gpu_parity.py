@@ -57,23 +57,41 @@ def _run_both(S, net, theta, x0, n, t_end, ts, obs_sp, seed, readout, max_steps=
     return snet, fw, orc, gpu_ev
 
 
-def _compare_events(orc, fw, gpu_ev):
-    """Returns the boolean mask of trajectories whose event sequences agree; asserts the
-    divergence rule."""
-    draws_g = fw.draws.cpu().numpy().astype(np.int64)
+def _divergence_rule(gpu_ev, draws_g, orc, crossing=None):
+    """Event-sequence parity for trajectories of any length. Returns the mask of trajectories whose
+    event sequences (and draw counts) agree with the oracle's, and asserts:
+    (i) at the first step where a trajectory differs, the oracle's selection margin (s1 - s2)/s1 is below
+        1e-6 (binary32 keys carry a few ulp), or `crossing(i, k)` says the divergence is a crossing
+        decision within the clock tolerance of t_end;
+    (ii) the number of trajectories that first differ at a near-tie is at most the oracle's own count of
+        steps with margin below 1e-6 over all trajectories: with ~1e6 draws per trajectory a few flips are
+        expected, so a floor on the identical fraction cannot hold, but each flip needs a near-tie."""
+    draws_g = np.asarray(draws_g).astype(np.int64)
     same = np.all(gpu_ev == orc.events, axis=1) & (draws_g == orc.draws)
-    bad = np.nonzero(~same)[0]
-    for i in bad:
+    n_tie = 0
+    for i in np.nonzero(~same)[0]:
         diff = np.nonzero(gpu_ev[i] != orc.events[i])[0]
         k = int(diff[0]) if diff.size else int(min(draws_g[i], orc.draws[i]))
-        # a divergence must come from a near-tie in the choice, or from a crossing decision made
-        # within the FP32 clock tolerance of t_end
         m = orc.margins[i, k] if k < orc.draws[i] else 0.0
-        assert m < MARGIN_TOL or _near_crossing(orc, i, k), (i, k, m)
+        if m < MARGIN_TOL:
+            n_tie += 1
+        else:
+            assert crossing is not None and crossing(i, k), (i, k, m)
+    steps = np.arange(orc.margins.shape[1])[None, :] < orc.draws[:, None]
+    n_small = int(np.count_nonzero((orc.margins < MARGIN_TOL) & steps))
+    assert n_tie <= n_small, (n_tie, n_small)
     return same
 
 
-_T_END = {}
+def _compare_events(orc, fw, gpu_ev, t_end, M, floor=0.999):
+    """`_divergence_rule` with the crossing decision at t_end (network of M reactions); `floor` is the
+    fraction of identical trajectories required of short trajectories (a few hundred draws; None for
+    long ones, where the count rule (ii) alone applies)."""
+    same = _divergence_rule(gpu_ev, fw.draws.cpu().numpy(), orc,
+                            crossing=lambda i, k: _near_crossing(orc, i, k, t_end, M))
+    if floor is not None:
+        assert same.mean() >= floor, same.mean()
+    return same
 
 
 def _clock_tol(M, t):
@@ -83,12 +101,10 @@ def _clock_tol(M, t):
     return 8.0 * (M + 2) * EPS32 * np.asarray(t)
 
 
-def _near_crossing(orc, i, k, M=2):
-    t_end = _T_END.get("t_end", None)
-    if t_end is None:
-        return False
+def _near_crossing(orc, i, k, t_end, M):
+    """Whether draw k of trajectory i is the crossing of t_end within the clock tolerance."""
     t = orc.times[i, k] if k < orc.times.shape[1] else np.nan
-    return np.isfinite(t) and abs(t - t_end) <= _clock_tol(M, t_end)
+    return bool(np.isfinite(t) and abs(t - t_end) <= _clock_tol(M, t_end))
 
 
 def _oracle_brackets(orc, ts):
@@ -118,6 +134,21 @@ def _bracket_agreement(orc, fw, ts, M):
     return agree
 
 
+def _bracket_flips(orc, fw, ts, M):
+    """[n, S] mask of the samples whose bracket differs from the oracle's, each checked to lie within the
+    clock tolerance of an event time. Over ~1e6 draws the binary32 waiting times move the clock by more
+    than the spacing of events, so most long trajectories flip a few of their samples; the gradient is
+    linear in dL/dobs, so zeroing the upstream gradient of exactly those samples on both sides compares
+    everything else."""
+    gb = fw.run.brackets().cpu().numpy()
+    ob = _oracle_brackets(orc, ts)
+    flip = gb != ob
+    for i, s in zip(*np.nonzero(flip)):
+        ev_t = orc.times[i, :orc.draws[i]]
+        assert np.min(np.abs(ev_t - ts[s])) <= _clock_tol(M, ts[s]), (i, s)
+    return flip
+
+
 def test_philox_words_bit_exact(S):
     rng = np.random.default_rng(0)
     traj = rng.integers(0, 2 ** 40, size=257)
@@ -130,13 +161,11 @@ def test_philox_words_bit_exact(S):
 
 def test_forward_c1_matches_oracle(S):
     wl = W.config_c1()
-    _T_END["t_end"] = wl.t_end
     snet, fw, orc, gpu_ev = _run_both(S, wl.net, wl.log_rates, wl.x0, wl.n_traj, wl.t_end, wl.sample_times,
                                       wl.obs_species, wl.seed, HOLD)
     st = fw.status.cpu().numpy()
     assert np.all(st == 0)
-    same = _compare_events(orc, fw, gpu_ev)
-    assert same.mean() >= 0.999, same.mean()
+    same = _compare_events(orc, fw, gpu_ev, wl.t_end, wl.net.n_reactions)
     obs_g = fw.obs.cpu().numpy()
     for i in np.nonzero(same)[0]:
         d = np.nonzero(np.any(obs_g[i] != orc.obs[i], axis=1))[0]
@@ -197,11 +226,9 @@ def test_replay_oracle_events_bit_exact_states(S, readout):
 
 def _grad_case(S, net, theta, x0, n, t_end, ts, obs_sp, seed, readout, T, dl_seed=5, K=64, max_steps=4096):
     dl = W.seeded_dl_dobs(dl_seed, n, len(ts), len(obs_sp), scale=1.0 / n)
-    _T_END["t_end"] = t_end
     snet, fw, orc, gpu_ev = _run_both(S, net, theta, x0, n, t_end, ts, obs_sp, seed, readout, max_steps=max_steps,
                                       dl=dl, T=T, K=K)
-    same = _compare_events(orc, fw, gpu_ev)
-    assert same.mean() >= 0.999, same.mean()
+    same = _compare_events(orc, fw, gpu_ev, t_end, net.n_reactions)
     agree = _bracket_agreement(orc, fw, np.asarray(ts), net.n_reactions)
     assert agree.mean() >= 0.99, agree.mean()
     same &= agree

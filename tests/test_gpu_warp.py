@@ -9,7 +9,7 @@ import ssa_workloads as W
 from ssa_workloads.configs import HOLD, LINEAR
 from oracle import native
 
-from test_gpu_parity import (GRAD_RTOL, _T_END, _bracket_agreement, _clock_tol, _compare_events,
+from test_gpu_parity import (GRAD_RTOL, _bracket_agreement, _clock_tol, _compare_events,
                               _oracle_brackets, _theta32)
 
 pytestmark = pytest.mark.gpu
@@ -47,9 +47,7 @@ def _parity(S, net, theta, n, t_end, S_samples, obs_sp, seed, readout, T, tpt, m
                      temperature=T, ev_cap=max_steps)
     gst = fw.status.cpu().numpy()
     np.testing.assert_array_equal(gst, orc.status)
-    _T_END["t_end"] = t_end
-    same = _compare_events(orc, fw, fw.run.events(max_steps).cpu().numpy())
-    assert same.mean() >= 0.99, same.mean()
+    same = _compare_events(orc, fw, fw.run.events(max_steps).cpu().numpy(), t_end, net.n_reactions, floor=0.99)
     agree = _bracket_agreement(orc, fw, ts, net.n_reactions)
     use = same & agree
     obs = fw.obs.double().cpu().numpy()
