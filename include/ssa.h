@@ -190,6 +190,38 @@ ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stri
                         float temperature, float *dl_dlog_rates, void *stream);
 
 /*
+ * ssa_backward_multi -- the straight-through gradient of one recorded forward at several temperatures
+ * (Eq. 3's T; e.g. T in {0.1, 0.5, 1.0}), each exactly what ssa_backward gives at that T. The reverse
+ * walk, the regenerated noise, the propensities and the keys do not depend on T: on the
+ * network-specialised kernels (ssa_run_variant = 2, Gumbel-max forward, HOLD or LINEAR readout) one walk
+ * serves up to three temperatures at once, each with its own lambda, mu and partial sums; otherwise,
+ * and for the remainder, one walk per temperature.
+ *   temperatures   host float [n_temps], each > 0; n_temps >= 1.
+ *   dl_dlog_rates  device float [n_temps][P], overwritten; row t for temperatures[t].
+ *   Other arguments and errors as ssa_backward.
+ */
+ssa_status ssa_backward_multi(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride,
+                              const float *temperatures, int32_t n_temps, float *dl_dlog_rates,
+                              void *stream);
+
+/*
+ * ssa_backward_wide -- the same straight-through gradient as ssa_backward (same equations, same walk,
+ * same noise) for trajectories whose adjoint leaves the binary32 range: over ~1e6 draws the
+ * recursion of Figure 1 can grow dL/dX geometrically (on the activator-repressor oscillator of
+ * Section 4.2 the binary64 gradient of one trajectory reaches ~1e73 at t = 400). Each trajectory
+ * carries its binary32 accumulators (lambda, mu, dL/dlog a_j) times 2^sc with its own integer
+ * exponent sc, renormalised by a power of two at every checkpoint once they exceed 2^32 (exact), and
+ * the per-trajectory results are summed in binary64.
+ *   dl_dlog_rates  device double [P], overwritten (deterministic reduction order).
+ *   Other arguments as ssa_backward. A trajectory whose accumulators overflow within one checkpoint
+ *   interval makes the result inf or NaN.
+ * Runs on recorded Gumbel-max forwards with the HOLD or LINEAR readout on the network-specialised
+ * kernels (ssa_run_variant = 2); SSA_ERR_UNSUPPORTED otherwise.
+ */
+ssa_status ssa_backward_wide(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride,
+                             float temperature, double *dl_dlog_rates, void *stream);
+
+/*
  * ssa_run_status -- synchronises `stream`, counts the per-trajectory status codes of the run into
  * host counts[SSA_TRAJ_N_CODES] and returns the number of backward consistency failures (the
  * recomputed Gumbel-max choice or a checkpoint disagreeing with the log) in *host_bwd_mismatch
@@ -284,6 +316,7 @@ ssa_status ssa_grn_activations(const ssa_run *run, float *E1_out, int32_t *host_
  * float [row_len]. Column sums run over fixed chunks of 256 trajectories, then over chunks, in a
  * fixed order, so the result is bitwise reproducible.
  *   workspace: device, >= ssa_ensemble_mean_workspace_bytes(n_traj, row_len).
+ *   Any n_traj: the chunks are spread over at most 65,535 blocks in y.
  */
 size_t ssa_ensemble_mean_workspace_bytes(int64_t n_traj, int64_t row_len);
 ssa_status ssa_ensemble_mean(const void *obs, int32_t obs_is_int, int64_t n_traj, int64_t row_len,
@@ -299,7 +332,9 @@ ssa_status ssa_ensemble_mean(const void *obs, int32_t obs_is_int, int64_t n_traj
  *   exits. ceil(n_traj / 256) * row_len must not exceed 1,048,576; larger inputs are rejected with
  *   SSA_ERR_UNSUPPORTED (use ssa_ensemble_mean with a workspace instead).
  *   The first call on a device looks up that device's address of the array
- *   (cudaGetSymbolAddress); make that first call before any stream capture on the device.
+ *   (cudaGetSymbolAddress); make that first call before any stream capture on the device (a first
+ *   call on a capturing stream returns SSA_ERR_UNSUPPORTED). The address is kept per device index
+ *   for the life of the process: do not use this entry point across a cudaDeviceReset.
  *   All calls share the one array: calls that may run at the same time on the GPU (different
  *   streams without ordering between them) race and corrupt each other's result. Each call writes
  *   every scratch entry it reads, so no clearing is needed between calls.

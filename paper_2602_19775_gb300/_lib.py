@@ -26,7 +26,7 @@ SSA_TRAJ_N_CODES = len(TRAJ_CODES)
 # every symbol the header declares
 EXPORTS = (
     "ssa_create_network", "ssa_destroy_network", "ssa_forward_workspace_bytes", "ssa_forward",
-    "ssa_forward_replay", "ssa_backward", "ssa_run_status", "ssa_run_events", "ssa_run_brackets", "ssa_destroy_run",
+    "ssa_forward_replay", "ssa_backward", "ssa_backward_wide", "ssa_backward_multi", "ssa_run_status", "ssa_run_events", "ssa_run_brackets", "ssa_destroy_run",
     "ssa_ensemble_mean_workspace_bytes", "ssa_ensemble_mean", "ssa_ensemble_mean_static", "ssa_philox_uniforms",
     "ssa_bf16_gemm", "ssa_pipe_rates", "ssa_last_error", "ssa_grn_create", "ssa_grn_destroy",
     "ssa_grn_workspace_bytes", "ssa_grn_forward", "ssa_grn_backward", "ssa_grn_activations",
@@ -94,6 +94,8 @@ def _declare(lib):
         "ssa_forward_replay": (i32, [p, p, i64, i64, p, i32, f64, p, i32, p, i32, u64, opts, p, p, i64, p, sz,
                                      p, p, p, p, ctypes.POINTER(p)]),
         "ssa_backward": (i32, [p, p, i64, f32, p, p]),
+        "ssa_backward_wide": (i32, [p, p, i64, f32, p, p]),
+        "ssa_backward_multi": (i32, [p, p, i64, p, i32, p, p]),
         "ssa_run_status": (i32, [p, p, p, p]),
         "ssa_run_events": (i32, [p, p, i64, p]),
         "ssa_run_brackets": (i32, [p, p, p]),

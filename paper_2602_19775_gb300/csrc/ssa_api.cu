@@ -46,6 +46,13 @@ cudaError_t jit_launch_forward(const JitKernels *k, const FwdParams &p, int read
                                int block, cudaStream_t st);
 cudaError_t jit_launch_backward(const JitKernels *k, const AdjParams &p, int readout, int block, int64_t grid,
                                 cudaStream_t st);
+cudaError_t jit_launch_backward_wide(const JitKernels *k, const AdjParams &p, int readout, int block, int64_t grid,
+                                     cudaStream_t st);
+cudaError_t jit_launch_backward_multi(const JitKernels *k, const AdjParams &p, int readout, int n_temps, int block,
+                                      int64_t grid, cudaStream_t st);
+constexpr int kMaxFusedTemps = 3;  // temperatures one specialised walk takes at once
+cudaError_t launch_reduce_partials64(const double *partial, int64_t nblk, int M, const int *rate_index, int P,
+                                     double *dA_tmp, double *dtheta, cudaStream_t st);
 constexpr int kJitBlock = 64;
 constexpr int kJitAdjBlock = 128;  // the specialised adjoint orders a block's trajectories by length over its 4 warps
 }  // namespace ssa
@@ -127,8 +134,15 @@ WsLayout layout(const ssa_network *net, int64_t n, int32_t S, const ssa_fwd_opts
         L.brk_s = take((size_t)S * n * sizeof(int));
         L.brk_tail = take((size_t)(n > 0 ? n : 1) * sizeof(int));
         L.bin_prefix = take((size_t)(S + 1) * SSA_BIN_MAX_OBS * sizeof(double));
-        L.partial = take((size_t)(L.max_blocks > 0 ? L.max_blocks : 1) * net->M * sizeof(float));
+        // block sums of one backward: the warp kernels launch the most blocks; a specialised walk over
+        // several temperatures writes one set of block sums per temperature
+        const int64_t fused_blocks = kMaxFusedTemps * ((n + kJitAdjBlock - 1) / kJitAdjBlock);
+        const int64_t part_rows = std::max<int64_t>(std::max<int64_t>(L.max_blocks, fused_blocks), 1);
+        L.partial = take((size_t)part_rows * net->M * sizeof(float));
         L.dA = take((size_t)net->M * sizeof(float));
+        const int64_t wide_blocks = (n + kJitAdjBlock - 1) / kJitAdjBlock;
+        L.partial64 = take((size_t)(wide_blocks > 0 ? wide_blocks : 1) * net->M * sizeof(double));
+        L.dA64 = take((size_t)net->M * sizeof(double));
     }
     L.total = off;
     return L;
@@ -486,8 +500,11 @@ extern "C" ssa_status ssa_forward_replay(const ssa_network *net, const float *lo
                         obs_out, draws_out, status_out, stream, run_out);
 }
 
-extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride, float temperature,
-                                   float *dl_dlog_rates, void *stream)
+// Everything ssa_backward and ssa_backward_wide share: argument checks, the kernel variant and launch
+// shape, and the adjoint parameters (the per-block sums are left unset).
+static ssa_status backward_setup(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride, float temperature,
+                                 const void *dl_dlog_rates, cudaStream_t st, AdjParams &p, const JitKernels *&jit,
+                                 int &block, int64_t &grid)
 {
     if (run && dl_traj_stride != 0 && dl_traj_stride < (int64_t)run->S * run->n_obs)
         return fail(SSA_ERR_INVALID_ARG, "dl_traj_stride must be 0 or >= n_samples * n_obs");
@@ -500,11 +517,10 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     const ssa_network *net = run->net;
     const WsLayout &L = run->L;
     unsigned char *ws = run->ws;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t limit = smem_limit();
-    int block = 0;
-    int64_t grid = 0;
-    const JitKernels *jit = nullptr;
+    block = 0;
+    grid = 0;
+    jit = nullptr;
     const bool soft = run->opts.selector == SSA_SELECT_SOFT;
     if (soft && temperature != run->opts.temperature)
         return fail(SSA_ERR_INVALID_ARG, "the gradient of a soft forward is taken at the forward's temperature");
@@ -523,7 +539,7 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     }
     int *flag = reinterpret_cast<int *>(ws + L.flag);
     CUDA_TRY(cudaMemsetAsync(flag + 2, 0, sizeof(int), st));  // mismatch counter
-    AdjParams p{};
+    p = AdjParams{};
     p.rx = run->variant == 32 ? net->d_rx_warp : net->d_rx;
     p.k_rates = reinterpret_cast<const float *>(ws + L.k_rates);
     p.tab_bytes = net->tab_bytes;
@@ -560,9 +576,24 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
         p.bin_prefix = pre;
     }
     p.invT = 1.0f / temperature;
-    p.partial = reinterpret_cast<float *>(ws + L.partial);
     p.mismatch = flag + 2;
     p.err = flag + 1;
+    return SSA_OK;
+}
+
+extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride, float temperature,
+                                   float *dl_dlog_rates, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AdjParams p;
+    const JitKernels *jit = nullptr;
+    int block = 0;
+    int64_t grid = 0;
+    const ssa_status s = backward_setup(run, dl_dobs, dl_traj_stride, temperature, dl_dlog_rates, st, p, jit, block, grid);
+    if (s != SSA_OK) return s;
+    const ssa_network *net = run->net;
+    unsigned char *ws = run->ws;
+    p.partial = reinterpret_cast<float *>(ws + run->L.partial);
     if (run->variant == 2)
         CUDA_TRY(jit_launch_backward(jit, p, run->opts.readout, block, grid, st));
     else if (run->variant == 1)
@@ -570,7 +601,79 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
     else
         CUDA_TRY(launch_backward_warp(p, run->opts.readout, kWarpsPerBlock, adj_warp_smem(net), grid, st));
     CUDA_TRY(launch_reduce_partials(p.partial, grid, net->M, net->d_rate_index, net->P,
-                                    reinterpret_cast<float *>(ws + L.dA), dl_dlog_rates, st));
+                                    reinterpret_cast<float *>(ws + run->L.dA), dl_dlog_rates, st));
+    return SSA_OK;
+}
+
+extern "C" ssa_status ssa_backward_multi(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride,
+                                         const float *temperatures, int32_t n_temps, float *dl_dlog_rates, void *stream)
+{
+    if (!run) return fail(SSA_ERR_INVALID_ARG, "run is NULL");
+    if (!run->net) return fail(SSA_ERR_STATE, "a gene-regulatory-network run is differentiated by ssa_grn_backward");
+    if (!dl_dlog_rates) return fail(SSA_ERR_INVALID_ARG, "dl_dlog_rates is NULL");
+    if (n_temps < 1 || !temperatures) return fail(SSA_ERR_INVALID_ARG, "n_temps must be >= 1 with a host temperature list");
+    for (int t = 0; t < n_temps; ++t)
+        if (!(temperatures[t] > 0.0f) || !(temperatures[t] < 3.0e38f))
+            return fail(SSA_ERR_INVALID_ARG, "temperature %d must be > 0", t);
+    const bool fused = run->variant == 2 && run->opts.selector == SSA_SELECT_GUMBEL &&
+                       (run->opts.readout == SSA_READOUT_HOLD || run->opts.readout == SSA_READOUT_LINEAR) &&
+                       n_temps >= 2;
+    if (!fused) {  // one walk per temperature
+        for (int t = 0; t < n_temps; ++t) {
+            const ssa_status s = ssa_backward(run, dl_dobs, dl_traj_stride, temperatures[t],
+                                              dl_dlog_rates + (size_t)t * run->net->P, stream);
+            if (s != SSA_OK) return s;
+        }
+        return SSA_OK;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const ssa_network *net = run->net;
+    unsigned char *ws = run->ws;
+    for (int t0 = 0; t0 < n_temps; t0 += kMaxFusedTemps) {
+        const int nt = std::min(kMaxFusedTemps, n_temps - t0);
+        float *out = dl_dlog_rates + (size_t)t0 * net->P;
+        if (nt == 1) {
+            const ssa_status s = ssa_backward(run, dl_dobs, dl_traj_stride, temperatures[t0], out, stream);
+            if (s != SSA_OK) return s;
+            continue;
+        }
+        AdjParams p;
+        const JitKernels *jit = nullptr;
+        int block = 0;
+        int64_t grid = 0;
+        const ssa_status s = backward_setup(run, dl_dobs, dl_traj_stride, temperatures[t0], out, st, p, jit, block, grid);
+        if (s != SSA_OK) return s;
+        for (int t = 0; t < nt; ++t) p.invT_multi[t] = 1.0f / temperatures[t0 + t];
+        p.partial = reinterpret_cast<float *>(ws + run->L.partial);
+        CUDA_TRY(jit_launch_backward_multi(jit, p, run->opts.readout, nt, block, grid, st));
+        for (int t = 0; t < nt; ++t)
+            CUDA_TRY(launch_reduce_partials(p.partial + (size_t)t * grid * net->M, grid, net->M, net->d_rate_index,
+                                            net->P, reinterpret_cast<float *>(ws + run->L.dA), out + (size_t)t * net->P,
+                                            st));
+    }
+    return SSA_OK;
+}
+
+extern "C" ssa_status ssa_backward_wide(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stride, float temperature,
+                                        double *dl_dlog_rates, void *stream)
+{
+    if (run && (run->variant != 2 || run->opts.selector != SSA_SELECT_GUMBEL ||
+                (run->opts.readout != SSA_READOUT_HOLD && run->opts.readout != SSA_READOUT_LINEAR)))
+        return fail(SSA_ERR_UNSUPPORTED, "the wide-range adjoint runs on a Gumbel-max forward with the HOLD or LINEAR "
+                                         "readout on the network-specialised kernels");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AdjParams p;
+    const JitKernels *jit = nullptr;
+    int block = 0;
+    int64_t grid = 0;
+    const ssa_status s = backward_setup(run, dl_dobs, dl_traj_stride, temperature, dl_dlog_rates, st, p, jit, block, grid);
+    if (s != SSA_OK) return s;
+    const ssa_network *net = run->net;
+    unsigned char *ws = run->ws;
+    p.partial64 = reinterpret_cast<double *>(ws + run->L.partial64);
+    CUDA_TRY(jit_launch_backward_wide(jit, p, run->opts.readout, block, grid, st));
+    CUDA_TRY(launch_reduce_partials64(p.partial64, grid, net->M, net->d_rate_index, net->P,
+                                      reinterpret_cast<double *>(ws + run->L.dA64), dl_dlog_rates, st));
     return SSA_OK;
 }
 

@@ -106,6 +106,32 @@ __global__ void map_params_kernel(const float *dA, int M, const int *rate_index,
     }
 }
 
+// The wide-range adjoint's reductions: as above, in binary64 (values beyond the binary32 range).
+__global__ void reduce_partials64_kernel(const double *partial, int64_t nblk, int M, double *dA)
+{
+    __shared__ double red[256];
+    const int j = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) acc += partial[b * M + j];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dA[j] = red[0];
+}
+
+__global__ void map_params64_kernel(const double *dA, int M, const int *rate_index, int P, double *dtheta)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P; r += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < M; ++j)
+            if (rate_index[j] == r) acc += dA[j];
+        dtheta[r] = acc;
+    }
+}
+
 template <int R, int MC>
 static cudaError_t launch_adj_t(const AdjParams &p, int block, size_t smem, int64_t grid, cudaStream_t st)
 {
@@ -146,6 +172,14 @@ cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, co
 {
     if (M > 0) reduce_partials_kernel<<<M, 256, 0, st>>>(partial, nblk, M, dA_tmp);
     if (P > 0) map_params_kernel<<<(P + 255) / 256, 256, 0, st>>>(dA_tmp, M, rate_index, P, dtheta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials64(const double *partial, int64_t nblk, int M, const int *rate_index, int P,
+                                     double *dA_tmp, double *dtheta, cudaStream_t st)
+{
+    if (M > 0) reduce_partials64_kernel<<<M, 256, 0, st>>>(partial, nblk, M, dA_tmp);
+    if (P > 0) map_params64_kernel<<<(P + 255) / 256, 256, 0, st>>>(dA_tmp, M, rate_index, P, dtheta);
     return cudaGetLastError();
 }
 

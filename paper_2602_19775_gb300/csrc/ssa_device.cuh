@@ -407,6 +407,12 @@ struct AdjParams {
     float *partial;   // [gridDim.x][M]
     int *mismatch;    // backward consistency failures
     int *err;
+    // wide-range adjoint (long trajectories): per-block binary64 sums of the per-reaction adjoints, each
+    // trajectory's binary32 accumulators scaled back by its power-of-two exponent
+    double *partial64;  // [gridDim.x][M]
+    // several temperatures in one walk (network-specialised kernels): 1/T_t, t < the kernel's count; the
+    // block sums of temperature t go to partial + t gridDim.x M
+    float invT_multi[4];
 };
 
 

@@ -31,6 +31,8 @@ struct JitKernels {
     cudaKernel_t fwd[3][2];     // [readout][record], Gumbel-max choice (soft set: the soft forward)
     cudaKernel_t fwd_direct[3]; // [readout], direct method, forward only (not in the soft set)
     cudaKernel_t adj[3];        // [readout]
+    cudaKernel_t adj_wide[2];   // [HOLD, LINEAR], wide-range adjoint (not in the soft set)
+    cudaKernel_t adj_multi[2][2];  // [HOLD, LINEAR][2 or 3 temperatures] in one walk (not in the soft set)
 };
 
 namespace {
@@ -263,6 +265,12 @@ const JitKernels *jit_load(const ssa_network *net, bool soft, std::string &why)
         ok &= cudaLibraryGetKernel(&k.adj[r], lib, ("ssa_jit_adj_" + base).c_str()) == cudaSuccess;
         if (!soft)
             ok &= cudaLibraryGetKernel(&k.fwd_direct[r], lib, ("ssa_jit_fwd_" + base + "_direct").c_str()) == cudaSuccess;
+        if (!soft && r < 2) {
+            ok &= cudaLibraryGetKernel(&k.adj_wide[r], lib, ("ssa_jit_adj_" + base + "_wide").c_str()) == cudaSuccess;
+            for (int nt = 2; nt <= 3; ++nt)
+                ok &= cudaLibraryGetKernel(&k.adj_multi[r][nt - 2], lib,
+                                           ("ssa_jit_adj_" + base + "_t" + std::to_string(nt)).c_str()) == cudaSuccess;
+        }
     }
     if (!ok) {
         why = "a specialised kernel is missing from the library";
@@ -295,6 +303,29 @@ cudaError_t jit_launch_backward(const JitKernels *k, const AdjParams &p, int rea
     void *args[] = {const_cast<AdjParams *>(&p)};
     const size_t smem = (size_t)4 * p.M * block;
     return cudaLaunchKernel(reinterpret_cast<const void *>(k->adj[readout]),
+                            dim3((unsigned)grid), dim3((unsigned)block), args, smem, st);
+}
+
+cudaError_t jit_launch_backward_wide(const JitKernels *k, const AdjParams &p, int readout, int block, int64_t grid,
+                                     cudaStream_t st)
+{
+    if (grid == 0) return cudaSuccess;
+    if (readout != SSA_READOUT_HOLD && readout != SSA_READOUT_LINEAR) return cudaErrorInvalidValue;
+    void *args[] = {const_cast<AdjParams *>(&p)};
+    const size_t smem = (size_t)8 * p.M * block;  // binary64 block reduction
+    return cudaLaunchKernel(reinterpret_cast<const void *>(k->adj_wide[readout]),
+                            dim3((unsigned)grid), dim3((unsigned)block), args, smem, st);
+}
+
+cudaError_t jit_launch_backward_multi(const JitKernels *k, const AdjParams &p, int readout, int n_temps, int block,
+                                      int64_t grid, cudaStream_t st)
+{
+    if (grid == 0) return cudaSuccess;
+    if ((readout != SSA_READOUT_HOLD && readout != SSA_READOUT_LINEAR) || n_temps < 2 || n_temps > 3)
+        return cudaErrorInvalidValue;
+    void *args[] = {const_cast<AdjParams *>(&p)};
+    const size_t smem = (size_t)4 * n_temps * p.M * block;
+    return cudaLaunchKernel(reinterpret_cast<const void *>(k->adj_multi[readout][n_temps - 2]),
                             dim3((unsigned)grid), dim3((unsigned)block), args, smem, st);
 }
 

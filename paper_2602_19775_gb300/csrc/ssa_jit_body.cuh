@@ -303,24 +303,42 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
 }
 
 // Per-trajectory adjoint; returns the trajectory's per-reaction adjoints in dAr.
-template <int READOUT>
+//
+// NT temperatures at once (NT > 1): the walk, the regenerated noise, the propensities, the race check and
+// the log keys do not depend on T, so they are computed once per step; each temperature t keeps its own
+// lambda, mu and dAr[t] and runs the T-dependent part (soft weights, psi, the state adjoint) with invT_t,
+// in the same operation order as a single-temperature walk, so every dAr[t] equals that walk's bit for bit.
+//
+// WIDE (long trajectories, NT = 1): the adjoint is linear in the upstream gradient, and over ~1e6 draws the
+// straight-through recursion can grow it far beyond the binary32 range (on the oscillator to ~1e73 at
+// t = 400 in binary64). The walk then keeps lambda, mu and dAr as binary32 values times 2^sc, one
+// exponent per trajectory: at every checkpoint boundary, when the largest magnitude exceeds 2^32, all of
+// them are multiplied by 2^-e (exact) and sc grows by e; each upstream-gradient term enters multiplied by
+// 2^-sc. The trajectory's result is dAr 2^sc. With sc = 0 the arithmetic is the plain walk's bit for bit.
+template <int READOUT, bool WIDE = false, int NT = 1>
 __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&kr)[JM], const int64_t i, const int st,
-                                             float (&dAr)[JM])
+                                             float (&dAr)[NT][JM], int &sc)
 {
+    static_assert(!WIDE || NT == 1, "the wide-range walk takes one temperature");
+    sc = 0;
+    float inj = 1.0f;  // 2^-sc: the factor of every upstream-gradient term
     const int64_t n = p.n_traj;
     const int d = p.draws[i];
     const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;  // index of the last visited state
     int X[JN];
-    float lam[JN];
+    float lam[NT][JN];
 #pragma unroll
     for (int s = 0; s < JN; ++s) {
         X[s] = p.xfinal[(int64_t)s * n + i];
-        lam[s] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) lam[t][s] = 0.0f;
     }
     const uint64_t gid = p.traj_offset + (uint64_t)i;
     const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32);
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
-    const float invT = p.invT;
+    float invT[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) invT[t] = NT == 1 ? p.invT : p.invT_multi[t];
     const float *gl = p.dl_dobs + i * p.dl_stride;
 
     int row_cached = -1;
@@ -339,7 +357,9 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
     BinSlots bslots{-1, -1};
     float d_first = 0.0f, d_last = 0.0f;
     if (READOUT == SSA_READOUT_BIN) bin_slots_init(bslots, p.brk_k, p.brk_tail, n, i);
-    float mu = 0.0f;
+    float mu[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) mu[t] = 0.0f;
     int mism = 0;
     int ck_row = L / p.K, ck_off = L - ck_row * p.K;  // checkpoint c holds X_{cK}
 
@@ -348,14 +368,15 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
     const bool draw_last = st == SSA_TRAJ_OK;
     step_noise<NQ>(E, (uint32_t)(draw_last ? L : (L > 0 ? L - 1 : 0)), c2, c3, key0, key1);
 
-    // BIN readout: gq = g of the bin that contains t_{k+1}, xo = X_{k+1} at the observables
+    // BIN readout (NT = 1): gq = g of the bin that contains t_{k+1}, xo = X_{k+1} at the observables
     constexpr bool kBin = READOUT == SSA_READOUT_BIN;
+    static_assert(!kBin || NT == 1, "the bin readout's adjoint takes one temperature");
     float gq[kBinMaxObs], gk[kBinMaxObs];
     int osp[kBinMaxObs], xo[kBinMaxObs];
 #pragma unroll
     for (int c = 0; c < kBinMaxObs; ++c) osp[c] = (kBin && c < p.n_obs) ? p.obs_sp[c] : 0;
     auto xobs = [&](int c) { return jit_xsel(X, osp[c]); };
-    auto addx = [&](int c, float v) { jit_lam_add(lam, osp[c], v); };
+    auto addx = [&](int c, float v) { jit_lam_add(lam[0], osp[c], v); };
     if (kBin) {
         bin_grad(gq, gl, p.n_obs, p.ts, p.S, p.S);
 #pragma unroll
@@ -402,7 +423,7 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             const float tau = __fdividef(E0, a0);
             tau_k = tau;
             // BIN: t_{k+1} ends this interval and starts the next, in the bin of gq
-            if (kBin) mu -= bin_transition(xobs, xo, gq, p.n_obs);
+            if (kBin) mu[0] -= bin_transition(xobs, xo, gq, p.n_obs);
             // readout terms that involve X_{k+1} and the clock (LINEAR interpolation)
             float dt_dir = 0.0f, dtau_dir = 0.0f;
             if (READOUT == SSA_READOUT_LINEAR) {
@@ -411,9 +432,10 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
                     if (alpha < 0.0f) continue;
                     float c = 0.0f;
                     for (int o = 0; o < p.n_obs; ++o) {
-                        const float g = gl[(int64_t)s * p.n_obs + o];
+                        const float g = WIDE ? gl[(int64_t)s * p.n_obs + o] * inj : gl[(int64_t)s * p.n_obs + o];
                         const int sp = p.obs_sp[o];
-                        jit_lam_add(lam, sp, alpha * g);
+#pragma unroll
+                        for (int t = 0; t < NT; ++t) jit_lam_add(lam[t], sp, alpha * g);
                         c += g * (float)jit_dv(jk, sp);
                     }
                     const float c_tau = __fdividef(c, tau);
@@ -421,30 +443,33 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
                     dtau_dir -= alpha * c_tau;
                 }
             }
-            const float dtau = mu + dtau_dir;
-            const float dLda0 = -dtau * tau / a0;
-            // pass 2: soft-sample weights y~_j ~ exp2((l_j - l_max)/T) and W = sum y~ w
-            float wr[JM];
-            jit_w(lam, wr);
-            float Z = 0.0f, Wq = 0.0f;
 #pragma unroll
-            for (int j = 0; j < JM; ++j) {
-                const float q = lr[j] == -CUDART_INF_F ? 0.0f : exp2f((lr[j] - lmax) * invT);
-                lr[j] = q;
-                Z += q;
-                Wq += q * wr[j];
-            }
-            const float invZ = __fdividef(1.0f, Z), Wbar = Wq * invZ;
-            // pass 3: per-reaction adjoints, then the state adjoint of every reaction in order
-            float psi[JM], ctau[JM];
+            for (int t = 0; t < NT; ++t) {
+                const float dtau = mu[t] + dtau_dir;
+                const float dLda0 = -dtau * tau / a0;
+                // pass 2: soft-sample weights y~_j ~ exp2((l_j - l_max)/T) and W = sum y~ w
+                float wr[JM], qr[JM];
+                jit_w(lam[t], wr);
+                float Z = 0.0f, Wq = 0.0f;
 #pragma unroll
-            for (int j = 0; j < JM; ++j) {
-                psi[j] = lr[j] > 0.0f ? lr[j] * invZ * (wr[j] - Wbar) * invT : 0.0f;
-                dAr[j] += psi[j] + dLda0 * a[j];
-                ctau[j] = dLda0 * kr[j];
+                for (int j = 0; j < JM; ++j) {
+                    const float q = lr[j] == -CUDART_INF_F ? 0.0f : exp2f((lr[j] - lmax) * invT[t]);
+                    qr[j] = q;
+                    Z += q;
+                    Wq += q * wr[j];
+                }
+                const float invZ = __fdividef(1.0f, Z), Wbar = Wq * invZ;
+                // pass 3: per-reaction adjoints, then the state adjoint of every reaction in order
+                float psi[JM], ctau[JM];
+#pragma unroll
+                for (int j = 0; j < JM; ++j) {
+                    psi[j] = qr[j] > 0.0f ? qr[j] * invZ * (wr[j] - Wbar) * invT[t] : 0.0f;
+                    dAr[t][j] += psi[j] + dLda0 * a[j];
+                    ctau[j] = dLda0 * kr[j];
+                }
+                jit_state_adj(X, a, h, psi, ctau, lam[t]);
+                mu[t] += dt_dir;  // t_{k+1} = t_k + tau_k
             }
-            jit_state_adj(X, a, h, psi, ctau, lam);
-            mu += dt_dir;  // t_{k+1} = t_k + tau_k
         }
         if (kBin) {
             bin_state_terms(addx, d_first, d_last, gl, p.bin_prefix, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
@@ -460,7 +485,11 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
                     const float alpha = p.brk_a[(int64_t)s * n + i];
                     if (alpha >= 0.0f) coef = 1.0f - alpha;
                 }
-                for (int o = 0; o < p.n_obs; ++o) jit_lam_add(lam, p.obs_sp[o], coef * gl[(int64_t)s * p.n_obs + o]);
+                for (int o = 0; o < p.n_obs; ++o) {
+                    const float g = WIDE ? gl[(int64_t)s * p.n_obs + o] * inj : gl[(int64_t)s * p.n_obs + o];
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) jit_lam_add(lam[t], p.obs_sp[o], coef * g);
+                }
             }
         }
         if (ck_off == 0) {
@@ -469,6 +498,24 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             for (int s = 0; s < JN; ++s) mism += (ck[(int64_t)s * n] != X[s]);
             --ck_row;
             ck_off = p.K;
+            if constexpr (WIDE) {
+                float m = fabsf(mu[0]);
+#pragma unroll
+                for (int s = 0; s < JN; ++s) m = fmaxf(m, fabsf(lam[0][s]));
+#pragma unroll
+                for (int j = 0; j < JM; ++j) m = fmaxf(m, fabsf(dAr[0][j]));
+                if (m > 0x1p32f && m <= 3.4028235e38f) {
+                    const int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;  // 32 <= e <= 127
+                    const float f = ldexpf(1.0f, -e);
+                    mu[0] *= f;
+#pragma unroll
+                    for (int s = 0; s < JN; ++s) lam[0][s] *= f;
+#pragma unroll
+                    for (int j = 0; j < JM; ++j) dAr[0][j] *= f;
+                    sc += e;
+                    inj = ldexpf(1.0f, -sc);
+                }
+            }
         }
         --ck_off;
         if (k > 0) jit_unapply(X, event_at(k - 1));
@@ -784,10 +831,10 @@ __device__ __forceinline__ void jit_adj_soft_traj(const AdjParams &p, const floa
     if (mism) atomicAdd(p.mismatch, mism);
 }
 
-template <int READOUT, bool SOFT>
+template <int READOUT, bool SOFT, bool WIDE = false, int NT = 1>
 __device__ __forceinline__ void jit_adj(const AdjParams &p)
 {
-    extern __shared__ float s_dA[];  // [JM][blockDim.x]
+    extern __shared__ float s_dA[];  // [NT][JM][blockDim.x] (WIDE: binary64)
     __shared__ int s_len[256], s_perm[256];
     const int B = blockDim.x, tid = threadIdx.x;
     const int64_t n = p.n_traj;
@@ -805,30 +852,53 @@ __device__ __forceinline__ void jit_adj(const AdjParams &p)
     s_perm[rank] = tid;
     __syncthreads();
     const int64_t i = i0 + s_perm[tid];
-    float kr[JM], dAr[JM];
+    float kr[JM], dAr[NT][JM];
 #pragma unroll
     for (int j = 0; j < JM; ++j) {
         kr[j] = p.k_rates[j];
-        dAr[j] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) dAr[t][j] = 0.0f;
     }
     int st = -1;
     if (i < n) st = p.status[i];
     const bool active = st == SSA_TRAJ_OK || st == SSA_TRAJ_ABSORBED || st == SSA_TRAJ_STEP_CAP;
+    int sc = 0;
     if (active) {
-        if constexpr (SOFT) jit_adj_soft_traj<READOUT>(p, kr, i, st, dAr);
-        else jit_adj_traj<READOUT>(p, kr, i, st, dAr);
+        if constexpr (SOFT) jit_adj_soft_traj<READOUT>(p, kr, i, st, dAr[0]);
+        else jit_adj_traj<READOUT, WIDE, NT>(p, kr, i, st, dAr, sc);
+    }
+    const int warp = tid >> 5, lane = tid & 31, nwarps = B >> 5;
+    if constexpr (WIDE) {
+        // binary64 values dAr 2^sc, reduced over the block in a fixed order
+        // (a trajectory whose accumulators overflowed within one segment contributes inf or NaN, which
+        // reaches the result)
+        double *s_dA64 = reinterpret_cast<double *>(s_dA);
+#pragma unroll
+        for (int j = 0; j < JM; ++j) s_dA64[j * B + tid] = ldexp((double)dAr[0][j], sc);
+        __syncthreads();
+        for (int j = warp; j < JM; j += nwarps) {
+            double acc = 0.0;
+            for (int u = lane; u < B; u += 32) acc += s_dA64[j * B + u];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) p.partial64[(int64_t)blockIdx.x * JM + j] = acc;
+        }
+        return;
     }
 #pragma unroll
-    for (int j = 0; j < JM; ++j) s_dA[j * B + tid] = dAr[j];
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int j = 0; j < JM; ++j) s_dA[(t * JM + j) * B + tid] = dAr[t][j];
     __syncthreads();
-    // fixed-order block reduction of the per-reaction adjoints (the generic kernels' order)
-    const int warp = tid >> 5, lane = tid & 31, nwarps = B >> 5;
-    for (int j = warp; j < JM; j += nwarps) {
+    // fixed-order block reduction of the per-reaction adjoints (the generic kernels' order); temperature t
+    // writes its block sums to partial + t gridDim.x JM
+    for (int tj = warp; tj < NT * JM; tj += nwarps) {
         float acc = 0.0f;
-        for (int u = lane; u < B; u += 32) acc += s_dA[j * B + u];
+        for (int u = lane; u < B; u += 32) acc += s_dA[tj * B + u];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) p.partial[(int64_t)blockIdx.x * JM + j] = acc;
+        const int t = tj / JM, j = tj - t * JM;
+        if (lane == 0) p.partial[((int64_t)t * gridDim.x + blockIdx.x) * JM + j] = acc;
     }
 }
 
@@ -882,6 +952,30 @@ extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_linear(const ssa::
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_bin(const ssa::AdjParams p)
 {
     ssa::jit_adj<SSA_READOUT_BIN, false>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_hold_t2(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_HOLD, false, false, 2>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_hold_t3(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_HOLD, false, false, 3>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_linear_t2(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_LINEAR, false, false, 2>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_linear_t3(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_LINEAR, false, false, 3>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_hold_wide(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_HOLD, false, true>(p);
+}
+extern "C" __global__ void __launch_bounds__(256) ssa_jit_adj_linear_wide(const ssa::AdjParams p)
+{
+    ssa::jit_adj<SSA_READOUT_LINEAR, false, true>(p);
 }
 #else  // the soft-forward program of the same network
 extern "C" __global__ void __launch_bounds__(256) ssa_jit_fwd_hold_soft(const ssa::FwdParams p)

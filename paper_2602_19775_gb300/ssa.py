@@ -207,10 +207,7 @@ def forward(net: Network, log_rates, n_traj: int, x0, t_end: float, sample_times
     return ForwardResult(obs_out, draws, status, run)
 
 
-def backward(fwd: ForwardResult | Run, dl_dobs: torch.Tensor, temperature: float, out: torch.Tensor | None = None,
-             stream=None) -> torch.Tensor:
-    """ssa_backward: dL/dlog k [P] (float32) for a recorded forward."""
-    run = fwd.run if isinstance(fwd, ForwardResult) else fwd
+def _upstream(run: Run, dl_dobs: torch.Tensor):
     g = dl_dobs.to(torch.float32).contiguous()
     if tuple(g.shape) == (run.n_traj, run.S, run.n_obs):
         stride = run.S * run.n_obs
@@ -219,10 +216,45 @@ def backward(fwd: ForwardResult | Run, dl_dobs: torch.Tensor, temperature: float
     else:
         raise SSAError(f"dl_dobs shape {tuple(g.shape)} is neither {(run.n_traj, run.S, run.n_obs)} "
                        f"nor {(run.S, run.n_obs)}")
+    return g, stride
+
+
+def backward(fwd: ForwardResult | Run, dl_dobs: torch.Tensor, temperature: float, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    """ssa_backward: dL/dlog k [P] (float32) for a recorded forward."""
+    run = fwd.run if isinstance(fwd, ForwardResult) else fwd
+    g, stride = _upstream(run, dl_dobs)
     if out is None:
         out = torch.empty(run.net.n_params, dtype=torch.float32, device=g.device)
     check(_lib.lib().ssa_backward(run.handle, _ptr(g), stride, ctypes.c_float(float(temperature)), _ptr(out),
                                   _stream(stream)))
+    return out
+
+
+def backward_multi(fwd: ForwardResult | Run, dl_dobs: torch.Tensor, temperatures, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """ssa_backward_multi: dL/dlog k [n_T, P] (float32), row t at temperatures[t], from one walk of the
+    recorded forward for up to three temperatures at a time (network-specialised kernels)."""
+    run = fwd.run if isinstance(fwd, ForwardResult) else fwd
+    g, stride = _upstream(run, dl_dobs)
+    temps = (ctypes.c_float * len(temperatures))(*[float(t) for t in temperatures])
+    if out is None:
+        out = torch.empty((len(temperatures), run.net.n_params), dtype=torch.float32, device=g.device)
+    check(_lib.lib().ssa_backward_multi(run.handle, _ptr(g), stride, temps, len(temperatures), _ptr(out),
+                                        _stream(stream)))
+    return out
+
+
+def backward_wide(fwd: ForwardResult | Run, dl_dobs: torch.Tensor, temperature: float,
+                  out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """ssa_backward_wide: dL/dlog k [P] (float64) with a per-trajectory exponent in the walk, for
+    trajectories whose adjoint grows beyond the binary32 range (network-specialised kernels, HOLD or LINEAR)."""
+    run = fwd.run if isinstance(fwd, ForwardResult) else fwd
+    g, stride = _upstream(run, dl_dobs)
+    if out is None:
+        out = torch.empty(run.net.n_params, dtype=torch.float64, device=g.device)
+    check(_lib.lib().ssa_backward_wide(run.handle, _ptr(g), stride, ctypes.c_float(float(temperature)), _ptr(out),
+                                       _stream(stream)))
     return out
 
 
