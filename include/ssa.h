@@ -191,7 +191,8 @@ ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t dl_traj_stri
 
 /*
  * ssa_backward_multi -- the straight-through gradient of one recorded forward at several temperatures
- * (Eq. 3's T; e.g. T in {0.1, 0.5, 1.0}), each exactly what ssa_backward gives at that T. The reverse
+ * (Eq. 3's T; e.g. T in {0.1, 0.5, 1.0}), each what ssa_backward gives at that T (to binary32 rounding
+ * where one walk serves several temperatures). The reverse
  * walk, the regenerated noise, the propensities and the keys do not depend on T: on the
  * network-specialised kernels (ssa_run_variant = 2, Gumbel-max forward, HOLD or LINEAR readout) one walk
  * serves up to three temperatures at once, each with its own lambda, mu and partial sums; otherwise,
@@ -481,7 +482,11 @@ ssa_status ssa_batch_item_brackets(const ssa_batch *batch, int32_t item, int32_t
  * variant (threads_per_traj = 0 and N, M <= 16) time min(pilot_traj, n_traj) trajectories through
  * ssa_forward(record) + ssa_backward under both and keep the faster. Then all items' pilots run
  * together as one pilot batch, and each item's cost estimate (used to order the work longest first)
- * becomes its pilot's mean draws (host_draws_out [n_items] receives them, may be NULL). Allocates and
+ * becomes its pilot's mean draws (host_draws_out [n_items] receives them, may be NULL). Last, the
+ * checkpoint interval of every item that did not fix one: the pilot batch is timed with K = c x
+ * 16 N (rounded to a multiple of 8 in [8, 4096]) for c in {1/4, 1, 4} and the fastest c is kept (the
+ * reverse walk rebuilds states exactly from the event log, so K sets only how often the state is
+ * stored and checked). Allocates and
  * frees pilot buffers with cudaMalloc, synchronises `stream`, writes nothing the caller owns.
  * Invalidates the captured graph and the workspace layout; the workspace size may change (more units
  * for the warp variant).
@@ -491,6 +496,9 @@ ssa_status ssa_batch_autotune(ssa_batch *batch, int64_t pilot_traj, void *stream
 
 /* ssa_batch_item_variant -- the item's planned variant: 1 (thread) or 32 (warp); 0 if invalid. */
 int32_t ssa_batch_item_variant(const ssa_batch *batch, int32_t item);
+
+/* ssa_batch_item_ckpt_interval -- the item's planned checkpoint interval K; 0 if invalid. */
+int32_t ssa_batch_item_ckpt_interval(const ssa_batch *batch, int32_t item);
 
 const char *ssa_last_error(void);
 

@@ -32,7 +32,7 @@ EXPORTS = (
     "ssa_grn_workspace_bytes", "ssa_grn_forward", "ssa_grn_backward", "ssa_grn_activations",
     "ssa_batch_create", "ssa_batch_destroy", "ssa_batch_set_plan", "ssa_batch_workspace_bytes", "ssa_batch_run",
     "ssa_batch_item_outputs", "ssa_batch_autotune", "ssa_batch_item_variant", "ssa_batch_item_events",
-    "ssa_batch_item_brackets", "ssa_run_variant", "ssa_network_specialize", "ssa_exp_variates",
+    "ssa_batch_item_brackets", "ssa_batch_item_ckpt_interval", "ssa_run_variant", "ssa_network_specialize", "ssa_exp_variates",
 )
 
 
@@ -122,6 +122,7 @@ def _declare(lib):
         "ssa_batch_item_outputs": (i32, [p, i32, p, p, p, p]),
         "ssa_batch_autotune": (i32, [p, i64, p, p]),
         "ssa_batch_item_variant": (i32, [p, i32]),
+        "ssa_batch_item_ckpt_interval": (i32, [p, i32]),
         "ssa_batch_item_events": (i32, [p, i32, p, i64, p]),
         "ssa_batch_item_brackets": (i32, [p, i32, p, p]),
         "ssa_run_variant": (i32, [p]),

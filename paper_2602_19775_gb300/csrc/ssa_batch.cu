@@ -271,6 +271,7 @@ struct ssa_batch {
     std::vector<ssa_batch_item> items;
     std::vector<int> variant, mc, K;
     std::vector<double> est_draws;
+    double ckpt_scale = 1.0;  // the autotuner's multiple of the default checkpoint interval
     int readout;
     float temperature;
     // laid out in the caller's workspace by the first run with it
@@ -364,9 +365,16 @@ void drop_graph(ssa_batch *bt)
 
 int default_ckpt(const ssa_network *net)
 {
-    // checkpoints cost 4N/K bytes per draw beside the 2-byte event; K ~ 16 N keeps them near a
-    // quarter of the log while bounding the re-simulation of each adjoint segment
+    // checkpoints cost 4N/K bytes per draw beside the 2-byte event; K ~ 16 N keeps them near an eighth of
+    // the log
     return std::min(1024, std::max(16, (16 * net->N + 7) / 8 * 8));
+}
+
+// c x the default interval, a multiple of 8 in [8, 4096]
+int scaled_ckpt(const ssa_network *net, double c)
+{
+    const int k = (int)(c * default_ckpt(net) / 8.0 + 0.5) * 8;
+    return std::min(4096, std::max(8, k));
 }
 
 }  // namespace
@@ -848,6 +856,58 @@ extern "C" ssa_status ssa_batch_autotune(ssa_batch *bt, int64_t pilot_traj, void
         if (pws) cudaFree(pws);
         ssa_batch_destroy(pb);
     }
+    // 3. checkpoint interval: the reverse walk rebuilds every state exactly from the event log, so K only sets
+    // how often the forward stores the state (4 N / K bytes per draw beside the 2-byte event) and the adjoint
+    // checks it. Time the pilot batch with K = c x the default of each network for c in {1/4, 1, 4} (one
+    // untimed and one timed launch each) and keep the fastest c.
+    if (rc == SSA_OK) {
+        const double scales[3] = {0.25, 1.0, 4.0};
+        float best_ms = -1.0f;
+        double best_c = 1.0;
+        for (double c : scales) {
+            std::vector<ssa_batch_item> pil(bt->items);
+            size_t off = 0;
+            for (size_t it = 0; it < n_items; ++it) {
+                ssa_batch_item &q = pil[it];
+                q.n_traj = np[it];
+                q.threads_per_traj = bt->variant[it];
+                q.ckpt_interval = scaled_ckpt(bt->items[it].net, c);
+                q.obs_out = static_cast<float *>(obs) + off;
+                q.dl_dobs = static_cast<float *>(dl) + off;
+                q.dl_traj_stride = (int64_t)q.n_samples * q.n_obs;
+                q.dl_dlog_rates = static_cast<float *>(dth) + p_max * it;
+                off += (size_t)np[it] * q.n_samples * q.n_obs;
+            }
+            ssa_batch *pb = nullptr;
+            rc = ssa_batch_create(pil.data(), (int32_t)n_items, bt->readout, bt->temperature, &pb);
+            for (size_t it = 0; it < n_items && rc == SSA_OK; ++it)
+                rc = ssa_batch_set_plan(pb, (int32_t)it, bt->variant[it], pil[it].ckpt_interval, bt->est_draws[it]);
+            void *pws = nullptr;
+            float ms = -1.0f;
+            if (rc == SSA_OK) {
+                const size_t need = ssa_batch_workspace_bytes(pb);
+                if (cudaMalloc(&pws, need) != cudaSuccess) rc = set_error(SSA_ERR_CUDA, "pilot batch allocation failed");
+                if (rc == SSA_OK) rc = ssa_batch_run(pb, pws, need, 0, stream);
+                if (rc == SSA_OK) {
+                    cudaEventRecord(e0, st);
+                    rc = ssa_batch_run(pb, pws, need, 0, stream);
+                    cudaEventRecord(e1, st);
+                    if (rc == SSA_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                }
+            }
+            if (pws) cudaFree(pws);
+            ssa_batch_destroy(pb);
+            if (rc != SSA_OK) break;
+            if (ms >= 0.0f && (best_ms < 0.0f || ms < best_ms)) {
+                best_ms = ms;
+                best_c = c;
+            }
+        }
+        if (rc == SSA_OK)
+            for (size_t it = 0; it < n_items; ++it)
+                if (!bt->items[it].ckpt_interval) bt->K[it] = scaled_ckpt(bt->items[it].net, best_c);
+        bt->ckpt_scale = best_c;
+    }
     if (host_draws_out)
         for (size_t it = 0; it < n_items; ++it) host_draws_out[it] = bt->est_draws[it];
     if (e0) cudaEventDestroy(e0);
@@ -867,4 +927,10 @@ extern "C" int32_t ssa_batch_item_variant(const ssa_batch *bt, int32_t item)
 {
     if (!bt || item < 0 || item >= (int)bt->items.size()) return 0;
     return bt->variant[item];
+}
+
+extern "C" int32_t ssa_batch_item_ckpt_interval(const ssa_batch *bt, int32_t item)
+{
+    if (!bt || item < 0 || item >= (int)bt->items.size()) return 0;
+    return bt->K[item];
 }

@@ -341,6 +341,10 @@ class Batch:
     def variant(self, item: int) -> int:
         return int(_lib.lib().ssa_batch_item_variant(self.handle, int(item)))
 
+    def ckpt_interval(self, item: int) -> int:
+        """The item's planned checkpoint interval K (the autotuner's choice unless the item fixed one)."""
+        return int(_lib.lib().ssa_batch_item_ckpt_interval(self.handle, int(item)))
+
     def run(self, use_graph: bool = False, stream=None) -> list:
         """ssa_batch_run: fills obs[i] and dtheta[i] for every item; returns dtheta."""
         need = self.workspace_bytes()

@@ -153,6 +153,16 @@ def test_batch_autotune_plan_is_valid_and_exact(S, specs):
     draws = b.autotune(pilot_traj=32)
     assert all(d >= 1.0 for d in draws)
     assert b.variant(5) == 32  # requested explicitly
+    # the checkpoint interval: c x 16 N for one of the three timed scales, or the item's own
+    for q, (spec, *_rest) in enumerate(specs):
+        K = b.ckpt_interval(q)
+        fixed = items[q].get("ckpt_interval", 0)
+        if fixed:
+            assert K == fixed
+        else:
+            base = min(1024, max(16, (16 * spec.n_species + 7) // 8 * 8))
+            assert K % 8 == 0 and 8 <= K <= 4096
+            assert K in {min(4096, max(8, int(c * base / 8.0 + 0.5) * 8)) for c in (0.25, 1.0, 4.0)}, (q, K)
     _fill_dl(b, specs)
     b.run()
     _check_against_single(S, b, specs, nets, items, 0.7)
@@ -318,3 +328,34 @@ def test_batch_matches_oracle_on_all_256_networks(S):
             continue
         rel = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30)
         assert rel < GRAD_RTOL, (q, rel)
+
+
+def test_batch_autotuned_checkpoint_interval_changes_no_result(S):
+    """Items that leave K free get the autotuner's interval (one of the three timed multiples of 16 N); the
+    results are those of the same batch with K fixed at 64 bit for bit (K only sets how often the state is
+    stored and checked)."""
+    wl = W.config_c4(n_nets=6, traj_scale=1.0 / 128)
+    nets = [S.Network(spec) for spec in wl.nets]
+
+    def items(K):
+        return [dict(net=nets[q], log_rates=spec.log_rates.astype(np.float32), n_traj=int(wl.n_traj[q]), x0=spec.x0,
+                     t_end=wl.t_end, sample_times=wl.sample_times, obs_species=wl.obs_species[q], seed=20 + q,
+                     max_steps=1 << 16, **({"ckpt_interval": K} if K else {})) for q, spec in enumerate(wl.nets)]
+
+    runs = []
+    for K in (0, 64):
+        b = S.Batch(items(K), readout="linear", temperature=wl.temperature)
+        b.autotune(pilot_traj=16)
+        for q in range(len(nets)):
+            b.dl_dobs[q].copy_(torch.tensor(W.seeded_dl_dobs(q, int(wl.n_traj[q]), len(wl.sample_times),
+                                                             len(wl.obs_species[q]), scale=1e-3), dtype=torch.float32))
+        b.run()
+        torch.cuda.synchronize()
+        runs.append(b)
+    free, fixed = runs
+    for q, spec in enumerate(wl.nets):
+        base = min(1024, max(16, (16 * spec.n_species + 7) // 8 * 8))
+        assert free.ckpt_interval(q) in {min(4096, max(8, int(c * base / 8.0 + 0.5) * 8)) for c in (0.25, 1.0, 4.0)}
+        assert fixed.ckpt_interval(q) == 64
+        assert torch.equal(free.obs[q], fixed.obs[q]) and torch.equal(free.dtheta[q], fixed.dtheta[q]), q
+        assert free.outputs(q)[2] == 0 and fixed.outputs(q)[2] == 0

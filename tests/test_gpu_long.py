@@ -96,8 +96,9 @@ def test_wide_adjoint_refuses_other_runs(S):
 
 @pytest.mark.parametrize("case,readout", [("dimer", "linear"), ("mixed_orders", "hold"), ("oscillator", "linear")])
 def test_multi_temperature_walk_equals_one_walk_per_temperature(S, case, readout):
-    """One walk for several temperatures gives, row by row, exactly the single-temperature gradients:
-    fused for 2 and 3 temperatures, 3 + 1 for 4, and one walk each on the generic kernels."""
+    """One walk for several temperatures gives, row by row, the single-temperature gradients to binary32
+    rounding (the two kernels may contract products into fused multiply-adds differently): fused for 2 and 3
+    temperatures, 3 + 1 for 4, and one walk each on the generic kernels (there bit for bit)."""
     spec, t_end, n = {"dimer": (W.dimerization_2a_b(), 50.0, 2000), "mixed_orders": (W.mixed_orders_toy(), 6.0, 1500),
                       "oscillator": (W.vilar_oscillator(), 1.0, 600)}[case]
     theta = torch.tensor(spec.log_rates.astype(np.float32), device="cuda")
@@ -113,6 +114,10 @@ def test_multi_temperature_walk_equals_one_walk_per_temperature(S, case, readout
             multi = S.backward_multi(fw, dl, temps)
             for t, T in enumerate(temps):
                 one = S.backward(fw, dl, T)
-                assert torch.equal(multi[t], one), (specialize, temps, t, multi[t], one)
+                if specialize:
+                    err = (multi[t] - one).abs().max().item()
+                    assert err <= 1e-5 * one.abs().max().item(), (temps, t, multi[t], one)
+                else:
+                    assert torch.equal(multi[t], one), (temps, t, multi[t], one)
         _, mism = fw.run.status_counts()
         assert mism == 0
