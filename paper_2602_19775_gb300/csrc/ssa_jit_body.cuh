@@ -44,9 +44,95 @@ __device__ __forceinline__ void jit_bin_init(const FwdParams &p, bool bad_obs, f
     }
 }
 
+// Coalesced sample stores. A trajectory's samples are one row of obs [n_traj][S][n_obs], written one at a
+// time as its clock passes them, so a warp's per-thread stores land in 32 different rows. Instead each
+// thread collects a window of W = 16 / n_obs consecutive samples (n_obs <= 4) in its row of a per-block
+// shared buffer; at the top of every step the warp's active lanes copy the completed windows together, two
+// windows per store instruction (consecutive words of two rows). A lane whose window fills
+// while it still has samples to write in the same step, and every lane after its last step, writes its own
+// window. The values and their places are those of direct stores.
+constexpr int kJitFwdBlock = 64;    // threads per block of the specialised forwards
+constexpr int kStageWords = 16;     // words of a thread's sample window
+
+struct SampleStage {
+    uint32_t *row;   // this thread's window in shared memory
+    uint32_t *out;   // obs_out as 32-bit words
+    int64_t base;    // first word of this trajectory's row
+    int n_obs, W, S;
+    int lo, cnt;     // the window holds samples lo .. lo + cnt - 1
+    bool ready;      // complete and not yet copied
+};
+
+__device__ __forceinline__ void stage_own_flush(SampleStage &g)
+{
+    const int words = g.cnt * g.n_obs;
+    uint32_t *dst = g.out + g.base + (int64_t)g.lo * g.n_obs;
+    for (int q = 0; q < words; ++q) dst[q] = g.row[q];
+    g.lo += g.cnt;
+    g.cnt = 0;
+    g.ready = false;
+}
+
+// one sample s (the next in order) of n_obs values
+template <class VAL>
+__device__ __forceinline__ void stage_put(SampleStage &g, int s, const VAL &val)
+{
+    if (g.ready) stage_own_flush(g);  // a second window completes within one step
+    uint32_t *w = g.row + g.cnt * g.n_obs;
+    for (int c = 0; c < g.n_obs; ++c) w[c] = val(c);
+    ++g.cnt;
+    if (g.cnt == g.W || s + 1 == g.S) g.ready = true;
+}
+
+// the warp's active lanes copy every completed window, two at a time
+__device__ __forceinline__ void stage_warp_flush(SampleStage &g, const uint32_t *s_stage)
+{
+    const unsigned m = __activemask();
+    unsigned rd = __ballot_sync(m, g.ready);
+    if (!rd) return;
+    const int lane = threadIdx.x & 31;
+    const int first = threadIdx.x & ~31;
+    const int rank = __popc(m & ((1u << lane) - 1u)), nm = __popc(m);
+    const int64_t dst = g.base + (int64_t)g.lo * g.n_obs;
+    const int words = g.cnt * g.n_obs;
+    __syncwarp(m);
+    while (rd) {
+        const int a = __ffs(rd) - 1;
+        rd &= rd - 1;
+        int b = -1;
+        if (rd) {
+            b = __ffs(rd) - 1;
+            rd &= rd - 1;
+        }
+        const long long da = __shfl_sync(m, (long long)dst, a);
+        const int wa = __shfl_sync(m, words, a);
+        long long db = 0;
+        int wb = 0;
+        if (b >= 0) {
+            db = __shfl_sync(m, (long long)dst, b);
+            wb = __shfl_sync(m, words, b);
+        }
+        // the words of window a, then of window b, shared out over the participating lanes in the order of
+        // their lane numbers (lanes that have left the step loop take no part): one store instruction when all
+        // 32 lanes take part, a few otherwise
+        for (int pw = rank; pw < wa + wb; pw += nm) {
+            const bool in_a = pw < wa;
+            const int q = in_a ? pw : pw - wa;
+            g.out[(in_a ? da : db) + q] = s_stage[(first + (in_a ? a : b)) * kStageWords + q];
+        }
+    }
+    __syncwarp(m);
+    if (g.ready) {
+        g.lo += g.cnt;
+        g.cnt = 0;
+        g.ready = false;
+    }
+}
+
 template <int READOUT, bool RECORD>
 __device__ __forceinline__ void jit_fwd(const FwdParams &p)
 {
+    __shared__ uint32_t s_stage[kJitFwdBlock * kStageWords];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n_traj) return;
     const int64_t n = p.n_traj;
@@ -83,8 +169,12 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
     int osp[kBinMaxObs];
     jit_bin_init(p, bad_obs, bacc, osp);
     auto xobs = [&](int c) { return jit_xsel(X, osp[c]); };
+    const bool staged = READOUT != SSA_READOUT_BIN && p.n_obs >= 1 && p.n_obs <= 4 && blockDim.x <= kJitFwdBlock;
+    SampleStage stg{s_stage + threadIdx.x * kStageWords, static_cast<uint32_t *>(p.obs_out), i * p.S * p.n_obs,
+                    p.n_obs, staged ? kStageWords / p.n_obs : 1, p.S, 0, 0, false};
 
     while (!bad_input) {
+        if (staged) stage_warp_flush(stg, s_stage);
         if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
         step_noise<NQ>(En, (uint32_t)(k + 1), c2, c3, key0, key1);  // next step, state-independent
         float a[JM], h[JM];
@@ -100,7 +190,7 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
         if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
         if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
         if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }
-        const float tau = __fdividef(E0, a0);
+        const float tau = waiting_time(E0, a0);
         const double t_next = t + f2d_pos(tau);
         const bool slow = gt_nonneg(t_next, thr);
         const bool cross = slow && gt_nonneg(t_next, p.t_end);
@@ -121,14 +211,23 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
             } else {
                 while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
                     if (READOUT == SSA_READOUT_HOLD) {
-                        int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                        for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
+                        if (staged) {
+                            stage_put(stg, s, [&](int c) { return (uint32_t)jit_xsel(X, p.obs_sp[c]); });
+                        } else {
+                            int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                            for (int c = 0; c < p.n_obs; ++c) o[c] = jit_xsel(X, p.obs_sp[c]);
+                        }
                     } else {
                         const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
-                        float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-                        for (int c = 0; c < p.n_obs; ++c) {
+                        auto lin = [&](int c) {
                             const int sp = p.obs_sp[c];
-                            o[c] = __fmaf_rn(alpha, (float)jit_dv(jb, sp), (float)jit_xsel(X, sp));
+                            return __fmaf_rn(alpha, (float)jit_dv(jb, sp), (float)jit_xsel(X, sp));
+                        };
+                        if (staged) {
+                            stage_put(stg, s, [&](int c) { return __float_as_uint(lin(c)); });
+                        } else {
+                            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                            for (int c = 0; c < p.n_obs; ++c) o[c] = lin(c);
                         }
                         if (RECORD) p.brk_a[(int64_t)s * n + i] = alpha;
                     }
@@ -159,15 +258,24 @@ __device__ __forceinline__ void jit_fwd(const FwdParams &p)
     if constexpr (READOUT == SSA_READOUT_BIN) bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs, bruns);
     for (; READOUT != SSA_READOUT_BIN && s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
-            int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-            for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : jit_xsel(X, p.obs_sp[c]);
+            if (staged) {
+                stage_put(stg, s, [&](int c) { return (uint32_t)(bad_obs ? 0 : jit_xsel(X, p.obs_sp[c])); });
+            } else {
+                int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0 : jit_xsel(X, p.obs_sp[c]);
+            }
         } else {
-            float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
-            for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)jit_xsel(X, p.obs_sp[c]);
+            if (staged) {
+                stage_put(stg, s, [&](int c) { return __float_as_uint(bad_obs ? 0.0f : (float)jit_xsel(X, p.obs_sp[c])); });
+            } else {
+                float *o = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+                for (int c = 0; c < p.n_obs; ++c) o[c] = bad_obs ? 0.0f : (float)jit_xsel(X, p.obs_sp[c]);
+            }
             if (RECORD) p.brk_a[(int64_t)s * n + i] = -1.0f;
         }
         if (RECORD) p.brk_k[(int64_t)s * n + i] = k;
     }
+    if (staged && stg.cnt > 0) stage_own_flush(stg);  // the last window, by the thread itself
     p.draws[i] = draws;
     p.status[i] = status;
     if (RECORD) {
@@ -248,7 +356,7 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
         }
         if (jb < 0) jb = last;  // u_1 a0 rounded up to a0: the last active reaction
         if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }
-        const float tau = __fdividef(E0, a0);
+        const float tau = waiting_time(E0, a0);
         const double t_next = t + f2d_pos(tau);
         const bool slow = gt_nonneg(t_next, thr);
         const bool cross = slow && gt_nonneg(t_next, p.t_end);
@@ -307,7 +415,8 @@ __device__ __forceinline__ void jit_fwd_direct(const FwdParams &p)
 // NT temperatures at once (NT > 1): the walk, the regenerated noise, the propensities, the race check and
 // the log keys do not depend on T, so they are computed once per step; each temperature t keeps its own
 // lambda, mu and dAr[t] and runs the T-dependent part (soft weights, psi, the state adjoint) with invT_t,
-// in the same operation order as a single-temperature walk, so every dAr[t] equals that walk's bit for bit.
+// in the same operation order as a single-temperature walk, so every dAr[t] equals that walk's to binary32
+// rounding (the two kernels may contract products into fused multiply-adds differently).
 //
 // WIDE (long trajectories, NT = 1): the adjoint is linear in the upstream gradient, and over ~1e6 draws the
 // straight-through recursion can grow it far beyond the binary32 range (on the oscillator to ~1e73 at
@@ -420,7 +529,7 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
                 lmax = fmaxf(lmax, lr[j]);
             }
             mism += (jb != jk);
-            const float tau = __fdividef(E0, a0);
+            const float tau = waiting_time(E0, a0);
             tau_k = tau;
             // BIN: t_{k+1} ends this interval and starts the next, in the bin of gq
             if (kBin) mu[0] -= bin_transition(xobs, xo, gq, p.n_obs);
@@ -618,7 +727,7 @@ __device__ __forceinline__ void jit_fwd_soft(const FwdParams &p)
         const float a0 = jit_soft_step(X, kr, E, p.invT, a, h, y, dX);
         if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
         if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
-        const float tau = __fdividef(E[0], a0);
+        const float tau = waiting_time(E[0], a0);
         const double t_next = t + f2d_pos(tau);
         const bool slow = gt_nonneg(t_next, thr);
         const bool cross = slow && gt_nonneg(t_next, p.t_end);
@@ -768,7 +877,7 @@ __device__ __forceinline__ void jit_adj_soft_traj(const AdjParams &p, const floa
                 float E[NQ], a[JM], h[JM], y[JM], dX[JN];
                 step_noise<NQ>(E, (uint32_t)k, c2, c3, key0, key1);
                 const float a0 = jit_soft_step(Xk, kr, E, invT, a, h, y, dX);
-                const float tau = __fdividef(E[0], a0);
+                const float tau = waiting_time(E[0], a0);
                 tau_k = tau;
                 float dt_dir = 0.0f, dtau_dir = 0.0f;
                 if (kBin) {  // t_{k+1} ends this interval and starts the next, in the bin of gq

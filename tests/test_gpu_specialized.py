@@ -131,3 +131,32 @@ def test_direct_method_is_forward_only(S):
     with pytest.raises(SSAError):
         S.forward(net, torch.tensor(spec.log_rates.astype(np.float32), device="cuda"), 8, spec.x0, 1.0, [1.0], [0],
                   0, record=True, selector="direct")
+
+
+@pytest.mark.parametrize("readout", ["hold", "linear"])
+@pytest.mark.parametrize("record", [False, True])
+def test_staged_sample_stores_match_direct_stores(S, readout, record):
+    """The specialised forward collects each thread's samples in windows and copies completed windows warp-wide;
+    the observables must be those of the generic kernels' direct stores bit for bit: dense grids where
+    several windows complete within one step, 1 to 4 observables (5 is stored directly), paths that absorb
+    early (the held tail), and a partial last warp."""
+    cases = [
+        (W.immigration_death(), 5.0, 2003, [0]),                       # ~100 samples per event
+        (W.mixed_orders_toy(), 6.0, 997, [0, 1]),
+        (W.mixed_orders_toy(), 6.0, 333, [2, 0, 1]),
+        (W.vilar_oscillator(), 0.5, 129, [6, 7, 8, 0]),
+        (W.vilar_oscillator(), 0.5, 77, [6, 7, 8, 0, 1]),              # n_obs = 5: direct stores
+        (W.network_from_reactions(["A"], [(["A"], [], "d")], {"d": 2.0}, {"A": 20}), 30.0, 600, [0]),  # absorbs
+    ]
+    for spec, t_end, n_s, obs in cases:
+        net = S.Network(spec)
+        theta = torch.tensor(spec.log_rates.astype(np.float32), device="cuda")
+        ts = W.uniform_sample_grid(t_end, n_s)
+        n = 1000
+        runs = [S.forward(net, theta, n, spec.x0, t_end, ts, obs, 11, readout=readout, record=record, max_steps=1 << 16,
+                          threads_per_traj=1, specialize=sp) for sp in (True, False)]
+        assert runs[0].run.variant == 2 and runs[1].run.variant == 1
+        assert torch.equal(runs[0].obs, runs[1].obs), (spec.species, n_s, obs)
+        assert torch.equal(runs[0].draws, runs[1].draws)
+        if record:
+            assert torch.equal(runs[0].run.brackets(), runs[1].run.brackets())
