@@ -152,7 +152,7 @@ __device__ __forceinline__ void thread_adj_body(const AdjParams &p, const int4 *
                 }
             }
             mism += (jb != jk);
-            const float tau = __fdividef(E0, a0);
+            const float tau = waiting_time(E0, a0);
             tau_k = tau;
             const int4 rk = s_rx[jk];
             // BIN: t_{k+1} ends this interval and starts the next, in the bin of gq

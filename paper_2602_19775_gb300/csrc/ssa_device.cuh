@@ -85,6 +85,21 @@ __device__ __forceinline__ float mass_action_h(const int4 rx, const int *X, int 
     return h_hetero(x1, X[rx.y * stride]);
 }
 
+// The same value as mass_action_h from selects instead of branches: the lanes of a warp-per-trajectory kernel
+// evaluate reactions of different orders side by side, and branches on the order would run one after another.
+// An absent reactant counts as 1 (order 0: 1 x 1; order 1: x1 x 1, exact); a homodimer multiplies x1 by
+// max(x1 - 1, 0) and halves (0 for x1 < 2). Counts of 2^23 and more take the exact 64-bit path.
+__device__ __forceinline__ float mass_action_h_sel(const int4 rx, const int *X)
+{
+    const bool homo = rx.y >= 0 && rx.y == rx.x;
+    const int x1 = rx.x >= 0 ? X[rx.x >= 0 ? rx.x : 0] : 1;
+    const int xr2 = X[rx.y >= 0 ? rx.y : 0];
+    const int x2 = homo ? max(x1 - 1, 0) : (rx.y >= 0 ? xr2 : 1);
+    if ((unsigned)(x1 | x2) >= (1u << 23)) return mass_action_h(rx, X, 1);
+    const float h = __fmul_rn(int2f(x1), int2f(x2));
+    return homo ? h * 0.5f : h;
+}
+
 // a > b for non-negative, non-NaN binary64 values: IEEE 754 orders them like their bit patterns
 // read as unsigned integers, so the comparison runs on the integer pipe instead of the FP64 pipe.
 __device__ __forceinline__ bool gt_nonneg(double a, double b)
@@ -154,6 +169,12 @@ __device__ __forceinline__ float exp_variate(uint32_t k, int q, uint32_t c2, uin
     }
     return neg_log_unit(u01(word_of(cache, q & 3)));
 }
+
+// The waiting time tau = E_0 / a0 (Section 2), rounded once (IEEE division). The clock adds ~1e6 of these
+// over a long trajectory; an approximate division's error is not centred on zero, and its bias would move
+// the clock systematically (by ~1e-5 over 1e6 draws of the oscillator), flipping sample brackets and the
+// LINEAR readout's interpolation weights.
+__device__ __forceinline__ float waiting_time(float E0, float a0) { return __fdiv_rn(E0, a0); }
 
 // The Gumbel-max choice as an exponential race: argmax_j a_j/E_j, compared as a_j E_b > a_b E_j
 // (binary32 products); ties keep the lowest j. The adjoint repeats the identical comparisons.

@@ -91,7 +91,7 @@ __device__ __forceinline__ void thread_fwd_body(const FwdParams &p, const int4 *
             }
         }
         if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }  // no positive key (NaN rates)
-        const float tau = __fdividef(E0, a0);
+        const float tau = waiting_time(E0, a0);
         const double t_next = t + f2d_pos(tau);
         const int4 rj = s_rx[jb];
         // a sample falls in [t_k, t_{k+1}) or the horizon ends (both clocks are non-negative)

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(128) grn_fwd_kernel(const GrnParams p, int rec
         if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
         if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
         if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }
-        const float tau = __fdividef(E0, a0);
+        const float tau = waiting_time(E0, a0);
         const double t_next = t + f2d_pos(tau);
         const bool slow = gt_nonneg(t_next, thr);
         const bool cross = slow && gt_nonneg(t_next, p.t_end);
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(128) grn_soft_fwd_kernel(const GrnParams p, fl
         const float a0 = grn_soft_weights(p, s_d, X, aH, aO, q, k, c2, c3, key0, key1, lane, E0, invZ);
         if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
         if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
-        const float tau = __fdividef(E0, a0);
+        const float tau = waiting_time(E0, a0);
         const double t_next = t + f2d_pos(tau);
         const bool slow = gt_nonneg(t_next, thr);
         const bool cross = slow && gt_nonneg(t_next, p.t_end);

@@ -57,7 +57,7 @@ __device__ __forceinline__ void warp_step_eval(const FwdParamsView &v, int k, co
                 }
                 // tables in lane-major order; padded entries (j >= M) have rate 0
                 const int pos = q * v.nb + b;
-                const float a = __fmul_rn(v.s_k[pos], mass_action_h(v.s_rx[pos], X, 1));
+                const float a = __fmul_rn(v.s_k[pos], mass_action_h_sel(v.s_rx[pos], X));
                 a0p = __fadd_rn(a0p, a);
                 float l = -CUDART_INF_F;
                 if (a > 0.0f) {
@@ -117,7 +117,7 @@ __device__ __forceinline__ void warp_fwd_body(const FwdParams &p, const int4 *s_
         if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
         if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
         if (jb < 0) { status = SSA_TRAJ_BAD_RATE; break; }
-        const float tau = __fdividef(E0, a0);
+        const float tau = waiting_time(E0, a0);
         const double t_next = t + f2d_pos(tau);
         const int4 rj = s_rx[jpos(jb, v.nb)];
         const bool slow = gt_nonneg(t_next, thr);
@@ -264,7 +264,7 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
             int jb;
             warp_step_eval<true>(v, k, X, a0, E0, ab, Eb, jb, aj, lj, lmax);
             mism += (jb != jk);
-            const float tau = __fdividef(E0, a0);
+            const float tau = waiting_time(E0, a0);
             const int4 rk = s_rx[jpos(jk, v.nb)];
             float dt_dir = 0.0f, dtau_dir = 0.0f;
             if (READOUT == SSA_READOUT_LINEAR) {
@@ -329,21 +329,19 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
                     float psi = 0.0f;
                     if (qv > 0.0f) psi = qv * invZ * (ct[pos] - Wbar) * invT;  // w_j from pass 2
                     dA[pos] += psi + dLda0 * a;
-                    float c1 = 0.0f, c2 = 0.0f;
-                    if (rx.x >= 0) {
-                        const float c_tau = dLda0 * s_k[pos];
-                        const float x1 = int2f(X[rx.x]);
-                        if (rx.y < 0) {
-                            c1 = (a > 0.0f ? __fdividef(psi, x1) : 0.0f) + c_tau;
-                        } else if (rx.y == rx.x) {
-                            const float dh = x1 - 0.5f;
-                            c1 = (a > 0.0f ? __fdividef(psi * dh, mass_action_h(rx, X, 1)) : 0.0f) + c_tau * dh;
-                        } else {
-                            const float x2 = int2f(X[rx.y]);
-                            c1 = (a > 0.0f ? __fdividef(psi, x1) : 0.0f) + c_tau * x2;
-                            c2 = (a > 0.0f ? __fdividef(psi, x2) : 0.0f) + c_tau * x1;
-                        }
-                    }
+                    // d log a_j / dX and d a_j / dX of each reactant slot, formed with selects (the lanes hold
+                    // reactions of different orders): first order is the hetero form with x2 = 1
+                    const bool has1 = rx.x >= 0, has2 = rx.y >= 0, homo = has2 && rx.y == rx.x;
+                    const float c_tau = dLda0 * s_k[pos];
+                    const float x1 = int2f(X[has1 ? rx.x : 0]);
+                    const float xr2 = int2f(X[has2 ? rx.y : 0]);
+                    const float x2 = (has2 && !homo) ? xr2 : 1.0f;
+                    const float dh = x1 - 0.5f;
+                    const float num = homo ? psi * dh : psi;
+                    const float den = homo ? mass_action_h_sel(rx, X) : x1;
+                    const float t1 = a > 0.0f ? __fdividef(num, den) : 0.0f;
+                    const float c1 = has1 ? t1 + c_tau * (homo ? dh : x2) : 0.0f;
+                    const float c2 = (has2 && !homo) ? (a > 0.0f ? __fdividef(psi, xr2) : 0.0f) + c_tau * x1 : 0.0f;
                     ct[pos] = c1;          // reactant slot 0
                     ct[p.Mp + pos] = c2;   // reactant slot 1
                 }
