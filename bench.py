@@ -690,7 +690,7 @@ def batch_grad_err(ssa, dev, wl, nets, max_steps, n_items: int = 16, n: int = 16
     orcs, uses = [], []
     for q in range(n_items):
         spec = wl.nets[q]
-        orc = native.run(spec, spec.log_rates.astype(np.float32).astype(np.float64), spec.x0, n, wl.t_end,
+        orc = native.run(spec, oracle_theta(spec.log_rates), spec.x0, n, wl.t_end,
                          wl.sample_times, wl.obs_species[q], 400 + q, native.LINEAR, max_steps=max_steps[q],
                          dl_dobs=dls[q], temperature=wl.temperature, ev_cap=max_steps[q])
         draws, status, _ = b.outputs(q)
@@ -1081,6 +1081,14 @@ def grn_grad_err(ssa, dev, p, x, tpi, t_end, seed, T):
             "identical_events": float(same.mean()), "temperature": float(T)}
 
 
+def oracle_theta(t32):
+    """Log-rates for the oracle such that exp of them equals the binary32 rate constants the kernels use
+    (k = exp(theta) in binary64, rounded once to binary32): a fixed relative rounding of every rate would
+    otherwise move a long trajectory's clock systematically against the oracle's."""
+    k32 = np.exp(np.asarray(t32, dtype=np.float32).astype(np.float64)).astype(np.float32)
+    return np.log(k32.astype(np.float64))
+
+
 def oracle_grad_err(ssa, dev, spec, theta32, x0, n, t_end, ts, obs_sp, seed, readout, T, cap, dl, wide=False,
                     threads_per_traj=0, traj_offset=0):
     """Relative error (norm over the parameters) of the GPU straight-through gradient against the FP64 oracle's
@@ -1092,7 +1100,7 @@ def oracle_grad_err(ssa, dev, spec, theta32, x0, n, t_end, ts, obs_sp, seed, rea
 
     from oracle import native
     net = ssa.Network(spec)
-    th64 = np.asarray(theta32, np.float32).astype(np.float64)
+    th64 = oracle_theta(theta32)
     fw = ssa.forward(net, torch.tensor(theta32, device=dev), n, x0, t_end, ts, obs_sp, seed, readout=readout,
                      record=True, max_steps=cap, threads_per_traj=threads_per_traj, traj_offset=traj_offset)
     code = {"hold": native.HOLD, "linear": native.LINEAR, "bin": native.BIN}[readout]
@@ -1234,7 +1242,7 @@ def grad_error_subset(ssa, net, wl, dev, n=2048):
                      readout="linear", record=True, max_steps=2048)
     ev = fw.run.events(2048).cpu().numpy()
     for T in TEMPS:
-        orc = native.run(wl.net, theta32.astype(np.float64), wl.x0, n, wl.t_end, wl.sample_times, wl.obs_species, 77,
+        orc = native.run(wl.net, oracle_theta(theta32), wl.x0, n, wl.t_end, wl.sample_times, wl.obs_species, 77,
                          native.LINEAR, max_steps=2048, dl_dobs=dl, temperature=T, ev_cap=2048)
         same = np.all(ev == orc.events, axis=1)
         dl2 = dl.copy()

@@ -15,7 +15,7 @@ import torch
 
 import ssa_workloads as W
 from oracle import native
-from test_gpu_parity import GRAD_RTOL, _bracket_flips, _compare_events
+from test_gpu_parity import GRAD_RTOL, _bracket_flips, _compare_events, _oracle_theta
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +37,7 @@ def test_oscillator_full_horizon_gradient_matches_oracle(S):
                    readout="linear", record=True, max_steps=cap, ckpt_interval=64)
     torch.cuda.synchronize()
     assert fw.run.variant == 2
-    orc = native.run(wl.net, t32.astype(np.float64), wl.x0, n, wl.t_end, ts, wl.obs_species, seed, native.LINEAR,
+    orc = native.run(wl.net, _oracle_theta(t32), wl.x0, n, wl.t_end, ts, wl.obs_species, seed, native.LINEAR,
                      max_steps=cap, ev_cap=cap)
     assert np.all(orc.status == 0) and np.all(fw.status.cpu().numpy() == 0)
     assert orc.draws.min() > 9e5
@@ -48,7 +48,7 @@ def test_oscillator_full_horizon_gradient_matches_oracle(S):
     # the upstream gradient of the trajectories whose events agree, without their flipped samples
     keep = same[:, None] & ~flip
     dl = W.seeded_dl_dobs(13, n, len(ts), 1, scale=1.0 / n) * keep[:, :, None]
-    orc_g = native.run(wl.net, t32.astype(np.float64), wl.x0, n, wl.t_end, ts, wl.obs_species, seed, native.LINEAR,
+    orc_g = native.run(wl.net, _oracle_theta(t32), wl.x0, n, wl.t_end, ts, wl.obs_species, seed, native.LINEAR,
                        max_steps=cap, dl_dobs=dl, temperature=T)
     ref = orc_g.dtheta.sum(0)
     assert np.all(np.isfinite(ref))
