@@ -395,7 +395,8 @@ def run_ours(args):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     legs = set() if args.no_extra else {x for x in args.legs.split(",") if x}
     orc = not args.no_oracle
-    osc = oscillator_extra(ssa, dev, oracle=orc) if (rank == 0 and "oscillator" in legs) else None
+    osc = (oscillator_extra(ssa, dev, oracle=orc, n_fwd=args.osc_traj, n_samples=args.osc_samples)
+           if (rank == 0 and "oscillator" in legs) else None)
     batch = (uneven_batch_extra(ssa, dev, args.batch_scale, sequential=args.batch_sequential, oracle=orc)
              if (rank == 0 and "batch" in legs) else None)
     grn = grn_extra(ssa, dev, n_img=args.grn_images, oracle=orc) if (rank == 0 and "grn" in legs) else None
@@ -488,24 +489,27 @@ def run_ours(args):
 
 
 def oscillator_extra(ssa, dev, n_fwd: int = 1 << 20, n_adj: int = 1 << 16, t_end: float = 10.0, reps: int = 2,
-                     oracle: bool = True):
+                     oracle: bool = True, n_samples: int = 10):
     """Forward-only and forward+adjoint SSA steps/s on the activator-repressor oscillator (the workload of the
     paper's throughput figure), 10 LINEAR samples of R, horizon t_end (truncated from 400 to bound the event
     log), timed with CUDA events after one warm-up launch."""
     import torch
 
     import ssa_workloads as W
-    wl = W.config_c3(n_traj=n_fwd, t_end=t_end, S=10)
+    wl = W.config_c3(n_traj=n_fwd, t_end=t_end, S=n_samples)
     net = ssa.Network(wl.net)
     th = torch.tensor(wl.log_rates.astype(np.float32), device=dev)
     stream = torch.cuda.current_stream()
-    out = {"workload": f"Vilar oscillator, 9 species, 16 reactions, t_end={t_end}, 10 LINEAR samples of R",
+    out = {"workload": f"Vilar oscillator, 9 species, 16 reactions, t_end={t_end}, {n_samples} LINEAR samples of R",
            "selectors": "forward: Gumbel-max (the method); forward_direct: the plain direct method; forward_soft: "
-                        "the relaxed forward of Eq. 4 at T = 0.5 (its own, different, step count)"}
+                        "the relaxed forward of Eq. 4 at T = 0.5 (its own, different, step count); "
+                        "forward_generic: the Gumbel-max forward on the generic table-driven kernels"}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for mode, n in (("forward", n_fwd), ("forward_direct", n_fwd), ("forward_soft", n_fwd), ("forward_adjoint", n_adj)):
+    for mode, n in (("forward", n_fwd), ("forward_generic", n_fwd), ("forward_direct", n_fwd), ("forward_soft", n_fwd),
+                    ("forward_adjoint", n_adj)):
         rec = mode == "forward_adjoint"
         sel = {"forward_direct": "direct", "forward_soft": "soft"}.get(mode, "gumbel")
+        spec_k = mode != "forward_generic"
         ms, steps = 0.0, 0
         for r in range(reps + 1):
             if r == 1:
@@ -513,7 +517,8 @@ def oscillator_extra(ssa, dev, n_fwd: int = 1 << 20, n_adj: int = 1 << 16, t_end
             if r >= 1:
                 ev[0].record(stream)
             fw = ssa.forward(net, th, n, wl.x0, t_end, wl.sample_times, wl.obs_species, 50 + r, readout="linear",
-                             record=rec, max_steps=1 << 16, selector=sel, temperature=0.5 if sel == "soft" else None)
+                             record=rec, max_steps=1 << 16, selector=sel, temperature=0.5 if sel == "soft" else None,
+                             specialize=spec_k)
             if rec:
                 dl = torch.full((len(wl.sample_times), 1), 1.0 / n, device=dev)
                 ssa.backward(fw, dl, 0.1)
@@ -1272,6 +1277,8 @@ def main():
                          "batch, grn, warp, ion (the ion channel of Section 4.4) ('none' for none)")
     ap.add_argument("--grn-images", type=int, default=512, help="images of the GRN field (64 trajectories each)")
     ap.add_argument("--ion-traj", type=int, default=262144, help="trajectories of the ion-channel field")
+    ap.add_argument("--osc-traj", type=int, default=1 << 20, help="forward trajectories of the oscillator field")
+    ap.add_argument("--osc-samples", type=int, default=10, help="LINEAR samples of R in the oscillator field")
     ap.add_argument("--warp-traj", type=int, default=16384, help="trajectories of the warp-kernel field")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="trajectories per network of the uneven batch, as a fraction of the full counts")

@@ -59,8 +59,8 @@ typedef int32_t ssa_status;
  * bins' right edges and must be strictly increasing with t_0 > 0 (else every trajectory reports
  * SSA_TRAJ_BAD_INPUT); a stopped path holds its last state. At most SSA_BIN_MAX_OBS observables
  * per call (call again with other species: the paths depend only on the seed). Runs on the
- * thread-per-trajectory kernels (generic and network-specialised); threads_per_traj = 32, the
- * batch and the GRN calls return SSA_ERR_UNSUPPORTED for it. */
+ * thread-per-trajectory kernels (generic and network-specialised), on the warp-per-trajectory
+ * kernels and in the batch; the GRN calls return SSA_ERR_UNSUPPORTED for it. */
 #define SSA_READOUT_BIN 2
 #define SSA_BIN_MAX_OBS 4
 
@@ -398,7 +398,8 @@ ssa_status ssa_pipe_rates(double *host_rates, double *host_sm_clock_mhz, int32_t
  *   t_end, sample_times device double [n_samples], obs_species device int32 [n_obs] (n_obs <= 64),
  *   max_steps, ckpt_interval (0: choose; else a multiple of 8), threads_per_traj (0: choose, 1, 32;
  *                    1 needs N <= 16 and M <= 16): as ssa_fwd_opts.
- *   obs_out          device [n_traj][n_samples][n_obs], int32 (HOLD) or float (LINEAR).
+ *   obs_out          device [n_traj][n_samples][n_obs], int32 (HOLD) or float (LINEAR, BIN; BIN:
+ *                    n_obs <= SSA_BIN_MAX_OBS and the bin-edge rule of SSA_READOUT_BIN).
  *   dl_dobs, dl_traj_stride: upstream gradient as in ssa_backward.
  *   dl_dlog_rates    device float [net P], overwritten with the item's dL/dtheta.
  */
@@ -427,8 +428,9 @@ typedef struct ssa_batch_item {
 
 /*
  * ssa_batch_create -- validate and copy the item descriptors (host array [n_items]); readout and
- * temperature T > 0 apply to every item. Allocates host memory only. Errors: SSA_ERR_INVALID_ARG,
- * SSA_ERR_UNSUPPORTED (thread variant requested for a network with N > 16 or M > 16).
+ * temperature T > 0 apply to every item (readout SSA_READOUT_HOLD, _LINEAR or _BIN). Allocates host
+ * memory only. Errors: SSA_ERR_INVALID_ARG, SSA_ERR_UNSUPPORTED (thread variant requested for a network
+ * with N > 16 or M > 16; the bin readout with more than SSA_BIN_MAX_OBS observables in an item).
  */
 ssa_status ssa_batch_create(const ssa_batch_item *items, int32_t n_items, int32_t readout,
                             float temperature, ssa_batch **out);

@@ -190,14 +190,13 @@ size_t fwd_warp_smem(const ssa_network *net)
 size_t adj_warp_smem(const ssa_network *net)
 {
     return net->tab_bytes + (size_t)net->Mp * 4 + 16 +
-           (size_t)kWarpsPerBlock * (2 * ((net->N + 3) & ~3) + 5 * (size_t)net->Mp) * 4;
+           (size_t)kWarpsPerBlock * (2 * ((net->N + 3) & ~3) + 4 * (size_t)net->Mp) * 4;
 }
 
 // one thread per trajectory up to 16 reactions (unrolled, register-resident), one warp above
 int pick_variant(const ssa_network *net, const ssa_fwd_opts *o)
 {
     if (o->threads_per_traj) return o->threads_per_traj;
-    if (o->readout == SSA_READOUT_BIN) return 1;  // the bin readout runs on the thread kernels only
     if (!o->no_specialize && jit_eligible(net)) return 1;
     return net->M <= 16 ? 1 : 32;
 }
@@ -376,8 +375,6 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
         jit = jit_kernels(net, why);
         if (jit) variant = 2;
     }
-    if (opts->readout == SSA_READOUT_BIN && variant == 32)
-        return fail(SSA_ERR_UNSUPPORTED, "the bin readout runs on the thread-per-trajectory kernels only");
     if (opts->readout == SSA_READOUT_BIN && n_obs > SSA_BIN_MAX_OBS)
         return fail(SSA_ERR_UNSUPPORTED, "the bin readout takes at most %d observables per call", SSA_BIN_MAX_OBS);
     if (opts->selector == SSA_SELECT_DIRECT && (variant != 2 || ev_in))

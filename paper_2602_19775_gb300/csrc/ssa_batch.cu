@@ -55,10 +55,15 @@ struct BatchUnit {
 
 constexpr int kBatchWarps = 4;
 constexpr int kBatchThreadMaxN = 16;  // thread variant inside a batch: N <= 16 and M <= 16
-constexpr int kBatchWarpBlocks = 6;  // resident blocks per SM the warp-unit kernels are compiled for
+// Resident blocks per SM the warp-unit kernels are compiled for (a tuning constant: more blocks hide more
+// latency, fewer leave more of the SM's 256 KB to L1, through which the batch kernels read their tables).
+#ifndef SSA_BATCH_WARP_BLOCKS
+#define SSA_BATCH_WARP_BLOCKS 5
+#endif
+constexpr int kBatchWarpBlocks = SSA_BATCH_WARP_BLOCKS;
 constexpr int kBatchWarpUnit = 1;     // trajectories per warp-variant unit (one: the finest grain for the tail)
 
-__global__ void batch_prepare_kernel(const BatchItem *items, int n_items)
+__global__ void batch_prepare_kernel(const BatchItem *items, int n_items, int strict)
 {
     // per network: k_j = exp(theta_{r(j)}) rounded once, and the check of its sample grid
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -72,11 +77,24 @@ __global__ void batch_prepare_kernel(const BatchItem *items, int n_items)
         }
         int *flag = const_cast<int *>(b.f.flag);
         for (int s = threadIdx.x; s < b.f.S; s += blockDim.x) {
-            const bool ok = b.f.ts[s] >= 0.0 && b.f.ts[s] <= b.f.t_end && (s == 0 || b.f.ts[s] >= b.f.ts[s - 1]);
+            // the bin readout needs strictly increasing edges with the first above 0 (its bins are (t_{s-1}, t_s])
+            const bool ok = b.f.ts[s] >= 0.0 && b.f.ts[s] <= b.f.t_end &&
+                            (s == 0 ? (!strict || b.f.ts[0] > 0.0)
+                                    : (strict ? b.f.ts[s] > b.f.ts[s - 1] : b.f.ts[s] >= b.f.ts[s - 1]));
             if (!ok) atomicOr(flag, kErrBadSamples);
         }
         for (int c = threadIdx.x; c < b.f.n_obs; c += blockDim.x)
             if (b.f.obs_sp[c] < 0 || b.f.obs_sp[c] >= b.f.N) atomicOr(flag, kErrBadObs);
+    }
+}
+
+// bin readout with a shared upstream gradient: one block per such item forms its binary64 prefix sums over
+// bins (the single-network path's scan, so the same bits)
+__global__ void __launch_bounds__(kPrefixThreads) batch_prefix_kernel(const BatchItem *items, int n_items)
+{
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const AdjParams &a = items[it].a;
+        if (a.bin_prefix) bin_prefix_block(a.dl_dobs, a.S, a.n_obs, const_cast<double *>(a.bin_prefix));
     }
 }
 
@@ -211,7 +229,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps, VARIANT == 1 ? 1 : kBatchWar
             float *aj = lam + Npad;
             float *lj = aj + p.Mp;
             float *ct = lj + p.Mp;
-            float *dA = ct + 2 * p.Mp;
+            float *dA = ct + p.Mp;
             for (int j = lane; j < p.Mp; j += 32) dA[j] = 0.0f;
             __syncwarp();
             for (int c = 0; c < u.count; ++c) {
@@ -309,11 +327,12 @@ int64_t units_of(const ssa_batch *bt, size_t it)
 
 // Workspace layout, shared by the size query and the build:
 //   flags [n_items][16] int | per item: k [Mp] | draws [n] | status [n] | xfinal [N][n] |
-//   events [rows][n] uint4 | checkpoints [n_ckpt][N][n] | brackets k, alpha [S][n] | dA [M] |
+//   events [rows][n] uint4 | checkpoints [n_ckpt][N][n] | brackets k, alpha [S][n] | bin readout: slot
+//   edges [S][n], slot counts [n], prefix sums of a shared upstream gradient [S + 1][4] double | dA [M] |
 //   unit slots [units][M] | item descriptors | units | reduction maps (item, j) | counters
 struct BatchLayout {
     size_t flags = 0;
-    std::vector<size_t> k, draws, status, xfinal, ev, ckpt, brk_k, brk_a, dA;
+    std::vector<size_t> k, draws, status, xfinal, ev, ckpt, brk_k, brk_a, brk_s, brk_tail, prefix, dA;
     size_t partial = 0, items = 0, units = 0, blk_item = 0, blk_j = 0, counters = 0, total = 0;
     int64_t n_units = 0, n_slots = 0, n_red = 0;
 };
@@ -342,6 +361,10 @@ BatchLayout batch_layout(const ssa_batch *bt)
         L.ckpt.push_back(take(nck * net->N * n * 4));
         L.brk_k.push_back(take((size_t)b.n_samples * n * 4));
         L.brk_a.push_back(take((size_t)b.n_samples * n * 4));
+        const bool bin = bt->readout == SSA_READOUT_BIN;
+        L.brk_s.push_back(bin ? take((size_t)b.n_samples * n * 4) : 0);
+        L.brk_tail.push_back(bin ? take(n * 4) : 0);
+        L.prefix.push_back(bin && b.dl_traj_stride == 0 ? take((size_t)(b.n_samples + 1) * SSA_BIN_MAX_OBS * 8) : 0);
         L.dA.push_back(take((size_t)net->M * 4));
         L.n_units += units_of(bt, it);
         L.n_slots += units_of(bt, it) * net->M;
@@ -385,8 +408,8 @@ extern "C" ssa_status ssa_batch_create(const ssa_batch_item *items, int32_t n_it
     if (!out) return set_error(SSA_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!items || n_items < 1) return set_error(SSA_ERR_INVALID_ARG, "no items");
-    if (readout == SSA_READOUT_BIN) return set_error(SSA_ERR_UNSUPPORTED, "the batch reads out with HOLD or LINEAR");
-    if (readout != SSA_READOUT_HOLD && readout != SSA_READOUT_LINEAR) return set_error(SSA_ERR_INVALID_ARG, "bad readout");
+    if (readout != SSA_READOUT_HOLD && readout != SSA_READOUT_LINEAR && readout != SSA_READOUT_BIN)
+        return set_error(SSA_ERR_INVALID_ARG, "bad readout");
     if (!(temperature > 0.0f)) return set_error(SSA_ERR_INVALID_ARG, "temperature must be > 0");
     for (int it = 0; it < n_items; ++it) {
         const ssa_batch_item &b = items[it];
@@ -400,6 +423,8 @@ extern "C" ssa_status ssa_batch_create(const ssa_batch_item *items, int32_t n_it
             return set_error(SSA_ERR_INVALID_ARG, "batch item without outputs or upstream gradient");
         if (b.threads_per_traj == 1 && !thread_eligible(b.net))
             return set_error(SSA_ERR_UNSUPPORTED, "thread variant in a batch needs N <= 16 and M <= 16");
+        if (readout == SSA_READOUT_BIN && b.n_obs > SSA_BIN_MAX_OBS)
+            return set_error(SSA_ERR_UNSUPPORTED, "the bin readout takes at most SSA_BIN_MAX_OBS observables per item");
     }
     ssa_batch *bt = new (std::nothrow) ssa_batch();
     if (!bt) return set_error(SSA_ERR_CUDA, "host allocation failed");
@@ -469,6 +494,11 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
         int *ckpt = reinterpret_cast<int *>(ws + L.ckpt[it]);
         int *brk_k = reinterpret_cast<int *>(ws + L.brk_k[it]);
         float *brk_a = reinterpret_cast<float *>(ws + L.brk_a[it]);
+        const bool bin = bt->readout == SSA_READOUT_BIN;
+        int *brk_s = bin ? reinterpret_cast<int *>(ws + L.brk_s[it]) : nullptr;
+        int *brk_tail = bin ? reinterpret_cast<int *>(ws + L.brk_tail[it]) : nullptr;
+        double *prefix = (bin && b.dl_traj_stride == 0 && b.n_samples > 0 && b.n_obs > 0)
+                             ? reinterpret_cast<double *>(ws + L.prefix[it]) : nullptr;
         BatchItem &bi = bt->h_items[it];
         FwdParams &p = bi.f;
         AdjParams &a = bi.a;
@@ -503,6 +533,8 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
         p.ckpt = ckpt;
         p.brk_k = brk_k;
         p.brk_a = brk_a;
+        p.brk_s = brk_s;
+        p.brk_tail = brk_tail;
         p.xfinal = xfinal;
         a.draws = draws;
         a.status = status;
@@ -510,6 +542,9 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
         a.ckpt = ckpt;
         a.brk_k = brk_k;
         a.brk_a = brk_a;
+        a.brk_s = brk_s;
+        a.brk_tail = brk_tail;
+        a.bin_prefix = prefix;
         a.xfinal = xfinal;
         a.dl_dobs = b.dl_dobs;
         a.dl_stride = b.dl_traj_stride;
@@ -591,16 +626,20 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
     bt->x_words[0] = kBatchThreadMaxN * 32;
     bt->w_words[0] = 3 * kBatchThreadMaxN * 32;
     bt->x_words[1] = maxNpad;
-    bt->w_words[1] = 2 * maxNpad + 5 * maxMpw;
+    bt->w_words[1] = 2 * maxNpad + 4 * maxMpw;
     int dev = 0, sms = 0, limit = 0;
     CUDA_TRY_B(cudaGetDevice(&dev));
     CUDA_TRY_B(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY_B(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const bool hold = bt->readout == SSA_READOUT_HOLD;
-    const void *fk[2] = {hold ? (const void *)batch_fwd_kernel<0, 1> : (const void *)batch_fwd_kernel<1, 1>,
-                         hold ? (const void *)batch_fwd_kernel<0, 32> : (const void *)batch_fwd_kernel<1, 32>};
-    const void *ak[2] = {hold ? (const void *)batch_adj_kernel<0, 1> : (const void *)batch_adj_kernel<1, 1>,
-                         hold ? (const void *)batch_adj_kernel<0, 32> : (const void *)batch_adj_kernel<1, 32>};
+    const int ro = bt->readout;
+    const void *fk[2] = {ro == 0 ? (const void *)batch_fwd_kernel<0, 1>
+                                 : ro == 1 ? (const void *)batch_fwd_kernel<1, 1> : (const void *)batch_fwd_kernel<2, 1>,
+                         ro == 0 ? (const void *)batch_fwd_kernel<0, 32>
+                                 : ro == 1 ? (const void *)batch_fwd_kernel<1, 32> : (const void *)batch_fwd_kernel<2, 32>};
+    const void *ak[2] = {ro == 0 ? (const void *)batch_adj_kernel<0, 1>
+                                 : ro == 1 ? (const void *)batch_adj_kernel<1, 1> : (const void *)batch_adj_kernel<2, 1>,
+                         ro == 0 ? (const void *)batch_adj_kernel<0, 32>
+                                 : ro == 1 ? (const void *)batch_adj_kernel<1, 32> : (const void *)batch_adj_kernel<2, 32>};
     for (int v = 0; v < 2; ++v) {
         bt->fwd_smem[v] = (size_t)kBatchWarps * (kItemWords + bt->x_words[v]) * 4;
         bt->adj_smem[v] = (size_t)kBatchWarps * (kItemWords + bt->w_words[v]) * 4;
@@ -623,40 +662,37 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
     return SSA_OK;
 }
 
-static ssa_status batch_enqueue(ssa_batch *bt, cudaStream_t st)
+template <int R>
+static void batch_launch_kernels(const ssa_batch *bt, cudaStream_t st)
 {
-    const int n_items = (int)bt->items.size();
-    CUDA_TRY_B(cudaMemsetAsync(bt->d_flags, 0, (size_t)n_items * 16 * sizeof(int), st));
-    CUDA_TRY_B(cudaMemsetAsync(bt->d_counters, 0, 64, st));
-    batch_prepare_kernel<<<std::min(n_items, 1024), 128, 0, st>>>(bt->d_items, n_items);
-    const bool hold = bt->readout == SSA_READOUT_HOLD;
     const BatchUnit *u0 = bt->d_units + bt->unit_begin[0], *u1 = bt->d_units + bt->unit_begin[1];
     const dim3 blk(32 * kBatchWarps);
     if (bt->n_units[0] > 0) {  // thread units: forward then adjoint
-        if (hold) {
-            batch_fwd_kernel<0, 1><<<bt->fwd_blocks[0], blk, bt->fwd_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
-                                                                                  bt->d_counters, bt->x_words[0]);
-            batch_adj_kernel<0, 1><<<bt->adj_blocks[0], blk, bt->adj_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
-                                                                                  bt->d_counters + 1, bt->w_words[0]);
-        } else {
-            batch_fwd_kernel<1, 1><<<bt->fwd_blocks[0], blk, bt->fwd_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
-                                                                                  bt->d_counters, bt->x_words[0]);
-            batch_adj_kernel<1, 1><<<bt->adj_blocks[0], blk, bt->adj_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
-                                                                                  bt->d_counters + 1, bt->w_words[0]);
-        }
+        batch_fwd_kernel<R, 1><<<bt->fwd_blocks[0], blk, bt->fwd_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
+                                                                              bt->d_counters, bt->x_words[0]);
+        batch_adj_kernel<R, 1><<<bt->adj_blocks[0], blk, bt->adj_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
+                                                                              bt->d_counters + 1, bt->w_words[0]);
     }
     if (bt->n_units[1] > 0) {  // warp units
-        if (hold) {
-            batch_fwd_kernel<0, 32><<<bt->fwd_blocks[1], blk, bt->fwd_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
-                                                                                   bt->d_counters + 2, bt->x_words[1]);
-            batch_adj_kernel<0, 32><<<bt->adj_blocks[1], blk, bt->adj_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
-                                                                                   bt->d_counters + 3, bt->w_words[1]);
-        } else {
-            batch_fwd_kernel<1, 32><<<bt->fwd_blocks[1], blk, bt->fwd_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
-                                                                                   bt->d_counters + 2, bt->x_words[1]);
-            batch_adj_kernel<1, 32><<<bt->adj_blocks[1], blk, bt->adj_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
-                                                                                   bt->d_counters + 3, bt->w_words[1]);
-        }
+        batch_fwd_kernel<R, 32><<<bt->fwd_blocks[1], blk, bt->fwd_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
+                                                                               bt->d_counters + 2, bt->x_words[1]);
+        batch_adj_kernel<R, 32><<<bt->adj_blocks[1], blk, bt->adj_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
+                                                                               bt->d_counters + 3, bt->w_words[1]);
+    }
+}
+
+static ssa_status batch_enqueue(ssa_batch *bt, cudaStream_t st)
+{
+    const int n_items = (int)bt->items.size();
+    const bool bin = bt->readout == SSA_READOUT_BIN;
+    CUDA_TRY_B(cudaMemsetAsync(bt->d_flags, 0, (size_t)n_items * 16 * sizeof(int), st));
+    CUDA_TRY_B(cudaMemsetAsync(bt->d_counters, 0, 64, st));
+    batch_prepare_kernel<<<std::min(n_items, 1024), 128, 0, st>>>(bt->d_items, n_items, bin ? 1 : 0);
+    if (bin) batch_prefix_kernel<<<std::min(n_items, 1024), kPrefixThreads, 0, st>>>(bt->d_items, n_items);
+    switch (bt->readout) {
+    case SSA_READOUT_HOLD: batch_launch_kernels<0>(bt, st); break;
+    case SSA_READOUT_LINEAR: batch_launch_kernels<1>(bt, st); break;
+    default: batch_launch_kernels<2>(bt, st); break;
     }
     if (bt->n_red_blocks > 0) batch_reduce_kernel<<<bt->n_red_blocks, 256, 0, st>>>(bt->d_items, bt->d_blk_item, bt->d_blk_j);
     batch_params_kernel<<<std::min(n_items, 1024), 128, 0, st>>>(bt->d_items, n_items);

@@ -326,6 +326,39 @@ __device__ __forceinline__ void bin_state_terms(const AF &addx, float d_first, f
         if (c < n_obs) addx(c, gk[c] * d_first);
 }
 
+// Bin readout with a shared upstream gradient g [S][n_obs]: prefix[s][c] = sum_{b < s} g[b][c] in binary64,
+// for s = 0..S ([S + 1][kBinMaxObs]), computed by one block of kPrefixThreads threads: each thread sums a
+// contiguous chunk of bins, the chunk totals are scanned in shared memory (fixed order), and each thread writes
+// its chunk's prefixes. Every block that runs it gets the same bits.
+constexpr int kPrefixThreads = 256;
+__device__ __forceinline__ void bin_prefix_block(const float *g, int S, int n_obs, double *prefix)
+{
+    __shared__ double part[kPrefixThreads];
+    const int tid = threadIdx.x;
+    const int chunk = (S + kPrefixThreads - 1) / kPrefixThreads;
+    const int lo = min(tid * chunk, S), hi = min(lo + chunk, S);
+    for (int c = 0; c < kBinMaxObs; ++c) {
+        double acc = 0.0;
+        if (c < n_obs)
+            for (int b = lo; b < hi; ++b) acc += (double)g[(int64_t)b * n_obs + c];
+        part[tid] = acc;
+        __syncthreads();
+        for (int off = 1; off < kPrefixThreads; off <<= 1) {  // inclusive scan of the chunk totals
+            const double v = tid >= off ? part[tid - off] : 0.0;
+            __syncthreads();
+            part[tid] += v;
+            __syncthreads();
+        }
+        double run = tid > 0 ? part[tid - 1] : 0.0;  // sum of the bins below this chunk
+        if (tid == 0) prefix[c] = 0.0;
+        for (int b = lo; b < hi; ++b) {
+            if (c < n_obs) run += (double)g[(int64_t)b * n_obs + c];
+            prefix[(int64_t)(b + 1) * kBinMaxObs + c] = run;
+        }
+        __syncthreads();
+    }
+}
+
 // The adjoint's walk over the recorded slots of the bin readout (from the last): at state k, if the
 // slot below is k's, its edges are first..s_top, and s_hi drops below them. Returns whether state k holds
 // edges; d_first/d_last are the offsets of its first and last edge from t_k.

@@ -70,29 +70,52 @@ __global__ void rates_kernel(const float *log_rates, const int *rate_index, int 
 }
 
 // Deterministic ensemble mean: per-chunk column sums (fixed order), then a fixed-order sum.
-// Chunk b (rows b*chunk .. b*chunk + chunk - 1) is summed by the blocks with blockIdx.y = b mod gridDim.y, so
-// any number of chunks fits the 65,535 limit of gridDim.y; each chunk's sum is the same whatever the grid.
+// Deterministic ensemble mean in two passes, both over tiles of 64 columns with 4 row groups per block
+// (256 threads): a warp reads 32 consecutive columns of one row (coalesced), each thread sums every 4th row
+// of its group, and the 4 group sums are added in a fixed order.
+// Pass 1: chunk b (rows b*chunk .. b*chunk + chunk - 1) -> partial[b][c]; the chunks are strided over
+// gridDim.y, so any number of chunks fits the 65,535 limit; each chunk's sum is the same whatever the grid.
+constexpr int kColTile = 64, kColGroups = 4;
 template <typename T>
-__global__ void colsum_chunks_kernel(const T *obs, int64_t n_traj, int64_t row_len, int64_t chunk, float *partial)
+__global__ void __launch_bounds__(kColTile * kColGroups) colsum_chunks_kernel(const T *obs, int64_t n_traj,
+                                                                              int64_t row_len, int64_t chunk,
+                                                                              float *partial)
 {
+    __shared__ float part[kColGroups][kColTile];
+    const int g = threadIdx.x / kColTile, cl = threadIdx.x % kColTile;
     const int64_t n_chunks = (n_traj + chunk - 1) / chunk;
-    for (int64_t b = blockIdx.y; b < n_chunks; b += gridDim.y) {
-        const int64_t t0 = b * chunk;
-        const int64_t t1 = min(n_traj, t0 + chunk);
-        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < row_len; c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ct = blockIdx.x; ct * kColTile < row_len; ct += gridDim.x) {
+        const int64_t c = ct * kColTile + cl;
+        for (int64_t b = blockIdx.y; b < n_chunks; b += gridDim.y) {
+            const int64_t t0 = b * chunk;
+            const int64_t t1 = min(n_traj, t0 + chunk);
             float acc = 0.0f;
-            for (int64_t t = t0; t < t1; ++t) acc += (float)obs[t * row_len + c];
-            partial[b * row_len + c] = acc;
+            if (c < row_len)
+                for (int64_t t = t0 + g; t < t1; t += kColGroups) acc += (float)obs[t * row_len + c];
+            part[g][cl] = acc;
+            __syncthreads();
+            if (g == 0 && c < row_len)
+                partial[b * row_len + c] = ((part[0][cl] + part[1][cl]) + part[2][cl]) + part[3][cl];
+            __syncthreads();
         }
     }
 }
 
-__global__ void colsum_final_kernel(const float *partial, int64_t n_chunks, int64_t row_len, float inv_n, float *out)
+// Pass 2: out[c] = (sum over chunks of partial[b][c]) inv_n, the chunks split over the 4 row groups.
+__global__ void __launch_bounds__(kColTile * kColGroups) colsum_final_kernel(const float *partial, int64_t n_chunks,
+                                                                             int64_t row_len, float inv_n, float *out)
 {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < row_len; c += (int64_t)gridDim.x * blockDim.x) {
+    __shared__ float part[kColGroups][kColTile];
+    const int g = threadIdx.x / kColTile, cl = threadIdx.x % kColTile;
+    for (int64_t ct = blockIdx.x; ct * kColTile < row_len; ct += gridDim.x) {
+        const int64_t c = ct * kColTile + cl;
         float acc = 0.0f;
-        for (int64_t b = 0; b < n_chunks; ++b) acc += partial[b * row_len + c];
-        out[c] = acc * inv_n;
+        if (c < row_len)
+            for (int64_t b = g; b < n_chunks; b += kColGroups) acc += partial[b * row_len + c];
+        part[g][cl] = acc;
+        __syncthreads();
+        if (g == 0 && c < row_len) out[c] = (((part[0][cl] + part[1][cl]) + part[2][cl]) + part[3][cl]) * inv_n;
+        __syncthreads();
     }
 }
 
@@ -133,36 +156,10 @@ __global__ void unpack_events_kernel(const uint4 *ev, const int *draws, int64_t 
     out[idx] = v;
 }
 
-// Bin readout with a shared upstream gradient g [S][n_obs]: prefix[s][c] = sum_{b < s} g[b][c] in binary64,
-// for s = 0..S ([S + 1][SSA_BIN_MAX_OBS]). One block: each thread sums a contiguous chunk of bins, the chunk
-// totals are scanned in shared memory (fixed order), and each thread writes its chunk's prefixes.
-constexpr int kPrefixThreads = 256;
+// Bin readout with a shared upstream gradient: its binary64 prefix sums over bins (bin_prefix_block)
 __global__ void __launch_bounds__(kPrefixThreads) bin_prefix_kernel(const float *g, int S, int n_obs, double *prefix)
 {
-    __shared__ double part[kPrefixThreads];
-    const int tid = threadIdx.x;
-    const int chunk = (S + kPrefixThreads - 1) / kPrefixThreads;
-    const int lo = min(tid * chunk, S), hi = min(lo + chunk, S);
-    for (int c = 0; c < SSA_BIN_MAX_OBS; ++c) {
-        double acc = 0.0;
-        if (c < n_obs)
-            for (int b = lo; b < hi; ++b) acc += (double)g[(int64_t)b * n_obs + c];
-        part[tid] = acc;
-        __syncthreads();
-        for (int off = 1; off < kPrefixThreads; off <<= 1) {  // inclusive scan of the chunk totals
-            const double v = tid >= off ? part[tid - off] : 0.0;
-            __syncthreads();
-            part[tid] += v;
-            __syncthreads();
-        }
-        double run = tid > 0 ? part[tid - 1] : 0.0;  // sum of the bins below this chunk
-        if (tid == 0) prefix[c] = 0.0;
-        for (int b = lo; b < hi; ++b) {
-            if (c < n_obs) run += (double)g[(int64_t)b * n_obs + c];
-            prefix[(int64_t)(b + 1) * SSA_BIN_MAX_OBS + c] = run;
-        }
-        __syncthreads();
-    }
+    bin_prefix_block(g, S, n_obs, prefix);
 }
 
 // Test hook: brackets [S][n] -> [n][S].
@@ -277,13 +274,17 @@ cudaError_t launch_ensemble_mean(const void *obs, bool is_int, int64_t n_traj, i
     if (row_len == 0) return cudaSuccess;
     const int64_t n_chunks = (n_traj + chunk - 1) / chunk;
     const float inv_n = n_traj > 0 ? 1.0f / (float)n_traj : 0.0f;
+    const unsigned tiles = (unsigned)std::min<int64_t>((row_len + kColTile - 1) / kColTile, 65535);
     if (n_chunks > 0) {
-        dim3 g((unsigned)std::min<int64_t>((row_len + 127) / 128, 65535), (unsigned)std::min<int64_t>(n_chunks, 65535));
-        if (is_int) colsum_chunks_kernel<int><<<g, 128, 0, st>>>(static_cast<const int *>(obs), n_traj, row_len, chunk, partial);
-        else colsum_chunks_kernel<float><<<g, 128, 0, st>>>(static_cast<const float *>(obs), n_traj, row_len, chunk, partial);
+        dim3 g(tiles, (unsigned)std::min<int64_t>(n_chunks, 65535));
+        if (is_int)
+            colsum_chunks_kernel<int><<<g, kColTile * kColGroups, 0, st>>>(static_cast<const int *>(obs), n_traj, row_len,
+                                                                           chunk, partial);
+        else
+            colsum_chunks_kernel<float><<<g, kColTile * kColGroups, 0, st>>>(static_cast<const float *>(obs), n_traj,
+                                                                             row_len, chunk, partial);
     }
-    colsum_final_kernel<<<(unsigned)std::min<int64_t>((row_len + 127) / 128, 65535), 128, 0, st>>>(partial, n_chunks, row_len,
-                                                                                                  inv_n, out);
+    colsum_final_kernel<<<tiles, kColTile * kColGroups, 0, st>>>(partial, n_chunks, row_len, inv_n, out);
     return cudaGetLastError();
 }
 
@@ -293,12 +294,12 @@ cudaError_t launch_column_sums(const float *x, int64_t n_rows, int64_t row_len, 
 {
     if (row_len == 0) return cudaSuccess;
     const int64_t n_chunks = (n_rows + chunk - 1) / chunk;
+    const unsigned tiles = (unsigned)std::min<int64_t>((row_len + kColTile - 1) / kColTile, 65535);
     if (n_chunks > 0) {
-        dim3 g((unsigned)std::min<int64_t>((row_len + 127) / 128, 65535), (unsigned)std::min<int64_t>(n_chunks, 65535));
-        colsum_chunks_kernel<float><<<g, 128, 0, st>>>(x, n_rows, row_len, chunk, partial);
+        dim3 g(tiles, (unsigned)std::min<int64_t>(n_chunks, 65535));
+        colsum_chunks_kernel<float><<<g, kColTile * kColGroups, 0, st>>>(x, n_rows, row_len, chunk, partial);
     }
-    colsum_final_kernel<<<(unsigned)std::min<int64_t>((row_len + 127) / 128, 65535), 128, 0, st>>>(partial, n_chunks, row_len,
-                                                                                                  1.0f, out);
+    colsum_final_kernel<<<tiles, kColTile * kColGroups, 0, st>>>(partial, n_chunks, row_len, 1.0f, out);
     return cudaGetLastError();
 }
 

@@ -66,8 +66,14 @@ struct SampleStage {
 __device__ __forceinline__ void stage_own_flush(SampleStage &g)
 {
     const int words = g.cnt * g.n_obs;
-    uint32_t *dst = g.out + g.base + (int64_t)g.lo * g.n_obs;
-    for (int q = 0; q < words; ++q) dst[q] = g.row[q];
+    const int64_t w0 = g.base + (int64_t)g.lo * g.n_obs;
+    uint32_t *dst = g.out + w0;
+    if (((reinterpret_cast<uintptr_t>(dst) & 7) | (words & 1)) == 0) {  // 8-byte stores when aligned
+        for (int q = 0; q < words; q += 2)
+            *reinterpret_cast<uint2 *>(dst + q) = *reinterpret_cast<const uint2 *>(g.row + q);
+    } else {
+        for (int q = 0; q < words; ++q) dst[q] = g.row[q];
+    }
     g.lo += g.cnt;
     g.cnt = 0;
     g.ready = false;
@@ -132,7 +138,7 @@ __device__ __forceinline__ void stage_warp_flush(SampleStage &g, const uint32_t 
 template <int READOUT, bool RECORD>
 __device__ __forceinline__ void jit_fwd(const FwdParams &p)
 {
-    __shared__ uint32_t s_stage[kJitFwdBlock * kStageWords];
+    __shared__ __align__(16) uint32_t s_stage[kJitFwdBlock * kStageWords];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n_traj) return;
     const int64_t n = p.n_traj;

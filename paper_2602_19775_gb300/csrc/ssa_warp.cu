@@ -57,16 +57,16 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(const AdjParams p)
     float *s_k = reinterpret_cast<float *>(smem + p.tab_bytes);
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + p.tab_bytes + p.k_bytes);
     int *s_ok = reinterpret_cast<int *>(smem + p.tab_bytes + p.k_bytes + 8);
-    // per warp: X [Npad] int, lambda [Npad], a_j [Mp], log keys / weights [Mp], slot contributions
-    // [2 Mp], dA [Mp]
-    const size_t per_warp = (size_t)2 * Npad + 5 * (size_t)Mp;
+    // per warp: X [Npad] int, lambda [Npad], a_j [Mp], log keys / weights, then slot-0 contributions [Mp],
+    // w_j, then slot-1 contributions [Mp], dA [Mp]
+    const size_t per_warp = (size_t)2 * Npad + 4 * (size_t)Mp;
     float *wbase = reinterpret_cast<float *>(smem + p.tab_bytes + p.k_bytes + 16) + wib * per_warp;
     int *X = reinterpret_cast<int *>(wbase);
     float *lam = wbase + Npad;
     float *aj = lam + Npad;
     float *lj = aj + Mp;
     float *ct = lj + Mp;
-    float *dA = ct + 2 * Mp;
+    float *dA = ct + Mp;
 
     if (!stage_tables(smem, p.rx, p.tab_bytes, s_k, p.k_rates, p.k_bytes, s_bar, s_ok, p.err)) {
         for (int j = threadIdx.x; j < M; j += blockDim.x) p.partial[(int64_t)blockIdx.x * M + j] = 0.0f;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) adj_warp_kernel(const AdjParams p)
     const int nb = (M + 4) >> 2;
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         float acc = 0.0f;
-        for (int w = 0; w < W; ++w) acc += base0[w * per_warp + 2 * Npad + 4 * Mp + jpos(j, nb)];
+        for (int w = 0; w < W; ++w) acc += base0[w * per_warp + 2 * Npad + 3 * Mp + jpos(j, nb)];
         p.partial[(int64_t)blockIdx.x * M + j] = acc;
     }
 }
@@ -108,6 +108,8 @@ cudaError_t launch_forward_warp(const FwdParams &p, int readout, bool record, in
     if (p.n_traj == 0) return cudaSuccess;
     if (readout == SSA_READOUT_HOLD)
         return record ? launch_fwd_w<0, true>(p, warps, smem, st) : launch_fwd_w<0, false>(p, warps, smem, st);
+    if (readout == SSA_READOUT_BIN)
+        return record ? launch_fwd_w<2, true>(p, warps, smem, st) : launch_fwd_w<2, false>(p, warps, smem, st);
     return record ? launch_fwd_w<1, true>(p, warps, smem, st) : launch_fwd_w<1, false>(p, warps, smem, st);
 }
 
@@ -125,8 +127,11 @@ cudaError_t launch_backward_warp(const AdjParams &p, int readout, int warps, siz
                                  cudaStream_t st)
 {
     if (grid == 0) return cudaSuccess;
-    return readout == SSA_READOUT_HOLD ? launch_adj_w<0>(p, warps, smem, grid, st)
-                                       : launch_adj_w<1>(p, warps, smem, grid, st);
+    switch (readout) {
+    case SSA_READOUT_HOLD: return launch_adj_w<0>(p, warps, smem, grid, st);
+    case SSA_READOUT_LINEAR: return launch_adj_w<1>(p, warps, smem, grid, st);
+    default: return launch_adj_w<2>(p, warps, smem, grid, st);
+    }
 }
 
 }  // namespace ssa

@@ -80,6 +80,78 @@ __device__ __forceinline__ void warp_step_eval(const FwdParamsView &v, int k, co
     if (STORE) lmax = warp_max(lmax);
 }
 
+// Bin readout (Section 4.4) on a warp-per-trajectory forward. Every lane runs the same bookkeeping on the
+// same values (the running integrals, the edges found by bisection, the slot count); lane 0 stores the bin an
+// interval's first edge closes and the slot record, and whole bins held at one state are written by the
+// warp along the trajectory's own row (consecutive lanes on consecutive floats). The values are those of
+// the thread kernels' bin readout.
+template <class XF>
+__device__ __forceinline__ void warp_bin_held(const FwdParams &p, int64_t i, int lo, int hi, const XF &xobs, bool zero)
+{
+    if (lo > hi) return;
+    const int lane = threadIdx.x & 31, no = p.n_obs;
+    float xv[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) xv[c] = (c < no && !zero) ? obs_f(xobs(c)) : 0.0f;
+    float *row = static_cast<float *>(p.obs_out) + i * (int64_t)p.S * no;
+    for (int64_t e = (int64_t)lo * no + lane; e < (int64_t)(hi + 1) * no; e += 32) {
+        const int c = no == 1 ? 0 : (int)(e % no);
+        float v = xv[0];
+#pragma unroll
+        for (int c2 = 1; c2 < kBinMaxObs; ++c2) v = c == c2 ? xv[c2] : v;
+        row[e] = v;
+    }
+}
+
+template <bool RECORD, class XF>
+__device__ __forceinline__ void warp_bin_first_edge(const FwdParams &p, int64_t i, int s, double t_k, int k,
+                                                    float (&acc)[kBinMaxObs], const XF &xobs, int &slots, bool zero)
+{
+    float o[kBinMaxObs];
+    const float d = bin_close(acc, xobs, p.n_obs, p.ts, s, t_k, true, o);
+    if ((threadIdx.x & 31) == 0) {
+        float *dst = static_cast<float *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
+        for (int c = 0; c < p.n_obs; ++c) dst[c] = zero ? 0.0f : o[c];
+        if (RECORD) {
+            const int64_t at = (int64_t)slots * p.n_traj + i;
+            p.brk_k[at] = k;
+            p.brk_s[at] = s;
+            p.brk_a[at] = d;
+        }
+    }
+    if (RECORD) ++slots;
+}
+
+// the edges in the state interval [t_k, t_next) from s on; returns the first edge at or after t_next
+template <bool RECORD, class XF>
+__device__ __forceinline__ int warp_bin_edges(const FwdParams &p, int64_t i, int s, double t_k, double t_next, int k,
+                                              float (&acc)[kBinMaxObs], const XF &xobs, int &slots)
+{
+    int lo = s, hi = p.S;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (gt_nonneg(t_next, p.ts[mid])) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo > s) {
+        warp_bin_first_edge<RECORD>(p, i, s, t_k, k, acc, xobs, slots, false);
+        warp_bin_held(p, i, s + 1, lo - 1, xobs, false);
+    }
+    return lo;
+}
+
+// after the last state (held from t_k on): close the first remaining bin, hold the rest, record the slot count
+template <bool RECORD, class XF>
+__device__ __forceinline__ void warp_bin_tail(const FwdParams &p, int64_t i, int s, double t_k, int k,
+                                              float (&acc)[kBinMaxObs], const XF &xobs, bool bad_obs, int &slots)
+{
+    if (s < p.S) {
+        warp_bin_first_edge<RECORD>(p, i, s, t_k, k, acc, xobs, slots, bad_obs);
+        warp_bin_held(p, i, s + 1, p.S - 1, xobs, bad_obs);
+    }
+    if (RECORD && (threadIdx.x & 31) == 0) p.brk_tail[i] = slots;
+}
+
 // Per-trajectory body of the warp forward (all 32 lanes of one warp); X = this warp's counts.
 template <int READOUT, bool RECORD>
 __device__ __forceinline__ void warp_fwd_body(const FwdParams &p, const int4 *s_rx, const int *s_st, const float *s_k,
@@ -108,6 +180,16 @@ __device__ __forceinline__ void warp_fwd_body(const FwdParams &p, const int4 *s_
     int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
     int k = 0, draws = 0, ck_left = p.K, ck_row = 0;
     uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+    constexpr bool kBin = READOUT == SSA_READOUT_BIN;
+    float bacc[kBinMaxObs];
+    int osp[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) {
+        bacc[c] = 0.0f;
+        osp[c] = (kBin && c < p.n_obs && !bad_obs) ? p.obs_sp[c] : 0;
+    }
+    auto xobs = [&](int c) { return X[osp[c]]; };
+    int slots = 0;
 
     while (!bad_input) {
         if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
@@ -142,7 +224,16 @@ __device__ __forceinline__ void warp_fwd_body(const FwdParams &p, const int4 *s_
         }
         draws = k + 1;
         if (status != SSA_TRAJ_OK) break;
-        if (slow) {
+        if (slow && kBin) {
+            const int s_first = s;
+            s = warp_bin_edges<RECORD>(p, i, s, t, t_next, k, bacc, xobs, slots);
+            if (!cross && s > s_first) bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
+            thr = s < p.S ? p.ts[s] : p.t_end;
+            if (cross) break;
+        } else if (kBin) {
+            bin_accumulate(bacc, xobs, p.n_obs, tau);
+        }
+        if (slow && !kBin) {
             while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
                 if (READOUT == SSA_READOUT_HOLD) {
                     int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
@@ -181,7 +272,8 @@ __device__ __forceinline__ void warp_fwd_body(const FwdParams &p, const int4 *s_
         }
     }
     __syncwarp();
-    for (; s < p.S; ++s) {
+    if constexpr (kBin) warp_bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs, slots);
+    for (; !kBin && s < p.S; ++s) {
         if (READOUT == SSA_READOUT_HOLD) {
             int *o = static_cast<int *>(p.obs_out) + ((int64_t)i * p.S + s) * p.n_obs;
             for (int c = lane; c < p.n_obs; c += 32) o[c] = bad_obs ? 0 : X[p.obs_sp[c]];
@@ -245,8 +337,25 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
         const uint32_t w = word_of(row, slot >> 1);
         return (slot & 1) ? (int)(w >> 16) : (int)(w & 0xffff);
     };
+    constexpr bool kBin = READOUT == SSA_READOUT_BIN;
     int s_hi = p.S - 1;
-    int brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    int brk_next = (!kBin && s_hi >= 0) ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    // BIN readout: the recorded slots (one per state interval with edges), gq = g of the bin that contains
+    // t_{k+1}, xo = X_{k+1} at the observables; every lane keeps the same copies
+    BinSlots bslots{-1, -1};
+    float d_first = 0.0f, d_last = 0.0f;
+    float gq[kBinMaxObs], gk[kBinMaxObs];
+    int osp[kBinMaxObs], xo[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) osp[c] = (kBin && c < p.n_obs) ? p.obs_sp[c] : 0;
+    auto xobs = [&](int c) { return X[osp[c]]; };
+    auto addx = [&](int c, float v) { lam[osp[c]] += v; };
+    if (kBin) {
+        bin_slots_init(bslots, p.brk_k, p.brk_tail, n, i);
+        bin_grad(gq, gl, p.n_obs, p.ts, p.S, p.S);
+#pragma unroll
+        for (int c = 0; c < kBinMaxObs; ++c) xo[c] = c < p.n_obs ? xobs(c) : 0;
+    }
     float mu = 0.0f;
     int mism = 0;
     int ck_row = L / p.K, ck_off = L - ck_row * p.K;
@@ -254,10 +363,20 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
     for (int k = L; k >= 0; --k) {
         const bool draw = (k < L) || (st == SSA_TRAJ_OK);
         const int s_top = s_hi;
-        while (s_hi >= 0 && brk_next == k) {
-            --s_hi;
-            brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+        if (kBin) {
+            bin_slots_step(bslots, p.brk_k, p.brk_s, p.brk_a, p.ts, n, i, k, s_hi, d_first, d_last);
+            if (s_hi < s_top) bin_grad(gk, gl, p.n_obs, p.ts, p.S, s_hi + 1);
+            else {
+#pragma unroll
+                for (int c = 0; c < kBinMaxObs; ++c) gk[c] = gq[c];
+            }
+        } else {
+            while (s_hi >= 0 && brk_next == k) {
+                --s_hi;
+                brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+            }
         }
+        float tau_k = 0.0f;
         if (draw) {
             const int jk = event_at(k);
             float a0, E0, ab, Eb, lmax;
@@ -265,7 +384,10 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
             warp_step_eval<true>(v, k, X, a0, E0, ab, Eb, jb, aj, lj, lmax);
             mism += (jb != jk);
             const float tau = waiting_time(E0, a0);
+            tau_k = tau;
             const int4 rk = s_rx[jpos(jk, v.nb)];
+            // BIN: t_{k+1} ends this interval and starts the next, in the bin of gq
+            if (kBin) mu -= bin_transition(xobs, xo, gq, p.n_obs);
             float dt_dir = 0.0f, dtau_dir = 0.0f;
             if (READOUT == SSA_READOUT_LINEAR) {
                 // serial on lane 0 (observed species may repeat), broadcast afterwards
@@ -342,8 +464,9 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
                     const float t1 = a > 0.0f ? __fdividef(num, den) : 0.0f;
                     const float c1 = has1 ? t1 + c_tau * (homo ? dh : x2) : 0.0f;
                     const float c2 = (has2 && !homo) ? (a > 0.0f ? __fdividef(psi, xr2) : 0.0f) + c_tau * x1 : 0.0f;
-                    ct[pos] = c1;          // reactant slot 0
-                    ct[p.Mp + pos] = c2;   // reactant slot 1
+                    // the soft weight and w_j of this reaction are spent: its slots take the contributions
+                    lj[pos] = c1;  // reactant slot 0
+                    ct[pos] = c2;  // reactant slot 1
                 }
             }
             __syncwarp();
@@ -362,7 +485,7 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
                     int e = s_inc_ptr[sp] + r;
                     auto slot_val = [&](int ee) {
                         const int slot = s_inc[ee];  // 2 j + reactant slot
-                        return ct[(slot & 1) * p.Mp + jpos(slot >> 1, v.nb)];
+                        return ((slot & 1) ? ct : lj)[jpos(slot >> 1, v.nb)];
                     };
                     for (; e + 3 * gsz < e1; e += 4 * gsz) {
                         c0 += slot_val(e);
@@ -379,7 +502,15 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
             mu += dt_dir;
         }
         __syncwarp();
-        if (lane == 0) {
+        if (kBin) {
+            if (lane == 0)
+                bin_state_terms(addx, d_first, d_last, gl, p.bin_prefix, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq, gk);
+#pragma unroll
+            for (int c = 0; c < kBinMaxObs; ++c) {
+                gq[c] = gk[c];
+                if (c < p.n_obs) xo[c] = xobs(c);
+            }
+        } else if (lane == 0) {
             for (int s = s_hi + 1; s <= s_top; ++s) {
                 float coef = 1.0f;
                 if (READOUT == SSA_READOUT_LINEAR && draw) {

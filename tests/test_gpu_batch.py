@@ -67,20 +67,20 @@ def _fill_dl(b, specs, seed=3):
         b.dl_dobs[q].copy_(torch.tensor(dl, dtype=torch.float32))
 
 
-def _single(S, net, item, variant, dl, T):
+def _single(S, net, item, variant, dl, T, readout="linear"):
     fw = S.forward(net, torch.tensor(item["log_rates"], device="cuda"), item["n_traj"], item["x0"], item["t_end"],
-                   item["sample_times"], item["obs_species"], item["seed"], readout="linear", record=True,
+                   item["sample_times"], item["obs_species"], item["seed"], readout=readout, record=True,
                    max_steps=item["max_steps"], traj_offset=item["traj_offset"], threads_per_traj=variant,
                    ckpt_interval=64)
     g = S.backward(fw, dl, T) if item["n_traj"] > 0 else torch.zeros(net.n_params, device="cuda")
     return fw, g
 
 
-def _check_against_single(S, b, specs, nets, items, T):
+def _check_against_single(S, b, specs, nets, items, T, readout="linear"):
     for q in range(len(specs)):
         v = b.variant(q)
         assert v in (1, 32)
-        fw, g = _single(S, nets[q], items[q], v, b.dl_dobs[q], T)
+        fw, g = _single(S, nets[q], items[q], v, b.dl_dobs[q], T, readout)
         draws, status, mism = b.outputs(q)
         assert mism == 0
         torch.testing.assert_close(b.obs[q], fw.obs, rtol=0, atol=0)
@@ -359,3 +359,23 @@ def test_batch_autotuned_checkpoint_interval_changes_no_result(S):
         assert fixed.ckpt_interval(q) == 64
         assert torch.equal(free.obs[q], fixed.obs[q]) and torch.equal(free.dtheta[q], fixed.dtheta[q]), q
         assert free.outputs(q)[2] == 0 and fixed.outputs(q)[2] == 0
+
+
+@pytest.mark.parametrize("shared", [False, True])
+def test_batch_bin_readout_matches_single_network_entry_points(S, specs, shared):
+    """The bin readout (Section 4.4) in the batch: thread units and warp units give the bin averages of the
+    single-network calls bit for bit and their gradients to binary32 rounding, with one upstream gradient
+    per trajectory or one shared by all of an item's trajectories (the binary64 prefix sums)."""
+    nets = [S.Network(sp[0]) for sp in specs]
+    items = _items(S, specs, nets)
+    for it in items:
+        it["obs_species"] = it["obs_species"][:4]
+        it["shared_dl"] = shared
+    b = S.Batch(items, readout="bin", temperature=0.6)
+    for q, (net, n, t_end, ns, obs, *_rest) in enumerate(specs):
+        shape = (1, ns, len(items[q]["obs_species"])) if shared else (n, ns, len(items[q]["obs_species"]))
+        dl = W.seeded_dl_dobs(40 + q, *shape, scale=1.0 / max(n, 1))
+        b.dl_dobs[q].copy_(torch.tensor(dl[0] if shared else dl, dtype=torch.float32))
+    b.run()
+    torch.cuda.synchronize()
+    _check_against_single(S, b, specs, nets, items, 0.6, readout="bin")

@@ -32,11 +32,11 @@ def _lo(ts):
     return np.concatenate([[0.0], np.asarray(ts)[:-1]])
 
 
-def _run_both(S, net, n, t_end, ts, obs_sp, seed, dl=None, T=1.0, max_steps=4096, specialize=True, K=64):
+def _run_both(S, net, n, t_end, ts, obs_sp, seed, dl=None, T=1.0, max_steps=4096, specialize=True, K=64, tpt=0):
     t32, t64 = _theta32(net.log_rates)
     snet = S.Network(net)
     fw = S.forward(snet, torch.tensor(t32, device="cuda"), n, net.x0, t_end, ts, obs_sp, seed, readout="bin",
-                   record=True, max_steps=max_steps, specialize=specialize, ckpt_interval=K)
+                   record=True, max_steps=max_steps, specialize=specialize, ckpt_interval=K, threads_per_traj=tpt)
     torch.cuda.synchronize()
     orc = native.run(net, t64, net.x0, n, t_end, ts, np.asarray(obs_sp, np.int32), seed, BIN, max_steps=max_steps,
                      dl_dobs=dl, temperature=T, ev_cap=max_steps)
@@ -164,14 +164,19 @@ def test_bin_input_rules_and_limits(S):
     # the same edges are fine for the HOLD readout
     fw = S.forward(snet, theta, 8, net.x0, 1.0, [0.0, 1.0], [0], 0, readout="hold")
     assert torch.all(fw.status <= 1)
-    # more than SSA_BIN_MAX_OBS observables, the warp kernels and the batch refuse the readout
+    # more than SSA_BIN_MAX_OBS observables are refused, on every kernel and in the batch
     with pytest.raises(RuntimeError):
         S.forward(snet, theta, 8, net.x0, 1.0, [1.0], [0, 1, 2, 0, 1], 0, readout="bin")
     with pytest.raises(RuntimeError):
-        S.forward(snet, theta, 8, net.x0, 1.0, [1.0], [0], 0, readout="bin", threads_per_traj=32)
+        S.forward(snet, theta, 8, net.x0, 1.0, [1.0], [0, 1, 2, 0, 1], 0, readout="bin", threads_per_traj=32)
     with pytest.raises(RuntimeError):
         S.Batch([dict(net=snet, log_rates=theta, n_traj=8, x0=net.x0, t_end=1.0, sample_times=[1.0],
+                      obs_species=[0, 1, 2, 0, 1], seed=0)], readout="bin")
+    # a batch item's bin edges follow the same rule: an empty first bin makes its trajectories BAD_INPUT
+    b = S.Batch([dict(net=snet, log_rates=theta, n_traj=8, x0=net.x0, t_end=1.0, sample_times=[0.0, 1.0],
                       obs_species=[0], seed=0)], readout="bin")
+    b.run()
+    assert torch.all(b.outputs(0)[1] == 6)
     # empty batch of trajectories
     fw = S.forward(snet, theta, 0, net.x0, 1.0, [0.5, 1.0], [0], 0, readout="bin", record=True)
     assert fw.obs.shape == (0, 2, 1)
@@ -205,7 +210,7 @@ def test_bin_on_the_generic_runtime_loop_kernels(S):
     obs_sp = [0, 1, 2]
     n = 512
     dl = W.seeded_dl_dobs(4, n, len(ts), len(obs_sp), scale=1.0 / n)
-    snet, fw, orc, gev = _run_both(S, spec, n, t_end, ts, obs_sp, 6, dl=dl, T=0.5, max_steps=1 << 14)
+    snet, fw, orc, gev = _run_both(S, spec, n, t_end, ts, obs_sp, 6, dl=dl, T=0.5, max_steps=1 << 14, tpt=1)
     assert fw.run.variant == 1
     same = _compare_events(orc, fw, gev, t_end, spec.n_reactions, floor=0.99)
     _check_obs(spec, fw, orc, same, ts, np.asarray(obs_sp))
@@ -285,3 +290,56 @@ def test_bin_without_samples(S):
     assert fw.obs.shape == (64, 0, 1) and torch.all(fw.status <= 1)
     g = S.backward(fw, torch.zeros(0, 1, device="cuda"), 0.5)
     assert torch.count_nonzero(g) == 0
+
+
+WARP_CASES = {
+    "ion_channel": lambda: (W.ion_channel_coi(), 8.0, W.uniform_sample_grid(8.0, 80), [1], 1024),
+    "ragged_bins": lambda: (W.mixed_orders_toy(), 5.0, np.array([1e-3, 0.5, 0.5 + 1e-6, 0.75, 3.0, 4.999, 5.0]),
+                            [0, 2], 333),
+    "held_runs": lambda: (W.immigration_death(1.0, 0.1), 100.0, W.uniform_sample_grid(100.0, 3000), [0], 96),
+    "random_160": lambda: (W.random_network(np.random.default_rng(31), n_species_range=(8, 16),
+                                            n_reactions_range=(160, 160)), None, None, [0, 1, 2, 3], 256),
+}
+
+
+@pytest.mark.parametrize("shared", [False, True])
+@pytest.mark.parametrize("case", sorted(WARP_CASES))
+def test_bin_on_warp_kernels_matches_oracle(S, case, shared):
+    """The bin readout on the warp-per-trajectory kernels (networks with hundreds of reactions): bin averages
+    within the tolerance above on the trajectories whose events agree (long held runs written warp-wide
+    included), and the straight-through gradient against the oracle's, with one upstream gradient per
+    trajectory and with one shared by all (the prefix-sum path)."""
+    net, t_end, ts, obs_sp, n = WARP_CASES[case]()
+    if t_end is None:
+        from test_gpu_warp import _pilot_t_end
+        t_end = _pilot_t_end(net, net.log_rates.astype(np.float32).astype(np.float64))
+        ts = W.uniform_sample_grid(t_end, 17)
+    ts = np.asarray(ts)
+    T = 0.4
+    g1 = W.seeded_dl_dobs(7, 1, len(ts), len(obs_sp), scale=1.0 / n)
+    dl = np.repeat(g1, n, axis=0) if shared else W.seeded_dl_dobs(7, n, len(ts), len(obs_sp), scale=1.0 / n)
+    snet, fw, orc, gev = _run_both(S, net, n, t_end, ts, obs_sp, 21, dl=dl, T=T, max_steps=1 << 15, K=16, tpt=32)
+    assert fw.run.variant == 32
+    np.testing.assert_array_equal(fw.status.cpu().numpy(), orc.status)
+    same = _compare_events(orc, fw, gev, t_end, net.n_reactions, floor=0.99)
+    _check_obs(net, fw, orc, same, ts, np.asarray(obs_sp))
+    agree = _bracket_agreement(orc, fw, ts, net.n_reactions)
+    same &= agree
+    if shared:
+        # one upstream gradient for every trajectory: the oracle's sum over the agreeing ones
+        assert same.all() or same.mean() > 0.98
+        up = torch.tensor(g1[0], dtype=torch.float32, device="cuda")
+        keep = same
+    else:
+        dl_g = dl.copy()
+        dl_g[~same] = 0.0
+        up = torch.tensor(dl_g, dtype=torch.float32, device="cuda")
+        keep = same
+    g = S.backward(fw, up, T).cpu().numpy().astype(np.float64)
+    _, mism = fw.run.status_counts()
+    assert mism == 0
+    if shared and not same.all():
+        pytest.skip("a trajectory disagrees; the shared upstream gradient cannot exclude it")
+    ref = orc.dtheta[keep].sum(0)
+    rel = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert rel < GRAD_RTOL, (rel, g, ref)
