@@ -1017,32 +1017,56 @@ def grn_extra(ssa, dev, n_img: int = 512, tpi: int = 64, t_end: float = 20.0, re
     out["soft_gradient"] = {"images": n_sg, "trajectories": ns, "ssa_steps": sg_steps, "forward_rec_ms": sf_ms,
                             "backward_ms": sa_ms, "fwd_adj_steps_per_s": sg_steps / ((sf_ms + sa_ms) / 1e3),
                             "temperature": 1.0}
-    # the tensor-core kernel alone: the GRN's contraction (8 six-bit limbs of W1 against 512 images)
-    # and a large square product
+    # the tensor-core kernel alone: the GRN's contraction (8 six-bit limbs of W1 against 512 images) and a
+    # large square product; the E1 shape has 4 output tiles of 128 x 256, so it is timed with the split-K
+    # work buffer (the default of the binding) and without it (one CTA per tile)
     gem = {}
+    L = ssa._lib.lib()
     for name, (M, N, K) in {"grn_E1_limbs": (n_img, p.n_hid, p.n_in * 8), "square_8192": (8192, 8192, 8192)}.items():
         A = torch.randn(M, K, device=dev).to(torch.bfloat16)
         B = torch.randn(N, K, device=dev).to(torch.bfloat16)
-        ssa.bf16_gemm(A, B)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        it = 5 if M >= 4096 else 50
-        Ap = torch.zeros((M, (K + 7) // 8 * 8), dtype=torch.bfloat16, device=dev)
-        Bp = torch.zeros((N, (K + 7) // 8 * 8), dtype=torch.bfloat16, device=dev)
+        ld = (K + 7) // 8 * 8
+        Ap = torch.zeros((M, ld), dtype=torch.bfloat16, device=dev)
+        Bp = torch.zeros((N, ld), dtype=torch.bfloat16, device=dev)
         Ap[:, :K], Bp[:, :K] = A, B
         D = torch.empty((M, N), device=dev)
         err = torch.zeros(1, dtype=torch.int32, device=dev)
-        ld = Ap.shape[1]
-        L = ssa._lib.lib()
-        e0.record(stream)
-        for _ in range(it):
-            ssa.check(L.ssa_bf16_gemm(ssa._ptr(Ap), ssa._ptr(Bp), M, N, K, ld, ld, None, ssa._ptr(D), N,
-                                      ssa._ptr(err), ssa._stream()))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / it
-        gem[name] = {"M": M, "N": N, "K": K, "ms": ms, "tflops": 2.0 * M * N * K / (ms / 1e3) / 1e12,
-                     "timeout_flag": int(err.item())}
+        it = 5 if M >= 4096 else 50
+        for split in (True, False):
+            words = int(L.ssa_bf16_gemm_work_words(M, N, K)) if split else 0
+            if not split and name != "grn_E1_limbs":
+                continue
+            work = torch.empty(max(words, 1), dtype=torch.float64, device=dev) if words else None
+            call = lambda: ssa.check(L.ssa_bf16_gemm(ssa._ptr(Ap), ssa._ptr(Bp), M, N, K, ld, ld, None, ssa._ptr(D), N,  # noqa: E731
+                                                     ssa._ptr(work), words, ssa._ptr(err), ssa._stream()))
+            for _ in range(3):
+                call()
+            torch.cuda.synchronize()
+            # the launches are captured in a CUDA graph and replayed, so that the host's tensor-map encoding
+            # does not pace the microsecond-scale product
+            side = torch.cuda.Stream()
+            side.wait_stream(stream)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(graph, stream=side):
+                    for _ in range(it):
+                        call()
+            stream.wait_stream(side)
+            graph.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / it
+            del graph
+            ent = {"M": M, "N": N, "K": K, "ms": ms, "tflops": 2.0 * M * N * K / (ms / 1e3) / 1e12,
+                   "k_split": max(1, words // (M * N)), "ctas": -(-M // 128) * -(-N // 256) * max(1, words // (M * N)),
+                   "timeout_flag": int(err.item()), "timing": f"one CUDA graph of {it} launches, replayed",
+                   "operands": "L2-resident across the repeated launches"}
+            gem[name if split else name + "_one_cta_per_tile"] = ent
+            del work
         del A, B, Ap, Bp, D
     try:
         peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])

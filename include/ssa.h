@@ -358,11 +358,22 @@ ssa_status ssa_philox_uniforms(uint64_t seed, const uint64_t *traj, const uint64
  * activation energy E = b + sum w x) is this product; the entry point exposes it for tests and users.
  *   A device bf16 [M][lda], B device bf16 [N][ldb] (K-major rows; lda, ldb multiples of 8 and
  *   16-byte aligned bases), D device float [M][ldd], bias device float [N] or NULL.
+ *   work, work_words: device binary64 scratch (16-byte aligned) of at least
+ *   ssa_bf16_gemm_work_words(M, N, K) words, owned by the caller, or NULL / 0. With it, a product
+ *   whose 128 x 256 output tiles fill few of the SMs splits K across CTAs: each split's binary32
+ *   tensor-memory sum is stored in binary64, a second kernel adds the splits in a fixed order and the
+ *   bias and rounds once to binary32 (deterministic). Without it, one CTA per tile takes all of K.
+ *   K = 0 writes D = bias (or 0).
  *   err_flag device int32, set nonzero by the kernel if a bounded wait timed out.
+ * Errors: SSA_ERR_INVALID_ARG (sizes, NULL operands, alignment), SSA_ERR_WORKSPACE (work too small).
  */
 ssa_status ssa_bf16_gemm(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K,
                          int32_t lda, int32_t ldb, const float *bias, float *D, int32_t ldd,
-                         int32_t *err_flag, void *stream);
+                         double *work, int64_t work_words, int32_t *err_flag, void *stream);
+
+/* ssa_bf16_gemm_work_words -- binary64 words of the work buffer ssa_bf16_gemm splits K into for this
+ * shape (0: it would not split). Host only. */
+int64_t ssa_bf16_gemm_work_words(int32_t M, int32_t N, int32_t K);
 
 /*
  * ssa_exp_variates -- test hook: out[i] = -ln u(words[i]) with u(x) = ((x >> 9) + 1/2) 2^-23, the

@@ -28,7 +28,7 @@ EXPORTS = (
     "ssa_create_network", "ssa_destroy_network", "ssa_forward_workspace_bytes", "ssa_forward",
     "ssa_forward_replay", "ssa_backward", "ssa_backward_wide", "ssa_backward_multi", "ssa_run_status", "ssa_run_events", "ssa_run_brackets", "ssa_destroy_run",
     "ssa_ensemble_mean_workspace_bytes", "ssa_ensemble_mean", "ssa_ensemble_mean_static", "ssa_philox_uniforms",
-    "ssa_bf16_gemm", "ssa_pipe_rates", "ssa_last_error", "ssa_grn_create", "ssa_grn_destroy",
+    "ssa_bf16_gemm", "ssa_bf16_gemm_work_words", "ssa_pipe_rates", "ssa_last_error", "ssa_grn_create", "ssa_grn_destroy",
     "ssa_grn_workspace_bytes", "ssa_grn_forward", "ssa_grn_backward", "ssa_grn_activations",
     "ssa_batch_create", "ssa_batch_destroy", "ssa_batch_set_plan", "ssa_batch_workspace_bytes", "ssa_batch_run",
     "ssa_batch_item_outputs", "ssa_batch_autotune", "ssa_batch_item_variant", "ssa_batch_item_events",
@@ -105,7 +105,8 @@ def _declare(lib):
         "ssa_ensemble_mean_static": (i32, [p, i32, i64, i64, p, p]),
         "ssa_philox_uniforms": (i32, [u64, p, p, i64, i32, p, p]),
         "ssa_pipe_rates": (i32, [p, p, p]),
-        "ssa_bf16_gemm": (i32, [p, p, i32, i32, i32, i32, i32, p, p, i32, p, p]),
+        "ssa_bf16_gemm": (i32, [p, p, i32, i32, i32, i32, i32, p, p, i32, p, i64, p, p]),
+        "ssa_bf16_gemm_work_words": (i64, [i32, i32, i32]),
         "ssa_last_error": (ctypes.c_char_p, []),
         "ssa_grn_create": (i32, [i32, i32, i32, f32, ctypes.POINTER(p)]),
         "ssa_grn_destroy": (None, [p]),

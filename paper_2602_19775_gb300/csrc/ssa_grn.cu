@@ -944,6 +944,9 @@ using namespace ssa;
 
 namespace {
 
+// N-tile of the tensor-core dW1 = G^T x (n_in columns)
+int grn_dw1_nt(const ssa_grn *g) { return (g->n_in % 112 == 0) ? 112 : 64; }
+
 WsLayout grn_layout(const ssa_grn *g, int64_t n_img, int64_t tpi, int32_t S, const ssa_fwd_opts *o)
 {
     WsLayout L{};
@@ -973,6 +976,11 @@ WsLayout grn_layout(const ssa_grn *g, int64_t n_img, int64_t tpi, int32_t S, con
     L.W2f = take((size_t)g->n_out * g->n_hid * 4);
     L.dvec = take((size_t)g->n_dyn * 4);
     L.grid = take(16 * sizeof(int));
+    // split-K partial sums of E1 (forward) and of dW1 (backward), when the product fills too few SMs
+    size_t tc_words = n_img > 0 ? tc_split_words((int)n_img, g->n_hid, g->n_in, 64) : 0;
+    if (o->record && n_img > 0)
+        tc_words = std::max(tc_words, tc_split_words(g->n_hid, g->n_in, (int)n_img, grn_dw1_nt(g)));
+    L.tcpart = take(std::max<size_t>(tc_words, 1) * sizeof(double));
     if (o->record) {
         // the soft forward keeps float checkpoints every 8 steps; the hard one int counts every K
         const int K = o->selector == SSA_SELECT_SOFT ? kGrnSoftK : o->ckpt_interval > 0 ? o->ckpt_interval : 64;
@@ -1130,6 +1138,7 @@ extern "C" ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, cons
                 return set_error(SSA_ERR_CUDA, "tensor map encoding failed");
         TcArgs args{(int)n_img, g->n_hid, g->n_in, 1, kGrnLimbs, kGrnLimbs, 1, b1,
                     reinterpret_cast<float *>(ws + L.E1), g->n_hid, flag + 4};
+        args.Dpart = reinterpret_cast<double *>(ws + L.tcpart);  // split K when the tiles underfill the SMs
         GRN_CUDA_TRY(tc_gemm_launch(maps, args, 64, st));
     }
     GrnParams p{};
@@ -1297,12 +1306,13 @@ extern "C" ssa_status ssa_grn_backward(ssa_run *run, const float *dl_dobs, int64
     // dW1[h][p] = sum_img G[img][h] x[img][p] on the tensor cores (hi + lo bf16 limbs of G)
     TcMaps maps;
     memset(&maps, 0, sizeof(maps));
-    const int nt = (g->n_in % 112 == 0) ? 112 : 64;
+    const int nt = grn_dw1_nt(g);
     if (!tc_make_map(&maps.a[0], Gt, g->n_hid, (int)run->n_img, L.n_img_pad, 128) ||
         !tc_make_map(&maps.a[1], Gt + gt_len, g->n_hid, (int)run->n_img, L.n_img_pad, 128) ||
         !tc_make_map(&maps.b[0], xT, g->n_in, (int)run->n_img, L.n_img_pad, nt))
         return set_error(SSA_ERR_CUDA, "tensor map encoding failed");
     TcArgs args{g->n_hid, g->n_in, (int)run->n_img, 2, 1, 2, 0, nullptr, dW1, g->n_in, flag + 4};
+    args.Dpart = reinterpret_cast<double *>(ws + L.tcpart);
     GRN_CUDA_TRY(tc_gemm_launch(maps, args, nt, st));
     return SSA_OK;
 }

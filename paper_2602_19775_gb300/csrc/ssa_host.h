@@ -36,6 +36,7 @@ struct WsLayout {
     size_t flag, counts, k_rates, ts, obs_sp, draws, status;
     size_t xfinal, ev, ckpt, brk_k, brk_a, brk_s, brk_tail, bin_prefix, partial, dA;
     size_t partial64, dA64;  // wide-range adjoint: binary64 block sums [ceil(n/128)][M] and [M]
+    size_t tcpart;           // GRN: binary64 split-K partial sums of the tensor-core contractions
     size_t total;
     int64_t ev_rows, n_ckpt, max_blocks;
     int M_pad;

@@ -18,6 +18,8 @@
 // last commit every warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) for the epilogue.
 // Terms either share one accumulator or keep one each (`separate`); separate accumulators are
 // summed in binary64 in the epilogue. Every wait is bounded and reports a timeout in `err`.
+#include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include <cuda.h>
@@ -104,6 +106,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
 
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
     const int n_acc = args.separate ? args.n_terms : 1;
+    // this CTA's K chunks (all of them without a split)
+    const int total_chunks = (args.K + 63) / 64;
+    const int c0 = args.k_split > 1 ? (int)blockIdx.z * args.chunks_per : 0;
+    const int my_chunks = args.k_split > 1 ? min(args.chunks_per, total_chunks - c0) : total_chunks;
     uint32_t ncols = 32;
     while (ncols < (uint32_t)(n_acc * NT)) ncols <<= 1;
 
@@ -123,7 +129,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     const uint32_t tmem = *s_tmem;
 
     if (tid == 0) {
-        const int n_chunks = (args.K + 63) / 64;
+        const int n_chunks = my_chunks;  // local chunk ch loads global chunk c0 + ch
         const uint32_t idesc = tc_idesc(128, NT);
         auto issue = [&](int ch) {
             unsigned char *st = stage0 + (ch & 1) * stage_bytes;
@@ -131,11 +137,11 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
             mbar_arrive_expect_tx(full, (uint32_t)stage_bytes);
             for (int a = 0; a < args.n_a; ++a)
                 for (int c = 0; c < 8; ++c)
-                    tma_load_2d(st + a * kTileA + c * (128 * 16), &maps.a[a], ch * 64 + 8 * c, m0, full);
+                    tma_load_2d(st + a * kTileA + c * (128 * 16), &maps.a[a], (c0 + ch) * 64 + 8 * c, m0, full);
             for (int b = 0; b < args.n_b; ++b)
                 for (int c = 0; c < 8; ++c)
-                    tma_load_2d(st + args.n_a * kTileA + b * kTileB + c * (NT * 16), &maps.b[b], ch * 64 + 8 * c, n0,
-                                full);
+                    tma_load_2d(st + args.n_a * kTileA + b * kTileB + c * (NT * 16), &maps.b[b], (c0 + ch) * 64 + 8 * c,
+                                n0, full);
         };
         bool ok = true;
         issue(0);
@@ -198,8 +204,12 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                 for (int i = 0; i < 8; ++i) {
                     const int col = n0 + 8 * c8 + i;
                     if (col < args.N) {
-                        const double b = args.bias ? (double)args.bias[col] : 0.0;
-                        args.D[(int64_t)row * args.ldd + col] = (float)(acc[i] + b);
+                        if (args.k_split > 1) {
+                            args.Dpart[((int64_t)blockIdx.z * args.M + row) * args.N + col] = acc[i];
+                        } else {
+                            const double b = args.bias ? (double)args.bias[col] : 0.0;
+                            args.D[(int64_t)row * args.ldd + col] = (float)(acc[i] + b);
+                        }
                     }
                 }
             }
@@ -253,10 +263,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// split K: with Dpart given, the CTAs of blockIdx.z = s take the 64-wide K blocks [s per, (s + 1) per) and
+// write their sums in binary64 to Dpart [gridDim.z][M][N] (no bias); tc_splitk_reduce_kernel adds them
 __global__ void __launch_bounds__(128, 1) tc_gemm_sw128_kernel(const __grid_constant__ CUtensorMap mapA,
                                                                 const __grid_constant__ CUtensorMap mapB, int M,
                                                                 int N, int K, const float *bias, float *D, int ldd,
-                                                                int *err)
+                                                                double *Dpart, int chunks_per, int *err)
 {
     extern __shared__ __align__(1024) unsigned char sw_raw[];
     // the swizzled tiles need 1,024-byte alignment
@@ -268,7 +280,9 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_sw128_kernel(const __grid_cons
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(done + 1);
     int *s_ok = reinterpret_cast<int *>(s_tmem + 1);
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * kSwBN;
-    const int nkb = (K + 63) / 64;
+    const int total_kb = (K + 63) / 64;
+    const int kb0 = Dpart ? (int)blockIdx.z * chunks_per : 0;
+    const int nkb = Dpart ? max(0, min(chunks_per, total_kb - kb0)) : total_kb;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
@@ -301,8 +315,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_sw128_kernel(const __grid_cons
             if (!*(volatile int *)s_ok) break;
             unsigned char *stage = sw + st * kSwStage;
             mbar_arrive_expect_tx(&full[st], (uint32_t)kSwStage);
-            tma_load_2d(stage, &mapA, kb * 64, m0, &full[st]);
-            tma_load_2d(stage + kSwTileA, &mapB, kb * 64, n0, &full[st]);
+            tma_load_2d(stage, &mapA, (kb0 + kb) * 64, m0, &full[st]);
+            tma_load_2d(stage + kSwTileA, &mapB, (kb0 + kb) * 64, n0, &full[st]);
         }
     } else if (tid == 32) {
         // MMA issuer: four K = 16 steps per block, advancing the descriptors by 32 bytes inside the atom
@@ -338,7 +352,18 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_sw128_kernel(const __grid_cons
             float v[16];
             tmem_ld16(lane_base + (uint32_t)(16 * c16), v);
             const int col0 = n0 + 16 * c16;
-            if (row < M) {
+            if (Dpart) {
+                if (row < M) {
+                    double *dp = Dpart + ((int64_t)blockIdx.z * M + row) * N + col0;
+                    if (col0 + 16 <= N && (N % 2) == 0) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 2)
+                            *reinterpret_cast<double2 *>(dp + i) = make_double2((double)v[i], (double)v[i + 1]);
+                    } else {
+                        for (int i = 0; i < 16 && col0 + i < N; ++i) dp[i] = (double)v[i];
+                    }
+                }
+            } else if (row < M) {
                 float *dst = D + (int64_t)row * ldd + col0;
                 if (col0 + 16 <= N && (ldd % 4) == 0 && (reinterpret_cast<uintptr_t>(D) & 15) == 0) {
 #pragma unroll
@@ -416,20 +441,97 @@ static bool tc_make_map_sw128(CUtensorMap *map, const void *base, int rows, int 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+
+// D[m][n] = (sum over splits s in order of Dpart[s][m][n]) + bias[n], rounded once to binary32
+__global__ void tc_splitk_reduce_kernel(const double *Dpart, int k_split, int M, int N, const float *bias, float *D,
+                                        int ldd)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * N) return;
+    const int m = (int)(e / N), n = (int)(e % N);
+    double acc = 0.0;
+    for (int s = 0; s < k_split; ++s) acc += Dpart[(int64_t)s * M * N + e];
+    D[(int64_t)m * ldd + n] = (float)(acc + (bias ? (double)bias[n] : 0.0));
+}
+
+int tc_split_count(int M, int N, int K, int nt)
+{
+    const int64_t tiles = (int64_t)((M + 127) / 128) * ((N + nt - 1) / nt);
+    const int total = (K + 63) / 64;
+    constexpr int kTargetCtas = 152;  // one CTA per SM of this part
+    if (tiles >= kTargetCtas || total <= 1) return 1;
+    int k = (int)std::min<int64_t>(total, kTargetCtas / tiles);
+    if (k <= 1) return 1;
+    const int per = (total + k - 1) / k;
+    return (total + per - 1) / per;  // every split non-empty
+}
+
+size_t tc_split_words(int M, int N, int K, int nt)
+{
+    const int k = tc_split_count(M, N, K, nt);
+    return k > 1 ? (size_t)k * M * N : 0;
+}
+
+// K splits of the plain GEMM (1: none) and the K blocks of each: the output tiles times the splits come up
+// to one CTA per SM, and every split keeps at least four K blocks so that each CTA still fills its ring
+static int sw_split(int M, int N, int K, int *per)
+{
+    const int64_t tiles = (int64_t)((M + 127) / 128) * ((N + kSwBN - 1) / kSwBN);
+    const int total = (K + 63) / 64;
+    constexpr int kTargetCtas = 152;
+    *per = total;
+    const int k = (int)std::min<int64_t>(total / 4, tiles >= kTargetCtas ? 1 : kTargetCtas / tiles);
+    if (k <= 1) return 1;
+    *per = (total + k - 1) / k;
+    return (total + *per - 1) / *per;  // every split non-empty
+}
+
 static cudaError_t tc_gemm_sw128_launch(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
-                                        const float *bias, float *D, int ldd, int *err, cudaStream_t st)
+                                        const float *bias, float *D, int ldd, double *work, int *err, cudaStream_t st)
 {
     const size_t smem = (size_t)kSwStages * kSwStage + 128 + 1024;  // ring, barriers, alignment slack
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_sw128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the attribute is set once per device and kept by the context, so calls inside a graph capture make no
+    // further runtime calls (after cudaDeviceReset the launch fails with an error instead)
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + kSwBN - 1) / kSwBN));
-    tc_gemm_sw128_kernel<<<grid, 128, smem, st>>>(ma, mb, M, N, K, bias, D, ldd, err);
+    if (dev >= 64 || !(attr_set.load() & (1ull << dev))) {
+        e = cudaFuncSetAttribute(tc_gemm_sw128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) attr_set.fetch_or(1ull << dev);
+    }
+    int per = (K + 63) / 64;
+    const int k_split = work ? sw_split(M, N, K, &per) : 1;
+    dim3 grid((unsigned)((M + 127) / 128), (unsigned)((N + kSwBN - 1) / kSwBN), (unsigned)k_split);
+    tc_gemm_sw128_kernel<<<grid, 128, smem, st>>>(ma, mb, M, N, K, bias, D, ldd, k_split > 1 ? work : nullptr, per,
+                                                  err);
+    if (k_split > 1) {
+        const int64_t n = (int64_t)M * N;
+        tc_splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(work, k_split, M, N, bias, D, ldd);
+    }
     return cudaGetLastError();
 }
 
-template <int NT>
-static cudaError_t tc_launch_t(const TcMaps &maps, const TcArgs &args, cudaStream_t st)
+int64_t sw_gemm_work_words(int M, int N, int K)
 {
+    if (M <= 0 || N <= 0 || K <= 0) return 0;
+    int per;
+    const int k_split = sw_split(M, N, K, &per);
+    return k_split > 1 ? (int64_t)k_split * M * N : 0;
+}
+
+template <int NT>
+static cudaError_t tc_launch_t(const TcMaps &maps, const TcArgs &args_in, cudaStream_t st)
+{
+    TcArgs args = args_in;
+    args.k_split = 1;
+    args.chunks_per = 0;
+    if (args.Dpart) {
+        args.k_split = tc_split_count(args.M, args.N, args.K, NT);
+        const int total = (args.K + 63) / 64;
+        args.chunks_per = (total + args.k_split - 1) / args.k_split;
+    }
     const size_t stage = (size_t)args.n_a * 128 * 128 + (size_t)args.n_b * NT * 128;
     // 64 KB of slack past the ring: every core-matrix address a descriptor can form from these
     // tiles stays inside the CTA's shared-memory allocation
@@ -437,8 +539,13 @@ static cudaError_t tc_launch_t(const TcMaps &maps, const TcArgs &args, cudaStrea
     if (smem > 232448) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((args.M + 127) / 128), (unsigned)((args.N + NT - 1) / NT));
+    dim3 grid((unsigned)((args.M + 127) / 128), (unsigned)((args.N + NT - 1) / NT), (unsigned)args.k_split);
     tc_gemm_kernel<NT><<<grid, 128, smem, st>>>(maps, args);
+    if (args.k_split > 1) {
+        const int64_t total = (int64_t)args.M * args.N;
+        tc_splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(args.Dpart, args.k_split, args.M, args.N,
+                                                                                 args.bias, args.D, args.ldd);
+    }
     return cudaGetLastError();
 }
 
@@ -457,18 +564,35 @@ ssa_status set_error(ssa_status code, const char *text);
 
 }  // namespace ssa
 
+extern "C" int64_t ssa_bf16_gemm_work_words(int32_t M, int32_t N, int32_t K)
+{
+    return ssa::sw_gemm_work_words(M, N, K);
+}
+
 extern "C" ssa_status ssa_bf16_gemm(const uint16_t *A, const uint16_t *B, int32_t M, int32_t N, int32_t K,
-                                    int32_t lda, int32_t ldb, const float *bias, float *D, int32_t ldd, int32_t *err_flag,
-                                    void *stream)
+                                    int32_t lda, int32_t ldb, const float *bias, float *D, int32_t ldd, double *work,
+                                    int64_t work_words, int32_t *err_flag, void *stream)
 {
     using namespace ssa;
     if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldd < N) return set_error(SSA_ERR_INVALID_ARG, "bad GEMM sizes");
-    if ((M > 0 && N > 0) && (!A || !B || !D || !err_flag)) return set_error(SSA_ERR_INVALID_ARG, "NULL GEMM operand");
+    if ((M > 0 && N > 0) && (!D || !err_flag || (K > 0 && (!A || !B))))
+        return set_error(SSA_ERR_INVALID_ARG, "NULL GEMM operand");
     if ((lda % 8) || (ldb % 8)) return set_error(SSA_ERR_INVALID_ARG, "lda and ldb must be multiples of 8 (16-byte rows)");
+    if (work && (reinterpret_cast<uintptr_t>(work) & 15))
+        return set_error(SSA_ERR_INVALID_ARG, "the GEMM work buffer must be 16-byte aligned");
+    if (work && work_words < sw_gemm_work_words(M, N, K))
+        return set_error(SSA_ERR_WORKSPACE, "GEMM work buffer smaller than ssa_bf16_gemm_work_words");
     if (M == 0 || N == 0) return SSA_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (K == 0) {  // an empty sum: D = bias (or 0)
+        const int64_t n = (int64_t)M * N;
+        tc_splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nullptr, 0, M, N, bias, D, ldd);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? SSA_OK : set_error(SSA_ERR_CUDA, cudaGetErrorString(e));
+    }
     CUtensorMap ma, mb;
     if (!tc_make_map_sw128(&ma, A, M, K, lda, 128) || !tc_make_map_sw128(&mb, B, N, K, ldb, kSwBN))
         return set_error(SSA_ERR_INVALID_ARG, "tensor map encoding failed (alignment or driver entry point)");
-    cudaError_t e = tc_gemm_sw128_launch(ma, mb, M, N, K, bias, D, ldd, err_flag, static_cast<cudaStream_t>(stream));
+    cudaError_t e = tc_gemm_sw128_launch(ma, mb, M, N, K, bias, D, ldd, work_words > 0 ? work : nullptr, err_flag, st);
     return e == cudaSuccess ? SSA_OK : set_error(SSA_ERR_CUDA, cudaGetErrorString(e));
 }

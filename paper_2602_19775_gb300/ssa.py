@@ -435,8 +435,11 @@ def pipe_rates() -> dict:
     return out
 
 
-def bf16_gemm(A: torch.Tensor, B: torch.Tensor, bias: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """ssa_bf16_gemm: A [M, K] bf16, B [N, K] bf16 (K-major) -> A B^T (+ bias) in float32 on tcgen05."""
+def bf16_gemm(A: torch.Tensor, B: torch.Tensor, bias: torch.Tensor | None = None, stream=None,
+              split_k: bool = True) -> torch.Tensor:
+    """ssa_bf16_gemm: A [M, K] bf16, B [N, K] bf16 (K-major) -> A B^T (+ bias) in float32 on tcgen05.
+    split_k gives the call its binary64 work buffer (ssa_bf16_gemm_work_words), so that products with few
+    output tiles split K across the SMs."""
     if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16:
         raise SSAError("bf16_gemm takes bfloat16 operands")
     M, K = A.shape
@@ -449,8 +452,11 @@ def bf16_gemm(A: torch.Tensor, B: torch.Tensor, bias: torch.Tensor | None = None
     D = torch.empty((M, N), dtype=torch.float32, device=A.device)
     err = torch.zeros(1, dtype=torch.int32, device=A.device)
     b = None if bias is None else bias.to(torch.float32).contiguous()
-    check(_lib.lib().ssa_bf16_gemm(_ptr(Ap), _ptr(Bp), M, N, K, ld, ld, _ptr(b), _ptr(D), N, _ptr(err),
-                                   _stream(stream)))
+    L = _lib.lib()
+    words = int(L.ssa_bf16_gemm_work_words(M, N, K)) if split_k else 0
+    work = torch.empty(max(words, 1), dtype=torch.float64, device=A.device) if words else None
+    check(L.ssa_bf16_gemm(_ptr(Ap), _ptr(Bp), M, N, K, ld, ld, _ptr(b), _ptr(D), N, _ptr(work), words, _ptr(err),
+                          _stream(stream)))
     if int(err.item()) != 0:
         raise SSAError("tensor-core GEMM timed out waiting for its copies")
     return D
