@@ -10,8 +10,8 @@
 // The dense contraction E1 = W1 x runs on the tcgen05 tensor cores, once per image. W1 (bf16) is
 // split into 6-bit limbs on a common power-of-two grid; with integer counts x <= 255 every partial
 // sum of one limb is an integer multiple of the limb's quantum below 2^24 quanta, so the binary32
-// accumulation in TMEM is exact, and the binary64 sum of the limbs reproduces W1 x exactly before
-// one final rounding. E2 = W2 h is kept exactly as an int64 fixed-point sum (bf16 W2 on its own
+// accumulation in TMEM is exact; the epilogue turns each accumulator into that integer and adds the limbs
+// in int64 (two 42-bit halves), which is W1 x exactly, rounded once to binary64 before b1 is added. E2 = W2 h is kept exactly as an int64 fixed-point sum (bf16 W2 on its own
 // grid times integer counts), updated by +-W2[:, i] when h_i changes.
 //
 // The SSA and the straight-through adjoint run one warp per trajectory (lanes own Philox blocks as
@@ -186,7 +186,10 @@ __global__ void grn_prepare_kernel(const uint16_t *W1, const uint16_t *W2, const
         q -= n_img * n_in_pad;
         dvec[q] = (float)exp((double)log_d[q]);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) grid[3] = g2;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        grid[3] = g2;
+        grid[4] = g1;  // the limb grid of the tensor-core contraction's exact sum
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -203,8 +206,9 @@ __global__ void __launch_bounds__(128) grn_fwd_kernel(const GrnParams p, int rec
     const int ndp = (nd + 3) & ~3, nhp = (nh + 3) & ~3;
     const int nop = (no + 3) & ~3;
     const size_t per_warp = (size_t)ndp + nhp + 3 * (size_t)nop;  // X, aH, E2acc (2 words each), aO
-    unsigned char *wb = smem + 4 * ((size_t)no * nh + nd + ((no + 3) & ~3));
-    wb = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(wb) + 15) & ~(uintptr_t)15);
+    // offsets from the shared array itself (not through an integer round trip), so that every access below
+    // compiles to a shared-memory load or store with 32-bit addressing
+    unsigned char *wb = smem + ((4 * ((size_t)no * nh + nd + ((no + 3) & ~3)) + 15) & ~(size_t)15);
     int *X = reinterpret_cast<int *>(wb) + wib * per_warp;
     float *aH = reinterpret_cast<float *>(X + ndp);
     long long *E2acc = reinterpret_cast<long long *>(aH + nhp);
@@ -683,8 +687,7 @@ __global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
     // aj, lj [Mp each], dlogd [ndp]. dL/dW2 goes to the trajectory's own row of p.dW2t (global, L2-resident
     // while the warp works on it), which keeps the per-warp shared memory independent of n_out x n_hid.
     const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + 6 * (size_t)nop + 2 * (size_t)Mp;
-    unsigned char *wb = smem + 4 * ((size_t)nd + nop);
-    wb = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(wb) + 15) & ~(uintptr_t)15);
+    unsigned char *wb = smem + ((4 * ((size_t)nd + nop) + 15) & ~(size_t)15);  // shared-space offsets (see the forward)
     float *wbase = reinterpret_cast<float *>(wb) + wib * per_warp;
     int *X = reinterpret_cast<int *>(wbase);
     float *lam = wbase + ndp;
@@ -718,6 +721,7 @@ __global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
         for (int q = lane; q < no * nh; q += 32) dW2[q] = 0.0f;
     if (active) {
         const float scale = exp2f((float)p.grid[0]);
+        const float inv_kmax = 1.0f / p.k_max;
         const float *E1 = p.E1 + (i / p.tpi) * nh;
         const int d = p.draws[i];
         const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;
@@ -793,52 +797,55 @@ __global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
                 const float lmax = warp_max(lmaxp);
                 mism += (jb != jk);
                 __syncwarp();
-                // pass 2: soft-sample weights; w_j = +lam_s (production) or -lam_s (degradation)
+                // pass 2: soft-sample weights q_j = exp2((l_j - l_max)/T), Z = sum q, W = sum q w with
+                // w_j = +lam_s (production of s) or -lam_s (degradation of s); one loop per reaction range, so
+                // neither pass branches on the kind of reaction
                 float Zp = 0.0f, Wp = 0.0f;
-                for (int b = lane; b < p.nb; b += 32) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = 4 * b + q - 1;
-                        if (j < 0 || j >= p.M) continue;
-                        const float qv = lj[j] == -CUDART_INF_F ? 0.0f : exp2f((lj[j] - lmax) * invT);
-                        lj[j] = qv;
-                        const float w = j < nd ? lam[j] : -lam[j - nd];
-                        Zp += qv;
-                        Wp += qv * w;
-                    }
+                for (int j = lane; j < nd; j += 32) {
+                    const float l = lj[j];
+                    const float qv = l > -CUDART_INF_F ? exp2f((l - lmax) * invT) : 0.0f;
+                    lj[j] = qv;
+                    Zp += qv;
+                    Wp = fmaf(qv, lam[j], Wp);
+                }
+                for (int s2 = lane; s2 < nd; s2 += 32) {
+                    const float l = lj[nd + s2];
+                    const float qv = l > -CUDART_INF_F ? exp2f((l - lmax) * invT) : 0.0f;
+                    lj[nd + s2] = qv;
+                    Zp += qv;
+                    Wp = fmaf(-qv, lam[s2], Wp);
                 }
                 const float Z = warp_sum(Zp), Wq = warp_sum(Wp);
                 const float invZ = __fdividef(1.0f, Z), Wbar = Wq * invZ;
-                // pass 3: choice-path adjoints per reaction (HOLD readout: no waiting-time path)
-                for (int b = lane; b < p.nb; b += 32) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = 4 * b + q - 1;
-                        if (j < 0 || j >= p.M) continue;
-                        const float w = j < nd ? lam[j] : -lam[j - nd];
-                        const float psi = lj[j] > 0.0f ? lj[j] * invZ * (w - Wbar) * invT : 0.0f;
-                        if (j < nh) {
-                            G1[j] += psi * (1.0f - __fdividef(aH[j], p.k_max));
-                        } else if (j < nd) {
-                            G2[j - nh] = psi * (1.0f - __fdividef(aO[j - nh], p.k_max));
-                        } else {
-                            const int s = j - nd;
-                            dlogd[s] += psi;
-                            ctd[s] = aj[j] > 0.0f ? __fdividef(psi, int2f(X[s])) : 0.0f;
-                        }
-                    }
+                const float cz = invZ * invT;
+                // pass 3: choice-path adjoints psi_j = q_j / Z (w_j - W/Z) / T per reaction (HOLD readout: no
+                // waiting-time path); d log(k_max sigma(E)) / dE = 1 - sigma(E)
+                for (int h = lane; h < nh; h += 32) {
+                    const float psi = lj[h] * cz * (lam[h] - Wbar);
+                    G1[h] = fmaf(psi, 1.0f - aH[h] * inv_kmax, G1[h]);
+                }
+                for (int o = lane; o < no; o += 32) {
+                    const float psi = lj[nh + o] * cz * (lam[nh + o] - Wbar);
+                    G2[o] = psi * (1.0f - aO[o] * inv_kmax);
+                }
+                for (int s2 = lane; s2 < nd; s2 += 32) {
+                    const float psi = lj[nd + s2] * cz * (-lam[s2] - Wbar);
+                    dlogd[s2] += psi;
+                    ctd[s2] = aj[nd + s2] > 0.0f ? __fdividef(psi, int2f(X[s2])) : 0.0f;
                 }
                 __syncwarp();
                 for (int o = lane; o < no; o += 32) {
                     db2[o] += G2[o];
                     R[o] += G2[o];
                 }
-                for (int s = lane; s < nd; s += 32) {
-                    float acc = ctd[s];
-                    if (s < nh)
-                        for (int o = 0; o < no; ++o) acc += __ldg(W2f + o * nh + s) * G2[o];
-                    lam[s] += acc;
+                // lam_h += (W2^T G2)_h for the hidden genes; every species adds its degradation term
+                for (int h = lane; h < nh; h += 32) {
+                    float acc = ctd[h];
+#pragma unroll 2
+                    for (int o = 0; o < no; ++o) acc = fmaf(__ldg(W2f + o * nh + h), G2[o], acc);
+                    lam[h] += acc;
                 }
+                for (int s2 = nh + lane; s2 < nd; s2 += 32) lam[s2] += ctd[s2];
             }
             __syncwarp();
             // HOLD samples of the outputs at state k
@@ -977,7 +984,7 @@ WsLayout grn_layout(const ssa_grn *g, int64_t n_img, int64_t tpi, int32_t S, con
     L.dvec = take((size_t)g->n_dyn * 4);
     L.grid = take(16 * sizeof(int));
     // split-K partial sums of E1 (forward) and of dW1 (backward), when the product fills too few SMs
-    size_t tc_words = n_img > 0 ? tc_split_words((int)n_img, g->n_hid, g->n_in, 64) : 0;
+    size_t tc_words = n_img > 0 ? 2 * tc_split_words((int)n_img, g->n_hid, g->n_in, 64) : 0;  // (lo, hi) pairs
     if (o->record && n_img > 0)
         tc_words = std::max(tc_words, tc_split_words(g->n_hid, g->n_in, (int)n_img, grn_dw1_nt(g)));
     L.tcpart = take(std::max<size_t>(tc_words, 1) * sizeof(double));
@@ -1139,6 +1146,8 @@ extern "C" ssa_status ssa_grn_forward(const ssa_grn *g, const uint16_t *W1, cons
         TcArgs args{(int)n_img, g->n_hid, g->n_in, 1, kGrnLimbs, kGrnLimbs, 1, b1,
                     reinterpret_cast<float *>(ws + L.E1), g->n_hid, flag + 4};
         args.Dpart = reinterpret_cast<double *>(ws + L.tcpart);  // split K when the tiles underfill the SMs
+        args.limb_grid = grid + 4;  // limb t is an integer multiple of 2^(g1 + 6 t): summed exactly in int64
+        args.limb_bits = kGrnLimbBits;
         GRN_CUDA_TRY(tc_gemm_launch(maps, args, 64, st));
     }
     GrnParams p{};

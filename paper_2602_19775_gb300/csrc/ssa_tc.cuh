@@ -29,6 +29,13 @@ struct TcArgs {
     // splits in order and the bias
     double *Dpart;          // nullptr: one pass over K per tile
     int k_split, chunks_per;
+    // exact limb sum (separate accumulators, n_terms = 8): term t is T_t 2^(g + limb_bits t) with T_t an
+    // integer below 2^24 in magnitude and g = *limb_grid. The epilogue converts each term to T_t and adds
+    // lo = sum_{t<4} T_t 2^(limb_bits t) and hi = sum_{t>=4} T_t 2^(limb_bits (t-4)) in int64 (exact), and
+    // D = (hi 2^(4 limb_bits) + lo) 2^g + bias, rounded once to binary64 and then to binary32. With a split,
+    // Dpart holds the (lo, hi) pairs of each split as int64 [k_split][M][N][2], added exactly.
+    const int *limb_grid;   // nullptr: binary64 sum of the accumulators
+    int limb_bits;
 };
 
 bool tc_make_map(CUtensorMap *map, const void *base, int rows, int K, int ld, int box_rows);
@@ -36,6 +43,6 @@ cudaError_t tc_gemm_launch(const TcMaps &maps, const TcArgs &args, int nt, cudaS
 // K splits tc_gemm_launch uses for an M x N x K product with N-tiles of nt (1: no split), and the binary64
 // words of its Dpart buffer
 int tc_split_count(int M, int N, int K, int nt);
-size_t tc_split_words(int M, int N, int K, int nt);
+size_t tc_split_words(int M, int N, int K, int nt);  // the exact limb sum takes twice as many
 
 }  // namespace ssa

@@ -89,6 +89,24 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 2^e as a binary64 power of two for |e| <= 1022 (its exponent field): an exact scale
+__device__ __forceinline__ double pow2_d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
 }  // namespace
 
 template <int NT>
@@ -180,7 +198,53 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (*s_ok) {
+    if (*s_ok && args.limb_grid) {
+        // exact limb sum: each accumulator to its integer T_t (a power-of-two scale, then an exact conversion),
+        // combined in int64; the split slabs keep the (lo, hi) pairs, otherwise one rounding to binary64.
+        // Sixteen columns per tensor-memory load, so a warp waits on 8 terms x NT/16 loads.
+        const int row = m0 + 32 * warp + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+        const int g = *args.limb_grid, lb = args.limb_bits;
+        for (int c16 = 0; c16 < NT / 16; ++c16) {
+            long long lo[16], hi[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) lo[i] = hi[i] = 0;
+            for (int t = 0; t < args.n_terms; ++t) {
+                float v[16];
+                tmem_ld16(lane_base + (uint32_t)(t * NT + 16 * c16), v);
+                // 2^-(g + lb t) as two binary32 powers of two (exponent fields), each inside the normal range for
+                // any grid a bf16 limb can sit on; both products are exact
+                const int e = -(g + lb * t), e1 = e >> 1, e2 = e - e1;
+                const float q1 = __int_as_float((127 + e1) << 23), q2 = __int_as_float((127 + e2) << 23);
+                const long long w = 1ll << (lb * (t & 3));
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const long long T = (long long)__float2int_rn((v[i] * q1) * q2);
+                    if (t < 4) lo[i] += T * w;
+                    else hi[i] += T * w;
+                }
+            }
+            if (row < args.M) {
+                // (hi 2^(4 lb) + lo) 2^g: both terms exact in binary64 (below 2^43 in magnitude), one rounding
+                const double sh = pow2_d(4 * lb + g), sl = pow2_d(g);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = n0 + 16 * c16 + i;
+                    if (col < args.N) {
+                        if (args.k_split > 1) {
+                            longlong2 *dp = reinterpret_cast<longlong2 *>(args.Dpart) +
+                                            ((int64_t)blockIdx.z * args.M + row) * args.N + col;
+                            *dp = make_longlong2(lo[i], hi[i]);
+                        } else {
+                            const double x = fma((double)hi[i], sh, (double)lo[i] * sl);
+                            const double b = args.bias ? (double)args.bias[col] : 0.0;
+                            args.D[(int64_t)row * args.ldd + col] = (float)(x + b);
+                        }
+                    }
+                }
+            }
+        }
+    } else if (*s_ok) {
         const int row = m0 + 32 * warp + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
         for (int c8 = 0; c8 < NT / 8; ++c8) {
@@ -248,20 +312,6 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void *p)
     return d;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // split K: with Dpart given, the CTAs of blockIdx.z = s take the 64-wide K blocks [s per, (s + 1) per) and
 // write their sums in binary64 to Dpart [gridDim.z][M][N] (no bias); tc_splitk_reduce_kernel adds them
@@ -454,6 +504,24 @@ __global__ void tc_splitk_reduce_kernel(const double *Dpart, int k_split, int M,
     D[(int64_t)m * ldd + n] = (float)(acc + (bias ? (double)bias[n] : 0.0));
 }
 
+// the same for the exact limb sum: int64 (lo, hi) pairs of every split, added exactly in split order
+__global__ void tc_splitk_reduce_limbs_kernel(const longlong2 *Dpart, int k_split, int M, int N, const int *limb_grid,
+                                             int limb_bits, const float *bias, float *D, int ldd)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * N) return;
+    const int m = (int)(e / N), n = (int)(e % N);
+    long long lo = 0, hi = 0;
+    for (int s = 0; s < k_split; ++s) {
+        const longlong2 v = Dpart[(int64_t)s * M * N + e];
+        lo += v.x;
+        hi += v.y;
+    }
+    const int g = *limb_grid;
+    const double x = fma((double)hi, pow2_d(4 * limb_bits + g), (double)lo * pow2_d(g));
+    D[(int64_t)m * ldd + n] = (float)(x + (bias ? (double)bias[n] : 0.0));
+}
+
 int tc_split_count(int M, int N, int K, int nt)
 {
     const int64_t tiles = (int64_t)((M + 127) / 128) * ((N + nt - 1) / nt);
@@ -543,8 +611,13 @@ static cudaError_t tc_launch_t(const TcMaps &maps, const TcArgs &args_in, cudaSt
     tc_gemm_kernel<NT><<<grid, 128, smem, st>>>(maps, args);
     if (args.k_split > 1) {
         const int64_t total = (int64_t)args.M * args.N;
-        tc_splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(args.Dpart, args.k_split, args.M, args.N,
-                                                                                 args.bias, args.D, args.ldd);
+        if (args.limb_grid)
+            tc_splitk_reduce_limbs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+                reinterpret_cast<const longlong2 *>(args.Dpart), args.k_split, args.M, args.N, args.limb_grid,
+                args.limb_bits, args.bias, args.D, args.ldd);
+        else
+            tc_splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(args.Dpart, args.k_split, args.M,
+                                                                                     args.N, args.bias, args.D, args.ldd);
     }
     return cudaGetLastError();
 }

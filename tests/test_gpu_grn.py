@@ -21,13 +21,16 @@ def S():
     return ssa
 
 
-def test_activation_energies_are_exact_on_tensor_cores(S):
+@pytest.mark.parametrize("n_img", [512, 40, 5000])
+def test_activation_energies_are_exact_on_tensor_cores(S, n_img):
+    """512 images: 16 output tiles, K split 7 ways (int64 limb pairs added across the splits); 40: one tile row;
+    5,000: 160 tiles, no split (the limb sum in the GEMM's own epilogue)."""
     p = G.grn_params(seed=5)
     p.b1[:] = np.random.default_rng(1).normal(0, 0.5, p.n_hid).astype(np.float32)
-    x, _ = G.prototype_images(seed=5, n_img=512)
+    x, _ = G.prototype_images(seed=5, n_img=n_img)
     net = S.GRN(p.n_in, p.n_hid, p.n_out, p.k_max)
     fw = S.grn_forward(net, p.W1, p.b1, p.W2, p.b2, p.log_d, x, 1, 0.0, [0.0], 3, record=False)
-    E1, flags = S.grn_activations(fw, 512)
+    E1, flags = S.grn_activations(fw, n_img)
     assert flags == (0, 0), flags
     # W1 x is exact in binary64 (bf16 weights times 8-bit counts on one grid); one rounding of (W1 x + b1)
     exact = x.astype(np.float64) @ p.W1.astype(np.float64).T + p.b1.astype(np.float64)
