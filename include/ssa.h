@@ -82,8 +82,10 @@ typedef struct ssa_fwd_opts {
                                  1: always the generic kernels                                  */
     int32_t selector;         /* SSA_SELECT_GUMBEL (the method), SSA_SELECT_DIRECT (the plain
                                  direct method, forward only: record must be 0) or
-                                 SSA_SELECT_SOFT (the relaxed forward of Eq. 4); the last two run
-                                 on the network-specialised kernels only                        */
+                                 SSA_SELECT_SOFT (the relaxed forward of Eq. 4). The direct
+                                 method runs on the network-specialised kernels only; the soft
+                                 forward on them where the network qualifies, otherwise on the
+                                 warp-per-trajectory kernels, without recording there         */
     float temperature;        /* SSA_SELECT_SOFT: T > 0 of its soft sample; else must be 0       */
 } ssa_fwd_opts;
 
@@ -96,7 +98,11 @@ typedef struct ssa_fwd_opts {
  * clock, the samples and the three readouts are the forward's; observables are float for every
  * readout. Recorded, it checkpoints the float state every 8 steps (ckpt_interval is ignored), and
  * ssa_backward then gives the exact gradient of this relaxed model (it re-runs each 8-step segment,
- * so its temperature argument must equal opts.temperature). No event log is kept. */
+ * so its temperature argument must equal opts.temperature). No event log is kept. Networks beyond the
+ * specialised kernels' limits (or threads_per_traj = 32, or no_specialize) run the soft forward one warp
+ * per trajectory: every species sums its changes in increasing reaction order as the specialised kernels
+ * do, a0 and the normaliser are warp sums (so the results agree with the specialised kernels to binary32
+ * rounding, not bit for bit); recording there returns SSA_ERR_UNSUPPORTED. */
 #define SSA_SELECT_SOFT 2
 
 /*

@@ -34,6 +34,7 @@ cudaError_t launch_backward_thread(const AdjParams &p, int readout, int block, s
 cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, const int *rate_index, int P,
                                    float *dA_tmp, float *dtheta, cudaStream_t st);
 cudaError_t launch_forward_warp(const FwdParams &p, int readout, bool record, int warps, size_t smem, cudaStream_t st);
+cudaError_t launch_forward_warp_soft(const FwdParams &p, int readout, int warps, size_t smem, cudaStream_t st);
 cudaError_t launch_backward_warp(const AdjParams &p, int readout, int warps, size_t smem, int64_t grid,
                                  cudaStream_t st);
 int thread_kernel_mc(int M);
@@ -187,6 +188,13 @@ size_t fwd_warp_smem(const ssa_network *net)
 {
     return net->tab_bytes + (size_t)net->Mp * 4 + 16 + (size_t)kWarpsPerBlock * ((net->N + 3) & ~3) * 4;
 }
+// the soft forward on the warp layout: tables, rates, the update list, and per warp X, dX [Npad] and y [Mp]
+size_t fwd_warp_soft_smem(const ssa_network *net)
+{
+    return net->tab_bytes + (size_t)net->Mp * 4 + 16 + (size_t)net->upd_words * 4 +
+           (size_t)kWarpsPerBlock * (2 * ((net->N + 3) & ~3) + (size_t)net->Mp) * 4;
+}
+
 size_t adj_warp_smem(const ssa_network *net)
 {
     return net->tab_bytes + (size_t)net->Mp * 4 + 16 +
@@ -270,6 +278,21 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
         }
         inc_ptr[sp + 1] = (int)inc_list.size();
     }
+    // species -> (lane-major position of j, delta) over the reactions that change it, in increasing j
+    const int nb_warp = (n_reactions + 4) >> 2;
+    std::vector<std::vector<int>> upd_by_species(n_species);
+    for (int j = 0; j < n_reactions; ++j)
+        for (int e = stoich_ptr[j]; e < stoich_ptr[j + 1]; ++e)
+            upd_by_species[stoich_species[e]].push_back((((j + 1) & 3) * nb_warp + ((j + 1) >> 2)) << 8 |
+                                                        (stoich_delta[e] & 0xff));
+    const int upd_ptr_pad = (n_species + 1 + 3) / 4 * 4;
+    std::vector<int> upd(upd_ptr_pad, 0);
+    for (int sp = 0; sp < n_species; ++sp) {
+        upd.insert(upd.end(), upd_by_species[sp].begin(), upd_by_species[sp].end());
+        upd[sp + 1] = (int)upd.size() - upd_ptr_pad;
+    }
+    for (int sp = n_species + 1; sp < upd_ptr_pad; ++sp) upd[sp] = upd[n_species];
+    upd.resize((upd.size() + 3) / 4 * 4, 0);
     const int inc_ptr_pad = (n_species + 1 + 3) / 4 * 4;
     const int inc_list_pad = ((int)inc_list.size() + 3) / 4 * 4;
     inc_ptr.resize(inc_ptr_pad, inc_ptr[n_species]);
@@ -287,7 +310,9 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
     net->inc_list_off = net->inc_off + (uint32_t)(4 * inc_ptr_pad);
     net->tab_bytes = net->inc_list_off + (uint32_t)(4 * inc_list_pad);
     // blob = [tables][rate_index: int Mp][tables again, with rx in the warp kernels' lane-major order]
-    const size_t bytes = 2 * (size_t)net->tab_bytes + (size_t)Mp * 4;
+    //        [species-major update list of the warp soft forward]
+    net->upd_words = (uint32_t)upd.size();
+    const size_t bytes = 2 * (size_t)net->tab_bytes + (size_t)Mp * 4 + 4 * (size_t)net->upd_words;
     cudaError_t e = cudaMalloc(&net->d_blob, bytes);
     if (e != cudaSuccess) {
         delete net;
@@ -308,6 +333,8 @@ extern "C" ssa_status ssa_create_network(int32_t n_species, int32_t n_reactions,
         e = cudaMemcpy(b + net->inc_list_off, inc_list.data(), 4 * (size_t)inc_list_pad, cudaMemcpyHostToDevice);
     net->d_rx_warp = reinterpret_cast<int4 *>(b + net->tab_bytes + (size_t)Mp * 4);
     if (e == cudaSuccess) e = cudaMemcpy(net->d_rx_warp, net->d_rx, net->tab_bytes, cudaMemcpyDeviceToDevice);
+    net->d_upd = reinterpret_cast<int *>(b + 2 * (size_t)net->tab_bytes + (size_t)Mp * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(net->d_upd, upd.data(), 4 * (size_t)net->upd_words, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         const int nb = (n_reactions + 4) >> 2;
         std::vector<int4> rxp(Mp, make_int4(-1, -1, 0, 0));
@@ -363,13 +390,22 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     int variant = ev_in ? 1 : pick_variant(net, opts);  // replay is a thread-per-trajectory test hook
     // the thread variant runs as network-specialised kernels when the network qualifies (variant 2)
     const JitKernels *jit = nullptr;
-    if (opts->selector == SSA_SELECT_SOFT) {  // the soft forward exists as specialised kernels only
-        if (variant != 1 || ev_in || opts->no_specialize)
-            return fail(SSA_ERR_UNSUPPORTED, "the soft forward runs on the network-specialised thread kernels only");
-        std::string why;
-        jit = jit_soft_kernels(net, why);
-        if (!jit) return fail(SSA_ERR_UNSUPPORTED, "soft forward unavailable: %s", why.c_str());
-        variant = 2;
+    if (opts->selector == SSA_SELECT_SOFT) {
+        // the network-specialised thread kernels (forward and gradient) where the network qualifies, else the
+        // warp kernels (forward only)
+        if (ev_in) return fail(SSA_ERR_UNSUPPORTED, "the soft forward has no replay mode");
+        std::string why = "the network is not eligible (N, M <= 24, at most 96 stoichiometric entries)";
+        if (variant == 1 && !opts->no_specialize && jit_eligible(net)) {
+            jit = jit_soft_kernels(net, why);
+            if (jit) variant = 2;
+        }
+        if (variant == 1 && opts->threads_per_traj == 1)
+            return fail(SSA_ERR_UNSUPPORTED, "the soft forward with one thread per trajectory needs the "
+                        "network-specialised kernels: %s", why.c_str());
+        if (variant == 1) variant = 32;
+        if (variant == 32 && opts->record)
+            return fail(SSA_ERR_UNSUPPORTED, "the soft forward's gradient runs on the network-specialised thread "
+                        "kernels (N, M <= 24); the warp kernels run the soft forward without recording");
     } else if (variant == 1 && !ev_in && !opts->no_specialize && jit_eligible(net)) {
         std::string why;
         jit = jit_kernels(net, why);
@@ -387,6 +423,9 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
         if (!block) return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory forward");
         if (opts->record && !pick_block(adj_smem, net, 0, limit))
             return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory adjoint");
+    } else if (opts->selector == SSA_SELECT_SOFT) {
+        if (fwd_warp_soft_smem(net) > limit)
+            return fail(SSA_ERR_UNSUPPORTED, "network too large for the warp-per-trajectory soft forward");
     } else {
         if (fwd_warp_smem(net) > limit || (opts->record && adj_warp_smem(net) > limit))
             return fail(SSA_ERR_UNSUPPORTED, "network too large for the warp-per-trajectory kernels");
@@ -427,6 +466,8 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     p.n_obs = n_obs;
     p.max_steps = opts->max_steps;
     p.invT = opts->selector == SSA_SELECT_SOFT ? 1.0f / opts->temperature : 0.0f;
+    p.upd = net->d_upd;
+    p.upd_words = net->upd_words;
     p.obs_out = obs_out;
     p.draws = reinterpret_cast<int *>(ws + L.draws);
     p.status = reinterpret_cast<int *>(ws + L.status);
@@ -449,6 +490,8 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
         CUDA_TRY(jit_launch_forward(jit, p, opts->readout, opts->record != 0, opts->selector, block, st));
     else if (variant == 1)
         CUDA_TRY(launch_forward_thread(p, opts->readout, opts->record != 0, ev_in != nullptr, block, fwd_smem(net, block), st));
+    else if (opts->selector == SSA_SELECT_SOFT)
+        CUDA_TRY(launch_forward_warp_soft(p, opts->readout, kWarpsPerBlock, fwd_warp_soft_smem(net), st));
     else
         CUDA_TRY(launch_forward_warp(p, opts->readout, opts->record != 0, kWarpsPerBlock, fwd_warp_smem(net), st));
     if (n_traj > 0 && draws_out) CUDA_TRY(cudaMemcpyAsync(draws_out, p.draws, (size_t)n_traj * 4, cudaMemcpyDeviceToDevice, st));

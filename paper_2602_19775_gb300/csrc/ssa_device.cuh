@@ -414,6 +414,8 @@ struct FwdParams {
     int n_obs;
     int64_t max_steps;
     float invT;       // soft forward (Eq. 4): 1/T of its soft sample
+    const int *upd;   // warp soft forward: species-major update list (ssa_network::d_upd), upd_words ints
+    uint32_t upd_words;
     void *obs_out;
     int *draws, *status;
     const int *flag;  // workspace error flags (bad sample times -> every trajectory BAD_INPUT)

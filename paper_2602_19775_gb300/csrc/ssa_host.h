@@ -17,6 +17,10 @@ struct ssa_network {
     uint32_t inc_off, inc_list_off;
     int4 *d_rx;
     int4 *d_rx_warp;  // the same tables with rx in lane-major order (jpos), for the warp kernels
+    // species -> the stoichiometric changes it receives, for the relaxed update of the warp soft forward:
+    // [upd_ptr: int N+1, padded to 4][upd_list: (jpos(j) << 8) | (delta & 0xff), reactions in increasing j]
+    int *d_upd;
+    uint32_t upd_words;
     int *d_stoich;
     int *d_rate_index;
     uint32_t tab_bytes;

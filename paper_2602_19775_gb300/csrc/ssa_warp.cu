@@ -43,6 +43,29 @@ __global__ void __launch_bounds__(256) fwd_warp_kernel(const FwdParams p)
     warp_fwd_body<READOUT, RECORD>(p, s_rx, s_st, s_k, X, i);
 }
 
+// The soft forward (Eq. 4) on the warp layout: the staged tables and rates, then the species-major update
+// list; per warp X [Npad], dX [Npad] (floats) and the keys / weights y [Mp].
+template <int READOUT>
+__global__ void __launch_bounds__(256) fwd_warp_soft_kernel(const FwdParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int wib = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int Npad = (p.N + 3) & ~3;
+    int4 *s_rx = reinterpret_cast<int4 *>(smem);
+    float *s_k = reinterpret_cast<float *>(smem + p.tab_bytes);
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + p.tab_bytes + p.k_bytes);
+    int *s_ok = reinterpret_cast<int *>(smem + p.tab_bytes + p.k_bytes + 8);
+    int *s_upd = reinterpret_cast<int *>(smem + p.tab_bytes + p.k_bytes + 16);
+    float *wbase = reinterpret_cast<float *>(s_upd + p.upd_words) + wib * (2 * Npad + p.Mp);
+
+    if (!stage_tables(smem, p.rx, p.tab_bytes, s_k, p.k_rates, p.k_bytes, s_bar, s_ok, p.err)) return;
+    for (uint32_t q = threadIdx.x; q < p.upd_words; q += blockDim.x) s_upd[q] = p.upd[q];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * W + wib;
+    if (i >= p.n_traj) return;  // whole warp
+    warp_soft_fwd_body<READOUT>(p, s_rx, s_k, s_upd, wbase, wbase + Npad, wbase + 2 * Npad, i);
+}
+
 template <int READOUT>
 __global__ void __launch_bounds__(256) adj_warp_kernel(const AdjParams p)
 {
@@ -111,6 +134,25 @@ cudaError_t launch_forward_warp(const FwdParams &p, int readout, bool record, in
     if (readout == SSA_READOUT_BIN)
         return record ? launch_fwd_w<2, true>(p, warps, smem, st) : launch_fwd_w<2, false>(p, warps, smem, st);
     return record ? launch_fwd_w<1, true>(p, warps, smem, st) : launch_fwd_w<1, false>(p, warps, smem, st);
+}
+
+template <int R>
+static cudaError_t launch_fwd_soft_w(const FwdParams &p, int warps, size_t smem, cudaStream_t st)
+{
+    auto kern = fwd_warp_soft_kernel<R>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = (p.n_traj + warps - 1) / warps;
+    kern<<<(unsigned)grid, warps * 32, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_warp_soft(const FwdParams &p, int readout, int warps, size_t smem, cudaStream_t st)
+{
+    if (p.n_traj == 0) return cudaSuccess;
+    if (readout == SSA_READOUT_HOLD) return launch_fwd_soft_w<0>(p, warps, smem, st);
+    if (readout == SSA_READOUT_BIN) return launch_fwd_soft_w<2>(p, warps, smem, st);
+    return launch_fwd_soft_w<1>(p, warps, smem, st);
 }
 
 template <int R>

@@ -305,6 +305,161 @@ __device__ __forceinline__ void warp_fwd_body(const FwdParams &p, const int4 *s_
     }
 }
 
+// Per-trajectory body of the warp soft forward (Section 3.3, Eq. 4), forward only: the state X is real and
+// moves every step by the expected change sum_j y~_j v_j of the soft sample y~ = softmax((log a + G)/T), with
+// the variates of the Gumbel-max forward. Per step, lane l evaluates the reactions of its Philox blocks (the
+// relaxed propensities, negative factors clipped at 0, and the keys log2 a_j - log2 E_j, kept in y by
+// lane-major position), the warp reduces a0 and the largest key, the lanes turn their keys into weights, and
+// each species sums its own changes through the species-major update list in increasing j (no atomics: the
+// same order as the specialised thread kernels' update). Clock, samples and readouts are the forward's.
+template <int READOUT>
+__device__ __forceinline__ void warp_soft_fwd_body(const FwdParams &p, const int4 *s_rx, const float *s_k,
+                                                   const int *s_upd, float *X, float *dX, float *y, const int64_t i)
+{
+    const int lane = threadIdx.x & 31;
+    const int N = p.N, M = p.M, nb = (M + 4) >> 2;
+    const int64_t n = p.n_traj;
+    const int upd_base = (N + 1 + 3) & ~3;  // the list follows the padded pointer array
+    const int *x0 = p.x0 + (p.x0_per_traj ? i * N : 0);
+    const bool bad_obs = (*p.flag & kErrBadObs) != 0;
+    bool neg = false;
+    for (int sp = lane; sp < N; sp += 32) {
+        X[sp] = int2f(x0[sp]);
+        neg |= x0[sp] < 0;
+    }
+    const bool bad_input = __any_sync(0xffffffffu, neg) || (*p.flag & (kErrBadSamples | kErrBadObs)) != 0;
+    __syncwarp();
+    const uint64_t gid = p.traj_offset + (uint64_t)i;
+    const uint32_t c2 = (uint32_t)gid, c3 = (uint32_t)(gid >> 32), key0 = (uint32_t)p.seed,
+                   key1 = (uint32_t)(p.seed >> 32);
+    double t = 0.0;
+    int s = 0;
+    double thr = p.S > 0 ? p.ts[0] : p.t_end;
+    int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
+    int k = 0, draws = 0;
+    constexpr bool kBin = READOUT == SSA_READOUT_BIN;
+    float bacc[kBinMaxObs];
+    int osp[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) {
+        bacc[c] = 0.0f;
+        osp[c] = (kBin && c < p.n_obs && !bad_obs) ? p.obs_sp[c] : 0;
+    }
+    auto xobs = [&](int c) { return X[osp[c]]; };
+    int slots = 0;
+    float *obs = static_cast<float *>(p.obs_out);
+
+    while (!bad_input) {
+        if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
+        // relaxed propensities and keys of this lane's reactions
+        float a0p = 0.0f, lmaxp = -CUDART_INF_F, E0 = 0.0f;
+        for (int b = lane; b < nb; b += 32) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * b + q - 1;
+                const float E = neg_log_unit(u01(word_of(r, q)));
+                if (j < 0) {
+                    E0 = E;
+                    continue;
+                }
+                const int pos = q * nb + b;
+                const int4 rx = s_rx[pos];
+                float h = 1.0f;
+                if (rx.x >= 0) {
+                    const float x1 = X[rx.x];
+                    h = rx.y < 0 ? hs_first(x1) : rx.y == rx.x ? hs_homodimer(x1) : hs_hetero(x1, X[rx.y]);
+                }
+                const float a = __fmul_rn(s_k[pos], h);
+                a0p = __fadd_rn(a0p, a);
+                const float l = a > 0.0f ? log2f(a) - log2f(E) : -CUDART_INF_F;
+                if (j < M) y[pos] = l;
+                lmaxp = fmaxf(lmaxp, l);
+            }
+        }
+        const float a0 = warp_sum(a0p), lmax = warp_max(lmaxp);
+        E0 = __shfl_sync(0xffffffffu, E0, 0);
+        if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
+        if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
+        // weights exp2((l_j - l_max)/T) and their sum
+        float Zp = 0.0f;
+        for (int b = lane; b < nb; b += 32) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * b + q - 1;
+                if (j < 0 || j >= M) continue;
+                const int pos = q * nb + b;
+                const float l = y[pos];
+                const float w = l == -CUDART_INF_F ? 0.0f : exp2f((l - lmax) * p.invT);
+                y[pos] = w;
+                Zp += w;
+            }
+        }
+        const float invZ = __fdividef(1.0f, warp_sum(Zp));
+        __syncwarp();
+        // dX_s = sum over the reactions changing s, in increasing j, of y~_j v_js
+        bool fin = true;
+        for (int sp = lane; sp < N; sp += 32) {
+            float d = 0.0f;
+            for (int e = s_upd[sp]; e < s_upd[sp + 1]; ++e) {
+                const int ent = s_upd[upd_base + e];
+                d = __fmaf_rn(y[ent >> 8] * invZ, (float)(int)(signed char)(ent & 0xff), d);
+            }
+            dX[sp] = d;
+            fin &= fabsf(__fadd_rn(X[sp], d)) < CUDART_INF_F;
+        }
+        const bool finite = __all_sync(0xffffffffu, fin);
+        __syncwarp();
+        const float tau = waiting_time(E0, a0);
+        const double t_next = t + f2d_pos(tau);
+        const bool slow = gt_nonneg(t_next, thr);
+        const bool cross = slow && gt_nonneg(t_next, p.t_end);
+        draws = k + 1;
+        if (!cross && !finite) { status = SSA_TRAJ_BAD_RATE; break; }
+        if (slow && kBin) {
+            const int s_first = s;
+            s = warp_bin_edges<false>(p, i, s, t, t_next, k, bacc, xobs, slots);
+            if (!cross && s > s_first) bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
+            thr = s < p.S ? p.ts[s] : p.t_end;
+            if (cross) break;
+        } else if (kBin) {
+            bin_accumulate(bacc, xobs, p.n_obs, tau);
+        }
+        if (slow && !kBin) {
+            while (s < p.S && gt_nonneg(t_next, p.ts[s])) {
+                float *o = obs + ((int64_t)i * p.S + s) * p.n_obs;
+                if (READOUT == SSA_READOUT_HOLD) {
+                    for (int c = lane; c < p.n_obs; c += 32) o[c] = X[p.obs_sp[c]];
+                } else {
+                    const float alpha = __fdiv_rn(d2f_nonneg(p.ts[s] - t), tau);
+                    for (int c = lane; c < p.n_obs; c += 32) {
+                        const int sp = p.obs_sp[c];
+                        o[c] = __fmaf_rn(alpha, dX[sp], X[sp]);
+                    }
+                }
+                ++s;
+            }
+            thr = s < p.S ? p.ts[s] : p.t_end;
+            if (cross) break;
+        }
+        __syncwarp();
+        for (int sp = lane; sp < N; sp += 32) X[sp] = __fadd_rn(X[sp], dX[sp]);
+        __syncwarp();
+        t = t_next;
+        ++k;
+    }
+    __syncwarp();
+    if constexpr (kBin) warp_bin_tail<false>(p, i, s, t, k, bacc, xobs, bad_obs, slots);
+    for (; !kBin && s < p.S; ++s) {
+        float *o = obs + ((int64_t)i * p.S + s) * p.n_obs;
+        for (int c = lane; c < p.n_obs; c += 32) o[c] = bad_obs ? 0.0f : X[p.obs_sp[c]];
+    }
+    if (lane == 0) {
+        p.draws[i] = draws;
+        p.status[i] = status;
+    }
+}
+
 // Per-trajectory body of the warp adjoint (all 32 lanes). X, lam, aj, lj, ct, dA are this warp's buffers;
 // dA accumulates over every trajectory the warp processes.
 template <int READOUT>

@@ -43,24 +43,35 @@ CASES = {
 }
 
 
-def _both(S, net, t_end, ts, obs_sp, T, n, readout, seed, dl=None, max_steps=4096):
+def _both(S, net, t_end, ts, obs_sp, T, n, readout, seed, dl=None, max_steps=4096, tpt=0):
     t32, t64 = _theta32(net.log_rates)
     snet = S.Network(net)
     fw = S.forward(snet, torch.tensor(t32, device="cuda"), n, net.x0, t_end, ts, obs_sp, seed, readout=NAMES[readout],
-                   record=dl is not None, max_steps=max_steps, selector="soft", temperature=T)
+                   record=dl is not None, max_steps=max_steps, selector="soft", temperature=T, threads_per_traj=tpt)
     torch.cuda.synchronize()
     orc = native.run(net, t64, net.x0, n, t_end, ts, np.asarray(obs_sp, np.int32), seed, readout, max_steps=max_steps,
                      selector="soft", temperature=float(np.float32(T)), dl_dobs=dl, ev_cap=max_steps)
     return snet, fw, orc
 
 
+WARP_CASES = {
+    # 160 reactions (a seed whose relaxed counts stay bounded to t_end): beyond the specialised kernels, the warp
+    # layout's own case (lanes hold up to 2 Philox blocks)
+    "random_160": lambda: (W.random_network(np.random.default_rng(16), n_species_range=(20, 20),
+                                            n_reactions_range=(160, 160)), 0.5, [0, 3, 7], 0.5, 128),
+}
+
+
 @pytest.mark.parametrize("readout", [HOLD, LINEAR, BIN])
-@pytest.mark.parametrize("case", sorted(CASES))
-def test_soft_forward_matches_oracle(S, case, readout):
-    net, t_end, obs_sp, T, n = CASES[case]()
+@pytest.mark.parametrize("case,kernels", [(c, k) for c in sorted(CASES) for k in ("specialised", "warp")] +
+                         [(c, "warp") for c in sorted(WARP_CASES)])
+def test_soft_forward_matches_oracle(S, case, kernels, readout):
+    """The soft forward on the network-specialised thread kernels and on the warp-per-trajectory kernels
+    (threads_per_traj = 32; the only layout for networks past the specialised kernels' limits)."""
+    net, t_end, obs_sp, T, n = {**CASES, **WARP_CASES}[case]()
     ts = W.uniform_sample_grid(t_end, 16)
-    snet, fw, orc = _both(S, net, t_end, ts, obs_sp, T, n, readout, 3)
-    assert fw.run.variant == 2
+    snet, fw, orc = _both(S, net, t_end, ts, obs_sp, T, n, readout, 3, tpt=32 if kernels == "warp" else 0)
+    assert fw.run.variant == (32 if kernels == "warp" else 2)
     st = fw.status.cpu().numpy()
     assert np.all(st <= 1) and np.all(orc.status <= 1)
     same = fw.draws.cpu().numpy() == orc.draws  # a crossing decided within the clock tolerance may differ
@@ -162,6 +173,22 @@ def test_soft_simulate_autograd_matches_backward(S):
     torch.testing.assert_close(theta.grad, S.backward(fw, dl, 0.5), rtol=1e-5, atol=1e-8)
 
 
+@pytest.mark.parametrize("readout", ["hold", "linear", "bin"])
+def test_warp_soft_forward_equals_specialised_on_two_reactions(S, readout):
+    """With M = 2 lane 0 holds every reaction of the warp layout, so a0, the largest key and the normaliser are
+    summed in the thread kernels' order (the other lanes add zeros): the two layouts agree bit for bit, which
+    checks the species-major update list and the readouts of the warp soft forward."""
+    net = W.dimerization_2a_b(0.01, 0.1, 100)
+    snet = S.Network(net)
+    th = torch.tensor(net.log_rates.astype(np.float32), device="cuda")
+    ts = W.uniform_sample_grid(20.0, 16)
+    runs = [S.forward(snet, th, 3000, net.x0, 20.0, ts, [0, 1], 7, readout=readout, selector="soft", temperature=0.4,
+                      threads_per_traj=tpt, max_steps=8192) for tpt in (0, 32)]
+    assert [r.run.variant for r in runs] == [2, 32]
+    assert torch.equal(runs[0].obs, runs[1].obs)
+    assert torch.equal(runs[0].draws, runs[1].draws) and torch.equal(runs[0].status, runs[1].status)
+
+
 def test_soft_rules(S):
     net = W.dimerization_2a_b()
     snet = S.Network(net)
@@ -169,10 +196,13 @@ def test_soft_rules(S):
     args = (snet, th, 64, net.x0, 1.0, [0.5, 1.0], [0], 0)
     with pytest.raises(RuntimeError):  # no temperature
         S.forward(*args, selector="soft")
-    with pytest.raises(RuntimeError):  # generic kernels do not have it
-        S.forward(*args, selector="soft", temperature=0.5, specialize=False)
+    # without the specialised kernels the warp kernels run it, forward only
+    assert S.forward(*args, selector="soft", temperature=0.5, specialize=False).run.variant == 32
+    assert S.forward(*args, selector="soft", temperature=0.5, threads_per_traj=32).run.variant == 32
     with pytest.raises(RuntimeError):
-        S.forward(*args, selector="soft", temperature=0.5, threads_per_traj=32)
+        S.forward(*args, selector="soft", temperature=0.5, threads_per_traj=32, record=True)
+    with pytest.raises(RuntimeError):
+        S.forward(*args, selector="soft", temperature=0.5, specialize=False, threads_per_traj=1)
     fw = S.forward(*args, selector="soft", temperature=0.5, record=True, readout="linear")
     with pytest.raises(RuntimeError):  # the gradient of the relaxed model is at its own temperature
         S.backward(fw, torch.zeros(64, 2, 1, device="cuda"), 0.25)
