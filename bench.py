@@ -925,6 +925,42 @@ def warp_extra(ssa, dev, n: int = 16384, reps: int = 2, oracle: bool = True):
            "fwd_steps_per_s": steps / (fms / 1e3), "adj_steps_per_s": steps / (ams / 1e3),
            "fwd_instr_per_s_T": instr_per_step_fwd(M, log_slots) * steps / (fms / 1e3) / 1e12,
            "adj_instr_per_s_T": instr_per_step_bwd(M, log_slots) * steps / (ams / 1e3) / 1e12}
+    # the soft forward of Eq. 4 on the same network and trajectories (warp kernels, forward only), at the
+    # batch's T; its step count is its own
+    sms, ssteps, sbad = 0.0, 0, 0
+    for r in range(reps + 1):
+        ev[0].record()
+        fw = ssa.forward(net, th, n, spec.x0, wl.t_end, wl.sample_times, wl.obs_species[q], 300 + r,
+                         readout="linear", max_steps=max_steps, threads_per_traj=32, selector="soft",
+                         temperature=wl.temperature)
+        ev[1].record()
+        torch.cuda.synchronize()
+        if r >= 1:
+            sms += ev[0].elapsed_time(ev[1])
+            ssteps += int(fw.draws.sum().item())
+            sbad = int((fw.status > 1).sum().item())
+        del fw
+    out["soft_forward"] = {"ms": sms / reps, "ssa_steps": ssteps // reps, "steps_per_s": ssteps / (sms / 1e3),
+                           "temperature": wl.temperature, "non_ok_trajectories": sbad}
+    # and its exact gradient (recorded soft forward, then the adjoint's segment re-runs)
+    gf = ga = 0.0
+    gsteps = 0
+    for r in range(reps + 1):
+        ev[0].record()
+        fw = ssa.forward(net, th, n, spec.x0, wl.t_end, wl.sample_times, wl.obs_species[q], 300 + r,
+                         readout="linear", record=True, max_steps=max_steps, threads_per_traj=32, selector="soft",
+                         temperature=wl.temperature)
+        ev[1].record()
+        ssa.backward(fw, dl, wl.temperature)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if r >= 1:
+            gf += ev[0].elapsed_time(ev[1])
+            ga += ev[1].elapsed_time(ev[2])
+            gsteps += int(fw.draws.sum().item())
+        del fw
+    out["soft_forward"]["gradient"] = {"forward_rec_ms": gf / reps, "backward_ms": ga / reps,
+                                       "fwd_adj_steps_per_s": gsteps / ((gf + ga) / 1e3)}
     if oracle:
         m = 256
         out["grad_rel_err_vs_fp64"] = oracle_grad_err(

@@ -85,7 +85,7 @@ typedef struct ssa_fwd_opts {
                                  SSA_SELECT_SOFT (the relaxed forward of Eq. 4). The direct
                                  method runs on the network-specialised kernels only; the soft
                                  forward on them where the network qualifies, otherwise on the
-                                 warp-per-trajectory kernels, without recording there         */
+                                 warp-per-trajectory kernels                                    */
     float temperature;        /* SSA_SELECT_SOFT: T > 0 of its soft sample; else must be 0       */
 } ssa_fwd_opts;
 
@@ -102,7 +102,7 @@ typedef struct ssa_fwd_opts {
  * specialised kernels' limits (or threads_per_traj = 32, or no_specialize) run the soft forward one warp
  * per trajectory: every species sums its changes in increasing reaction order as the specialised kernels
  * do, a0 and the normaliser are warp sums (so the results agree with the specialised kernels to binary32
- * rounding, not bit for bit); recording there returns SSA_ERR_UNSUPPORTED. */
+ * rounding, not bit for bit), and ssa_backward there re-runs each 8-step segment the same way. */
 #define SSA_SELECT_SOFT 2
 
 /*

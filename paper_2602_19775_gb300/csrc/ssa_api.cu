@@ -34,7 +34,10 @@ cudaError_t launch_backward_thread(const AdjParams &p, int readout, int block, s
 cudaError_t launch_reduce_partials(const float *partial, int64_t nblk, int M, const int *rate_index, int P,
                                    float *dA_tmp, float *dtheta, cudaStream_t st);
 cudaError_t launch_forward_warp(const FwdParams &p, int readout, bool record, int warps, size_t smem, cudaStream_t st);
-cudaError_t launch_forward_warp_soft(const FwdParams &p, int readout, int warps, size_t smem, cudaStream_t st);
+cudaError_t launch_forward_warp_soft(const FwdParams &p, int readout, bool record, int warps, size_t smem,
+                                     cudaStream_t st);
+cudaError_t launch_backward_warp_soft(const AdjParams &p, const int *upd, uint32_t upd_words, int readout, int warps,
+                                      size_t smem, int64_t grid, cudaStream_t st);
 cudaError_t launch_backward_warp(const AdjParams &p, int readout, int warps, size_t smem, int64_t grid,
                                  cudaStream_t st);
 int thread_kernel_mc(int M);
@@ -193,6 +196,13 @@ size_t fwd_warp_soft_smem(const ssa_network *net)
 {
     return net->tab_bytes + (size_t)net->Mp * 4 + 16 + (size_t)net->upd_words * 4 +
            (size_t)kWarpsPerBlock * (2 * ((net->N + 3) & ~3) + (size_t)net->Mp) * 4;
+}
+
+// its gradient: tables, rates, the update list, and per warp Xs [kSoftK][Npad], lam, dX [Npad], a, h, y, c1, c2, dA [Mp]
+size_t adj_warp_soft_smem(const ssa_network *net)
+{
+    return net->tab_bytes + (size_t)net->Mp * 4 + 16 + (size_t)net->upd_words * 4 +
+           (size_t)kWarpsPerBlock * ((kSoftK + 2) * (size_t)((net->N + 3) & ~3) + 6 * (size_t)net->Mp) * 4;
 }
 
 size_t adj_warp_smem(const ssa_network *net)
@@ -403,9 +413,6 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
             return fail(SSA_ERR_UNSUPPORTED, "the soft forward with one thread per trajectory needs the "
                         "network-specialised kernels: %s", why.c_str());
         if (variant == 1) variant = 32;
-        if (variant == 32 && opts->record)
-            return fail(SSA_ERR_UNSUPPORTED, "the soft forward's gradient runs on the network-specialised thread "
-                        "kernels (N, M <= 24); the warp kernels run the soft forward without recording");
     } else if (variant == 1 && !ev_in && !opts->no_specialize && jit_eligible(net)) {
         std::string why;
         jit = jit_kernels(net, why);
@@ -424,7 +431,7 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
         if (opts->record && !pick_block(adj_smem, net, 0, limit))
             return fail(SSA_ERR_UNSUPPORTED, "network too large for the thread-per-trajectory adjoint");
     } else if (opts->selector == SSA_SELECT_SOFT) {
-        if (fwd_warp_soft_smem(net) > limit)
+        if (fwd_warp_soft_smem(net) > limit || (opts->record && adj_warp_soft_smem(net) > limit))
             return fail(SSA_ERR_UNSUPPORTED, "network too large for the warp-per-trajectory soft forward");
     } else {
         if (fwd_warp_smem(net) > limit || (opts->record && adj_warp_smem(net) > limit))
@@ -491,7 +498,8 @@ static ssa_status forward_impl(const ssa_network *net, const float *log_rates, i
     else if (variant == 1)
         CUDA_TRY(launch_forward_thread(p, opts->readout, opts->record != 0, ev_in != nullptr, block, fwd_smem(net, block), st));
     else if (opts->selector == SSA_SELECT_SOFT)
-        CUDA_TRY(launch_forward_warp_soft(p, opts->readout, kWarpsPerBlock, fwd_warp_soft_smem(net), st));
+        CUDA_TRY(launch_forward_warp_soft(p, opts->readout, opts->record != 0, kWarpsPerBlock, fwd_warp_soft_smem(net),
+                                          st));
     else
         CUDA_TRY(launch_forward_warp(p, opts->readout, opts->record != 0, kWarpsPerBlock, fwd_warp_smem(net), st));
     if (n_traj > 0 && draws_out) CUDA_TRY(cudaMemcpyAsync(draws_out, p.draws, (size_t)n_traj * 4, cudaMemcpyDeviceToDevice, st));
@@ -638,6 +646,9 @@ extern "C" ssa_status ssa_backward(ssa_run *run, const float *dl_dobs, int64_t d
         CUDA_TRY(jit_launch_backward(jit, p, run->opts.readout, block, grid, st));
     else if (run->variant == 1)
         CUDA_TRY(launch_backward_thread(p, run->opts.readout, block, adj_smem(net, block), grid, st));
+    else if (run->opts.selector == SSA_SELECT_SOFT)
+        CUDA_TRY(launch_backward_warp_soft(p, net->d_upd, net->upd_words, run->opts.readout, kWarpsPerBlock,
+                                           adj_warp_soft_smem(net), grid, st));
     else
         CUDA_TRY(launch_backward_warp(p, run->opts.readout, kWarpsPerBlock, adj_warp_smem(net), grid, st));
     CUDA_TRY(launch_reduce_partials(p.partial, grid, net->M, net->d_rate_index, net->P,

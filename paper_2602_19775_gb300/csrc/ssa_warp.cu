@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) fwd_warp_kernel(const FwdParams p)
 
 // The soft forward (Eq. 4) on the warp layout: the staged tables and rates, then the species-major update
 // list; per warp X [Npad], dX [Npad] (floats) and the keys / weights y [Mp].
-template <int READOUT>
+template <int READOUT, bool RECORD>
 __global__ void __launch_bounds__(256) fwd_warp_soft_kernel(const FwdParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -63,7 +63,62 @@ __global__ void __launch_bounds__(256) fwd_warp_soft_kernel(const FwdParams p)
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * W + wib;
     if (i >= p.n_traj) return;  // whole warp
-    warp_soft_fwd_body<READOUT>(p, s_rx, s_k, s_upd, wbase, wbase + Npad, wbase + 2 * Npad, i);
+    warp_soft_fwd_body<READOUT, RECORD>(p, s_rx, s_k, s_upd, wbase, wbase + Npad, wbase + 2 * Npad, i);
+}
+
+// Gradient of the soft forward on the warp layout: tables, rates, the update list, then per warp
+// Xs [kSoftK][Npad], lam [Npad], dX [Npad], a, h, y, c1, c2, dA [Mp]; dA reduced over the block in a fixed order.
+template <int READOUT>
+__global__ void __launch_bounds__(256) adj_warp_soft_kernel(const AdjParams p, const int *upd, uint32_t upd_words)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int N = p.N, M = p.M, Mp = p.Mp;
+    const int Npad = (N + 3) & ~3;
+    int4 *s_rx = reinterpret_cast<int4 *>(smem);
+    int *s_st = reinterpret_cast<int *>(smem + 16 * Mp);
+    const int *s_inc_ptr = reinterpret_cast<const int *>(smem + p.inc_off);
+    const int *s_inc = reinterpret_cast<const int *>(smem + p.inc_list_off);
+    float *s_k = reinterpret_cast<float *>(smem + p.tab_bytes);
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem + p.tab_bytes + p.k_bytes);
+    int *s_ok = reinterpret_cast<int *>(smem + p.tab_bytes + p.k_bytes + 8);
+    int *s_upd = reinterpret_cast<int *>(smem + p.tab_bytes + p.k_bytes + 16);
+    const size_t per_warp = (size_t)(kSoftK + 2) * Npad + 6 * (size_t)Mp;
+    float *base0 = reinterpret_cast<float *>(s_upd + upd_words);
+    float *wbase = base0 + wib * per_warp;
+    float *Xs = wbase;
+    float *lam = Xs + kSoftK * Npad;
+    float *dX = lam + Npad;
+    float *aj = dX + Npad;
+    float *hj = aj + Mp;
+    float *y = hj + Mp;
+    float *c1 = y + Mp;
+    float *c2 = c1 + Mp;
+    float *dA = c2 + Mp;
+
+    if (!stage_tables(smem, p.rx, p.tab_bytes, s_k, p.k_rates, p.k_bytes, s_bar, s_ok, p.err)) {
+        for (int j = threadIdx.x; j < M; j += blockDim.x) p.partial[(int64_t)blockIdx.x * M + j] = 0.0f;
+        return;
+    }
+    for (uint32_t q = threadIdx.x; q < upd_words; q += blockDim.x) s_upd[q] = upd[q];
+    for (int j = lane; j < Mp; j += 32) dA[j] = 0.0f;
+    __syncthreads();
+
+    const int64_t n = p.n_traj;
+    const int64_t i = (int64_t)blockIdx.x * W + wib;
+    int st = -1;
+    if (i < n) st = p.status[i];
+    const bool active = st == SSA_TRAJ_OK || st == SSA_TRAJ_ABSORBED || st == SSA_TRAJ_STEP_CAP;
+    if (active)
+        warp_soft_adj_body<READOUT>(p, s_rx, s_st, s_inc_ptr, s_inc, s_k, s_upd, Xs, lam, dX, aj, hj, y, c1, c2, dA, i,
+                                    st);
+    __syncthreads();
+    const int nb = (M + 4) >> 2;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        float acc = 0.0f;
+        for (int w = 0; w < W; ++w) acc += base0[w * per_warp + (kSoftK + 2) * Npad + 5 * Mp + jpos(j, nb)];
+        p.partial[(int64_t)blockIdx.x * M + j] = acc;
+    }
 }
 
 template <int READOUT>
@@ -136,10 +191,10 @@ cudaError_t launch_forward_warp(const FwdParams &p, int readout, bool record, in
     return record ? launch_fwd_w<1, true>(p, warps, smem, st) : launch_fwd_w<1, false>(p, warps, smem, st);
 }
 
-template <int R>
+template <int R, bool REC>
 static cudaError_t launch_fwd_soft_w(const FwdParams &p, int warps, size_t smem, cudaStream_t st)
 {
-    auto kern = fwd_warp_soft_kernel<R>;
+    auto kern = fwd_warp_soft_kernel<R, REC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = (p.n_traj + warps - 1) / warps;
@@ -147,12 +202,35 @@ static cudaError_t launch_fwd_soft_w(const FwdParams &p, int warps, size_t smem,
     return cudaGetLastError();
 }
 
-cudaError_t launch_forward_warp_soft(const FwdParams &p, int readout, int warps, size_t smem, cudaStream_t st)
+cudaError_t launch_forward_warp_soft(const FwdParams &p, int readout, bool record, int warps, size_t smem,
+                                     cudaStream_t st)
 {
     if (p.n_traj == 0) return cudaSuccess;
-    if (readout == SSA_READOUT_HOLD) return launch_fwd_soft_w<0>(p, warps, smem, st);
-    if (readout == SSA_READOUT_BIN) return launch_fwd_soft_w<2>(p, warps, smem, st);
-    return launch_fwd_soft_w<1>(p, warps, smem, st);
+    if (readout == SSA_READOUT_HOLD)
+        return record ? launch_fwd_soft_w<0, true>(p, warps, smem, st) : launch_fwd_soft_w<0, false>(p, warps, smem, st);
+    if (readout == SSA_READOUT_BIN)
+        return record ? launch_fwd_soft_w<2, true>(p, warps, smem, st) : launch_fwd_soft_w<2, false>(p, warps, smem, st);
+    return record ? launch_fwd_soft_w<1, true>(p, warps, smem, st) : launch_fwd_soft_w<1, false>(p, warps, smem, st);
+}
+
+template <int R>
+static cudaError_t launch_adj_soft_w(const AdjParams &p, const int *upd, uint32_t upd_words, int warps, size_t smem,
+                                     int64_t grid, cudaStream_t st)
+{
+    auto kern = adj_warp_soft_kernel<R>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, warps * 32, smem, st>>>(p, upd, upd_words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward_warp_soft(const AdjParams &p, const int *upd, uint32_t upd_words, int readout, int warps,
+                                      size_t smem, int64_t grid, cudaStream_t st)
+{
+    if (grid == 0) return cudaSuccess;
+    if (readout == SSA_READOUT_HOLD) return launch_adj_soft_w<0>(p, upd, upd_words, warps, smem, grid, st);
+    if (readout == SSA_READOUT_BIN) return launch_adj_soft_w<2>(p, upd, upd_words, warps, smem, grid, st);
+    return launch_adj_soft_w<1>(p, upd, upd_words, warps, smem, grid, st);
 }
 
 template <int R>

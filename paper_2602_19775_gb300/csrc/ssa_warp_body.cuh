@@ -305,21 +305,96 @@ __device__ __forceinline__ void warp_fwd_body(const FwdParams &p, const int4 *s_
     }
 }
 
-// Per-trajectory body of the warp soft forward (Section 3.3, Eq. 4), forward only: the state X is real and
-// moves every step by the expected change sum_j y~_j v_j of the soft sample y~ = softmax((log a + G)/T), with
-// the variates of the Gumbel-max forward. Per step, lane l evaluates the reactions of its Philox blocks (the
-// relaxed propensities, negative factors clipped at 0, and the keys log2 a_j - log2 E_j, kept in y by
-// lane-major position), the warp reduces a0 and the largest key, the lanes turn their keys into weights, and
-// each species sums its own changes through the species-major update list in increasing j (no atomics: the
-// same order as the specialised thread kernels' update). Clock, samples and readouts are the forward's.
-template <int READOUT>
+// One step of the soft forward (Section 3.3, Eq. 4) at the real state X, all 32 lanes: lane l evaluates the
+// reactions of its Philox blocks (relaxed propensities with negative factors clipped at 0, keys
+// l_j = log2 a_j - log2 E_j), the warp reduces a0 and the largest key, the lanes turn their keys into
+// unnormalised weights w_j = exp2((l_j - l_max)/T) (kept in y by lane-major position), and each species sums
+// its own change dX_s = sum_j (w_j / Z) v_js through the species-major update list in increasing j (no atomics:
+// the specialised thread kernels' order of the update). With AH, a_j and h_j are kept too (the adjoint's
+// re-evaluation). Returns a0; sets E0, invZ = 1/Z and whether X + dX is finite. The forward and the adjoint's
+// segment re-runs call this one function, so the regenerated states are the forward's bit for bit.
+template <bool AH>
+__device__ __forceinline__ float warp_soft_step(const int4 *s_rx, const float *s_k, const int *s_upd, int N, int M,
+                                                float invT, int k, uint32_t c2, uint32_t c3, uint32_t key0,
+                                                uint32_t key1, const float *X, float *a_out, float *h_out, float *y,
+                                                float *dX, float &E0, float &invZ, bool &finite)
+{
+    const int lane = threadIdx.x & 31, nb = (M + 4) >> 2;
+    const int upd_base = (N + 1 + 3) & ~3;  // the list follows the padded pointer array
+    float a0p = 0.0f, lmaxp = -CUDART_INF_F;
+    E0 = 0.0f;
+    for (int b = lane; b < nb; b += 32) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 4 * b + q - 1;
+            const float E = neg_log_unit(u01(word_of(r, q)));
+            if (j < 0) {
+                E0 = E;
+                continue;
+            }
+            const int pos = q * nb + b;
+            const int4 rx = s_rx[pos];
+            float h = 1.0f;
+            if (rx.x >= 0) {
+                const float x1 = X[rx.x];
+                h = rx.y < 0 ? hs_first(x1) : rx.y == rx.x ? hs_homodimer(x1) : hs_hetero(x1, X[rx.y]);
+            }
+            const float a = __fmul_rn(s_k[pos], h);
+            a0p = __fadd_rn(a0p, a);
+            const float l = a > 0.0f ? log2f(a) - log2f(E) : -CUDART_INF_F;
+            if (j < M) {
+                y[pos] = l;
+                if (AH) {
+                    a_out[pos] = a;
+                    h_out[pos] = h;
+                }
+            }
+            lmaxp = fmaxf(lmaxp, l);
+        }
+    }
+    const float a0 = warp_sum(a0p), lmax = warp_max(lmaxp);
+    E0 = __shfl_sync(0xffffffffu, E0, 0);
+    float Zp = 0.0f;
+    for (int b = lane; b < nb; b += 32) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 4 * b + q - 1;
+            if (j < 0 || j >= M) continue;
+            const int pos = q * nb + b;
+            const float l = y[pos];
+            const float w = l == -CUDART_INF_F ? 0.0f : exp2f((l - lmax) * invT);
+            y[pos] = w;
+            Zp += w;
+        }
+    }
+    invZ = __fdividef(1.0f, warp_sum(Zp));
+    __syncwarp();
+    bool fin = true;
+    for (int sp = lane; sp < N; sp += 32) {
+        float d = 0.0f;
+        for (int e = s_upd[sp]; e < s_upd[sp + 1]; ++e) {
+            const int ent = s_upd[upd_base + e];
+            d = __fmaf_rn(y[ent >> 8] * invZ, (float)(int)(signed char)(ent & 0xff), d);
+        }
+        dX[sp] = d;
+        fin &= fabsf(__fadd_rn(X[sp], d)) < CUDART_INF_F;
+    }
+    finite = __all_sync(0xffffffffu, fin);
+    __syncwarp();
+    return a0;
+}
+
+// Per-trajectory body of the warp soft forward (Eq. 4). Clock, samples and readouts are the forward's;
+// recorded, the float state is checkpointed every kSoftK steps ([n_ckpt][N][n_traj], checkpoint 0 = X_0) with
+// the sample brackets, for the adjoint's segment re-runs.
+template <int READOUT, bool RECORD>
 __device__ __forceinline__ void warp_soft_fwd_body(const FwdParams &p, const int4 *s_rx, const float *s_k,
                                                    const int *s_upd, float *X, float *dX, float *y, const int64_t i)
 {
     const int lane = threadIdx.x & 31;
-    const int N = p.N, M = p.M, nb = (M + 4) >> 2;
+    const int N = p.N, M = p.M;
     const int64_t n = p.n_traj;
-    const int upd_base = (N + 1 + 3) & ~3;  // the list follows the padded pointer array
     const int *x0 = p.x0 + (p.x0_per_traj ? i * N : 0);
     const bool bad_obs = (*p.flag & kErrBadObs) != 0;
     bool neg = false;
@@ -336,7 +411,7 @@ __device__ __forceinline__ void warp_soft_fwd_body(const FwdParams &p, const int
     int s = 0;
     double thr = p.S > 0 ? p.ts[0] : p.t_end;
     int status = bad_input ? SSA_TRAJ_BAD_INPUT : SSA_TRAJ_OK;
-    int k = 0, draws = 0;
+    int k = 0, draws = 0, ck_left = p.K, ck_row = 0;
     constexpr bool kBin = READOUT == SSA_READOUT_BIN;
     float bacc[kBinMaxObs];
     int osp[kBinMaxObs];
@@ -348,68 +423,16 @@ __device__ __forceinline__ void warp_soft_fwd_body(const FwdParams &p, const int
     auto xobs = [&](int c) { return X[osp[c]]; };
     int slots = 0;
     float *obs = static_cast<float *>(p.obs_out);
+    float *ckf = reinterpret_cast<float *>(p.ckpt);
 
     while (!bad_input) {
         if (k >= p.max_steps) { status = SSA_TRAJ_STEP_CAP; break; }
-        // relaxed propensities and keys of this lane's reactions
-        float a0p = 0.0f, lmaxp = -CUDART_INF_F, E0 = 0.0f;
-        for (int b = lane; b < nb; b += 32) {
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = 4 * b + q - 1;
-                const float E = neg_log_unit(u01(word_of(r, q)));
-                if (j < 0) {
-                    E0 = E;
-                    continue;
-                }
-                const int pos = q * nb + b;
-                const int4 rx = s_rx[pos];
-                float h = 1.0f;
-                if (rx.x >= 0) {
-                    const float x1 = X[rx.x];
-                    h = rx.y < 0 ? hs_first(x1) : rx.y == rx.x ? hs_homodimer(x1) : hs_hetero(x1, X[rx.y]);
-                }
-                const float a = __fmul_rn(s_k[pos], h);
-                a0p = __fadd_rn(a0p, a);
-                const float l = a > 0.0f ? log2f(a) - log2f(E) : -CUDART_INF_F;
-                if (j < M) y[pos] = l;
-                lmaxp = fmaxf(lmaxp, l);
-            }
-        }
-        const float a0 = warp_sum(a0p), lmax = warp_max(lmaxp);
-        E0 = __shfl_sync(0xffffffffu, E0, 0);
+        float E0, invZ;
+        bool finite;
+        const float a0 = warp_soft_step<false>(s_rx, s_k, s_upd, N, M, p.invT, k, c2, c3, key0, key1, X, nullptr,
+                                               nullptr, y, dX, E0, invZ, finite);
         if (!(a0 < CUDART_INF_F)) { status = SSA_TRAJ_BAD_RATE; break; }
         if (a0 == 0.0f) { status = SSA_TRAJ_ABSORBED; break; }
-        // weights exp2((l_j - l_max)/T) and their sum
-        float Zp = 0.0f;
-        for (int b = lane; b < nb; b += 32) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = 4 * b + q - 1;
-                if (j < 0 || j >= M) continue;
-                const int pos = q * nb + b;
-                const float l = y[pos];
-                const float w = l == -CUDART_INF_F ? 0.0f : exp2f((l - lmax) * p.invT);
-                y[pos] = w;
-                Zp += w;
-            }
-        }
-        const float invZ = __fdividef(1.0f, warp_sum(Zp));
-        __syncwarp();
-        // dX_s = sum over the reactions changing s, in increasing j, of y~_j v_js
-        bool fin = true;
-        for (int sp = lane; sp < N; sp += 32) {
-            float d = 0.0f;
-            for (int e = s_upd[sp]; e < s_upd[sp + 1]; ++e) {
-                const int ent = s_upd[upd_base + e];
-                d = __fmaf_rn(y[ent >> 8] * invZ, (float)(int)(signed char)(ent & 0xff), d);
-            }
-            dX[sp] = d;
-            fin &= fabsf(__fadd_rn(X[sp], d)) < CUDART_INF_F;
-        }
-        const bool finite = __all_sync(0xffffffffu, fin);
-        __syncwarp();
         const float tau = waiting_time(E0, a0);
         const double t_next = t + f2d_pos(tau);
         const bool slow = gt_nonneg(t_next, thr);
@@ -418,7 +441,7 @@ __device__ __forceinline__ void warp_soft_fwd_body(const FwdParams &p, const int
         if (!cross && !finite) { status = SSA_TRAJ_BAD_RATE; break; }
         if (slow && kBin) {
             const int s_first = s;
-            s = warp_bin_edges<false>(p, i, s, t, t_next, k, bacc, xobs, slots);
+            s = warp_bin_edges<RECORD>(p, i, s, t, t_next, k, bacc, xobs, slots);
             if (!cross && s > s_first) bin_accumulate(bacc, xobs, p.n_obs, d2f_nonneg(t_next - p.ts[s - 1]));
             thr = s < p.S ? p.ts[s] : p.t_end;
             if (cross) break;
@@ -436,7 +459,9 @@ __device__ __forceinline__ void warp_soft_fwd_body(const FwdParams &p, const int
                         const int sp = p.obs_sp[c];
                         o[c] = __fmaf_rn(alpha, dX[sp], X[sp]);
                     }
+                    if (RECORD && lane == 0) p.brk_a[(int64_t)s * n + i] = alpha;
                 }
+                if (RECORD && lane == 0) p.brk_k[(int64_t)s * n + i] = k;
                 ++s;
             }
             thr = s < p.S ? p.ts[s] : p.t_end;
@@ -447,17 +472,235 @@ __device__ __forceinline__ void warp_soft_fwd_body(const FwdParams &p, const int
         __syncwarp();
         t = t_next;
         ++k;
+        if (RECORD && --ck_left == 0) {
+            ck_left = p.K;
+            ++ck_row;
+            for (int sp = lane; sp < N; sp += 32) ckf[((int64_t)ck_row * N + sp) * n + i] = X[sp];
+        }
     }
     __syncwarp();
-    if constexpr (kBin) warp_bin_tail<false>(p, i, s, t, k, bacc, xobs, bad_obs, slots);
+    if constexpr (kBin) warp_bin_tail<RECORD>(p, i, s, t, k, bacc, xobs, bad_obs, slots);
     for (; !kBin && s < p.S; ++s) {
         float *o = obs + ((int64_t)i * p.S + s) * p.n_obs;
         for (int c = lane; c < p.n_obs; c += 32) o[c] = bad_obs ? 0.0f : X[p.obs_sp[c]];
+        if (RECORD && lane == 0) {
+            if (READOUT == SSA_READOUT_LINEAR) p.brk_a[(int64_t)s * n + i] = -1.0f;
+            p.brk_k[(int64_t)s * n + i] = k;
+        }
     }
     if (lane == 0) {
         p.draws[i] = draws;
         p.status[i] = status;
     }
+    if (RECORD)
+        for (int sp = lane; sp < N; sp += 32) ckf[(int64_t)sp * n + i] = int2f(x0[sp]);  // checkpoint 0 = X_0
+}
+
+// Exact gradient of the soft forward on the warp layout, one trajectory (all 32 lanes): the specialised thread
+// kernels' soft adjoint in the warp's arrays. Segment by segment from the end, the kSoftK states are
+// regenerated from the float checkpoint with the forward's own step (the state after a segment must equal the
+// next checkpoint bit for bit), then walked back: the step is evaluated again at X_k, the readout terms give
+// the waiting-time adjoint, w_j = v_j . lambda, psi_j = y~_j (w_j - sum y~ w) / T, dA_j += psi_j + dL/da0 a_j,
+// and every reactant slot's contribution (choice path and waiting-time path, clipped where a factor is) is
+// gathered per species through the reactant-slot incidence list in increasing j, added to lambda in that
+// order. Per-warp arrays: Xs [kSoftK][Npad], lam, dX [Npad]; a, h, y, c1, c2 [Mp]; dA [Mp] accumulates.
+template <int READOUT>
+__device__ __forceinline__ void warp_soft_adj_body(const AdjParams &p, const int4 *s_rx, const int *s_st,
+                                                   const int *s_inc_ptr, const int *s_inc, const float *s_k,
+                                                   const int *s_upd, float *Xs, float *lam, float *dX, float *aj,
+                                                   float *hj, float *y, float *c1, float *c2, float *dA,
+                                                   const int64_t i, const int st)
+{
+    const int lane = threadIdx.x & 31;
+    const int N = p.N, M = p.M, nb = (M + 4) >> 2, Npad = (N + 3) & ~3;
+    const int64_t n = p.n_traj;
+    const int d = p.draws[i];
+    const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;  // index of the last visited state
+    const bool draw_last = st == SSA_TRAJ_OK;
+    const int K = p.K;  // kSoftK
+    const uint64_t gid = p.traj_offset + (uint64_t)i;
+    const uint32_t c2w = (uint32_t)gid, c3w = (uint32_t)(gid >> 32), key0 = (uint32_t)p.seed,
+                   key1 = (uint32_t)(p.seed >> 32);
+    const float invT = p.invT;
+    const float *gl = p.dl_dobs + i * p.dl_stride;
+    const float *ckf = reinterpret_cast<const float *>(p.ckpt);
+    for (int sp = lane; sp < N; sp += 32) lam[sp] = 0.0f;
+    int s_hi = p.S - 1;
+    int brk_next = (READOUT != SSA_READOUT_BIN && s_hi >= 0) ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    constexpr bool kBin = READOUT == SSA_READOUT_BIN;
+    BinSlots bslots{-1, -1};
+    float d_first = 0.0f, d_last = 0.0f;
+    if (kBin) bin_slots_init(bslots, p.brk_k, p.brk_tail, n, i);
+    float mu = 0.0f;
+    int mism = 0;
+    float gq[kBinMaxObs], gk[kBinMaxObs];
+    int osp[kBinMaxObs];
+#pragma unroll
+    for (int c = 0; c < kBinMaxObs; ++c) osp[c] = (kBin && c < p.n_obs) ? p.obs_sp[c] : 0;
+    auto addx = [&](int c, float v) { lam[osp[c]] += v; };
+    if (kBin) bin_grad(gq, gl, p.n_obs, p.ts, p.S, p.S);
+    __syncwarp();
+
+    for (int c = L / K; c >= 0; --c) {
+        const int k0 = c * K, k1 = min(k0 + K - 1, L);
+        // regenerate the segment's states: Xs[kk - k0] = X_kk
+        for (int sp = lane; sp < N; sp += 32) Xs[sp] = ckf[((int64_t)c * N + sp) * n + i];
+        __syncwarp();
+        for (int kk = k0; kk < k1 || (kk == k1 && k1 < L); ++kk) {
+            const float *Xc = Xs + (size_t)(kk - k0) * Npad;
+            float E0, invZ;
+            bool finite;
+            warp_soft_step<false>(s_rx, s_k, s_upd, N, M, invT, kk, c2w, c3w, key0, key1, Xc, nullptr, nullptr, y, dX,
+                                  E0, invZ, finite);
+            if (kk < k1) {
+                float *Xn = Xs + (size_t)(kk + 1 - k0) * Npad;
+                for (int sp = lane; sp < N; sp += 32) Xn[sp] = __fadd_rn(Xc[sp], dX[sp]);
+            } else {  // the state after the segment: the next checkpoint
+                int bad = 0;
+                for (int sp = lane; sp < N; sp += 32)
+                    bad += __fadd_rn(Xc[sp], dX[sp]) != ckf[((int64_t)(c + 1) * N + sp) * n + i];
+                mism += __reduce_add_sync(0xffffffffu, bad);
+            }
+            __syncwarp();
+        }
+        for (int k = k1; k >= k0; --k) {
+            const float *Xk = Xs + (size_t)(k - k0) * Npad;
+            const bool draw = (k < L) || draw_last;
+            const int s_top = s_hi;
+            if (kBin) {
+                bin_slots_step(bslots, p.brk_k, p.brk_s, p.brk_a, p.ts, n, i, k, s_hi, d_first, d_last);
+                if (s_hi < s_top) bin_grad(gk, gl, p.n_obs, p.ts, p.S, s_hi + 1);
+                else {
+#pragma unroll
+                    for (int q = 0; q < kBinMaxObs; ++q) gk[q] = gq[q];
+                }
+            } else {
+                while (s_hi >= 0 && brk_next == k) {
+                    --s_hi;
+                    brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+                }
+            }
+            float tau_k = 0.0f;
+            if (draw) {
+                float E0, invZ;
+                bool finite;
+                const float a0 = warp_soft_step<true>(s_rx, s_k, s_upd, N, M, invT, k, c2w, c3w, key0, key1, Xk, aj,
+                                                      hj, y, dX, E0, invZ, finite);
+                const float tau = waiting_time(E0, a0);
+                tau_k = tau;
+                float dt_dir = 0.0f, dtau_dir = 0.0f;
+                if (kBin) {  // t_{k+1} ends this interval and starts the next, in the bin of gq
+                    float cb = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < kBinMaxObs; ++q)
+                        if (q < p.n_obs) cb = __fmaf_rn(gq[q], dX[osp[q]], cb);
+                    mu -= cb;
+                }
+                if (READOUT == SSA_READOUT_LINEAR) {
+                    // serial on lane 0 (observed species may repeat), broadcast afterwards
+                    if (lane == 0) {
+                        for (int s = s_hi + 1; s <= s_top; ++s) {
+                            const float alpha = p.brk_a[(int64_t)s * n + i];
+                            if (alpha < 0.0f) continue;
+                            float cl = 0.0f;
+                            for (int o = 0; o < p.n_obs; ++o) {
+                                const float g = gl[(int64_t)s * p.n_obs + o];
+                                const int sp = p.obs_sp[o];
+                                lam[sp] += alpha * g;
+                                cl += g * dX[sp];
+                            }
+                            const float c_tau = __fdividef(cl, tau);
+                            dt_dir -= c_tau;
+                            dtau_dir -= alpha * c_tau;
+                        }
+                    }
+                    dt_dir = __shfl_sync(0xffffffffu, dt_dir, 0);
+                    dtau_dir = __shfl_sync(0xffffffffu, dtau_dir, 0);
+                }
+                __syncwarp();
+                const float dtau = mu + dtau_dir;
+                const float dLda0 = -dtau * tau / a0;
+                // w_j = v_j . lambda (kept in c1 until the slots take it) and sum_j y~_j w_j
+                float Wp = 0.0f;
+                for (int b = lane; b < nb; b += 32) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = 4 * b + q - 1;
+                        if (j < 0 || j >= M) continue;
+                        const int pos = q * nb + b;
+                        const int4 rx = s_rx[pos];
+                        float w = 0.0f;
+                        for (int e = rx.z; e < rx.w; ++e) w += (float)stoich_delta(s_st[e]) * lam[stoich_species(s_st[e])];
+                        c1[pos] = w;
+                        Wp += (y[pos] * invZ) * w;
+                    }
+                }
+                const float Wbar = warp_sum(Wp);
+                __syncwarp();
+                // psi, dA and the reactant-slot contributions (choice path where a > 0, waiting-time path where
+                // the factor is not clipped)
+                for (int b = lane; b < nb; b += 32) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = 4 * b + q - 1;
+                        if (j < 0 || j >= M) continue;
+                        const int pos = q * nb + b;
+                        const float yj = y[pos] * invZ, a = aj[pos];
+                        const float psi = yj > 0.0f ? yj * (c1[pos] - Wbar) * invT : 0.0f;
+                        dA[pos] += psi + dLda0 * a;
+                        const float ctau = dLda0 * s_k[pos];
+                        const int4 rx = s_rx[pos];
+                        float v1 = 0.0f, v2 = 0.0f;
+                        if (rx.x >= 0) {
+                            const float x1 = Xk[rx.x];
+                            if (rx.y < 0) {
+                                v1 = sadj_first(x1, a, psi, x1 < 0.0f ? 0.0f : ctau);
+                            } else if (rx.y == rx.x) {
+                                v1 = sadj_homodimer(x1, a, hj[pos], psi, __fmul_rn(x1, x1 - 1.0f) < 0.0f ? 0.0f : ctau);
+                            } else {
+                                const float x2 = Xk[rx.y];
+                                const float cc = __fmul_rn(x1, x2) < 0.0f ? 0.0f : ctau;
+                                v1 = sadj_hetero(x1, x2, a, psi, cc);
+                                v2 = sadj_hetero(x2, x1, a, psi, cc);
+                            }
+                        }
+                        c1[pos] = v1;
+                        c2[pos] = v2;
+                    }
+                }
+                __syncwarp();
+                // lambda_s += the contributions of its reactant slots, one at a time in increasing j
+                for (int sp = lane; sp < N; sp += 32) {
+                    float acc = lam[sp];
+                    for (int e = s_inc_ptr[sp]; e < s_inc_ptr[sp + 1]; ++e) {
+                        const int slot = s_inc[e];  // 2 j + reactant slot
+                        acc += ((slot & 1) ? c2 : c1)[jpos(slot >> 1, nb)];
+                    }
+                    lam[sp] = acc;
+                }
+                mu += dt_dir;
+            }
+            __syncwarp();
+            if (kBin) {
+                if (lane == 0)
+                    bin_state_terms(addx, d_first, d_last, gl, p.bin_prefix, p.n_obs, s_hi + 1, s_top, draw, tau_k, gq,
+                                    gk);
+#pragma unroll
+                for (int q = 0; q < kBinMaxObs; ++q) gq[q] = gk[q];
+            } else if (lane == 0) {
+                for (int s = s_hi + 1; s <= s_top; ++s) {
+                    float coef = 1.0f;
+                    if (READOUT == SSA_READOUT_LINEAR && draw) {
+                        const float alpha = p.brk_a[(int64_t)s * n + i];
+                        if (alpha >= 0.0f) coef = 1.0f - alpha;
+                    }
+                    for (int o = 0; o < p.n_obs; ++o) lam[p.obs_sp[o]] += coef * gl[(int64_t)s * p.n_obs + o];
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0 && mism) atomicAdd(p.mismatch, mism);
 }
 
 // Per-trajectory body of the warp adjoint (all 32 lanes). X, lam, aj, lj, ct, dA are this warp's buffers;
