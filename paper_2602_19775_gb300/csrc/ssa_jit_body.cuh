@@ -33,6 +33,35 @@ __device__ __forceinline__ void jit_lam_add(float (&lam)[JN], int sp, float v)
         if (s == sp) lam[s] += v;
 }
 
+// Compensated accumulation for walks of ~1e6 steps (the wide-range adjoint): hi + lo carries the running sum
+// to about twice binary32's precision. Each step adds a small increment to a state adjoint that it changes by
+// ~1e-4 of its size, so a binary32 sum would drop most of the increment's bits every step; emulating that
+// rounding in the FP64 oracle moves its full-horizon gradient by ~1e-3. (Knuth's two-sum: the rounding error
+// of hi + v is exact in binary32.)
+__device__ __forceinline__ void acc2(float &hi, float &lo, float v)
+{
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+// hi <- the binary32 sum of hi + lo, lo <- its remainder (fast two-sum; |lo| is far below |hi|)
+__device__ __forceinline__ void fold2(float &hi, float &lo)
+{
+    const float s = __fadd_rn(hi, lo);
+    lo = __fsub_rn(lo, __fsub_rn(s, hi));
+    hi = s;
+}
+
+__device__ __forceinline__ void jit_lam_add2(float (&lam)[JN], float (&lo)[JN], int sp, float v)
+{
+#pragma unroll
+    for (int s = 0; s < JN; ++s)
+        if (s == sp) acc2(lam[s], lo[s], v);
+}
+
 // BIN readout state of a forward: cleared integrals, observed species (0 where the list is invalid)
 __device__ __forceinline__ void jit_bin_init(const FwdParams &p, bool bad_obs, float (&bacc)[kBinMaxObs],
                                              int (&osp)[kBinMaxObs])
@@ -442,9 +471,11 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
     const int L = (st == SSA_TRAJ_OK) ? d - 1 : d;  // index of the last visited state
     int X[JN];
     float lam[NT][JN];
+    float lam_lo[JN], mu_lo = 0.0f;  // WIDE: compensation terms of lam[0] and mu[0]
 #pragma unroll
     for (int s = 0; s < JN; ++s) {
         X[s] = p.xfinal[(int64_t)s * n + i];
+        lam_lo[s] = 0.0f;
 #pragma unroll
         for (int t = 0; t < NT; ++t) lam[t][s] = 0.0f;
     }
@@ -549,8 +580,11 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
                     for (int o = 0; o < p.n_obs; ++o) {
                         const float g = WIDE ? gl[(int64_t)s * p.n_obs + o] * inj : gl[(int64_t)s * p.n_obs + o];
                         const int sp = p.obs_sp[o];
+                        if (WIDE) jit_lam_add2(lam[0], lam_lo, sp, alpha * g);
+                        else {
 #pragma unroll
-                        for (int t = 0; t < NT; ++t) jit_lam_add(lam[t], sp, alpha * g);
+                            for (int t = 0; t < NT; ++t) jit_lam_add(lam[t], sp, alpha * g);
+                        }
                         c += g * (float)jit_dv(jk, sp);
                     }
                     const float c_tau = __fdividef(c, tau);
@@ -560,7 +594,7 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             }
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
-                const float dtau = mu[t] + dtau_dir;
+                const float dtau = WIDE ? (mu[t] + dtau_dir) + mu_lo : mu[t] + dtau_dir;
                 const float dLda0 = -dtau * tau / a0;
                 // pass 2: soft-sample weights y~_j ~ exp2((l_j - l_max)/T) and W = sum y~ w
                 float wr[JM], qr[JM];
@@ -582,8 +616,19 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
                     dAr[t][j] += psi[j] + dLda0 * a[j];
                     ctau[j] = dLda0 * kr[j];
                 }
-                jit_state_adj(X, a, h, psi, ctau, lam[t]);
-                mu[t] += dt_dir;  // t_{k+1} = t_k + tau_k
+                if (WIDE) {
+                    // this step's state-adjoint increment in binary32, then added to the compensated sum
+                    float dl[JN];
+#pragma unroll
+                    for (int s = 0; s < JN; ++s) dl[s] = 0.0f;
+                    jit_state_adj(X, a, h, psi, ctau, dl);
+#pragma unroll
+                    for (int s = 0; s < JN; ++s) acc2(lam[0][s], lam_lo[s], dl[s]);
+                    acc2(mu[0], mu_lo, dt_dir);  // t_{k+1} = t_k + tau_k
+                } else {
+                    jit_state_adj(X, a, h, psi, ctau, lam[t]);
+                    mu[t] += dt_dir;  // t_{k+1} = t_k + tau_k
+                }
             }
         }
         if (kBin) {
@@ -602,10 +647,18 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
                 }
                 for (int o = 0; o < p.n_obs; ++o) {
                     const float g = WIDE ? gl[(int64_t)s * p.n_obs + o] * inj : gl[(int64_t)s * p.n_obs + o];
+                    if (WIDE) jit_lam_add2(lam[0], lam_lo, p.obs_sp[o], coef * g);
+                    else {
 #pragma unroll
-                    for (int t = 0; t < NT; ++t) jit_lam_add(lam[t], p.obs_sp[o], coef * g);
+                        for (int t = 0; t < NT; ++t) jit_lam_add(lam[t], p.obs_sp[o], coef * g);
+                    }
                 }
             }
+        }
+        if (WIDE) {  // keep the binary32 parts the rounded sums, which the next step's w_j and dtau read
+#pragma unroll
+            for (int s = 0; s < JN; ++s) fold2(lam[0][s], lam_lo[s]);
+            fold2(mu[0], mu_lo);
         }
         if (ck_off == 0) {
             const int *ck = p.ckpt + (int64_t)ck_row * JN * n + i;
@@ -623,8 +676,12 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
                     const int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;  // 32 <= e <= 127
                     const float f = ldexpf(1.0f, -e);
                     mu[0] *= f;
+                    mu_lo *= f;
 #pragma unroll
-                    for (int s = 0; s < JN; ++s) lam[0][s] *= f;
+                    for (int s = 0; s < JN; ++s) {
+                        lam[0][s] *= f;
+                        lam_lo[s] *= f;
+                    }
 #pragma unroll
                     for (int j = 0; j < JM; ++j) dAr[0][j] *= f;
                     sc += e;
