@@ -675,7 +675,10 @@ __global__ void __launch_bounds__(128, 5) grn_soft_adj_kernel(const GrnParams p)
 // ---------------------------------------------------------------------------------------------
 // backward: one warp per trajectory, reverse walk
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
+#ifndef SSA_GRN_ADJ_BLOCKS
+#define SSA_GRN_ADJ_BLOCKS 6  // resident blocks per SM the adjoint is compiled for (36 KB of shared memory each)
+#endif
+__global__ void __launch_bounds__(128, SSA_GRN_ADJ_BLOCKS) grn_adj_kernel(const GrnParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, W = blockDim.x >> 5;
@@ -684,9 +687,9 @@ __global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
     float *s_b2 = s_d + nd;
     const int ndp = (nd + 3) & ~3, nhp = (nh + 3) & ~3, nop = (no + 3) & ~3;
     // per warp (words): X, lam, ctd [ndp each], aH, G1 [nhp each], E2acc [2 nop], aO, G2, R, db2 [nop each],
-    // aj, lj [Mp each], dlogd [ndp]. dL/dW2 goes to the trajectory's own row of p.dW2t (global, L2-resident
-    // while the warp works on it), which keeps the per-warp shared memory independent of n_out x n_hid.
-    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + 6 * (size_t)nop + 2 * (size_t)Mp;
+    // lj [Mp], dlogd [ndp]. dL/dW2 goes to the trajectory's own row of p.dW2t (global, L2-resident while the
+    // warp works on it), which keeps the per-warp shared memory independent of n_out x n_hid.
+    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + 6 * (size_t)nop + (size_t)Mp;
     unsigned char *wb = smem + ((4 * ((size_t)nd + nop) + 15) & ~(size_t)15);  // shared-space offsets (see the forward)
     float *wbase = reinterpret_cast<float *>(wb) + wib * per_warp;
     int *X = reinterpret_cast<int *>(wbase);
@@ -699,8 +702,7 @@ __global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
     float *G2 = aO + nop;
     float *R = G2 + nop;
     float *db2 = R + nop;
-    float *aj = db2 + nop;
-    float *lj = aj + Mp;
+    float *lj = db2 + nop;
     float *dlogd = lj + Mp;
     const int *__restrict__ W2fix = p.W2fix;
     const float *__restrict__ W2f = p.W2f;
@@ -787,10 +789,7 @@ __global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
                             l = __log2f(a) - __log2f(E);
                             lmaxp = fmaxf(lmaxp, l);
                         }
-                        if (j < p.M) {
-                            aj[j] = a;
-                            lj[j] = l;
-                        }
+                        if (j < p.M) lj[j] = l;
                     }
                 }
                 warp_race_combine(ab, Eb, jb);
@@ -831,7 +830,7 @@ __global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
                 for (int s2 = lane; s2 < nd; s2 += 32) {
                     const float psi = lj[nd + s2] * cz * (-lam[s2] - Wbar);
                     dlogd[s2] += psi;
-                    ctd[s2] = aj[nd + s2] > 0.0f ? __fdividef(psi, int2f(X[s2])) : 0.0f;
+                    ctd[s2] = X[s2] > 0 ? __fdividef(psi, int2f(X[s2])) : 0.0f;  // a = d X > 0 where X > 0
                 }
                 __syncwarp();
                 for (int o = lane; o < no; o += 32) {
@@ -890,7 +889,7 @@ __global__ void __launch_bounds__(128, 5) grn_adj_kernel(const GrnParams p)
         float acc = 0.0f;
         for (int w = 0; w < W; ++w) {
             const float *wp = base0 + w * per_warp;
-            acc += q < no ? wp[3 * ndp + 2 * nhp + 5 * nop + q] : wp[3 * ndp + 2 * nhp + 6 * nop + 2 * Mp + (q - no)];
+            acc += q < no ? wp[3 * ndp + 2 * nhp + 5 * nop + q] : wp[3 * ndp + 2 * nhp + 6 * nop + Mp + (q - no)];
         }
         p.partial[(int64_t)blockIdx.x * red + q] = acc;
     }
@@ -1041,7 +1040,7 @@ constexpr size_t kGrnMaxSmem = 227 * 1024;
 size_t grn_adj_smem(const ssa_grn *g)
 {
     const int ndp = (g->n_dyn + 3) & ~3, nhp = (g->n_hid + 3) & ~3, nop = (g->n_out + 3) & ~3;
-    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + 6 * (size_t)nop + 2 * (size_t)g->Mp;
+    const size_t per_warp = 4 * (size_t)ndp + 2 * (size_t)nhp + 6 * (size_t)nop + (size_t)g->Mp;
     return 4 * ((size_t)g->n_dyn + nop) + 16 + 4 * (size_t)kGrnWarps * per_warp;
 }
 
