@@ -462,6 +462,18 @@ ssa_status ssa_batch_set_plan(ssa_batch *batch, int32_t item, int32_t threads_pe
                               int32_t ckpt_interval, double est_draws);
 
 /* ssa_batch_workspace_bytes -- device workspace ssa_batch_run needs under the current plan. */
+/*
+ * ssa_batch_set_soft -- soft = 1: every item runs the soft forward of Eq. 4 (Section 3.3, as
+ * SSA_SELECT_SOFT) at the batch temperature, recorded, and the adjoint gives the exact gradient of that
+ * relaxed model at the same temperature (the per-item dL/dlog k). Every item runs as warp units with a
+ * float checkpoint every 8 steps (ckpt_interval and the autotuner's choices do not apply; the autotuner
+ * returns without work); observables are float for every readout; there is no event log
+ * (ssa_batch_item_events returns SSA_ERR_STATE). soft = 0 restores the Gumbel-max batch. Call before a
+ * run: the next run rebuilds the plan and the workspace size changes (ssa_batch_workspace_bytes).
+ * Errors: SSA_ERR_INVALID_ARG, SSA_ERR_UNSUPPORTED (an item asks for threads_per_traj = 1).
+ */
+ssa_status ssa_batch_set_soft(ssa_batch *batch, int32_t soft);
+
 size_t ssa_batch_workspace_bytes(const ssa_batch *batch);
 
 /*

@@ -30,7 +30,7 @@ EXPORTS = (
     "ssa_ensemble_mean_workspace_bytes", "ssa_ensemble_mean", "ssa_ensemble_mean_static", "ssa_philox_uniforms",
     "ssa_bf16_gemm", "ssa_bf16_gemm_work_words", "ssa_pipe_rates", "ssa_last_error", "ssa_grn_create", "ssa_grn_destroy",
     "ssa_grn_workspace_bytes", "ssa_grn_forward", "ssa_grn_backward", "ssa_grn_activations",
-    "ssa_batch_create", "ssa_batch_destroy", "ssa_batch_set_plan", "ssa_batch_workspace_bytes", "ssa_batch_run",
+    "ssa_batch_create", "ssa_batch_destroy", "ssa_batch_set_plan", "ssa_batch_set_soft", "ssa_batch_workspace_bytes", "ssa_batch_run",
     "ssa_batch_item_outputs", "ssa_batch_autotune", "ssa_batch_item_variant", "ssa_batch_item_events",
     "ssa_batch_item_brackets", "ssa_batch_item_ckpt_interval", "ssa_run_variant", "ssa_network_specialize", "ssa_exp_variates",
 )
@@ -118,6 +118,7 @@ def _declare(lib):
         "ssa_batch_create": (i32, [ctypes.POINTER(BatchItem), i32, i32, f32, ctypes.POINTER(p)]),
         "ssa_batch_destroy": (None, [p]),
         "ssa_batch_set_plan": (i32, [p, i32, i32, i32, f64]),
+        "ssa_batch_set_soft": (i32, [p, i32]),
         "ssa_batch_workspace_bytes": (sz, [p]),
         "ssa_batch_run": (i32, [p, p, sz, i32, p]),
         "ssa_batch_item_outputs": (i32, [p, i32, p, p, p, p]),

@@ -131,7 +131,7 @@ __device__ __forceinline__ void batch_fwd_thread_unit(const BatchItem &b, const 
 
 // VARIANT 1 runs the thread units, VARIANT 32 the warp units (separate kernels, so that the warp
 // kernel is not compiled with the register budget of the unrolled thread bodies)
-template <int READOUT, int VARIANT>
+template <int READOUT, int VARIANT, bool SOFT = false>
 __global__ void __launch_bounds__(32 * kBatchWarps, VARIANT == 1 ? 1 : kBatchWarpBlocks) batch_fwd_kernel(const BatchItem *items, const BatchUnit *units,
                                                                     int n_units, int *counter, int x_words)
 {
@@ -152,6 +152,16 @@ __global__ void __launch_bounds__(32 * kBatchWarps, VARIANT == 1 ? 1 : kBatchWar
             case 4: batch_fwd_thread_unit<READOUT, 4>(b, u, Xw); break;
             case 8: batch_fwd_thread_unit<READOUT, 8>(b, u, Xw); break;
             default: batch_fwd_thread_unit<READOUT, 16>(b, u, Xw); break;
+            }
+        } else if constexpr (SOFT) {
+            // the soft forward (Eq. 4), recorded: per warp X, dX [Npad] and the keys / weights [Mp] (floats)
+            const FwdParams &p = b.f;
+            float *Xf = reinterpret_cast<float *>(Xw);
+            const int Npad = (p.N + 3) & ~3;
+            for (int c = 0; c < u.count; ++c) {
+                warp_soft_fwd_body<READOUT, true>(p, p.rx, p.k_rates, p.upd, Xf, Xf + Npad, Xf + 2 * Npad,
+                                                  u.traj_begin + c);
+                __syncwarp();
             }
         } else {
             const FwdParams &p = b.f;
@@ -194,7 +204,7 @@ __device__ __forceinline__ void batch_adj_thread_unit(const BatchItem &b, const 
     }
 }
 
-template <int READOUT, int VARIANT>
+template <int READOUT, int VARIANT, bool SOFT = false>
 __global__ void __launch_bounds__(32 * kBatchWarps, VARIANT == 1 ? 1 : kBatchWarpBlocks) batch_adj_kernel(const BatchItem *items, const BatchUnit *units,
                                                                     int n_units, int *counter, int w_words)
 {
@@ -224,20 +234,44 @@ __global__ void __launch_bounds__(32 * kBatchWarps, VARIANT == 1 ? 1 : kBatchWar
             const int *st = reinterpret_cast<const int *>(tb + 16 * p.Mp);
             const int *inc_ptr = reinterpret_cast<const int *>(tb + p.inc_off);
             const int *inc = reinterpret_cast<const int *>(tb + p.inc_list_off);
-            int *X = reinterpret_cast<int *>(wsm);
-            float *lam = wsm + Npad;
-            float *aj = lam + Npad;
-            float *lj = aj + p.Mp;
-            float *ct = lj + p.Mp;
-            float *dA = ct + p.Mp;
-            for (int j = lane; j < p.Mp; j += 32) dA[j] = 0.0f;
-            __syncwarp();
-            for (int c = 0; c < u.count; ++c) {
-                const int64_t i = u.traj_begin + c;
-                const int stt = p.status[i];
-                if (stt == SSA_TRAJ_OK || stt == SSA_TRAJ_ABSORBED || stt == SSA_TRAJ_STEP_CAP)
-                    warp_adj_body<READOUT>(p, rx, st, inc_ptr, inc, p.k_rates, X, lam, aj, lj, ct, dA, i, stt);
+            float *dA;
+            if constexpr (SOFT) {
+                // the soft forward's gradient: Xs [kSoftK][Npad], lam, dX [Npad]; a, h, y, c1, c2, dA [Mp]
+                float *Xs = wsm;
+                float *lam = Xs + kSoftK * Npad;
+                float *dX = lam + Npad;
+                float *aj = dX + Npad;
+                float *hj = aj + p.Mp;
+                float *y = hj + p.Mp;
+                float *c1 = y + p.Mp;
+                float *c2 = c1 + p.Mp;
+                dA = c2 + p.Mp;
+                for (int j = lane; j < p.Mp; j += 32) dA[j] = 0.0f;
                 __syncwarp();
+                for (int c = 0; c < u.count; ++c) {
+                    const int64_t i = u.traj_begin + c;
+                    const int stt = p.status[i];
+                    if (stt == SSA_TRAJ_OK || stt == SSA_TRAJ_ABSORBED || stt == SSA_TRAJ_STEP_CAP)
+                        warp_soft_adj_body<READOUT>(p, rx, st, inc_ptr, inc, p.k_rates, b.f.upd, Xs, lam, dX, aj, hj, y,
+                                                    c1, c2, dA, i, stt);
+                    __syncwarp();
+                }
+            } else {
+                int *X = reinterpret_cast<int *>(wsm);
+                float *lam = wsm + Npad;
+                float *aj = lam + Npad;
+                float *lj = aj + p.Mp;
+                float *ct = lj + p.Mp;
+                dA = ct + p.Mp;
+                for (int j = lane; j < p.Mp; j += 32) dA[j] = 0.0f;
+                __syncwarp();
+                for (int c = 0; c < u.count; ++c) {
+                    const int64_t i = u.traj_begin + c;
+                    const int stt = p.status[i];
+                    if (stt == SSA_TRAJ_OK || stt == SSA_TRAJ_ABSORBED || stt == SSA_TRAJ_STEP_CAP)
+                        warp_adj_body<READOUT>(p, rx, st, inc_ptr, inc, p.k_rates, X, lam, aj, lj, ct, dA, i, stt);
+                    __syncwarp();
+                }
             }
             float *slot = p.partial + b.slot_off + (int64_t)u.slot * p.M;
             const int nb = (p.M + 4) >> 2;
@@ -290,6 +324,7 @@ struct ssa_batch {
     std::vector<int> variant, mc, K;
     std::vector<double> est_draws;
     double ckpt_scale = 1.0;  // the autotuner's multiple of the default checkpoint interval
+    bool soft = false;        // every item runs the soft forward (Eq. 4) and its exact gradient, on warp units
     int readout;
     float temperature;
     // laid out in the caller's workspace by the first run with it
@@ -458,10 +493,36 @@ extern "C" ssa_status ssa_batch_set_plan(ssa_batch *bt, int32_t item, int32_t th
     if (threads_per_traj != 1 && threads_per_traj != 32) return set_error(SSA_ERR_INVALID_ARG, "threads_per_traj 1 or 32");
     if (threads_per_traj == 1 && !thread_eligible(bt->items[item].net))
         return set_error(SSA_ERR_UNSUPPORTED, "thread variant in a batch needs N <= 16 and M <= 16");
+    if (threads_per_traj == 1 && bt->soft)
+        return set_error(SSA_ERR_UNSUPPORTED, "a soft batch runs warp units only");
     if (ckpt_interval < 8 || ckpt_interval % 8) return set_error(SSA_ERR_INVALID_ARG, "ckpt_interval: multiple of 8");
     bt->variant[item] = threads_per_traj;
-    bt->K[item] = ckpt_interval;
+    bt->K[item] = bt->soft ? kSoftK : ckpt_interval;
     if (est_draws > 0) bt->est_draws[item] = est_draws;
+    bt->ready = false;
+    bt->ws = nullptr;
+    drop_graph(bt);
+    return SSA_OK;
+}
+
+extern "C" ssa_status ssa_batch_set_soft(ssa_batch *bt, int32_t soft)
+{
+    if (!bt) return set_error(SSA_ERR_INVALID_ARG, "batch is NULL");
+    if (soft != 0 && soft != 1) return set_error(SSA_ERR_INVALID_ARG, "soft must be 0 or 1");
+    for (size_t it = 0; soft && it < bt->items.size(); ++it)
+        if (bt->items[it].threads_per_traj == 1)
+            return set_error(SSA_ERR_UNSUPPORTED, "a soft batch runs warp units only (an item asks for threads_per_traj = 1)");
+    bt->soft = soft != 0;
+    for (size_t it = 0; it < bt->items.size(); ++it) {
+        const ssa_batch_item &b = bt->items[it];
+        if (bt->soft) {
+            bt->variant[it] = 32;
+            bt->K[it] = kSoftK;  // float checkpoints every 8 steps, re-run by the adjoint
+        } else {
+            bt->variant[it] = b.threads_per_traj ? b.threads_per_traj : (thread_eligible(b.net) ? 1 : 32);
+            bt->K[it] = b.ckpt_interval ? b.ckpt_interval : default_ckpt(b.net);
+        }
+    }
     bt->ready = false;
     bt->ws = nullptr;
     drop_graph(bt);
@@ -549,6 +610,9 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
         a.dl_dobs = b.dl_dobs;
         a.dl_stride = b.dl_traj_stride;
         a.invT = 1.0f / bt->temperature;
+        p.invT = bt->soft ? a.invT : 0.0f;  // the soft forward's T is the gradient's
+        p.upd = net->d_upd;
+        p.upd_words = net->upd_words;
         a.partial = partial;
         a.mismatch = flag + 2;
         a.err = flag + 1;
@@ -625,21 +689,28 @@ static ssa_status batch_build(ssa_batch *bt, void *workspace, size_t bytes, cuda
     const int maxNpad = (maxNw + 3) & ~3;
     bt->x_words[0] = kBatchThreadMaxN * 32;
     bt->w_words[0] = 3 * kBatchThreadMaxN * 32;
-    bt->x_words[1] = maxNpad;
-    bt->w_words[1] = 2 * maxNpad + 4 * maxMpw;
+    bt->x_words[1] = bt->soft ? 2 * maxNpad + maxMpw : maxNpad;
+    bt->w_words[1] = bt->soft ? (kSoftK + 2) * maxNpad + 6 * maxMpw : 2 * maxNpad + 4 * maxMpw;
     int dev = 0, sms = 0, limit = 0;
     CUDA_TRY_B(cudaGetDevice(&dev));
     CUDA_TRY_B(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY_B(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int ro = bt->readout;
+    const bool sf = bt->soft;
     const void *fk[2] = {ro == 0 ? (const void *)batch_fwd_kernel<0, 1>
                                  : ro == 1 ? (const void *)batch_fwd_kernel<1, 1> : (const void *)batch_fwd_kernel<2, 1>,
-                         ro == 0 ? (const void *)batch_fwd_kernel<0, 32>
-                                 : ro == 1 ? (const void *)batch_fwd_kernel<1, 32> : (const void *)batch_fwd_kernel<2, 32>};
+                         sf ? (ro == 0 ? (const void *)batch_fwd_kernel<0, 32, true>
+                                       : ro == 1 ? (const void *)batch_fwd_kernel<1, 32, true>
+                                                 : (const void *)batch_fwd_kernel<2, 32, true>)
+                            : (ro == 0 ? (const void *)batch_fwd_kernel<0, 32>
+                                       : ro == 1 ? (const void *)batch_fwd_kernel<1, 32> : (const void *)batch_fwd_kernel<2, 32>)};
     const void *ak[2] = {ro == 0 ? (const void *)batch_adj_kernel<0, 1>
                                  : ro == 1 ? (const void *)batch_adj_kernel<1, 1> : (const void *)batch_adj_kernel<2, 1>,
-                         ro == 0 ? (const void *)batch_adj_kernel<0, 32>
-                                 : ro == 1 ? (const void *)batch_adj_kernel<1, 32> : (const void *)batch_adj_kernel<2, 32>};
+                         sf ? (ro == 0 ? (const void *)batch_adj_kernel<0, 32, true>
+                                       : ro == 1 ? (const void *)batch_adj_kernel<1, 32, true>
+                                                 : (const void *)batch_adj_kernel<2, 32, true>)
+                            : (ro == 0 ? (const void *)batch_adj_kernel<0, 32>
+                                       : ro == 1 ? (const void *)batch_adj_kernel<1, 32> : (const void *)batch_adj_kernel<2, 32>)};
     for (int v = 0; v < 2; ++v) {
         bt->fwd_smem[v] = (size_t)kBatchWarps * (kItemWords + bt->x_words[v]) * 4;
         bt->adj_smem[v] = (size_t)kBatchWarps * (kItemWords + bt->w_words[v]) * 4;
@@ -673,7 +744,12 @@ static void batch_launch_kernels(const ssa_batch *bt, cudaStream_t st)
         batch_adj_kernel<R, 1><<<bt->adj_blocks[0], blk, bt->adj_smem[0], st>>>(bt->d_items, u0, bt->n_units[0],
                                                                               bt->d_counters + 1, bt->w_words[0]);
     }
-    if (bt->n_units[1] > 0) {  // warp units
+    if (bt->n_units[1] > 0 && bt->soft) {  // warp units of a soft batch
+        batch_fwd_kernel<R, 32, true><<<bt->fwd_blocks[1], blk, bt->fwd_smem[1], st>>>(
+            bt->d_items, u1, bt->n_units[1], bt->d_counters + 2, bt->x_words[1]);
+        batch_adj_kernel<R, 32, true><<<bt->adj_blocks[1], blk, bt->adj_smem[1], st>>>(
+            bt->d_items, u1, bt->n_units[1], bt->d_counters + 3, bt->w_words[1]);
+    } else if (bt->n_units[1] > 0) {  // warp units
         batch_fwd_kernel<R, 32><<<bt->fwd_blocks[1], blk, bt->fwd_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
                                                                                bt->d_counters + 2, bt->x_words[1]);
         batch_adj_kernel<R, 32><<<bt->adj_blocks[1], blk, bt->adj_smem[1], st>>>(bt->d_items, u1, bt->n_units[1],
@@ -757,6 +833,7 @@ extern "C" ssa_status ssa_batch_item_events(const ssa_batch *bt, int32_t item, i
 {
     if (!bt || !bt->ready || item < 0 || item >= (int)bt->items.size() || !events_out || stride < 1)
         return set_error(SSA_ERR_INVALID_ARG, "bad arguments");
+    if (bt->soft) return set_error(SSA_ERR_STATE, "a soft batch keeps no event log");
     const FwdParams &p = bt->h_items[item].f;
     CUDA_TRY_B(launch_unpack_events(p.ev, p.draws, p.n_traj, stride, events_out, static_cast<cudaStream_t>(stream)));
     return SSA_OK;
@@ -781,6 +858,11 @@ extern "C" ssa_status ssa_batch_item_brackets(const ssa_batch *bt, int32_t item,
 extern "C" ssa_status ssa_batch_autotune(ssa_batch *bt, int64_t pilot_traj, void *stream, double *host_draws_out)
 {
     if (!bt || pilot_traj < 1) return set_error(SSA_ERR_INVALID_ARG, "bad batch or pilot size");
+    if (bt->soft) {  // warp units and a checkpoint every 8 steps: nothing to choose
+        if (host_draws_out)
+            for (size_t it = 0; it < bt->items.size(); ++it) host_draws_out[it] = bt->est_draws[it];
+        return SSA_OK;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t n_items = bt->items.size();
     std::vector<int64_t> np(n_items);

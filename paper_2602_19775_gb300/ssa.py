@@ -267,13 +267,14 @@ class Batch:
     optionally traj_offset, max_steps, ckpt_interval, threads_per_traj, shared_dl (True: one upstream
     gradient [S, n_obs] for all trajectories). The batch owns fixed device tensors per item --
     log_rates[i], obs[i], dl_dobs[i], dtheta[i] -- whose addresses are baked into the plan: write new
-    parameters or upstream gradients into them in place (copy_) between runs.
+    parameters or upstream gradients into them in place (copy_) between runs. soft: every item runs the soft
+    forward of Eq. 4 at `temperature` and the exact gradient of that relaxed model (float observables).
     """
 
-    def __init__(self, items, readout="hold", temperature=0.5, device=None):
+    def __init__(self, items, readout="hold", temperature=0.5, device=None, soft=False):
         device = torch.device(device) if device is not None else torch.device("cuda")
         ro = READOUTS[readout] if isinstance(readout, str) else int(readout)
-        odt = torch.int32 if ro == _lib.SSA_READOUT_HOLD else torch.float32
+        odt = torch.int32 if ro == _lib.SSA_READOUT_HOLD and not soft else torch.float32
         self.readout, self.device = ro, device
         self.log_rates, self.obs, self.dl_dobs, self.dtheta, self._keep = [], [], [], [], []
         self.nets = []
@@ -318,6 +319,8 @@ class Batch:
         h = ctypes.c_void_p()
         check(_lib.lib().ssa_batch_create(arr, len(items), ro, ctypes.c_float(float(temperature)), ctypes.byref(h)))
         self.handle = h
+        if soft:  # the soft forward of Eq. 4 and the gradient of that relaxed model (ssa_batch_set_soft)
+            check(_lib.lib().ssa_batch_set_soft(h, 1))
         self.workspace = None
 
     def __len__(self):

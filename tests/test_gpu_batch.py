@@ -379,3 +379,43 @@ def test_batch_bin_readout_matches_single_network_entry_points(S, specs, shared)
     b.run()
     torch.cuda.synchronize()
     _check_against_single(S, b, specs, nets, items, 0.6, readout="bin")
+
+
+def test_soft_batch_matches_single_network_warp_calls(S, specs):
+    """ssa_batch_set_soft: every item runs the soft forward (Eq. 4) and the exact gradient of the relaxed model
+    as warp units; observables, draws and status equal the single-network warp soft calls bit for bit (the same
+    per-trajectory bodies), gradients to binary32 summation order. T = 2, where these relaxed models are well
+    conditioned."""
+    T = 2.0
+    sp = [specs[0], specs[1], specs[3], specs[5], specs[6]]
+    nets = [S.Network(s[0]) for s in sp]
+    items = _items(S, sp, nets)
+    for it in items:
+        it["threads_per_traj"] = 0
+    b = S.Batch(items, readout="linear", temperature=T, soft=True)
+    assert all(b.variant(q) == 32 for q in range(len(sp)))
+    _fill_dl(b, sp)
+    b.run()
+    for q in range(len(sp)):
+        it = items[q]
+        fw = S.forward(nets[q], torch.tensor(it["log_rates"], device="cuda"), it["n_traj"], it["x0"], it["t_end"],
+                       it["sample_times"], it["obs_species"], it["seed"], readout="linear", record=True,
+                       max_steps=it["max_steps"], traj_offset=it["traj_offset"], threads_per_traj=32,
+                       selector="soft", temperature=T)
+        draws, status, mism = b.outputs(q)
+        assert mism == 0
+        assert torch.equal(b.obs[q], fw.obs), q
+        assert torch.equal(draws, fw.draws) and torch.equal(status, fw.status), q
+        if it["n_traj"] == 0:
+            assert torch.all(b.dtheta[q] == 0)
+            continue
+        g = S.backward(fw, b.dl_dobs[q], T).double().cpu().numpy()
+        gb = b.dtheta[q].double().cpu().numpy()
+        scale = max(np.abs(g).max(), 1e-12)
+        assert np.abs(gb - g).max() <= 1e-4 * scale, (q, np.abs(gb - g).max(), scale)
+    # no event log in a soft batch; threads are refused
+    from paper_2602_19775_gb300 import SSAError
+    with pytest.raises(SSAError):
+        b.events(0, 64)
+    with pytest.raises(SSAError):
+        b.set_plan(0, 1, 64)
