@@ -41,6 +41,7 @@ cudaError_t launch_column_sums(const float *x, int64_t n_rows, int64_t row_len, 
 
 constexpr int kGrnLimbs = 8;       // 6-bit limbs of W1 on one grid: 48 bits of dynamic range
 constexpr int kGrnLimbBits = 6;
+constexpr int kGrnOutBatch = 12;   // output counts up to this take the adjoint's batched W2 column loads
 constexpr int kGrnWarps = 4;
 
 struct GrnParams {
@@ -838,11 +839,25 @@ __global__ void __launch_bounds__(128, SSA_GRN_ADJ_BLOCKS) grn_adj_kernel(const 
                     R[o] += G2[o];
                 }
                 // lam_h += (W2^T G2)_h for the hidden genes; every species adds its degradation term
-                for (int h = lane; h < nh; h += 32) {
-                    float acc = ctd[h];
-#pragma unroll 2
-                    for (int o = 0; o < no; ++o) acc = fmaf(__ldg(W2f + o * nh + h), G2[o], acc);
-                    lam[h] += acc;
+                if (no <= kGrnOutBatch) {
+                    // up to kGrnOutBatch outputs: the column's loads are issued together (one L1 latency per
+                    // hidden gene instead of one per output), then summed in output order
+                    for (int h = lane; h < nh; h += 32) {
+                        float w[kGrnOutBatch];
+#pragma unroll
+                        for (int o = 0; o < kGrnOutBatch; ++o) w[o] = o < no ? __ldg(W2f + o * nh + h) : 0.0f;
+                        float acc = ctd[h];
+#pragma unroll
+                        for (int o = 0; o < kGrnOutBatch; ++o)
+                            if (o < no) acc = fmaf(w[o], G2[o], acc);
+                        lam[h] += acc;
+                    }
+                } else {
+                    for (int h = lane; h < nh; h += 32) {
+                        float acc = ctd[h];
+                        for (int o = 0; o < no; ++o) acc = fmaf(__ldg(W2f + o * nh + h), G2[o], acc);
+                        lam[h] += acc;
+                    }
                 }
                 for (int s2 = nh + lane; s2 < nd; s2 += 32) lam[s2] += ctd[s2];
             }
