@@ -819,20 +819,31 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
             for (int b = lane; b < v.nb; b += 32) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
+                    // predicated rather than branched (the lanes hold reactions with 1 to 4 stoichiometric
+                    // entries); the slots of j = -1 and j >= M hold no entries, and their weight is 0
                     const int j = 4 * b + q - 1;
-                    if (j < 0 || j >= M) continue;
+                    const bool live = j >= 0 && j < M;
                     const int pos = q * v.nb + b;
-                    const float l = lj[pos];
+                    const float l = live ? lj[pos] : -CUDART_INF_F;
                     const float qv = l == -CUDART_INF_F ? 0.0f : exp2f((l - lmax) * invT);
-                    lj[pos] = qv;
-                    if (qv > 0.0f) {
-                        const int4 rx = s_rx[pos];
-                        float w = 0.0f;
+                    const int4 rx = s_rx[pos];
+                    float w = 0.0f;
+                    if (rx.w - rx.z <= 4) {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            if (rx.z + t < rx.w) {
+                                const int se = s_st[rx.z + t];
+                                w += (float)stoich_delta(se) * lam[stoich_species(se)];
+                            }
+                    } else {
                         for (int e = rx.z; e < rx.w; ++e) w += (float)stoich_delta(s_st[e]) * lam[stoich_species(s_st[e])];
-                        ct[pos] = w;  // kept for pass 3, which overwrites the slot afterwards
-                        Zp += qv;
-                        Wp += qv * w;
                     }
+                    if (live) {
+                        lj[pos] = qv;
+                        ct[pos] = w;  // kept for pass 3, which overwrites the slot afterwards
+                    }
+                    Zp += qv;  // + 0 where qv = 0: the same bits
+                    Wp += qv > 0.0f ? qv * w : 0.0f;
                 }
             }
             const float Z = warp_sum(Zp), Wq = warp_sum(Wp);
