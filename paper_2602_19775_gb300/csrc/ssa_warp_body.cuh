@@ -50,26 +50,22 @@ __device__ __forceinline__ void warp_step_eval(const FwdParamsView &v, int k, co
             if (b >= v.nb) break;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                // predicated rather than branched: word 0 of lane 0's first block (j = -1) drives the waiting
+                // time, and its table slot, like the padded ones (j >= M), has rate 0, so it adds 0 to a0, never
+                // wins the race (a_j E_b > a_b E_j fails for a_j = 0) and its key is -inf (log2 0)
                 const int j = 4 * b + q - 1;
-                if (j < 0) {
-                    E0 = E[t][0];
-                    continue;
-                }
-                // tables in lane-major order; padded entries (j >= M) have rate 0
+                if (q == 0 && j < 0) E0 = E[t][0];
                 const int pos = q * v.nb + b;
                 const float a = __fmul_rn(v.s_k[pos], mass_action_h_sel(v.s_rx[pos], X));
                 a0p = __fadd_rn(a0p, a);
-                float l = -CUDART_INF_F;
-                if (a > 0.0f) {
-                    race(a, E[t][q], j, ab, Eb, jb);
-                    if (STORE) {
-                        l = __log2f(a) - __log2f(E[t][q]);
-                        lmax = fmaxf(lmax, l);
+                race(a, E[t][q], j, ab, Eb, jb);
+                if (STORE) {
+                    const float l = __log2f(a) - __log2f(E[t][q]);
+                    lmax = fmaxf(lmax, l);
+                    if (j >= 0 && j < v.M) {
+                        aj[pos] = a;
+                        lj[pos] = l;
                     }
-                }
-                if (STORE && j < v.M) {
-                    aj[pos] = a;
-                    lj[pos] = l;
                 }
             }
         }
@@ -853,13 +849,13 @@ __device__ __forceinline__ void warp_adj_body(const AdjParams &p, const int4 *s_
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int j = 4 * b + q - 1;
-                    if (j < 0 || j >= M) continue;
+                    const bool live = j >= 0 && j < M;  // predicated: the other slots write zero contributions
                     const int pos = q * v.nb + b;
                     const int4 rx = s_rx[pos];
-                    const float qv = lj[pos], a = aj[pos];
+                    const float qv = live ? lj[pos] : 0.0f, a = live ? aj[pos] : 0.0f;
                     float psi = 0.0f;
                     if (qv > 0.0f) psi = qv * invZ * (ct[pos] - Wbar) * invT;  // w_j from pass 2
-                    dA[pos] += psi + dLda0 * a;
+                    if (live) dA[pos] += psi + dLda0 * a;
                     // d log a_j / dX and d a_j / dX of each reactant slot, formed with selects (the lanes hold
                     // reactions of different orders): first order is the hetero form with x2 = 1
                     const bool has1 = rx.x >= 0, has2 = rx.y >= 0, homo = has2 && rx.y == rx.x;
