@@ -250,11 +250,14 @@ __global__ void __launch_bounds__(128) grn_fwd_kernel(const GrnParams p, int rec
             const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                // predicated: every word's variate is formed (the warp forms it whenever one lane needs it), word
+                // 0 of lane 0's first block is E0, and j = -1 takes part with rate 0 (adds 0, never wins)
                 const int j = 4 * b + q - 1;
-                if (j < 0) { E0 = neg_log_unit(u01(r.x)); continue; }
-                const float a = grn_prop(p, j, aH, aO, X, s_d);
+                const float E = neg_log_unit(u01(word_of(r, q)));
+                if (q == 0 && j < 0) E0 = E;
+                const float a = j < 0 ? 0.0f : grn_prop(p, max(j, 0), aH, aO, X, s_d);
                 a0p = __fadd_rn(a0p, a);
-                if (a > 0.0f) race(a, neg_log_unit(u01(word_of(r, q))), j, ab, Eb, jb);
+                race(a, E, j, ab, Eb, jb);
             }
         }
         const float a0 = warp_sum(a0p);
@@ -780,17 +783,14 @@ __global__ void __launch_bounds__(128, SSA_GRN_ADJ_BLOCKS) grn_adj_kernel(const 
                     const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
+                        // predicated as in the forward (j = -1 and a = 0 add nothing and have key -inf)
                         const int j = 4 * b + q - 1;
-                        if (j < 0) continue;
-                        const float a = grn_prop(p, j, aH, aO, X, s_d);
-                        float l = -CUDART_INF_F;
-                        if (a > 0.0f) {
-                            const float E = neg_log_unit(u01(word_of(r, q)));
-                            race(a, E, j, ab, Eb, jb);
-                            l = __log2f(a) - __log2f(E);
-                            lmaxp = fmaxf(lmaxp, l);
-                        }
-                        if (j < p.M) lj[j] = l;
+                        const float E = neg_log_unit(u01(word_of(r, q)));
+                        const float a = j < 0 ? 0.0f : grn_prop(p, max(j, 0), aH, aO, X, s_d);
+                        race(a, E, j, ab, Eb, jb);
+                        const float l = a > 0.0f ? __log2f(a) - __log2f(E) : -CUDART_INF_F;
+                        lmaxp = fmaxf(lmaxp, l);
+                        if (j >= 0 && j < p.M) lj[j] = l;
                     }
                 }
                 warp_race_combine(ab, Eb, jb);
