@@ -53,6 +53,16 @@ void emit(std::string &out, const char *fmt, ...)
     out += buf;
 }
 
+// The event hooks written as selects (bit 1: X -= v_jb, 2: a component of v_jb, 4: X += v_jb, 8: the range
+// check) for networks with up to kJitSelectNnz stoichiometric entries; the others switch on jb. Timed on one
+// box (C2 step: adjoint 0.745 ms with switches, 0.716 with the component as selects, 0.739 with X -= v_jb as
+// selects, 0.713 with both; the oscillator's forward + adjoint 4.75e9 steps/s with switches and with the
+// component as selects, 4.62e9 once X -= v_jb is selects): the component only.
+#ifndef SSA_JIT_SELECT
+#define SSA_JIT_SELECT 2
+#endif
+constexpr int kJitSelectNnz = 48;
+
 int st_species(int e) { return e >> 8; }
 int st_delta(int e) { return (int)(signed char)(e & 0xff); }
 
@@ -75,40 +85,83 @@ std::string jit_source(const ssa_network *net)
         emit(s, "    a[%d] = __fmul_rn(k[%d], h[%d]);\n", j, j, j);
     }
     s += "}\n";
+    // The event-dependent hooks (range check, X += v_jb, X -= v_jb, a component of v_jb) switch on jb, whose
+    // cases the lanes of a warp run one after another when their events differ; up to kJitSelectNnz
+    // stoichiometric entries, the hooks named in SSA_JIT_SELECT are written instead as selects over every entry
+    // (the same results, no divergence; a tuning choice, set by timing both forms).
+    const bool small = net->nnz <= kJitSelectNnz;
+    const bool sel_check = small && (SSA_JIT_SELECT & 8), sel_apply = small && (SSA_JIT_SELECT & 4);
+    const bool sel_unapply = small && (SSA_JIT_SELECT & 1), sel_dv = small && (SSA_JIT_SELECT & 2);
     // range check of X + v_jb (entries in table order; the last failing entry decides)
-    s += "__device__ __forceinline__ int jit_check(const int (&X)[JN], int jb)\n{\n    int st = SSA_TRAJ_OK;\n"
-         "    switch (jb) {\n";
-    for (int j = 0; j < M; ++j) {
-        emit(s, "    case %d:\n", j);
-        for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e) {
-            const int sp = st_species(net->h_st[e]), d = st_delta(net->h_st[e]);
-            if (d < 0) emit(s, "        if (X[%d] + (%d) < 0) st = SSA_TRAJ_NEG_COUNT;\n", sp, d);
-            else if (d > 0) emit(s, "        if (X[%d] > 2147483647 - %d) st = SSA_TRAJ_OVERFLOW;\n", sp, d);
+    s += "__device__ __forceinline__ int jit_check(const int (&X)[JN], int jb)\n{\n    int st = SSA_TRAJ_OK;\n";
+    if (sel_check) {
+        for (int j = 0; j < M; ++j)
+            for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e) {
+                const int sp = st_species(net->h_st[e]), d = st_delta(net->h_st[e]);
+                if (d < 0) emit(s, "    st = (jb == %d && X[%d] + (%d) < 0) ? SSA_TRAJ_NEG_COUNT : st;\n", j, sp, d);
+                else if (d > 0) emit(s, "    st = (jb == %d && X[%d] > 2147483647 - %d) ? SSA_TRAJ_OVERFLOW : st;\n", j, sp, d);
+            }
+    } else {
+        s += "    switch (jb) {\n";
+        for (int j = 0; j < M; ++j) {
+            emit(s, "    case %d:\n", j);
+            for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e) {
+                const int sp = st_species(net->h_st[e]), d = st_delta(net->h_st[e]);
+                if (d < 0) emit(s, "        if (X[%d] + (%d) < 0) st = SSA_TRAJ_NEG_COUNT;\n", sp, d);
+                else if (d > 0) emit(s, "        if (X[%d] > 2147483647 - %d) st = SSA_TRAJ_OVERFLOW;\n", sp, d);
+            }
+            s += "        break;\n";
         }
-        s += "        break;\n";
+        s += "    default: break;\n    }\n";
     }
-    s += "    default: break;\n    }\n    return st;\n}\n";
+    s += "    return st;\n}\n";
     // X += v_jb and X -= v_jb
     for (int dir = 0; dir < 2; ++dir) {
-        emit(s, "__device__ __forceinline__ void %s(int (&X)[JN], int jb)\n{\n    switch (jb) {\n",
-             dir == 0 ? "jit_apply" : "jit_unapply");
+        emit(s, "__device__ __forceinline__ void %s(int (&X)[JN], int jb)\n{\n", dir == 0 ? "jit_apply" : "jit_unapply");
+        if (dir == 0 ? sel_apply : sel_unapply) {
+            // per species, the change of the reaction that fired (a chain of selects over its entries)
+            for (int sp = 0; sp < N; ++sp) {
+                std::string expr = "0";
+                for (int j = M - 1; j >= 0; --j)
+                    for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e)
+                        if (st_species(net->h_st[e]) == sp) {
+                            char buf[64];
+                            snprintf(buf, sizeof(buf), "(jb == %d ? %d : ", j, st_delta(net->h_st[e]));
+                            expr = buf + expr + ")";
+                        }
+                // appended directly: the expression may exceed emit's buffer
+                if (expr != "0") s += "    X[" + std::to_string(sp) + "] " + (dir == 0 ? "+=" : "-=") + " " + expr + ";\n";
+            }
+        } else {
+            s += "    switch (jb) {\n";
+            for (int j = 0; j < M; ++j) {
+                emit(s, "    case %d:\n", j);
+                for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e)
+                    emit(s, "        X[%d] %s %d;\n", st_species(net->h_st[e]), dir == 0 ? "+=" : "-=",
+                         st_delta(net->h_st[e]));
+                s += "        break;\n";
+            }
+            s += "    default: break;\n    }\n";
+        }
+        s += "}\n";
+    }
+    // component sp of v_jb
+    s += "__device__ __forceinline__ int jit_dv(int jb, int sp)\n{\n    int v = 0;\n";
+    if (sel_dv) {
+        for (int j = 0; j < M; ++j)
+            for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e)
+                emit(s, "    v += (jb == %d && sp == %d) ? %d : 0;\n", j, st_species(net->h_st[e]), st_delta(net->h_st[e]));
+    } else {
+        s += "    switch (jb) {\n";
         for (int j = 0; j < M; ++j) {
             emit(s, "    case %d:\n", j);
             for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e)
-                emit(s, "        X[%d] %s %d;\n", st_species(net->h_st[e]), dir == 0 ? "+=" : "-=", st_delta(net->h_st[e]));
+                emit(s, "        if (sp == %d) v += %d;\n", st_species(net->h_st[e]), st_delta(net->h_st[e]));
             s += "        break;\n";
         }
-        s += "    default: break;\n    }\n}\n";
+        s += "    default: break;\n    }\n";
     }
-    // component sp of v_jb
-    s += "__device__ __forceinline__ int jit_dv(int jb, int sp)\n{\n    int v = 0;\n    switch (jb) {\n";
-    for (int j = 0; j < M; ++j) {
-        emit(s, "    case %d:\n", j);
-        for (int e = net->h_rx[j].z; e < net->h_rx[j].w; ++e)
-            emit(s, "        if (sp == %d) v += %d;\n", st_species(net->h_st[e]), st_delta(net->h_st[e]));
-        s += "        break;\n";
-    }
-    s += "    default: break;\n    }\n    return v;\n}\n";
+    s += "    return v;\n}\n";
     // w_j = v_j . lambda, summed over the entries in table order from zero
     s += "__device__ __forceinline__ void jit_w(const float (&lam)[JN], float (&w)[JM])\n{\n";
     for (int j = 0; j < M; ++j) {
