@@ -38,7 +38,7 @@ typedef int32_t ssa_status;
 #define SSA_ERR_INVALID_ARG (-1) /* an argument is out of range or inconsistent */
 #define SSA_ERR_CUDA (-2)        /* a CUDA runtime call failed (text in ssa_last_error) */
 #define SSA_ERR_WORKSPACE (-3)   /* workspace too small or misaligned (need 256-byte alignment) */
-#define SSA_ERR_UNSUPPORTED (-4) /* valid but outside this build's limits (e.g. M > 65535) */
+#define SSA_ERR_UNSUPPORTED (-4) /* valid but outside the library's limits (e.g. M > 65535) */
 #define SSA_ERR_STATE (-5)       /* the run handle cannot serve this call (e.g. not recorded) */
 
 /* per-trajectory status codes */
