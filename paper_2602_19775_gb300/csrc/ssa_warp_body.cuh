@@ -323,23 +323,19 @@ __device__ __forceinline__ float warp_soft_step(const int4 *s_rx, const float *s
         const uint4 r = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)k, c2, c3), key0, key1);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            // predicated: the waiting-time word's slot (j = -1) and the padded ones have rate 0 (they add 0 to
+            // a0 and have key -inf), and the factor is chosen by selects rather than by branches on the order
             const int j = 4 * b + q - 1;
             const float E = neg_log_unit(u01(word_of(r, q)));
-            if (j < 0) {
-                E0 = E;
-                continue;
-            }
+            if (q == 0 && j < 0) E0 = E;
             const int pos = q * nb + b;
             const int4 rx = s_rx[pos];
-            float h = 1.0f;
-            if (rx.x >= 0) {
-                const float x1 = X[rx.x];
-                h = rx.y < 0 ? hs_first(x1) : rx.y == rx.x ? hs_homodimer(x1) : hs_hetero(x1, X[rx.y]);
-            }
+            const float x1 = X[rx.x >= 0 ? rx.x : 0], x2 = X[rx.y >= 0 ? rx.y : 0];
+            const float h = rx.x < 0 ? 1.0f : rx.y < 0 ? hs_first(x1) : rx.y == rx.x ? hs_homodimer(x1) : hs_hetero(x1, x2);
             const float a = __fmul_rn(s_k[pos], h);
             a0p = __fadd_rn(a0p, a);
             const float l = a > 0.0f ? log2f(a) - log2f(E) : -CUDART_INF_F;
-            if (j < M) {
+            if (j >= 0 && j < M) {
                 y[pos] = l;
                 if (AH) {
                     a_out[pos] = a;
@@ -356,12 +352,12 @@ __device__ __forceinline__ float warp_soft_step(const int4 *s_rx, const float *s
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = 4 * b + q - 1;
-            if (j < 0 || j >= M) continue;
+            const bool live = j >= 0 && j < M;
             const int pos = q * nb + b;
-            const float l = y[pos];
+            const float l = live ? y[pos] : -CUDART_INF_F;
             const float w = l == -CUDART_INF_F ? 0.0f : exp2f((l - lmax) * invT);
-            y[pos] = w;
-            Zp += w;
+            if (live) y[pos] = w;
+            Zp += w;  // + 0 outside the live slots: the same bits
         }
     }
     invZ = __fdividef(1.0f, warp_sum(Zp));
