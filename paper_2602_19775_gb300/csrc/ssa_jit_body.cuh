@@ -487,18 +487,28 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
     for (int t = 0; t < NT; ++t) invT[t] = NT == 1 ? p.invT : p.invT_multi[t];
     const float *gl = p.dl_dobs + i * p.dl_stride;
 
+    // The walk's loads are issued well before their use (a load consumed where it is issued stalls the
+    // trajectory for the memory latency): the log row below the current one, the brackets of the next two
+    // samples and the weight of the next, the next checkpoint.
     int row_cached = -1;
-    uint4 row = make_uint4(0, 0, 0, 0);
+    uint4 row = make_uint4(0, 0, 0, 0), row_below = row;
     auto event_at = [&](int kk) -> int {
         const int r = kk >> 3;
-        if (r != row_cached) { row = p.ev[(int64_t)r * n + i]; row_cached = r; }
+        if (r != row_cached) {
+            row = (r == row_cached - 1) ? row_below : p.ev[(int64_t)r * n + i];
+            row_cached = r;
+            if (r > 0) row_below = p.ev[(int64_t)(r - 1) * n + i];
+        }
         const int slot = kk & 7;
         const uint32_t w = word_of(row, slot >> 1);
         return (slot & 1) ? (int)(w >> 16) : (int)(w & 0xffff);
     };
 
     int s_hi = p.S - 1;
-    int brk_next = (READOUT != SSA_READOUT_BIN && s_hi >= 0) ? p.brk_k[(int64_t)s_hi * n + i] : -1;
+    auto brk_k_at = [&](int s) { return (READOUT != SSA_READOUT_BIN && s >= 0) ? p.brk_k[(int64_t)s * n + i] : -1; };
+    auto brk_a_at = [&](int s) { return (READOUT == SSA_READOUT_LINEAR && s >= 0) ? p.brk_a[(int64_t)s * n + i] : 0.0f; };
+    int brk_next = brk_k_at(s_hi), brk_next2 = brk_k_at(s_hi - 1);
+    float a_next = brk_a_at(s_hi), a_top = 0.0f;  // the weights of samples s_hi and s_top
     // BIN: one recorded slot per state interval that holds edges
     BinSlots bslots{-1, -1};
     float d_first = 0.0f, d_last = 0.0f;
@@ -508,6 +518,9 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
     for (int t = 0; t < NT; ++t) mu[t] = 0.0f;
     int mism = 0;
     int ck_row = L / p.K, ck_off = L - ck_row * p.K;  // checkpoint c holds X_{cK}
+    int ckv[JN];
+#pragma unroll
+    for (int s = 0; s < JN; ++s) ckv[s] = p.ckpt[((int64_t)ck_row * JN + s) * n + i];
 
     constexpr int NQ = JM + 1;
     float E[NQ], En[NQ];
@@ -534,11 +547,14 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
         const int s_top = s_hi;
         if (READOUT == SSA_READOUT_BIN) {
             bin_slots_step(bslots, p.brk_k, p.brk_s, p.brk_a, p.ts, n, i, k, s_hi, d_first, d_last);
-        } else {
-            while (s_hi >= 0 && brk_next == k) {
+        } else if (s_hi >= 0 && brk_next == k) {
+            a_top = a_next;
+            do {
                 --s_hi;
-                brk_next = s_hi >= 0 ? p.brk_k[(int64_t)s_hi * n + i] : -1;
-            }
+                brk_next = brk_next2;
+                brk_next2 = brk_k_at(s_hi - 1);
+            } while (s_hi >= 0 && brk_next == k);
+            a_next = brk_a_at(s_hi);
         }
         // samples s_hi+1 .. s_top are bracketed by state k
         if (kBin) {
@@ -574,7 +590,7 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             float dt_dir = 0.0f, dtau_dir = 0.0f;
             if (READOUT == SSA_READOUT_LINEAR) {
                 for (int s = s_hi + 1; s <= s_top; ++s) {
-                    const float alpha = p.brk_a[(int64_t)s * n + i];
+                    const float alpha = s == s_top ? a_top : p.brk_a[(int64_t)s * n + i];
                     if (alpha < 0.0f) continue;
                     float c = 0.0f;
                     for (int o = 0; o < p.n_obs; ++o) {
@@ -642,7 +658,7 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             for (int s = s_hi + 1; s <= s_top; ++s) {
                 float coef = 1.0f;
                 if (READOUT == SSA_READOUT_LINEAR && draw) {
-                    const float alpha = p.brk_a[(int64_t)s * n + i];
+                    const float alpha = s == s_top ? a_top : p.brk_a[(int64_t)s * n + i];
                     if (alpha >= 0.0f) coef = 1.0f - alpha;
                 }
                 for (int o = 0; o < p.n_obs; ++o) {
@@ -661,11 +677,14 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
             fold2(mu[0], mu_lo);
         }
         if (ck_off == 0) {
-            const int *ck = p.ckpt + (int64_t)ck_row * JN * n + i;
 #pragma unroll
-            for (int s = 0; s < JN; ++s) mism += (ck[(int64_t)s * n] != X[s]);
+            for (int s = 0; s < JN; ++s) mism += (ckv[s] != X[s]);
             --ck_row;
             ck_off = p.K;
+            if (ck_row >= 0) {
+#pragma unroll
+                for (int s = 0; s < JN; ++s) ckv[s] = p.ckpt[((int64_t)ck_row * JN + s) * n + i];
+            }
             if constexpr (WIDE) {
                 float m = fabsf(mu[0]);
 #pragma unroll
