@@ -582,7 +582,13 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
                 lmax = fmaxf(lmax, lr[j]);
             }
             mism += (jb != jk);
-            const float tau = waiting_time(E0, a0);
+            // The walk's divisions by a0 (tau = E0/a0 and d tau/d a0 = -tau/a0) take one approximate
+            // reciprocal per step, accurate to 2 ulp where a0 s lies in [2^-126, 2^126]: the power of two s
+            // puts it there. They only enter the gradient (the clock is the forward's), and without the IEEE
+            // division's slow-path branches the step is one block of straight-line code.
+            const float sc_a0 = a0 < 0x1p-126f ? 0x1p24f : (a0 > 0x1p126f ? 0x1p-24f : 1.0f);
+            const float ra0 = __fdividef(1.0f, a0 * sc_a0);
+            const float tau = (E0 * sc_a0) * ra0;
             tau_k = tau;
             // BIN: t_{k+1} ends this interval and starts the next, in the bin of gq
             if (kBin) mu[0] -= bin_transition(xobs, xo, gq, p.n_obs);
@@ -611,7 +617,7 @@ __device__ __forceinline__ void jit_adj_traj(const AdjParams &p, const float (&k
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 const float dtau = WIDE ? (mu[t] + dtau_dir) + mu_lo : mu[t] + dtau_dir;
-                const float dLda0 = -dtau * tau / a0;
+                const float dLda0 = ((-dtau * tau) * sc_a0) * ra0;
                 // pass 2: soft-sample weights y~_j ~ exp2((l_j - l_max)/T) and W = sum y~ w
                 float wr[JM], qr[JM];
                 jit_w(lam[t], wr);
